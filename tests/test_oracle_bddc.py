@@ -1,0 +1,414 @@
+"""Pins of the oracle's BDDC pieces (Sect. 3-4) against what the paper and
+the mathematics fix: brute-force Schur complements and minimisations,
+library eigensolvers, closed forms, the partition of unity, the lemma
+inequalities, and invariances."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import bddc, fem
+from oracle.krylov import gmres
+from paper_2501_01676_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def o222():
+    return bddc.BDDC(W.random_small(1, (2, 2, 2), 3, (-3, 3)), theta_E=1.5)
+
+
+@pytest.fixture(scope="module")
+def o333():
+    return bddc.BDDC(W.random_small(1, (3, 3, 3), 3, (-3, 3)), theta_E=1.5)
+
+
+def rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- Schur system
+def test_schur_sum_equals_global_schur(o222):
+    """sum_i R_i^T S^(i) R_i = A_GG - A_GI A_II^{-1} A_IG of the global matrix."""
+    o = o222
+    A = o.A.toarray()
+    G = o.mesh.gamma
+    I = np.setdiff1d(np.arange(o.mesh.ndof), G)
+    Sg = A[np.ix_(G, G)] - A[np.ix_(G, I)] @ np.linalg.solve(A[np.ix_(I, I)], A[np.ix_(I, G)])
+    np.testing.assert_allclose(o.S_dense(), Sg, rtol=1e-10, atol=1e-12 * np.abs(Sg).max())
+    F = o.F
+    g = F[G] - A[np.ix_(G, I)] @ np.linalg.solve(A[np.ix_(I, I)], F[I])
+    np.testing.assert_allclose(o.condense(), g, rtol=1e-10, atol=1e-12 * np.abs(g).max())
+
+
+def test_recover_reproduces_direct_solution(o222):
+    o = o222
+    u = fem.direct_solve(o.A, o.F)
+    u2 = o.recover(u[o.mesh.gamma])
+    np.testing.assert_allclose(u2, u, rtol=1e-10, atol=1e-13 * np.abs(u).max())
+
+
+def test_classification_counts():
+    """Tensor partition counts: faces, edges, vertices and their sizes."""
+    from oracle.mesh import Mesh
+    m = Mesh([[4, 4]] * 3)
+    assert (len(m.faces), len(m.edges), len(m.vertices)) == (12, 6, 1)
+    assert {len(f['dofs']) for f in m.faces} == {9}
+    assert {len(e['dofs']) for e in m.edges} == {3}
+    m = Mesh([[8] * 4] * 3)
+    assert (len(m.faces), len(m.edges), len(m.vertices)) == (144, 108, 27)
+    assert len(m.gamma) == 7839
+    m = Mesh([[3, 5], [2, 4, 3], [6]])
+    assert all(len(e['subs']) == 4 for e in m.edges)
+
+
+# ---------------------------------------------------------------- scaling
+def test_partition_of_unity(o333):
+    o = o333
+    for ei, e in enumerate(o.mesh.entities):
+        tot = sum(o.D[(ei, k)] for k in e['subs'])
+        np.testing.assert_allclose(tot, np.eye(tot.shape[0]), atol=1e-12)
+
+
+def test_deluxe_average_is_operator_weighted_mean(o333):
+    """The deluxe average w^ = sum_k D^(k) w_k solves sum_k S_XX^(k) (w^ - w_k) = 0."""
+    o = o333
+    r = rng(11)
+    for ei, e in enumerate(o.mesh.entities):
+        if e['kind'] == 'V':
+            continue
+        S = {k: o.S[k][np.ix_(o.pos[(ei, k)], o.pos[(ei, k)])] for k in e['subs']}
+        w = {k: r.standard_normal(len(e['dofs'])) for k in e['subs']}
+        hat = sum(o.D[(ei, k)] @ w[k] for k in e['subs'])
+        res = sum(S[k] @ (hat - w[k]) for k in e['subs'])
+        scale = sum(np.abs(S[k]).max() * np.abs(w[k]).max() for k in e['subs'])
+        assert np.abs(res).max() < 1e-11 * scale
+
+
+# ---------------------------------------------------------------- building blocks
+def test_parallel_sum_properties():
+    r = rng(1)
+    # scalar case
+    assert abs(bddc.parallel_sum(np.array([[2.0]]), np.array([[3.0]]))[0, 0] - 6.0 / 5.0) < 1e-15
+    X = r.standard_normal((6, 6))
+    Y = r.standard_normal((6, 6))
+    A = X @ X.T + 0.1 * np.eye(6)
+    B = Y @ Y.T + 0.1 * np.eye(6)
+    P = bddc.parallel_sum(A, B)
+    np.testing.assert_allclose(P, bddc.parallel_sum(B, A), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(P, np.linalg.inv(np.linalg.inv(A) + np.linalg.inv(B)), rtol=1e-9)
+    assert np.linalg.eigvalsh(A - 0.5 * (P + P.T)).min() > -1e-10
+    assert np.linalg.eigvalsh(B - 0.5 * (P + P.T)).min() > -1e-10
+    # semidefinite: common kernel stays in the kernel
+    v = r.standard_normal(6)
+    Pr = np.eye(6) - np.outer(v, v) / (v @ v)
+    As, Bs = Pr @ A @ Pr, Pr @ B @ Pr
+    Ps = bddc.parallel_sum(As, Bs)
+    assert np.abs(Ps @ v).max() < 1e-10
+
+
+def test_schur_is_minimal_energy(o222):
+    o = o222
+    ei = next(i for i, e in enumerate(o.mesh.entities) if e['kind'] == 'F')
+    k = o.mesh.entities[ei]['subs'][0]
+    p = o.pos[(ei, k)]
+    Bk = o.B[k]
+    Bt = bddc.schur(Bk, p)
+    r = rng(2)
+    wF = r.standard_normal(len(p))
+    rest = np.setdiff1d(np.arange(Bk.shape[0]), p)
+    # brute force: minimise over the free entries by least squares on the normal equations
+    z = np.linalg.lstsq(Bk[np.ix_(rest, rest)], -Bk[np.ix_(rest, p)] @ wF, rcond=None)[0]
+    w = np.zeros(Bk.shape[0]); w[p] = wF; w[rest] = z
+    assert abs(w @ Bk @ w - wF @ Bt @ wF) < 1e-10 * abs(wF @ Bt @ wF)
+    for _ in range(5):
+        w2 = w.copy(); w2[rest] += r.standard_normal(len(rest))
+        assert w2 @ Bk @ w2 >= wF @ Bt @ wF - 1e-12
+
+
+def test_sigma_pencil_matches_eigh_random():
+    r = rng(3)
+    for n in (1, 3, 7, 12):
+        X = r.standard_normal((n, n)); X = X @ X.T
+        Y = r.standard_normal((n, n)); Y = Y @ Y.T + 0.05 * np.eye(n)
+        sig, lam, V = bddc.sigma_pencil(X, Y)
+        ref = np.sort(sla.eigh(X, Y, eigvals_only=True))[::-1]
+        np.testing.assert_allclose(lam, ref, rtol=1e-9, atol=1e-12)
+        ref2 = np.sort(np.linalg.eigvals(np.linalg.solve(Y, X)).real)[::-1]
+        np.testing.assert_allclose(lam, ref2, rtol=1e-8, atol=1e-11)
+        np.testing.assert_allclose(V.T @ (X + Y) @ V, np.eye(n), atol=1e-9)
+
+
+def test_sigma_pencil_singular_rhs():
+    """Directions killed by Y but not X get lambda = inf; common kernel is dropped."""
+    X = np.diag([2.0, 1.0, 0.0, 3.0])
+    Y = np.diag([1.0, 0.0, 0.0, 3.0])
+    sig, lam, V = bddc.sigma_pencil(X, Y)
+    assert len(lam) == 3
+    assert np.isinf(lam[0])
+    np.testing.assert_allclose(np.sort(lam[1:]), [1.0, 2.0])
+    assert len(bddc.select(sig, 10.0)) == 1
+
+
+def test_face_gep_matches_eigh(o333):
+    o = o333
+    checked = 0
+    for ei, info in o.face_info.items():
+        Bt = 0.5 * (info['Bt'] + info['Bt'].T)
+        if np.linalg.eigvalsh(Bt).min() <= 1e-8 * np.abs(Bt).max():
+            continue
+        ref = np.sort(sla.eigh(0.5 * (info['BF'] + info['BF'].T), Bt, eigvals_only=True))[::-1]
+        np.testing.assert_allclose(info['lam'], ref, rtol=1e-8)
+        checked += 1
+    assert checked > 0
+
+
+def test_face_BF_identity(o333):
+    """LHS of the face estimate equals (w_i - w_j)^T B_F (w_i - w_j)."""
+    o = o333
+    r = rng(4)
+    for ei, info in list(o.face_info.items())[:6]:
+        i, j = o.mesh.entities[ei]['subs']
+        D = {i: o.D[(ei, i)], j: o.D[(ei, j)]}
+        BFk = {k: o.B[k][np.ix_(o.pos[(ei, k)], o.pos[(ei, k)])] for k in (i, j)}
+        w = {i: r.standard_normal(D[i].shape[0]), j: r.standard_normal(D[i].shape[0])}
+        lhs = 0.0
+        for a in (i, j):
+            v = sum(D[k] @ (w[a] - w[k]) for k in (i, j))
+            lhs += v @ BFk[a] @ v
+        d = w[i] - w[j]
+        assert abs(lhs - d @ info['BF'] @ d) < 1e-10 * max(1.0, abs(lhs))
+
+
+def test_face_lemma(o333):
+    """Lemma (faces): with the face constraints, LHS <= 2 Theta_F sum w_i^T B^(i) w_i."""
+    o = o333
+    r = rng(5)
+    for ei, info in o.face_info.items():
+        e = o.mesh.entities[ei]
+        i, j = e['subs']
+        pi, pj = o.pos[(ei, i)], o.pos[(ei, j)]
+        Q = info['Q']
+        th = o.theta_F_of(e)
+        BFk = {i: o.B[i][np.ix_(pi, pi)], j: o.B[j][np.ix_(pj, pj)]}
+        D = {i: o.D[(ei, i)], j: o.D[(ei, j)]}
+        for _ in range(20):
+            wi = r.standard_normal(o.B[i].shape[0])
+            wj = r.standard_normal(o.B[j].shape[0])
+            d = wi[pi] - wj[pj]
+            wi[pi] -= Q @ (Q.T @ d)                   # enforce Q^T (w_iF - w_jF) = 0
+            wF = {i: wi[pi], j: wj[pj]}
+            lhs = 0.0
+            for a in (i, j):
+                v = sum(D[k] @ (wF[a] - wF[k]) for k in (i, j))
+                lhs += v @ BFk[a] @ v
+            rhs = 2 * th * (wi @ o.B[i] @ wi + wj @ o.B[j] @ wj)
+            assert lhs <= rhs * (1 + 1e-9) + 1e-12
+
+
+# ---------------------------------------------------------------- new edge GEP
+def edges(o):
+    return [ei for ei, e in enumerate(o.mesh.entities) if e['kind'] == 'E']
+
+
+def test_edge_ME_identity(o333):
+    """w_check^T M_E w_check equals sum_i (w_iE - sum_k D^(k) w_kE)^T B_E^(i) (...)."""
+    o = o333
+    r = rng(6)
+    for ei in edges(o)[:8]:
+        info = o.edge_info[ei]
+        subs = info['subs']
+        n = len(o.mesh.entities[ei]['dofs'])
+        w = {k: r.standard_normal(n) for k in subs}
+        hat = sum(o.D[(ei, k)] @ w[k] for k in subs)
+        lhs = 0.0
+        for k in subs:
+            v = w[k] - hat
+            lhs += v @ o.B[k][np.ix_(o.pos[(ei, k)], o.pos[(ei, k)])] @ v
+        wc = np.concatenate([w[k] - w[subs[0]] for k in subs[1:]])
+        assert abs(lhs - wc @ info['M_E'] @ wc) < 1e-10 * max(1.0, abs(lhs))
+
+
+def edge_brute_force(o, ei):
+    """min over {w_k : w_kE - w_k1E = w_check_k, shared vertex values and shared
+    face primal coordinates equal} of sum_k w_k^T B^(k) w_k, as a quadratic form."""
+    mesh = o.mesh
+    subs = list(mesh.entities[ei]['subs'])
+    sizes = [o.B[k].shape[0] for k in subs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    N = offs[-1]
+    n = len(mesh.entities[ei]['dofs'])
+    Bblk = sla.block_diag(*[o.B[k] for k in subs])
+    rows, rhs = [], []
+    nw = (len(subs) - 1) * n
+    for b, k in enumerate(subs[1:]):
+        for t in range(n):
+            r = np.zeros(N)
+            r[offs[b + 1] + o.pos[(ei, k)][t]] = 1.0
+            r[offs[0] + o.pos[(ei, subs[0])][t]] = -1.0
+            rows.append(r)
+            e = np.zeros(nw); e[b * n + t] = 1.0
+            rhs.append(e)
+    for xj, x in enumerate(mesh.entities):
+        share = [a for a, k in enumerate(subs) if k in x['subs']]
+        if len(share) < 2 or x['kind'] == 'E':
+            continue
+        if x['kind'] == 'V':
+            fun = np.eye(1)
+        else:
+            fun = o.Q[xj].T
+        a0 = share[0]
+        for a in share[1:]:
+            for l in range(fun.shape[0]):
+                r = np.zeros(N)
+                r[offs[a] + o.pos[(xj, subs[a])]] = fun[l]
+                r[offs[a0] + o.pos[(xj, subs[a0])]] = -fun[l]
+                rows.append(r)
+                rhs.append(np.zeros(nw))
+    Ac = np.array(rows)
+    Ec = np.array(rhs)
+    Xp = np.linalg.pinv(Ac) @ Ec
+    Nul = sla.null_space(Ac)
+    BN = Bblk @ Nul
+    red = Bblk - BN @ np.linalg.pinv(Nul.T @ BN, rcond=1e-13) @ BN.T
+    return Xp.T @ red @ Xp
+
+
+def test_edge_BB_brute_force(o222):
+    o = o222
+    for ei in edges(o):
+        BB = o.edge_info[ei]['BB']
+        ref = edge_brute_force(o, ei)
+        np.testing.assert_allclose(BB, ref, rtol=1e-7, atol=1e-9 * np.abs(ref).max())
+
+
+def test_edge_lemma_subspace(o333):
+    """On w_check with (M_E v_l)^T w_check = 0 for the selected l:
+    w_check^T M_E w_check <= Theta_E w_check^T B~~_E w_check."""
+    o = o333
+    r = rng(7)
+    sel_total = 0
+    for ei in edges(o):
+        info = o.edge_info[ei]
+        C = info['M_E'] @ info['V'][:, info['sel']]
+        sel_total += C.shape[1]
+        P = sla.null_space(C.T) if C.shape[1] else np.eye(C.shape[0])
+        for _ in range(20):
+            w = P @ r.standard_normal(P.shape[1])
+            assert w @ info['M_E'] @ w <= o.theta_E * (w @ info['BB'] @ w) * (1 + 1e-8) + 1e-12
+    assert sel_total > 0
+
+
+def test_edge_lemma_full_chain(o333):
+    """For w satisfying vertex, face and edge primal constraints on the
+    subdomains of n(E): sum_i |w_iE - sum_k D^(k) w_kE|^2_{B_E^(i)} <= Theta_E sum_k w_k^T B^(k) w_k."""
+    o = o333
+    mesh = o.mesh
+    r = rng(8)
+    for ei in edges(o)[:10]:
+        subs = list(mesh.entities[ei]['subs'])
+        sizes = [o.B[k].shape[0] for k in subs]
+        offs = np.concatenate([[0], np.cumsum(sizes)])
+        N = offs[-1]
+        rows = []
+        for xj, x in enumerate(mesh.entities):
+            share = [a for a, k in enumerate(subs) if k in x['subs']]
+            if len(share) < 2:
+                continue
+            fun = np.eye(1) if x['kind'] == 'V' else o.Q[xj].T
+            for a in share[1:]:
+                for l in range(fun.shape[0]):
+                    row = np.zeros(N)
+                    row[offs[a] + o.pos[(xj, subs[a])]] = fun[l]
+                    row[offs[share[0]] + o.pos[(xj, subs[share[0]])]] = -fun[l]
+                    rows.append(row)
+        P = sla.null_space(np.array(rows)) if rows else np.eye(N)
+        for _ in range(10):
+            x = P @ r.standard_normal(P.shape[1])
+            w = {k: x[offs[a]:offs[a + 1]] for a, k in enumerate(subs)}
+            wE = {k: w[k][o.pos[(ei, k)]] for k in subs}
+            hat = sum(o.D[(ei, k)] @ wE[k] for k in subs)
+            lhs = sum((wE[k] - hat) @ o.B[k][np.ix_(o.pos[(ei, k)], o.pos[(ei, k)])] @ (wE[k] - hat)
+                      for k in subs)
+            rhs = o.theta_E * sum(w[k] @ o.B[k] @ w[k] for k in subs)
+            assert lhs <= rhs * (1 + 1e-8) + 1e-12
+
+
+def test_edge_reference_invariance(o333):
+    """Another reference subdomain gives the same eigenvalues and Q_E span."""
+    o = o333
+    for ei in edges(o)[:6]:
+        a = o.edge_info[ei]
+        subs = a['subs']
+        b = o.edge_gep_new(ei, ref=subs[2])
+        fa, fb = np.isfinite(a['lam']), np.isfinite(b['lam'])
+        np.testing.assert_allclose(a['lam'][fa], b['lam'][fb], rtol=1e-7)
+        assert a['Q'].shape == b['Q'].shape
+        if a['Q'].shape[1]:
+            sv = np.linalg.svd(a['Q'].T @ b['Q'], compute_uv=False)
+            np.testing.assert_allclose(sv, 1.0, atol=1e-7)
+
+
+def test_new_edge_gep_fewer_primals_than_old():
+    """On random-coefficient cases the new edge GEP selects no more edge primals."""
+    for seed in (1, 2):
+        p = W.random_small(seed, (3, 3, 3), 3, (-3, 3))
+        new = bddc.BDDC(p)
+        old = bddc.BDDC(p, edge_gep='old')
+        assert new.pnumE <= old.pnumE
+        assert new.pnumF == old.pnumF
+
+
+# ---------------------------------------------------------------- preconditioner
+def test_all_primal_is_exact_solve():
+    p = W.random_small(3, (2, 2, 2), 3, (-2, 1))
+    o = bddc.BDDC(p, all_primal=True)
+    Sg = o.S_dense()
+    np.testing.assert_allclose(o.M_dense() @ Sg, np.eye(o.nG), atol=1e-9)
+    u, info = o.solve()
+    assert info['iters'] == 1 and info['true_relres'] < 1e-12
+
+
+def test_two_routes_agree(o333):
+    """KKT (constrained local solves + coarse) equals S~ assembled on W~."""
+    o = o333
+    St, Rt = o.wtilde_operator()
+    r = rng(9)
+    for _ in range(3):
+        v = r.standard_normal(o.nG)
+        z1, z2 = o.apply_M(v), o.apply_M_wtilde(v, St, Rt)
+        np.testing.assert_allclose(z1, z2, rtol=1e-9, atol=1e-11 * np.abs(z1).max())
+
+
+def test_bddc_gmres_matches_direct_solution(o333):
+    o = o333
+    ustar = fem.direct_solve(o.A, o.F)
+    u, info = o.solve(rtol=1e-12)
+    assert info['converged']
+    assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < 1e-9
+    u0, info0 = o.solve(rtol=1e-12, precondition=False)
+    assert np.linalg.norm(u0 - ustar) / np.linalg.norm(ustar) < 1e-8
+    assert info['iters'] < info0['iters']
+
+
+def test_more_constraints_do_not_slow_convergence():
+    p = W.random_small(2, (3, 3, 3), 3, (-3, 3))
+    base = bddc.BDDC(p).solve()[1]['iters']
+    more = bddc.BDDC(p, theta_E=1.0, theta_F=1.0).solve()[1]['iters']
+    none = bddc.BDDC(p, face_gep=False, edge_gep='none').solve()[1]['iters']
+    assert more <= base <= none + 2
+    assert more <= 5
+
+
+def test_gmres_is_minimal_residual():
+    """Each GMRES iterate minimises ||b - A x|| over the Krylov space (brute force)."""
+    r = rng(10)
+    n = 30
+    A = np.eye(n) * 3 + r.standard_normal((n, n)) * 0.4
+    b = r.standard_normal(n)
+    for k in (1, 3, 7):
+        x, info = gmres(lambda v: A @ v, b, rtol=0.0, max_iter=k)
+        K = np.array([np.linalg.matrix_power(A, j) @ b for j in range(k)]).T
+        y = np.linalg.lstsq(A @ K, b, rcond=None)[0]
+        ref = np.linalg.norm(b - A @ K @ y)
+        assert abs(np.linalg.norm(b - A @ x) - ref) < 1e-9 * np.linalg.norm(b)
+    x, info = gmres(lambda v: A @ v, b, rtol=1e-12, restart=7, max_iter=300)
+    assert info['converged'] and info['relres'] < 1e-11
