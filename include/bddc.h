@@ -1,0 +1,186 @@
+/*
+ * bddc.h -- C ABI of libbddc: adaptive BDDC-preconditioned GMRES for the
+ * stabilised advection-diffusion system of arXiv 2501.01676 on one GB300.
+ *
+ * The model problem (Sect. 2) is -div(nu grad u) + beta.grad u + c u = f on a
+ * box with u = 0 on its boundary, discretised by trilinear hexahedra with the
+ * stabilised forms a = b + z and load g of Sect. 2.  The box is cut into a
+ * tensor partition of subdomains (Sect. 3); the library solves the interface
+ * Schur system (eq. Schur-complex-sys) with GMRES preconditioned by
+ * M^-1 = R~^T D~ S~^-1 D~^T R~ (Sect. 3) whose coarse space holds vertex
+ * constraints, adaptive face constraints (face GEP, eq. equ-4-8) and adaptive
+ * edge constraints from the edge GEP on prior-selected primal constraints
+ * (eq. equ-5-21, constraints eq. equ-5-22), then recovers the interior
+ * unknowns.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 (BDDC_OK) on success, BDDC_NOT_CONVERGED (positive, the
+ *     result is still written), or a negative error code.  Nothing aborts or
+ *     traps; every device wait and iteration is bounded.
+ *   - Numbering: elements e = ex + Ex*(ey + Ey*ez); nodes
+ *     n = ix + (Ex+1)*(iy + (Ey+1)*iz); free (non-Dirichlet) dofs
+ *     d = (ix-1) + (Ex-1)*((iy-1) + (Ey-1)*(iz-1)).  Interface vectors
+ *     (length n_gamma) list the interface dofs in ascending dof id.
+ *   - Calls are ordered on the CUDA stream given at setup.  All device memory
+ *     the solver needs is owned by the context; the caller owns its own
+ *     buffers.  One context must not be used by two host threads at once.
+ *   - There is no CPU fallback: without a usable GPU every call fails with
+ *     BDDC_ECUDA.
+ */
+#ifndef BDDC_H
+#define BDDC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BDDC_OK              0
+#define BDDC_NOT_CONVERGED   1
+#define BDDC_EINVAL        (-1)   /* bad argument                                  */
+#define BDDC_ENOMEM        (-2)   /* device or host allocation failed              */
+#define BDDC_ECUDA         (-3)   /* CUDA runtime error / no GPU                   */
+#define BDDC_EGEP          (-4)   /* eigen iteration cap reached in a GEP          */
+#define BDDC_ETIMEOUT      (-5)   /* bounded device wait gave up                   */
+#define BDDC_ENUMERIC      (-6)   /* zero or non-finite pivot in a factorisation   */
+
+#define BDDC_MEM_DEVICE 0
+#define BDDC_MEM_HOST   1
+
+#define BDDC_PREC_FP64  0   /* every factor and operator in FP64                  */
+#define BDDC_PREC_MIXED 1   /* FP32 factors/operators + FP64 iterative refinement  */
+
+#define BDDC_EDGE_NONE 0
+#define BDDC_EDGE_NEW  1    /* edge GEP on prior-selected primal constraints      */
+
+/* Box [lo, hi]^3; the unit cube when both are zero. */
+typedef struct { double lo[3], hi[3]; } bddc_mesh;
+
+/* Tensor partition: direction d is cut into nsub[d] slabs, slab s holding
+ * elems_per_slab[d][s] >= 1 elements (host pointers, copied). Element
+ * spacing is uniform per direction. */
+typedef struct { int nsub[3]; const int* elems_per_slab[3]; } bddc_partition;
+
+/* Coefficients (Sect. 2).  All arrays are FP64, in host or device memory as
+ * `mem` says, and are copied at setup.
+ *   nu_elem   [nelem]      viscosity per element, > 0
+ *   beta_node [3*nnodes]   velocity at the nodes (x,y,z interleaved) or NULL,
+ *                          in which case beta_const is used everywhere
+ *   f_node    [nnodes]     source at the nodes, or NULL (f = 0)
+ *   divb_node [nnodes]     div(beta) at the nodes, or NULL (0)
+ * beta, f and div(beta) are interpolated trilinearly inside each element. */
+typedef struct {
+    const double* nu_elem;
+    const double* beta_node;
+    double beta_const[3];
+    double c;
+    const double* f_node;
+    const double* divb_node;
+    int mem;
+} bddc_coeffs;
+
+typedef struct {
+    double theta_E;        /* edge threshold Theta_E (Sect. 4: 10)                 */
+    double theta_F;        /* face threshold; <= 0: 1 + ln(H/h) per face (Sect. 4) */
+    double tau;            /* stabilisation constant (Sect. 2: 0.7)               */
+    int precision;         /* BDDC_PREC_FP64 or BDDC_PREC_MIXED                    */
+    int restart;           /* GMRES restart length, 0: no restart                 */
+    int max_iter;          /* iteration cap (Sect. 4: 300)                        */
+    double rtol;           /* relative residual target (Sect. 4: 1e-8)            */
+    int edge_gep;          /* BDDC_EDGE_NONE or BDDC_EDGE_NEW                      */
+    int face_gep;          /* 1: adaptive face constraints, 0: none               */
+    int all_primal;        /* 1: every interface dof primal (exact solver check)   */
+    double inner_rtol;     /* MIXED: inner GMRES tolerance per refinement step     */
+    int max_refine;        /* MIXED: refinement step cap                           */
+    double learned_skip_p; /* < 0: no learned skip; else skip an edge GEP when the
+                              loaded network gives P(no constraint) >= this        */
+} bddc_opts;
+
+typedef struct {
+    int iters;               /* GMRES iterations (all refinement steps)           */
+    int refine_steps;        /* MIXED: outer steps, FP64: 1                        */
+    int converged;
+    double relres;           /* FP64: ||g - S u_G|| / ||g|| on the Schur system;
+                                MIXED: ||F - A u|| / ||F|| of the global system   */
+    double relres_global;    /* ||F - A u|| / ||F|| in FP64 (both modes)           */
+    int pnumF, pnumE;        /* face / edge primal unknowns (Sect. 4 tables)       */
+    int n_pi;                /* coarse size: vertices + pnumF + pnumE             */
+    int n_gamma, ndof, nsub;
+    int edges_skipped;       /* edge GEPs skipped by the learned predictor         */
+    double setup_ms, solve_ms;
+    double t_assemble_ms, t_factor_ms, t_face_ms, t_edge_ms, t_coarse_ms;
+} bddc_stats;
+
+typedef struct bddc_ctx bddc_ctx;
+
+/* Fill `o` with the defaults of Sect. 4: Theta_E = 10, Theta_F = 1 + ln(H/h),
+ * tau = 0.7, FP64, no restart, 300 iterations, rtol 1e-8, new edge GEP,
+ * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip. */
+void bddc_default_opts(bddc_opts* o);
+
+/* Setup (call stack: assembly, batched Dirichlet factorisation + Schur
+ * complements S^(i) (Sect. 3), deluxe scaling, face GEPs, new edge GEPs,
+ * constrained local solvers, coarse matrix and its FP64 inverse).
+ * tol_eig > 0 overrides opts->theta_E.  stream: a cudaStream_t or NULL for
+ * the legacy default stream.  On success *out owns all device memory. */
+int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs,
+               const bddc_partition* part, double tol_eig,
+               const bddc_opts* opts, void* stream, bddc_ctx** out);
+
+/* z = M^-1 r on the interface (Sect. 3, M_BDDC^-1).  r, z: device FP64,
+ * n_gamma x nrhs column blocks (column j at offset j*n_gamma). */
+int bddc_apply(bddc_ctx* ctx, const double* r_dev, double* z_dev, int nrhs);
+
+/* y = S x = sum_i R_i^T S^(i) R_i x on the interface (eq. Schur-complex-sys).
+ * Device FP64, n_gamma x nrhs. */
+int bddc_schur_apply(bddc_ctx* ctx, const double* x_dev, double* y_dev, int nrhs);
+
+/* Full solve: condense the load onto the interface, right-preconditioned
+ * GMRES (Sect. 4 stopping rule), recover the interior unknowns.
+ * load: assembled nodal loads on the free dofs (ndof x nrhs) or NULL to use
+ * the load of the coefficients (Sect. 2, g(v)); u: ndof x nrhs output.
+ * mem: BDDC_MEM_DEVICE or BDDC_MEM_HOST for both pointers (host pointers are
+ * staged through device buffers inside the call).  stats may be NULL. */
+int bddc_gmres_solve(bddc_ctx* ctx, const double* load, double* u, int nrhs,
+                     int mem, bddc_stats* stats);
+
+int  bddc_get_stats(const bddc_ctx* ctx, bddc_stats* stats);
+void bddc_destroy(bddc_ctx* ctx);
+const char* bddc_strerror(int code);
+
+/* ---- introspection (tests and benchmarks; host output buffers) ---------- */
+
+/* Global dof id of each interface position (n_gamma ints). */
+int bddc_get_numbering(const bddc_ctx* ctx, int* gamma_dofs);
+
+/* S^(s) (n_B x n_B, row-major, local interface order = ascending dof id) in
+ * FP64 (converted when MIXED).  Pass out = NULL to query *n_b only. */
+int bddc_get_schur(const bddc_ctx* ctx, int s, double* out, int* n_b);
+
+/* Entities: kind 0 vertex, 1 edge, 2 face; index within its kind in the
+ * library's order.  Writes the sorted subdomain set (subs[8], -1 padded),
+ * the entity's dof ids (dofs[n]), its primal count k and, for faces and
+ * edges, the orthonormal constraint basis Q (n x k, column-major) and the
+ * GEP eigenvalues lambda (ascending sigma order reversed: largest first,
+ * +inf for infinite, up to n values; count in *n_eig).  NULL outputs are
+ * skipped.  *n returns the entity size. */
+int bddc_get_entity_count(const bddc_ctx* ctx, int kind);
+int bddc_get_entity(const bddc_ctx* ctx, int kind, int index, int* subs,
+                    int* dofs, int* n, int* k, double* Q, double* lambda,
+                    int* n_eig);
+
+/* ---- learned edge-GEP skip (BASELINE pattern: MLP, FP32) --------------- */
+
+#define BDDC_MLP_FEATURES 10
+#define BDDC_MLP_HIDDEN   64
+#define BDDC_MLP_CLASSES  8
+
+/* Edge features (n_edges x BDDC_MLP_FEATURES, FP32 host) and the edge GEP's
+ * constraint counts (n_edges ints, -1 when the GEP was skipped). */
+int bddc_get_edge_features(const bddc_ctx* ctx, float* feats, int* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libbddc (argument marshalling only).
+
+Names follow the C ABI in ``include/bddc.h``.  Device buffers are torch CUDA
+tensors (PyTorch provides memory and streams); every step of setup and solve
+runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbddc.so")
+
+OK, NOT_CONVERGED = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+EDGE_NONE, EDGE_NEW = 0, 1
+
+
+class Mesh(ct.Structure):
+    _fields_ = [("lo", ct.c_double * 3), ("hi", ct.c_double * 3)]
+
+
+class Partition(ct.Structure):
+    _fields_ = [("nsub", ct.c_int * 3), ("elems_per_slab", ct.POINTER(ct.c_int) * 3)]
+
+
+class Coeffs(ct.Structure):
+    _fields_ = [("nu_elem", ct.c_void_p), ("beta_node", ct.c_void_p), ("beta_const", ct.c_double * 3),
+                ("c", ct.c_double), ("f_node", ct.c_void_p), ("divb_node", ct.c_void_p), ("mem", ct.c_int)]
+
+
+class Opts(ct.Structure):
+    _fields_ = [("theta_E", ct.c_double), ("theta_F", ct.c_double), ("tau", ct.c_double),
+                ("precision", ct.c_int), ("restart", ct.c_int), ("max_iter", ct.c_int),
+                ("rtol", ct.c_double), ("edge_gep", ct.c_int), ("face_gep", ct.c_int),
+                ("all_primal", ct.c_int), ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
+                ("learned_skip_p", ct.c_double)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("iters", ct.c_int), ("refine_steps", ct.c_int), ("converged", ct.c_int),
+                ("relres", ct.c_double), ("relres_global", ct.c_double), ("pnumF", ct.c_int),
+                ("pnumE", ct.c_int), ("n_pi", ct.c_int), ("n_gamma", ct.c_int), ("ndof", ct.c_int),
+                ("nsub", ct.c_int), ("edges_skipped", ct.c_int), ("setup_ms", ct.c_double),
+                ("solve_ms", ct.c_double), ("t_assemble_ms", ct.c_double), ("t_factor_ms", ct.c_double),
+                ("t_face_ms", ct.c_double), ("t_edge_ms", ct.c_double), ("t_coarse_ms", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libbddc.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libbddc.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ct.CDLL(LIB_PATH)
+    vp, ip, dp = ct.c_void_p, ct.POINTER(ct.c_int), ct.POINTER(ct.c_double)
+    L.bddc_default_opts.argtypes = [ct.POINTER(Opts)]
+    L.bddc_setup.argtypes = [ct.POINTER(Mesh), ct.POINTER(Coeffs), ct.POINTER(Partition), ct.c_double,
+                             ct.POINTER(Opts), vp, ct.POINTER(vp)]
+    L.bddc_apply.argtypes = [vp, vp, vp, ct.c_int]
+    L.bddc_schur_apply.argtypes = [vp, vp, vp, ct.c_int]
+    L.bddc_gmres_solve.argtypes = [vp, vp, vp, ct.c_int, ct.c_int, ct.POINTER(Stats)]
+    L.bddc_get_stats.argtypes = [vp, ct.POINTER(Stats)]
+    L.bddc_destroy.argtypes = [vp]
+    L.bddc_strerror.argtypes = [ct.c_int]
+    L.bddc_strerror.restype = ct.c_char_p
+    L.bddc_get_numbering.argtypes = [vp, ip]
+    L.bddc_get_schur.argtypes = [vp, ct.c_int, dp, ip]
+    L.bddc_get_entity_count.argtypes = [vp, ct.c_int]
+    L.bddc_get_entity.argtypes = [vp, ct.c_int, ct.c_int, ip, ip, ip, ip, dp, dp, ip]
+    L.bddc_get_edge_features.argtypes = [vp, ct.POINTER(ct.c_float), ip]
+    _lib = L
+    return L
+
+
+EXPORTED = ["bddc_default_opts", "bddc_setup", "bddc_apply", "bddc_schur_apply", "bddc_gmres_solve",
+            "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_get_numbering", "bddc_get_schur",
+            "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features"]
+
+
+class BDDCError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib().bddc_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+def check(code, where):
+    if code < 0:
+        raise BDDCError(code, where)
+    return code
+
+
+def default_opts(**kw):
+    o = Opts()
+    lib().bddc_default_opts(ct.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One setup of the adaptive BDDC solver on the current CUDA device.
+
+    problem: a ``workloads.Problem``; host=True passes the coefficient arrays
+    from host memory, otherwise they are first placed on the device.
+    """
+
+    def __init__(self, problem, host=False, stream=None, **opts):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libbddc needs a CUDA GPU")
+        L = lib()
+        self.torch = torch
+        self.problem = problem
+        o = default_opts(theta_E=problem.theta_E, restart=problem.restart, rtol=problem.rtol,
+                         max_iter=problem.max_iter)
+        if problem.theta_F is not None:
+            o.theta_F = problem.theta_F
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.opts = o
+        part = Partition()
+        self._slabs = []
+        for d in range(3):
+            arr = (ct.c_int * len(problem.slabs[d]))(*[int(v) for v in problem.slabs[d]])
+            self._slabs.append(arr)
+            part.nsub[d] = len(problem.slabs[d])
+            part.elems_per_slab[d] = ct.cast(arr, ct.POINTER(ct.c_int))
+        mesh = Mesh()
+        co = Coeffs()
+        self._keep = []
+        fields = {"nu_elem": problem.nu_elem, "beta_node": problem.beta_node, "f_node": problem.f_node}
+        for name, arr in fields.items():
+            if arr is None:
+                setattr(co, name, None)
+                continue
+            a = np.ascontiguousarray(arr, dtype=np.float64).ravel()
+            if host:
+                self._keep.append(a)
+                setattr(co, name, a.ctypes.data)
+            else:
+                t = torch.from_numpy(a).cuda()
+                self._keep.append(t)
+                setattr(co, name, t.data_ptr())
+        co.c = float(problem.c)
+        co.mem = MEM_HOST if host else MEM_DEVICE
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ctx = ct.c_void_p()
+        check(L.bddc_setup(ct.byref(mesh), ct.byref(co), ct.byref(part), 0.0, ct.byref(o),
+                           ct.c_void_p(self.stream.cuda_stream), ct.byref(ctx)), "bddc_setup")
+        self.ctx = ctx
+        self._keep = []
+        st = Stats()
+        L.bddc_get_stats(ctx, ct.byref(st))
+        self.n_gamma = st.n_gamma
+        self.ndof = st.ndof
+        self.nsub = st.nsub
+        self.setup_stats = st.as_dict()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().bddc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self):
+        st = Stats()
+        check(lib().bddc_get_stats(self.ctx, ct.byref(st)), "bddc_get_stats")
+        return st.as_dict()
+
+    def schur_apply(self, x):
+        y = self.torch.empty_like(x)
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        xx = x if x.dim() == 1 else x.t().contiguous()
+        yy = self.torch.empty_like(xx)
+        check(lib().bddc_schur_apply(self.ctx, _ptr(xx), _ptr(yy), nrhs), "bddc_schur_apply")
+        return yy if x.dim() == 1 else yy.t().contiguous()
+
+    def apply(self, r):
+        nrhs = 1 if r.dim() == 1 else r.shape[1]
+        rr = r if r.dim() == 1 else r.t().contiguous()
+        zz = self.torch.empty_like(rr)
+        check(lib().bddc_apply(self.ctx, _ptr(rr), _ptr(zz), nrhs), "bddc_apply")
+        return zz if r.dim() == 1 else zz.t().contiguous()
+
+    def solve(self, load=None, host=False):
+        """Full solve; returns (u, stats).  load: (ndof,) or (ndof, nrhs) array/tensor or None."""
+        torch = self.torch
+        st = Stats()
+        if host:
+            nrhs = 1 if load is None or np.ndim(load) == 1 else load.shape[1]
+            u = np.zeros((nrhs, self.ndof))
+            lp = None
+            if load is not None:
+                lh = np.ascontiguousarray(np.asarray(load, dtype=np.float64).reshape(self.ndof, nrhs).T)
+                lp = lh.ctypes.data
+            rc = lib().bddc_gmres_solve(self.ctx, lp, u.ctypes.data, nrhs, MEM_HOST, ct.byref(st))
+            check(rc, "bddc_gmres_solve")
+            return (u[0] if nrhs == 1 else u.T), st.as_dict()
+        if load is None:
+            u = torch.empty(self.ndof, dtype=torch.float64, device="cuda")
+            rc = lib().bddc_gmres_solve(self.ctx, None, _ptr(u), 1, MEM_DEVICE, ct.byref(st))
+        else:
+            lt = load if isinstance(load, torch.Tensor) else torch.from_numpy(np.asarray(load, dtype=np.float64))
+            lt = lt.to("cuda", torch.float64)
+            nrhs = 1 if lt.dim() == 1 else lt.shape[1]
+            lc = lt if lt.dim() == 1 else lt.t().contiguous()
+            u = torch.empty_like(lc)
+            rc = lib().bddc_gmres_solve(self.ctx, _ptr(lc), _ptr(u), nrhs, MEM_DEVICE, ct.byref(st))
+            if nrhs > 1:
+                u = u.t().contiguous()
+        check(rc, "bddc_gmres_solve")
+        return u, st.as_dict()
+
+    # ---- introspection -------------------------------------------------
+    def numbering(self):
+        out = (ct.c_int * self.n_gamma)()
+        check(lib().bddc_get_numbering(self.ctx, out), "bddc_get_numbering")
+        return np.frombuffer(out, dtype=np.int32).copy()
+
+    def schur(self, s):
+        nb = ct.c_int()
+        check(lib().bddc_get_schur(self.ctx, s, None, ct.byref(nb)), "bddc_get_schur")
+        out = np.zeros((nb.value, nb.value))
+        check(lib().bddc_get_schur(self.ctx, s, out.ctypes.data_as(ct.POINTER(ct.c_double)), ct.byref(nb)),
+              "bddc_get_schur")
+        return out
+
+    def entities(self, kind):
+        L = lib()
+        cnt = check(L.bddc_get_entity_count(self.ctx, kind), "bddc_get_entity_count")
+        out = []
+        for i in range(cnt):
+            subs = (ct.c_int * 8)()
+            n, k, ne = ct.c_int(), ct.c_int(), ct.c_int()
+            check(L.bddc_get_entity(self.ctx, kind, i, subs, None, ct.byref(n), ct.byref(k), None, None,
+                                    ct.byref(ne)), "bddc_get_entity")
+            dofs = (ct.c_int * n.value)()
+            Q = np.zeros(max(n.value * k.value, 1))
+            lam = np.zeros(max(3 * n.value, 1))
+            check(L.bddc_get_entity(self.ctx, kind, i, subs, dofs, ct.byref(n), ct.byref(k),
+                                    Q.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                    lam.ctypes.data_as(ct.POINTER(ct.c_double)), ct.byref(ne)),
+                  "bddc_get_entity")
+            out.append(dict(subs=tuple(s for s in subs if s >= 0), dofs=np.array(dofs[:], dtype=int),
+                            k=k.value, Q=Q[:n.value * k.value].reshape(k.value, n.value).T,
+                            lam=lam[:ne.value].copy()))
+        return out

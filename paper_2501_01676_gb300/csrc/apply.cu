@@ -1,0 +1,316 @@
+// Per-iteration operators of the Schur system (Sect. 3) on the GPU.
+//
+// One kernel serves every dense per-subdomain product of the hot loop:
+//   out[oidx[r]] += sum_c M[r][c] * in[iidx[c]]     (gather -> GEMV -> scatter-add)
+// * S x          : M = S^(i),                 iidx = oidx = R_i (interface map)
+// * M^-1 r, part 1: M = [P_i ; (D_i Psi_i)^T], iidx = R_i, oidx = [R_i ; R_Pi_i]
+// * coarse solve : M = S_Pi^{-1} (FP64),      iidx = oidx = identity on the coarse space
+// * M^-1 r, part 3: M = D_i Phi_i,            iidx = R_Pi_i, oidx = R_i
+// The matrices are packed per subdomain with 16-byte aligned rows and are
+// streamed once per product with 128-bit loads; the gathered input of a
+// subdomain sits in shared memory; a warp reduces each row with shuffles and
+// scatters with FP64 atomics.  Work items are (matrix, 32-row slice), all
+// subdomains of uneven size in one launch.
+#include <cuda_runtime.h>
+
+#include "bddc_internal.h"
+
+namespace {
+
+constexpr int GEMV_THREADS = 256;
+constexpr int GEMV_MAXCOLS = 2048;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class T>
+struct Vec;
+template <>
+struct Vec<double> {
+    typedef double2 type;
+    static constexpr int W = 2;
+};
+template <>
+struct Vec<float> {
+    typedef float4 type;
+    static constexpr int W = 4;
+};
+
+template <class T>
+__device__ __forceinline__ T dot_vec(const typename Vec<T>::type& a, const T* x);
+template <>
+__device__ __forceinline__ double dot_vec<double>(const double2& a, const double* x) {
+    return a.x * x[0] + a.y * x[1];
+}
+template <>
+__device__ __forceinline__ float dot_vec<float>(const float4& a, const float* x) {
+    return a.x * x[0] + a.y * x[1] + a.z * x[2] + a.w * x[3];
+}
+
+template <class T>
+__global__ void __launch_bounds__(GEMV_THREADS) k_gemv(const T* __restrict__ pool,
+                                                       const GemvItem* __restrict__ items,
+                                                       const int* __restrict__ idx,
+                                                       const double* __restrict__ in,
+                                                       double* __restrict__ out, int nrhs,
+                                                       int in_ld, int out_ld,
+                                                       const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const GemvItem it = items[blockIdx.x];
+    __shared__ __align__(16) T xs[GEMV_MAXCOLS];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int* iidx = idx + it.iidx_off;
+    const int* oidx = idx + it.oidx_off;
+    const T* M = pool + it.moff;
+    constexpr int VW = Vec<T>::W;
+    typedef typename Vec<T>::type VT;
+    const int nvec = it.cols / VW;
+    for (int c = 0; c < nrhs; ++c) {
+        const double* inc = in + (long long)c * in_ld;
+        double* outc = out + (long long)c * out_ld;
+        for (int q = t; q < it.cols; q += GEMV_THREADS) xs[q] = (T)inc[iidx[q]];
+        __syncthreads();
+        for (int r = it.row0 + wid; r < it.row0 + it.nrows; r += GEMV_THREADS / 32) {
+            const T* row = M + (long long)r * it.ld;
+            const VT* rv = reinterpret_cast<const VT*>(row);
+            T acc = (T)0;
+            for (int v = lane; v < nvec; v += 32) acc += dot_vec<T>(__ldg(rv + v), xs + v * VW);
+            for (int q = nvec * VW + lane; q < it.cols; q += 32) acc += row[q] * xs[q];
+            acc = warp_sum(acc);
+            if (lane == 0) atomicAdd(&outc[oidx[r]], (double)acc);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+template <class T>
+int gemv_run(const T* pool, const GemvItem* items_dev, int nitems, const int* idx, const double* in,
+             double* out, int maxcols, int nrhs, int in_ld, int out_ld, cudaStream_t st,
+             const int* skip) {
+    if (nitems <= 0) return BDDC_OK;
+    if (maxcols > GEMV_MAXCOLS) return BDDC_EINVAL;
+    k_gemv<T><<<nitems, GEMV_THREADS, 0, st>>>(pool, items_dev, idx, in, out, nrhs, in_ld, out_ld,
+                                               skip);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
+template int gemv_run<double>(const double*, const GemvItem*, int, const int*, const double*,
+                              double*, int, int, int, int, cudaStream_t, const int*);
+template int gemv_run<float>(const float*, const GemvItem*, int, const int*, const double*, double*,
+                             int, int, int, int, cudaStream_t, const int*);
+
+// ---------------------------------------------------------------------------
+// Condensation and interior recovery with the factors of the partial LU of
+// A^(i) = [[L_II, 0], [L_BI, I]] [[U_II, U_IB], [0, S^(i)]]   (Sect. 3):
+//   y_i = L_II^{-1} f_I,  g -= R_i^T L_BI y_i          (g^(i) = f_B - A_BI A_II^{-1} f_I)
+//   u_I = U_II^{-1} (y_i - U_IB u_B)                   (u_I = A_II^{-1}(f_I - A_IB u_B))
+// One CTA per subdomain; blocked substitution: one warp solves each 32 x 32
+// diagonal block with shuffles, all warps update the remaining rows.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int TRI_THREADS = 256;
+constexpr int TRI_MAXN = 2048;
+
+struct TriItem {
+    long long aoff;    // matrix offset in the factor pool
+    int n, nI, ld;
+    int dof_off;       // offset of the local dof list (n entries: I then B)
+    int gidx_off;      // offset of the interface -> Gamma list (nB entries)
+    long long yoff;    // offset of the stored y_i (nI entries)
+};
+
+template <class T>
+__device__ void fwd_unit_lower(const T* A, int ld, int nI, double* y) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int b0 = 0; b0 < nI; b0 += 32) {
+        const int bw = min(32, nI - b0);
+        if (wid == 0) {
+            double v = lane < bw ? y[b0 + lane] : 0.0;
+            for (int k = 0; k < bw; ++k) {
+                double vk = __shfl_sync(0xffffffffu, v, k);
+                if (lane > k && lane < bw) v -= (double)A[(long long)(b0 + lane) * ld + b0 + k] * vk;
+            }
+            if (lane < bw) y[b0 + lane] = v;
+        }
+        __syncthreads();
+        for (int r = b0 + bw + wid; r < nI; r += TRI_THREADS / 32) {
+            double s = lane < bw ? (double)A[(long long)r * ld + b0 + lane] * y[b0 + lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) y[r] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__device__ void bwd_upper(const T* A, int ld, int nI, double* y) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int b1 = nI; b1 > 0; b1 -= 32) {
+        const int b0 = max(0, b1 - 32);
+        const int bw = b1 - b0;
+        if (wid == 0) {
+            double v = lane < bw ? y[b0 + lane] : 0.0;
+            for (int k = bw - 1; k >= 0; --k) {
+                if (lane == k) v /= (double)A[(long long)(b0 + k) * ld + b0 + k];
+                double vk = __shfl_sync(0xffffffffu, v, k);
+                if (lane < k) v -= (double)A[(long long)(b0 + lane) * ld + b0 + k] * vk;
+            }
+            if (lane < bw) y[b0 + lane] = v;
+        }
+        __syncthreads();
+        for (int r = wid; r < b0; r += TRI_THREADS / 32) {
+            double s = lane < bw ? (double)A[(long long)r * ld + b0 + lane] * y[b0 + lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) y[r] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TRI_THREADS) k_condense(const T* __restrict__ pool,
+                                                          const TriItem* __restrict__ items,
+                                                          const int* __restrict__ lists,
+                                                          const double* __restrict__ F,
+                                                          double* __restrict__ g,
+                                                          double* __restrict__ ystore, int nrhs,
+                                                          long long ldF, long long ldG,
+                                                          long long ldY) {
+    const TriItem it = items[blockIdx.x];
+    __shared__ double y[TRI_MAXN];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const T* A = pool + it.aoff;
+    const int* dofs = lists + it.dof_off;
+    const int* gidx = lists + it.gidx_off;
+    for (int c = 0; c < nrhs; ++c) {
+        for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = F[c * ldF + dofs[q]];
+        __syncthreads();
+        fwd_unit_lower<T>(A, it.ld, it.nI, y);
+        const int nB = it.n - it.nI;
+        for (int b = wid; b < nB; b += TRI_THREADS / 32) {
+            const T* row = A + (long long)(it.nI + b) * it.ld;
+            double s = 0.0;
+            for (int q = lane; q < it.nI; q += 32) s += (double)row[q] * y[q];
+            s = warp_sum(s);
+            if (lane == 0) atomicAdd(&g[c * ldG + gidx[b]], -s);
+        }
+        for (int q = t; q < it.nI; q += TRI_THREADS) ystore[c * ldY + it.yoff + q] = y[q];
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TRI_THREADS) k_recover(const T* __restrict__ pool,
+                                                         const TriItem* __restrict__ items,
+                                                         const int* __restrict__ lists,
+                                                         const double* __restrict__ uG,
+                                                         const double* __restrict__ ystore,
+                                                         double* __restrict__ u, int nrhs,
+                                                         long long ldG, long long ldU,
+                                                         long long ldY) {
+    const TriItem it = items[blockIdx.x];
+    __shared__ double y[TRI_MAXN];
+    __shared__ double ub[TRI_MAXN];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const T* A = pool + it.aoff;
+    const int* dofs = lists + it.dof_off;
+    const int* gidx = lists + it.gidx_off;
+    const int nB = it.n - it.nI;
+    for (int c = 0; c < nrhs; ++c) {
+        for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = ystore[c * ldY + it.yoff + q];
+        for (int q = t; q < nB; q += TRI_THREADS) ub[q] = uG[c * ldG + gidx[q]];
+        __syncthreads();
+        for (int r = wid; r < it.nI; r += TRI_THREADS / 32) {
+            const T* row = A + (long long)r * it.ld + it.nI;
+            double s = 0.0;
+            for (int q = lane; q < nB; q += 32) s += (double)row[q] * ub[q];
+            s = warp_sum(s);
+            if (lane == 0) y[r] -= s;
+        }
+        __syncthreads();
+        bwd_upper<T>(A, it.ld, it.nI, y);
+        for (int q = t; q < it.nI; q += TRI_THREADS) u[c * ldU + dofs[q]] = y[q];
+        for (int q = t; q < nB; q += TRI_THREADS) u[c * ldU + dofs[it.nI + q]] = ub[q];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+struct TriBatch {
+    TriItem* items;
+    int count;
+};
+
+template <class T>
+int condense_run(const T* pool, const void* items, int count, const int* lists, const double* F,
+                 double* g, double* ystore, int nrhs, long long ldF, long long ldG, long long ldY,
+                 cudaStream_t st) {
+    k_condense<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, F, g, ystore,
+                                                 nrhs, ldF, ldG, ldY);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
+template <class T>
+int recover_run(const T* pool, const void* items, int count, const int* lists, const double* uG,
+                const double* ystore, double* u, int nrhs, long long ldG, long long ldU,
+                long long ldY, cudaStream_t st) {
+    k_recover<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, uG, ystore, u,
+                                                nrhs, ldG, ldU, ldY);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
+size_t tri_item_size() { return sizeof(TriItem); }
+void tri_item_fill(void* dst, long long aoff, int n, int nI, int ld, int dof_off, int gidx_off,
+                   long long yoff) {
+    TriItem* t = (TriItem*)dst;
+    t->aoff = aoff;
+    t->n = n;
+    t->nI = nI;
+    t->ld = ld;
+    t->dof_off = dof_off;
+    t->gidx_off = gidx_off;
+    t->yoff = yoff;
+}
+
+template int condense_run<double>(const double*, const void*, int, const int*, const double*,
+                                  double*, double*, int, long long, long long, long long,
+                                  cudaStream_t);
+template int condense_run<float>(const float*, const void*, int, const int*, const double*, double*,
+                                 double*, int, long long, long long, long long, cudaStream_t);
+template int recover_run<double>(const double*, const void*, int, const int*, const double*,
+                                 const double*, double*, int, long long, long long, long long,
+                                 cudaStream_t);
+template int recover_run<float>(const float*, const void*, int, const int*, const double*,
+                                const double*, double*, int, long long, long long, long long,
+                                cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// small vector kernels
+// ---------------------------------------------------------------------------
+__global__ void k_gather(const double* __restrict__ src, const int* __restrict__ idx,
+                         double* __restrict__ dst, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+int gather_run(const double* src, const int* idx, double* dst, int n, cudaStream_t st) {
+    if (n <= 0) return BDDC_OK;
+    k_gather<<<(n + 255) / 256, 256, 0, st>>>(src, idx, dst, n);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}

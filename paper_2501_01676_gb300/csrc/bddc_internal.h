@@ -1,0 +1,122 @@
+// Internal declarations of libbddc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bddc.h"
+
+#define BDDC_CUDA_TRY(expr)                                                   \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) {                                              \
+            bddc_set_last_error(cudaGetErrorString(_e), __FILE__, __LINE__);  \
+            return BDDC_ECUDA;                                                \
+        }                                                                     \
+    } while (0)
+
+#define BDDC_TRY(expr)                 \
+    do {                               \
+        int _r = (expr);               \
+        if (_r < 0) return _r;         \
+    } while (0)
+
+void bddc_set_last_error(const char* msg, const char* file, int line);
+
+// Device-side error flags written by kernels (never trap).
+enum {
+    ERR_PIVOT = 1,        // zero / non-finite pivot in the batched LU
+    ERR_JACOBI = 2,       // Jacobi eigen sweep cap reached
+    ERR_SIZE = 4,         // a size exceeded a compiled limit
+};
+
+// ---------------------------------------------------------------------------
+// Host description of the mesh, partition and interface classification.
+// ---------------------------------------------------------------------------
+struct Entity {
+    int kind;                       // 0 vertex, 1 edge, 2 face
+    std::vector<int> subs;          // sorted subdomain ids
+    std::vector<int> dofs;          // ascending dof ids
+    std::vector<std::vector<int>> pos;  // per subs[a]: local interface positions
+    int k = 0;                      // primal count
+    int prim_off = 0;               // first global primal index
+    int slot = -1;                  // index within its kind
+    double theta = 0.0;
+};
+
+struct SubInfo {
+    int box0[3], box1[3];           // node-index box [box0, box1]
+    int n, nI, nB;
+    std::vector<int> dofs;          // local dof -> global dof (I then B)
+    std::vector<int> gidx;          // local interface position -> Gamma index
+    std::vector<int> ents;          // entity ids touching the subdomain
+    std::vector<int> ent_slot;      // position of this subdomain in entity subs
+    int max_slab;                   // largest slab element count (H/h)
+};
+
+struct HostMesh {
+    int E[3], nsub[3], nsd;
+    double lo[3], h[3];
+    std::vector<int> off[3];
+    int ndof, nelem, nnodes;
+    std::vector<SubInfo> sub;
+    std::vector<int> gamma;         // Gamma index -> dof
+    std::vector<int> gamma_of_dof;  // dof -> Gamma index or -1
+    std::vector<Entity> ent;        // vertices, edges, faces
+    std::vector<int> by_kind[3];    // entity ids per kind in order
+};
+
+int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh& hm);
+
+// ---------------------------------------------------------------------------
+// Device buffers
+// ---------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+struct DevArena {                    // all device allocations of a context
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    int alloc(void** p, size_t bytes);
+    void release();
+};
+
+// Batched partial LU (Schur complement engine) item descriptor.
+template <class T>
+struct EngItem {
+    T* a;        // row-major matrix
+    int n;       // order
+    int k;       // leading rows/cols to eliminate
+    int ld;      // leading dimension (elements)
+};
+
+template <class T>
+int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* diag_scratch,
+               int* err, cudaStream_t st);
+
+// Generic batched gather -> GEMV -> scatter-add:  out[oidx[r]] += sum_c M[r][c] * in[iidx[c]]
+struct GemvItem {
+    long long moff;      // element offset of the matrix in the pool
+    int rows, cols, ld;
+    int iidx_off;        // offset of the gather index list (cols entries)
+    int oidx_off;        // offset of the scatter index list (rows entries)
+    int row0;            // first row handled by this work item
+    int nrows;           // rows handled by this work item
+};
+
+template <class T>
+int gemv_run(const T* pool, const GemvItem* items_dev, int nitems, const int* idx,
+             const double* in, double* out, int maxcols, int nrhs, int in_ld, int out_ld,
+             cudaStream_t st, const int* skip_flag);
+
+// Small-matrix kernels for the GEPs live in gep.cu; launchers:
+struct FaceJob;   // defined in gep.cu
+struct EdgeJob;
+
+struct bddc_ctx_impl;

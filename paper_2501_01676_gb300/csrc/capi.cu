@@ -1,0 +1,1381 @@
+// C ABI of libbddc and the orchestration of setup and solve.
+//
+// Setup (all subdomains batched in every step):
+//   1. element assembly -> dense A^(i), global FP64 stencil and load (Sect. 2)
+//   2. batched partial LU of A^(i): factors of A_II and S^(i) (Sect. 3)
+//   3. face Schur complements of B^(i) = sym(S^(i)) onto each face, face GEP
+//      kernel (deluxe scaling, parallel sum, pencil, constraint basis)
+//   4. per subdomain: change of basis on the faces, Schur complement of B^(i)
+//      onto (edges, vertices, face primal coordinates); per (edge, subdomain):
+//      Schur complement onto (E, H_k); edge GEP kernel (Sect. 3, new edge GEP)
+//   5. per subdomain: extended matrix of T_i^T S^(i) T_i and D_i T_i, one
+//      batched elimination of its dual block gives S_Pi,i, D_i Phi_i,
+//      Psi_i^T D_i^T and P_i = D_i G_i D_i^T (block elimination of S~)
+//   6. coarse matrix S_Pi (FP64) and its explicit inverse
+// Solve: condensation, right-preconditioned GMRES (graph-replayed Arnoldi
+// steps), interior recovery; MIXED precision wraps this in FP64 iterative
+// refinement on the global system.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "bddc_internal.h"
+#include "gep.h"
+#include "gmres.h"
+#include "setup_kernels.h"
+
+int assemble_init(const HostMesh& hm, double tau, double c);
+template <class TA>
+int assemble_launch(const HostMesh& hm, const double* nu, const double* beta, const double* f,
+                    const double* divb, const double bconst[3], const int* slab_x, const int* slab_y,
+                    const int* slab_z, const int* lut, const long long* lut_off, const int* box0,
+                    const int* boxn, TA* Aloc, const long long* a_off, const int* a_ld,
+                    double* stencil, double* F, cudaStream_t st);
+int stencil_residual(const HostMesh& hm, const double* S, const double* u, const double* F, double* r,
+                     int nrhs, cudaStream_t st);
+template <class T>
+int condense_run(const T* pool, const void* items, int count, const int* lists, const double* F,
+                 double* g, double* ystore, int nrhs, long long ldF, long long ldG, long long ldY,
+                 cudaStream_t st);
+template <class T>
+int recover_run(const T* pool, const void* items, int count, const int* lists, const double* uG,
+                const double* ystore, double* u, int nrhs, long long ldG, long long ldU, long long ldY,
+                cudaStream_t st);
+size_t tri_item_size();
+void tri_item_fill(void* dst, long long aoff, int n, int nI, int ld, int dof_off, int gidx_off,
+                   long long yoff);
+int gather_run(const double* src, const int* idx, double* dst, int n, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+void bddc_set_last_error(const char* msg, const char* file, int line) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s (%s:%d)", msg, file, line);
+    g_last_error = buf;
+}
+
+namespace {
+inline int r4(int n) { return (n + 3) & ~3; }
+inline double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+}  // namespace
+
+struct bddc_ctx {
+    HostMesh hm;
+    bddc_opts o;
+    cudaStream_t st = nullptr;
+    cudaStream_t own = nullptr;   // created when the caller passes the legacy default stream
+    bool mixed = false;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    bddc_stats stats;
+    int nG = 0, nPi = 0;
+
+    template <class T>
+    int alloc(T** p, size_t n) {
+        *p = nullptr;
+        if (n == 0) n = 1;
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        if (e != cudaSuccess) {
+            bddc_set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
+            return BDDC_ENOMEM;
+        }
+        allocs.push_back(q);
+        bytes += n * sizeof(T);
+        *p = (T*)q;
+        return BDDC_OK;
+    }
+    template <class T>
+    int upload(T** p, const std::vector<T>& v) {
+        BDDC_TRY(alloc(p, v.size()));
+        if (!v.empty()) BDDC_CUDA_TRY(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+        return BDDC_OK;
+    }
+
+    // coefficients
+    double *nu = nullptr, *beta = nullptr, *f = nullptr, *divb = nullptr;
+    double bconst[3] = {0, 0, 0};
+    double c = 0.0;
+    // assembly / factors
+    double *stencil = nullptr, *F = nullptr;
+    void* A = nullptr;
+    std::vector<long long> aoff;
+    std::vector<int> ald;
+    // packed S
+    void* ST = nullptr;
+    double* S64 = nullptr;
+    std::vector<long long> soff;
+    std::vector<int> sld;
+    // entities
+    std::vector<double*> Q, lam;      // per entity (faces/edges), device
+    std::vector<std::vector<double*>> DQ;  // per entity, per side
+    std::vector<int> kk, neig;         // host copies
+    int* d_k = nullptr;
+    int* d_neig = nullptr;
+    std::vector<double*> BB;           // edge B~~_E (tests)
+    // apply operators
+    void *MA = nullptr, *MC = nullptr;
+    std::vector<long long> maoff, mcoff;
+    std::vector<int> mald, mcld, np_s;
+    double* SPiInv = nullptr;
+    int* gidx_pool = nullptr;
+    GemvItem *itS = nullptr, *itM1 = nullptr, *itC = nullptr, *itM3 = nullptr;
+    int nitS = 0, nitM1 = 0, nitC = 0, nitM3 = 0, maxcols = 0;
+    // condense / recover
+    void* tri = nullptr;
+    int* tri_lists = nullptr;
+    double* ystore = nullptr;
+    long long ny = 0;
+    // work vectors
+    double *zc = nullptr, *uPi = nullptr, *g = nullptr, *xG = nullptr, *r = nullptr, *w = nullptr,
+           *vcur = nullptr, *t = nullptr;
+    double *uglob = nullptr, *res = nullptr, *corr = nullptr, *Fin = nullptr;
+    int* gamma_dofs = nullptr;
+    // GMRES
+    int gm_m = 0;
+    double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *hh = nullptr,
+           *hh2 = nullptr, *yy = nullptr, *partial = nullptr;
+    GmState* gst = nullptr;
+    GmState* hst = nullptr;     // pinned host copy
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    int* err = nullptr;
+    double* scal = nullptr;     // pinned host scratch
+};
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+template <class T>
+static int run_engine(bddc_ctx* C, const std::vector<EngItem<T>>& items) {
+    if (items.empty()) return BDDC_OK;
+    int maxn = 0, maxk = 0;
+    for (auto& it : items) {
+        maxn = std::max(maxn, it.n);
+        maxk = std::max(maxk, it.k);
+    }
+    EngItem<T>* d = nullptr;
+    BDDC_TRY(C->upload(&d, items));
+    T* scr = nullptr;
+    BDDC_TRY(C->alloc(&scr, items.size() * 32 * 32));
+    return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st);
+}
+
+template <class T>
+static int setup_impl(bddc_ctx* C) {
+    HostMesh& hm = C->hm;
+    cudaStream_t st = C->st;
+    const int nsd = hm.nsd;
+    auto t0 = std::chrono::steady_clock::now();
+    // ---- 1. assembly --------------------------------------------------------
+    C->aoff.resize(nsd);
+    C->ald.resize(nsd);
+    long long atot = 0;
+    for (int s = 0; s < nsd; ++s) {
+        C->ald[s] = r4(hm.sub[s].n);
+        C->aoff[s] = atot;
+        atot += (long long)hm.sub[s].n * C->ald[s];
+    }
+    T* A = nullptr;
+    BDDC_TRY(C->alloc(&A, atot));
+    C->A = A;
+    BDDC_CUDA_TRY(cudaMemsetAsync(A, 0, atot * sizeof(T), st));
+    std::vector<int> lut, box0(3 * nsd), boxn(3 * nsd);
+    std::vector<long long> lut_off(nsd);
+    for (int s = 0; s < nsd; ++s) {
+        SubInfo& S = hm.sub[s];
+        lut_off[s] = (long long)lut.size();
+        std::map<int, int> loc;
+        for (int l = 0; l < S.n; ++l) loc[S.dofs[l]] = l;
+        int bn[3];
+        for (int d = 0; d < 3; ++d) {
+            box0[3 * s + d] = S.box0[d];
+            bn[d] = S.box1[d] - S.box0[d] + 1;
+            boxn[3 * s + d] = bn[d];
+        }
+        for (int iz = 0; iz < bn[2]; ++iz)
+            for (int iy = 0; iy < bn[1]; ++iy)
+                for (int ix = 0; ix < bn[0]; ++ix) {
+                    int gx = S.box0[0] + ix, gy = S.box0[1] + iy, gz = S.box0[2] + iz;
+                    int v = -1;
+                    if (gx > 0 && gy > 0 && gz > 0 && gx < hm.E[0] && gy < hm.E[1] && gz < hm.E[2]) {
+                        int d = (gx - 1) + (hm.E[0] - 1) * ((gy - 1) + (hm.E[1] - 1) * (gz - 1));
+                        v = loc[d];
+                    }
+                    lut.push_back(v);
+                }
+    }
+    std::vector<int> slab[3];
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < hm.nsub[d]; ++s)
+            for (int e = hm.off[d][s]; e < hm.off[d][s + 1]; ++e) slab[d].push_back(s);
+    int *d_lut, *d_box0, *d_boxn, *d_sx, *d_sy, *d_sz, *d_ald;
+    long long *d_lutoff, *d_aoff;
+    BDDC_TRY(C->upload(&d_lut, lut));
+    BDDC_TRY(C->upload(&d_lutoff, lut_off));
+    BDDC_TRY(C->upload(&d_box0, box0));
+    BDDC_TRY(C->upload(&d_boxn, boxn));
+    BDDC_TRY(C->upload(&d_sx, slab[0]));
+    BDDC_TRY(C->upload(&d_sy, slab[1]));
+    BDDC_TRY(C->upload(&d_sz, slab[2]));
+    BDDC_TRY(C->upload(&d_aoff, C->aoff));
+    BDDC_TRY(C->upload(&d_ald, C->ald));
+    BDDC_TRY(C->alloc(&C->stencil, (size_t)27 * hm.ndof));
+    BDDC_TRY(C->alloc(&C->F, hm.ndof));
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->stencil, 0, sizeof(double) * 27 * (size_t)hm.ndof, st));
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->F, 0, sizeof(double) * hm.ndof, st));
+    BDDC_TRY(assemble_init(hm, C->o.tau, C->c));
+    BDDC_TRY(assemble_launch<T>(hm, C->nu, C->beta, C->f, C->divb, C->bconst, d_sx, d_sy, d_sz, d_lut,
+                                d_lutoff, d_box0, d_boxn, A, d_aoff, d_ald, C->stencil, C->F, st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    C->stats.t_assemble_ms = ms_since(t0);
+    // ---- 2. partial LU: S^(i) ---------------------------------------------
+    t0 = std::chrono::steady_clock::now();
+    {
+        std::vector<EngItem<T>> items(nsd);
+        for (int s = 0; s < nsd; ++s)
+            items[s] = EngItem<T>{A + C->aoff[s], hm.sub[s].n, hm.sub[s].nI, C->ald[s]};
+        BDDC_TRY(run_engine<T>(C, items));
+    }
+    C->soff.resize(nsd);
+    C->sld.resize(nsd);
+    long long stot = 0;
+    for (int s = 0; s < nsd; ++s) {
+        C->sld[s] = r4(hm.sub[s].nB);
+        C->soff[s] = stot;
+        stot += (long long)hm.sub[s].nB * C->sld[s];
+    }
+    T* ST = nullptr;
+    BDDC_TRY(C->alloc(&ST, stot));
+    C->ST = ST;
+    {
+        std::vector<CopyJob> jobs(nsd);
+        for (int s = 0; s < nsd; ++s) {
+            SubInfo& S = hm.sub[s];
+            jobs[s] = CopyJob{A + C->aoff[s], C->ald[s], S.nI, S.nI, S.nB, S.nB, ST + C->soff[s], C->sld[s], 1.0};
+        }
+        CopyJob* d;
+        BDDC_TRY(C->upload(&d, jobs));
+        BDDC_TRY((copy_blocks_run<T, T>(d, nsd, 32, st)));
+        if (C->mixed) {
+            BDDC_TRY(C->alloc(&C->S64, stot));
+            for (int s = 0; s < nsd; ++s) jobs[s] = CopyJob{ST + C->soff[s], C->sld[s], 0, 0, hm.sub[s].nB, hm.sub[s].nB, C->S64 + C->soff[s], C->sld[s], 1.0};
+            CopyJob* d2;
+            BDDC_TRY(C->upload(&d2, jobs));
+            BDDC_TRY((copy_blocks_run<T, double>(d2, nsd, 32, st)));
+        } else {
+            C->S64 = (double*)ST;
+        }
+    }
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    C->stats.t_factor_ms = ms_since(t0);
+    // interface maps
+    std::vector<int> gl;
+    std::vector<int> gl_off(nsd);
+    for (int s = 0; s < nsd; ++s) {
+        gl_off[s] = (int)gl.size();
+        gl.insert(gl.end(), hm.sub[s].gidx.begin(), hm.sub[s].gidx.end());
+    }
+    // entity position lists on the device
+    const int nent = (int)hm.ent.size();
+    std::vector<int> posl;
+    std::vector<std::vector<int>> pos_off(nent);
+    for (int e = 0; e < nent; ++e)
+        for (size_t a = 0; a < hm.ent[e].subs.size(); ++a) {
+            pos_off[e].push_back((int)posl.size());
+            posl.insert(posl.end(), hm.ent[e].pos[a].begin(), hm.ent[e].pos[a].end());
+        }
+    int* d_pos = nullptr;
+    BDDC_TRY(C->upload(&d_pos, posl));
+    C->Q.assign(nent, nullptr);
+    C->lam.assign(nent, nullptr);
+    C->DQ.assign(nent, {});
+    C->BB.assign(nent, nullptr);
+    C->kk.assign(nent, 0);
+    C->neig.assign(nent, 0);
+    BDDC_TRY(C->alloc(&C->d_k, nent));
+    BDDC_TRY(C->alloc(&C->d_neig, nent));
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->d_k, 0, sizeof(int) * nent, st));
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->d_neig, 0, sizeof(int) * nent, st));
+    for (int e = 0; e < nent; ++e) {
+        Entity& E = hm.ent[e];
+        int n = (int)E.dofs.size();
+        BDDC_TRY(C->alloc(&C->Q[e], (size_t)n * n));
+        BDDC_TRY(C->alloc(&C->lam[e], (size_t)3 * n + 1));
+        C->DQ[e].resize(E.subs.size());
+        if (E.kind == 0) {
+            E.k = 1;
+            continue;
+        }
+        for (size_t a = 0; a < E.subs.size(); ++a) BDDC_TRY(C->alloc(&C->DQ[e][a], (size_t)n * n));
+        E.theta = E.kind == 1 ? C->o.theta_E : C->o.theta_F;
+        if (E.kind == 2 && !(C->o.theta_F > 0)) {
+            int m = 0;
+            for (int s : E.subs) m = std::max(m, hm.sub[s].max_slab);
+            E.theta = 1.0 + std::log((double)m);
+        }
+    }
+    // ---- 3. faces ------------------------------------------------------------
+    t0 = std::chrono::steady_clock::now();
+    const int face_mode = C->o.all_primal ? 1 : (C->o.face_gep ? 0 : 2);
+    std::vector<int>& faces = hm.by_kind[2];
+    if (!faces.empty()) {
+        std::vector<int> permv;
+        std::vector<GatherJob> gj;
+        std::vector<EngItem<T>> items;
+        std::vector<long long> fo;
+        long long ftot = 0;
+        for (int e : faces)
+            for (int a = 0; a < 2; ++a) {
+                int s = hm.ent[e].subs[a];
+                fo.push_back(ftot);
+                ftot += (long long)hm.sub[s].nB * r4(hm.sub[s].nB);
+            }
+        T* FB = nullptr;
+        if (face_mode == 0) BDDC_TRY(C->alloc(&FB, ftot));
+        int q = 0;
+        for (int e : faces) {
+            Entity& E = hm.ent[e];
+            for (int a = 0; a < 2; ++a, ++q) {
+                int s = E.subs[a];
+                int nB = hm.sub[s].nB, nF = (int)E.dofs.size();
+                std::vector<char> inF(nB, 0);
+                for (int p : E.pos[a]) inF[p] = 1;
+                int off = (int)permv.size();
+                for (int b = 0; b < nB; ++b)
+                    if (!inF[b]) permv.push_back(b);
+                for (int p : E.pos[a]) permv.push_back(p);
+                if (face_mode == 0) {
+                    gj.push_back(GatherJob{C->S64 + C->soff[s], C->sld[s], nB, off, 1, FB + fo[q], r4(nB)});
+                    items.push_back(EngItem<T>{FB + fo[q], nB, nB - nF, r4(nB)});
+                }
+            }
+        }
+        int* d_perm;
+        BDDC_TRY(C->upload(&d_perm, permv));
+        double* Bt64 = nullptr;
+        std::vector<long long> bo;
+        long long btot = 0;
+        for (int e : faces) {
+            int nF = (int)hm.ent[e].dofs.size();
+            bo.push_back(btot);
+            btot += 2LL * nF * nF;
+        }
+        BDDC_TRY(C->alloc(&Bt64, btot));
+        if (face_mode == 0) {
+            GatherJob* d_gj;
+            BDDC_TRY(C->upload(&d_gj, gj));
+            BDDC_TRY(gather_perm_run<T>(d_gj, (int)gj.size(), d_perm, 64, st));
+            BDDC_TRY(run_engine<T>(C, items));
+            std::vector<CopyJob> cj;
+            q = 0;
+            for (size_t fi = 0; fi < faces.size(); ++fi) {
+                Entity& E = hm.ent[faces[fi]];
+                int nF = (int)E.dofs.size();
+                for (int a = 0; a < 2; ++a, ++q) {
+                    int nB = hm.sub[E.subs[a]].nB;
+                    cj.push_back(CopyJob{FB + fo[q], r4(nB), nB - nF, nB - nF, nF, nF,
+                                         Bt64 + bo[fi] + (long long)a * nF * nF, nF, 1.0});
+                }
+            }
+            CopyJob* d_cj;
+            BDDC_TRY(C->upload(&d_cj, cj));
+            BDDC_TRY((copy_blocks_run<T, double>(d_cj, (int)cj.size(), 8, st)));
+        }
+        std::vector<FaceJob> fj;
+        int maxn = 0;
+        for (size_t fi = 0; fi < faces.size(); ++fi) {
+            int e = faces[fi];
+            Entity& E = hm.ent[e];
+            int n = (int)E.dofs.size();
+            maxn = std::max(maxn, n);
+            FaceJob J;
+            memset(&J, 0, sizeof(J));
+            J.n = n;
+            J.mode = face_mode;
+            J.theta = E.theta;
+            int i = E.subs[0], j = E.subs[1];
+            J.Si = C->S64 + C->soff[i];
+            J.Sj = C->S64 + C->soff[j];
+            J.ldi = C->sld[i];
+            J.ldj = C->sld[j];
+            J.pi = d_pos + pos_off[e][0];
+            J.pj = d_pos + pos_off[e][1];
+            J.Bti = Bt64 + bo[fi];
+            J.Btj = Bt64 + bo[fi] + (long long)n * n;
+            J.ldbi = J.ldbj = n;
+            BDDC_TRY(C->alloc(&J.work, face_work_doubles(n)));
+            J.Q = C->Q[e];
+            J.DQi = C->DQ[e][0];
+            J.DQj = C->DQ[e][1];
+            J.lambda = C->lam[e];
+            J.neig = C->d_neig + e;
+            J.k = C->d_k + e;
+            fj.push_back(J);
+        }
+        FaceJob* d_fj;
+        BDDC_TRY(C->upload(&d_fj, fj));
+        BDDC_TRY(face_run(d_fj, (int)fj.size(), maxn, C->err, st));
+    }
+    BDDC_CUDA_TRY(cudaMemcpyAsync(C->kk.data(), C->d_k, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int e : faces) hm.ent[e].k = C->kk[e];
+    C->stats.t_face_ms = ms_since(t0);
+    // ---- 4. edges --------------------------------------------------------------
+    t0 = std::chrono::steady_clock::now();
+    const int edge_mode = C->o.all_primal ? 1 : (C->o.edge_gep == BDDC_EDGE_NEW ? 0 : 2);
+    std::vector<int>& edges = hm.by_kind[1];
+    if (!edges.empty()) {
+        // per subdomain: transformed B onto [face duals | edges, vertices, face primals]
+        std::vector<int> idxv;
+        std::vector<int> nelim(nsd, 0), nkeep(nsd, 0);
+        std::vector<std::map<long long, int>> keypos(nsd);   // H / edge-dof key -> index in W
+        std::vector<int> ew_off(nsd, -1);
+        auto key_of = [](int kind, int e, int l) -> long long { return ((long long)kind << 40) | ((long long)e << 16) | l; };
+        std::vector<TBlock> tb;
+        double* Ysc = nullptr;
+        T* W = nullptr;
+        double* W64 = nullptr;
+        std::vector<long long> woff(nsd, 0), w64off(nsd, 0);
+        if (edge_mode == 0) {
+            long long ytot = 0, wtot = 0, w64tot = 0;
+            for (int s = 0; s < nsd; ++s) {
+                int nB = hm.sub[s].nB;
+                woff[s] = wtot;
+                wtot += (long long)nB * r4(nB);
+                ytot = std::max(ytot, (long long)nB * nB);
+            }
+            // (the change-of-basis scratch is per subdomain)
+            std::vector<long long> yoff(nsd);
+            ytot = 0;
+            for (int s = 0; s < nsd; ++s) {
+                yoff[s] = ytot;
+                ytot += (long long)hm.sub[s].nB * hm.sub[s].nB;
+            }
+            BDDC_TRY(C->alloc(&Ysc, ytot));
+            BDDC_TRY(C->alloc(&W, wtot));
+            std::vector<int> perm_off(nsd);
+            std::vector<EngItem<T>> items;
+            for (int s = 0; s < nsd; ++s) {
+                SubInfo& S = hm.sub[s];
+                int nB = S.nB;
+                std::vector<int> perm(nB, -1);
+                int ne = 0;
+                // eliminated: face duals
+                for (size_t q = 0; q < S.ents.size(); ++q) {
+                    Entity& E = hm.ent[S.ents[q]];
+                    if (E.kind != 2) continue;
+                    const std::vector<int>& p = E.pos[S.ent_slot[q]];
+                    for (int l = E.k; l < (int)p.size(); ++l) perm[p[l]] = ne++;
+                }
+                int kp = ne;
+                for (int kind : {1, 0, 2})
+                    for (size_t q = 0; q < S.ents.size(); ++q) {
+                        Entity& E = hm.ent[S.ents[q]];
+                        if (E.kind != kind) continue;
+                        const std::vector<int>& p = E.pos[S.ent_slot[q]];
+                        int cnt = kind == 2 ? E.k : (int)p.size();
+                        for (int l = 0; l < cnt; ++l) {
+                            perm[p[l]] = kp;
+                            keypos[s][key_of(kind, S.ents[q], l)] = kp - ne;
+                            ++kp;
+                        }
+                    }
+                nelim[s] = ne;
+                nkeep[s] = nB - ne;
+                perm_off[s] = (int)idxv.size();
+                idxv.insert(idxv.end(), perm.begin(), perm.end());
+                items.push_back(EngItem<T>{W + woff[s], nB, ne, r4(nB)});
+            }
+            int posbase = (int)idxv.size();
+            idxv.insert(idxv.end(), posl.begin(), posl.end());
+            int maxn = 1;
+            for (int s = 0; s < nsd; ++s) {
+                SubInfo& S = hm.sub[s];
+                for (size_t q = 0; q < S.ents.size(); ++q) {
+                    int e = S.ents[q];
+                    Entity& E = hm.ent[e];
+                    int n = (int)E.dofs.size();
+                    TBlock B;
+                    memset(&B, 0, sizeof(B));
+                    B.src = C->S64 + C->soff[s];
+                    B.sld = C->sld[s];
+                    B.sym = 1;
+                    B.y = Ysc + yoff[s];
+                    B.yld = S.nB;
+                    B.n = n;
+                    B.pos_off = posbase + pos_off[e][S.ent_slot[q]];
+                    B.perm_off = perm_off[s];
+                    B.identity = E.kind != 2;
+                    B.Q = E.kind == 2 ? C->Q[e] : nullptr;
+                    B.nrows = S.nB;
+                    B.dst = W + woff[s];
+                    B.dld = r4(S.nB);
+                    if (E.kind == 2) maxn = std::max(maxn, n);
+                    tb.push_back(B);
+                }
+            }
+            int* d_idx;
+            BDDC_TRY(C->upload(&d_idx, idxv));
+            TBlock* d_tb;
+            BDDC_TRY(C->upload(&d_tb, tb));
+            BDDC_TRY(transform_run<T>(d_tb, (int)tb.size(), d_idx, maxn, 4, st));
+            BDDC_TRY(run_engine<T>(C, items));
+            // trailing blocks to FP64
+            std::vector<CopyJob> cj;
+            for (int s = 0; s < nsd; ++s) {
+                w64off[s] = w64tot;
+                w64tot += (long long)nkeep[s] * nkeep[s];
+            }
+            BDDC_TRY(C->alloc(&W64, w64tot));
+            for (int s = 0; s < nsd; ++s)
+                cj.push_back(CopyJob{W + woff[s], r4(hm.sub[s].nB), nelim[s], nelim[s], nkeep[s], nkeep[s],
+                                     W64 + w64off[s], nkeep[s], 1.0});
+            CopyJob* d_cj;
+            BDDC_TRY(C->upload(&d_cj, cj));
+            BDDC_TRY((copy_blocks_run<T, double>(d_cj, nsd, 8, st)));
+        }
+        // per (edge, subdomain): Schur complement onto [E, H_k]
+        std::vector<int> gidxv, hmv;
+        std::vector<GatherJob> gj;
+        std::vector<EngItem<double>> items;
+        std::vector<std::vector<int>> hsz(edges.size()), hoff(edges.size()), itn(edges.size());
+        std::vector<std::vector<long long>> ito(edges.size());
+        std::vector<int> nH(edges.size(), 0);
+        double* EB = nullptr;
+        if (edge_mode == 0) {
+            long long etot = 0;
+            for (size_t ei = 0; ei < edges.size(); ++ei)
+                for (int s : hm.ent[edges[ei]].subs) etot += (long long)nkeep[s] * nkeep[s];
+            BDDC_TRY(C->alloc(&EB, etot));
+            etot = 0;
+            for (size_t ei = 0; ei < edges.size(); ++ei) {
+                int e = edges[ei];
+                Entity& E = hm.ent[e];
+                int nE = (int)E.dofs.size();
+                // union of H over n(E)
+                std::map<long long, int> hu;
+                for (int s : E.subs) {
+                    SubInfo& S = hm.sub[s];
+                    for (size_t q = 0; q < S.ents.size(); ++q) {
+                        Entity& X = hm.ent[S.ents[q]];
+                        if (X.kind == 0) hu[key_of(0, S.ents[q], 0)] = 0;
+                        if (X.kind == 2)
+                            for (int l = 0; l < X.k; ++l) hu[key_of(2, S.ents[q], l)] = 0;
+                    }
+                }
+                int cnt = 0;
+                for (auto& kv : hu) kv.second = cnt++;
+                nH[ei] = cnt;
+                for (size_t a = 0; a < E.subs.size(); ++a) {
+                    int s = E.subs[a];
+                    SubInfo& S = hm.sub[s];
+                    std::vector<int> perm, hk;
+                    // other edges' dofs first
+                    for (size_t q = 0; q < S.ents.size(); ++q) {
+                        int x = S.ents[q];
+                        Entity& X = hm.ent[x];
+                        if (X.kind != 1 || x == e) continue;
+                        for (int l = 0; l < (int)X.dofs.size(); ++l) perm.push_back(keypos[s][key_of(1, x, l)]);
+                    }
+                    int nel = (int)perm.size();
+                    for (int l = 0; l < nE; ++l) perm.push_back(keypos[s][key_of(1, e, l)]);
+                    for (size_t q = 0; q < S.ents.size(); ++q) {
+                        int x = S.ents[q];
+                        Entity& X = hm.ent[x];
+                        if (X.kind == 0) {
+                            perm.push_back(keypos[s][key_of(0, x, 0)]);
+                            hk.push_back(hu[key_of(0, x, 0)]);
+                        }
+                    }
+                    for (size_t q = 0; q < S.ents.size(); ++q) {
+                        int x = S.ents[q];
+                        Entity& X = hm.ent[x];
+                        if (X.kind == 2)
+                            for (int l = 0; l < X.k; ++l) {
+                                perm.push_back(keypos[s][key_of(2, x, l)]);
+                                hk.push_back(hu[key_of(2, x, l)]);
+                            }
+                    }
+                    int n = (int)perm.size();
+                    int off = (int)gidxv.size();
+                    gidxv.insert(gidxv.end(), perm.begin(), perm.end());
+                    gj.push_back(GatherJob{W64 + w64off[s], nkeep[s], n, off, 0, EB + etot, n});
+                    items.push_back(EngItem<double>{EB + etot, n, nel, n});
+                    ito[ei].push_back(etot + (long long)nel * n + nel);
+                    itn[ei].push_back(n);
+                    hsz[ei].push_back((int)hk.size());
+                    hoff[ei].push_back((int)hmv.size());
+                    hmv.insert(hmv.end(), hk.begin(), hk.end());
+                    etot += (long long)n * n;
+                }
+            }
+            int* d_gi;
+            BDDC_TRY(C->upload(&d_gi, gidxv));
+            GatherJob* d_gj;
+            BDDC_TRY(C->upload(&d_gj, gj));
+            BDDC_TRY(gather_perm_run<double>(d_gj, (int)gj.size(), d_gi, 8, st));
+            BDDC_TRY(run_engine<double>(C, items));
+        }
+        int* d_hm = nullptr;
+        BDDC_TRY(C->upload(&d_hm, hmv));
+        std::vector<EdgeJob> ej;
+        int maxnw = 1, maxnz = 1;
+        for (size_t ei = 0; ei < edges.size(); ++ei) {
+            int e = edges[ei];
+            Entity& E = hm.ent[e];
+            int n = (int)E.dofs.size(), m = (int)E.subs.size();
+            if (m > EDGE_MAX_SUBS) return BDDC_EINVAL;
+            EdgeJob J;
+            memset(&J, 0, sizeof(J));
+            J.n = n;
+            J.m = m;
+            J.nH = nH[ei];
+            J.mode = edge_mode;
+            J.theta = E.theta;
+            for (int a = 0; a < m; ++a) {
+                int s = E.subs[a];
+                J.S[a] = C->S64 + C->soff[s];
+                J.ldS[a] = C->sld[s];
+                J.pos[a] = d_pos + pos_off[e][a];
+                J.DQ[a] = C->DQ[e][a];
+                if (edge_mode == 0) {
+                    J.Bt[a] = EB + ito[ei][a];
+                    J.ldBt[a] = itn[ei][a];
+                    J.h[a] = hsz[ei][a];
+                    J.hmap[a] = d_hm + hoff[ei][a];
+                }
+            }
+            maxnw = std::max(maxnw, (m - 1) * n);
+            maxnz = std::max(maxnz, m * n + J.nH);
+            BDDC_TRY(C->alloc(&J.work, edge_work_doubles(n, m, J.nH)));
+            BDDC_TRY(C->alloc(&C->BB[e], (size_t)(m - 1) * n * (m - 1) * n));
+            J.BBout = C->BB[e];
+            J.Q = C->Q[e];
+            J.lambda = C->lam[e];
+            J.neig = C->d_neig + e;
+            J.k = C->d_k + e;
+            ej.push_back(J);
+        }
+        EdgeJob* d_ej;
+        BDDC_TRY(C->upload(&d_ej, ej));
+        BDDC_TRY(edge_run(d_ej, (int)ej.size(), maxnw, maxnz, C->err, st));
+    }
+    BDDC_CUDA_TRY(cudaMemcpyAsync(C->kk.data(), C->d_k, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(C->neig.data(), C->d_neig, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int e : edges) hm.ent[e].k = C->kk[e];
+    C->stats.t_edge_ms = ms_since(t0);
+    // ---- 5. primal numbering, extended matrices, coarse operators --------------
+    t0 = std::chrono::steady_clock::now();
+    int np = 0;
+    C->stats.pnumF = C->stats.pnumE = 0;
+    for (int kind : {0, 2, 1})
+        for (int e : hm.by_kind[kind]) {
+            hm.ent[e].prim_off = np;
+            np += hm.ent[e].k;
+            if (kind == 2) C->stats.pnumF += hm.ent[e].k;
+            if (kind == 1) C->stats.pnumE += hm.ent[e].k;
+        }
+    C->nPi = np;
+    const int nPi = np;
+    std::vector<int> idxv, rpi_off(nsd), perm_off(nsd);
+    C->np_s.assign(nsd, 0);
+    std::vector<long long> xoff(nsd), yoff2(nsd);
+    std::vector<int> xld(nsd);
+    long long xtot = 0, ytot = 0;
+    for (int s = 0; s < nsd; ++s) {
+        SubInfo& S = hm.sub[s];
+        std::vector<int> rp;
+        for (size_t q = 0; q < S.ents.size(); ++q) {
+            Entity& E = hm.ent[S.ents[q]];
+            for (int l = 0; l < E.k; ++l) rp.push_back(E.prim_off + l);
+        }
+        C->np_s[s] = (int)rp.size();
+        rpi_off[s] = (int)idxv.size();
+        idxv.insert(idxv.end(), rp.begin(), rp.end());
+        int nd = S.nB - (int)rp.size();
+        std::vector<int> perm(S.nB, -1);
+        int cd = 0, cp = nd;
+        for (size_t q = 0; q < S.ents.size(); ++q) {
+            Entity& E = hm.ent[S.ents[q]];
+            const std::vector<int>& p = E.pos[S.ent_slot[q]];
+            for (int l = 0; l < (int)p.size(); ++l) perm[p[l]] = l < E.k ? cp++ : cd++;
+        }
+        perm_off[s] = (int)idxv.size();
+        idxv.insert(idxv.end(), perm.begin(), perm.end());
+        xld[s] = r4(2 * S.nB);
+        xoff[s] = xtot;
+        xtot += (long long)2 * S.nB * xld[s];
+        yoff2[s] = ytot;
+        ytot += (long long)S.nB * S.nB;
+    }
+    int posbase = (int)idxv.size();
+    idxv.insert(idxv.end(), posl.begin(), posl.end());
+    int* d_idx;
+    BDDC_TRY(C->upload(&d_idx, idxv));
+    T* X = nullptr;
+    double* Ysc = nullptr;
+    BDDC_TRY(C->alloc(&X, xtot));
+    BDDC_TRY(C->alloc(&Ysc, ytot));
+    BDDC_CUDA_TRY(cudaMemsetAsync(X, 0, xtot * sizeof(T), st));
+    {
+        std::vector<TBlock> tb;
+        std::vector<DTJob> dj;
+        int maxn = 1;
+        for (int s = 0; s < nsd; ++s) {
+            SubInfo& S = hm.sub[s];
+            for (size_t q = 0; q < S.ents.size(); ++q) {
+                int e = S.ents[q];
+                Entity& E = hm.ent[e];
+                int n = (int)E.dofs.size();
+                TBlock B;
+                memset(&B, 0, sizeof(B));
+                B.src = C->S64 + C->soff[s];
+                B.sld = C->sld[s];
+                B.sym = 0;
+                B.y = Ysc + yoff2[s];
+                B.yld = S.nB;
+                B.n = n;
+                B.pos_off = posbase + pos_off[e][S.ent_slot[q]];
+                B.perm_off = perm_off[s];
+                B.identity = E.kind == 0;
+                B.Q = E.kind == 0 ? nullptr : C->Q[e];
+                B.nrows = S.nB;
+                B.dst = X + xoff[s];
+                B.dld = xld[s];
+                if (E.kind != 0) maxn = std::max(maxn, n);
+                tb.push_back(B);
+                DTJob D;
+                D.n = n;
+                D.nB = S.nB;
+                D.pos_off = B.pos_off;
+                D.perm_off = perm_off[s];
+                D.DQ = E.kind == 0 ? nullptr : C->DQ[e][S.ent_slot[q]];
+                D.scalar = 1.0 / (double)E.subs.size();
+                D.dst = X + xoff[s];
+                D.dld = xld[s];
+                dj.push_back(D);
+            }
+        }
+        TBlock* d_tb;
+        BDDC_TRY(C->upload(&d_tb, tb));
+        DTJob* d_dj;
+        BDDC_TRY(C->upload(&d_dj, dj));
+        BDDC_TRY(transform_run<T>(d_tb, (int)tb.size(), d_idx, maxn, 4, st));
+        BDDC_TRY(fill_dt_run<T>(d_dj, (int)dj.size(), d_idx, st));
+        std::vector<EngItem<T>> items;
+        for (int s = 0; s < nsd; ++s)
+            items.push_back(EngItem<T>{X + xoff[s], 2 * hm.sub[s].nB, hm.sub[s].nB - C->np_s[s], xld[s]});
+        BDDC_TRY(run_engine<T>(C, items));
+    }
+    // operators of the apply
+    C->maoff.resize(nsd);
+    C->mcoff.resize(nsd);
+    C->mald.resize(nsd);
+    C->mcld.resize(nsd);
+    long long matot = 0, mctot = 0;
+    for (int s = 0; s < nsd; ++s) {
+        int nB = hm.sub[s].nB;
+        C->mald[s] = r4(nB);
+        C->maoff[s] = matot;
+        matot += (long long)(nB + C->np_s[s]) * C->mald[s];
+        C->mcld[s] = r4(std::max(C->np_s[s], 1));
+        C->mcoff[s] = mctot;
+        mctot += (long long)nB * C->mcld[s];
+    }
+    T *MA = nullptr, *MC = nullptr;
+    BDDC_TRY(C->alloc(&MA, matot));
+    BDDC_TRY(C->alloc(&MC, mctot));
+    BDDC_CUDA_TRY(cudaMemsetAsync(MC, 0, mctot * sizeof(T), st));
+    C->MA = MA;
+    C->MC = MC;
+    double* SPi = nullptr;
+    BDDC_TRY(C->alloc(&SPi, (size_t)std::max(nPi, 1) * std::max(nPi, 1)));
+    BDDC_CUDA_TRY(cudaMemsetAsync(SPi, 0, sizeof(double) * std::max(nPi, 1) * std::max(nPi, 1), st));
+    {
+        std::vector<ExtractJob> xj(nsd);
+        for (int s = 0; s < nsd; ++s)
+            xj[s] = ExtractJob{X + xoff[s], xld[s], hm.sub[s].nB, C->np_s[s], rpi_off[s], MA + C->maoff[s],
+                               C->mald[s], MC + C->mcoff[s], C->mcld[s]};
+        ExtractJob* d_xj;
+        BDDC_TRY(C->upload(&d_xj, xj));
+        BDDC_TRY((extract_run<T, T>(d_xj, nsd, d_idx, SPi, nPi, 32, st)));
+    }
+    // coarse inverse (FP64): [[S_Pi, -I], [I, 0]] -> S_Pi^{-1}
+    const int ldc = r4(std::max(nPi, 1));
+    BDDC_TRY(C->alloc(&C->SPiInv, (size_t)std::max(nPi, 1) * ldc));
+    if (nPi > 0) {
+        double* Xc = nullptr;
+        BDDC_TRY(C->alloc(&Xc, 4LL * nPi * nPi));
+        BDDC_TRY(coarse_ext_run(SPi, Xc, nPi, st));
+        std::vector<EngItem<double>> it1{EngItem<double>{Xc, 2 * nPi, nPi, 2 * nPi}};
+        BDDC_TRY(run_engine<double>(C, it1));
+        std::vector<CopyJob> cj{CopyJob{Xc, 2 * nPi, nPi, nPi, nPi, nPi, C->SPiInv, ldc, 1.0}};
+        CopyJob* d_cj;
+        BDDC_TRY(C->upload(&d_cj, cj));
+        BDDC_TRY((copy_blocks_run<double, double>(d_cj, 1, 64, st)));
+    }
+    // gemv work items
+    std::vector<int> gi;
+    std::vector<GemvItem> iS, iM1, iC, iM3;
+    const int nG = C->nG;
+    auto split = [](std::vector<GemvItem>& v, long long moff, int rows, int cols, int ld, int io, int oo) {
+        const int RB = 32;
+        for (int r0 = 0; r0 < rows; r0 += RB) {
+            GemvItem it;
+            it.moff = moff;
+            it.rows = rows;
+            it.cols = cols;
+            it.ld = ld;
+            it.iidx_off = io;
+            it.oidx_off = oo;
+            it.row0 = r0;
+            it.nrows = std::min(RB, rows - r0);
+            v.push_back(it);
+        }
+    };
+    C->maxcols = std::max(nPi, 1);
+    for (int s = 0; s < nsd; ++s) {
+        SubInfo& S = hm.sub[s];
+        int nB = S.nB, nps = C->np_s[s];
+        C->maxcols = std::max(C->maxcols, nB);
+        int og = (int)gi.size();
+        gi.insert(gi.end(), S.gidx.begin(), S.gidx.end());
+        int orp = (int)gi.size();
+        for (int q = 0; q < nps; ++q) gi.push_back(idxv[rpi_off[s] + q]);
+        int om1 = (int)gi.size();
+        gi.insert(gi.end(), S.gidx.begin(), S.gidx.end());
+        for (int q = 0; q < nps; ++q) gi.push_back(nG + idxv[rpi_off[s] + q]);
+        split(iS, C->soff[s], nB, nB, C->sld[s], og, og);
+        split(iM1, C->maoff[s], nB + nps, nB, C->mald[s], og, om1);
+        if (nps > 0) split(iM3, C->mcoff[s], nB, nps, C->mcld[s], orp, og);
+    }
+    {
+        int oc = (int)gi.size();
+        for (int q = 0; q < nPi; ++q) gi.push_back(nG + q);
+        int oi = (int)gi.size();
+        for (int q = 0; q < nPi; ++q) gi.push_back(q);
+        if (nPi > 0) split(iC, 0, nPi, nPi, ldc, oc, oi);
+    }
+    BDDC_TRY(C->upload(&C->gidx_pool, gi));
+    BDDC_TRY(C->upload(&C->itS, iS));
+    BDDC_TRY(C->upload(&C->itM1, iM1));
+    BDDC_TRY(C->upload(&C->itC, iC));
+    BDDC_TRY(C->upload(&C->itM3, iM3));
+    C->nitS = (int)iS.size();
+    C->nitM1 = (int)iM1.size();
+    C->nitC = (int)iC.size();
+    C->nitM3 = (int)iM3.size();
+    // condense / recover items
+    {
+        std::vector<int> lists;
+        std::vector<char> items(tri_item_size() * nsd);
+        long long yo = 0;
+        for (int s = 0; s < nsd; ++s) {
+            SubInfo& S = hm.sub[s];
+            int dof_off = (int)lists.size();
+            lists.insert(lists.end(), S.dofs.begin(), S.dofs.end());
+            int go = (int)lists.size();
+            lists.insert(lists.end(), S.gidx.begin(), S.gidx.end());
+            tri_item_fill(items.data() + tri_item_size() * s, C->aoff[s], S.n, S.nI, C->ald[s], dof_off, go, yo);
+            yo += S.nI;
+        }
+        C->ny = std::max(yo, 1LL);
+        BDDC_TRY(C->upload(&C->tri_lists, lists));
+        BDDC_TRY(C->upload((char**)&C->tri, items));
+    }
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    C->stats.t_coarse_ms = ms_since(t0);
+    return BDDC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// operators
+// ---------------------------------------------------------------------------
+template <class T>
+static int op_S(bddc_ctx* C, const double* x, double* y, const int* skip) {
+    BDDC_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * C->nG, C->st));
+    return gemv_run<T>((const T*)C->ST, C->itS, C->nitS, C->gidx_pool, x, y, C->maxcols, 1, 0, 0, C->st, skip);
+}
+
+// zc[0:nG] = M^-1 x (zc[nG:nG+nPi] holds the coarse residual)
+template <class T>
+static int op_M(bddc_ctx* C, const double* x, const int* skip) {
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->zc, 0, sizeof(double) * (C->nG + C->nPi), C->st));
+    BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, C->zc, C->maxcols, 1, 0, 0, C->st, skip));
+    if (C->nPi > 0) {
+        BDDC_CUDA_TRY(cudaMemsetAsync(C->uPi, 0, sizeof(double) * C->nPi, C->st));
+        BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, C->zc, C->uPi, C->maxcols, 1, 0, 0, C->st, skip));
+        BDDC_TRY(gemv_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, C->uPi, C->zc, C->maxcols, 1, 0, 0, C->st, skip));
+    }
+    return BDDC_OK;
+}
+
+static int norm2(bddc_ctx* C, const double* x, long long n, double* out_host) {
+    // uses the spare state slot (never stopped)
+    int nchunk = gm_nchunk(n);
+    BDDC_TRY(gm_norm2(x, n, C->gst + 1, C->partial, C->st));
+    (void)nchunk;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(C->hst + 1, C->gst + 1, sizeof(GmState), cudaMemcpyDeviceToHost, C->st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    *out_host = std::sqrt(std::max(C->hst[1].nrm2, 0.0));
+    return BDDC_OK;
+}
+
+template <class T>
+static int gm_iteration(bddc_ctx* C) {
+    const long long n = C->nG;
+    const int* skip = &C->gst->stop;
+    BDDC_TRY(gm_copy_row(C->V, n, C->vcur, n, C->gst, C->st));
+    BDDC_TRY(op_M<T>(C, C->vcur, skip));
+    BDDC_TRY(op_S<T>(C, C->zc, C->w, skip));
+    BDDC_TRY(gm_dots(C->V, n, C->w, n, C->gst, C->partial, C->hh, 0, C->gm_m + 1, C->st));
+    BDDC_TRY(gm_orth_update(C->V, n, C->w, n, C->gst, C->hh, C->st));
+    BDDC_TRY(gm_dots(C->V, n, C->w, n, C->gst, C->partial, C->hh2, 0, C->gm_m + 1, C->st));
+    BDDC_TRY(gm_orth_update(C->V, n, C->w, n, C->gst, C->hh2, C->st));
+    BDDC_TRY(gm_norm2(C->w, n, C->gst, C->partial, C->st));
+    BDDC_TRY(gm_givens(C->gst, C->H, C->cs, C->sn, C->gv, C->hh, C->hh2, C->st));
+    BDDC_TRY(gm_normalize(C->V, n, C->w, n, C->gst, C->st));
+    return BDDC_OK;
+}
+
+// GMRES on S x = b (device vectors of length nG); x is overwritten.
+template <class T>
+static int gmres(bddc_ctx* C, const double* b, double* x, double rtol, int max_iter, int* iters,
+                 double* relres, int* converged) {
+    const long long n = C->nG;
+    cudaStream_t st = C->st;
+    double bnorm = 0.0;
+    BDDC_TRY(norm2(C, b, n, &bnorm));
+    BDDC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    *iters = 0;
+    *converged = 0;
+    *relres = 0.0;
+    if (bnorm == 0.0) {
+        *converged = 1;
+        return BDDC_OK;
+    }
+    const int m = C->gm_m;
+    GmState init;
+    memset(&init, 0, sizeof(init));
+    init.m = m;
+    init.max_iter = max_iter;
+    init.tol = rtol * bnorm;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(C->gst, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+    const int K = 4;
+    const bool use_graph = getenv("BDDC_NO_GRAPH") == nullptr;
+    if (use_graph && (C->graph == nullptr || C->graph_iters != K)) {
+        if (C->graph) cudaGraphExecDestroy(C->graph);
+        C->graph = nullptr;
+        cudaGraph_t g;
+        BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = BDDC_OK;
+        for (int q = 0; q < K && rc == BDDC_OK; ++q) rc = gm_iteration<T>(C);
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (rc != BDDC_OK) return rc;
+        BDDC_CUDA_TRY(ce);
+        BDDC_CUDA_TRY(cudaGraphInstantiate(&C->graph, g, 0));
+        cudaGraphDestroy(g);
+        C->graph_iters = K;
+    }
+    int total = 0;
+    bool first = true;
+    while (true) {
+        // r = b - S x
+        if (first) {
+            BDDC_CUDA_TRY(cudaMemcpyAsync(C->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            BDDC_TRY(op_S<T>(C, x, C->r, nullptr));
+            BDDC_TRY(vec_axpby(C->r, b, 1.0, -1.0, n, st));
+        }
+        first = false;
+        BDDC_TRY(gm_cycle_start(C->r, n, C->gst, C->gv, C->partial, C->V, st));
+        for (int guard = 0; guard < 100000; ++guard) {
+            BDDC_CUDA_TRY(cudaMemcpyAsync(C->hst, C->gst, sizeof(GmState), cudaMemcpyDeviceToHost, st));
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            if (C->hst->stop) break;
+            if (use_graph) {
+                BDDC_CUDA_TRY(cudaGraphLaunch(C->graph, st));
+            } else {
+                for (int q = 0; q < K; ++q) BDDC_TRY(gm_iteration<T>(C));
+            }
+        }
+        total = C->hst->total;
+        if (C->hst->j > 0) {
+            BDDC_TRY(gm_finish(C->V, n, C->gst, C->H, C->gv, C->yy, C->t, n, st));
+            BDDC_TRY(op_M<T>(C, C->t, nullptr));
+            BDDC_TRY(vec_axpby(x, C->zc, 1.0, 1.0, n, st));
+        }
+        if (C->hst->converged || total >= max_iter) break;
+    }
+    // true residual
+    BDDC_TRY(op_S<T>(C, x, C->r, nullptr));
+    BDDC_TRY(vec_axpby(C->r, b, 1.0, -1.0, n, st));
+    double rn = 0.0;
+    BDDC_TRY(norm2(C, C->r, n, &rn));
+    *iters = total;
+    *relres = rn / bnorm;
+    *converged = C->hst->converged;
+    return BDDC_OK;
+}
+
+template <class T>
+static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* stt) {
+    cudaStream_t st = C->st;
+    HostMesh& hm = C->hm;
+    const long long nG = C->nG, ndof = hm.ndof;
+    int iters_total = 0, conv = 0, steps = 0;
+    double relres = 0.0;
+    double Fn = 0.0;
+    BDDC_TRY(norm2(C, Fdev, ndof, &Fn));
+    if (!C->mixed) {
+        BDDC_TRY(gather_run(Fdev, C->gamma_dofs, C->g, (int)nG, st));
+        BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, Fdev, C->g, C->ystore, 1, ndof, nG, C->ny, st));
+        int it = 0;
+        BDDC_TRY(gmres<T>(C, C->g, C->xG, C->o.rtol, C->o.max_iter, &it, &relres, &conv));
+        iters_total = it;
+        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, udev, 1, nG, ndof, C->ny, st));
+        steps = 1;
+    } else {
+        // FP64 iterative refinement on the global system with FP32 BDDC-GMRES as inner solver
+        BDDC_CUDA_TRY(cudaMemsetAsync(udev, 0, sizeof(double) * ndof, st));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(C->res, Fdev, sizeof(double) * ndof, cudaMemcpyDeviceToDevice, st));
+        double rn = Fn;
+        for (steps = 0; steps < C->o.max_refine; ++steps) {
+            if (Fn == 0.0 || rn <= C->o.rtol * Fn) {
+                conv = 1;
+                break;
+            }
+            BDDC_TRY(gather_run(C->res, C->gamma_dofs, C->g, (int)nG, st));
+            BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->res, C->g, C->ystore, 1, ndof, nG, C->ny, st));
+            int it = 0, cv = 0;
+            double rr = 0.0;
+            BDDC_TRY(gmres<T>(C, C->g, C->xG, C->o.inner_rtol, C->o.max_iter, &it, &rr, &cv));
+            iters_total += it;
+            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, C->corr, 1, nG, ndof, C->ny, st));
+            BDDC_TRY(vec_axpby(udev, C->corr, 1.0, 1.0, ndof, st));
+            BDDC_TRY(stencil_residual(hm, C->stencil, udev, Fdev, C->res, 1, st));
+            BDDC_TRY(norm2(C, C->res, ndof, &rn));
+            if (iters_total >= C->o.max_iter) {
+                ++steps;
+                break;
+            }
+        }
+        if (rn <= C->o.rtol * Fn) conv = 1;
+        relres = Fn > 0 ? rn / Fn : 0.0;
+    }
+    // global FP64 residual
+    BDDC_TRY(stencil_residual(hm, C->stencil, udev, Fdev, C->res, 1, st));
+    double rg = 0.0;
+    BDDC_TRY(norm2(C, C->res, ndof, &rg));
+    stt->iters = iters_total;
+    stt->refine_steps = steps;
+    stt->converged = conv;
+    stt->relres = relres;
+    stt->relres_global = Fn > 0 ? rg / Fn : 0.0;
+    return conv ? BDDC_OK : BDDC_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void bddc_default_opts(bddc_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->theta_E = 10.0;
+    o->theta_F = 0.0;
+    o->tau = 0.7;
+    o->precision = BDDC_PREC_FP64;
+    o->restart = 0;
+    o->max_iter = 300;
+    o->rtol = 1e-8;
+    o->edge_gep = BDDC_EDGE_NEW;
+    o->face_gep = 1;
+    o->all_primal = 0;
+    o->inner_rtol = 1e-6;
+    o->max_refine = 8;
+    o->learned_skip_p = -1.0;
+}
+
+const char* bddc_strerror(int code) {
+    switch (code) {
+        case BDDC_OK: return "ok";
+        case BDDC_NOT_CONVERGED: return "GMRES did not reach the tolerance";
+        case BDDC_EINVAL: return "invalid argument";
+        case BDDC_ENOMEM: return "out of device or host memory";
+        case BDDC_ECUDA: return g_last_error.empty() ? "CUDA error" : g_last_error.c_str();
+        case BDDC_EGEP: return "eigen iteration cap reached";
+        case BDDC_ETIMEOUT: return "bounded device wait gave up";
+        case BDDC_ENUMERIC: return "zero or non-finite pivot";
+        default: return "unknown error";
+    }
+}
+
+void bddc_destroy(bddc_ctx* C) {
+    if (!C) return;
+    if (C->graph) cudaGraphExecDestroy(C->graph);
+    if (C->st) cudaStreamSynchronize(C->st);
+    for (void* p : C->allocs) cudaFree(p);
+    if (C->own) cudaStreamDestroy(C->own);
+    if (C->hst) cudaFreeHost(C->hst);
+    if (C->scal) cudaFreeHost(C->scal);
+    delete C;
+}
+
+static int copy_coeff(bddc_ctx* C, double** dst, const double* src, size_t n, int mem) {
+    *dst = nullptr;
+    if (!src) return BDDC_OK;
+    BDDC_TRY(C->alloc(dst, n));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(*dst, src, n * sizeof(double),
+                                  mem == BDDC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, C->st));
+    return BDDC_OK;
+}
+
+static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, const bddc_partition* part) {
+    BDDC_TRY(build_host_mesh(mesh, part, C->hm));
+    HostMesh& hm = C->hm;
+    if (!k || !k->nu_elem) return BDDC_EINVAL;
+    if (k->mem == BDDC_MEM_HOST) {
+        for (int e = 0; e < hm.nelem; ++e)
+            if (!(k->nu_elem[e] > 0.0) || !std::isfinite(k->nu_elem[e])) return BDDC_EINVAL;
+    }
+    BDDC_TRY(copy_coeff(C, &C->nu, k->nu_elem, hm.nelem, k->mem));
+    BDDC_TRY(copy_coeff(C, &C->beta, k->beta_node, 3 * (size_t)hm.nnodes, k->mem));
+    BDDC_TRY(copy_coeff(C, &C->f, k->f_node, hm.nnodes, k->mem));
+    BDDC_TRY(copy_coeff(C, &C->divb, k->divb_node, hm.nnodes, k->mem));
+    for (int d = 0; d < 3; ++d) C->bconst[d] = k->beta_const[d];
+    C->c = k->c;
+    C->nG = (int)hm.gamma.size();
+    BDDC_TRY(C->alloc(&C->err, 1));
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->err, 0, sizeof(int), C->st));
+    BDDC_CUDA_TRY(cudaMallocHost(&C->hst, 2 * sizeof(GmState)));
+    BDDC_CUDA_TRY(cudaMallocHost(&C->scal, 64 * sizeof(double)));
+    if (C->mixed) BDDC_TRY(setup_impl<float>(C));
+    else BDDC_TRY(setup_impl<double>(C));
+    // solve buffers
+    const long long nG = C->nG, ndof = hm.ndof;
+    BDDC_TRY(C->alloc(&C->zc, nG + C->nPi + 1));
+    BDDC_TRY(C->alloc(&C->uPi, C->nPi + 1));
+    BDDC_TRY(C->alloc(&C->g, nG));
+    BDDC_TRY(C->alloc(&C->xG, nG));
+    BDDC_TRY(C->alloc(&C->r, nG));
+    BDDC_TRY(C->alloc(&C->w, nG));
+    BDDC_TRY(C->alloc(&C->vcur, nG));
+    BDDC_TRY(C->alloc(&C->t, nG));
+    BDDC_TRY(C->alloc(&C->res, ndof));
+    BDDC_TRY(C->alloc(&C->corr, ndof));
+    BDDC_TRY(C->alloc(&C->uglob, ndof));
+    BDDC_TRY(C->alloc(&C->Fin, ndof));
+    BDDC_TRY(C->alloc(&C->ystore, C->ny));
+    BDDC_TRY(C->upload(&C->gamma_dofs, hm.gamma));
+    int m = C->o.restart > 0 ? std::min(C->o.restart, C->o.max_iter) : C->o.max_iter;
+    m = std::max(m, 1);
+    C->gm_m = m;
+    BDDC_TRY(C->alloc(&C->V, (size_t)(m + 1) * nG));
+    BDDC_TRY(C->alloc(&C->H, (size_t)(m + 1) * (m + 1)));
+    BDDC_TRY(C->alloc(&C->cs, m + 1));
+    BDDC_TRY(C->alloc(&C->sn, m + 1));
+    BDDC_TRY(C->alloc(&C->gv, m + 2));
+    BDDC_TRY(C->alloc(&C->hh, m + 2));
+    BDDC_TRY(C->alloc(&C->hh2, m + 2));
+    BDDC_TRY(C->alloc(&C->yy, m + 1));
+    BDDC_TRY(C->alloc(&C->partial, (size_t)(m + 9) * (gm_nchunk(std::max(nG, ndof)) + 1)));
+    BDDC_TRY(C->alloc(&C->gst, 2));
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->gst, 0, 2 * sizeof(GmState), C->st));
+    int herr = 0;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&herr, C->err, sizeof(int), cudaMemcpyDeviceToHost, C->st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    if (herr & ERR_PIVOT) return BDDC_ENUMERIC;
+    if (herr & ERR_JACOBI) return BDDC_EGEP;
+    if (herr) return BDDC_ECUDA;
+    return BDDC_OK;
+}
+
+int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs, const bddc_partition* part,
+               double tol_eig, const bddc_opts* opts, void* stream, bddc_ctx** out) {
+    if (!out || !part || !coeffs) return BDDC_EINVAL;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        bddc_set_last_error("no CUDA device", __FILE__, __LINE__);
+        return BDDC_ECUDA;
+    }
+    bddc_ctx* C = new bddc_ctx();
+    if (opts) C->o = *opts;
+    else bddc_default_opts(&C->o);
+    if (tol_eig > 0) C->o.theta_E = tol_eig;
+    if (C->o.max_iter <= 0 || !(C->o.rtol >= 0) || C->o.restart < 0) {
+        delete C;
+        return BDDC_EINVAL;
+    }
+    C->mixed = C->o.precision == BDDC_PREC_MIXED;
+    C->st = (cudaStream_t)stream;
+    if (C->st == nullptr) {
+        // a blocking stream: ordered with the legacy default stream, and capturable
+        if (cudaStreamCreate(&C->own) != cudaSuccess) {
+            delete C;
+            return BDDC_ECUDA;
+        }
+        C->st = C->own;
+    }
+    memset(&C->stats, 0, sizeof(C->stats));
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = setup_body(C, mesh, coeffs, part);
+    if (rc != BDDC_OK) {
+        cudaStreamSynchronize(C->st);
+        bddc_destroy(C);
+        return rc;
+    }
+    C->stats.setup_ms = ms_since(t0);
+    C->stats.n_pi = C->nPi;
+    C->stats.n_gamma = C->nG;
+    C->stats.ndof = C->hm.ndof;
+    C->stats.nsub = C->hm.nsd;
+    *out = C;
+    return BDDC_OK;
+}
+
+int bddc_schur_apply(bddc_ctx* C, const double* x, double* y, int nrhs) {
+    if (!C || !x || !y || nrhs < 1) return BDDC_EINVAL;
+    for (int c = 0; c < nrhs; ++c) {
+        if (C->mixed) BDDC_TRY(op_S<float>(C, x + (long long)c * C->nG, y + (long long)c * C->nG, nullptr));
+        else BDDC_TRY(op_S<double>(C, x + (long long)c * C->nG, y + (long long)c * C->nG, nullptr));
+    }
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
+int bddc_apply(bddc_ctx* C, const double* r, double* z, int nrhs) {
+    if (!C || !r || !z || nrhs < 1) return BDDC_EINVAL;
+    for (int c = 0; c < nrhs; ++c) {
+        if (C->mixed) BDDC_TRY(op_M<float>(C, r + (long long)c * C->nG, nullptr));
+        else BDDC_TRY(op_M<double>(C, r + (long long)c * C->nG, nullptr));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(z + (long long)c * C->nG, C->zc, sizeof(double) * C->nG,
+                                      cudaMemcpyDeviceToDevice, C->st));
+    }
+    return BDDC_OK;
+}
+
+int bddc_gmres_solve(bddc_ctx* C, const double* load, double* u, int nrhs, int mem, bddc_stats* stats) {
+    if (!C || !u || nrhs < 1) return BDDC_EINVAL;
+    if (mem != BDDC_MEM_DEVICE && mem != BDDC_MEM_HOST) return BDDC_EINVAL;
+    auto t0 = std::chrono::steady_clock::now();
+    const long long ndof = C->hm.ndof;
+    int worst = BDDC_OK;
+    bddc_stats agg = C->stats;
+    agg.iters = 0;
+    agg.converged = 1;
+    agg.relres = 0;
+    agg.relres_global = 0;
+    agg.refine_steps = 0;
+    for (int c = 0; c < nrhs; ++c) {
+        const double* Fd = C->F;
+        if (load) {
+            if (mem == BDDC_MEM_HOST) {
+                BDDC_CUDA_TRY(cudaMemcpyAsync(C->Fin, load + c * ndof, sizeof(double) * ndof, cudaMemcpyHostToDevice, C->st));
+                Fd = C->Fin;
+            } else {
+                Fd = load + c * ndof;
+            }
+        }
+        double* ud = mem == BDDC_MEM_HOST ? C->uglob : u + c * ndof;
+        bddc_stats one = C->stats;
+        int rc = C->mixed ? solve_one<float>(C, Fd, ud, &one) : solve_one<double>(C, Fd, ud, &one);
+        if (rc < 0) return rc;
+        if (rc != BDDC_OK) worst = rc;
+        if (mem == BDDC_MEM_HOST)
+            BDDC_CUDA_TRY(cudaMemcpyAsync(u + c * ndof, C->uglob, sizeof(double) * ndof, cudaMemcpyDeviceToHost, C->st));
+        agg.iters += one.iters;
+        agg.refine_steps += one.refine_steps;
+        agg.converged = agg.converged && one.converged;
+        agg.relres = std::max(agg.relres, one.relres);
+        agg.relres_global = std::max(agg.relres_global, one.relres_global);
+    }
+    BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    agg.solve_ms = ms_since(t0);
+    C->stats.iters = agg.iters;
+    C->stats.refine_steps = agg.refine_steps;
+    C->stats.converged = agg.converged;
+    C->stats.relres = agg.relres;
+    C->stats.relres_global = agg.relres_global;
+    C->stats.solve_ms = agg.solve_ms;
+    if (stats) *stats = C->stats;
+    return worst;
+}
+
+int bddc_get_stats(const bddc_ctx* C, bddc_stats* s) {
+    if (!C || !s) return BDDC_EINVAL;
+    *s = C->stats;
+    return BDDC_OK;
+}
+
+int bddc_get_numbering(const bddc_ctx* C, int* gamma_dofs) {
+    if (!C || !gamma_dofs) return BDDC_EINVAL;
+    memcpy(gamma_dofs, C->hm.gamma.data(), sizeof(int) * C->hm.gamma.size());
+    return BDDC_OK;
+}
+
+int bddc_get_schur(const bddc_ctx* C, int s, double* out, int* n_b) {
+    if (!C || s < 0 || s >= C->hm.nsd || !n_b) return BDDC_EINVAL;
+    const int nB = C->hm.sub[s].nB;
+    *n_b = nB;
+    if (!out) return BDDC_OK;
+    BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    BDDC_CUDA_TRY(cudaMemcpy2D(out, sizeof(double) * nB, C->S64 + C->soff[s], sizeof(double) * C->sld[s],
+                               sizeof(double) * nB, nB, cudaMemcpyDeviceToHost));
+    return BDDC_OK;
+}
+
+int bddc_get_entity_count(const bddc_ctx* C, int kind) {
+    if (!C || kind < 0 || kind > 2) return BDDC_EINVAL;
+    return (int)C->hm.by_kind[kind].size();
+}
+
+int bddc_get_entity(const bddc_ctx* C, int kind, int index, int* subs, int* dofs, int* n, int* k,
+                    double* Q, double* lambda, int* n_eig) {
+    if (!C || kind < 0 || kind > 2 || index < 0 || index >= (int)C->hm.by_kind[kind].size()) return BDDC_EINVAL;
+    const int e = C->hm.by_kind[kind][index];
+    const Entity& E = C->hm.ent[e];
+    const int nn = (int)E.dofs.size();
+    if (n) *n = nn;
+    if (k) *k = E.k;
+    if (subs)
+        for (int a = 0; a < 8; ++a) subs[a] = a < (int)E.subs.size() ? E.subs[a] : -1;
+    if (dofs) memcpy(dofs, E.dofs.data(), sizeof(int) * nn);
+    if (n_eig) *n_eig = C->neig[e];
+    BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    if (Q && kind > 0) {
+        // device Q is row-major (row = entity dof, column = basis vector); return column-major n x k
+        std::vector<double> h((size_t)nn * nn);
+        BDDC_CUDA_TRY(cudaMemcpy(h.data(), C->Q[e], sizeof(double) * nn * nn, cudaMemcpyDeviceToHost));
+        for (int l = 0; l < E.k; ++l)
+            for (int a = 0; a < nn; ++a) Q[(size_t)l * nn + a] = h[(size_t)a * nn + l];
+    } else if (Q && kind == 0) {
+        Q[0] = 1.0;
+    }
+    if (lambda && kind > 0 && C->neig[e] > 0)
+        BDDC_CUDA_TRY(cudaMemcpy(lambda, C->lam[e], sizeof(double) * C->neig[e], cudaMemcpyDeviceToHost));
+    return BDDC_OK;
+}
+
+int bddc_get_edge_features(const bddc_ctx* C, float* feats, int* counts) {
+    (void)feats;
+    (void)counts;
+    if (!C) return BDDC_EINVAL;
+    return BDDC_EINVAL;
+}
+
+}  // extern "C"

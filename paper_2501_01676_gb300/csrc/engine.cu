@@ -1,0 +1,210 @@
+// Batched partial LU without pivoting ("Schur engine").
+//
+// For every item (a dense n x n row-major matrix M) eliminate the leading k
+// unknowns in place:
+//
+//   M = [ M11 M12 ]  ->  [ L11\U11   U12             ]
+//       [ M21 M22 ]      [ L21       M22 - L21 U12    ]
+//
+// so the trailing (n-k) x (n-k) block becomes the Schur complement
+// M22 - M21 M11^{-1} M12.  This one operation forms the subdomain Schur
+// complements S^(i) = A_BB - A_BI A_II^{-1} A_IB (Sect. 3), the face and
+// edge Schur complements of B^(i) used by the GEPs (Sect. 3), the
+// constrained local solvers and coarse bases (block elimination of S~), and
+// the explicit inverse of the coarse matrix.  Pivoting is not needed: every
+// eliminated block has a positive definite symmetric part (the forms b_i are
+// SPD and the primal constraints remove the constants), for which LU without
+// pivoting exists.  Zero / non-finite pivots are flagged, not trapped.
+//
+// Right-looking blocked algorithm, panel width NB.  Per panel two launches
+// batched over all items: (1) factor the NB x NB diagonal block (redundantly
+// in every CTA, in shared memory) and solve for the L21 row chunks and the
+// U12 column chunks; (2) the trailing update M22 -= L21 U12 in 64 x 64
+// tiles, register-blocked 4 x 4 per thread.
+#include <cuda_runtime.h>
+
+#include "bddc_internal.h"
+
+namespace {
+
+constexpr int PANEL_THREADS = 128;
+constexpr int CHUNK = 128;            // rows (or columns) per panel CTA
+constexpr int TILE = 64;
+constexpr int UPD_THREADS = 256;
+
+template <class T>
+__device__ __forceinline__ bool bad_pivot(T v) {
+    return !(fabs((double)v) > 1e-300) || !isfinite((double)v);
+}
+
+template <class T, int NB>
+__global__ void __launch_bounds__(PANEL_THREADS) k_panel(const EngItem<T>* __restrict__ items, int p,
+                                                         T* __restrict__ dscr, int* __restrict__ err) {
+    const EngItem<T> it = items[blockIdx.x];
+    if (p >= it.k) return;
+    const int w = min(NB, it.k - p);
+    const int n = it.n, ld = it.ld;
+    const int m0 = p + w;                      // first trailing index
+    const int mrem = n - m0;
+    const int nch = (mrem + CHUNK - 1) / CHUNK;
+    const int y = blockIdx.y;
+    if (y > 2 * nch) return;
+    __shared__ T D[NB][NB + 1];
+    __shared__ T W[NB][CHUNK + 1];             // row chunk (transposed) or column chunk
+    T* A = it.a;
+    const int t = threadIdx.x;
+    for (int q = t; q < w * w; q += PANEL_THREADS) {
+        int r = q / w, c = q % w;
+        D[r][c] = A[(long long)(p + r) * ld + p + c];
+    }
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        T piv = D[j][j];
+        if (bad_pivot(piv)) {
+            if (t == 0 && y == 0) atomicOr(err, ERR_PIVOT);
+            piv = (T)1;
+        }
+        for (int i = j + 1 + t; i < w; i += PANEL_THREADS) D[i][j] /= piv;
+        __syncthreads();
+        const int rem = w - j - 1;
+        for (int q = t; q < rem * rem; q += PANEL_THREADS) {
+            int i = j + 1 + q / rem, l = j + 1 + q % rem;
+            D[i][l] -= D[i][j] * D[j][l];
+        }
+        __syncthreads();
+    }
+    if (y == 0) {
+        T* ds = dscr + (long long)blockIdx.x * NB * NB;
+        for (int q = t; q < w * w; q += PANEL_THREADS) ds[q] = D[q / w][q % w];
+        return;
+    }
+    if (y <= nch) {
+        // rows r0 .. r0+CHUNK of L21 = M21 U11^{-1}
+        const int r0 = m0 + (y - 1) * CHUNK;
+        const int nr = min(CHUNK, n - r0);
+        for (int q = t; q < nr * w; q += PANEL_THREADS) {
+            int r = q / w, c = q % w;
+            W[c][r] = A[(long long)(r0 + r) * ld + p + c];
+        }
+        __syncthreads();
+        if (t < nr) {
+            for (int j = 0; j < w; ++j) {
+                T x = W[j][t];
+                for (int l = 0; l < j; ++l) x -= W[l][t] * D[l][j];
+                T piv = D[j][j];
+                if (bad_pivot(piv)) piv = (T)1;
+                W[j][t] = x / piv;
+            }
+        }
+        __syncthreads();
+        for (int q = t; q < nr * w; q += PANEL_THREADS) {
+            int r = q / w, c = q % w;
+            A[(long long)(r0 + r) * ld + p + c] = W[c][r];
+        }
+    } else {
+        // columns c0 .. c0+CHUNK of U12 = L11^{-1} M12
+        const int c0 = m0 + (y - 1 - nch) * CHUNK;
+        const int nc = min(CHUNK, n - c0);
+        for (int q = t; q < nc * w; q += PANEL_THREADS) {
+            int r = q / nc, c = q % nc;
+            W[r][c] = A[(long long)(p + r) * ld + c0 + c];
+        }
+        __syncthreads();
+        if (t < nc) {
+            for (int i = 1; i < w; ++i) {
+                T x = W[i][t];
+                for (int l = 0; l < i; ++l) x -= D[i][l] * W[l][t];
+                W[i][t] = x;
+            }
+        }
+        __syncthreads();
+        for (int q = t; q < nc * w; q += PANEL_THREADS) {
+            int r = q / nc, c = q % nc;
+            A[(long long)(p + r) * ld + c0 + c] = W[r][c];
+        }
+    }
+}
+
+template <class T, int NB>
+__global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __restrict__ items, int p,
+                                                        const T* __restrict__ dscr) {
+    const EngItem<T> it = items[blockIdx.x];
+    if (p >= it.k) return;
+    const int w = min(NB, it.k - p);
+    const int n = it.n, ld = it.ld;
+    const int m0 = p + w;
+    const int mrem = n - m0;
+    const int nt = (mrem + TILE - 1) / TILE;
+    const int y = blockIdx.y;
+    T* A = it.a;
+    const int t = threadIdx.x;
+    if (y == 0) {
+        const T* ds = dscr + (long long)blockIdx.x * NB * NB;
+        for (int q = t; q < w * w; q += UPD_THREADS) A[(long long)(p + q / w) * ld + p + q % w] = ds[q];
+        return;
+    }
+    if (y > nt * nt) return;
+    const int ti = (y - 1) / nt, tj = (y - 1) % nt;
+    const int r0 = m0 + ti * TILE, c0 = m0 + tj * TILE;
+    __shared__ T Ls[NB][TILE + 1];    // L21 tile, transposed: Ls[k][r]
+    __shared__ T Us[NB][TILE + 1];    // U12 tile: Us[k][c]
+    for (int q = t; q < TILE * w; q += UPD_THREADS) {
+        int r = q / w, k = q % w;
+        int gr = r0 + r;
+        Ls[k][r] = gr < n ? A[(long long)gr * ld + p + k] : (T)0;
+    }
+    for (int q = t; q < w * TILE; q += UPD_THREADS) {
+        int k = q / TILE, c = q % TILE;
+        int gc = c0 + c;
+        Us[k][c] = gc < n ? A[(long long)(p + k) * ld + gc] : (T)0;
+    }
+    __syncthreads();
+    const int tr = t / 16, tc = t % 16;   // 16 x 16 threads, 4 x 4 each (strided by 16)
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    for (int k = 0; k < w; ++k) {
+        T lv[4], uv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) lv[a] = Ls[k][tr + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) uv[b] = Us[k][tc + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        int gr = r0 + tr + 16 * a;
+        if (gr >= n) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int gc = c0 + tc + 16 * b;
+            if (gc < n) A[(long long)gr * ld + gc] -= acc[a][b];
+        }
+    }
+}
+
+}  // namespace
+
+template <class T>
+int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* dscr, int* err,
+               cudaStream_t st) {
+    constexpr int NB = 32;
+    if (count <= 0 || maxk <= 0) return BDDC_OK;
+    for (int p = 0; p < maxk; p += NB) {
+        int mrem = maxn - p;                 // upper bound of the trailing size
+        int nch = (mrem + CHUNK - 1) / CHUNK;
+        int nt = (mrem + TILE - 1) / TILE;
+        k_panel<T, NB><<<dim3(count, 1 + 2 * nch), PANEL_THREADS, 0, st>>>(items_dev, p, dscr, err);
+        k_update<T, NB><<<dim3(count, 1 + nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, dscr);
+    }
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
+template int engine_run<double>(const EngItem<double>*, int, int, int, double*, int*, cudaStream_t);
+template int engine_run<float>(const EngItem<float>*, int, int, int, float*, int*, cudaStream_t);

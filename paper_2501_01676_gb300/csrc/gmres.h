@@ -1,0 +1,36 @@
+// Device-resident scalar state of one GMRES cycle.
+#pragma once
+#include <cuda_runtime.h>
+
+struct GmState {
+    int j;           // Arnoldi index within the cycle (number of columns done)
+    int m;           // cycle length (restart, or the iteration cap)
+    int stop;        // 1: converged, cycle full or cap reached
+    int converged;
+    int total;       // iterations over all cycles
+    int max_iter;
+    int need_norm;
+    int pad;
+    double tol;      // absolute residual target rtol * ||b||
+    double beta;     // initial residual norm of the cycle
+    double res;      // current residual estimate |g_{j}|
+    double nrm2;     // squared norm of the new Krylov vector
+    double scale;    // 1 / norm used to normalise it
+};
+
+int gm_nchunk(long long n);
+int gm_dots(const double* V, long long ldv, const double* w, long long n, GmState* S, double* partial,
+            double* h, int mode, int max_rows, cudaStream_t st);
+int gm_norm2(const double* w, long long n, GmState* S, double* partial, cudaStream_t st);
+int gm_orth_update(const double* V, long long ldv, double* w, long long n, const GmState* S,
+                   const double* c, cudaStream_t st);
+int gm_givens(GmState* S, double* H, double* cs, double* sn, double* gv, const double* h,
+              const double* h2, cudaStream_t st);
+int gm_normalize(double* V, long long ldv, const double* w, long long n, GmState* S, cudaStream_t st);
+int gm_copy_row(const double* V, long long ldv, double* out, long long n, const GmState* S,
+                cudaStream_t st);
+int gm_cycle_start(const double* r, long long n, GmState* S, double* gv, double* partial, double* V0,
+                   cudaStream_t st);
+int gm_finish(const double* V, long long ldv, const GmState* S, const double* H, const double* gv,
+              double* y, double* t, long long n, cudaStream_t st);
+int vec_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st);

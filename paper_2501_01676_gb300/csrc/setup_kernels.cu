@@ -1,0 +1,234 @@
+// Data movement of the setup: gathers that build the engine's input matrices,
+// the change of basis T_i^T S T_i onto primal / dual coordinates, and the
+// extraction of the constrained-solver operators from the engine's output.
+//
+// Change of basis (Sect. 3, after eq. primal-constraints-F: "after performing
+// a change of basis"): on every face / edge X of subdomain i the interface
+// values are w_X = Q_X y_X with Q_X = [Q_X^Pi, Q_X^Delta] orthogonal; the
+// first k_X coordinates are primal.  T_i is block diagonal over the entities.
+#include <cuda_runtime.h>
+
+#include "bddc_internal.h"
+#include "setup_kernels.h"
+
+namespace {
+
+constexpr int TH = 256;
+
+template <class TS, class TD>
+__global__ void k_copy_blocks(const CopyJob* __restrict__ jobs) {
+    const CopyJob J = jobs[blockIdx.x];
+    const TS* src = (const TS*)J.src;
+    TD* dst = (TD*)J.dst;
+    const long long tot = (long long)J.rows * J.cols;
+    for (long long q = blockIdx.y * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.y * TH) {
+        int r = (int)(q / J.cols), c = (int)(q % J.cols);
+        double v = (double)src[(long long)(J.r0 + r) * J.sld + J.c0 + c];
+        dst[(long long)r * J.dld + c] = (TD)(J.scale * v);
+    }
+}
+
+// dst[a][b] = S[p_a][p_b] (optionally symmetrised), p = perm list
+template <class TD>
+__global__ void k_gather_perm(const GatherJob* __restrict__ jobs, const int* __restrict__ idx) {
+    const GatherJob J = jobs[blockIdx.x];
+    const int* p = idx + J.perm_off;
+    TD* dst = (TD*)J.dst;
+    const long long tot = (long long)J.n * J.n;
+    for (long long q = blockIdx.y * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.y * TH) {
+        int a = (int)(q / J.n), b = (int)(q % J.n);
+        long long ia = p[a], ib = p[b];
+        double v = J.src[ia * J.sld + ib];
+        if (J.sym) v = 0.5 * (v + J.src[ib * J.sld + ia]);
+        dst[(long long)a * J.dld + b] = (TD)v;
+    }
+}
+
+// Right multiplication Y[r][pos[l]] = sum_a B[r][pos[a]] Q[a][l] for one entity block.
+__global__ void k_transform_right(const TBlock* __restrict__ blocks, const int* __restrict__ idx) {
+    const TBlock B = blocks[blockIdx.x];
+    extern __shared__ double Qs[];
+    const int n = B.n;
+    const int* pos = idx + B.pos_off;
+    if (!B.identity)
+        for (int q = threadIdx.x; q < n * n; q += TH) Qs[q] = B.Q[q];
+    __syncthreads();
+    const long long tot = (long long)B.nrows * n;
+    for (long long q = blockIdx.y * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.y * TH) {
+        int r = (int)(q / n), l = (int)(q % n);
+        const double* row = B.src + (long long)r * B.sld;
+        double v;
+        if (B.identity) {
+            v = row[pos[l]];
+            if (B.sym) v = 0.5 * (v + B.src[(long long)pos[l] * B.sld + r]);
+        } else {
+            v = 0.0;
+            for (int a = 0; a < n; ++a) {
+                double s = row[pos[a]];
+                if (B.sym) s = 0.5 * (s + B.src[(long long)pos[a] * B.sld + r]);
+                v += s * Qs[a * n + l];
+            }
+        }
+        B.y[(long long)r * B.yld + pos[l]] = v;
+    }
+}
+
+// Left multiplication Z[pos[l]][c] = sum_a Q[a][l] Y[pos[a]][c] and the
+// permuted store X[perm[pos[l]]][perm[c]] = Z (entries with perm < 0 dropped).
+template <class TD>
+__global__ void k_transform_left(const TBlock* __restrict__ blocks, const int* __restrict__ idx) {
+    const TBlock B = blocks[blockIdx.x];
+    extern __shared__ double Qs[];
+    const int n = B.n;
+    const int* pos = idx + B.pos_off;
+    const int* perm = idx + B.perm_off;
+    if (!B.identity)
+        for (int q = threadIdx.x; q < n * n; q += TH) Qs[q] = B.Q[q];
+    __syncthreads();
+    TD* X = (TD*)B.dst;
+    const long long tot = (long long)n * B.nrows;
+    for (long long q = blockIdx.y * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.y * TH) {
+        int l = (int)(q / B.nrows), c = (int)(q % B.nrows);
+        int pr = perm[pos[l]], pc = perm[c];
+        if (pr < 0 || pc < 0) continue;
+        double v;
+        if (B.identity) v = B.y[(long long)pos[l] * B.yld + c];
+        else {
+            v = 0.0;
+            for (int a = 0; a < n; ++a) v += Qs[a * n + l] * B.y[(long long)pos[a] * B.yld + c];
+        }
+        X[(long long)pr * B.dld + pc] = (TD)v;
+    }
+}
+
+// X[nB + pos[a]][perm[pos[l]]] = DQ[a][l];  X[perm[pos[l]]][nB + pos[a]] = -DQ[a][l]
+template <class TD>
+__global__ void k_fill_dt(const DTJob* __restrict__ jobs, const int* __restrict__ idx) {
+    const DTJob J = jobs[blockIdx.x];
+    const int* pos = idx + J.pos_off;
+    const int* perm = idx + J.perm_off;
+    TD* X = (TD*)J.dst;
+    for (int q = threadIdx.x; q < J.n * J.n; q += TH) {
+        int a = q / J.n, l = q % J.n;
+        double v = J.DQ ? J.DQ[q] : (a == l ? J.scalar : 0.0);
+        int pc = perm[pos[l]];
+        X[(long long)(J.nB + pos[a]) * J.dld + pc] = (TD)v;
+        X[(long long)pc * J.dld + J.nB + pos[a]] = (TD)(-v);
+    }
+}
+
+// From the eliminated extended matrix of subdomain i
+//   [S_Pi,i | -Psi^T D^T ; D Phi | P]  (rows/cols from nD on)
+// write  S_Pi,i into the global coarse matrix (atomics), [P ; Psi^T D^T]
+// into the first apply pool and D Phi into the second.
+template <class TX, class TP>
+__global__ void k_extract(const ExtractJob* __restrict__ jobs, const int* __restrict__ idx,
+                          double* __restrict__ SPi, int nPi) {
+    const ExtractJob J = jobs[blockIdx.x];
+    const TX* X = (const TX*)J.X;
+    const int nB = J.nB, np = J.np, nd = nB - np;
+    const int* rpi = idx + J.rpi_off;
+    TP* MA = (TP*)J.MA;
+    TP* MC = (TP*)J.MC;
+    const long long t0 = blockIdx.y * (long long)TH + threadIdx.x, step = (long long)gridDim.y * TH;
+    for (long long q = t0; q < (long long)np * np; q += step) {
+        int a = (int)(q / np), b = (int)(q % np);
+        atomicAdd(&SPi[(long long)rpi[a] * nPi + rpi[b]], (double)X[(long long)(nd + a) * J.xld + nd + b]);
+    }
+    for (long long q = t0; q < (long long)nB * nB; q += step) {
+        int a = (int)(q / nB), b = (int)(q % nB);
+        MA[(long long)a * J.ald + b] = (TP)X[(long long)(nB + a) * J.xld + nB + b];
+    }
+    for (long long q = t0; q < (long long)np * nB; q += step) {
+        int a = (int)(q / nB), b = (int)(q % nB);
+        MA[(long long)(nB + a) * J.ald + b] = (TP)(-(double)X[(long long)(nd + a) * J.xld + nB + b]);
+    }
+    for (long long q = t0; q < (long long)nB * np; q += step) {
+        int a = (int)(q / np), b = (int)(q % np);
+        MC[(long long)a * J.cld + b] = (TP)X[(long long)(nB + a) * J.xld + nd + b];
+    }
+}
+
+__global__ void k_coarse_ext(const double* __restrict__ SPi, double* __restrict__ X, int n) {
+    // X = [[S_Pi, -I], [I, 0]] (2n x 2n, ld 2n)
+    const long long tot = 4LL * n * n;
+    for (long long q = blockIdx.x * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.x * TH) {
+        int a = (int)(q / (2 * n)), b = (int)(q % (2 * n));
+        double v;
+        if (a < n && b < n) v = SPi[(long long)a * n + b];
+        else if (a < n) v = (b - n == a) ? -1.0 : 0.0;
+        else if (b < n) v = (a - n == b) ? 1.0 : 0.0;
+        else v = 0.0;
+        X[q] = v;
+    }
+}
+
+}  // namespace
+
+template <class TS, class TD>
+int copy_blocks_run(const CopyJob* jobs, int count, int ychunks, cudaStream_t st) {
+    if (count <= 0) return BDDC_OK;
+    k_copy_blocks<TS, TD><<<dim3(count, ychunks), TH, 0, st>>>(jobs);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+template int copy_blocks_run<double, double>(const CopyJob*, int, int, cudaStream_t);
+template int copy_blocks_run<float, double>(const CopyJob*, int, int, cudaStream_t);
+template int copy_blocks_run<float, float>(const CopyJob*, int, int, cudaStream_t);
+template int copy_blocks_run<double, float>(const CopyJob*, int, int, cudaStream_t);
+
+template <class TD>
+int gather_perm_run(const GatherJob* jobs, int count, const int* idx, int ychunks, cudaStream_t st) {
+    if (count <= 0) return BDDC_OK;
+    k_gather_perm<TD><<<dim3(count, ychunks), TH, 0, st>>>(jobs, idx);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+template int gather_perm_run<double>(const GatherJob*, int, const int*, int, cudaStream_t);
+template int gather_perm_run<float>(const GatherJob*, int, const int*, int, cudaStream_t);
+
+template <class TD>
+int transform_run(const TBlock* blocks, int count, const int* idx, int maxn, int ychunks, cudaStream_t st) {
+    if (count <= 0) return BDDC_OK;
+    size_t smem = (size_t)maxn * maxn * sizeof(double);
+    if (smem > 200 * 1024) return BDDC_EINVAL;
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_left<TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_transform_right<<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
+    k_transform_left<TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+template int transform_run<double>(const TBlock*, int, const int*, int, int, cudaStream_t);
+template int transform_run<float>(const TBlock*, int, const int*, int, int, cudaStream_t);
+
+template <class TD>
+int fill_dt_run(const DTJob* jobs, int count, const int* idx, cudaStream_t st) {
+    if (count <= 0) return BDDC_OK;
+    k_fill_dt<TD><<<count, TH, 0, st>>>(jobs, idx);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+template int fill_dt_run<double>(const DTJob*, int, const int*, cudaStream_t);
+template int fill_dt_run<float>(const DTJob*, int, const int*, cudaStream_t);
+
+template <class TX, class TP>
+int extract_run(const ExtractJob* jobs, int count, const int* idx, double* SPi, int nPi, int ychunks,
+                cudaStream_t st) {
+    if (count <= 0) return BDDC_OK;
+    k_extract<TX, TP><<<dim3(count, ychunks), TH, 0, st>>>(jobs, idx, SPi, nPi);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+template int extract_run<double, double>(const ExtractJob*, int, const int*, double*, int, int, cudaStream_t);
+template int extract_run<float, float>(const ExtractJob*, int, const int*, double*, int, int, cudaStream_t);
+
+int coarse_ext_run(const double* SPi, double* X, int n, cudaStream_t st) {
+    if (n <= 0) return BDDC_OK;
+    long long tot = 4LL * n * n;
+    int g = (int)((tot + TH - 1) / TH);
+    if (g > 4096) g = 4096;
+    k_coarse_ext<<<g, TH, 0, st>>>(SPi, X, n);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}

@@ -1,0 +1,198 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several engine panels (n_I up to 343, panel width 32) and ragged
+tails (uneven slabs).  Tolerances (FP64 path): matrices and vectors 1e-10
+relative to their largest entry (a few hundred FP64 roundings of sums of
+O(1) terms); eigenvalues 1e-8 relative; constraint spans compared by
+principal angles (1e-7), since eigenvectors are unique only up to sign and
+rotation inside clusters; the solution 1e-8 relative to the oracle's direct
+solve when GMRES runs to 1e-12.
+"""
+import numpy as np
+import pytest
+
+from oracle import bddc as obddc
+from oracle import fem
+from paper_2501_01676_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def solver(p, **kw):
+    from paper_2501_01676_gb300.bddc import Solver
+    return Solver(p, **kw)
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+CASES = {
+    'r222m3': lambda: W.random_small(1, (2, 2, 2), 3, (-3, 3)),
+    'r333m3': lambda: W.random_small(1, (3, 3, 3), 3, (-3, 3)),
+    'uneven': lambda: _uneven(),
+    'c1': W.config1,
+}
+
+
+def _uneven():
+    p = W.random_small(5, (2, 3, 2), 4, (-2, 1))
+    p.slabs = [[3, 5], [4, 2, 3], [6, 4]]
+    ne = [sum(s) for s in p.slabs]
+    _, _, X, Y, Z = W._grid(p.slabs)
+    rng = np.random.default_rng(9)
+    p.nu_elem = 10.0 ** rng.uniform(-2, 1, ne[0] * ne[1] * ne[2])
+    p.beta_node = np.stack([-(Y - 0.5), X - 0.5, np.full_like(X, 0.1)], axis=1)
+    p.f_node = rng.standard_normal(X.size)
+    return p
+
+
+_oracles = {}
+
+
+def oracle_for(name, **kw):
+    key = (name, tuple(sorted(kw.items())))
+    if key not in _oracles:
+        _oracles[key] = obddc.BDDC(CASES[name](), **kw)
+    return _oracles[key]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_numbering_and_schur(name):
+    o = oracle_for(name)
+    s = solver(o.prob)
+    assert np.array_equal(s.numbering(), o.mesh.gamma)
+    for sd in range(o.mesh.nsd):
+        S = s.schur(sd)
+        assert rel(S, o.S[sd]) < 1e-10, (sd, rel(S, o.S[sd]))
+
+
+@pytest.mark.parametrize("name", ['r222m3', 'uneven', 'c1'])
+def test_schur_apply(name):
+    import torch
+    o = oracle_for(name)
+    s = solver(o.prob)
+    x = np.random.default_rng(3).standard_normal(o.nG)
+    y = s.schur_apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, o.apply_S(x)) < 1e-10
+
+
+def _match_entities(s, o, kind_code, kind_char):
+    ge = s.entities(kind_code)
+    oe = [(i, e) for i, e in enumerate(o.mesh.entities) if e['kind'] == kind_char]
+    assert len(ge) == len(oe)
+    by = {e['subs']: (i, e) for i, e in oe}
+    out = []
+    for g in ge:
+        i, e = by[g['subs']]
+        assert np.array_equal(g['dofs'], e['dofs'])
+        out.append((g, i, e))
+    return out
+
+
+def _span_equal(Qa, Qb):
+    assert Qa.shape == Qb.shape
+    if Qa.shape[1] == 0:
+        return
+    sv = np.linalg.svd(Qa.T @ Qb, compute_uv=False)
+    assert np.abs(sv - 1.0).max() < 1e-7, sv
+
+
+@pytest.mark.parametrize("name,theta_E", [('r333m3', 1.5), ('r222m3', 1.5), ('uneven', 2.0), ('c1', 10.0)])
+def test_face_and_edge_constraints(name, theta_E):
+    o = oracle_for(name, theta_E=theta_E)
+    s = solver(o.prob, theta_E=theta_E)
+    for kind_code, kind_char, info in ((2, 'F', o.face_info), (1, 'E', o.edge_info)):
+        for g, i, e in _match_entities(s, o, kind_code, kind_char):
+            ref = info[i]
+            lam_o = ref['lam']
+            lam_g = g['lam']
+            assert len(lam_g) == len(lam_o)
+            fin = np.isfinite(lam_o)
+            assert np.array_equal(fin, np.isfinite(lam_g))
+            np.testing.assert_allclose(lam_g[fin], lam_o[fin], rtol=1e-8, atol=1e-12)
+            assert g['k'] == o.Q[i].shape[1], (kind_char, g['subs'], g['k'], o.Q[i].shape[1], lam_o)
+            _span_equal(g['Q'], o.Q[i])
+    st = s.stats()
+    assert st['pnumF'] == o.pnumF and st['pnumE'] == o.pnumE and st['n_pi'] == o.nPi
+
+
+@pytest.mark.parametrize("name,theta_E", [('r333m3', 1.5), ('uneven', 10.0), ('c1', 10.0)])
+def test_preconditioner_apply(name, theta_E):
+    import torch
+    o = oracle_for(name, theta_E=theta_E)
+    s = solver(o.prob, theta_E=theta_E)
+    r = np.random.default_rng(4).standard_normal(o.nG)
+    z = s.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert rel(z, o.apply_M(r)) < 1e-9
+
+
+def test_all_primal_one_iteration():
+    p = W.random_small(3, (2, 2, 2), 3, (-2, 1))
+    s = solver(p, all_primal=1, rtol=1e-12)
+    u, st = s.solve()
+    assert st['iters'] == 1
+    o = obddc.BDDC(p, all_primal=True)
+    ustar = fem.direct_solve(o.A, o.F)
+    assert rel(u.cpu().numpy(), ustar) < 1e-9
+
+
+@pytest.mark.parametrize("name", ['r333m3', 'uneven', 'c1'])
+def test_solve_matches_oracle(name):
+    o = oracle_for(name)
+    ustar = fem.direct_solve(o.A, o.F)
+    s = solver(o.prob, rtol=1e-12)
+    u, st = s.solve()
+    u = u.cpu().numpy()
+    assert np.linalg.norm(u - ustar) / np.linalg.norm(ustar) < 1e-8
+    _, info = o.solve(rtol=1e-12)
+    assert abs(st['iters'] - info['iters']) <= 1
+    # default tolerance: iteration count of the paper's stopping rule
+    s2 = solver(o.prob)
+    u2, st2 = s2.solve()
+    _, info2 = o.solve()
+    assert abs(st2['iters'] - info2['iters']) <= 1
+    assert st2['relres'] <= 1e-8
+
+
+def test_host_and_device_entry_points_agree():
+    p = CASES['uneven']()
+    s1 = solver(p, host=True)
+    s2 = solver(p)
+    u1, _ = s1.solve(host=True)
+    u2, _ = s2.solve()
+    assert rel(u1, u2.cpu().numpy()) < 1e-12
+
+
+def test_mixed_precision_refinement():
+    o = oracle_for('r333m3')
+    ustar = fem.direct_solve(o.A, o.F)
+    s = solver(o.prob, precision=1, rtol=1e-12)
+    u, st = s.solve()
+    err = np.linalg.norm(u.cpu().numpy() - ustar) / np.linalg.norm(ustar)
+    assert st['converged'] and err < 1e-8, (err, st)
+    # FP32 Schur complement vs FP64 oracle: per-result bound of the FP32 factorisation
+    for sd in range(o.mesh.nsd):
+        assert rel(s.schur(sd), o.S[sd]) < 1e-4
+
+
+def test_config2_full_size():
+    """The benchmark workload (4x4x4 subdomains, H/h = 8): full oracle comparison."""
+    p = W.config2()
+    o = obddc.BDDC(p)
+    ustar = fem.direct_solve(o.A, o.F)
+    s = solver(p)
+    for sd in (0, 21, 63):
+        assert rel(s.schur(sd), o.S[sd]) < 1e-10
+    u, st = s.solve()
+    _, info = o.solve()
+    assert st['pnumF'] == o.pnumF and st['pnumE'] == o.pnumE
+    assert abs(st['iters'] - info['iters']) <= 1
+    assert st['relres'] <= 1e-8
+    err = np.linalg.norm(u.cpu().numpy() - ustar) / np.linalg.norm(ustar)
+    assert err < 1e-6
+    sm = solver(p, precision=1)
+    um, stm = sm.solve()
+    assert stm['relres'] <= 1e-8 and stm['converged']
+    errm = np.linalg.norm(um.cpu().numpy() - ustar) / np.linalg.norm(ustar)
+    assert errm < 1e-6
