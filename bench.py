@@ -1,0 +1,314 @@
+"""Benchmark: time to solve the advection-diffusion Schur system with adaptive
+BDDC-GMRES to relative residual 1e-8 on one GB300.
+
+Workload (default): 4x4x4 subdomains, H/h = 8 (32^3 hexahedra, 29 791 dofs),
+nu = 0.01, beta = (1, 0.5, 0.25), f = 1, GMRES(50), Theta_E = 10,
+Theta_F = 1 + ln 8.  A step is the whole hot path for one synthetic input:
+assembly, batched subdomain factorisation and Schur complements, face GEPs,
+edge GEPs on prior-selected primal constraints, constrained local solvers,
+coarse space, then condensation, preconditioned GMRES and interior recovery,
+in the mixed-precision solver (FP32 factors and operators, FP64 refinement).
+The plain FP64 GPU path is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle as it stands on the host cores.
+Under torchrun (N > 1) each rank solves its own independent replica (the
+solver is single-GPU) and rank 0 prints the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "BDDC-GMRES time to rel.res 1e-8 (setup + solve)"
+WORKLOAD = "4x4x4 subdomains, H/h=8 (32^3 Q1 hexes, 29791 dofs), nu=0.01, beta=(1,0.5,0.25), f=1, GMRES(50)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            P = json.load(f)
+        return P.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, dist
+
+
+def barrier(dist):
+    import torch
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(dist, v):
+    import torch
+    if dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        try:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+        except Exception:
+            pass
+        try:
+            dev = int(os.environ.get("LOCAL_RANK", "0"))
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+            rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(dev)]
+            sm = [float(r[1]) for r in rows if r[1].replace('.', '', 1).isdigit()]
+            mx = [float(r[2]) for r in rows if r[2].replace('.', '', 1).isdigit()]
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = set()
+            for r in rows:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                   "reasons": sorted(reasons), "samples": len(rows)}
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        return out
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2501_01676_gb300 import bddc as B
+    from paper_2501_01676_gb300 import workloads as W
+
+    rank, ws, dist = dist_init()
+    torch.cuda.init()
+    B.lib()
+    p = W.config2()
+    arrays = B.resident_arrays(p)
+    pinned = B.resident_arrays(p, pinned_host=True)
+    stream = torch.cuda.Stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    torch.cuda.synchronize()
+
+    def step(precision, timed_events=None):
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s = B.Solver(p, stream=stream, arrays=arrays, precision=precision)
+            u, st = s.solve()
+            e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.close()
+        return ms, st, u
+
+    if args.part == "fp64":
+        for _ in range(args.warmup + args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            ms, st, _ = step(B.PREC_FP64)
+        if rank == 0:
+            print(json.dumps({"part": "fp64", "ms": ms, "iters": st["iters"]}), flush=True)
+        return
+    # warm-up
+    for _ in range(args.warmup):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        step(B.PREC_MIXED)
+    times, stats = [], None
+    clocks = Clocks()
+    barrier(dist)
+    clocks.start()
+    l0 = B.kernel_launches()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        ms, st, u = step(B.PREC_MIXED)
+        times.append(ms)
+        stats = st
+    barrier(dist)
+    t_wall = time.perf_counter() - t_wall0
+    launches = B.kernel_launches() - l0
+    ck = clocks.stop()
+    ms_step = max_over_ranks(dist, sum(times) / len(times))
+    if args.part == "mixed":
+        if rank == 0:
+            print(json.dumps({"part": "mixed", "ms": ms_step, "iters": stats["iters"],
+                              "launches": int(launches)}), flush=True)
+        return
+    # plain FP64 GPU path on the same GPU
+    fp64_times, st64 = [], None
+    flush_l2(flush)
+    torch.cuda.synchronize()
+    step(B.PREC_FP64)
+    for _ in range(max(1, min(args.steps, 3))):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        ms, st64, _ = step(B.PREC_FP64)
+        fp64_times.append(ms)
+    ms64 = max_over_ranks(dist, sum(fp64_times) / len(fp64_times))
+    # end to end through the C ABI with host (pinned) buffers
+    e2e_times = []
+    h2d = sum(v.numel() * 8 for v in pinned.values() if v is not None)
+    d2h = 8 * stats["ndof"]
+    for r in range(args.warmup + args.steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = B.Solver(p, host=True, stream=stream, arrays=pinned, precision=B.PREC_MIXED)
+        u_host, _ = s.solve(host=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s.close()
+        if r >= args.warmup:
+            e2e_times.append((t1 - t0) * 1e3)
+    e2e_ms = max_over_ranks(dist, sum(e2e_times) / len(e2e_times))
+    hbm, which = peaks()
+    out = {
+        "metric": METRIC, "value": round(ms_step, 4), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "subdomains": 64, "H_over_h": 8, "global_batch": 1,
+                   "parallelism": "replicas" if ws > 1 else "single-gpu", "l2_flush": True,
+                   "inputs": "device-resident FP64 coefficient arrays"},
+        "iters": stats["iters"], "refine_steps": stats["refine_steps"], "relres": stats["relres"],
+        "relres_global": stats["relres_global"], "pnumF": stats["pnumF"], "pnumE": stats["pnumE"],
+        "n_pi": stats["n_pi"],
+        "plain_fp64_ms": round(ms64, 4), "plain_fp64_iters": st64["iters"],
+        "speedup_vs_fp64": round(ms64 / ms_step, 3),
+        "setup_breakdown_ms": {k: round(stats[k], 3) for k in ("t_assemble_ms", "t_factor_ms", "t_face_ms",
+                                                               "t_edge_ms", "t_coarse_ms")},
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "wall_s_timed": round(t_wall, 3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(p):
+    """The FP64 oracle as it stands (setup + BDDC-GMRES) on the host cores."""
+    from oracle import bddc as ob
+    t0 = time.perf_counter()
+    o = ob.BDDC(p)
+    _, info = o.solve()
+    dt = time.perf_counter() - t0
+    return {"value": round(dt * 1e3, 1), "unit": "ms", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": "the full workload once (oracle setup + GMRES, numpy/scipy FP64)",
+            "iters": info["iters"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import bddc as ob
+    from paper_2501_01676_gb300 import workloads as W
+    p = W.config2()
+    times, info = [], None
+    for r in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        o = ob.BDDC(p)
+        _, info = o.solve()
+        dt = (time.perf_counter() - t0) * 1e3
+        if r >= args.warmup:
+            times.append(dt)
+    v = sum(times) / len(times)
+    cores = len(os.sched_getaffinity(0))
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "subdomains": 64, "H_over_h": 8},
+           "iters": info["iters"], "pnumF": info["pnumF"], "pnumE": info["pnumE"],
+           "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+                            "sample": "the full workload per step (oracle setup + GMRES)"},
+           "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--part", default="all", choices=["all", "mixed", "fp64"],
+                    help="all: the full JSON line; mixed/fp64: time only that path (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: at least 3 warm-up steps are required for a valid number", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

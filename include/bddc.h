@@ -151,6 +151,10 @@ const char* bddc_strerror(int code);
 
 /* ---- introspection (tests and benchmarks; host output buffers) ---------- */
 
+/* Process-wide number of kernels the library has launched so far (a CUDA
+ * graph replay counts its kernel nodes).  Host-only, never fails. */
+unsigned long long bddc_kernel_launches(void);
+
 /* Global dof id of each interface position (n_gamma ints). */
 int bddc_get_numbering(const bddc_ctx* ctx, int* gamma_dofs);
 

@@ -81,13 +81,19 @@ def lib():
     L.bddc_get_entity_count.argtypes = [vp, ct.c_int]
     L.bddc_get_entity.argtypes = [vp, ct.c_int, ct.c_int, ip, ip, ip, ip, dp, dp, ip]
     L.bddc_get_edge_features.argtypes = [vp, ct.POINTER(ct.c_float), ip]
+    L.bddc_kernel_launches.argtypes = []
+    L.bddc_kernel_launches.restype = ct.c_ulonglong
     _lib = L
     return L
 
 
 EXPORTED = ["bddc_default_opts", "bddc_setup", "bddc_apply", "bddc_schur_apply", "bddc_gmres_solve",
             "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_get_numbering", "bddc_get_schur",
-            "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features"]
+            "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features", "bddc_kernel_launches"]
+
+
+def kernel_launches():
+    return int(lib().bddc_kernel_launches())
 
 
 class BDDCError(RuntimeError):
@@ -117,6 +123,21 @@ def _ptr(t):
     return ct.c_void_p(t.data_ptr())
 
 
+def resident_arrays(problem, pinned_host=False):
+    """Coefficient arrays of `problem` as torch tensors: on the device, or in
+    pinned host memory (for end-to-end timing through host pointers)."""
+    import torch
+    out = {}
+    for name in ("nu_elem", "beta_node", "f_node"):
+        arr = getattr(problem, name)
+        if arr is None:
+            out[name] = None
+            continue
+        t = torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float64).ravel())
+        out[name] = t.pin_memory() if pinned_host else t.cuda()
+    return out
+
+
 class Solver:
     """One setup of the adaptive BDDC solver on the current CUDA device.
 
@@ -124,7 +145,7 @@ class Solver:
     from host memory, otherwise they are first placed on the device.
     """
 
-    def __init__(self, problem, host=False, stream=None, **opts):
+    def __init__(self, problem, host=False, stream=None, arrays=None, **opts):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libbddc needs a CUDA GPU")
@@ -150,6 +171,10 @@ class Solver:
         self._keep = []
         fields = {"nu_elem": problem.nu_elem, "beta_node": problem.beta_node, "f_node": problem.f_node}
         for name, arr in fields.items():
+            if arrays is not None:
+                t = arrays.get(name)
+                setattr(co, name, None if t is None else t.data_ptr())
+                continue
             if arr is None:
                 setattr(co, name, None)
                 continue

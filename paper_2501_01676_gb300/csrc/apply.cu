@@ -101,6 +101,7 @@ int gemv_run(const T* pool, const GemvItem* items_dev, int nitems, const int* id
     if (maxcols > GEMV_MAXCOLS) return BDDC_EINVAL;
     k_gemv<T><<<nitems, GEMV_THREADS, 0, st>>>(pool, items_dev, idx, in, out, nrhs, in_ld, out_ld,
                                                skip);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -260,6 +261,7 @@ int condense_run(const T* pool, const void* items, int count, const int* lists, 
                  cudaStream_t st) {
     k_condense<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, F, g, ystore,
                                                  nrhs, ldF, ldG, ldY);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -270,6 +272,7 @@ int recover_run(const T* pool, const void* items, int count, const int* lists, c
                 long long ldY, cudaStream_t st) {
     k_recover<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, uG, ystore, u,
                                                 nrhs, ldG, ldU, ldY);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -311,6 +314,7 @@ __global__ void k_gather(const double* __restrict__ src, const int* __restrict__
 int gather_run(const double* src, const int* idx, double* dst, int n, cudaStream_t st) {
     if (n <= 0) return BDDC_OK;
     k_gather<<<(n + 255) / 256, 256, 0, st>>>(src, idx, dst, n);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }

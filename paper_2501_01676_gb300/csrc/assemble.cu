@@ -207,6 +207,7 @@ int assemble_launch(const HostMesh& hm, const double* nu, const double* beta, co
     k_assemble<TA><<<hm.nelem, 64, 0, st>>>(nu, beta, f, divb, bc, slab_x, slab_y, slab_z, hm.nsub[0],
                                             hm.nsub[1], lut, lut_off, box0, boxn, Aloc, a_off, a_ld,
                                             stencil, F);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -250,6 +251,7 @@ int stencil_residual(const HostMesh& hm, const double* S, const double* u, const
     int th = 256;
     k_stencil_residual<<<(unsigned)((n + th - 1) / th), th, 0, st>>>(
         S, u, F, r, hm.E[0] - 1, hm.E[1] - 1, hm.E[2] - 1, nrhs, n);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }

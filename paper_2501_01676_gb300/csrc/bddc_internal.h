@@ -26,6 +26,11 @@
 
 void bddc_set_last_error(const char* msg, const char* file, int line);
 
+// Process-wide count of kernels launched by the library (launches recorded
+// while a stream is being captured are not counted; graph replays add their
+// kernel nodes).
+void bddc_note_launches(unsigned long long n);
+
 // Device-side error flags written by kernels (never trap).
 enum {
     ERR_PIVOT = 1,        // zero / non-finite pivot in the batched LU

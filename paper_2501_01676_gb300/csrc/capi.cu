@@ -55,7 +55,13 @@ void tri_item_fill(void* dst, long long aoff, int n, int nI, int ld, int dof_off
 int gather_run(const double* src, const int* idx, double* dst, int n, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
+#include <atomic>
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local bool g_capturing = false;
+void bddc_note_launches(unsigned long long n) {
+    if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 void bddc_set_last_error(const char* msg, const char* file, int line) {
     char buf[512];
     snprintf(buf, sizeof(buf), "%s (%s:%d)", msg, file, line);
@@ -149,6 +155,7 @@ struct bddc_ctx {
     GmState* hst = nullptr;     // pinned host copy
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
+    unsigned long long graph_kernels = 0;
     int* err = nullptr;
     double* scal = nullptr;     // pinned host scratch
 };
@@ -980,11 +987,23 @@ static int gmres(bddc_ctx* C, const double* b, double* x, double rtol, int max_i
         C->graph = nullptr;
         cudaGraph_t g;
         BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        g_capturing = true;
         int rc = BDDC_OK;
         for (int q = 0; q < K && rc == BDDC_OK; ++q) rc = gm_iteration<T>(C);
+        g_capturing = false;
         cudaError_t ce = cudaStreamEndCapture(st, &g);
         if (rc != BDDC_OK) return rc;
         BDDC_CUDA_TRY(ce);
+        size_t nn = 0;
+        BDDC_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        BDDC_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+        C->graph_kernels = 0;
+        for (auto& nd : nodes) {
+            cudaGraphNodeType ty;
+            BDDC_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+            if (ty == cudaGraphNodeTypeKernel) ++C->graph_kernels;
+        }
         BDDC_CUDA_TRY(cudaGraphInstantiate(&C->graph, g, 0));
         cudaGraphDestroy(g);
         C->graph_iters = K;
@@ -1007,6 +1026,7 @@ static int gmres(bddc_ctx* C, const double* b, double* x, double rtol, int max_i
             if (C->hst->stop) break;
             if (use_graph) {
                 BDDC_CUDA_TRY(cudaGraphLaunch(C->graph, st));
+                bddc_note_launches(C->graph_kernels);
             } else {
                 for (int q = 0; q < K; ++q) BDDC_TRY(gm_iteration<T>(C));
             }
@@ -1370,6 +1390,8 @@ int bddc_get_entity(const bddc_ctx* C, int kind, int index, int* subs, int* dofs
         BDDC_CUDA_TRY(cudaMemcpy(lambda, C->lam[e], sizeof(double) * C->neig[e], cudaMemcpyDeviceToHost));
     return BDDC_OK;
 }
+
+unsigned long long bddc_kernel_launches(void) { return g_launches.load(); }
 
 int bddc_get_edge_features(const bddc_ctx* C, float* feats, int* counts) {
     (void)feats;

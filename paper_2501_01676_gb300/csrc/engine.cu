@@ -200,7 +200,9 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         int nch = (mrem + CHUNK - 1) / CHUNK;
         int nt = (mrem + TILE - 1) / TILE;
         k_panel<T, NB><<<dim3(count, 1 + 2 * nch), PANEL_THREADS, 0, st>>>(items_dev, p, dscr, err);
+    bddc_note_launches(1);
         k_update<T, NB><<<dim3(count, 1 + nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, dscr);
+    bddc_note_launches(1);
     }
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;

@@ -712,6 +712,7 @@ int face_run(const FaceJob* jobs_dev, int count, int maxn, int* err, cudaStream_
     if (np > 128 || smem > 200 * 1024) return BDDC_EINVAL;
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_face, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_face<<<count, GT, smem, st>>>(jobs_dev, err);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -723,6 +724,7 @@ int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, int* err,
     if (np > 128 || smem > 200 * 1024 || maxnz > 1024) return BDDC_EINVAL;
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_edge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_edge<<<count, GT, smem, st>>>(jobs_dev, err);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }

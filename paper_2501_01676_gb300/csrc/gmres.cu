@@ -226,7 +226,9 @@ int gm_dots(const double* V, long long ldv, const double* w, long long n, GmStat
     int nchunk = gm_nchunk(n);
     dim3 grid(nchunk, (max_rows + DOT_ROWS - 1) / DOT_ROWS);
     k_dots<<<grid, DOT_THREADS, 0, st>>>(V, ldv, w, n, S, 0, partial, nchunk);
+    bddc_note_launches(1);
     k_dots_reduce<<<(max_rows + 7) / 8, 256, 0, st>>>(partial, nchunk, S, h, mode, 0);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -234,7 +236,9 @@ int gm_dots(const double* V, long long ldv, const double* w, long long n, GmStat
 int gm_norm2(const double* w, long long n, GmState* S, double* partial, cudaStream_t st) {
     int nchunk = gm_nchunk(n);
     k_dots<<<dim3(nchunk, 1), DOT_THREADS, 0, st>>>(nullptr, 0, w, n, S, 1, partial, nchunk);
+    bddc_note_launches(1);
     k_dots_reduce<<<1, 32, 0, st>>>(partial, nchunk, S, nullptr, 2, 1);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -242,6 +246,7 @@ int gm_norm2(const double* w, long long n, GmState* S, double* partial, cudaStre
 int gm_orth_update(const double* V, long long ldv, double* w, long long n, const GmState* S,
                    const double* c, cudaStream_t st) {
     k_orth_update<<<grid_for(n), 256, 0, st>>>(V, ldv, w, n, S, c);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -249,13 +254,16 @@ int gm_orth_update(const double* V, long long ldv, double* w, long long n, const
 int gm_givens(GmState* S, double* H, double* cs, double* sn, double* gv, const double* h,
               const double* h2, cudaStream_t st) {
     k_givens<<<1, 32, 0, st>>>(S, H, cs, sn, gv, h, h2);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
 int gm_normalize(double* V, long long ldv, const double* w, long long n, GmState* S, cudaStream_t st) {
     k_normalize<<<grid_for(n), 256, 0, st>>>(V, ldv, w, n, S);
+    bddc_note_launches(1);
     k_clear_norm<<<1, 1, 0, st>>>(S);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -263,6 +271,7 @@ int gm_normalize(double* V, long long ldv, const double* w, long long n, GmState
 int gm_copy_row(const double* V, long long ldv, double* out, long long n, const GmState* S,
                 cudaStream_t st) {
     k_copy_row<<<grid_for(n), 256, 0, st>>>(V, ldv, out, n, S);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -272,8 +281,11 @@ int gm_cycle_start(const double* r, long long n, GmState* S, double* gv, double*
     int nchunk = gm_nchunk(n);
     // plain norm pass that ignores the stop flag: use a private state copy
     k_dots<<<dim3(nchunk, 1), DOT_THREADS, 0, st>>>(nullptr, 0, r, n, S + 1, 1, partial, nchunk);
+    bddc_note_launches(1);
     k_cycle_start<<<1, 32, 0, st>>>(S, gv, partial, nchunk);
+    bddc_note_launches(1);
     k_scale_into<<<grid_for(n), 256, 0, st>>>(V0, r, n, S);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -281,13 +293,16 @@ int gm_cycle_start(const double* r, long long n, GmState* S, double* gv, double*
 int gm_finish(const double* V, long long ldv, const GmState* S, const double* H, const double* gv,
               double* y, double* t, long long n, cudaStream_t st) {
     k_backsolve<<<1, 32, 0, st>>>(S, H, gv, y);
+    bddc_note_launches(1);
     k_combine<<<grid_for(n), 256, 0, st>>>(V, ldv, y, S, t, n);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
 int vec_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st) {
     k_axpby<<<grid_for(n), 256, 0, st>>>(y, x, a, b, n);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }

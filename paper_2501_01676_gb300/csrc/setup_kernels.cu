@@ -169,6 +169,7 @@ template <class TS, class TD>
 int copy_blocks_run(const CopyJob* jobs, int count, int ychunks, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
     k_copy_blocks<TS, TD><<<dim3(count, ychunks), TH, 0, st>>>(jobs);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -181,6 +182,7 @@ template <class TD>
 int gather_perm_run(const GatherJob* jobs, int count, const int* idx, int ychunks, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
     k_gather_perm<TD><<<dim3(count, ychunks), TH, 0, st>>>(jobs, idx);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -195,7 +197,9 @@ int transform_run(const TBlock* blocks, int count, const int* idx, int maxn, int
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_left<TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_transform_right<<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
+    bddc_note_launches(1);
     k_transform_left<TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -206,6 +210,7 @@ template <class TD>
 int fill_dt_run(const DTJob* jobs, int count, const int* idx, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
     k_fill_dt<TD><<<count, TH, 0, st>>>(jobs, idx);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -217,6 +222,7 @@ int extract_run(const ExtractJob* jobs, int count, const int* idx, double* SPi, 
                 cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
     k_extract<TX, TP><<<dim3(count, ychunks), TH, 0, st>>>(jobs, idx, SPi, nPi);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
@@ -229,6 +235,7 @@ int coarse_ext_run(const double* SPi, double* X, int n, cudaStream_t st) {
     int g = (int)((tot + TH - 1) / TH);
     if (g > 4096) g = 4096;
     k_coarse_ext<<<g, TH, 0, st>>>(SPi, X, n);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
