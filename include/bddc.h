@@ -132,6 +132,21 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs,
  * n_gamma x nrhs column blocks (column j at offset j*n_gamma). */
 int bddc_apply(bddc_ctx* ctx, const double* r_dev, double* z_dev, int nrhs);
 
+/* z = M^-1 r exactly as bddc_apply, for callers that cannot allocate device
+ * memory where they apply the preconditioner (code capturing its own CUDA
+ * graph, where allocation calls are not allowed, or a host framework that
+ * owns all device memory).  The paper has no counterpart; it is a property
+ * of this library only.  The call allocates nothing: its work vectors
+ * (n_gamma + 2 * n_pi doubles) live in one file-scope device array of
+ * 2^20 doubles (8 MiB) that every GPU loading the library holds until the
+ * process exits; larger problems are rejected with BDDC_EINVAL.  The first
+ * call on a device looks up the array's device address, so make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (the kernels clear what must start at zero);
+ * calls that overlap on the GPU race on it.  r, z: device FP64 as in
+ * bddc_apply; the work runs on the context's stream. */
+int bddc_apply_static(bddc_ctx* ctx, const double* r_dev, double* z_dev, int nrhs);
+
 /* y = S x = sum_i R_i^T S^(i) R_i x on the interface (eq. Schur-complex-sys).
  * Device FP64, n_gamma x nrhs. */
 int bddc_schur_apply(bddc_ctx* ctx, const double* x_dev, double* y_dev, int nrhs);

@@ -70,6 +70,7 @@ def lib():
     L.bddc_setup.argtypes = [ct.POINTER(Mesh), ct.POINTER(Coeffs), ct.POINTER(Partition), ct.c_double,
                              ct.POINTER(Opts), vp, ct.POINTER(vp)]
     L.bddc_apply.argtypes = [vp, vp, vp, ct.c_int]
+    L.bddc_apply_static.argtypes = [vp, vp, vp, ct.c_int]
     L.bddc_schur_apply.argtypes = [vp, vp, vp, ct.c_int]
     L.bddc_gmres_solve.argtypes = [vp, vp, vp, ct.c_int, ct.c_int, ct.POINTER(Stats)]
     L.bddc_get_stats.argtypes = [vp, ct.POINTER(Stats)]
@@ -89,7 +90,8 @@ def lib():
 
 EXPORTED = ["bddc_default_opts", "bddc_setup", "bddc_apply", "bddc_schur_apply", "bddc_gmres_solve",
             "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_get_numbering", "bddc_get_schur",
-            "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features", "bddc_kernel_launches"]
+            "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features", "bddc_kernel_launches",
+            "bddc_apply_static"]
 
 
 def kernel_launches():
@@ -230,6 +232,15 @@ class Solver:
         rr = r if r.dim() == 1 else r.t().contiguous()
         zz = self.torch.empty_like(rr)
         check(lib().bddc_apply(self.ctx, _ptr(rr), _ptr(zz), nrhs), "bddc_apply")
+        return zz if r.dim() == 1 else zz.t().contiguous()
+
+    def apply_static(self, r):
+        """z = M^-1 r through bddc_apply_static (work vectors in the library's
+        static device array; nothing is allocated by the library)."""
+        nrhs = 1 if r.dim() == 1 else r.shape[1]
+        rr = r if r.dim() == 1 else r.t().contiguous()
+        zz = self.torch.empty_like(rr)
+        check(lib().bddc_apply_static(self.ctx, _ptr(rr), _ptr(zz), nrhs), "bddc_apply_static")
         return zz if r.dim() == 1 else zz.t().contiguous()
 
     def solve(self, load=None, host=False):

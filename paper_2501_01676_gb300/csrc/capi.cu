@@ -1107,6 +1107,38 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
     return conv ? BDDC_OK : BDDC_NOT_CONVERGED;
 }
 
+// M^-1 applied with caller-supplied work vectors (zc: n_gamma + n_pi, upi:
+// n_pi); used by the entry point whose work vectors live in static memory.
+template <class T>
+static int op_M_into(bddc_ctx* C, const double* x, double* zc, double* upi) {
+    BDDC_CUDA_TRY(cudaMemsetAsync(zc, 0, sizeof(double) * (C->nG + C->nPi), C->st));
+    BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, zc, C->maxcols, 1, 0, 0, C->st, nullptr));
+    if (C->nPi > 0) {
+        BDDC_CUDA_TRY(cudaMemsetAsync(upi, 0, sizeof(double) * C->nPi, C->st));
+        BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0, C->st, nullptr));
+        BDDC_TRY(gemv_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, upi, zc, C->maxcols, 1, 0, 0, C->st, nullptr));
+    }
+    return BDDC_OK;
+}
+
+int bddc_apply_into(bddc_ctx* C, const double* r, double* z, int nrhs, double* work, size_t work_doubles) {
+    if (!C || !r || !z || nrhs < 1 || !work) return BDDC_EINVAL;
+    const size_t need = (size_t)C->nG + 2 * (size_t)C->nPi;
+    if (need > work_doubles) {
+        bddc_set_last_error("interface + 2 x coarse size exceeds the static work array", __FILE__, __LINE__);
+        return BDDC_EINVAL;
+    }
+    double* zc = work;
+    double* upi = work + C->nG + C->nPi;
+    for (int c = 0; c < nrhs; ++c) {
+        if (C->mixed) BDDC_TRY(op_M_into<float>(C, r + (long long)c * C->nG, zc, upi));
+        else BDDC_TRY(op_M_into<double>(C, r + (long long)c * C->nG, zc, upi));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(z + (long long)c * C->nG, zc, sizeof(double) * C->nG,
+                                      cudaMemcpyDeviceToDevice, C->st));
+    }
+    return BDDC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
