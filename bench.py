@@ -89,7 +89,7 @@ class Clocks:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-f", self.path],
+                                          "-lms", "50", "-f", self.path],
                                          stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -177,6 +177,7 @@ def run_ours(args):
     clocks = Clocks()
     barrier(dist)
     clocks.start()
+    B.kernel_timer(B.KT_ENGINE_UPDATE)       # CUDA events around every trailing-update launch
     l0 = B.kernel_launches()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -188,6 +189,8 @@ def run_ours(args):
     barrier(dist)
     t_wall = time.perf_counter() - t_wall0
     launches = B.kernel_launches() - l0
+    kt = B.kernel_timer_read()
+    B.kernel_timer(B.KT_NONE)
     ck = clocks.stop()
     ms_step = max_over_ranks(dist, sum(times) / len(times))
     if args.part == "mixed":
@@ -223,6 +226,17 @@ def run_ours(args):
             e2e_times.append((t1 - t0) * 1e3)
     e2e_ms = max_over_ranks(dist, sum(e2e_times) / len(e2e_times))
     hbm, which = peaks()
+    sm_mhz = ck.get("sm_mhz") or 2070.0
+    # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x clock
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    ach = kt["flops"] / (kt["ms"] * 1e-3) / 1e12 if kt["ms"] > 0 else 0.0
+    roofline = {"kernel": "k_update<float> (Schur engine trailing update, FP32 CUDA cores)",
+                "bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(ach / fp32_peak, 4), "traffic": None,
+                "launches": kt["launches"], "avg_launch_us": round(1e3 * kt["ms"] / max(kt["launches"], 1), 2),
+                "flops_per_launch": round(kt["flops"] / max(kt["launches"], 1)),
+                "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 x median SM clock"}
+    apply = apply_bandwidth(B, W, hbm, which) if args.apply else None
     out = {
         "metric": METRIC, "value": round(ms_step, 4), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": False,
@@ -236,11 +250,14 @@ def run_ours(args):
         "n_pi": stats["n_pi"],
         "plain_fp64_ms": round(ms64, 4), "plain_fp64_iters": st64["iters"],
         "speedup_vs_fp64": round(ms64 / ms_step, 3),
-        "setup_breakdown_ms": {k: round(stats[k], 3) for k in ("t_assemble_ms", "t_factor_ms", "t_face_ms",
-                                                               "t_edge_ms", "t_coarse_ms")},
+        "setup_breakdown_ms": {k: round(stats[k], 3) for k in ("setup_ms", "t_assemble_ms", "t_factor_ms",
+                                                               "t_face_ms", "t_edge_ms", "t_coarse_ms")},
+        "solve_ms": round(stats["solve_ms"], 3), "jacobi_sweeps_max": stats["jacobi_sweeps_max"],
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
+        "roofline": roofline,
+        "apply": apply,
         "clocks": ck,
         "wall_s_timed": round(t_wall, 3),
     }
@@ -250,6 +267,37 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def apply_bandwidth(B, W, hbm, which, reps=20):
+    """HBM throughput of the apply kernels on the 8x8x8, H/h=8 workload, whose
+    operators exceed the 129 MB L2: S x (the gather-GEMV-scatter over all 512
+    subdomains) and M^-1 r (its three launches), FP32 and FP64 operators."""
+    import torch
+    p = W.config3()
+    out = {"workload": "8x8x8 subdomains, H/h=8 (64^3 hexes, 250047 dofs)", "hbm_peak_gbs": hbm,
+           "peak_source": which}
+    for prec, name in ((B.PREC_MIXED, "fp32"), (B.PREC_FP64, "fp64")):
+        s = B.Solver(p, precision=prec)
+        x = torch.randn(s.n_gamma, dtype=torch.float64, device="cuda")
+        res = {}
+        for op, fn in (("S", s.schur_apply), ("M", s.apply)):
+            for _ in range(3):
+                fn(x)
+            torch.cuda.synchronize()
+            B.kernel_timer(B.KT_GEMV)
+            for _ in range(reps):
+                fn(x)
+            kt = B.kernel_timer_read()
+            B.kernel_timer(B.KT_NONE)
+            gbs = kt["bytes"] / (kt["ms"] * 1e-3) / 1e9 if kt["ms"] > 0 else 0.0
+            res[op] = {"GB/s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 4),
+                       "kernel_us_per_apply": round(1e3 * kt["ms"] / reps, 2),
+                       "bytes_per_apply": round(kt["bytes"] / reps)}
+        out[name] = res
+        s.close()
+        torch.cuda.synchronize()
+    return out
 
 
 def cpu_baseline(p):
@@ -295,10 +343,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-apply", dest="apply", action="store_false",
+                    help="skip the apply-bandwidth measurement on the 8x8x8 workload")
     ap.add_argument("--part", default="all", choices=["all", "mixed", "fp64"],
                     help="all: the full JSON line; mixed/fp64: time only that path (profiling runs)")
     args = ap.parse_args()

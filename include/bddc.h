@@ -110,6 +110,7 @@ typedef struct {
     int edges_skipped;       /* edge GEPs skipped by the learned predictor         */
     double setup_ms, solve_ms;
     double t_assemble_ms, t_factor_ms, t_face_ms, t_edge_ms, t_coarse_ms;
+    int jacobi_sweeps_max;   /* most sweeps any GEP eigen-decomposition needed   */
 } bddc_stats;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -169,6 +170,17 @@ const char* bddc_strerror(int code);
 /* Process-wide number of kernels the library has launched so far (a CUDA
  * graph replay counts its kernel nodes).  Host-only, never fails. */
 unsigned long long bddc_kernel_launches(void);
+
+/* Kernel timer for roofline reporting: after bddc_kernel_timer(kind) every
+ * launch of that kernel class (1 engine trailing update, 2 engine panel,
+ * 3 apply GEMV, 4 face GEP, 5 edge GEP; 0 off) is bracketed by CUDA events on
+ * its stream (launches captured into graphs are not).  _read synchronises on
+ * the recorded events and returns their summed duration, the number of
+ * launches and, where the library knows them, the algorithmic flops and
+ * bytes of those launches.  Process-wide; not thread-safe with concurrent
+ * solves. */
+int bddc_kernel_timer(int kind);
+int bddc_kernel_timer_read(double* total_ms, long long* launches, double* flops, double* bytes);
 
 /* Global dof id of each interface position (n_gamma ints). */
 int bddc_get_numbering(const bddc_ctx* ctx, int* gamma_dofs);

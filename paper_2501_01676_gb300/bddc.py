@@ -48,7 +48,8 @@ class Stats(ct.Structure):
                 ("pnumE", ct.c_int), ("n_pi", ct.c_int), ("n_gamma", ct.c_int), ("ndof", ct.c_int),
                 ("nsub", ct.c_int), ("edges_skipped", ct.c_int), ("setup_ms", ct.c_double),
                 ("solve_ms", ct.c_double), ("t_assemble_ms", ct.c_double), ("t_factor_ms", ct.c_double),
-                ("t_face_ms", ct.c_double), ("t_edge_ms", ct.c_double), ("t_coarse_ms", ct.c_double)]
+                ("t_face_ms", ct.c_double), ("t_edge_ms", ct.c_double), ("t_coarse_ms", ct.c_double),
+                ("jacobi_sweeps_max", ct.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +83,8 @@ def lib():
     L.bddc_get_entity_count.argtypes = [vp, ct.c_int]
     L.bddc_get_entity.argtypes = [vp, ct.c_int, ct.c_int, ip, ip, ip, ip, dp, dp, ip]
     L.bddc_get_edge_features.argtypes = [vp, ct.POINTER(ct.c_float), ip]
+    L.bddc_kernel_timer.argtypes = [ct.c_int]
+    L.bddc_kernel_timer_read.argtypes = [dp, ct.POINTER(ct.c_longlong), dp, dp]
     L.bddc_kernel_launches.argtypes = []
     L.bddc_kernel_launches.restype = ct.c_ulonglong
     _lib = L
@@ -91,7 +94,20 @@ def lib():
 EXPORTED = ["bddc_default_opts", "bddc_setup", "bddc_apply", "bddc_schur_apply", "bddc_gmres_solve",
             "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_get_numbering", "bddc_get_schur",
             "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features", "bddc_kernel_launches",
-            "bddc_apply_static"]
+            "bddc_apply_static", "bddc_kernel_timer", "bddc_kernel_timer_read"]
+
+KT_NONE, KT_ENGINE_UPDATE, KT_ENGINE_PANEL, KT_GEMV, KT_FACE, KT_EDGE = range(6)
+
+
+def kernel_timer(kind):
+    check(lib().bddc_kernel_timer(kind), "bddc_kernel_timer")
+
+
+def kernel_timer_read():
+    ms, n, fl, by = ct.c_double(), ct.c_longlong(), ct.c_double(), ct.c_double()
+    check(lib().bddc_kernel_timer_read(ct.byref(ms), ct.byref(n), ct.byref(fl), ct.byref(by)),
+          "bddc_kernel_timer_read")
+    return dict(ms=ms.value, launches=n.value, flops=fl.value, bytes=by.value)
 
 
 def kernel_launches():

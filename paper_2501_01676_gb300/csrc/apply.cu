@@ -18,7 +18,7 @@
 namespace {
 
 constexpr int GEMV_THREADS = 256;
-constexpr int GEMV_MAXCOLS = 2048;
+constexpr int GEMV_MAXCOLS = 2048;     // must match the column-slice width of the work items
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -69,21 +69,22 @@ __global__ void __launch_bounds__(GEMV_THREADS) k_gemv(const T* __restrict__ poo
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int* iidx = idx + it.iidx_off;
     const int* oidx = idx + it.oidx_off;
-    const T* M = pool + it.moff;
+    const T* M = pool + it.moff + it.col0;
     constexpr int VW = Vec<T>::W;
     typedef typename Vec<T>::type VT;
-    const int nvec = it.cols / VW;
+    const int ncols = it.ncols;
+    const int nvec = ncols / VW;
     for (int c = 0; c < nrhs; ++c) {
         const double* inc = in + (long long)c * in_ld;
         double* outc = out + (long long)c * out_ld;
-        for (int q = t; q < it.cols; q += GEMV_THREADS) xs[q] = (T)inc[iidx[q]];
+        for (int q = t; q < ncols; q += GEMV_THREADS) xs[q] = (T)inc[iidx[it.col0 + q]];
         __syncthreads();
         for (int r = it.row0 + wid; r < it.row0 + it.nrows; r += GEMV_THREADS / 32) {
             const T* row = M + (long long)r * it.ld;
             const VT* rv = reinterpret_cast<const VT*>(row);
             T acc = (T)0;
             for (int v = lane; v < nvec; v += 32) acc += dot_vec<T>(__ldg(rv + v), xs + v * VW);
-            for (int q = nvec * VW + lane; q < it.cols; q += 32) acc += row[q] * xs[q];
+            for (int q = nvec * VW + lane; q < ncols; q += 32) acc += row[q] * xs[q];
             acc = warp_sum(acc);
             if (lane == 0) atomicAdd(&outc[oidx[r]], (double)acc);
         }
@@ -96,20 +97,22 @@ __global__ void __launch_bounds__(GEMV_THREADS) k_gemv(const T* __restrict__ poo
 template <class T>
 int gemv_run(const T* pool, const GemvItem* items_dev, int nitems, const int* idx, const double* in,
              double* out, int maxcols, int nrhs, int in_ld, int out_ld, cudaStream_t st,
-             const int* skip) {
+             const int* skip, double bytes) {
     if (nitems <= 0) return BDDC_OK;
-    if (maxcols > GEMV_MAXCOLS) return BDDC_EINVAL;
+    (void)maxcols;                     // items are split into column slices of <= GEMV_MAXCOLS
+    ktimer_begin(KT_GEMV, st);
     k_gemv<T><<<nitems, GEMV_THREADS, 0, st>>>(pool, items_dev, idx, in, out, nrhs, in_ld, out_ld,
                                                skip);
     bddc_note_launches(1);
+    ktimer_end(KT_GEMV, st, 0.0, bytes * nrhs);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
 template int gemv_run<double>(const double*, const GemvItem*, int, const int*, const double*,
-                              double*, int, int, int, int, cudaStream_t, const int*);
+                              double*, int, int, int, int, cudaStream_t, const int*, double);
 template int gemv_run<float>(const float*, const GemvItem*, int, const int*, const double*, double*,
-                             int, int, int, int, cudaStream_t, const int*);
+                             int, int, int, int, cudaStream_t, const int*, double);
 
 // ---------------------------------------------------------------------------
 // Condensation and interior recovery with the factors of the partial LU of
@@ -133,21 +136,21 @@ struct TriItem {
 };
 
 template <class T>
-__device__ void fwd_unit_lower(const T* A, int ld, int nI, double* y) {
+__device__ void fwd_unit_lower(const T* A, int ld, int nI, T* y) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int b0 = 0; b0 < nI; b0 += 32) {
         const int bw = min(32, nI - b0);
         if (wid == 0) {
-            double v = lane < bw ? y[b0 + lane] : 0.0;
+            T v = lane < bw ? y[b0 + lane] : (T)0;
             for (int k = 0; k < bw; ++k) {
-                double vk = __shfl_sync(0xffffffffu, v, k);
-                if (lane > k && lane < bw) v -= (double)A[(long long)(b0 + lane) * ld + b0 + k] * vk;
+                T vk = __shfl_sync(0xffffffffu, v, k);
+                if (lane > k && lane < bw) v -= A[(long long)(b0 + lane) * ld + b0 + k] * vk;
             }
             if (lane < bw) y[b0 + lane] = v;
         }
         __syncthreads();
         for (int r = b0 + bw + wid; r < nI; r += TRI_THREADS / 32) {
-            double s = lane < bw ? (double)A[(long long)r * ld + b0 + lane] * y[b0 + lane] : 0.0;
+            T s = lane < bw ? A[(long long)r * ld + b0 + lane] * y[b0 + lane] : (T)0;
             s = warp_sum(s);
             if (lane == 0) y[r] -= s;
         }
@@ -156,23 +159,23 @@ __device__ void fwd_unit_lower(const T* A, int ld, int nI, double* y) {
 }
 
 template <class T>
-__device__ void bwd_upper(const T* A, int ld, int nI, double* y) {
+__device__ void bwd_upper(const T* A, int ld, int nI, T* y) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int b1 = nI; b1 > 0; b1 -= 32) {
         const int b0 = max(0, b1 - 32);
         const int bw = b1 - b0;
         if (wid == 0) {
-            double v = lane < bw ? y[b0 + lane] : 0.0;
+            T v = lane < bw ? y[b0 + lane] : (T)0;
             for (int k = bw - 1; k >= 0; --k) {
-                if (lane == k) v /= (double)A[(long long)(b0 + k) * ld + b0 + k];
-                double vk = __shfl_sync(0xffffffffu, v, k);
-                if (lane < k) v -= (double)A[(long long)(b0 + lane) * ld + b0 + k] * vk;
+                if (lane == k) v /= A[(long long)(b0 + k) * ld + b0 + k];
+                T vk = __shfl_sync(0xffffffffu, v, k);
+                if (lane < k) v -= A[(long long)(b0 + lane) * ld + b0 + k] * vk;
             }
             if (lane < bw) y[b0 + lane] = v;
         }
         __syncthreads();
         for (int r = wid; r < b0; r += TRI_THREADS / 32) {
-            double s = lane < bw ? (double)A[(long long)r * ld + b0 + lane] * y[b0 + lane] : 0.0;
+            T s = lane < bw ? A[(long long)r * ld + b0 + lane] * y[b0 + lane] : (T)0;
             s = warp_sum(s);
             if (lane == 0) y[r] -= s;
         }
@@ -190,24 +193,24 @@ __global__ void __launch_bounds__(TRI_THREADS) k_condense(const T* __restrict__ 
                                                           long long ldF, long long ldG,
                                                           long long ldY) {
     const TriItem it = items[blockIdx.x];
-    __shared__ double y[TRI_MAXN];
+    __shared__ T y[TRI_MAXN];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const T* A = pool + it.aoff;
     const int* dofs = lists + it.dof_off;
     const int* gidx = lists + it.gidx_off;
     for (int c = 0; c < nrhs; ++c) {
-        for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = F[c * ldF + dofs[q]];
+        for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = (T)F[c * ldF + dofs[q]];
         __syncthreads();
         fwd_unit_lower<T>(A, it.ld, it.nI, y);
         const int nB = it.n - it.nI;
         for (int b = wid; b < nB; b += TRI_THREADS / 32) {
             const T* row = A + (long long)(it.nI + b) * it.ld;
-            double s = 0.0;
-            for (int q = lane; q < it.nI; q += 32) s += (double)row[q] * y[q];
+            T s = 0;
+            for (int q = lane; q < it.nI; q += 32) s += row[q] * y[q];
             s = warp_sum(s);
-            if (lane == 0) atomicAdd(&g[c * ldG + gidx[b]], -s);
+            if (lane == 0) atomicAdd(&g[c * ldG + gidx[b]], -(double)s);
         }
-        for (int q = t; q < it.nI; q += TRI_THREADS) ystore[c * ldY + it.yoff + q] = y[q];
+        for (int q = t; q < it.nI; q += TRI_THREADS) ystore[c * ldY + it.yoff + q] = (double)y[q];
         __syncthreads();
     }
 }
@@ -222,28 +225,28 @@ __global__ void __launch_bounds__(TRI_THREADS) k_recover(const T* __restrict__ p
                                                          long long ldG, long long ldU,
                                                          long long ldY) {
     const TriItem it = items[blockIdx.x];
-    __shared__ double y[TRI_MAXN];
-    __shared__ double ub[TRI_MAXN];
+    __shared__ T y[TRI_MAXN];
+    __shared__ T ub[TRI_MAXN];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const T* A = pool + it.aoff;
     const int* dofs = lists + it.dof_off;
     const int* gidx = lists + it.gidx_off;
     const int nB = it.n - it.nI;
     for (int c = 0; c < nrhs; ++c) {
-        for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = ystore[c * ldY + it.yoff + q];
-        for (int q = t; q < nB; q += TRI_THREADS) ub[q] = uG[c * ldG + gidx[q]];
+        for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = (T)ystore[c * ldY + it.yoff + q];
+        for (int q = t; q < nB; q += TRI_THREADS) ub[q] = (T)uG[c * ldG + gidx[q]];
         __syncthreads();
         for (int r = wid; r < it.nI; r += TRI_THREADS / 32) {
             const T* row = A + (long long)r * it.ld + it.nI;
-            double s = 0.0;
-            for (int q = lane; q < nB; q += 32) s += (double)row[q] * ub[q];
+            T s = 0;
+            for (int q = lane; q < nB; q += 32) s += row[q] * ub[q];
             s = warp_sum(s);
             if (lane == 0) y[r] -= s;
         }
         __syncthreads();
         bwd_upper<T>(A, it.ld, it.nI, y);
-        for (int q = t; q < it.nI; q += TRI_THREADS) u[c * ldU + dofs[q]] = y[q];
-        for (int q = t; q < nB; q += TRI_THREADS) u[c * ldU + dofs[it.nI + q]] = ub[q];
+        for (int q = t; q < it.nI; q += TRI_THREADS) u[c * ldU + dofs[q]] = (double)y[q];
+        for (int q = t; q < nB; q += TRI_THREADS) u[c * ldU + dofs[it.nI + q]] = uG[c * ldG + gidx[q]];
         __syncthreads();
     }
 }

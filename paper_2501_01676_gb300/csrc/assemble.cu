@@ -31,6 +31,7 @@ struct AsmParams {
     double N[27 * 8];     // shape values at the Gauss points
     double G[27 * 8 * 3]; // physical gradients
     double w[27];         // weights * |J|
+    double wN[27 * 8];    // w_q N_a(x_q)
 };
 
 __constant__ AsmParams cP;
@@ -55,7 +56,8 @@ __global__ void __launch_bounds__(64) k_assemble(
     const int Ex = cP.E[0], Ey = cP.E[1];
     const int ex = e % Ex, ey = (e / Ex) % Ey, ez = e / (Ex * Ey);
     __shared__ double sb[8][3], sf[8], sdv[8];
-    __shared__ double bg[27][8], Lp[27][8], fq[27], cq[27];
+    __shared__ double bg[27][8], Lp[27][8], wLp[27][8], wf[27], cq[27];
+    __shared__ double P[8][9];
     __shared__ double bmax2[64];
     __shared__ double CK;
     if (t < 8) {
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(64) k_assemble(
         sdv[t] = divb_node ? divb_node[nd] : 0.0;
     }
     __syncthreads();
-    // beta, f, div(beta) at the Gauss points; beta.grad phi_a
+    // per Gauss point q (thread q): beta, f, c~, beta.grad phi_a, L phi_a, w_q L phi_a
     double bm = 0.0;
     if (t < 27) {
         double b0 = 0, b1 = 0, b2 = 0, ff = 0, dd = 0;
@@ -86,13 +88,16 @@ __global__ void __launch_bounds__(64) k_assemble(
             ff += n * sf[a];
             dd += n * sdv[a];
         }
-        fq[t] = ff;
-        cq[t] = cP.c - 0.5 * dd;
+        const double w = cP.w[t];
+        wf[t] = w * ff;
+        cq[t] = w * (cP.c - 0.5 * dd);
         for (int a = 0; a < 8; ++a) {
             const double* g = &cP.G[(t * 8 + a) * 3];
             double v = b0 * g[0] + b1 * g[1] + b2 * g[2];
+            double l = v + cP.c * cP.N[t * 8 + a];
             bg[t][a] = v;
-            Lp[t][a] = v + cP.c * cP.N[t * 8 + a];
+            Lp[t][a] = l;
+            wLp[t][a] = w * l;
         }
         bm = b0 * b0 + b1 * b1 + b2 * b2;
     } else if (t >= 32 && t < 40) {
@@ -110,19 +115,25 @@ __global__ void __launch_bounds__(64) k_assemble(
         double PK = hK * bmax / (2.0 * nu);
         CK = (PK >= 1.0) ? cP.tau * hK / (2.0 * bmax) : cP.tau * hK * hK / (4.0 * nu);
     }
-    __syncthreads();
     const int i = t >> 3, j = t & 7;      // test i, trial j
-    const double nu = nu_elem[e];
-    const double Ck = CK;
-    double acc = nu * cP.K0[i * 8 + j];
-    double fl = 0.0;
-#pragma unroll 3
+    // GLS part sum_q w L phi_j L phi_i and P_ij = sum_q w N_i beta.grad phi_j
+    double gls = 0.0, pij = 0.0, reac = 0.0;
+#pragma unroll 9
     for (int q = 0; q < 27; ++q) {
-        double w = cP.w[q];
-        double Ni = cP.N[q * 8 + i], Nj = cP.N[q * 8 + j];
-        acc += w * (Ck * Lp[q][j] * Lp[q][i] + cq[q] * Nj * Ni + 0.5 * (bg[q][j] * Ni - bg[q][i] * Nj));
-        if (j == 0) fl += w * fq[q] * (Ni + Ck * Lp[q][i]);
+        gls += wLp[q][j] * Lp[q][i];
+        pij += cP.wN[q * 8 + i] * bg[q][j];
     }
+    if (divb_node) {
+        for (int q = 0; q < 27; ++q) reac += cq[q] * cP.N[q * 8 + i] * cP.N[q * 8 + j];
+    } else {
+        reac = cP.c * cP.M0[i * 8 + j];
+    }
+    P[i][j] = pij;
+    __syncthreads();
+    const double acc = nu_elem[e] * cP.K0[i * 8 + j] + CK * gls + reac + 0.5 * (pij - P[j][i]);
+    double fl = 0.0;
+    if (j == 0)
+        for (int q = 0; q < 27; ++q) fl += wf[q] * (cP.N[q * 8 + i] + CK * Lp[q][i]);
     // node indices of the entry
     const int ix = ex + (i & 1), iy = ey + ((i >> 1) & 1), iz = ez + ((i >> 2) & 1);
     const int jx = ex + (j & 1), jy = ey + ((j >> 1) & 1), jz = ez + ((j >> 2) & 1);
@@ -180,6 +191,8 @@ int assemble_init(const HostMesh& hm, double tau, double c) {
                     P.G[(q * 8 + a) * 3 + 2] = f1[0] * f1[1] * df[2] / hm.h[2];
                 }
             }
+    for (int q = 0; q < 27; ++q)
+        for (int a = 0; a < 8; ++a) P.wN[q * 8 + a] = P.w[q] * P.N[q * 8 + a];
     for (int i = 0; i < 8; ++i)
         for (int j = 0; j < 8; ++j) {
             double k0 = 0.0, m0 = 0.0;

@@ -31,6 +31,12 @@ void bddc_set_last_error(const char* msg, const char* file, int line);
 // kernel nodes).
 void bddc_note_launches(unsigned long long n);
 
+// Optional CUDA-event timing of one kernel class (for roofline reporting).
+enum { KT_NONE = 0, KT_ENGINE_UPDATE = 1, KT_ENGINE_PANEL = 2, KT_GEMV = 3, KT_FACE = 4, KT_EDGE = 5 };
+bool ktimer_on(int kind);
+void ktimer_begin(int kind, cudaStream_t st);
+void ktimer_end(int kind, cudaStream_t st, double flops, double bytes);
+
 // Device-side error flags written by kernels (never trap).
 enum {
     ERR_PIVOT = 1,        // zero / non-finite pivot in the batched LU
@@ -103,7 +109,7 @@ struct EngItem {
 
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* diag_scratch,
-               int* err, cudaStream_t st);
+               int* err, cudaStream_t st, const int* host_n = nullptr, const int* host_k = nullptr);
 
 // Generic batched gather -> GEMV -> scatter-add:  out[oidx[r]] += sum_c M[r][c] * in[iidx[c]]
 struct GemvItem {
@@ -113,12 +119,14 @@ struct GemvItem {
     int oidx_off;        // offset of the scatter index list (rows entries)
     int row0;            // first row handled by this work item
     int nrows;           // rows handled by this work item
+    int col0;            // first column of this item's column slice
+    int ncols;           // columns of the slice (<= the kernel's staging limit)
 };
 
 template <class T>
 int gemv_run(const T* pool, const GemvItem* items_dev, int nitems, const int* idx,
              const double* in, double* out, int maxcols, int nrhs, int in_ld, int out_ld,
-             cudaStream_t st, const int* skip_flag);
+             cudaStream_t st, const int* skip_flag, double bytes = 0.0);
 
 // Small-matrix kernels for the GEPs live in gep.cu; launchers:
 struct FaceJob;   // defined in gep.cu

@@ -24,6 +24,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,42 @@ static thread_local bool g_capturing = false;
 void bddc_note_launches(unsigned long long n) {
     if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
+
+// ---- kernel timer: CUDA events around every launch of one kernel class ----
+namespace {
+struct KTimer {
+    int kind = KT_NONE;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    cudaEvent_t open = nullptr;
+    double flops = 0, bytes = 0;
+    long long launches = 0;
+};
+std::mutex g_kt_mu;
+KTimer g_kt;
+}  // namespace
+
+bool ktimer_on(int kind) { return !g_capturing && g_kt.kind == kind && kind != KT_NONE; }
+
+void ktimer_begin(int kind, cudaStream_t st) {
+    if (!ktimer_on(kind)) return;
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    cudaEventCreate(&g_kt.open);
+    cudaEventRecord(g_kt.open, st);
+}
+
+void ktimer_end(int kind, cudaStream_t st, double flops, double bytes) {
+    if (!ktimer_on(kind)) return;
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    if (!g_kt.open) return;
+    cudaEvent_t e1;
+    cudaEventCreate(&e1);
+    cudaEventRecord(e1, st);
+    g_kt.ev.push_back({g_kt.open, e1});
+    g_kt.open = nullptr;
+    g_kt.flops += flops;
+    g_kt.bytes += bytes;
+    g_kt.launches += 1;
+}
 void bddc_set_last_error(const char* msg, const char* file, int line) {
     char buf[512];
     snprintf(buf, sizeof(buf), "%s (%s:%d)", msg, file, line);
@@ -91,7 +128,7 @@ struct bddc_ctx {
         *p = nullptr;
         if (n == 0) n = 1;
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        cudaError_t e = cudaMallocAsync(&q, n * sizeof(T), st);
         if (e != cudaSuccess) {
             bddc_set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
             return BDDC_ENOMEM;
@@ -137,6 +174,8 @@ struct bddc_ctx {
     int* gidx_pool = nullptr;
     GemvItem *itS = nullptr, *itM1 = nullptr, *itC = nullptr, *itM3 = nullptr;
     int nitS = 0, nitM1 = 0, nitC = 0, nitM3 = 0, maxcols = 0;
+    // algorithmic bytes of one product: matrix stream + gathered inputs + scattered outputs
+    double bytesS = 0, bytesM1 = 0, bytesC = 0, bytesM3 = 0;
     // condense / recover
     void* tri = nullptr;
     int* tri_lists = nullptr;
@@ -175,7 +214,12 @@ static int run_engine(bddc_ctx* C, const std::vector<EngItem<T>>& items) {
     BDDC_TRY(C->upload(&d, items));
     T* scr = nullptr;
     BDDC_TRY(C->alloc(&scr, items.size() * 32 * 32));
-    return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st);
+    std::vector<int> hn(items.size()), hk(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
+        hn[i] = items[i].n;
+        hk[i] = items[i].k;
+    }
+    return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st, hn.data(), hk.data());
 }
 
 template <class T>
@@ -199,10 +243,10 @@ static int setup_impl(bddc_ctx* C) {
     BDDC_CUDA_TRY(cudaMemsetAsync(A, 0, atot * sizeof(T), st));
     std::vector<int> lut, box0(3 * nsd), boxn(3 * nsd);
     std::vector<long long> lut_off(nsd);
+    std::vector<int> loc(hm.ndof, -1);
     for (int s = 0; s < nsd; ++s) {
         SubInfo& S = hm.sub[s];
         lut_off[s] = (long long)lut.size();
-        std::map<int, int> loc;
         for (int l = 0; l < S.n; ++l) loc[S.dofs[l]] = l;
         int bn[3];
         for (int d = 0; d < 3; ++d) {
@@ -221,6 +265,7 @@ static int setup_impl(bddc_ctx* C) {
                     }
                     lut.push_back(v);
                 }
+        for (int l = 0; l < S.n; ++l) loc[S.dofs[l]] = -1;
     }
     std::vector<int> slab[3];
     for (int d = 0; d < 3; ++d)
@@ -421,7 +466,9 @@ static int setup_impl(bddc_ctx* C) {
             J.Bti = Bt64 + bo[fi];
             J.Btj = Bt64 + bo[fi] + (long long)n * n;
             J.ldbi = J.ldbj = n;
-            BDDC_TRY(C->alloc(&J.work, face_work_doubles(n)));
+            T* fw = nullptr;
+            BDDC_TRY(C->alloc(&fw, face_work_doubles(n)));
+            J.work = fw;
             J.Q = C->Q[e];
             J.DQi = C->DQ[e][0];
             J.DQj = C->DQ[e][1];
@@ -432,7 +479,7 @@ static int setup_impl(bddc_ctx* C) {
         }
         FaceJob* d_fj;
         BDDC_TRY(C->upload(&d_fj, fj));
-        BDDC_TRY(face_run(d_fj, (int)fj.size(), maxn, C->err, st));
+        BDDC_TRY(face_run<T>(d_fj, (int)fj.size(), maxn, C->err, st));
     }
     BDDC_CUDA_TRY(cudaMemcpyAsync(C->kk.data(), C->d_k, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -450,7 +497,7 @@ static int setup_impl(bddc_ctx* C) {
         std::vector<int> ew_off(nsd, -1);
         auto key_of = [](int kind, int e, int l) -> long long { return ((long long)kind << 40) | ((long long)e << 16) | l; };
         std::vector<TBlock> tb;
-        double* Ysc = nullptr;
+        T* Ysc = nullptr;
         T* W = nullptr;
         double* W64 = nullptr;
         std::vector<long long> woff(nsd, 0), w64off(nsd, 0);
@@ -555,11 +602,11 @@ static int setup_impl(bddc_ctx* C) {
         // per (edge, subdomain): Schur complement onto [E, H_k]
         std::vector<int> gidxv, hmv;
         std::vector<GatherJob> gj;
-        std::vector<EngItem<double>> items;
+        std::vector<EngItem<T>> items;
         std::vector<std::vector<int>> hsz(edges.size()), hoff(edges.size()), itn(edges.size());
         std::vector<std::vector<long long>> ito(edges.size());
         std::vector<int> nH(edges.size(), 0);
-        double* EB = nullptr;
+        T* EB = nullptr;
         if (edge_mode == 0) {
             long long etot = 0;
             for (size_t ei = 0; ei < edges.size(); ++ei)
@@ -618,7 +665,7 @@ static int setup_impl(bddc_ctx* C) {
                     int off = (int)gidxv.size();
                     gidxv.insert(gidxv.end(), perm.begin(), perm.end());
                     gj.push_back(GatherJob{W64 + w64off[s], nkeep[s], n, off, 0, EB + etot, n});
-                    items.push_back(EngItem<double>{EB + etot, n, nel, n});
+                    items.push_back(EngItem<T>{EB + etot, n, nel, n});
                     ito[ei].push_back(etot + (long long)nel * n + nel);
                     itn[ei].push_back(n);
                     hsz[ei].push_back((int)hk.size());
@@ -631,8 +678,8 @@ static int setup_impl(bddc_ctx* C) {
             BDDC_TRY(C->upload(&d_gi, gidxv));
             GatherJob* d_gj;
             BDDC_TRY(C->upload(&d_gj, gj));
-            BDDC_TRY(gather_perm_run<double>(d_gj, (int)gj.size(), d_gi, 8, st));
-            BDDC_TRY(run_engine<double>(C, items));
+            BDDC_TRY(gather_perm_run<T>(d_gj, (int)gj.size(), d_gi, 8, st));
+            BDDC_TRY(run_engine<T>(C, items));
         }
         int* d_hm = nullptr;
         BDDC_TRY(C->upload(&d_hm, hmv));
@@ -665,7 +712,9 @@ static int setup_impl(bddc_ctx* C) {
             }
             maxnw = std::max(maxnw, (m - 1) * n);
             maxnz = std::max(maxnz, m * n + J.nH);
-            BDDC_TRY(C->alloc(&J.work, edge_work_doubles(n, m, J.nH)));
+            T* ew = nullptr;
+            BDDC_TRY(C->alloc(&ew, edge_work_doubles(n, m, J.nH)));
+            J.work = ew;
             BDDC_TRY(C->alloc(&C->BB[e], (size_t)(m - 1) * n * (m - 1) * n));
             J.BBout = C->BB[e];
             J.Q = C->Q[e];
@@ -676,7 +725,7 @@ static int setup_impl(bddc_ctx* C) {
         }
         EdgeJob* d_ej;
         BDDC_TRY(C->upload(&d_ej, ej));
-        BDDC_TRY(edge_run(d_ej, (int)ej.size(), maxnw, maxnz, C->err, st));
+        BDDC_TRY(edge_run<T>(d_ej, (int)ej.size(), maxnw, maxnz, C->err, st));
     }
     BDDC_CUDA_TRY(cudaMemcpyAsync(C->kk.data(), C->d_k, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaMemcpyAsync(C->neig.data(), C->d_neig, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
@@ -732,7 +781,7 @@ static int setup_impl(bddc_ctx* C) {
     int* d_idx;
     BDDC_TRY(C->upload(&d_idx, idxv));
     T* X = nullptr;
-    double* Ysc = nullptr;
+    T* Ysc = nullptr;
     BDDC_TRY(C->alloc(&X, xtot));
     BDDC_TRY(C->alloc(&Ysc, ytot));
     BDDC_CUDA_TRY(cudaMemsetAsync(X, 0, xtot * sizeof(T), st));
@@ -839,18 +888,22 @@ static int setup_impl(bddc_ctx* C) {
     const int nG = C->nG;
     auto split = [](std::vector<GemvItem>& v, long long moff, int rows, int cols, int ld, int io, int oo) {
         const int RB = 32;
-        for (int r0 = 0; r0 < rows; r0 += RB) {
-            GemvItem it;
-            it.moff = moff;
-            it.rows = rows;
-            it.cols = cols;
-            it.ld = ld;
-            it.iidx_off = io;
-            it.oidx_off = oo;
-            it.row0 = r0;
-            it.nrows = std::min(RB, rows - r0);
-            v.push_back(it);
-        }
+        const int CB = 2048;           // staging width of the GEMV kernel (multiple of the vector width)
+        for (int c0 = 0; c0 < cols; c0 += CB)
+            for (int r0 = 0; r0 < rows; r0 += RB) {
+                GemvItem it;
+                it.moff = moff;
+                it.rows = rows;
+                it.cols = cols;
+                it.ld = ld;
+                it.iidx_off = io;
+                it.oidx_off = oo;
+                it.row0 = r0;
+                it.nrows = std::min(RB, rows - r0);
+                it.col0 = c0;
+                it.ncols = std::min(CB, cols - c0);
+                v.push_back(it);
+            }
     };
     C->maxcols = std::max(nPi, 1);
     for (int s = 0; s < nsd; ++s) {
@@ -867,6 +920,10 @@ static int setup_impl(bddc_ctx* C) {
         split(iS, C->soff[s], nB, nB, C->sld[s], og, og);
         split(iM1, C->maoff[s], nB + nps, nB, C->mald[s], og, om1);
         if (nps > 0) split(iM3, C->mcoff[s], nB, nps, C->mcld[s], orp, og);
+        const double ts = sizeof(T), iv = 8.0 + 4.0;   // FP64 value + int32 index per gather/scatter
+        C->bytesS += ts * nB * nB + iv * 2.0 * nB;
+        C->bytesM1 += ts * (nB + nps) * nB + iv * (nB + nB + nps);
+        C->bytesM3 += ts * nB * nps + iv * (nps + nB);
     }
     {
         int oc = (int)gi.size();
@@ -874,6 +931,7 @@ static int setup_impl(bddc_ctx* C) {
         int oi = (int)gi.size();
         for (int q = 0; q < nPi; ++q) gi.push_back(q);
         if (nPi > 0) split(iC, 0, nPi, nPi, ldc, oc, oi);
+        C->bytesC = 8.0 * nPi * nPi + 24.0 * nPi;
     }
     BDDC_TRY(C->upload(&C->gidx_pool, gi));
     BDDC_TRY(C->upload(&C->itS, iS));
@@ -913,18 +971,22 @@ static int setup_impl(bddc_ctx* C) {
 template <class T>
 static int op_S(bddc_ctx* C, const double* x, double* y, const int* skip) {
     BDDC_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * C->nG, C->st));
-    return gemv_run<T>((const T*)C->ST, C->itS, C->nitS, C->gidx_pool, x, y, C->maxcols, 1, 0, 0, C->st, skip);
+    return gemv_run<T>((const T*)C->ST, C->itS, C->nitS, C->gidx_pool, x, y, C->maxcols, 1, 0, 0, C->st, skip,
+                       C->bytesS);
 }
 
 // zc[0:nG] = M^-1 x (zc[nG:nG+nPi] holds the coarse residual)
 template <class T>
 static int op_M(bddc_ctx* C, const double* x, const int* skip) {
     BDDC_CUDA_TRY(cudaMemsetAsync(C->zc, 0, sizeof(double) * (C->nG + C->nPi), C->st));
-    BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, C->zc, C->maxcols, 1, 0, 0, C->st, skip));
+    BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, C->zc, C->maxcols, 1, 0, 0, C->st, skip,
+                         C->bytesM1));
     if (C->nPi > 0) {
         BDDC_CUDA_TRY(cudaMemsetAsync(C->uPi, 0, sizeof(double) * C->nPi, C->st));
-        BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, C->zc, C->uPi, C->maxcols, 1, 0, 0, C->st, skip));
-        BDDC_TRY(gemv_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, C->uPi, C->zc, C->maxcols, 1, 0, 0, C->st, skip));
+        BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, C->zc, C->uPi, C->maxcols, 1, 0, 0, C->st,
+                                  skip, C->bytesC));
+        BDDC_TRY(gemv_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, C->uPi, C->zc, C->maxcols, 1, 0, 0, C->st,
+                             skip, C->bytesM3));
     }
     return BDDC_OK;
 }
@@ -1081,7 +1143,9 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
             BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->res, C->g, C->ystore, 1, ndof, nG, C->ny, st));
             int it = 0, cv = 0;
             double rr = 0.0;
-            BDDC_TRY(gmres<T>(C, C->g, C->xG, C->o.inner_rtol, C->o.max_iter, &it, &rr, &cv));
+            // the loosest inner tolerance that still reaches rtol (with a factor-2 margin)
+            const double tol_k = std::max(C->o.inner_rtol, 0.5 * C->o.rtol * Fn / rn);
+            BDDC_TRY(gmres<T>(C, C->g, C->xG, std::min(tol_k, 0.5), C->o.max_iter - iters_total, &it, &rr, &cv));
             iters_total += it;
             BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, C->corr, 1, nG, ndof, C->ny, st));
             BDDC_TRY(vec_axpby(udev, C->corr, 1.0, 1.0, ndof, st));
@@ -1179,12 +1243,38 @@ const char* bddc_strerror(int code) {
 void bddc_destroy(bddc_ctx* C) {
     if (!C) return;
     if (C->graph) cudaGraphExecDestroy(C->graph);
+    for (void* p : C->allocs) cudaFreeAsync(p, C->st);
     if (C->st) cudaStreamSynchronize(C->st);
-    for (void* p : C->allocs) cudaFree(p);
     if (C->own) cudaStreamDestroy(C->own);
-    if (C->hst) cudaFreeHost(C->hst);
-    if (C->scal) cudaFreeHost(C->scal);
     delete C;
+}
+
+// Pinned host slots for the small device->host reads of the solve; one block
+// per host thread, reused by every context the thread drives (each call
+// synchronises before it reads them).
+static int pinned_scratch(GmState** out) {
+    static thread_local GmState* block = nullptr;
+    if (!block) BDDC_CUDA_TRY(cudaMallocHost(&block, 4 * sizeof(GmState)));
+    *out = block;
+    return BDDC_OK;
+}
+
+// Keep freed device memory in the stream-ordered pool of each device so that
+// repeated setups reuse it instead of returning it to the driver.
+static int keep_pool_memory() {
+    int dev = 0;
+    BDDC_CUDA_TRY(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static bool done[256] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 256 && !done[dev]) {
+        cudaMemPool_t pool;
+        BDDC_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+        unsigned long long thr = ~0ULL;
+        BDDC_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        done[dev] = true;
+    }
+    return BDDC_OK;
 }
 
 static int copy_coeff(bddc_ctx* C, double** dst, const double* src, size_t n, int mem) {
@@ -1211,10 +1301,9 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     for (int d = 0; d < 3; ++d) C->bconst[d] = k->beta_const[d];
     C->c = k->c;
     C->nG = (int)hm.gamma.size();
-    BDDC_TRY(C->alloc(&C->err, 1));
-    BDDC_CUDA_TRY(cudaMemsetAsync(C->err, 0, sizeof(int), C->st));
-    BDDC_CUDA_TRY(cudaMallocHost(&C->hst, 2 * sizeof(GmState)));
-    BDDC_CUDA_TRY(cudaMallocHost(&C->scal, 64 * sizeof(double)));
+    BDDC_TRY(C->alloc(&C->err, 2));        // [0] error flags, [1] largest Jacobi sweep count
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->err, 0, 2 * sizeof(int), C->st));
+    BDDC_TRY(pinned_scratch(&C->hst));
     if (C->mixed) BDDC_TRY(setup_impl<float>(C));
     else BDDC_TRY(setup_impl<double>(C));
     // solve buffers
@@ -1247,9 +1336,11 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     BDDC_TRY(C->alloc(&C->partial, (size_t)(m + 9) * (gm_nchunk(std::max(nG, ndof)) + 1)));
     BDDC_TRY(C->alloc(&C->gst, 2));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->gst, 0, 2 * sizeof(GmState), C->st));
-    int herr = 0;
-    BDDC_CUDA_TRY(cudaMemcpyAsync(&herr, C->err, sizeof(int), cudaMemcpyDeviceToHost, C->st));
+    int herr2[2] = {0, 0};
+    BDDC_CUDA_TRY(cudaMemcpyAsync(herr2, C->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, C->st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    const int herr = herr2[0];
+    C->stats.jacobi_sweeps_max = herr2[1];
     if (herr & ERR_PIVOT) return BDDC_ENUMERIC;
     if (herr & ERR_JACOBI) return BDDC_EGEP;
     if (herr) return BDDC_ECUDA;
@@ -1265,6 +1356,8 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs, const bddc_part
         bddc_set_last_error("no CUDA device", __FILE__, __LINE__);
         return BDDC_ECUDA;
     }
+    int prc = keep_pool_memory();
+    if (prc != BDDC_OK) return prc;
     bddc_ctx* C = new bddc_ctx();
     if (opts) C->o = *opts;
     else bddc_default_opts(&C->o);
@@ -1424,6 +1517,34 @@ int bddc_get_entity(const bddc_ctx* C, int kind, int index, int* subs, int* dofs
 }
 
 unsigned long long bddc_kernel_launches(void) { return g_launches.load(); }
+
+int bddc_kernel_timer(int kind) {
+    if (kind < KT_NONE || kind > KT_EDGE) return BDDC_EINVAL;
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    for (auto& pr : g_kt.ev) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    g_kt = KTimer();
+    g_kt.kind = kind;
+    return BDDC_OK;
+}
+
+int bddc_kernel_timer_read(double* total_ms, long long* launches, double* flops, double* bytes) {
+    std::lock_guard<std::mutex> lk(g_kt_mu);
+    double tot = 0.0;
+    for (auto& pr : g_kt.ev) {
+        BDDC_CUDA_TRY(cudaEventSynchronize(pr.second));
+        float ms = 0.f;
+        BDDC_CUDA_TRY(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = g_kt.launches;
+    if (flops) *flops = g_kt.flops;
+    if (bytes) *bytes = g_kt.bytes;
+    return BDDC_OK;
+}
 
 int bddc_get_edge_features(const bddc_ctx* C, float* feats, int* counts) {
     (void)feats;

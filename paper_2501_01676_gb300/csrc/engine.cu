@@ -23,6 +23,8 @@
 // tiles, register-blocked 4 x 4 per thread.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "bddc_internal.h"
 
 namespace {
@@ -40,6 +42,7 @@ __device__ __forceinline__ bool bad_pivot(T v) {
 template <class T, int NB>
 __global__ void __launch_bounds__(PANEL_THREADS) k_panel(const EngItem<T>* __restrict__ items, int p,
                                                          T* __restrict__ dscr, int* __restrict__ err) {
+    static_assert(NB == 32, "one lane per panel column");
     const EngItem<T> it = items[blockIdx.x];
     if (p >= it.k) return;
     const int w = min(NB, it.k - p);
@@ -52,11 +55,10 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(const EngItem<T>* __res
     __shared__ T D[NB][NB + 1];
     __shared__ T W[NB][CHUNK + 1];             // row chunk (transposed) or column chunk
     T* A = it.a;
-    const int t = threadIdx.x;
-    for (int q = t; q < w * w; q += PANEL_THREADS) {
-        int r = q / w, c = q % w;
-        D[r][c] = A[(long long)(p + r) * ld + p + c];
-    }
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    constexpr int NW = PANEL_THREADS / 32;
+    for (int r = wid; r < w; r += NW)
+        if (lane < w) D[r][lane] = A[(long long)(p + r) * ld + p + lane];
     __syncthreads();
     for (int j = 0; j < w; ++j) {
         T piv = D[j][j];
@@ -64,28 +66,24 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(const EngItem<T>* __res
             if (t == 0 && y == 0) atomicOr(err, ERR_PIVOT);
             piv = (T)1;
         }
-        for (int i = j + 1 + t; i < w; i += PANEL_THREADS) D[i][j] /= piv;
+        if (t > j && t < w) D[t][j] /= piv;
         __syncthreads();
-        const int rem = w - j - 1;
-        for (int q = t; q < rem * rem; q += PANEL_THREADS) {
-            int i = j + 1 + q / rem, l = j + 1 + q % rem;
-            D[i][l] -= D[i][j] * D[j][l];
-        }
+        for (int i = j + 1 + wid; i < w; i += NW)
+            if (lane > j && lane < w) D[i][lane] -= D[i][j] * D[j][lane];
         __syncthreads();
     }
     if (y == 0) {
         T* ds = dscr + (long long)blockIdx.x * NB * NB;
-        for (int q = t; q < w * w; q += PANEL_THREADS) ds[q] = D[q / w][q % w];
+        for (int r = wid; r < w; r += NW)
+            if (lane < w) ds[r * w + lane] = D[r][lane];
         return;
     }
     if (y <= nch) {
         // rows r0 .. r0+CHUNK of L21 = M21 U11^{-1}
         const int r0 = m0 + (y - 1) * CHUNK;
         const int nr = min(CHUNK, n - r0);
-        for (int q = t; q < nr * w; q += PANEL_THREADS) {
-            int r = q / w, c = q % w;
-            W[c][r] = A[(long long)(r0 + r) * ld + p + c];
-        }
+        for (int r = wid; r < nr; r += NW)
+            if (lane < w) W[lane][r] = A[(long long)(r0 + r) * ld + p + lane];
         __syncthreads();
         if (t < nr) {
             for (int j = 0; j < w; ++j) {
@@ -97,18 +95,14 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(const EngItem<T>* __res
             }
         }
         __syncthreads();
-        for (int q = t; q < nr * w; q += PANEL_THREADS) {
-            int r = q / w, c = q % w;
-            A[(long long)(r0 + r) * ld + p + c] = W[c][r];
-        }
+        for (int r = wid; r < nr; r += NW)
+            if (lane < w) A[(long long)(r0 + r) * ld + p + lane] = W[lane][r];
     } else {
         // columns c0 .. c0+CHUNK of U12 = L11^{-1} M12
         const int c0 = m0 + (y - 1 - nch) * CHUNK;
         const int nc = min(CHUNK, n - c0);
-        for (int q = t; q < nc * w; q += PANEL_THREADS) {
-            int r = q / nc, c = q % nc;
-            W[r][c] = A[(long long)(p + r) * ld + c0 + c];
-        }
+        for (int r = 0; r < w; ++r)
+            for (int c = t; c < nc; c += PANEL_THREADS) W[r][c] = A[(long long)(p + r) * ld + c0 + c];
         __syncthreads();
         if (t < nc) {
             for (int i = 1; i < w; ++i) {
@@ -118,11 +112,23 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(const EngItem<T>* __res
             }
         }
         __syncthreads();
-        for (int q = t; q < nc * w; q += PANEL_THREADS) {
-            int r = q / nc, c = q % nc;
-            A[(long long)(p + r) * ld + c0 + c] = W[r][c];
-        }
+        for (int r = 0; r < w; ++r)
+            for (int c = t; c < nc; c += PANEL_THREADS) A[(long long)(p + r) * ld + c0 + c] = W[r][c];
     }
+}
+
+template <class T>
+__device__ __forceinline__ void lds4(const T* p, T out[4]);
+template <>
+__device__ __forceinline__ void lds4<float>(const float* p, float out[4]) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void lds4<double>(const double* p, double out[4]) {
+    double2 v0 = *reinterpret_cast<const double2*>(p);
+    double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+    out[0] = v0.x; out[1] = v0.y; out[2] = v1.x; out[3] = v1.y;
 }
 
 template <class T, int NB>
@@ -137,29 +143,30 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
     const int nt = (mrem + TILE - 1) / TILE;
     const int y = blockIdx.y;
     T* A = it.a;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     if (y == 0) {
         const T* ds = dscr + (long long)blockIdx.x * NB * NB;
-        for (int q = t; q < w * w; q += UPD_THREADS) A[(long long)(p + q / w) * ld + p + q % w] = ds[q];
+        for (int r = wid; r < w; r += UPD_THREADS / 32)
+            if (lane < w) A[(long long)(p + r) * ld + p + lane] = ds[r * w + lane];
         return;
     }
     if (y > nt * nt) return;
-    const int ti = (y - 1) / nt, tj = (y - 1) % nt;
+    const int ti = (y - 1) / nt, tj = (y - 1) - ti * nt;
     const int r0 = m0 + ti * TILE, c0 = m0 + tj * TILE;
-    __shared__ T Ls[NB][TILE + 1];    // L21 tile, transposed: Ls[k][r]
-    __shared__ T Us[NB][TILE + 1];    // U12 tile: Us[k][c]
-    for (int q = t; q < TILE * w; q += UPD_THREADS) {
-        int r = q / w, k = q % w;
+    constexpr int LDT = TILE + 4;      // 16-byte aligned rows for vector loads
+    __shared__ __align__(16) T Ls[NB][LDT];    // L21 tile, transposed: Ls[k][r]
+    __shared__ __align__(16) T Us[NB][LDT];    // U12 tile: Us[k][c]
+    for (int r = wid; r < TILE; r += UPD_THREADS / 32) {
         int gr = r0 + r;
-        Ls[k][r] = gr < n ? A[(long long)gr * ld + p + k] : (T)0;
+        if (lane < w) Ls[lane][r] = gr < n ? A[(long long)gr * ld + p + lane] : (T)0;
     }
-    for (int q = t; q < w * TILE; q += UPD_THREADS) {
-        int k = q / TILE, c = q % TILE;
+    for (int k = t >> 6; k < w; k += UPD_THREADS / TILE) {
+        int c = t & (TILE - 1);
         int gc = c0 + c;
         Us[k][c] = gc < n ? A[(long long)(p + k) * ld + gc] : (T)0;
     }
     __syncthreads();
-    const int tr = t / 16, tc = t % 16;   // 16 x 16 threads, 4 x 4 each (strided by 16)
+    const int tr = (t >> 4) * 4, tc = (t & 15) * 4;   // 16 x 16 threads, a 4 x 4 block each
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -167,10 +174,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
         for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
     for (int k = 0; k < w; ++k) {
         T lv[4], uv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) lv[a] = Ls[k][tr + 16 * a];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) uv[b] = Us[k][tc + 16 * b];
+        lds4<T>(&Ls[k][tr], lv);
+        lds4<T>(&Us[k][tc], uv);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -178,12 +183,13 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        int gr = r0 + tr + 16 * a;
+        int gr = r0 + tr + a;
         if (gr >= n) continue;
+        T* row = A + (long long)gr * ld;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            int gc = c0 + tc + 16 * b;
-            if (gc < n) A[(long long)gr * ld + gc] -= acc[a][b];
+            int gc = c0 + tc + b;
+            if (gc < n) row[gc] -= acc[a][b];
         }
     }
 }
@@ -192,21 +198,37 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
 
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* dscr, int* err,
-               cudaStream_t st) {
+               cudaStream_t st, const int* hn, const int* hk) {
     constexpr int NB = 32;
     if (count <= 0 || maxk <= 0) return BDDC_OK;
     for (int p = 0; p < maxk; p += NB) {
         int mrem = maxn - p;                 // upper bound of the trailing size
         int nch = (mrem + CHUNK - 1) / CHUNK;
         int nt = (mrem + TILE - 1) / TILE;
+        // algorithmic work of this panel: trailing update 2 m^2 w, panel solves ~ 2 w^2 m
+        double fu = 0.0, fp = 0.0, bu = 0.0;
+        if (hn && (ktimer_on(KT_ENGINE_UPDATE) || ktimer_on(KT_ENGINE_PANEL)))
+            for (int i = 0; i < count; ++i) {
+                if (p >= hk[i]) continue;
+                double w = std::min(NB, hk[i] - p), m = hn[i] - p - w;
+                fu += 2.0 * m * m * w;
+                fp += 2.0 * w * w * m;
+                bu += sizeof(T) * (2.0 * m * m + 2.0 * m * w);   // read + write M22, read L21, U12
+            }
+        ktimer_begin(KT_ENGINE_PANEL, st);
         k_panel<T, NB><<<dim3(count, 1 + 2 * nch), PANEL_THREADS, 0, st>>>(items_dev, p, dscr, err);
-    bddc_note_launches(1);
+        bddc_note_launches(1);
+        ktimer_end(KT_ENGINE_PANEL, st, fp, 0.0);
+        ktimer_begin(KT_ENGINE_UPDATE, st);
         k_update<T, NB><<<dim3(count, 1 + nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, dscr);
-    bddc_note_launches(1);
+        bddc_note_launches(1);
+        ktimer_end(KT_ENGINE_UPDATE, st, fu, bu);
     }
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
-template int engine_run<double>(const EngItem<double>*, int, int, int, double*, int*, cudaStream_t);
-template int engine_run<float>(const EngItem<float>*, int, int, int, float*, int*, cudaStream_t);
+template int engine_run<double>(const EngItem<double>*, int, int, int, double*, int*, cudaStream_t,
+                                const int*, const int*);
+template int engine_run<float>(const EngItem<float>*, int, int, int, float*, int*, cudaStream_t,
+                               const int*, const int*);

@@ -30,39 +30,101 @@
 
 namespace {
 
-constexpr int GT = 256;                 // threads per GEP CTA
-constexpr double EIG_DROP = 1e-12;
-constexpr double RANK_TOL = 1e-10;
+constexpr int GT = 512;                 // threads per GEP CTA
+// Tolerances per precision: the FP64 values are the readings of the paper
+// (1e-12 null-space drop, 1e-10 rank); FP32 uses values above its noise floor.
+template <class T> struct Tol;
+template <> struct Tol<double> {
+    static constexpr double drop = 1e-12, rank = 1e-10, slack = 1e-12, tiny = 1e-300;
+    static constexpr double rot_rel = 1e-14, rot_abs = 1e-15, chol = 1e-12;
+};
+template <> struct Tol<float> {
+    static constexpr double drop = 1e-6, rank = 1e-5, slack = 1e-6, tiny = 1e-30;
+    static constexpr double rot_rel = 1e-6, rot_abs = 1e-7, chol = 1e-5;
+};
 constexpr int JACOBI_MAX_SWEEPS = 60;
 
 __device__ __forceinline__ void bar() { __syncthreads(); }
 
+// Visit every (i, j) of an m x n index space with the CTA's threads; one
+// integer division per thread instead of one per element (integer division
+// by a run-time value is a long instruction sequence on this GPU).  An empty
+// extent (m <= 0 or n <= 0) visits nothing.
+#define CTA_FOR_2D(i, j, m, n)                                                             \
+    for (int i##_n = (n) > 0 ? (n) : 1, i = (n) > 0 ? (int)threadIdx.x / i##_n : (m),      \
+             j = (int)threadIdx.x % i##_n, i##_st = GT / i##_n, j##_st = GT % i##_n;       \
+         i < (m); i += i##_st, j += j##_st, i += (j >= i##_n), j -= (j >= i##_n) ? i##_n : 0)
+
+template <class T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the CTA (every thread gets the result).
+template <class T>
+__device__ T block_sum(T v) {
+    __shared__ T red[GT / 32];
+    v = wsum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    bar();
+    T tot = 0;
+#pragma unroll
+    for (int q = 0; q < GT / 32; ++q) tot += red[q];
+    bar();
+    return tot;
+}
+
+// Arg-max over the CTA of (value, index); ties keep the smaller index.
+template <class T>
+__device__ void block_argmax(T v, int i, T* vout, int* iout) {
+    __shared__ T rv[GT / 32];
+    __shared__ int ri[GT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+    }
+    if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = v; ri[threadIdx.x >> 5] = i; }
+    bar();
+    T bv = rv[0];
+    int bi = ri[0];
+    for (int q = 1; q < GT / 32; ++q)
+        if (rv[q] > bv || (rv[q] == bv && ri[q] < bi)) { bv = rv[q]; bi = ri[q]; }
+    *vout = bv;
+    *iout = bi;
+    bar();
+}
+
 // C = alpha * op(A) * op(B) + beta * C ; row-major; transA/transB flags
-__device__ void mm(const double* A, int lda, bool ta, const double* B, int ldb, bool tb, double* C,
-                   int ldc, int m, int n, int k, double alpha, double beta) {
-    for (int q = threadIdx.x; q < m * n; q += GT) {
-        int i = q / n, j = q % n;
-        double s = 0.0;
+template <class T, class TA, class TB, class TC>
+__device__ void mm(const TA* A, int lda, bool ta, const TB* B, int ldb, bool tb, TC* C,
+                   int ldc, int m, int n, int k, T alpha, T beta) {
+    CTA_FOR_2D(i, j, m, n) {
+        T s = 0;
         for (int l = 0; l < k; ++l) {
-            double a = ta ? A[l * lda + i] : A[i * lda + l];
-            double b = tb ? B[j * ldb + l] : B[l * ldb + j];
+            T a = ta ? (T)A[l * lda + i] : (T)A[i * lda + l];
+            T b = tb ? (T)B[j * ldb + l] : (T)B[l * ldb + j];
             s += a * b;
         }
-        C[i * ldc + j] = alpha * s + (beta == 0.0 ? 0.0 : beta * C[i * ldc + j]);
+        C[i * ldc + j] = (TC)(alpha * s + (beta == (T)0 ? (T)0 : beta * (T)C[i * ldc + j]));
     }
     bar();
 }
 
-__device__ void copy_mat(const double* A, int lda, double* B, int ldb, int m, int n) {
-    for (int q = threadIdx.x; q < m * n; q += GT) B[(q / n) * ldb + q % n] = A[(q / n) * lda + q % n];
+template <class TA, class TB>
+__device__ void copy_mat(const TA* A, int lda, TB* B, int ldb, int m, int n) {
+    CTA_FOR_2D(i, j, m, n) B[i * ldb + j] = (TB)A[i * lda + j];
     bar();
 }
 
-__device__ void symmetrize(double* A, int ld, int n) {
-    for (int q = threadIdx.x; q < n * n; q += GT) {
-        int i = q / n, j = q % n;
+template <class T>
+__device__ void symmetrize(T* A, int ld, int n) {
+    CTA_FOR_2D(i, j, n, n) {
         if (i < j) {
-            double v = 0.5 * (A[i * ld + j] + A[j * ld + i]);
+            T v = (T)0.5 * (A[i * ld + j] + A[j * ld + i]);
             A[i * ld + j] = v;
             A[j * ld + i] = v;
         }
@@ -72,24 +134,25 @@ __device__ void symmetrize(double* A, int ld, int n) {
 
 // Solve A X = B in place (A n x n overwritten by its LU, B n x nr overwritten by X);
 // Gaussian elimination with partial pivoting.
-__device__ void lu_solve(double* A, int lda, double* B, int ldb, int n, int nr, int* err) {
+template <class T>
+__device__ void lu_solve(T* A, int lda, T* B, int ldb, int n, int nr, int* err) {
     __shared__ int piv_s;
-    __shared__ double pv_s[32];
+    __shared__ T pv_s[32];
     __shared__ int pi_s[32];
     for (int c = 0; c < n; ++c) {
         // pivot search by warp 0
         if (threadIdx.x < 32) {
-            double best = -1.0;
+            T best = -1.0;
             int bi = c;
             for (int r = c + threadIdx.x; r < n; r += 32) {
-                double v = fabs(A[r * lda + c]);
+                T v = fabs(A[r * lda + c]);
                 if (v > best) { best = v; bi = r; }
             }
             pv_s[threadIdx.x] = best;
             pi_s[threadIdx.x] = bi;
             __syncwarp();
             if (threadIdx.x == 0) {
-                double b = -1.0;
+                T b = -1.0;
                 int ii = c;
                 for (int q = 0; q < 32; ++q)
                     if (pv_s[q] > b) { b = pv_s[q]; ii = pi_s[q]; }
@@ -101,21 +164,22 @@ __device__ void lu_solve(double* A, int lda, double* B, int ldb, int n, int nr, 
         const int p = piv_s;
         if (p != c) {
             for (int q = threadIdx.x; q < n; q += GT) {
-                double t = A[c * lda + q]; A[c * lda + q] = A[p * lda + q]; A[p * lda + q] = t;
+                T t = A[c * lda + q]; A[c * lda + q] = A[p * lda + q]; A[p * lda + q] = t;
             }
             for (int q = threadIdx.x; q < nr; q += GT) {
-                double t = B[c * ldb + q]; B[c * ldb + q] = B[p * ldb + q]; B[p * ldb + q] = t;
+                T t = B[c * ldb + q]; B[c * ldb + q] = B[p * ldb + q]; B[p * ldb + q] = t;
             }
         }
         bar();
-        double d = A[c * lda + c];
-        if (d == 0.0) d = 1e-300;
+        T d = A[c * lda + c];
+        if (d == (T)0) d = (T)Tol<T>::tiny;
         for (int r = c + 1 + threadIdx.x; r < n; r += GT) A[r * lda + c] /= d;
         bar();
         const int rem = n - c - 1;
-        for (int q = threadIdx.x; q < rem * (rem + nr); q += GT) {
-            int r = c + 1 + q / (rem + nr), j = q % (rem + nr);
-            double l = A[r * lda + c];
+        const int wid = rem + nr;
+        CTA_FOR_2D(rr, j, rem, wid) {
+            const int r = c + 1 + rr;
+            T l = A[r * lda + c];
             if (j < rem) A[r * lda + c + 1 + j] -= l * A[c * lda + c + 1 + j];
             else B[r * ldb + (j - rem)] -= l * B[c * ldb + (j - rem)];
         }
@@ -123,12 +187,11 @@ __device__ void lu_solve(double* A, int lda, double* B, int ldb, int n, int nr, 
     }
     // back substitution, column-parallel over the right-hand sides
     for (int c = n - 1; c >= 0; --c) {
-        double d = A[c * lda + c];
-        if (d == 0.0) d = 1e-300;
+        T d = A[c * lda + c];
+        if (d == (T)0) d = (T)Tol<T>::tiny;
         for (int q = threadIdx.x; q < nr; q += GT) B[c * ldb + q] /= d;
         bar();
-        for (int q = threadIdx.x; q < c * nr; q += GT) {
-            int r = q / nr, j = q % nr;
+        CTA_FOR_2D(r, j, c, nr) {
             B[r * ldb + j] -= A[r * lda + c] * B[c * ldb + j];
         }
         bar();
@@ -139,33 +202,38 @@ __device__ void lu_solve(double* A, int lda, double* B, int ldb, int n, int nr, 
 // indices [r0, n) by symmetric diagonal pivoting; pivots <= tol * (largest
 // initial diagonal among them) are left (their directions carry no energy).
 // The leading r0 x r0 block then holds M_ww - M_wr M_rr^+ M_rw.
-__device__ void pinv_schur_tail(double* M, int ld, int n, int r0, unsigned char* done) {
-    __shared__ double dmax0_s, best_s;
+template <class T>
+__device__ void pinv_schur_tail(T* M, int ld, int n, int r0, unsigned char* done) {
+    __shared__ T dmax0_s, best_s;
     __shared__ int bi_s;
     for (int q = threadIdx.x; q < n; q += GT) done[q] = q < r0 ? 1 : 0;
     if (threadIdx.x == 0) {
-        double d = 0.0;
+        T d = 0.0;
         for (int q = r0; q < n; ++q) d = fmax(d, M[q * ld + q]);
         dmax0_s = d;
     }
     bar();
-    const double tol = EIG_DROP * dmax0_s;
+    const T tol = (T)Tol<T>::drop * dmax0_s;
     for (int step = r0; step < n; ++step) {
-        if (threadIdx.x == 0) {
-            double b = -1.0;
-            int bi = -1;
-            for (int q = r0; q < n; ++q)
+        {
+            T b = (T)-1;
+            int bi = n;
+            for (int q = r0 + threadIdx.x; q < n; q += GT)
                 if (!done[q] && M[q * ld + q] > b) { b = M[q * ld + q]; bi = q; }
-            best_s = b;
-            bi_s = bi;
+            T bv;
+            int bidx;
+            block_argmax(b, bi, &bv, &bidx);
+            if (threadIdx.x == 0) {
+                best_s = bv;
+                bi_s = bidx < n ? bidx : -1;
+            }
+            bar();
         }
-        bar();
         if (bi_s < 0 || !(best_s > tol)) break;
         const int p = bi_s;
-        const double dp = M[p * ld + p];
+        const T dp = M[p * ld + p];
         // update all not-yet-eliminated rows/cols (including the kept block)
-        for (int q = threadIdx.x; q < n * n; q += GT) {
-            int i = q / n, j = q % n;
+        CTA_FOR_2D(i, j, n, n) {
             if (i == p || j == p) continue;
             if ((i >= r0 && done[i]) || (j >= r0 && done[j])) continue;
             M[i * ld + j] -= M[i * ld + p] * M[p * ld + j] / dp;
@@ -176,37 +244,32 @@ __device__ void pinv_schur_tail(double* M, int ld, int n, int r0, unsigned char*
     }
 }
 
-// Cyclic parallel Jacobi on a symmetric n x n matrix held in shared memory
-// (ld = np = n rounded up to even).  On exit diag(A) = eigenvalues, V = eigenvectors.
-__device__ void jacobi(double* A, double* V, int n, int np, double* cs, double* sn, int* pp, int* qq,
-                       int* err) {
-    const int ld = np;
-    for (int q = threadIdx.x; q < np * np; q += GT) {
-        int i = q / np, j = q % np;
-        V[q] = i == j ? 1.0 : 0.0;
-        if (i >= n || j >= n) A[i * ld + j] = 0.0;
+// Cyclic parallel Jacobi (round-robin pairs) on a symmetric positive
+// semi-definite n x n matrix in shared memory, row stride ld (odd: no bank
+// conflicts on column access), np = n rounded up to even.  A rotation is
+// applied only when |a_pq| exceeds both rot_rel * sqrt|a_pp a_qq| and
+// rot_abs * max_k a_kk; the sweep in which no rotation was applied ends the
+// iteration.  On exit diag(A) = eigenvalues, V = eigenvectors (columns).
+template <class T>
+__device__ int jacobi(T* A, T* V, int n, int np, int ld, T* cs, T* sn, int* pp, int* qq, int* err) {
+    CTA_FOR_2D(i, j, np, np) {
+        V[i * ld + j] = i == j ? (T)1 : (T)0;
+        if (i >= n || j >= n) A[i * ld + j] = 0;
+    }
+    __shared__ T amax_s;
+    __shared__ int rotated_s;
+    bar();
+    if (threadIdx.x == 0) {
+        T m = 0;
+        for (int i = 0; i < n; ++i) m = fmax(m, fabs(A[i * ld + i]));
+        amax_s = m;
     }
     bar();
-    __shared__ double off_s, tot_s;
+    const T floor_abs = (T)Tol<T>::rot_abs * amax_s;
     const int half = np / 2;
+    if (threadIdx.x == 0) rotated_s = 0;
+    bar();
     for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
-        if (threadIdx.x == 0) {
-            double off = 0.0, tot = 0.0;
-            for (int i = 0; i < n; ++i)
-                for (int j = 0; j < n; ++j) {
-                    double v = A[i * ld + j] * A[i * ld + j];
-                    tot += v;
-                    if (i != j) off += v;
-                }
-            off_s = off;
-            tot_s = tot;
-        }
-        bar();
-        if (off_s <= 1e-26 * tot_s || tot_s == 0.0) return;
-        if (sweep == JACOBI_MAX_SWEEPS - 1) {
-            if (threadIdx.x == 0) atomicOr(err, ERR_JACOBI);
-            return;
-        }
         for (int r = 0; r < np - 1; ++r) {
             for (int k = threadIdx.x; k < half; k += GT) {
                 int p = (r + k) % (np - 1);
@@ -214,58 +277,72 @@ __device__ void jacobi(double* A, double* V, int n, int np, double* cs, double* 
                 if (p > q) { int t = p; p = q; q = t; }
                 pp[k] = p;
                 qq[k] = q;
-                double c = 1.0, s = 0.0;
-                double apq = A[p * ld + q];
-                if (q < n && fabs(apq) > 1e-300) {
-                    double app = A[p * ld + p], aqq = A[q * ld + q];
-                    double th = (aqq - app) / (2.0 * apq);
-                    double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
+                T c = 1, s = 0;
+                T apq = A[p * ld + q];
+                if (q < n) {
+                    T app = A[p * ld + p], aqq = A[q * ld + q];
+                    T lim = fmax((T)Tol<T>::rot_rel * sqrt(fabs(app * aqq)), floor_abs);
+                    if (fabs(apq) > lim && fabs(apq) > (T)Tol<T>::tiny) {
+                        T th = (aqq - app) / ((T)2 * apq);
+                        T t = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + sqrt((T)1 + th * th));
+                        c = (T)1 / sqrt((T)1 + t * t);
+                        s = t * c;
+                        rotated_s = 1;
+                    }
                 }
                 cs[k] = c;
                 sn[k] = s;
             }
             bar();
-            for (int q = threadIdx.x; q < half * np; q += GT) {       // rows p, q
-                int k = q / np, col = q % np;
+            CTA_FOR_2D(k, col, half, np) {                             // rows p, q
+                T s = sn[k];
+                if (s == (T)0) continue;
                 int p = pp[k], qi = qq[k];
-                double c = cs[k], s = sn[k];
-                double a = A[p * ld + col], b = A[qi * ld + col];
+                T c = cs[k];
+                T a = A[p * ld + col], b = A[qi * ld + col];
                 A[p * ld + col] = c * a - s * b;
                 A[qi * ld + col] = s * a + c * b;
             }
             bar();
-            for (int q = threadIdx.x; q < half * np; q += GT) {       // columns p, q
-                int k = q / np, row = q % np;
+            CTA_FOR_2D(k, row, half, np) {                             // columns p, q
+                T s = sn[k];
+                if (s == (T)0) continue;
                 int p = pp[k], qi = qq[k];
-                double c = cs[k], s = sn[k];
-                double a = A[row * ld + p], b = A[row * ld + qi];
+                T c = cs[k];
+                T a = A[row * ld + p], b = A[row * ld + qi];
                 A[row * ld + p] = c * a - s * b;
                 A[row * ld + qi] = s * a + c * b;
-                double va = V[row * ld + p], vb = V[row * ld + qi];
+                T va = V[row * ld + p], vb = V[row * ld + qi];
                 V[row * ld + p] = c * va - s * vb;
                 V[row * ld + qi] = s * va + c * vb;
             }
             bar();
             for (int k = threadIdx.x; k < half; k += GT) {          // the rotated pair is zero
-                if (sn[k] != 0.0) {
-                    A[pp[k] * ld + qq[k]] = 0.0;
-                    A[qq[k] * ld + pp[k]] = 0.0;
+                if (sn[k] != (T)0) {
+                    A[pp[k] * ld + qq[k]] = 0;
+                    A[qq[k] * ld + pp[k]] = 0;
                 }
             }
-            bar();
         }
+        bar();
+        const int any = rotated_s;      // every thread reads the flag before it is reset
+        bar();
+        if (threadIdx.x == 0) rotated_s = 0;
+        bar();                          // and the reset lands before the next sweep sets it
+        if (!any) return sweep + 1;
     }
+    if (threadIdx.x == 0) atomicOr(err, ERR_JACOBI);
+    return JACOBI_MAX_SWEEPS;
 }
 
 // Sort (val, vec columns) by decreasing value (n small; thread 0 computes the order).
-__device__ void sort_desc(const double* A, int ld, int n, int* order) {
+template <class T>
+__device__ void sort_desc(const T* A, int ld, int n, int* order) {
     if (threadIdx.x == 0) {
         for (int i = 0; i < n; ++i) order[i] = i;
         for (int i = 1; i < n; ++i) {
             int v = order[i];
-            double key = A[v * ld + v];
+            T key = A[v * ld + v];
             int j = i - 1;
             while (j >= 0 && A[order[j] * ld + order[j]] < key) { order[j + 1] = order[j]; --j; }
             order[j + 1] = v;
@@ -274,71 +351,157 @@ __device__ void sort_desc(const double* A, int ld, int n, int* order) {
     bar();
 }
 
-// Solve X v = sigma (X + Y) v for symmetric PSD X, Y (n x n in global scratch).
-// On exit: sig[0..r) decreasing, Vout (n x r, ld n) = eigenvectors, r returned.
-__device__ int sigma_pencil(const double* X, const double* Y, int n, double* Ash, double* Vsh, int np,
-                            double* work1, double* work2, double* sig, double* Vout, double* cs,
-                            double* sn, int* pp, int* qq, int* order, int* err) {
-    __shared__ int r_s;
-    __shared__ double kmax_s;
-    for (int q = threadIdx.x; q < n * n; q += GT) {
-        int i = q / n, j = q % n;
-        Ash[i * np + j] = 0.5 * (X[i * n + j] + X[j * n + i]) + 0.5 * (Y[i * n + j] + Y[j * n + i]);
+// In-place Cholesky K = L L^T (lower triangle, shared memory, stride ld);
+// returns false when a pivot falls to <= tol * (largest initial diagonal).
+template <class T>
+__device__ bool cholesky(T* A, int n, int ld, T tol) {
+    __shared__ T dmax_s;
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        T m = 0;
+        for (int i = 0; i < n; ++i) m = fmax(m, A[i * ld + i]);
+        dmax_s = m;
+        ok_s = m > (T)0;
     }
     bar();
-    jacobi(Ash, Vsh, n, np, cs, sn, pp, qq, err);
+    for (int k = 0; k < n && ok_s; ++k) {
+        T d = A[k * ld + k];
+        bar();
+        if (!(d > tol * dmax_s)) {
+            if (threadIdx.x == 0) ok_s = 0;
+            bar();
+            break;
+        }
+        const T l = sqrt(d);
+        for (int i = k + threadIdx.x; i < n; i += GT) A[i * ld + k] = i == k ? l : A[i * ld + k] / l;
+        bar();
+        const int rem = n - k - 1;
+        CTA_FOR_2D(ii, jj, rem, rem) {
+            if (jj <= ii) {
+                const int i = k + 1 + ii, j = k + 1 + jj;
+                A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
+            }
+        }
+        bar();
+    }
+    return ok_s != 0;
+}
+
+// X <- L^{-1} X for an n x m block X (row stride ldx), L lower in (Ls, ldl).
+template <class T>
+__device__ void trsm_lower(const T* Ls, int ldl, T* X, int ldx, int n, int m) {
+    for (int k = 0; k < n; ++k) {
+        const T inv = (T)1 / Ls[k * ldl + k];
+        for (int c = threadIdx.x; c < m; c += GT) X[k * ldx + c] *= inv;
+        bar();
+        const int rem = n - k - 1;
+        CTA_FOR_2D(ii, c, rem, m) {
+            const int i = k + 1 + ii;
+            X[i * ldx + c] -= Ls[i * ldl + k] * X[k * ldx + c];
+        }
+        bar();
+    }
+}
+
+// X <- L^{-T} X for an n x m block X.
+template <class T>
+__device__ void trsm_lower_t(const T* Ls, int ldl, T* X, int ldx, int n, int m) {
+    for (int k = n - 1; k >= 0; --k) {
+        const T inv = (T)1 / Ls[k * ldl + k];
+        for (int c = threadIdx.x; c < m; c += GT) X[k * ldx + c] *= inv;
+        bar();
+        CTA_FOR_2D(i, c, k, m) X[i * ldx + c] -= Ls[k * ldl + i] * X[k * ldx + c];
+        bar();
+    }
+}
+
+// Solve X v = sigma (X + Y) v for symmetric PSD X, Y (n x n in global scratch).
+// On exit: sig[0..r) decreasing, Vout (n x r, row stride r) = eigenvectors
+// with Vout^T (X+Y) Vout = I, r returned.  FP64 (the oracle's reading):
+// eigen-decompose K = X + Y, drop its null directions, reduce, eigen-decompose.
+// FP32: when K is safely positive definite, reduce by its Cholesky factor
+// instead of the first eigen-decomposition.
+template <class T>
+__device__ int sigma_pencil(const T* X, const T* Y, int n, T* Ash, T* Vsh, int np, int ld,
+                            T* work1, T* work2, T* sig, T* Vout, T* cs,
+                            T* sn, int* pp, int* qq, int* order, int* err, int* sweeps) {
+    __shared__ int r_s;
+    CTA_FOR_2D(i, j, n, n) {
+        Ash[i * ld + j] = (T)0.5 * (X[i * n + j] + X[j * n + i]) + (T)0.5 * (Y[i * n + j] + Y[j * n + i]);
+    }
+    bar();
+    if (sizeof(T) == 4 && cholesky(Ash, n, ld, (T)Tol<T>::chol)) {
+        // L -> work1 (n x n), C = L^{-1} X L^{-T} -> Ash
+        CTA_FOR_2D(i, j, n, n) work1[i * n + j] = j <= i ? Ash[i * ld + j] : (T)0;
+        bar();
+        CTA_FOR_2D(i, j, n, n) work2[i * n + j] = X[i * n + j];
+        bar();
+        trsm_lower(work1, n, work2, n, n, n);                     // Z = L^{-1} X
+        CTA_FOR_2D(i, j, n, n) Ash[i * ld + j] = work2[j * n + i];  // Z^T
+        bar();
+        trsm_lower(work1, n, Ash, ld, n, n);                      // L^{-1} Z^T = C
+        CTA_FOR_2D(i, j, n, n) {
+            if (i < j) {
+                T v = (T)0.5 * (Ash[i * ld + j] + Ash[j * ld + i]);
+                Ash[i * ld + j] = v;
+                Ash[j * ld + i] = v;
+            }
+        }
+        bar();
+        int sw = jacobi(Ash, Vsh, n, np, ld, cs, sn, pp, qq, err);
+        if (threadIdx.x == 0) atomicMax(sweeps, sw);
+        sort_desc(Ash, ld, n, order);
+        for (int q = threadIdx.x; q < n; q += GT) sig[q] = Ash[order[q] * ld + order[q]];
+        CTA_FOR_2D(i, c, n, n) Vout[i * n + c] = Vsh[i * ld + order[c]];
+        bar();
+        trsm_lower_t(work1, n, Vout, n, n, n);                    // V = L^{-T} Y
+        return n;
+    }
+    // eigen-decomposition route (also the fallback of the FP32 path)
+    CTA_FOR_2D(i, j, n, n) {
+        Ash[i * ld + j] = (T)0.5 * (X[i * n + j] + X[j * n + i]) + (T)0.5 * (Y[i * n + j] + Y[j * n + i]);
+    }
+    bar();
+    int sw = jacobi(Ash, Vsh, n, np, ld, cs, sn, pp, qq, err);
     if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int i = 0; i < n; ++i) m = fmax(m, Ash[i * np + i]);
-        kmax_s = m;
+        atomicMax(sweeps, sw);
+        T m = 0;
+        for (int i = 0; i < n; ++i) m = fmax(m, Ash[i * ld + i]);
         int r = 0;
         for (int i = 0; i < n; ++i)
-            if (m > 0.0 && Ash[i * np + i] > EIG_DROP * m) order[r++] = i;
+            if (m > (T)0 && Ash[i * ld + i] > (T)Tol<T>::drop * m) order[r++] = i;
         r_s = r;
     }
     bar();
     const int r = r_s;
     if (r == 0) return 0;
     // W = U_keep / sqrt(kappa)  (n x r) -> work1
-    for (int q = threadIdx.x; q < n * r; q += GT) {
-        int i = q / r, c = q % r;
+    CTA_FOR_2D(i, c, n, r) {
         int col = order[c];
-        work1[i * r + c] = Vsh[i * np + col] / sqrt(Ash[col * np + col]);
+        work1[i * r + c] = Vsh[i * ld + col] / sqrt(Ash[col * ld + col]);
     }
     bar();
     // C = W^T X W -> shared A (r x r)
-    mm(X, n, false, work1, r, false, work2, r, n, r, n, 1.0, 0.0);        // X W  (n x r)
-    for (int q = threadIdx.x; q < np * np; q += GT) Ash[q] = 0.0;
-    bar();
-    mm(work1, r, true, work2, r, false, Ash, np, r, r, n, 1.0, 0.0);     // W^T (X W)
-    // symmetrize in shared
-    for (int q = threadIdx.x; q < r * r; q += GT) {
-        int i = q / r, j = q % r;
+    mm(X, n, false, work1, r, false, work2, r, n, r, n, (T)1, (T)0);        // X W  (n x r)
+    mm(work1, r, true, work2, r, false, Ash, ld, r, r, n, (T)1, (T)0);     // W^T (X W)
+    CTA_FOR_2D(i, j, r, r) {
         if (i < j) {
-            double v = 0.5 * (Ash[i * np + j] + Ash[j * np + i]);
-            Ash[i * np + j] = v;
-            Ash[j * np + i] = v;
+            T v = (T)0.5 * (Ash[i * ld + j] + Ash[j * ld + i]);
+            Ash[i * ld + j] = v;
+            Ash[j * ld + i] = v;
         }
     }
     bar();
     const int rp = (r + 1) & ~1;
-    // repack to ld rp for the second Jacobi (in place is unsafe: copy through work2)
-    for (int q = threadIdx.x; q < r * r; q += GT) work2[q] = Ash[(q / r) * np + q % r];
-    bar();
-    for (int q = threadIdx.x; q < rp * rp; q += GT) {
-        int i = q / rp, j = q % rp;
-        Ash[q] = (i < r && j < r) ? work2[i * r + j] : 0.0;
-    }
-    bar();
-    jacobi(Ash, Vsh, r, rp, cs, sn, pp, qq, err);
-    sort_desc(Ash, rp, r, order);
-    for (int q = threadIdx.x; q < r; q += GT) sig[q] = Ash[order[q] * rp + order[q]];
+    sw = jacobi(Ash, Vsh, r, rp, ld, cs, sn, pp, qq, err);
+    if (threadIdx.x == 0) atomicMax(sweeps, sw);
+    sort_desc(Ash, ld, r, order);
+    for (int q = threadIdx.x; q < r; q += GT) sig[q] = Ash[order[q] * ld + order[q]];
     // Vout = W Y(:, order)
-    for (int q = threadIdx.x; q < n * r; q += GT) {
-        int i = q / r, c = q % r;
+    CTA_FOR_2D(i, c, n, r) {
         int col = order[c];
-        double s = 0.0;
-        for (int l = 0; l < r; ++l) s += work1[i * r + l] * Vsh[l * rp + col];
+        T s = 0;
+        for (int l = 0; l < r; ++l) s += work1[i * r + l] * Vsh[l * ld + col];
         Vout[i * r + c] = s;
     }
     bar();
@@ -348,50 +511,51 @@ __device__ int sigma_pencil(const double* X, const double* Y, int n, double* Ash
 // Householder QR with column pivoting of C (n x m, ld m, destroyed).  Returns
 // the numerical rank k and writes Q (n x n, ld n): its first k columns span
 // range(C), the rest its orthogonal complement.
-__device__ int qr_basis(double* C, int n, int m, double* Q, double* vbuf /* n*n */, double* norms,
-                        double* tau) {
+template <class T>
+__device__ int qr_basis(T* C, int n, int m, T* Q, T* vbuf /* n*n */, T* norms,
+                        T* tau) {
     __shared__ int k_s, piv_s;
-    __shared__ double n0_s, alpha_s;
-    for (int q = threadIdx.x; q < n * n; q += GT) Q[q] = (q / n == q % n) ? 1.0 : 0.0;
+    __shared__ T n0_s, alpha_s;
+    for (int q = threadIdx.x; q < n * n; q += GT) Q[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
     if (threadIdx.x == 0) k_s = 0;
     bar();
     int steps = min(n, m);
     for (int j = 0; j < steps; ++j) {
         // column norms of the trailing part
         for (int c = threadIdx.x; c < m; c += GT) {
-            double s = 0.0;
+            T s = 0.0;
             if (c >= j)
                 for (int i = j; i < n; ++i) s += C[i * m + c] * C[i * m + c];
             norms[c] = s;
         }
         bar();
         if (threadIdx.x == 0) {
-            double b = -1.0;
+            T b = -1.0;
             int bi = j;
             for (int c = j; c < m; ++c)
                 if (norms[c] > b) { b = norms[c]; bi = c; }
             piv_s = bi;
-            double nb = sqrt(fmax(b, 0.0));
+            T nb = sqrt(b > (T)0 ? b : (T)0);
             if (j == 0) n0_s = nb;
             alpha_s = nb;
         }
         bar();
-        const double al = alpha_s, n0 = n0_s;
+        const T al = alpha_s, n0 = n0_s;
         const int p = piv_s;
         bar();
-        if (!(al > RANK_TOL * n0) || n0 == 0.0) break;
+        if (!(al > (T)Tol<T>::rank * n0) || n0 == 0.0) break;
         if (p != j) {
             for (int i = threadIdx.x; i < n; i += GT) {
-                double t = C[i * m + j]; C[i * m + j] = C[i * m + p]; C[i * m + p] = t;
+                T t = C[i * m + j]; C[i * m + j] = C[i * m + p]; C[i * m + p] = t;
             }
             bar();
         }
         // Householder vector for column j, rows j..n-1
         if (threadIdx.x == 0) {
-            double x0 = C[j * m + j];
-            double a = x0 >= 0 ? -al : al;       // reflect to a e_j
-            double v0 = x0 - a;
-            double vn2 = al * al - x0 * x0 + v0 * v0;
+            T x0 = C[j * m + j];
+            T a = x0 >= 0 ? -al : al;       // reflect to a e_j
+            T v0 = x0 - a;
+            T vn2 = al * al - x0 * x0 + v0 * v0;
             tau[j] = vn2 > 0 ? 2.0 / vn2 : 0.0;
             vbuf[j * n + j] = v0;
         }
@@ -400,7 +564,7 @@ __device__ int qr_basis(double* C, int n, int m, double* Q, double* vbuf /* n*n 
         bar();
         // apply H = I - tau v v^T to columns j..m-1
         for (int c = j + threadIdx.x; c < m; c += GT) {
-            double s = 0.0;
+            T s = 0.0;
             for (int i = j; i < n; ++i) s += vbuf[j * n + i] * C[i * m + c];
             s *= tau[j];
             for (int i = j; i < n; ++i) C[i * m + c] -= s * vbuf[j * n + i];
@@ -413,7 +577,7 @@ __device__ int qr_basis(double* C, int n, int m, double* Q, double* vbuf /* n*n 
     // Q = H_0 H_1 ... H_{k-1} I
     for (int j = k - 1; j >= 0; --j) {
         for (int c = threadIdx.x; c < n; c += GT) {
-            double s = 0.0;
+            T s = 0.0;
             for (int i = j; i < n; ++i) s += vbuf[j * n + i] * Q[i * n + c];
             s *= tau[j];
             for (int i = j; i < n; ++i) Q[i * n + c] -= s * vbuf[j * n + i];
@@ -424,28 +588,30 @@ __device__ int qr_basis(double* C, int n, int m, double* Q, double* vbuf /* n*n 
 }
 
 // ------------------------------------------------------------------- face
+template <class T>
 __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, int* __restrict__ err) {
     const FaceJob J = jobs[blockIdx.x];
     const int n = J.n, np = (n + 1) & ~1;
-    extern __shared__ double shm[];
-    double* Ash = shm;
-    double* Vsh = shm + np * np;
-    __shared__ double cs[64], sn[64];
+    extern __shared__ __align__(16) unsigned char shm_raw[];
+    T* shm = reinterpret_cast<T*>(shm_raw);
+    T* Ash = shm;
+    const int ldj = np + 1;                    // odd shared-memory row stride
+    T* Vsh = shm + np * ldj;
+    __shared__ T cs[64], sn[64];
     __shared__ int pp[64], qq[64];
     __shared__ int order[128];
     __shared__ unsigned char done[256];
-    double* w = J.work;
+    T* w = (T*)J.work;
     const int nn = n * n;
-    double *Si = w, *Sj = w + nn, *Ssum = w + 2 * nn, *Dij = w + 3 * nn /* n x 2n */;
-    double *BF = w + 5 * nn, *Bti = w + 6 * nn, *Btj = w + 7 * nn, *Bt = w + 8 * nn;
-    double *T1 = w + 9 * nn, *T2 = w + 10 * nn, *V = w + 11 * nn, *W1 = w + 12 * nn,
+    T *Si = w, *Sj = w + nn, *Ssum = w + 2 * nn, *Dij = w + 3 * nn /* n x 2n */;
+    T *BF = w + 5 * nn, *Bti = w + 6 * nn, *Btj = w + 7 * nn, *Bt = w + 8 * nn;
+    T *T1 = w + 9 * nn, *T2 = w + 10 * nn, *V = w + 11 * nn, *W1 = w + 12 * nn,
            *W2 = w + 13 * nn, *Cm = w + 14 * nn, *vb = w + 15 * nn, *PS = w + 16 * nn /* 4 nn */;
-    double* aux = w + 20 * nn;   // 3n
+    T* aux = w + 20 * nn;   // 3n
     // gather S_FF blocks
-    for (int q = threadIdx.x; q < nn; q += GT) {
-        int a = q / n, b = q % n;
-        Si[q] = J.Si[(long long)J.pi[a] * J.ldi + J.pi[b]];
-        Sj[q] = J.Sj[(long long)J.pj[a] * J.ldj + J.pj[b]];
+    CTA_FOR_2D(a, b, n, n) {
+        Si[a * n + b] = J.Si[(long long)J.pi[a] * J.ldi + J.pi[b]];
+        Sj[a * n + b] = J.Sj[(long long)J.pj[a] * J.ldj + J.pj[b]];
     }
     bar();
     for (int q = threadIdx.x; q < nn; q += GT) {
@@ -457,14 +623,13 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     bar();
     lu_solve(Ssum, n, Dij, 2 * n, n, 2 * n, err);              // [D^(i) | D^(j)]
     // B_F = D_j^T B_FF^(i) D_j + D_i^T B_FF^(j) D_i   (B_FF = sym(S_FF))
-    for (int q = threadIdx.x; q < nn; q += GT) {
-        int a = q / n, b = q % n;
-        T1[q] = 0.5 * (Si[a * n + b] + Si[b * n + a]);
-        T2[q] = 0.5 * (Sj[a * n + b] + Sj[b * n + a]);
+    CTA_FOR_2D(a, b, n, n) {
+        T1[a * n + b] = (T)0.5 * (Si[a * n + b] + Si[b * n + a]);
+        T2[a * n + b] = (T)0.5 * (Sj[a * n + b] + Sj[b * n + a]);
     }
     bar();
-    const double* Di = Dij;
-    const double* Dj = Dij + n;
+    const T* Di = Dij;
+    const T* Dj = Dij + n;
     mm(T1, n, false, Dj, 2 * n, false, W1, n, n, n, n, 1.0, 0.0);
     mm(Dj, 2 * n, true, W1, n, false, BF, n, n, n, n, 1.0, 0.0);
     mm(T2, n, false, Di, 2 * n, false, W1, n, n, n, n, 1.0, 0.0);
@@ -476,14 +641,13 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     symmetrize(Bti, n, n);
     symmetrize(Btj, n, n);
     const int n2 = 2 * n;
-    for (int q = threadIdx.x; q < n2 * n2; q += GT) {
-        int a = q / n2, b = q % n2;
-        double v;
+    CTA_FOR_2D(a, b, n2, n2) {
+        T v;
         if (a < n && b < n) v = Bti[a * n + b];
         else if (a < n) v = Bti[a * n + b - n];
         else if (b < n) v = Bti[(a - n) * n + b];
         else v = Bti[(a - n) * n + b - n] + Btj[(a - n) * n + b - n];
-        PS[q] = v;        // order [B~_i, B~_i; B~_i, B~_i + B~_j]: eliminate the tail
+        PS[a * n2 + b] = v;        // order [B~_i, B~_i; B~_i, B~_i + B~_j]: eliminate the tail
     }
     bar();
     pinv_schur_tail(PS, n2, n2, n, done);
@@ -491,14 +655,14 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     symmetrize(Bt, n, n);
     int k = 0;
     if (J.mode == 0) {
-        int r = sigma_pencil(BF, Bt, n, Ash, Vsh, np, W1, W2, aux, V, cs, sn, pp, qq, order, err);
-        const double sth = J.theta / (1.0 + J.theta) - 1e-12;
+        int r = sigma_pencil(BF, Bt, n, Ash, Vsh, np, ldj, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1);
+        const T sth = (T)(J.theta / (1.0 + J.theta) - Tol<T>::slack);
         __shared__ int nsel_s;
         if (threadIdx.x == 0) {
             int c = 0;
             for (int q = 0; q < r; ++q) {
-                double sg = aux[q];
-                J.lambda[q] = (1.0 - sg <= 1e-12) ? INFINITY : sg / (1.0 - sg);
+                T sg = aux[q];
+                J.lambda[q] = (1.0 - (double)sg <= Tol<T>::slack) ? INFINITY : (double)sg / (1.0 - (double)sg);
                 if (sg >= sth) ++c;
             }
             for (int q = r; q < n; ++q) J.lambda[q] = NAN;
@@ -512,11 +676,11 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
             mm(BF, n, false, V, r, false, Cm, s, n, s, n, 1.0, 0.0);
             k = qr_basis(Cm, n, s, T1, vb, aux + n, aux + 2 * n);
         } else {
-            for (int q = threadIdx.x; q < nn; q += GT) T1[q] = (q / n == q % n) ? 1.0 : 0.0;
+            for (int q = threadIdx.x; q < nn; q += GT) T1[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
             bar();
         }
     } else {
-        for (int q = threadIdx.x; q < nn; q += GT) T1[q] = (q / n == q % n) ? 1.0 : 0.0;
+        for (int q = threadIdx.x; q < nn; q += GT) T1[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
         if (threadIdx.x == 0) *J.neig = 0;
         bar();
         k = J.mode == 1 ? n : 0;
@@ -529,53 +693,55 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
 }
 
 // ------------------------------------------------------------------- edge
+template <class T>
 __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, int* __restrict__ err) {
     const EdgeJob J = jobs[blockIdx.x];
     const int n = J.n, m = J.m, nw = (m - 1) * n, mn = m * n;
     const int nz = mn + J.nH;
     const int np = (nw + 1) & ~1;
-    extern __shared__ double shm[];
-    double* Ash = shm;
-    double* Vsh = shm + np * np;
-    __shared__ double cs[64], sn[64];
+    extern __shared__ __align__(16) unsigned char shm_raw[];
+    T* shm = reinterpret_cast<T*>(shm_raw);
+    T* Ash = shm;
+    const int ldj = np + 1;                    // odd shared-memory row stride
+    T* Vsh = shm + np * ldj;
+    __shared__ T cs[64], sn[64];
     __shared__ int pp[64], qq[64];
     __shared__ int order[128];
     __shared__ unsigned char done[1024];
-    double* w = J.work;
+    T* w = (T*)J.work;
     const int nn = n * n;
-    double* Ssum = w;                     // n x n
-    double* Dall = Ssum + nn;             // n x (m n): [D^(k_1) ... D^(k_m)]
-    double* Tk = Dall + n * mn;           // m blocks of n x (m n)
-    double* BE = Tk + m * n * mn;         // m blocks n x n (sym S_EE)
-    double* ME = BE + m * nn;             // nw x nw
-    double* T1 = ME + nw * nw;            // scratch  (max(n x mn, nz x nz))
-    double* Bt = T1 + (size_t)nz * nz;    // nz x nz
-    double* BB = Bt + (size_t)nz * nz;    // nw x nw
-    double* W1 = BB + nw * nw;            // nw x nw
-    double* W2 = W1 + nw * nw;
-    double* V = W2 + nw * nw;
-    double* Cm = V + nw * nw;             // n x (m-1) nw
-    double* vb = Cm + n * nw * (m - 1) + nw;
-    double* Qo = vb + nn;
-    double* aux = Qo + nn;                // sigma (nw), QR norms ((m-1) nw), tau (n)
+    T* Ssum = w;                     // n x n
+    T* Dall = Ssum + nn;             // n x (m n): [D^(k_1) ... D^(k_m)]
+    T* Tk = Dall + n * mn;           // m blocks of n x (m n)
+    T* BE = Tk + m * n * mn;         // m blocks n x n (sym S_EE)
+    T* ME = BE + m * nn;             // nw x nw
+    T* T1 = ME + nw * nw;            // scratch  (max(n x mn, nz x nz))
+    T* Bt = T1 + (size_t)nz * nz;    // nz x nz
+    T* BB = Bt + (size_t)nz * nz;    // nw x nw
+    T* W1 = BB + nw * nw;            // nw x nw
+    T* W2 = W1 + nw * nw;
+    T* V = W2 + nw * nw;
+    T* Cm = V + nw * nw;             // n x (m-1) nw
+    T* vb = Cm + n * nw * (m - 1) + nw;
+    T* Qo = vb + nn;
+    T* aux = Qo + nn;                // sigma (nw), QR norms ((m-1) nw), tau (n)
     // deluxe scaling D^(k) = (sum_l S_EE^(l))^{-1} S_EE^(k)
-    for (int q = threadIdx.x; q < nn; q += GT) {
-        int a = q / n, b = q % n;
-        double s = 0.0;
+    CTA_FOR_2D(a, b, n, n) {
+        T s = 0.0;
         for (int t = 0; t < m; ++t) {
-            double v = J.S[t][(long long)J.pos[t][a] * J.ldS[t] + J.pos[t][b]];
+            T v = J.S[t][(long long)J.pos[t][a] * J.ldS[t] + J.pos[t][b]];
             s += v;
             Dall[a * mn + t * n + b] = v;
         }
-        Ssum[q] = s;
+        Ssum[a * n + b] = s;
     }
     bar();
     for (int q = threadIdx.x; q < m * nn; q += GT) {
         int t = q / nn, a = (q % nn) / n, b = q % n;
         const double* St = J.S[t];
-        double v1 = St[(long long)J.pos[t][a] * J.ldS[t] + J.pos[t][b]];
-        double v2 = St[(long long)J.pos[t][b] * J.ldS[t] + J.pos[t][a]];
-        BE[q] = 0.5 * (v1 + v2);
+        T v1 = St[(long long)J.pos[t][a] * J.ldS[t] + J.pos[t][b]];
+        T v2 = St[(long long)J.pos[t][b] * J.ldS[t] + J.pos[t][a]];
+        BE[q] = (T)0.5 * (v1 + v2);
     }
     bar();
     lu_solve(Ssum, n, Dall, mn, n, mn, err);
@@ -583,7 +749,7 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
     for (int q = threadIdx.x; q < m * n * mn; q += GT) {
         int t = q / (n * mn), a = (q % (n * mn)) / mn, col = q % mn;
         int blk = col / n, b = col % n;
-        double v;
+        T v;
         if (blk == m - 1) v = (a == b) ? 1.0 : 0.0;
         else {
             int l = blk + 1;
@@ -606,39 +772,36 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
     for (int q = threadIdx.x; q < nz * nz; q += GT) Bt[q] = 0.0;
     bar();
     for (int t = 0; t < m; ++t) {
-        const double* G = J.Bt[t];
+        const T* G = (const T*)J.Bt[t];
         const int ldg = J.ldBt[t];
         const int h = J.h[t];
         const int* hm = J.hmap[t];
-        const double* T = Tk + t * n * mn;
+        const T* Tm = Tk + t * n * mn;
         // EE: T^T G_EE T  ->  Bt[0:mn, 0:mn]
         for (int q = threadIdx.x; q < n * mn; q += GT) {        // T1 = G_EE T  (n x mn)
             int a = q / mn, c = q % mn;
-            double s = 0.0;
-            for (int l = 0; l < n; ++l) s += G[a * ldg + l] * T[l * mn + c];
+            T s = 0.0;
+            for (int l = 0; l < n; ++l) s += G[a * ldg + l] * Tm[l * mn + c];
             T1[q] = s;
         }
         bar();
-        for (int q = threadIdx.x; q < mn * mn; q += GT) {
-            int a = q / mn, c = q % mn;
-            double s = 0.0;
-            for (int l = 0; l < n; ++l) s += T[l * mn + a] * T1[l * mn + c];
+        CTA_FOR_2D(a, c, mn, mn) {
+            T s = 0.0;
+            for (int l = 0; l < n; ++l) s += Tm[l * mn + a] * T1[l * mn + c];
             Bt[a * nz + c] += s;
         }
         bar();
         // EH and HE: T^T G_EH
-        for (int q = threadIdx.x; q < mn * h; q += GT) {
-            int a = q / h, u = q % h;
-            double s = 0.0;
-            for (int l = 0; l < n; ++l) s += T[l * mn + a] * G[l * ldg + n + u];
+        CTA_FOR_2D(a, u, mn, h) {
+            T s = 0.0;
+            for (int l = 0; l < n; ++l) s += Tm[l * mn + a] * G[l * ldg + n + u];
             Bt[a * nz + mn + hm[u]] += s;
-            double s2 = 0.0;
-            for (int l = 0; l < n; ++l) s2 += G[(n + u) * ldg + l] * T[l * mn + a];
+            T s2 = 0.0;
+            for (int l = 0; l < n; ++l) s2 += G[(n + u) * ldg + l] * Tm[l * mn + a];
             Bt[(mn + hm[u]) * nz + a] += s2;
         }
         bar();
-        for (int q = threadIdx.x; q < h * h; q += GT) {
-            int u = q / h, v = q % h;
+        CTA_FOR_2D(u, v, h, h) {
             Bt[(mn + hm[u]) * nz + mn + hm[v]] += G[(n + u) * ldg + n + v];
         }
         bar();
@@ -652,17 +815,17 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
     bar();
     }
     int k = 0;
-    for (int q = threadIdx.x; q < nn; q += GT) Qo[q] = (q / n == q % n) ? 1.0 : 0.0;
+    for (int q = threadIdx.x; q < nn; q += GT) Qo[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
     bar();
     if (J.mode == 0) {
-        int r = sigma_pencil(ME, BB, nw, Ash, Vsh, np, W1, W2, aux, V, cs, sn, pp, qq, order, err);
-        const double sth = J.theta / (1.0 + J.theta) - 1e-12;
+        int r = sigma_pencil(ME, BB, nw, Ash, Vsh, np, ldj, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1);
+        const T sth = (T)(J.theta / (1.0 + J.theta) - Tol<T>::slack);
         __shared__ int nsel_s;
         if (threadIdx.x == 0) {
             int c = 0;
             for (int q = 0; q < r; ++q) {
-                double sg = aux[q];
-                J.lambda[q] = (1.0 - sg <= 1e-12) ? INFINITY : sg / (1.0 - sg);
+                T sg = aux[q];
+                J.lambda[q] = (1.0 - (double)sg <= Tol<T>::slack) ? INFINITY : (double)sg / (1.0 - (double)sg);
                 if (sg >= sth) ++c;
             }
             for (int q = r; q < nw; ++q) J.lambda[q] = NAN;
@@ -674,11 +837,10 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
         if (s > 0) {
             // c_l = M_E v_l (nw); Cm columns = its n-blocks: col (l * (m-1) + b)
             const int nc = s * (m - 1);
-            for (int q = threadIdx.x; q < n * nc; q += GT) {
-                int a = q / nc, cidx = q % nc;
+            CTA_FOR_2D(a, cidx, n, nc) {
                 int l = cidx / (m - 1), b = cidx % (m - 1);
                 int row = b * n + a;
-                double acc = 0.0;
+                T acc = 0.0;
                 for (int t = 0; t < nw; ++t) acc += ME[row * nw + t] * V[t * r + l];
                 Cm[a * nc + cidx] = acc;
             }
@@ -705,26 +867,33 @@ size_t edge_work_doubles(int n, int m, int nH) {
            (size_t)n * nw * (m - 1) + nw + (size_t)m * nw + n + 64;
 }
 
+template <class T>
 int face_run(const FaceJob* jobs_dev, int count, int maxn, int* err, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
     int np = (maxn + 1) & ~1;
-    size_t smem = (size_t)2 * np * np * sizeof(double);
+    size_t smem = (size_t)2 * np * (np + 1) * sizeof(T);
     if (np > 128 || smem > 200 * 1024) return BDDC_EINVAL;
-    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_face, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_face<<<count, GT, smem, st>>>(jobs_dev, err);
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_face<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_face<T><<<count, GT, smem, st>>>(jobs_dev, err);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
+template <class T>
 int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, int* err, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
     int np = (maxnw + 1) & ~1;
-    size_t smem = (size_t)2 * np * np * sizeof(double);
+    size_t smem = (size_t)2 * np * (np + 1) * sizeof(T);
     if (np > 128 || smem > 200 * 1024 || maxnz > 1024) return BDDC_EINVAL;
-    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_edge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_edge<<<count, GT, smem, st>>>(jobs_dev, err);
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_edge<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_edge<T><<<count, GT, smem, st>>>(jobs_dev, err);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
+
+template int face_run<double>(const FaceJob*, int, int, int*, cudaStream_t);
+template int face_run<float>(const FaceJob*, int, int, int*, cudaStream_t);
+template int edge_run<double>(const EdgeJob*, int, int, int, int*, cudaStream_t);
+template int edge_run<float>(const EdgeJob*, int, int, int, int*, cudaStream_t);

@@ -17,7 +17,7 @@ struct FaceJob {
     const double* Bti;        // Schur complement of B^(i) onto F (ld ldbi)
     const double* Btj;
     int ldbi, ldbj;
-    double* work;             // face_work_doubles(n) doubles
+    void* work;               // face_work_doubles(n) elements of the kernel precision
     double* Q;                // out: n x n orthogonal, first k columns primal (row-major)
     double* DQi;              // out: D^(i) Q
     double* DQj;              // out: D^(j) Q
@@ -35,11 +35,11 @@ struct EdgeJob {
     const double* S[EDGE_MAX_SUBS];    // packed S^(k) in sorted n(E) order
     int ldS[EDGE_MAX_SUBS];
     const int* pos[EDGE_MAX_SUBS];     // local positions of the edge in S^(k)
-    const double* Bt[EDGE_MAX_SUBS];   // Schur complement of B^(k) onto [E, H_k]
+    const void* Bt[EDGE_MAX_SUBS];     // Schur complement of B^(k) onto [E, H_k] (kernel precision)
     int ldBt[EDGE_MAX_SUBS];
     int h[EDGE_MAX_SUBS];              // |H_k|
     const int* hmap[EDGE_MAX_SUBS];    // H_k coordinate -> union index
-    double* work;
+    void* work;
     double* Q;                // out: n x n
     double* DQ[EDGE_MAX_SUBS];// out: D^(k) Q
     double* lambda;           // out: (m-1) n eigenvalues
@@ -50,5 +50,7 @@ struct EdgeJob {
 
 size_t face_work_doubles(int n);
 size_t edge_work_doubles(int n, int m, int nH);
+template <class T>
 int face_run(const FaceJob* jobs_dev, int count, int maxn, int* err, cudaStream_t st);
+template <class T>
 int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, int* err, cudaStream_t st);

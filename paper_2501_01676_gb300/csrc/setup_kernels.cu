@@ -20,11 +20,10 @@ __global__ void k_copy_blocks(const CopyJob* __restrict__ jobs) {
     const CopyJob J = jobs[blockIdx.x];
     const TS* src = (const TS*)J.src;
     TD* dst = (TD*)J.dst;
-    const long long tot = (long long)J.rows * J.cols;
-    for (long long q = blockIdx.y * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.y * TH) {
-        int r = (int)(q / J.cols), c = (int)(q % J.cols);
-        double v = (double)src[(long long)(J.r0 + r) * J.sld + J.c0 + c];
-        dst[(long long)r * J.dld + c] = (TD)(J.scale * v);
+    for (int r = blockIdx.y; r < J.rows; r += gridDim.y) {
+        const TS* sr = src + (long long)(J.r0 + r) * J.sld + J.c0;
+        TD* dr = dst + (long long)r * J.dld;
+        for (int c = threadIdx.x; c < J.cols; c += TH) dr[c] = (TD)(J.scale * (double)sr[c]);
     }
 }
 
@@ -34,68 +33,76 @@ __global__ void k_gather_perm(const GatherJob* __restrict__ jobs, const int* __r
     const GatherJob J = jobs[blockIdx.x];
     const int* p = idx + J.perm_off;
     TD* dst = (TD*)J.dst;
-    const long long tot = (long long)J.n * J.n;
-    for (long long q = blockIdx.y * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.y * TH) {
-        int a = (int)(q / J.n), b = (int)(q % J.n);
-        long long ia = p[a], ib = p[b];
-        double v = J.src[ia * J.sld + ib];
-        if (J.sym) v = 0.5 * (v + J.src[ib * J.sld + ia]);
-        dst[(long long)a * J.dld + b] = (TD)v;
+    for (int a = blockIdx.y; a < J.n; a += gridDim.y) {
+        const long long ia = p[a];
+        for (int b = threadIdx.x; b < J.n; b += TH) {
+            const long long ib = p[b];
+            double v = J.src[ia * J.sld + ib];
+            if (J.sym) v = 0.5 * (v + J.src[ib * J.sld + ia]);
+            dst[(long long)a * J.dld + b] = (TD)v;
+        }
     }
 }
 
-// Right multiplication Y[r][pos[l]] = sum_a B[r][pos[a]] Q[a][l] for one entity block.
+// Right multiplication Y[r][pos[l]] = sum_a B[r][pos[a]] Q[a][l] for one entity block
+// (arithmetic and the scratch Y in precision TY).
+template <class TY>
 __global__ void k_transform_right(const TBlock* __restrict__ blocks, const int* __restrict__ idx) {
     const TBlock B = blocks[blockIdx.x];
-    extern __shared__ double Qs[];
+    extern __shared__ __align__(16) unsigned char qraw[];
+    TY* Qs = reinterpret_cast<TY*>(qraw);
     const int n = B.n;
     const int* pos = idx + B.pos_off;
+    TY* Y = (TY*)B.y;
     if (!B.identity)
-        for (int q = threadIdx.x; q < n * n; q += TH) Qs[q] = B.Q[q];
+        for (int q = threadIdx.x; q < n * n; q += TH) Qs[q] = (TY)B.Q[q];
     __syncthreads();
-    const long long tot = (long long)B.nrows * n;
-    for (long long q = blockIdx.y * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.y * TH) {
-        int r = (int)(q / n), l = (int)(q % n);
+    const int rpi = n < TH ? TH / n : 1;                 // rows per CTA pass
+    const int lr = (int)threadIdx.x / n, l0 = (int)threadIdx.x % n;
+    if (lr >= rpi) return;
+    for (int r = blockIdx.y * rpi + lr; r < B.nrows; r += gridDim.y * rpi)
+    for (int l = l0; l < n; l += (n < TH ? n : TH)) {
         const double* row = B.src + (long long)r * B.sld;
-        double v;
+        TY v;
         if (B.identity) {
-            v = row[pos[l]];
-            if (B.sym) v = 0.5 * (v + B.src[(long long)pos[l] * B.sld + r]);
+            v = (TY)row[pos[l]];
+            if (B.sym) v = (TY)0.5 * (v + (TY)B.src[(long long)pos[l] * B.sld + r]);
         } else {
-            v = 0.0;
+            v = 0;
             for (int a = 0; a < n; ++a) {
-                double s = row[pos[a]];
-                if (B.sym) s = 0.5 * (s + B.src[(long long)pos[a] * B.sld + r]);
-                v += s * Qs[a * n + l];
+                TY sv = (TY)row[pos[a]];
+                if (B.sym) sv = (TY)0.5 * (sv + (TY)B.src[(long long)pos[a] * B.sld + r]);
+                v += sv * Qs[a * n + l];
             }
         }
-        B.y[(long long)r * B.yld + pos[l]] = v;
+        Y[(long long)r * B.yld + pos[l]] = v;
     }
 }
 
 // Left multiplication Z[pos[l]][c] = sum_a Q[a][l] Y[pos[a]][c] and the
 // permuted store X[perm[pos[l]]][perm[c]] = Z (entries with perm < 0 dropped).
-template <class TD>
+template <class TY, class TD>
 __global__ void k_transform_left(const TBlock* __restrict__ blocks, const int* __restrict__ idx) {
     const TBlock B = blocks[blockIdx.x];
-    extern __shared__ double Qs[];
+    extern __shared__ __align__(16) unsigned char qraw[];
+    TY* Qs = reinterpret_cast<TY*>(qraw);
     const int n = B.n;
     const int* pos = idx + B.pos_off;
     const int* perm = idx + B.perm_off;
+    const TY* Y = (const TY*)B.y;
     if (!B.identity)
-        for (int q = threadIdx.x; q < n * n; q += TH) Qs[q] = B.Q[q];
+        for (int q = threadIdx.x; q < n * n; q += TH) Qs[q] = (TY)B.Q[q];
     __syncthreads();
     TD* X = (TD*)B.dst;
-    const long long tot = (long long)n * B.nrows;
-    for (long long q = blockIdx.y * (long long)TH + threadIdx.x; q < tot; q += (long long)gridDim.y * TH) {
-        int l = (int)(q / B.nrows), c = (int)(q % B.nrows);
+    for (int l = 0; l < n; ++l)
+    for (int c = blockIdx.y * TH + threadIdx.x; c < B.nrows; c += gridDim.y * TH) {
         int pr = perm[pos[l]], pc = perm[c];
         if (pr < 0 || pc < 0) continue;
-        double v;
-        if (B.identity) v = B.y[(long long)pos[l] * B.yld + c];
+        TY v;
+        if (B.identity) v = Y[(long long)pos[l] * B.yld + c];
         else {
-            v = 0.0;
-            for (int a = 0; a < n; ++a) v += Qs[a * n + l] * B.y[(long long)pos[a] * B.yld + c];
+            v = 0;
+            for (int a = 0; a < n; ++a) v += Qs[a * n + l] * Y[(long long)pos[a] * B.yld + c];
         }
         X[(long long)pr * B.dld + pc] = (TD)v;
     }
@@ -130,22 +137,17 @@ __global__ void k_extract(const ExtractJob* __restrict__ jobs, const int* __rest
     const int* rpi = idx + J.rpi_off;
     TP* MA = (TP*)J.MA;
     TP* MC = (TP*)J.MC;
-    const long long t0 = blockIdx.y * (long long)TH + threadIdx.x, step = (long long)gridDim.y * TH;
-    for (long long q = t0; q < (long long)np * np; q += step) {
-        int a = (int)(q / np), b = (int)(q % np);
-        atomicAdd(&SPi[(long long)rpi[a] * nPi + rpi[b]], (double)X[(long long)(nd + a) * J.xld + nd + b]);
+    for (int a = blockIdx.y; a < np; a += gridDim.y)
+        for (int b = threadIdx.x; b < np; b += TH)
+            atomicAdd(&SPi[(long long)rpi[a] * nPi + rpi[b]], (double)X[(long long)(nd + a) * J.xld + nd + b]);
+    for (int a = blockIdx.y; a < nB; a += gridDim.y) {
+        const TX* xr = X + (long long)(nB + a) * J.xld;
+        for (int b = threadIdx.x; b < nB; b += TH) MA[(long long)a * J.ald + b] = (TP)xr[nB + b];
+        for (int b = threadIdx.x; b < np; b += TH) MC[(long long)a * J.cld + b] = (TP)xr[nd + b];
     }
-    for (long long q = t0; q < (long long)nB * nB; q += step) {
-        int a = (int)(q / nB), b = (int)(q % nB);
-        MA[(long long)a * J.ald + b] = (TP)X[(long long)(nB + a) * J.xld + nB + b];
-    }
-    for (long long q = t0; q < (long long)np * nB; q += step) {
-        int a = (int)(q / nB), b = (int)(q % nB);
-        MA[(long long)(nB + a) * J.ald + b] = (TP)(-(double)X[(long long)(nd + a) * J.xld + nB + b]);
-    }
-    for (long long q = t0; q < (long long)nB * np; q += step) {
-        int a = (int)(q / np), b = (int)(q % np);
-        MC[(long long)a * J.cld + b] = (TP)X[(long long)(nB + a) * J.xld + nd + b];
+    for (int a = blockIdx.y; a < np; a += gridDim.y) {
+        const TX* xr = X + (long long)(nd + a) * J.xld + nB;
+        for (int b = threadIdx.x; b < nB; b += TH) MA[(long long)(nB + a) * J.ald + b] = (TP)(-xr[b]);
     }
 }
 
@@ -192,13 +194,13 @@ template int gather_perm_run<float>(const GatherJob*, int, const int*, int, cuda
 template <class TD>
 int transform_run(const TBlock* blocks, int count, const int* idx, int maxn, int ychunks, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
-    size_t smem = (size_t)maxn * maxn * sizeof(double);
+    size_t smem = (size_t)maxn * maxn * sizeof(TD);
     if (smem > 200 * 1024) return BDDC_EINVAL;
-    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_left<TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_transform_right<<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_right<TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_left<TD, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_transform_right<TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
     bddc_note_launches(1);
-    k_transform_left<TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
+    k_transform_left<TD, TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;

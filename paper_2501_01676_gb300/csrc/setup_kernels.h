@@ -25,7 +25,7 @@ struct TBlock {             // one entity block of one subdomain's change of bas
     const double* src;      // packed S^(i) (FP64)
     long long sld;
     int sym;                // use the symmetric part B^(i)
-    double* y;              // n_B x n_B scratch of the subdomain
+    void* y;                // n_B x n_B scratch of the subdomain (precision of the output)
     long long yld;
     int n;                  // entity size
     int pos_off;            // local interface positions of the entity
