@@ -147,12 +147,16 @@ def run_ours(args):
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
     torch.cuda.synchronize()
 
-    def step(precision, timed_events=None):
+    mlp = B.load_mlp_params()
+    learned = {} if mlp is None else {"learned_skip_p": 0.9, "mlp_params": mlp}
+
+    def step(precision, skip=True):
+        kw = learned if (precision == B.PREC_MIXED and skip) else {}
         with torch.cuda.stream(stream):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            s = B.Solver(p, stream=stream, arrays=arrays, precision=precision)
+            s = B.Solver(p, stream=stream, arrays=arrays, precision=precision, **kw)
             u, st = s.solve()
             e1.record(stream)
         stream.synchronize()
@@ -198,6 +202,14 @@ def run_ours(args):
             print(json.dumps({"part": "mixed", "ms": ms_step, "iters": stats["iters"],
                               "launches": int(launches)}), flush=True)
         return
+    # the same mixed solver without the learned skip (every edge runs its GEP)
+    noskip = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        ms, st_ns, _ = step(B.PREC_MIXED, skip=False)
+        noskip.append(ms)
+    ms_noskip = max_over_ranks(dist, sum(noskip) / len(noskip))
     # plain FP64 GPU path on the same GPU
     fp64_times, st64 = [], None
     flush_l2(flush)
@@ -217,7 +229,7 @@ def run_ours(args):
         flush_l2(flush)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s = B.Solver(p, host=True, stream=stream, arrays=pinned, precision=B.PREC_MIXED)
+        s = B.Solver(p, host=True, stream=stream, arrays=pinned, precision=B.PREC_MIXED, **learned)
         u_host, _ = s.solve(host=True)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -248,6 +260,8 @@ def run_ours(args):
         "iters": stats["iters"], "refine_steps": stats["refine_steps"], "relres": stats["relres"],
         "relres_global": stats["relres_global"], "pnumF": stats["pnumF"], "pnumE": stats["pnumE"],
         "n_pi": stats["n_pi"],
+        "edges_skipped": stats["edges_skipped"], "learned_skip": bool(learned),
+        "mixed_without_skip_ms": round(ms_noskip, 4), "mixed_without_skip_iters": st_ns["iters"],
         "plain_fp64_ms": round(ms64, 4), "plain_fp64_iters": st64["iters"],
         "speedup_vs_fp64": round(ms64 / ms_step, 3),
         "setup_breakdown_ms": {k: round(stats[k], 3) for k in ("setup_ms", "t_assemble_ms", "t_factor_ms",

@@ -94,7 +94,9 @@ typedef struct {
     double inner_rtol;     /* MIXED: inner GMRES tolerance per refinement step     */
     int max_refine;        /* MIXED: refinement step cap                           */
     double learned_skip_p; /* < 0: no learned skip; else skip an edge GEP when the
-                              loaded network gives P(no constraint) >= this        */
+                              network gives P(no constraint) >= this               */
+    const float* mlp_params; /* host, BDDC_MLP_PARAMS floats (layout below), copied at
+                                setup; NULL: no learned skip                        */
 } bddc_opts;
 
 typedef struct {
@@ -201,15 +203,47 @@ int bddc_get_entity(const bddc_ctx* ctx, int kind, int index, int* subs,
                     int* dofs, int* n, int* k, double* Q, double* lambda,
                     int* n_eig);
 
-/* ---- learned edge-GEP skip (BASELINE pattern: MLP, FP32) --------------- */
+/* ---- learned edge-GEP skip ---------------------------------------------
+ * Not in the paper.  A small FP32 network predicts from local coefficient
+ * features how many constraints the edge GEP (eq. equ-5-21 and the selection
+ * below it) will select on an edge; at setup, edges whose predicted
+ * probability of selecting none is >= learned_skip_p skip the GEP (no edge
+ * constraint; deluxe scaling is still computed); every other edge runs the
+ * full GEP.  Features of an edge (a line of n_E interior dofs along axis a;
+ * "touching" elements are the 4 (n_E + 1) elements holding the segment):
+ *   0-2 min / max / mean log10 nu over touching elements,
+ *   3   max - min over n(E) of the per-subdomain mean log10 nu,
+ *   4-6 mean |beta_a|, max |beta_a|, mean |beta| over the edge nodes,
+ *   7   edge length (n_E + 1) h_a, 8 (H/h)/10, 9 log10(h_a * f6 / (2 * 10^f2)).
+ * Network: 10 -> 64 -> 64 -> 64 (ReLU) -> 8 logits (class = min(k_E, 7)),
+ * loss = mean softmax cross-entropy.  Parameters are one FP32 array:
+ * W1[10][64], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64][8],
+ * b4[8] (row-major, input index first). */
 
 #define BDDC_MLP_FEATURES 10
 #define BDDC_MLP_HIDDEN   64
 #define BDDC_MLP_CLASSES  8
+#define BDDC_MLP_PARAMS   9544
 
-/* Edge features (n_edges x BDDC_MLP_FEATURES, FP32 host) and the edge GEP's
- * constraint counts (n_edges ints, -1 when the GEP was skipped). */
+/* Edge features of the context (n_edges x BDDC_MLP_FEATURES, FP32 host) and
+ * the edge GEP's constraint counts (n_edges ints, -1 where it was skipped),
+ * edges in the order of bddc_get_entity(kind 1). */
 int bddc_get_edge_features(const bddc_ctx* ctx, float* feats, int* counts);
+
+/* Class probabilities (rows x 8, device) of feature rows X (rows x 10,
+ * device) for the parameters params (host).  Synchronous on `stream`. */
+int bddc_mlp_forward(const float* params, const float* X_dev, int rows, float* probs_dev, void* stream);
+
+/* Mean cross-entropy over the rows (labels y_dev in 0..7) and its gradient
+ * (BDDC_MLP_PARAMS floats, host) by the library's backward kernels. */
+int bddc_mlp_loss_grad(const float* params, const float* X_dev, const int* y_dev, int rows,
+                       float* grad, float* loss, void* stream);
+
+/* Full-batch Adam training on the GPU (beta1 0.9, beta2 0.999, eps 1e-8):
+ * params (host) are read and overwritten; loss (host, epochs + 1 values,
+ * may be NULL) receives the loss before every step and after the last. */
+int bddc_mlp_train(float* params, const float* X_dev, const int* y_dev, int rows, int epochs,
+                   float lr, float* loss, void* stream);
 
 #ifdef __cplusplus
 }

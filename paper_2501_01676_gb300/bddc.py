@@ -39,7 +39,7 @@ class Opts(ct.Structure):
                 ("precision", ct.c_int), ("restart", ct.c_int), ("max_iter", ct.c_int),
                 ("rtol", ct.c_double), ("edge_gep", ct.c_int), ("face_gep", ct.c_int),
                 ("all_primal", ct.c_int), ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
-                ("learned_skip_p", ct.c_double)]
+                ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p)]
 
 
 class Stats(ct.Structure):
@@ -83,6 +83,10 @@ def lib():
     L.bddc_get_entity_count.argtypes = [vp, ct.c_int]
     L.bddc_get_entity.argtypes = [vp, ct.c_int, ct.c_int, ip, ip, ip, ip, dp, dp, ip]
     L.bddc_get_edge_features.argtypes = [vp, ct.POINTER(ct.c_float), ip]
+    fp = ct.POINTER(ct.c_float)
+    L.bddc_mlp_forward.argtypes = [fp, vp, ct.c_int, vp, vp]
+    L.bddc_mlp_loss_grad.argtypes = [fp, vp, vp, ct.c_int, fp, fp, vp]
+    L.bddc_mlp_train.argtypes = [fp, vp, vp, ct.c_int, ct.c_int, ct.c_float, fp, vp]
     L.bddc_kernel_timer.argtypes = [ct.c_int]
     L.bddc_kernel_timer_read.argtypes = [dp, ct.POINTER(ct.c_longlong), dp, dp]
     L.bddc_kernel_launches.argtypes = []
@@ -94,7 +98,58 @@ def lib():
 EXPORTED = ["bddc_default_opts", "bddc_setup", "bddc_apply", "bddc_schur_apply", "bddc_gmres_solve",
             "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_get_numbering", "bddc_get_schur",
             "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features", "bddc_kernel_launches",
-            "bddc_apply_static", "bddc_kernel_timer", "bddc_kernel_timer_read"]
+            "bddc_apply_static", "bddc_kernel_timer", "bddc_kernel_timer_read", "bddc_mlp_forward",
+            "bddc_mlp_loss_grad", "bddc_mlp_train"]
+
+MLP_FEATURES, MLP_CLASSES, MLP_PARAMS = 10, 8, 9544
+MLP_PARAMS_FILE = os.path.join(HERE, "edge_mlp_params.npy")
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_float))
+
+
+def _stream_ptr(stream):
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(st.cuda_stream)
+
+
+def mlp_forward(params, X, stream=None):
+    """Class probabilities of feature rows X (torch CUDA float32, rows x 10)."""
+    import torch
+    th = np.ascontiguousarray(params, dtype=np.float32)
+    X = X.contiguous()
+    P = torch.empty((X.shape[0], MLP_CLASSES), dtype=torch.float32, device="cuda")
+    check(lib().bddc_mlp_forward(_fptr(th), _ptr(X), X.shape[0], _ptr(P), _stream_ptr(stream)), "bddc_mlp_forward")
+    return P
+
+
+def mlp_loss_grad(params, X, y, stream=None):
+    th = np.ascontiguousarray(params, dtype=np.float32)
+    g = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    y = y.to(dtype=__import__("torch").int32).contiguous()
+    check(lib().bddc_mlp_loss_grad(_fptr(th), _ptr(X.contiguous()), _ptr(y), X.shape[0], _fptr(g), _fptr(loss),
+                                   _stream_ptr(stream)), "bddc_mlp_loss_grad")
+    return float(loss[0]), g
+
+
+def mlp_train(params, X, y, epochs, lr=3e-3, stream=None):
+    """Adam on the GPU; returns (new params, loss history of epochs + 1 values)."""
+    th = np.ascontiguousarray(params, dtype=np.float32).copy()
+    hist = np.zeros(epochs + 1, dtype=np.float32)
+    y = y.to(dtype=__import__("torch").int32).contiguous()
+    check(lib().bddc_mlp_train(_fptr(th), _ptr(X.contiguous()), _ptr(y), X.shape[0], epochs, lr, _fptr(hist),
+                               _stream_ptr(stream)), "bddc_mlp_train")
+    return th, hist
+
+
+def load_mlp_params():
+    """The trained parameters shipped with the package, or None."""
+    if not os.path.exists(MLP_PARAMS_FILE):
+        return None
+    return np.ascontiguousarray(np.load(MLP_PARAMS_FILE), dtype=np.float32)
 
 KT_NONE, KT_ENGINE_UPDATE, KT_ENGINE_PANEL, KT_GEMV, KT_FACE, KT_EDGE = range(6)
 
@@ -174,7 +229,12 @@ class Solver:
                          max_iter=problem.max_iter)
         if problem.theta_F is not None:
             o.theta_F = problem.theta_F
+        self._mlp = None
         for k, v in opts.items():
+            if k == "mlp_params":
+                self._mlp = None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+                o.mlp_params = None if v is None else self._mlp.ctypes.data
+                continue
             setattr(o, k, v)
         self.opts = o
         part = Partition()
@@ -289,6 +349,15 @@ class Solver:
         return u, st.as_dict()
 
     # ---- introspection -------------------------------------------------
+    def edge_features(self):
+        """(features (n_edges x 10) float32, constraint counts (-1: skipped))."""
+        ne = check(lib().bddc_get_entity_count(self.ctx, 1), "bddc_get_entity_count")
+        F = np.zeros((max(ne, 1), MLP_FEATURES), dtype=np.float32)
+        cnt = np.zeros(max(ne, 1), dtype=np.int32)
+        check(lib().bddc_get_edge_features(self.ctx, _fptr(F), cnt.ctypes.data_as(ct.POINTER(ct.c_int))),
+              "bddc_get_edge_features")
+        return F[:ne], cnt[:ne]
+
     def numbering(self):
         out = (ct.c_int * self.n_gamma)()
         check(lib().bddc_get_numbering(self.ctx, out), "bddc_get_numbering")

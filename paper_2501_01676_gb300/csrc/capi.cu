@@ -31,6 +31,7 @@
 #include "bddc_internal.h"
 #include "gep.h"
 #include "gmres.h"
+#include "mlp.h"
 #include "setup_kernels.h"
 
 int assemble_init(const HostMesh& hm, double tau, double c);
@@ -166,6 +167,9 @@ struct bddc_ctx {
     int* d_k = nullptr;
     int* d_neig = nullptr;
     std::vector<double*> BB;           // edge B~~_E (tests)
+    float* d_feat = nullptr;           // edge features (n_edges x BDDC_MLP_FEATURES)
+    float* mlp_params = nullptr;       // device copy of the network, when the learned skip is on
+    std::vector<char> edge_skipped;    // per edge (edge order)
     // apply operators
     void *MA = nullptr, *MC = nullptr;
     std::vector<long long> maoff, mcoff;
@@ -489,6 +493,72 @@ static int setup_impl(bddc_ctx* C) {
     t0 = std::chrono::steady_clock::now();
     const int edge_mode = C->o.all_primal ? 1 : (C->o.edge_gep == BDDC_EDGE_NEW ? 0 : 2);
     std::vector<int>& edges = hm.by_kind[1];
+    // edge features (always) and the learned skip decision
+    C->edge_skipped.assign(edges.size(), 0);
+    std::vector<char> active(nsd, 0);
+    if (!edges.empty()) {
+        std::vector<EdgeDesc> ed(edges.size());
+        for (size_t ei = 0; ei < edges.size(); ++ei) {
+            Entity& E = hm.ent[edges[ei]];
+            EdgeDesc& D = ed[ei];
+            auto coords = [&](int d, int* c) {
+                c[0] = d % (hm.E[0] - 1) + 1;
+                c[1] = (d / (hm.E[0] - 1)) % (hm.E[1] - 1) + 1;
+                c[2] = d / ((hm.E[0] - 1) * (hm.E[1] - 1)) + 1;
+            };
+            int a0[3], a1[3];
+            coords(E.dofs.front(), a0);
+            coords(E.dofs.back(), a1);
+            int axis = -1;
+            for (int d = 0; d < 3; ++d)
+                if (a0[d] != a1[d]) axis = d;
+            if (axis < 0) {   // one-dof edge: the direction in which all owners share a slab
+                for (int d = 0; d < 3 && axis < 0; ++d) {
+                    bool same = true;
+                    int c0 = -1;
+                    for (int sd : E.subs) {
+                        int sc = d == 0 ? sd % hm.nsub[0] : (d == 1 ? (sd / hm.nsub[0]) % hm.nsub[1] : sd / (hm.nsub[0] * hm.nsub[1]));
+                        if (c0 < 0) c0 = sc;
+                        else if (sc != c0) same = false;
+                    }
+                    if (same) axis = d;
+                }
+            }
+            if (axis < 0) return BDDC_EINVAL;
+            D.axis = axis;
+            D.lo = a0[axis];
+            D.hi = a1[axis];
+            const int f0 = axis == 0 ? 1 : 0, f1 = axis == 2 ? 1 : 2;
+            D.c0 = a0[f0];
+            D.c1 = a0[f1];
+            D.m = 0;
+            for (int q = 0; q < 4; ++q) {
+                D.subs[q] = q < (int)E.subs.size() ? E.subs[q] : -1;
+                if (q < (int)E.subs.size()) D.m = std::max(D.m, hm.sub[E.subs[q]].max_slab);
+            }
+        }
+        EdgeDesc* d_ed;
+        BDDC_TRY(C->upload(&d_ed, ed));
+        BDDC_TRY(C->alloc(&C->d_feat, edges.size() * BDDC_MLP_FEATURES));
+        BDDC_TRY(mlp_edge_features(d_ed, (int)edges.size(), C->nu, C->beta, C->bconst, d_sx, d_sy, d_sz, hm.nsub[0],
+                                   hm.nsub[1], hm.E[0], hm.E[1], hm.h, C->d_feat, st));
+        if (edge_mode == 0 && C->o.learned_skip_p >= 0.0 && C->mlp_params) {
+            float* probs = nullptr;
+            BDDC_TRY(C->alloc(&probs, edges.size() * BDDC_MLP_CLASSES));
+            BDDC_TRY(mlp_probs(C->mlp_params, C->d_feat, (int)edges.size(), probs, st));
+            std::vector<float> hp(edges.size() * BDDC_MLP_CLASSES);
+            BDDC_CUDA_TRY(cudaMemcpyAsync(hp.data(), probs, sizeof(float) * hp.size(), cudaMemcpyDeviceToHost, st));
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            for (size_t ei = 0; ei < edges.size(); ++ei)
+                C->edge_skipped[ei] = hp[ei * BDDC_MLP_CLASSES] >= (float)C->o.learned_skip_p;
+        }
+        for (size_t ei = 0; ei < edges.size(); ++ei)
+            if (!C->edge_skipped[ei])
+                for (int sd : hm.ent[edges[ei]].subs) active[sd] = 1;
+        int nsk = 0;
+        for (char c : C->edge_skipped) nsk += c;
+        C->stats.edges_skipped = nsk;
+    }
     if (!edges.empty()) {
         // per subdomain: transformed B onto [face duals | edges, vertices, face primals]
         std::vector<int> idxv;
@@ -521,6 +591,7 @@ static int setup_impl(bddc_ctx* C) {
             std::vector<int> perm_off(nsd);
             std::vector<EngItem<T>> items;
             for (int s = 0; s < nsd; ++s) {
+                if (!active[s]) continue;
                 SubInfo& S = hm.sub[s];
                 int nB = S.nB;
                 std::vector<int> perm(nB, -1);
@@ -555,6 +626,7 @@ static int setup_impl(bddc_ctx* C) {
             idxv.insert(idxv.end(), posl.begin(), posl.end());
             int maxn = 1;
             for (int s = 0; s < nsd; ++s) {
+                if (!active[s]) continue;
                 SubInfo& S = hm.sub[s];
                 for (size_t q = 0; q < S.ents.size(); ++q) {
                     int e = S.ents[q];
@@ -593,11 +665,12 @@ static int setup_impl(bddc_ctx* C) {
             }
             BDDC_TRY(C->alloc(&W64, w64tot));
             for (int s = 0; s < nsd; ++s)
-                cj.push_back(CopyJob{W + woff[s], r4(hm.sub[s].nB), nelim[s], nelim[s], nkeep[s], nkeep[s],
-                                     W64 + w64off[s], nkeep[s], 1.0});
+                if (active[s])
+                    cj.push_back(CopyJob{W + woff[s], r4(hm.sub[s].nB), nelim[s], nelim[s], nkeep[s], nkeep[s],
+                                         W64 + w64off[s], nkeep[s], 1.0});
             CopyJob* d_cj;
             BDDC_TRY(C->upload(&d_cj, cj));
-            BDDC_TRY((copy_blocks_run<T, double>(d_cj, nsd, 8, st)));
+            BDDC_TRY((copy_blocks_run<T, double>(d_cj, (int)cj.size(), 8, st)));
         }
         // per (edge, subdomain): Schur complement onto [E, H_k]
         std::vector<int> gidxv, hmv;
@@ -610,10 +683,12 @@ static int setup_impl(bddc_ctx* C) {
         if (edge_mode == 0) {
             long long etot = 0;
             for (size_t ei = 0; ei < edges.size(); ++ei)
-                for (int s : hm.ent[edges[ei]].subs) etot += (long long)nkeep[s] * nkeep[s];
+                if (!C->edge_skipped[ei])
+                    for (int s : hm.ent[edges[ei]].subs) etot += (long long)nkeep[s] * nkeep[s];
             BDDC_TRY(C->alloc(&EB, etot));
             etot = 0;
             for (size_t ei = 0; ei < edges.size(); ++ei) {
+                if (C->edge_skipped[ei]) continue;
                 int e = edges[ei];
                 Entity& E = hm.ent[e];
                 int nE = (int)E.dofs.size();
@@ -695,7 +770,7 @@ static int setup_impl(bddc_ctx* C) {
             J.n = n;
             J.m = m;
             J.nH = nH[ei];
-            J.mode = edge_mode;
+            J.mode = C->edge_skipped[ei] ? 2 : edge_mode;
             J.theta = E.theta;
             for (int a = 0; a < m; ++a) {
                 int s = E.subs[a];
@@ -703,7 +778,7 @@ static int setup_impl(bddc_ctx* C) {
                 J.ldS[a] = C->sld[s];
                 J.pos[a] = d_pos + pos_off[e][a];
                 J.DQ[a] = C->DQ[e][a];
-                if (edge_mode == 0) {
+                if (J.mode == 0) {
                     J.Bt[a] = EB + ito[ei][a];
                     J.ldBt[a] = itn[ei][a];
                     J.h[a] = hsz[ei][a];
@@ -1301,6 +1376,10 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     for (int d = 0; d < 3; ++d) C->bconst[d] = k->beta_const[d];
     C->c = k->c;
     C->nG = (int)hm.gamma.size();
+    if (C->o.mlp_params && C->o.learned_skip_p >= 0.0) {
+        std::vector<float> hp(C->o.mlp_params, C->o.mlp_params + BDDC_MLP_PARAMS);
+        BDDC_TRY(C->upload(&C->mlp_params, hp));
+    }
     BDDC_TRY(C->alloc(&C->err, 2));        // [0] error flags, [1] largest Jacobi sweep count
     BDDC_CUDA_TRY(cudaMemsetAsync(C->err, 0, 2 * sizeof(int), C->st));
     BDDC_TRY(pinned_scratch(&C->hst));
@@ -1547,10 +1626,15 @@ int bddc_kernel_timer_read(double* total_ms, long long* launches, double* flops,
 }
 
 int bddc_get_edge_features(const bddc_ctx* C, float* feats, int* counts) {
-    (void)feats;
-    (void)counts;
     if (!C) return BDDC_EINVAL;
-    return BDDC_EINVAL;
+    const std::vector<int>& edges = C->hm.by_kind[1];
+    BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    if (feats && !edges.empty())
+        BDDC_CUDA_TRY(cudaMemcpy(feats, C->d_feat, sizeof(float) * edges.size() * BDDC_MLP_FEATURES,
+                                 cudaMemcpyDeviceToHost));
+    if (counts)
+        for (size_t ei = 0; ei < edges.size(); ++ei) counts[ei] = C->edge_skipped[ei] ? -1 : C->kk[edges[ei]];
+    return BDDC_OK;
 }
 
 }  // extern "C"

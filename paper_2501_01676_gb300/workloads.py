@@ -205,4 +205,27 @@ def random_small(seed, nsub=(2, 2, 2), m=3, nu_range=(-3.0, 0.0), rotate=True):
     return Problem(f'random_s{seed}', slabs, nu, beta, rng.standard_normal(X.size))
 
 
+def rotating_checker(test=3, nsub=2, m=6, nu_hi=1.0, nu_lo=1e-7, c=1.0):
+    """The coefficient patterns of the paper's uniform-partition tests (Sect. 4)
+    moved to the unit cube: beta = (-2 pi (y-1/2), 2 pi (x-1/2), sin 2 pi (x-1/2)),
+    reaction c, nu_hi / nu_lo on two subdomain classes -- test 1: halves in x,
+    test 2: columns (x+y parity), test 3: checkerboard (x+y+z parity); f = 1 and
+    homogeneous Dirichlet conditions instead of the paper's boundary data."""
+    p = uniform(nsub, m, nu=1.0, beta=(0.0, 0.0, 0.0), f=1.0, name=f'rot_checker_t{test}')
+    ne, h, X, Y, Z = _grid(p.slabs)
+    p.beta_node = np.stack([-2 * math.pi * (Y - 0.5), 2 * math.pi * (X - 0.5), np.sin(2 * math.pi * (X - 0.5))], axis=1)
+    p.c = c
+    sub = _elem_subdomain(p.slabs)
+    ns = nsub if isinstance(nsub, (list, tuple)) else (nsub,) * 3
+    sx, sy, sz = sub % ns[0], (sub // ns[0]) % ns[1], sub // (ns[0] * ns[1])
+    if test == 1:
+        hi = sx < (ns[0] + 1) // 2
+    elif test == 2:
+        hi = (sx + sy) % 2 == 0
+    else:
+        hi = (sx + sy + sz) % 2 == 0
+    p.nu_elem = np.where(hi, nu_hi, nu_lo)
+    return p
+
+
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
