@@ -108,10 +108,10 @@ def element_matrices(mesh, nu_elem, beta_node, f_node, c=0.0, divb_node=None, ta
     Lphi = bg + c * N[None, :, :]
     ct = c - 0.5 * dq
     w = wq * detJ
-    diff = np.einsum('e,q,qjd,qid->eij', nu, w, G, G)
-    stab = np.einsum('e,q,eqj,eqi->eij', CK, w, Lphi, Lphi)
-    reac = np.einsum('q,eq,qj,qi->eij', w, ct, N, N)
-    skew = 0.5 * (np.einsum('q,eqj,qi->eij', w, bg, N) - np.einsum('q,eqi,qj->eij', w, bg, N))
+    diff = np.einsum('e,q,qjd,qid->eij', nu, w, G, G, optimize=True)
+    stab = np.einsum('e,q,eqj,eqi->eij', CK, w, Lphi, Lphi, optimize=True)
+    reac = np.einsum('q,eq,qj,qi->eij', w, ct, N, N, optimize=True)
+    skew = 0.5 * (np.einsum('q,eqj,qi->eij', w, bg, N, optimize=True) - np.einsum('q,eqi,qj->eij', w, bg, N, optimize=True))
     A = diff + stab + reac + skew
     F = np.einsum('q,eq,qi->ei', w, fq, N) + np.einsum('e,q,eq,eqi->ei', CK, w, fq, Lphi)
     return A, F, nodes

@@ -56,6 +56,16 @@ __device__ __forceinline__ float dot_vec<float>(const float4& a, const float* x)
 }
 
 template <class T>
+__device__ __forceinline__ typename Vec<T>::type vzero();
+template <>
+__device__ __forceinline__ double2 vzero<double>() { return make_double2(0.0, 0.0); }
+template <>
+__device__ __forceinline__ float4 vzero<float>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// Each warp streams two rows at a time and issues up to CH 128-bit loads per
+// lane for both rows before it multiplies, so every lane keeps 2*CH loads in
+// flight; the gathered input sits in shared memory.
+template <class T>
 __global__ void __launch_bounds__(GEMV_THREADS) k_gemv(const T* __restrict__ pool,
                                                        const GemvItem* __restrict__ items,
                                                        const int* __restrict__ idx,
@@ -71,22 +81,81 @@ __global__ void __launch_bounds__(GEMV_THREADS) k_gemv(const T* __restrict__ poo
     const int* oidx = idx + it.oidx_off;
     const T* M = pool + it.moff + it.col0;
     constexpr int VW = Vec<T>::W;
+    constexpr int CH = 4;
     typedef typename Vec<T>::type VT;
     const int ncols = it.ncols;
     const int nvec = ncols / VW;
+    const int rend = it.row0 + it.nrows;
     for (int c = 0; c < nrhs; ++c) {
         const double* inc = in + (long long)c * in_ld;
         double* outc = out + (long long)c * out_ld;
         for (int q = t; q < ncols; q += GEMV_THREADS) xs[q] = (T)inc[iidx[it.col0 + q]];
         __syncthreads();
-        for (int r = it.row0 + wid; r < it.row0 + it.nrows; r += GEMV_THREADS / 32) {
-            const T* row = M + (long long)r * it.ld;
-            const VT* rv = reinterpret_cast<const VT*>(row);
-            T acc = (T)0;
-            for (int v = lane; v < nvec; v += 32) acc += dot_vec<T>(__ldg(rv + v), xs + v * VW);
-            for (int q = nvec * VW + lane; q < ncols; q += 32) acc += row[q] * xs[q];
-            acc = warp_sum(acc);
-            if (lane == 0) atomicAdd(&outc[oidx[r]], (double)acc);
+        for (int r = it.row0 + 2 * wid; r < rend; r += 2 * (GEMV_THREADS / 32)) {
+            const bool two = r + 1 < rend;
+            const VT* rv0 = reinterpret_cast<const VT*>(M + (long long)r * it.ld);
+            const VT* rv1 = reinterpret_cast<const VT*>(M + (long long)(two ? r + 1 : r) * it.ld);
+            T acc0 = 0, acc1 = 0;
+            for (int base = 0; base < nvec; base += 32 * CH) {
+                VT a0[CH], a1[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const int v = base + lane + 32 * u;
+                    a0[u] = v < nvec ? __ldg(rv0 + v) : vzero<T>();
+                    a1[u] = (v < nvec && two) ? __ldg(rv1 + v) : vzero<T>();
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const int v = base + lane + 32 * u;
+                    if (v < nvec) {
+                        acc0 += dot_vec<T>(a0[u], xs + v * VW);
+                        acc1 += dot_vec<T>(a1[u], xs + v * VW);
+                    }
+                }
+            }
+            const T* row0 = M + (long long)r * it.ld;
+            const T* row1 = M + (long long)(two ? r + 1 : r) * it.ld;
+            for (int q = nvec * VW + lane; q < ncols; q += 32) {
+                acc0 += row0[q] * xs[q];
+                if (two) acc1 += row1[q] * xs[q];
+            }
+            acc0 = warp_sum(acc0);
+            acc1 = warp_sum(acc1);
+            if (lane == 0) {
+                atomicAdd(&outc[oidx[r]], (double)acc0);
+                if (two) atomicAdd(&outc[oidx[r + 1]], (double)acc1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Tall narrow operators stored transposed (cols x rows, row stride ld):
+// one thread per output row, the input of the item in shared memory.
+template <class T>
+__global__ void __launch_bounds__(GEMV_THREADS) k_gemv_t(const T* __restrict__ pool,
+                                                         const GemvItem* __restrict__ items,
+                                                         const int* __restrict__ idx,
+                                                         const double* __restrict__ in,
+                                                         double* __restrict__ out, int nrhs,
+                                                         int in_ld, int out_ld,
+                                                         const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const GemvItem it = items[blockIdx.x];
+    __shared__ T xs[GEMV_MAXCOLS];
+    const int t = threadIdx.x;
+    const int* iidx = idx + it.iidx_off;
+    const int* oidx = idx + it.oidx_off;
+    const T* Mt = pool + it.moff;
+    for (int c = 0; c < nrhs; ++c) {
+        const double* inc = in + (long long)c * in_ld;
+        double* outc = out + (long long)c * out_ld;
+        for (int q = t; q < it.ncols; q += GEMV_THREADS) xs[q] = (T)inc[iidx[it.col0 + q]];
+        __syncthreads();
+        for (int r = it.row0 + t; r < it.row0 + it.nrows; r += GEMV_THREADS) {
+            T acc = 0;
+            for (int q = 0; q < it.ncols; ++q) acc += Mt[(long long)(it.col0 + q) * it.ld + r] * xs[q];
+            atomicAdd(&outc[oidx[r]], (double)acc);
         }
         __syncthreads();
     }
@@ -108,6 +177,22 @@ int gemv_run(const T* pool, const GemvItem* items_dev, int nitems, const int* id
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
+
+template <class T>
+int gemv_t_run(const T* pool, const GemvItem* items_dev, int nitems, const int* idx, const double* in,
+               double* out, int nrhs, int in_ld, int out_ld, cudaStream_t st, const int* skip, double bytes) {
+    if (nitems <= 0) return BDDC_OK;
+    ktimer_begin(KT_GEMV, st);
+    k_gemv_t<T><<<nitems, GEMV_THREADS, 0, st>>>(pool, items_dev, idx, in, out, nrhs, in_ld, out_ld, skip);
+    bddc_note_launches(1);
+    ktimer_end(KT_GEMV, st, 0.0, bytes * nrhs);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+template int gemv_t_run<double>(const double*, const GemvItem*, int, const int*, const double*, double*, int, int,
+                                int, cudaStream_t, const int*, double);
+template int gemv_t_run<float>(const float*, const GemvItem*, int, const int*, const double*, double*, int, int, int,
+                               cudaStream_t, const int*, double);
 
 template int gemv_run<double>(const double*, const GemvItem*, int, const int*, const double*,
                               double*, int, int, int, int, cudaStream_t, const int*, double);

@@ -128,6 +128,11 @@ int gemv_run(const T* pool, const GemvItem* items_dev, int nitems, const int* id
              const double* in, double* out, int maxcols, int nrhs, int in_ld, int out_ld,
              cudaStream_t st, const int* skip_flag, double bytes = 0.0);
 
+// Same product for tall, narrow operators stored transposed (ld = stride of a column).
+template <class T>
+int gemv_t_run(const T* pool, const GemvItem* items_dev, int nitems, const int* idx, const double* in,
+               double* out, int nrhs, int in_ld, int out_ld, cudaStream_t st, const int* skip, double bytes);
+
 // Small-matrix kernels for the GEPs live in gep.cu; launchers:
 struct FaceJob;   // defined in gep.cu
 struct EdgeJob;

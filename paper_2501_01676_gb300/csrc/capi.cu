@@ -175,11 +175,12 @@ struct bddc_ctx {
     std::vector<long long> maoff, mcoff;
     std::vector<int> mald, mcld, np_s;
     double* SPiInv = nullptr;
+    float* SPiInv32 = nullptr;         // MIXED: FP32 copy of the FP64 coarse inverse
     int* gidx_pool = nullptr;
     GemvItem *itS = nullptr, *itM1 = nullptr, *itC = nullptr, *itM3 = nullptr;
     int nitS = 0, nitM1 = 0, nitC = 0, nitM3 = 0, maxcols = 0;
     // algorithmic bytes of one product: matrix stream + gathered inputs + scattered outputs
-    double bytesS = 0, bytesM1 = 0, bytesC = 0, bytesM3 = 0;
+    double bytesS = 0, bytesM1 = 0, bytesC = 0, bytesC32 = 0, bytesM3 = 0;
     // condense / recover
     void* tri = nullptr;
     int* tri_lists = nullptr;
@@ -921,9 +922,9 @@ static int setup_impl(bddc_ctx* C) {
         C->mald[s] = r4(nB);
         C->maoff[s] = matot;
         matot += (long long)(nB + C->np_s[s]) * C->mald[s];
-        C->mcld[s] = r4(std::max(C->np_s[s], 1));
+        C->mcld[s] = r4(nB);                       // D_i Phi_i stored transposed: np x nB
         C->mcoff[s] = mctot;
-        mctot += (long long)nB * C->mcld[s];
+        mctot += (long long)std::max(C->np_s[s], 1) * C->mcld[s];
     }
     T *MA = nullptr, *MC = nullptr;
     BDDC_TRY(C->alloc(&MA, matot));
@@ -956,14 +957,22 @@ static int setup_impl(bddc_ctx* C) {
         CopyJob* d_cj;
         BDDC_TRY(C->upload(&d_cj, cj));
         BDDC_TRY((copy_blocks_run<double, double>(d_cj, 1, 64, st)));
+        if (C->mixed) {
+            // the coarse problem is factorised in FP64; the mixed apply streams its inverse in FP32
+            BDDC_TRY(C->alloc(&C->SPiInv32, (size_t)std::max(nPi, 1) * ldc));
+            std::vector<CopyJob> cj2{CopyJob{C->SPiInv, ldc, 0, 0, nPi, nPi, C->SPiInv32, ldc, 1.0}};
+            CopyJob* d_cj2;
+            BDDC_TRY(C->upload(&d_cj2, cj2));
+            BDDC_TRY((copy_blocks_run<double, float>(d_cj2, 1, 64, st)));
+        }
     }
     // gemv work items
     std::vector<int> gi;
     std::vector<GemvItem> iS, iM1, iC, iM3;
     const int nG = C->nG;
-    auto split = [](std::vector<GemvItem>& v, long long moff, int rows, int cols, int ld, int io, int oo) {
-        const int RB = 32;
-        const int CB = 2048;           // staging width of the GEMV kernel (multiple of the vector width)
+    auto split = [](std::vector<GemvItem>& v, long long moff, int rows, int cols, int ld, int io, int oo,
+                    int RB = 32, int CB = 2048) {
+        // CB: column-slice width, <= the GEMV kernel's staging width and a multiple of its vector width
         for (int c0 = 0; c0 < cols; c0 += CB)
             for (int r0 = 0; r0 < rows; r0 += RB) {
                 GemvItem it;
@@ -981,6 +990,11 @@ static int setup_impl(bddc_ctx* C) {
             }
     };
     C->maxcols = std::max(nPi, 1);
+    // rows per work item: large enough that the gather of a subdomain's input is
+    // amortised over many streamed rows, small enough for ~4 items per SM
+    long long rows_tot = 0;
+    for (int s = 0; s < nsd; ++s) rows_tot += hm.sub[s].nB;
+    const int RBs = (int)std::max(32LL, std::min(128LL, (rows_tot / (4 * 152) + 31) / 32 * 32));
     for (int s = 0; s < nsd; ++s) {
         SubInfo& S = hm.sub[s];
         int nB = S.nB, nps = C->np_s[s];
@@ -992,9 +1006,9 @@ static int setup_impl(bddc_ctx* C) {
         int om1 = (int)gi.size();
         gi.insert(gi.end(), S.gidx.begin(), S.gidx.end());
         for (int q = 0; q < nps; ++q) gi.push_back(nG + idxv[rpi_off[s] + q]);
-        split(iS, C->soff[s], nB, nB, C->sld[s], og, og);
-        split(iM1, C->maoff[s], nB + nps, nB, C->mald[s], og, om1);
-        if (nps > 0) split(iM3, C->mcoff[s], nB, nps, C->mcld[s], orp, og);
+        split(iS, C->soff[s], nB, nB, C->sld[s], og, og, RBs);
+        split(iM1, C->maoff[s], nB + nps, nB, C->mald[s], og, om1, RBs);
+        if (nps > 0) split(iM3, C->mcoff[s], nB, nps, C->mcld[s], orp, og, 256);
         const double ts = sizeof(T), iv = 8.0 + 4.0;   // FP64 value + int32 index per gather/scatter
         C->bytesS += ts * nB * nB + iv * 2.0 * nB;
         C->bytesM1 += ts * (nB + nps) * nB + iv * (nB + nB + nps);
@@ -1005,8 +1019,9 @@ static int setup_impl(bddc_ctx* C) {
         for (int q = 0; q < nPi; ++q) gi.push_back(nG + q);
         int oi = (int)gi.size();
         for (int q = 0; q < nPi; ++q) gi.push_back(q);
-        if (nPi > 0) split(iC, 0, nPi, nPi, ldc, oc, oi);
+        if (nPi > 0) split(iC, 0, nPi, nPi, ldc, oc, oi, 32, 512);
         C->bytesC = 8.0 * nPi * nPi + 24.0 * nPi;
+        C->bytesC32 = 4.0 * nPi * nPi + 24.0 * nPi;
     }
     BDDC_TRY(C->upload(&C->gidx_pool, gi));
     BDDC_TRY(C->upload(&C->itS, iS));
@@ -1058,10 +1073,14 @@ static int op_M(bddc_ctx* C, const double* x, const int* skip) {
                          C->bytesM1));
     if (C->nPi > 0) {
         BDDC_CUDA_TRY(cudaMemsetAsync(C->uPi, 0, sizeof(double) * C->nPi, C->st));
-        BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, C->zc, C->uPi, C->maxcols, 1, 0, 0, C->st,
-                                  skip, C->bytesC));
-        BDDC_TRY(gemv_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, C->uPi, C->zc, C->maxcols, 1, 0, 0, C->st,
-                             skip, C->bytesM3));
+        if (C->mixed)
+            BDDC_TRY(gemv_run<float>(C->SPiInv32, C->itC, C->nitC, C->gidx_pool, C->zc, C->uPi, C->maxcols, 1, 0, 0,
+                                     C->st, skip, C->bytesC32));
+        else
+            BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, C->zc, C->uPi, C->maxcols, 1, 0, 0,
+                                      C->st, skip, C->bytesC));
+        BDDC_TRY(gemv_t_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, C->uPi, C->zc, 1, 0, 0, C->st, skip,
+                               C->bytesM3));
     }
     return BDDC_OK;
 }
@@ -1254,8 +1273,13 @@ static int op_M_into(bddc_ctx* C, const double* x, double* zc, double* upi) {
     BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, zc, C->maxcols, 1, 0, 0, C->st, nullptr));
     if (C->nPi > 0) {
         BDDC_CUDA_TRY(cudaMemsetAsync(upi, 0, sizeof(double) * C->nPi, C->st));
-        BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0, C->st, nullptr));
-        BDDC_TRY(gemv_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, upi, zc, C->maxcols, 1, 0, 0, C->st, nullptr));
+        if (C->mixed)
+            BDDC_TRY(gemv_run<float>(C->SPiInv32, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0, C->st,
+                                     nullptr));
+        else
+            BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0, C->st,
+                                      nullptr));
+        BDDC_TRY(gemv_t_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, upi, zc, 1, 0, 0, C->st, nullptr, 0.0));
     }
     return BDDC_OK;
 }

@@ -143,7 +143,7 @@ __global__ void k_extract(const ExtractJob* __restrict__ jobs, const int* __rest
     for (int a = blockIdx.y; a < nB; a += gridDim.y) {
         const TX* xr = X + (long long)(nB + a) * J.xld;
         for (int b = threadIdx.x; b < nB; b += TH) MA[(long long)a * J.ald + b] = (TP)xr[nB + b];
-        for (int b = threadIdx.x; b < np; b += TH) MC[(long long)a * J.cld + b] = (TP)xr[nd + b];
+        for (int b = threadIdx.x; b < np; b += TH) MC[(long long)b * J.cld + a] = (TP)xr[nd + b];
     }
     for (int a = blockIdx.y; a < np; a += gridDim.y) {
         const TX* xr = X + (long long)(nd + a) * J.xld + nB;

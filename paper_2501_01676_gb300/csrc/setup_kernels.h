@@ -53,7 +53,7 @@ struct ExtractJob {
     int rpi_off;            // global primal index of each local primal coordinate
     void* MA;               // [P ; Psi^T D^T]  ((nB + np) x nB)
     long long ald;
-    void* MC;               // D Phi (nB x np)
+    void* MC;               // D Phi stored transposed (np x nB)
     long long cld;
 };
 
