@@ -97,6 +97,9 @@ typedef struct {
                               network gives P(no constraint) >= this               */
     const float* mlp_params; /* host, BDDC_MLP_PARAMS floats (layout below), copied at
                                 setup; NULL: no learned skip                        */
+    int tensor_cores;      /* MIXED: 1 = trailing updates of the FP32 eliminations on
+                              the tensor cores (tcgen05, split TF32), 0 = FP32 CUDA
+                              cores; ignored by the FP64 path                       */
 } bddc_opts;
 
 typedef struct {
@@ -119,7 +122,8 @@ typedef struct bddc_ctx bddc_ctx;
 
 /* Fill `o` with the defaults of Sect. 4: Theta_E = 10, Theta_F = 1 + ln(H/h),
  * tau = 0.7, FP64, no restart, 300 iterations, rtol 1e-8, new edge GEP,
- * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip. */
+ * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip, CUDA-core
+ * trailing updates (tensor_cores 0). */
 void bddc_default_opts(bddc_opts* o);
 
 /* Setup (call stack: assembly, batched Dirichlet factorisation + Schur
@@ -172,6 +176,14 @@ const char* bddc_strerror(int code);
 /* Process-wide number of kernels the library has launched so far (a CUDA
  * graph replay counts its kernel nodes).  Host-only, never fails. */
 unsigned long long bddc_kernel_launches(void);
+
+/* Self-test of the tensor-core trailing update (no counterpart in the paper):
+ * C (128 x 128, row-major, host) -= A (128 x 32, row-major) * B (32 x 128,
+ * row-major) restricted to rows < nr, columns < nc and the first K (<= 32)
+ * columns of A / rows of B, computed by one CTA with tcgen05.mma (split TF32:
+ * hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory).  Host buffers;
+ * BDDC_ETIMEOUT if the bounded wait for the MMAs gave up. */
+int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, int K);
 
 /* Kernel timer for roofline reporting: after bddc_kernel_timer(kind) every
  * launch of that kernel class (1 engine trailing update, 2 engine panel,

@@ -39,7 +39,7 @@ class Opts(ct.Structure):
                 ("precision", ct.c_int), ("restart", ct.c_int), ("max_iter", ct.c_int),
                 ("rtol", ct.c_double), ("edge_gep", ct.c_int), ("face_gep", ct.c_int),
                 ("all_primal", ct.c_int), ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
-                ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p)]
+                ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p), ("tensor_cores", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -87,6 +87,7 @@ def lib():
     L.bddc_mlp_forward.argtypes = [fp, vp, ct.c_int, vp, vp]
     L.bddc_mlp_loss_grad.argtypes = [fp, vp, vp, ct.c_int, fp, fp, vp]
     L.bddc_mlp_train.argtypes = [fp, vp, vp, ct.c_int, ct.c_int, ct.c_float, fp, vp]
+    L.bddc_tc_selftest.argtypes = [fp, fp, fp, ct.c_int, ct.c_int, ct.c_int]
     L.bddc_kernel_timer.argtypes = [ct.c_int]
     L.bddc_kernel_timer_read.argtypes = [dp, ct.POINTER(ct.c_longlong), dp, dp]
     L.bddc_kernel_launches.argtypes = []
@@ -99,7 +100,16 @@ EXPORTED = ["bddc_default_opts", "bddc_setup", "bddc_apply", "bddc_schur_apply",
             "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_get_numbering", "bddc_get_schur",
             "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features", "bddc_kernel_launches",
             "bddc_apply_static", "bddc_kernel_timer", "bddc_kernel_timer_read", "bddc_mlp_forward",
-            "bddc_mlp_loss_grad", "bddc_mlp_train"]
+            "bddc_mlp_loss_grad", "bddc_mlp_train", "bddc_tc_selftest"]
+
+
+def tc_selftest(A, B, C, nr=128, nc=128, K=32):
+    """C - A @ B on one 128 x 128 tile through the tensor-core path (host arrays)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    Cc = np.ascontiguousarray(C, dtype=np.float32).copy()
+    check(lib().bddc_tc_selftest(_fptr(A), _fptr(B), _fptr(Cc), nr, nc, K), "bddc_tc_selftest")
+    return Cc
 
 MLP_FEATURES, MLP_CLASSES, MLP_PARAMS = 10, 8, 9544
 MLP_PARAMS_FILE = os.path.join(HERE, "edge_mlp_params.npy")

@@ -220,16 +220,28 @@ struct TriItem {
     long long yoff;    // offset of the stored y_i (nI entries)
 };
 
+// The 32 x 32 diagonal block of a substitution step is staged in shared memory
+// (one coalesced load) before the warp walks its dependent chain.
+template <class T>
+__device__ __forceinline__ void load_diag(const T* A, int ld, int b0, int bw, T (*D)[33]) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int r = wid; r < bw; r += TRI_THREADS / 32)
+        if (lane < bw) D[r][lane] = A[(long long)(b0 + r) * ld + b0 + lane];
+    __syncthreads();
+}
+
 template <class T>
 __device__ void fwd_unit_lower(const T* A, int ld, int nI, T* y) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    __shared__ T D[32][33];
     for (int b0 = 0; b0 < nI; b0 += 32) {
         const int bw = min(32, nI - b0);
+        load_diag(A, ld, b0, bw, D);
         if (wid == 0) {
             T v = lane < bw ? y[b0 + lane] : (T)0;
             for (int k = 0; k < bw; ++k) {
                 T vk = __shfl_sync(0xffffffffu, v, k);
-                if (lane > k && lane < bw) v -= A[(long long)(b0 + lane) * ld + b0 + k] * vk;
+                if (lane > k && lane < bw) v -= D[lane][k] * vk;
             }
             if (lane < bw) y[b0 + lane] = v;
         }
@@ -246,15 +258,17 @@ __device__ void fwd_unit_lower(const T* A, int ld, int nI, T* y) {
 template <class T>
 __device__ void bwd_upper(const T* A, int ld, int nI, T* y) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    __shared__ T D[32][33];
     for (int b1 = nI; b1 > 0; b1 -= 32) {
         const int b0 = max(0, b1 - 32);
         const int bw = b1 - b0;
+        load_diag(A, ld, b0, bw, D);
         if (wid == 0) {
             T v = lane < bw ? y[b0 + lane] : (T)0;
             for (int k = bw - 1; k >= 0; --k) {
-                if (lane == k) v /= A[(long long)(b0 + k) * ld + b0 + k];
+                if (lane == k) v /= D[k][k];
                 T vk = __shfl_sync(0xffffffffu, v, k);
-                if (lane < k) v -= A[(long long)(b0 + lane) * ld + b0 + k] * vk;
+                if (lane < k) v -= D[lane][k] * vk;
             }
             if (lane < bw) y[b0 + lane] = v;
         }

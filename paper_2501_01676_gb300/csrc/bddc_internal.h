@@ -42,6 +42,7 @@ enum {
     ERR_PIVOT = 1,        // zero / non-finite pivot in the batched LU
     ERR_JACOBI = 2,       // Jacobi eigen sweep cap reached
     ERR_SIZE = 4,         // a size exceeded a compiled limit
+    ERR_TIMEOUT_TC = 8,   // a bounded wait for tensor-core work gave up
 };
 
 // ---------------------------------------------------------------------------
@@ -109,7 +110,13 @@ struct EngItem {
 
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* diag_scratch,
-               int* err, cudaStream_t st, const int* host_n = nullptr, const int* host_k = nullptr);
+               int* err, cudaStream_t st, const int* host_n = nullptr, const int* host_k = nullptr,
+               bool tensor_cores = false);
+
+// Tensor-core (tcgen05, split TF32) trailing update of one FP32 engine panel.
+int tc_update_run(const EngItem<float>* items_dev, int count, int maxn, int p, const float* dscr, int* err,
+                  cudaStream_t st);
+int tc_selftest_run(const float* A, const float* B, float* C, int nr, int nc, int K, int* err, cudaStream_t st);
 
 // Generic batched gather -> GEMV -> scatter-add:  out[oidx[r]] += sum_c M[r][c] * in[iidx[c]]
 struct GemvItem {

@@ -224,7 +224,8 @@ static int run_engine(bddc_ctx* C, const std::vector<EngItem<T>>& items) {
         hn[i] = items[i].n;
         hk[i] = items[i].k;
     }
-    return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st, hn.data(), hk.data());
+    return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st, hn.data(), hk.data(),
+                         C->o.tensor_cores != 0);
 }
 
 template <class T>
@@ -1323,6 +1324,8 @@ void bddc_default_opts(bddc_opts* o) {
     o->inner_rtol = 1e-6;
     o->max_refine = 8;
     o->learned_skip_p = -1.0;
+    o->mlp_params = nullptr;
+    o->tensor_cores = 0;
 }
 
 const char* bddc_strerror(int code) {
@@ -1620,6 +1623,42 @@ int bddc_get_entity(const bddc_ctx* C, int kind, int index, int* subs, int* dofs
 }
 
 unsigned long long bddc_kernel_launches(void) { return g_launches.load(); }
+
+int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, int K) {
+    if (!A || !B || !C || nr < 1 || nc < 1 || nr > 128 || nc > 128 || K < 1 || K > 32) return BDDC_EINVAL;
+    cudaStream_t st;
+    BDDC_CUDA_TRY(cudaStreamCreate(&st));
+    float *dA = nullptr, *dB = nullptr, *dC = nullptr;
+    int* derr = nullptr;
+    int rc = BDDC_OK;
+    int herr = 0;
+    if (cudaMallocAsync((void**)&dA, 128 * 32 * sizeof(float), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&dB, 32 * 128 * sizeof(float), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&dC, 128 * 128 * sizeof(float), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&derr, sizeof(int), st) != cudaSuccess) {
+        rc = BDDC_ENOMEM;
+    } else {
+        cudaMemcpyAsync(dA, A, 128 * 32 * sizeof(float), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(dB, B, 32 * 128 * sizeof(float), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(dC, C, 128 * 128 * sizeof(float), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(derr, 0, sizeof(int), st);
+        rc = tc_selftest_run(dA, dB, dC, nr, nc, K, derr, st);
+        cudaMemcpyAsync(C, dC, 128 * 128 * sizeof(float), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+    }
+    cudaFreeAsync(dA, st);
+    cudaFreeAsync(dB, st);
+    cudaFreeAsync(dC, st);
+    cudaFreeAsync(derr, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess) {
+        bddc_set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
+        return BDDC_ECUDA;
+    }
+    if (rc == BDDC_OK && herr) rc = BDDC_ETIMEOUT;
+    return rc;
+}
 
 int bddc_kernel_timer(int kind) {
     if (kind < KT_NONE || kind > KT_EDGE) return BDDC_EINVAL;

@@ -197,8 +197,31 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
 }  // namespace
 
 template <class T>
+static int launch_update(const EngItem<T>* items_dev, int count, int maxn, int p, T* dscr, int* err, cudaStream_t st,
+                         bool tc);
+template <>
+int launch_update<double>(const EngItem<double>* items_dev, int count, int maxn, int p, double* dscr, int* err,
+                          cudaStream_t st, bool tc) {
+    (void)tc;
+    (void)err;
+    const int nt = (maxn - p + TILE - 1) / TILE;
+    k_update<double, 32><<<dim3(count, 1 + nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, dscr);
+    bddc_note_launches(1);
+    return BDDC_OK;
+}
+template <>
+int launch_update<float>(const EngItem<float>* items_dev, int count, int maxn, int p, float* dscr, int* err,
+                         cudaStream_t st, bool tc) {
+    if (tc) return tc_update_run(items_dev, count, maxn, p, dscr, err, st);
+    const int nt = (maxn - p + TILE - 1) / TILE;
+    k_update<float, 32><<<dim3(count, 1 + nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, dscr);
+    bddc_note_launches(1);
+    return BDDC_OK;
+}
+
+template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* dscr, int* err,
-               cudaStream_t st, const int* hn, const int* hk) {
+               cudaStream_t st, const int* hn, const int* hk, bool tc) {
     constexpr int NB = 32;
     if (count <= 0 || maxk <= 0) return BDDC_OK;
     for (int p = 0; p < maxk; p += NB) {
@@ -220,15 +243,15 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         bddc_note_launches(1);
         ktimer_end(KT_ENGINE_PANEL, st, fp, 0.0);
         ktimer_begin(KT_ENGINE_UPDATE, st);
-        k_update<T, NB><<<dim3(count, 1 + nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, dscr);
-        bddc_note_launches(1);
+        BDDC_TRY(launch_update<T>(items_dev, count, maxn, p, dscr, err, st, tc));
         ktimer_end(KT_ENGINE_UPDATE, st, fu, bu);
+        (void)nt;
     }
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
 template int engine_run<double>(const EngItem<double>*, int, int, int, double*, int*, cudaStream_t,
-                                const int*, const int*);
+                                const int*, const int*, bool);
 template int engine_run<float>(const EngItem<float>*, int, int, int, float*, int*, cudaStream_t,
-                               const int*, const int*);
+                               const int*, const int*, bool);

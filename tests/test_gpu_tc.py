@@ -1,0 +1,45 @@
+"""The tcgen05 (split TF32) trailing update against FP64 products.
+
+Split TF32 represents each FP32 operand as hi + lo (both TF32) and drops the
+lo*lo term: the error per product is about 2^-21 relative, so K = 32 terms stay
+within 1e-5 of the largest partial sum; the test allows 1e-4.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def B():
+    from paper_2501_01676_gb300 import bddc
+    return bddc
+
+
+@pytest.mark.parametrize("nr,nc,K", [(128, 128, 32), (97, 45, 32), (128, 128, 17), (5, 128, 3)])
+def test_tile_against_fp64(nr, nc, K):
+    rng = np.random.default_rng(nr * 1000 + nc + K)
+    A = rng.standard_normal((128, 32)).astype(np.float32)
+    Bm = rng.standard_normal((32, 128)).astype(np.float32)
+    C = rng.standard_normal((128, 128)).astype(np.float32)
+    out = B().tc_selftest(A, Bm, C, nr, nc, K)
+    ref = C.astype(np.float64).copy()
+    ref[:nr, :nc] -= A[:nr, :K].astype(np.float64) @ Bm[:K, :nc].astype(np.float64)
+    scale = np.abs(A[:nr, :K]).max() * np.abs(Bm[:K, :nc]).max() * K
+    assert np.abs(out - ref).max() <= 1e-4 * scale
+    # entries outside the nr x nc block are untouched
+    assert np.array_equal(out[nr:, :], C[nr:, :]) and np.array_equal(out[:, nc:], C[:, nc:])
+
+
+def test_engine_tensor_cores_match_cuda_cores():
+    """Schur complements of the mixed path: tcgen05 trailing updates vs FP32 CUDA cores."""
+    from paper_2501_01676_gb300 import workloads as W
+    p = W.random_small(2, (3, 3, 3), 4, (-2, 1))
+    a = B().Solver(p, precision=1, tensor_cores=1)
+    b = B().Solver(p, precision=1, tensor_cores=0)
+    for sd in range(27):
+        Sa, Sb = a.schur(sd), b.schur(sd)
+        assert np.abs(Sa - Sb).max() <= 2e-5 * np.abs(Sb).max()
+    ua, sa = a.solve()
+    ub, sb = b.solve()
+    assert sa["converged"] and sb["converged"]
+    assert (ua - ub).abs().max().item() <= 1e-7 * ub.abs().max().item()
