@@ -116,6 +116,9 @@ typedef struct {
     double setup_ms, solve_ms;
     double t_assemble_ms, t_factor_ms, t_face_ms, t_edge_ms, t_coarse_ms;
     int jacobi_sweeps_max;   /* most sweeps any GEP eigen-decomposition needed   */
+    double t_mesh_ms;        /* host numbering / entity lists / coefficient staging */
+    double t_basis_ms;       /* change of basis + extended elimination (part of
+                                t_coarse_ms)                                      */
 } bddc_stats;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -187,7 +190,8 @@ int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, i
 
 /* Kernel timer for roofline reporting: after bddc_kernel_timer(kind) every
  * launch of that kernel class (1 engine trailing update, 2 engine panel,
- * 3 apply GEMV, 4 face GEP, 5 edge GEP; 0 off) is bracketed by CUDA events on
+ * 3 apply GEMV, 4 face GEP, 5 edge GEP, 6 element assembly, 7 change of basis,
+ * 8 interior condense / recover solves; 0 off) is bracketed by CUDA events on
  * its stream (launches captured into graphs are not).  _read synchronises on
  * the recorded events and returns their summed duration, the number of
  * launches and, where the library knows them, the algorithmic flops and

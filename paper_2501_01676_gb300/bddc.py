@@ -49,7 +49,7 @@ class Stats(ct.Structure):
                 ("nsub", ct.c_int), ("edges_skipped", ct.c_int), ("setup_ms", ct.c_double),
                 ("solve_ms", ct.c_double), ("t_assemble_ms", ct.c_double), ("t_factor_ms", ct.c_double),
                 ("t_face_ms", ct.c_double), ("t_edge_ms", ct.c_double), ("t_coarse_ms", ct.c_double),
-                ("jacobi_sweeps_max", ct.c_int)]
+                ("jacobi_sweeps_max", ct.c_int), ("t_mesh_ms", ct.c_double), ("t_basis_ms", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -161,7 +161,7 @@ def load_mlp_params():
         return None
     return np.ascontiguousarray(np.load(MLP_PARAMS_FILE), dtype=np.float32)
 
-KT_NONE, KT_ENGINE_UPDATE, KT_ENGINE_PANEL, KT_GEMV, KT_FACE, KT_EDGE = range(6)
+KT_NONE, KT_ENGINE_UPDATE, KT_ENGINE_PANEL, KT_GEMV, KT_FACE, KT_EDGE, KT_ASSEMBLE, KT_TRANSFORM, KT_TRI = range(9)
 
 
 def kernel_timer(kind):

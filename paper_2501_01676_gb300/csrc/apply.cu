@@ -204,8 +204,10 @@ template int gemv_run<float>(const float*, const GemvItem*, int, const int*, con
 // A^(i) = [[L_II, 0], [L_BI, I]] [[U_II, U_IB], [0, S^(i)]]   (Sect. 3):
 //   y_i = L_II^{-1} f_I,  g -= R_i^T L_BI y_i          (g^(i) = f_B - A_BI A_II^{-1} f_I)
 //   u_I = U_II^{-1} (y_i - U_IB u_B)                   (u_I = A_II^{-1}(f_I - A_IB u_B))
-// One CTA per subdomain; blocked substitution: one warp solves each 32 x 32
-// diagonal block with shuffles, all warps update the remaining rows.
+// One CTA per subdomain; blocked left-looking substitution: all warps reduce the
+// solved part into a 32-row block (several rows per warp, so that many factor
+// loads are in flight), one warp solves the 32 x 32 diagonal block with
+// shuffles.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -227,9 +229,30 @@ __device__ __forceinline__ void load_diag(const T* A, int ld, int b0, int bw, T 
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int r = wid; r < bw; r += TRI_THREADS / 32)
         if (lane < bw) D[r][lane] = A[(long long)(b0 + r) * ld + b0 + lane];
-    __syncthreads();
 }
 
+// s[j] = sum_{c0 <= c < c1} A[r0 + j][c] x[c] for the R rows r0 + j < rlim, by one
+// warp (lanes across columns, the R rows' loads in flight together); the sums
+// are returned in every lane.
+template <class T, int R>
+__device__ __forceinline__ void warp_rows_dot(const T* __restrict__ A, long long ld, int r0, int rlim, int c0,
+                                              int c1, const T* x, T (&s)[R]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < R; ++j) s[j] = (T)0;
+    for (int c = c0 + lane; c < c1; c += 32) {
+        const T xv = x[c];
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if (r0 + j < rlim) s[j] += A[(long long)(r0 + j) * ld + c] * xv;
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) s[j] = warp_sum(s[j]);
+}
+
+// y <- L^{-1} y, L unit lower (the strictly lower part of A's leading nI x nI
+// block).  Left-looking: the 32 rows of a block first subtract the solved
+// columns (four rows per warp, all eight warps), then warp 0 finishes the block.
 template <class T>
 __device__ void fwd_unit_lower(const T* A, int ld, int nI, T* y) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -237,6 +260,14 @@ __device__ void fwd_unit_lower(const T* A, int ld, int nI, T* y) {
     for (int b0 = 0; b0 < nI; b0 += 32) {
         const int bw = min(32, nI - b0);
         load_diag(A, ld, b0, bw, D);
+        if (b0 > 0) {
+            T s[4];
+            warp_rows_dot<T, 4>(A, ld, b0 + 4 * wid, b0 + bw, 0, b0, y, s);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (lane == 0 && 4 * wid + j < bw) y[b0 + 4 * wid + j] -= s[j];
+        }
+        __syncthreads();
         if (wid == 0) {
             T v = lane < bw ? y[b0 + lane] : (T)0;
             for (int k = 0; k < bw; ++k) {
@@ -246,15 +277,11 @@ __device__ void fwd_unit_lower(const T* A, int ld, int nI, T* y) {
             if (lane < bw) y[b0 + lane] = v;
         }
         __syncthreads();
-        for (int r = b0 + bw + wid; r < nI; r += TRI_THREADS / 32) {
-            T s = lane < bw ? A[(long long)r * ld + b0 + lane] * y[b0 + lane] : (T)0;
-            s = warp_sum(s);
-            if (lane == 0) y[r] -= s;
-        }
-        __syncthreads();
     }
 }
 
+// y <- U^{-1} y, U the upper part of A's leading nI x nI block; left-looking
+// from the last block.
 template <class T>
 __device__ void bwd_upper(const T* A, int ld, int nI, T* y) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -263,6 +290,14 @@ __device__ void bwd_upper(const T* A, int ld, int nI, T* y) {
         const int b0 = max(0, b1 - 32);
         const int bw = b1 - b0;
         load_diag(A, ld, b0, bw, D);
+        if (b1 < nI) {
+            T s[4];
+            warp_rows_dot<T, 4>(A, ld, b0 + 4 * wid, b1, b1, nI, y, s);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (lane == 0 && 4 * wid + j < bw) y[b0 + 4 * wid + j] -= s[j];
+        }
+        __syncthreads();
         if (wid == 0) {
             T v = lane < bw ? y[b0 + lane] : (T)0;
             for (int k = bw - 1; k >= 0; --k) {
@@ -271,12 +306,6 @@ __device__ void bwd_upper(const T* A, int ld, int nI, T* y) {
                 if (lane < k) v -= D[lane][k] * vk;
             }
             if (lane < bw) y[b0 + lane] = v;
-        }
-        __syncthreads();
-        for (int r = wid; r < b0; r += TRI_THREADS / 32) {
-            T s = lane < bw ? A[(long long)r * ld + b0 + lane] * y[b0 + lane] : (T)0;
-            s = warp_sum(s);
-            if (lane == 0) y[r] -= s;
         }
         __syncthreads();
     }
@@ -297,17 +326,18 @@ __global__ void __launch_bounds__(TRI_THREADS) k_condense(const T* __restrict__ 
     const T* A = pool + it.aoff;
     const int* dofs = lists + it.dof_off;
     const int* gidx = lists + it.gidx_off;
+    const int nB = it.n - it.nI;
     for (int c = 0; c < nrhs; ++c) {
         for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = (T)F[c * ldF + dofs[q]];
         __syncthreads();
         fwd_unit_lower<T>(A, it.ld, it.nI, y);
-        const int nB = it.n - it.nI;
-        for (int b = wid; b < nB; b += TRI_THREADS / 32) {
-            const T* row = A + (long long)(it.nI + b) * it.ld;
-            T s = 0;
-            for (int q = lane; q < it.nI; q += 32) s += row[q] * y[q];
-            s = warp_sum(s);
-            if (lane == 0) atomicAdd(&g[c * ldG + gidx[b]], -(double)s);
+        // g -= L_BI y: eight rows per warp at a time
+        for (int rb = 8 * wid; rb < nB; rb += 8 * (TRI_THREADS / 32)) {
+            T s[8];
+            warp_rows_dot<T, 8>(A + (long long)it.nI * it.ld, it.ld, rb, nB, 0, it.nI, y, s);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (lane == j && rb + j < nB) atomicAdd(&g[c * ldG + gidx[rb + j]], -(double)s[j]);
         }
         for (int q = t; q < it.nI; q += TRI_THREADS) ystore[c * ldY + it.yoff + q] = (double)y[q];
         __syncthreads();
@@ -335,12 +365,13 @@ __global__ void __launch_bounds__(TRI_THREADS) k_recover(const T* __restrict__ p
         for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = (T)ystore[c * ldY + it.yoff + q];
         for (int q = t; q < nB; q += TRI_THREADS) ub[q] = (T)uG[c * ldG + gidx[q]];
         __syncthreads();
-        for (int r = wid; r < it.nI; r += TRI_THREADS / 32) {
-            const T* row = A + (long long)r * it.ld + it.nI;
-            T s = 0;
-            for (int q = lane; q < nB; q += 32) s += row[q] * ub[q];
-            s = warp_sum(s);
-            if (lane == 0) y[r] -= s;
+        // y -= U_IB u_B: eight rows per warp at a time
+        for (int rb = 8 * wid; rb < it.nI; rb += 8 * (TRI_THREADS / 32)) {
+            T s[8];
+            warp_rows_dot<T, 8>(A + it.nI, it.ld, rb, it.nI, 0, nB, ub, s);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (lane == j && rb + j < it.nI) y[rb + j] -= s[j];
         }
         __syncthreads();
         bwd_upper<T>(A, it.ld, it.nI, y);
@@ -361,8 +392,10 @@ template <class T>
 int condense_run(const T* pool, const void* items, int count, const int* lists, const double* F,
                  double* g, double* ystore, int nrhs, long long ldF, long long ldG, long long ldY,
                  cudaStream_t st) {
+    ktimer_begin(KT_TRI, st);
     k_condense<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, F, g, ystore,
                                                  nrhs, ldF, ldG, ldY);
+    ktimer_end(KT_TRI, st, 0.0, 0.0);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
@@ -372,8 +405,10 @@ template <class T>
 int recover_run(const T* pool, const void* items, int count, const int* lists, const double* uG,
                 const double* ystore, double* u, int nrhs, long long ldG, long long ldU,
                 long long ldY, cudaStream_t st) {
+    ktimer_begin(KT_TRI, st);
     k_recover<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, uG, ystore, u,
                                                 nrhs, ldG, ldU, ldY);
+    ktimer_end(KT_TRI, st, 0.0, 0.0);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;

@@ -32,7 +32,8 @@ void bddc_set_last_error(const char* msg, const char* file, int line);
 void bddc_note_launches(unsigned long long n);
 
 // Optional CUDA-event timing of one kernel class (for roofline reporting).
-enum { KT_NONE = 0, KT_ENGINE_UPDATE = 1, KT_ENGINE_PANEL = 2, KT_GEMV = 3, KT_FACE = 4, KT_EDGE = 5 };
+enum { KT_NONE = 0, KT_ENGINE_UPDATE = 1, KT_ENGINE_PANEL = 2, KT_GEMV = 3, KT_FACE = 4, KT_EDGE = 5,
+       KT_ASSEMBLE = 6, KT_TRANSFORM = 7, KT_TRI = 8, KT_LAST = 8 };
 bool ktimer_on(int kind);
 void ktimer_begin(int kind, cudaStream_t st);
 void ktimer_end(int kind, cudaStream_t st, double flops, double bytes);
@@ -113,9 +114,11 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* di
                int* err, cudaStream_t st, const int* host_n = nullptr, const int* host_k = nullptr,
                bool tensor_cores = false);
 
-// Tensor-core (tcgen05, split TF32) trailing update of one FP32 engine panel.
-int tc_update_run(const EngItem<float>* items_dev, int count, int maxn, int p, const float* dscr, int* err,
-                  cudaStream_t st);
+// Scratch elements engine_run needs for `count` items (FP64 if dbl).
+long long engine_scratch_elems(int count, bool dbl);
+
+// Tensor-core (tcgen05, split TF32) trailing update of one FP32 engine panel of width <= nb.
+int tc_update_run(const EngItem<float>* items_dev, int count, int maxn, int p, int nb, int* err, cudaStream_t st);
 int tc_selftest_run(const float* A, const float* B, float* C, int nr, int nc, int K, int* err, cudaStream_t st);
 
 // Generic batched gather -> GEMV -> scatter-add:  out[oidx[r]] += sum_c M[r][c] * in[iidx[c]]

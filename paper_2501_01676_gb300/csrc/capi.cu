@@ -124,17 +124,39 @@ struct bddc_ctx {
     bddc_stats stats;
     int nG = 0, nPi = 0;
 
-    template <class T>
-    int alloc(T** p, size_t n) {
-        *p = nullptr;
-        if (n == 0) n = 1;
-        void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, n * sizeof(T), st);
+    // Device memory lives as long as the context.  Requests under 1 MiB are
+    // carved (256-byte aligned) out of 16 MiB chunks, so the ~10^3 small
+    // per-entity buffers of a setup cost a handful of pool calls.
+    static constexpr size_t kSmall = size_t(1) << 20, kChunk = size_t(16) << 20;
+    char* chunk = nullptr;
+    size_t chunk_used = 0;
+    int raw_alloc(void** q, size_t b) {
+        cudaError_t e = cudaMallocAsync(q, b, st);
         if (e != cudaSuccess) {
             bddc_set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
             return BDDC_ENOMEM;
         }
-        allocs.push_back(q);
+        allocs.push_back(*q);
+        return BDDC_OK;
+    }
+    template <class T>
+    int alloc(T** p, size_t n) {
+        *p = nullptr;
+        if (n == 0) n = 1;
+        const size_t b = (n * sizeof(T) + 255) & ~size_t(255);
+        void* q = nullptr;
+        if (b >= kSmall) {
+            BDDC_TRY(raw_alloc(&q, b));
+        } else {
+            if (!chunk || chunk_used + b > kChunk) {
+                void* c = nullptr;
+                BDDC_TRY(raw_alloc(&c, kChunk));
+                chunk = (char*)c;
+                chunk_used = 0;
+            }
+            q = chunk + chunk_used;
+            chunk_used += b;
+        }
         bytes += n * sizeof(T);
         *p = (T*)q;
         return BDDC_OK;
@@ -218,7 +240,7 @@ static int run_engine(bddc_ctx* C, const std::vector<EngItem<T>>& items) {
     EngItem<T>* d = nullptr;
     BDDC_TRY(C->upload(&d, items));
     T* scr = nullptr;
-    BDDC_TRY(C->alloc(&scr, items.size() * 32 * 32));
+    BDDC_TRY(C->alloc(&scr, (size_t)engine_scratch_elems((int)items.size(), sizeof(T) == 8)));
     std::vector<int> hn(items.size()), hk(items.size());
     for (size_t i = 0; i < items.size(); ++i) {
         hn[i] = items[i].n;
@@ -226,6 +248,108 @@ static int run_engine(bddc_ctx* C, const std::vector<EngItem<T>>& items) {
     }
     return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st, hn.data(), hk.data(),
                          C->o.tensor_cores != 0);
+}
+
+// Change of basis of a list of entity blocks (TBlock, grouped by output
+// matrix): the block kernel when its shared-memory tiles fit, else the
+// row/column kernel pair.  Identity entities of a subdomain are merged into
+// blocks of at most 64 positions.
+template <class T>
+static int change_basis(bddc_ctx* C, const std::vector<TBlock>& tb, const int* d_idx, const std::vector<int>& idxv,
+                        int maxn_q, cudaStream_t st) {
+    if (tb.empty()) return BDDC_OK;
+    constexpr int IDCHUNK = 64;
+    std::vector<int> extra;
+    struct HB { int n; long long pos; bool ext; const double* Q; };
+    std::vector<std::vector<HB>> groups;
+    std::vector<const TBlock*> head;
+    std::vector<int> gid(tb.size());
+    for (size_t i = 0; i < tb.size(); ++i) {
+        int g = -1;
+        if (!head.empty() && head.back()->dst == tb[i].dst) g = (int)head.size() - 1;
+        else {
+            for (size_t h = 0; h < head.size(); ++h)
+                if (head[h]->dst == tb[i].dst) g = (int)h;
+        }
+        if (g < 0) {
+            g = (int)head.size();
+            head.push_back(&tb[i]);
+            groups.emplace_back();
+        }
+        gid[i] = g;
+    }
+    int nmax = 1;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        std::vector<int> ids;
+        for (size_t i = 0; i < tb.size(); ++i) {
+            if (gid[i] != (int)g) continue;
+            const TBlock& B = tb[i];
+            if (B.identity) {
+                for (int l = 0; l < B.n; ++l) ids.push_back(idxv[B.pos_off + l]);
+            } else {
+                groups[g].push_back(HB{B.n, (long long)B.pos_off, false, B.Q});
+                nmax = std::max(nmax, B.n);
+            }
+        }
+        for (size_t c0 = 0; c0 < ids.size(); c0 += IDCHUNK) {
+            const int n = (int)std::min<size_t>(IDCHUNK, ids.size() - c0);
+            groups[g].push_back(HB{n, (long long)extra.size(), true, nullptr});
+            extra.insert(extra.end(), ids.begin() + c0, ids.begin() + c0 + n);
+            nmax = std::max(nmax, n);
+        }
+    }
+    (void)maxn_q;
+    if (basis_smem(nmax, sizeof(T)) > 200 * 1024) {
+        // large entities: two passes through an n_B x n_B scratch per output
+        size_t ytot = 0;
+        std::vector<TBlock> tb2 = tb;
+        std::vector<long long> yo(groups.size());
+        for (size_t g = 0; g < groups.size(); ++g) {
+            yo[g] = (long long)ytot;
+            ytot += (size_t)head[g]->nrows * head[g]->nrows;
+        }
+        T* Y = nullptr;
+        BDDC_TRY(C->alloc(&Y, ytot));
+        int mq = 1;
+        for (size_t i = 0; i < tb2.size(); ++i) {
+            tb2[i].y = Y + yo[gid[i]];
+            tb2[i].yld = tb2[i].nrows;
+            if (!tb2[i].identity) mq = std::max(mq, tb2[i].n);
+        }
+        TBlock* d_tb;
+        BDDC_TRY(C->upload(&d_tb, tb2));
+        return transform_run<T>(d_tb, (int)tb2.size(), d_idx, mq, 4, st);
+    }
+    int* d_extra = nullptr;
+    BDDC_TRY(C->upload(&d_extra, extra));
+    std::vector<XBlock> xb;
+    std::vector<XSub> xs;
+    std::vector<XRow> xr;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const TBlock& H = *head[g];
+        XSub S;
+        S.src = H.src;
+        S.sld = H.sld;
+        S.sym = H.sym;
+        S.nblk = (int)groups[g].size();
+        S.blk_off = (int)xb.size();
+        S.perm = d_idx + H.perm_off;
+        S.dst = H.dst;
+        S.dld = H.dld;
+        for (size_t b = 0; b < groups[g].size(); ++b) {
+            const HB& h = groups[g][b];
+            xb.push_back(XBlock{h.n, h.ext ? d_extra + h.pos : d_idx + h.pos, h.Q});
+            xr.push_back(XRow{(int)xs.size(), (int)b});
+        }
+        xs.push_back(S);
+    }
+    XBlock* d_xb;
+    XSub* d_xs;
+    XRow* d_xr;
+    BDDC_TRY(C->upload(&d_xb, xb));
+    BDDC_TRY(C->upload(&d_xs, xs));
+    BDDC_TRY(C->upload(&d_xr, xr));
+    return basis_run<T>(d_xr, (int)xr.size(), d_xs, d_xb, nmax, st);
 }
 
 template <class T>
@@ -293,8 +417,10 @@ static int setup_impl(bddc_ctx* C) {
     BDDC_CUDA_TRY(cudaMemsetAsync(C->stencil, 0, sizeof(double) * 27 * (size_t)hm.ndof, st));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->F, 0, sizeof(double) * hm.ndof, st));
     BDDC_TRY(assemble_init(hm, C->o.tau, C->c));
+    ktimer_begin(KT_ASSEMBLE, st);
     BDDC_TRY(assemble_launch<T>(hm, C->nu, C->beta, C->f, C->divb, C->bconst, d_sx, d_sy, d_sz, d_lut,
                                 d_lutoff, d_box0, d_boxn, A, d_aoff, d_ald, C->stencil, C->F, st));
+    ktimer_end(KT_ASSEMBLE, st, 0.0, 0.0);
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
     C->stats.t_assemble_ms = ms_since(t0);
     // ---- 2. partial LU: S^(i) ---------------------------------------------
@@ -485,7 +611,9 @@ static int setup_impl(bddc_ctx* C) {
         }
         FaceJob* d_fj;
         BDDC_TRY(C->upload(&d_fj, fj));
+        ktimer_begin(KT_FACE, st);
         BDDC_TRY(face_run<T>(d_fj, (int)fj.size(), maxn, C->err, st));
+        ktimer_end(KT_FACE, st, 0.0, 0.0);
     }
     BDDC_CUDA_TRY(cudaMemcpyAsync(C->kk.data(), C->d_k, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -569,26 +697,16 @@ static int setup_impl(bddc_ctx* C) {
         std::vector<int> ew_off(nsd, -1);
         auto key_of = [](int kind, int e, int l) -> long long { return ((long long)kind << 40) | ((long long)e << 16) | l; };
         std::vector<TBlock> tb;
-        T* Ysc = nullptr;
         T* W = nullptr;
         double* W64 = nullptr;
         std::vector<long long> woff(nsd, 0), w64off(nsd, 0);
         if (edge_mode == 0) {
-            long long ytot = 0, wtot = 0, w64tot = 0;
+            long long wtot = 0, w64tot = 0;
             for (int s = 0; s < nsd; ++s) {
                 int nB = hm.sub[s].nB;
                 woff[s] = wtot;
                 wtot += (long long)nB * r4(nB);
-                ytot = std::max(ytot, (long long)nB * nB);
             }
-            // (the change-of-basis scratch is per subdomain)
-            std::vector<long long> yoff(nsd);
-            ytot = 0;
-            for (int s = 0; s < nsd; ++s) {
-                yoff[s] = ytot;
-                ytot += (long long)hm.sub[s].nB * hm.sub[s].nB;
-            }
-            BDDC_TRY(C->alloc(&Ysc, ytot));
             BDDC_TRY(C->alloc(&W, wtot));
             std::vector<int> perm_off(nsd);
             std::vector<EngItem<T>> items;
@@ -639,8 +757,8 @@ static int setup_impl(bddc_ctx* C) {
                     B.src = C->S64 + C->soff[s];
                     B.sld = C->sld[s];
                     B.sym = 1;
-                    B.y = Ysc + yoff[s];
-                    B.yld = S.nB;
+                    B.y = nullptr;           // scratch of the two-pass fallback: set by change_basis
+                    B.yld = 0;
                     B.n = n;
                     B.pos_off = posbase + pos_off[e][S.ent_slot[q]];
                     B.perm_off = perm_off[s];
@@ -655,9 +773,9 @@ static int setup_impl(bddc_ctx* C) {
             }
             int* d_idx;
             BDDC_TRY(C->upload(&d_idx, idxv));
-            TBlock* d_tb;
-            BDDC_TRY(C->upload(&d_tb, tb));
-            BDDC_TRY(transform_run<T>(d_tb, (int)tb.size(), d_idx, maxn, 4, st));
+            ktimer_begin(KT_TRANSFORM, st);
+            BDDC_TRY(change_basis<T>(C, tb, d_idx, idxv, maxn, st));
+            ktimer_end(KT_TRANSFORM, st, 0.0, 0.0);
             BDDC_TRY(run_engine<T>(C, items));
             // trailing blocks to FP64
             std::vector<CopyJob> cj;
@@ -802,7 +920,9 @@ static int setup_impl(bddc_ctx* C) {
         }
         EdgeJob* d_ej;
         BDDC_TRY(C->upload(&d_ej, ej));
+        ktimer_begin(KT_EDGE, st);
         BDDC_TRY(edge_run<T>(d_ej, (int)ej.size(), maxnw, maxnz, C->err, st));
+        ktimer_end(KT_EDGE, st, 0.0, 0.0);
     }
     BDDC_CUDA_TRY(cudaMemcpyAsync(C->kk.data(), C->d_k, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
     BDDC_CUDA_TRY(cudaMemcpyAsync(C->neig.data(), C->d_neig, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
@@ -824,9 +944,9 @@ static int setup_impl(bddc_ctx* C) {
     const int nPi = np;
     std::vector<int> idxv, rpi_off(nsd), perm_off(nsd);
     C->np_s.assign(nsd, 0);
-    std::vector<long long> xoff(nsd), yoff2(nsd);
+    std::vector<long long> xoff(nsd);
     std::vector<int> xld(nsd);
-    long long xtot = 0, ytot = 0;
+    long long xtot = 0;
     for (int s = 0; s < nsd; ++s) {
         SubInfo& S = hm.sub[s];
         std::vector<int> rp;
@@ -850,17 +970,13 @@ static int setup_impl(bddc_ctx* C) {
         xld[s] = r4(2 * S.nB);
         xoff[s] = xtot;
         xtot += (long long)2 * S.nB * xld[s];
-        yoff2[s] = ytot;
-        ytot += (long long)S.nB * S.nB;
     }
     int posbase = (int)idxv.size();
     idxv.insert(idxv.end(), posl.begin(), posl.end());
     int* d_idx;
     BDDC_TRY(C->upload(&d_idx, idxv));
     T* X = nullptr;
-    T* Ysc = nullptr;
     BDDC_TRY(C->alloc(&X, xtot));
-    BDDC_TRY(C->alloc(&Ysc, ytot));
     BDDC_CUDA_TRY(cudaMemsetAsync(X, 0, xtot * sizeof(T), st));
     {
         std::vector<TBlock> tb;
@@ -877,8 +993,8 @@ static int setup_impl(bddc_ctx* C) {
                 B.src = C->S64 + C->soff[s];
                 B.sld = C->sld[s];
                 B.sym = 0;
-                B.y = Ysc + yoff2[s];
-                B.yld = S.nB;
+                B.y = nullptr;
+                B.yld = 0;
                 B.n = n;
                 B.pos_off = posbase + pos_off[e][S.ent_slot[q]];
                 B.perm_off = perm_off[s];
@@ -901,17 +1017,19 @@ static int setup_impl(bddc_ctx* C) {
                 dj.push_back(D);
             }
         }
-        TBlock* d_tb;
-        BDDC_TRY(C->upload(&d_tb, tb));
         DTJob* d_dj;
         BDDC_TRY(C->upload(&d_dj, dj));
-        BDDC_TRY(transform_run<T>(d_tb, (int)tb.size(), d_idx, maxn, 4, st));
+        ktimer_begin(KT_TRANSFORM, st);
+        BDDC_TRY(change_basis<T>(C, tb, d_idx, idxv, maxn, st));
+        ktimer_end(KT_TRANSFORM, st, 0.0, 0.0);
         BDDC_TRY(fill_dt_run<T>(d_dj, (int)dj.size(), d_idx, st));
         std::vector<EngItem<T>> items;
         for (int s = 0; s < nsd; ++s)
             items.push_back(EngItem<T>{X + xoff[s], 2 * hm.sub[s].nB, hm.sub[s].nB - C->np_s[s], xld[s]});
         BDDC_TRY(run_engine<T>(C, items));
     }
+    BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+    C->stats.t_basis_ms = ms_since(t0);
     // operators of the apply
     C->maoff.resize(nsd);
     C->mcoff.resize(nsd);
@@ -1389,6 +1507,7 @@ static int copy_coeff(bddc_ctx* C, double** dst, const double* src, size_t n, in
 }
 
 static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, const bddc_partition* part) {
+    const auto t0 = std::chrono::steady_clock::now();
     BDDC_TRY(build_host_mesh(mesh, part, C->hm));
     HostMesh& hm = C->hm;
     if (!k || !k->nu_elem) return BDDC_EINVAL;
@@ -1410,6 +1529,7 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     BDDC_TRY(C->alloc(&C->err, 2));        // [0] error flags, [1] largest Jacobi sweep count
     BDDC_CUDA_TRY(cudaMemsetAsync(C->err, 0, 2 * sizeof(int), C->st));
     BDDC_TRY(pinned_scratch(&C->hst));
+    C->stats.t_mesh_ms = ms_since(t0);
     if (C->mixed) BDDC_TRY(setup_impl<float>(C));
     else BDDC_TRY(setup_impl<double>(C));
     // solve buffers
@@ -1661,7 +1781,7 @@ int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, i
 }
 
 int bddc_kernel_timer(int kind) {
-    if (kind < KT_NONE || kind > KT_EDGE) return BDDC_EINVAL;
+    if (kind < KT_NONE || kind > KT_LAST) return BDDC_EINVAL;
     std::lock_guard<std::mutex> lk(g_kt_mu);
     for (auto& pr : g_kt.ev) {
         cudaEventDestroy(pr.first);

@@ -14,13 +14,26 @@
 // the explicit inverse of the coarse matrix.  Pivoting is not needed: every
 // eliminated block has a positive definite symmetric part (the forms b_i are
 // SPD and the primal constraints remove the constants), for which LU without
-// pivoting exists.  Zero / non-finite pivots are flagged, not trapped.
+// pivoting exists.  Zero / non-finite pivots are flagged (and replaced by 1),
+// not trapped.
 //
-// Right-looking blocked algorithm, panel width NB.  Per panel two launches
-// batched over all items: (1) factor the NB x NB diagonal block (redundantly
-// in every CTA, in shared memory) and solve for the L21 row chunks and the
-// U12 column chunks; (2) the trailing update M22 -= L21 U12 in 64 x 64
-// tiles, register-blocked 4 x 4 per thread.
+// Right-looking blocked algorithm, panel width NB (128 in FP32, 64 in FP64).
+// Per panel three launches, each batched over all items:
+//   k_diag    one CTA per item factors the NB x NB diagonal block in shared
+//             memory, 32 columns at a time (warp-level LU of each 32 x 32
+//             block, strip substitutions, rank-32 update), writes L11\U11
+//             back and the pivot reciprocals to a scratch;
+//   k_trsm    L21 = M21 U11^{-1} in 64-row chunks and U12 = L11^{-1} M12 in
+//             64-column chunks (the latter solved transposed, so both run the
+//             same blocked substitution: per 32-column block subtract the
+//             solved blocks, then substitute within the block);
+//   k_update  M22 -= L21 U12 in TILE x TILE tiles, K staged through shared
+//             memory in chunks of 32, register-blocked (8 x 8 per thread in
+//             FP32, 4 x 4 in FP64).  The FP32 update can run on the tensor
+//             cores instead (tc_update.cu).
+// A wider panel divides the passes over the trailing matrices (the HBM
+// traffic of the update) by the width: NB = 128 does a quarter of the
+// passes of a 32-wide panel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,223 +42,428 @@
 
 namespace {
 
-constexpr int PANEL_THREADS = 128;
-constexpr int CHUNK = 128;            // rows (or columns) per panel CTA
-constexpr int TILE = 64;
+template <class T>
+struct EngCfg;
+template <>
+struct EngCfg<float> {
+    static constexpr int NB = 128, TILE = 128;
+};
+template <>
+struct EngCfg<double> {
+    static constexpr int NB = 64, TILE = 64;
+};
+
+constexpr int DIAG_THREADS = 512;
+constexpr int TRSM_THREADS = 256;
 constexpr int UPD_THREADS = 256;
+constexpr int CH = 64;      // rows (columns) of L21 (U12) per k_trsm CTA
+constexpr int KC = 32;      // K chunk of the update
+constexpr int IB = 32;      // inner block of the diagonal factorisation
+constexpr int ILD = IB + 1;
 
 template <class T>
 __device__ __forceinline__ bool bad_pivot(T v) {
     return !(fabs((double)v) > 1e-300) || !isfinite((double)v);
 }
 
+// Per-item scratch: reciprocals of the NB pivots of the current diagonal block.
+template <class T>
+__host__ __device__ constexpr long long scratch_per_item() {
+    return (long long)EngCfg<T>::NB;
+}
+
+// Solve x U = b within one 32-column block for NR vectors held by a group of 8
+// lanes (lane cg of the group owns entries cg, cg+8, cg+16, cg+24 of every
+// vector in acc[.][0..3]).  U(c, c') = U[c*s1 + c'*s2] for c < c' < bw; its
+// diagonal enters through the reciprocals d (nullptr: unit diagonal).  Column
+// c is final once the update from columns < c is in: its owner scales it and
+// broadcasts it by shuffle, and every lane updates its later columns, so the
+// dependent chain is 32 short steps instead of a 32 x 32 triangle per thread.
+// All 32 lanes of the warp must call it (the shuffles are warp-wide).
+template <class T, int NR>
+__device__ __forceinline__ void subst8(T (&acc)[NR][4], const T* __restrict__ U, int s1, int s2,
+                                       const T* __restrict__ d, int bw, int cg) {
+#pragma unroll
+    for (int ec = 0; ec < 4; ++ec) {
+        for (int gc = 0; gc < 8; ++gc) {
+            const int c = gc + 8 * ec;
+            if (c >= bw) break;
+            const T dc = d ? d[c] : (T)1;
+            T x[NR];
+#pragma unroll
+            for (int a = 0; a < NR; ++a) {
+                x[a] = __shfl_sync(0xffffffffu, acc[a][ec] * dc, gc, 8);
+                if (cg == gc) acc[a][ec] = x[a];
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int cp = cg + 8 * e;
+                if (cp > c && cp < bw) {
+                    const T u = U[c * s1 + cp * s2];
+#pragma unroll
+                    for (int a = 0; a < NR; ++a) acc[a][e] -= x[a] * u;
+                }
+            }
+        }
+    }
+}
+
+// LU of the w x w diagonal block in shared memory, 32 columns at a time.  The
+// code is kept compact (loops over shared memory, no long unrolled chains): it
+// runs once per launch, so straight-line code would be fetched from beyond the
+// instruction cache for every instruction.
 template <class T, int NB>
-__global__ void __launch_bounds__(PANEL_THREADS) k_panel(const EngItem<T>* __restrict__ items, int p,
-                                                         T* __restrict__ dscr, int* __restrict__ err) {
-    static_assert(NB == 32, "one lane per panel column");
+__global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag(const EngItem<T>* __restrict__ items, int p,
+                                                          T* __restrict__ scr, int* __restrict__ err) {
     const EngItem<T> it = items[blockIdx.x];
     if (p >= it.k) return;
     const int w = min(NB, it.k - p);
-    const int n = it.n, ld = it.ld;
-    const int m0 = p + w;                      // first trailing index
-    const int mrem = n - m0;
-    const int nch = (mrem + CHUNK - 1) / CHUNK;
-    const int y = blockIdx.y;
-    if (y > 2 * nch) return;
-    __shared__ T D[NB][NB + 1];
-    __shared__ T W[NB][CHUNK + 1];             // row chunk (transposed) or column chunk
-    T* A = it.a;
+    const long long ld = it.ld;
+    T* A = it.a + (long long)p * ld + p;
+    constexpr int LD = NB + 1;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    T* D = reinterpret_cast<T*>(dsm);        // NB x LD: L\U of the diagonal block
+    T* dinv = D + NB * LD;                    // NB reciprocal pivots
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    constexpr int NW = PANEL_THREADS / 32;
-    for (int r = wid; r < w; r += NW)
-        if (lane < w) D[r][lane] = A[(long long)(p + r) * ld + p + lane];
+    for (int q = t; q < w * w; q += DIAG_THREADS) {
+        const int r = q / w, c = q - r * w;
+        D[r * LD + c] = A[r * ld + c];
+    }
     __syncthreads();
-    for (int j = 0; j < w; ++j) {
-        T piv = D[j][j];
-        if (bad_pivot(piv)) {
-            if (t == 0 && y == 0) atomicOr(err, ERR_PIVOT);
-            piv = (T)1;
+    for (int b0 = 0; b0 < w; b0 += IB) {
+        const int bw = min(IB, w - b0);
+        // (a) unblocked LU of the 32 x 32 diagonal block, one warp, lane = row
+        if (wid == 0) {
+            bool bad = false;
+            for (int j = 0; j < bw; ++j) {
+                T piv = D[(b0 + j) * LD + b0 + j];
+                if (bad_pivot(piv)) {
+                    bad = true;
+                    piv = (T)1;
+                }
+                const T ri = (T)1 / piv;
+                __syncwarp();
+                if (lane == j) {
+                    D[(b0 + j) * LD + b0 + j] = piv;
+                    dinv[b0 + j] = ri;
+                }
+                if (lane > j && lane < bw) {
+                    T* row = D + (b0 + lane) * LD + b0;
+                    const T* prow = D + (b0 + j) * LD + b0;
+                    const T l = row[j] * ri;
+                    row[j] = l;
+#pragma unroll 4
+                    for (int c = j + 1; c < bw; ++c) row[c] -= l * prow[c];
+                }
+                __syncwarp();
+            }
+            if (bad && lane == 0) atomicOr(err, ERR_PIVOT);
         }
-        if (t > j && t < w) D[t][j] /= piv;
         __syncthreads();
-        for (int i = j + 1 + wid; i < w; i += NW)
-            if (lane > j && lane < w) D[i][lane] -= D[i][j] * D[j][lane];
-        __syncthreads();
-    }
-    if (y == 0) {
-        T* ds = dscr + (long long)blockIdx.x * NB * NB;
-        for (int r = wid; r < w; r += NW)
-            if (lane < w) ds[r * w + lane] = D[r][lane];
-        return;
-    }
-    if (y <= nch) {
-        // rows r0 .. r0+CHUNK of L21 = M21 U11^{-1}
-        const int r0 = m0 + (y - 1) * CHUNK;
-        const int nr = min(CHUNK, n - r0);
-        for (int r = wid; r < nr; r += NW)
-            if (lane < w) W[lane][r] = A[(long long)(r0 + r) * ld + p + lane];
-        __syncthreads();
-        if (t < nr) {
-            for (int j = 0; j < w; ++j) {
-                T x = W[j][t];
-                for (int l = 0; l < j; ++l) x -= W[l][t] * D[l][j];
-                T piv = D[j][j];
-                if (bad_pivot(piv)) piv = (T)1;
-                W[j][t] = x / piv;
+        // (b) strips by substitution, one 8-lane group per vector: rows below solve
+        //     x U_bb = a, columns to the right solve L_bb y = a (the transposed
+        //     form of the same recurrence, unit diagonal)
+        const int rem = w - b0 - bw;
+        if (rem > 0) {
+            const int grp = t >> 3, cg = t & 7;
+            constexpr int NG = DIAG_THREADS / 8;
+            const T* Db = D + b0 * LD + b0;
+            for (int j0 = 0; j0 < 2 * rem; j0 += NG) {
+                const int job = j0 + grp;
+                const bool valid = job < 2 * rem;
+                const bool colv = job >= rem;
+                const int g = b0 + bw + (colv ? job - rem : job);
+                T acc[1][4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = cg + 8 * e;
+                    acc[0][e] = (valid && c < bw) ? (colv ? D[(b0 + c) * LD + g] : D[g * LD + b0 + c]) : (T)0;
+                }
+                // groups of one warp may differ in side: pass the side's strides per lane
+                subst8<T, 1>(acc, Db, colv ? 1 : LD, colv ? LD : 1, colv ? nullptr : dinv + b0, bw, cg);
+                if (valid) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = cg + 8 * e;
+                        if (c < bw) {
+                            if (colv) D[(b0 + c) * LD + g] = acc[0][e];
+                            else D[g * LD + b0 + c] = acc[0][e];
+                        }
+                    }
+                }
             }
         }
         __syncthreads();
-        for (int r = wid; r < nr; r += NW)
-            if (lane < w) A[(long long)(r0 + r) * ld + p + lane] = W[lane][r];
+        // (c) rank-bw update of the remaining rem x rem block; lane = column within a
+        //     32-column group, four rows per thread
+        if (rem > 0) {
+            const int ncg = (rem + 31) / 32, nrg = (rem + 3) / 4;
+            const int base = b0 + bw;
+            for (int job = wid; job < ncg * nrg; job += DIAG_THREADS / 32) {
+                const int cg = job % ncg, rg = job / ncg;
+                const int c = base + cg * 32 + lane;
+                const int r0 = base + rg * 4;
+                if (c < w) {
+                    T acc[4] = {0, 0, 0, 0};
+                    for (int l = 0; l < bw; ++l) {
+                        const T u = D[(b0 + l) * LD + c];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+                            if (r0 + a < w) acc[a] += D[(r0 + a) * LD + b0 + l] * u;
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        if (r0 + a < w) D[(r0 + a) * LD + c] -= acc[a];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    T* out = scr + (long long)blockIdx.x * scratch_per_item<T>();
+    for (int q = t; q < w; q += DIAG_THREADS) out[q] = dinv[q];
+    for (int q = t; q < w * w; q += DIAG_THREADS) {
+        const int r = q / w, c = q - r * w;
+        A[r * ld + c] = D[r * LD + c];
+    }
+}
+
+// Blocked substitution on a chunk of R <= CH rows, X (R x w, in shared memory):
+//   X <- X U^{-1}, U upper triangular w x w given by the accessor U(l, c), l <= c.
+// L21 chunks use U = U11 (pivot reciprocals from k_diag); U12 chunks are solved
+// transposed with U = L11^T (unit diagonal).  Per 32-column block: subtract the
+// solved blocks (register-blocked, 2 rows x 4 columns per thread), then
+// substitute within the block (subst8: 8 lanes per row pair).
+template <class T, int NB>
+__global__ void __launch_bounds__(TRSM_THREADS, 2) k_trsm(const EngItem<T>* __restrict__ items, int p,
+                                                          const T* __restrict__ scr, int nch) {
+    const EngItem<T> it = items[blockIdx.x];
+    if (p >= it.k) return;
+    const int w = min(NB, it.k - p);
+    const int n = it.n;
+    const long long ld = it.ld;
+    const int m0 = p + w;
+    const bool colside = (int)blockIdx.y >= nch;
+    const int chunk = colside ? blockIdx.y - nch : blockIdx.y;
+    const int g0 = m0 + chunk * CH;
+    if (g0 >= n) return;
+    const int R = min(CH, n - g0);
+    constexpr int LDX = NB + 1;
+    extern __shared__ __align__(16) unsigned char tsm_[];
+    T* X = reinterpret_cast<T*>(tsm_);        // CH x LDX
+    T* Us = X + CH * LDX;                     // NB x 33: U(l, b0 + c) for l < b0 + 32
+    T* dv = Us + NB * (IB + 1);               // 32 reciprocal diagonal entries of the block
+    const T* A = it.a;
+    const T* pinv = scr + (long long)blockIdx.x * scratch_per_item<T>();
+    const int t = threadIdx.x;
+    if (!colside) {
+        for (int q = t; q < CH * w; q += TRSM_THREADS) {
+            const int r = q / w, c = q - r * w;
+            X[r * LDX + c] = r < R ? A[(long long)(g0 + r) * ld + p + c] : (T)0;
+        }
     } else {
-        // columns c0 .. c0+CHUNK of U12 = L11^{-1} M12
-        const int c0 = m0 + (y - 1 - nch) * CHUNK;
-        const int nc = min(CHUNK, n - c0);
-        for (int r = 0; r < w; ++r)
-            for (int c = t; c < nc; c += PANEL_THREADS) W[r][c] = A[(long long)(p + r) * ld + c0 + c];
-        __syncthreads();
-        if (t < nc) {
-            for (int i = 1; i < w; ++i) {
-                T x = W[i][t];
-                for (int l = 0; l < i; ++l) x -= D[i][l] * W[l][t];
-                W[i][t] = x;
+        // X[c][k] = M12[k][c]: rows of M12 are contiguous along c
+        for (int q = t; q < CH * w; q += TRSM_THREADS) {
+            const int k = q / CH, c = q - k * CH;
+            X[c * LDX + k] = c < R ? A[(long long)(p + k) * ld + g0 + c] : (T)0;
+        }
+    }
+    const int rg = t >> 3, cg = t & 7;        // rows 2rg, 2rg+1; columns cg + 8e
+    for (int b0 = 0; b0 < w; b0 += IB) {
+        const int bw = min(IB, w - b0);
+        const int nl = b0 + bw;
+        if (!colside) {
+            for (int q = t; q < nl * IB; q += TRSM_THREADS) {
+                const int l = q / IB, c = q - l * IB;
+                Us[l * (IB + 1) + c] = c < bw ? A[(long long)(p + l) * ld + p + b0 + c] : (T)0;
             }
+            if (t < IB) dv[t] = t < bw ? pinv[b0 + t] : (T)1;
+        } else {
+            // U(l, b0 + c) = L11[b0 + c][l]: rows of L11, read along l
+            for (int q = t; q < nl * IB; q += TRSM_THREADS) {
+                const int c = q / nl, l = q - c * nl;
+                Us[l * (IB + 1) + c] = c < bw ? A[(long long)(p + b0 + c) * ld + p + l] : (T)0;
+            }
+            if (t < IB) dv[t] = (T)1;
         }
         __syncthreads();
-        for (int r = 0; r < w; ++r)
-            for (int c = t; c < nc; c += PANEL_THREADS) A[(long long)(p + r) * ld + c0 + c] = W[r][c];
+        T acc[2][4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[a][e] = X[(2 * rg + a) * LDX + b0 + cg + 8 * e];
+        for (int l = 0; l < b0; ++l) {
+            const T x0 = X[(2 * rg) * LDX + l], x1 = X[(2 * rg + 1) * LDX + l];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const T u = Us[l * (IB + 1) + cg + 8 * e];
+                acc[0][e] -= x0 * u;
+                acc[1][e] -= x1 * u;
+            }
+        }
+        subst8<T, 2>(acc, Us + b0 * (IB + 1), IB + 1, 1, dv, bw, cg);
+        __syncthreads();        // every read of this block's X and of Us is done
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) X[(2 * rg + a) * LDX + b0 + cg + 8 * e] = acc[a][e];
+        __syncthreads();
+    }
+    T* Aw = it.a;
+    if (!colside) {
+        for (int q = t; q < R * w; q += TRSM_THREADS) {
+            const int r = q / w, c = q - r * w;
+            Aw[(long long)(g0 + r) * ld + p + c] = X[r * LDX + c];
+        }
+    } else {
+        for (int q = t; q < R * w; q += TRSM_THREADS) {
+            const int k = q / R, c = q - k * R;
+            Aw[(long long)(p + k) * ld + g0 + c] = X[c * LDX + k];
+        }
     }
 }
 
 template <class T>
-__device__ __forceinline__ void lds4(const T* p, T out[4]);
+__device__ __forceinline__ void lds16(const T* p, T* out);
 template <>
-__device__ __forceinline__ void lds4<float>(const float* p, float out[4]) {
-    float4 v = *reinterpret_cast<const float4*>(p);
+__device__ __forceinline__ void lds16<float>(const float* p, float* out) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
     out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
 }
 template <>
-__device__ __forceinline__ void lds4<double>(const double* p, double out[4]) {
-    double2 v0 = *reinterpret_cast<const double2*>(p);
-    double2 v1 = *reinterpret_cast<const double2*>(p + 2);
-    out[0] = v0.x; out[1] = v0.y; out[2] = v1.x; out[3] = v1.y;
+__device__ __forceinline__ void lds16<double>(const double* p, double* out) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    out[0] = v.x; out[1] = v.y;
 }
 
-template <class T, int NB>
-__global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __restrict__ items, int p,
-                                                        const T* __restrict__ dscr) {
+// M22 -= L21 U12 on one TILE x TILE tile.  Thread (tr, tc) of a 16 x 16 grid owns
+// rows {tr*H + a, TILE/2 + tr*H + a} and columns {tc*H + b, TILE/2 + tc*H + b},
+// H = TILE/32 (16-byte shared-memory vectors, conflict-free per quarter warp).
+template <class T, int NB, int TILE>
+__global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __restrict__ items, int p, int nt) {
     const EngItem<T> it = items[blockIdx.x];
     if (p >= it.k) return;
     const int w = min(NB, it.k - p);
-    const int n = it.n, ld = it.ld;
+    const int n = it.n;
+    const long long ld = it.ld;
     const int m0 = p + w;
-    const int mrem = n - m0;
-    const int nt = (mrem + TILE - 1) / TILE;
     const int y = blockIdx.y;
-    T* A = it.a;
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    if (y == 0) {
-        const T* ds = dscr + (long long)blockIdx.x * NB * NB;
-        for (int r = wid; r < w; r += UPD_THREADS / 32)
-            if (lane < w) A[(long long)(p + r) * ld + p + lane] = ds[r * w + lane];
-        return;
-    }
-    if (y > nt * nt) return;
-    const int ti = (y - 1) / nt, tj = (y - 1) - ti * nt;
+    const int ti = y / nt, tj = y - ti * nt;
     const int r0 = m0 + ti * TILE, c0 = m0 + tj * TILE;
-    constexpr int LDT = TILE + 4;      // 16-byte aligned rows for vector loads
-    __shared__ __align__(16) T Ls[NB][LDT];    // L21 tile, transposed: Ls[k][r]
-    __shared__ __align__(16) T Us[NB][LDT];    // U12 tile: Us[k][c]
-    for (int r = wid; r < TILE; r += UPD_THREADS / 32) {
-        int gr = r0 + r;
-        if (lane < w) Ls[lane][r] = gr < n ? A[(long long)gr * ld + p + lane] : (T)0;
+    if (r0 >= n || c0 >= n) return;
+    constexpr int H = TILE / 32;              // elements per half per thread (4 in FP32, 2 in FP64)
+    constexpr int LDT = TILE + 4;
+    __shared__ __align__(16) T Ls[KC][LDT];  // L21 chunk, transposed: Ls[k][r]
+    __shared__ __align__(16) T Us[KC][LDT];  // U12 chunk: Us[k][c]
+    T* A = it.a;
+    const int t = threadIdx.x;
+    const int tr = t >> 4, tc = t & 15;
+    T acc[2 * H][2 * H];
+#pragma unroll
+    for (int a = 0; a < 2 * H; ++a)
+#pragma unroll
+        for (int b = 0; b < 2 * H; ++b) acc[a][b] = (T)0;
+    for (int k0 = 0; k0 < w; k0 += KC) {
+        const int kw = min(KC, w - k0);
+        for (int q = t; q < TILE * KC; q += UPD_THREADS) {
+            const int r = q / KC, k = q - r * KC;
+            const int gr = r0 + r;
+            Ls[k][r] = (gr < n && k < kw) ? A[(long long)gr * ld + p + k0 + k] : (T)0;
+        }
+        for (int q = t; q < TILE * KC; q += UPD_THREADS) {
+            const int k = q / TILE, c = q - k * TILE;
+            const int gc = c0 + c;
+            Us[k][c] = (gc < n && k < kw) ? A[(long long)(p + k0 + k) * ld + gc] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < KC; ++k) {
+            T lv[2 * H], uv[2 * H];
+            lds16<T>(&Ls[k][tr * H], lv);
+            lds16<T>(&Ls[k][TILE / 2 + tr * H], lv + H);
+            lds16<T>(&Us[k][tc * H], uv);
+            lds16<T>(&Us[k][TILE / 2 + tc * H], uv + H);
+#pragma unroll
+            for (int a = 0; a < 2 * H; ++a)
+#pragma unroll
+                for (int b = 0; b < 2 * H; ++b) acc[a][b] += lv[a] * uv[b];
+        }
+        __syncthreads();
     }
-    for (int k = t >> 6; k < w; k += UPD_THREADS / TILE) {
-        int c = t & (TILE - 1);
-        int gc = c0 + c;
-        Us[k][c] = gc < n ? A[(long long)(p + k) * ld + gc] : (T)0;
-    }
-    __syncthreads();
-    const int tr = (t >> 4) * 4, tc = (t & 15) * 4;   // 16 x 16 threads, a 4 x 4 block each
-    T acc[4][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-    for (int k = 0; k < w; ++k) {
-        T lv[4], uv[4];
-        lds4<T>(&Ls[k][tr], lv);
-        lds4<T>(&Us[k][tc], uv);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        int gr = r0 + tr + a;
+    for (int a = 0; a < 2 * H; ++a) {
+        const int gr = r0 + (a < H ? tr * H + a : TILE / 2 + tr * H + a - H);
         if (gr >= n) continue;
         T* row = A + (long long)gr * ld;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            int gc = c0 + tc + b;
+        for (int b = 0; b < 2 * H; ++b) {
+            const int gc = c0 + (b < H ? tc * H + b : TILE / 2 + tc * H + b - H);
             if (gc < n) row[gc] -= acc[a][b];
         }
     }
 }
 
-}  // namespace
+template <class T>
+size_t trsm_smem() {
+    constexpr int NB = EngCfg<T>::NB;
+    return sizeof(T) * ((size_t)CH * (NB + 1) + (size_t)NB * (IB + 1) + IB);
+}
 
 template <class T>
-static int launch_update(const EngItem<T>* items_dev, int count, int maxn, int p, T* dscr, int* err, cudaStream_t st,
-                         bool tc);
-template <>
-int launch_update<double>(const EngItem<double>* items_dev, int count, int maxn, int p, double* dscr, int* err,
-                          cudaStream_t st, bool tc) {
-    (void)tc;
-    (void)err;
-    const int nt = (maxn - p + TILE - 1) / TILE;
-    k_update<double, 32><<<dim3(count, 1 + nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, dscr);
-    bddc_note_launches(1);
-    return BDDC_OK;
+size_t diag_smem() {
+    constexpr int NB = EngCfg<T>::NB;
+    return sizeof(T) * ((size_t)NB * (NB + 1) + NB);
 }
-template <>
-int launch_update<float>(const EngItem<float>* items_dev, int count, int maxn, int p, float* dscr, int* err,
-                         cudaStream_t st, bool tc) {
-    if (tc) return tc_update_run(items_dev, count, maxn, p, dscr, err, st);
-    const int nt = (maxn - p + TILE - 1) / TILE;
-    k_update<float, 32><<<dim3(count, 1 + nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, dscr);
-    bddc_note_launches(1);
-    return BDDC_OK;
+
+}  // namespace
+
+long long engine_scratch_elems(int count, bool dbl) {
+    return (long long)count * (dbl ? scratch_per_item<double>() : scratch_per_item<float>());
 }
 
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* dscr, int* err,
                cudaStream_t st, const int* hn, const int* hk, bool tc) {
-    constexpr int NB = 32;
+    constexpr int NB = EngCfg<T>::NB, TILE = EngCfg<T>::TILE;
     if (count <= 0 || maxk <= 0) return BDDC_OK;
+    const size_t dsm = diag_smem<T>();
+    const size_t tsm = trsm_smem<T>();
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_diag<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_trsm<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
     for (int p = 0; p < maxk; p += NB) {
-        int mrem = maxn - p;                 // upper bound of the trailing size
-        int nch = (mrem + CHUNK - 1) / CHUNK;
-        int nt = (mrem + TILE - 1) / TILE;
-        // algorithmic work of this panel: trailing update 2 m^2 w, panel solves ~ 2 w^2 m
+        const int mrem = std::max(maxn - p, 1);          // bound of the trailing size
+        const int nch = (mrem + CH - 1) / CH;
+        const int nt = (mrem + TILE - 1) / TILE;
+        // algorithmic work of this panel: trailing update 2 m^2 w; diagonal block
+        // (2/3) w^3 and substitutions 2 w^2 m
         double fu = 0.0, fp = 0.0, bu = 0.0;
         if (hn && (ktimer_on(KT_ENGINE_UPDATE) || ktimer_on(KT_ENGINE_PANEL)))
             for (int i = 0; i < count; ++i) {
                 if (p >= hk[i]) continue;
                 double w = std::min(NB, hk[i] - p), m = hn[i] - p - w;
                 fu += 2.0 * m * m * w;
-                fp += 2.0 * w * w * m;
+                fp += 2.0 * w * w * w / 3.0 + 2.0 * w * w * m;
                 bu += sizeof(T) * (2.0 * m * m + 2.0 * m * w);   // read + write M22, read L21, U12
             }
         ktimer_begin(KT_ENGINE_PANEL, st);
-        k_panel<T, NB><<<dim3(count, 1 + 2 * nch), PANEL_THREADS, 0, st>>>(items_dev, p, dscr, err);
-        bddc_note_launches(1);
+        k_diag<T, NB><<<count, DIAG_THREADS, dsm, st>>>(items_dev, p, dscr, err);
+        k_trsm<T, NB><<<dim3(count, 2 * nch), TRSM_THREADS, tsm, st>>>(items_dev, p, dscr, nch);
+        bddc_note_launches(2);
         ktimer_end(KT_ENGINE_PANEL, st, fp, 0.0);
         ktimer_begin(KT_ENGINE_UPDATE, st);
-        BDDC_TRY(launch_update<T>(items_dev, count, maxn, p, dscr, err, st, tc));
+        if constexpr (sizeof(T) == 4) {
+            if (tc) {
+                BDDC_TRY(tc_update_run(reinterpret_cast<const EngItem<float>*>(items_dev), count, maxn, p, NB,
+                                       err, st));
+            } else {
+                k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt);
+                bddc_note_launches(1);
+            }
+        } else {
+            (void)tc;
+            k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt);
+            bddc_note_launches(1);
+        }
         ktimer_end(KT_ENGINE_UPDATE, st, fu, bu);
-        (void)nt;
     }
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;

@@ -3,7 +3,6 @@
 // the set of subdomains sharing X).
 #include <algorithm>
 #include <cmath>
-#include <map>
 
 #include "bddc_internal.h"
 
@@ -39,14 +38,6 @@ int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh&
         if (ix <= 0 || iy <= 0 || iz <= 0 || ix >= Ex || iy >= Ey || iz >= Ez) return -1;
         return (ix - 1) + (Ex - 1) * ((iy - 1) + (Ey - 1) * (iz - 1));
     };
-    // slabs holding node index i in direction d
-    auto slabs_of = [&](int d, int i, int* out) -> int {
-        int c = 0;
-        const std::vector<int>& o = hm.off[d];
-        for (int s = 0; s < hm.nsub[d]; ++s)
-            if (o[s] <= i && i <= o[s + 1]) out[c++] = s;
-        return c;
-    };
     hm.sub.assign(hm.nsd, SubInfo());
     for (int sz = 0; sz < hm.nsub[2]; ++sz)
         for (int sy = 0; sy < hm.nsub[1]; ++sy)
@@ -60,7 +51,12 @@ int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh&
                     S.box1[d] = hm.off[d][c[d] + 1];
                     S.max_slab = std::max(S.max_slab, S.box1[d] - S.box0[d]);
                 }
+                // the box is walked with x fastest, so both lists come out ascending
                 std::vector<int> in, bd;
+                const long long nbox = (long long)(S.box1[0] - S.box0[0] + 1) * (S.box1[1] - S.box0[1] + 1) *
+                                       (S.box1[2] - S.box0[2] + 1);
+                in.reserve((size_t)nbox);
+                bd.reserve((size_t)nbox);
                 for (int iz = S.box0[2]; iz <= S.box1[2]; ++iz)
                     for (int iy = S.box0[1]; iy <= S.box1[1]; ++iy)
                         for (int ix = S.box0[0]; ix <= S.box1[0]; ++ix) {
@@ -70,62 +66,75 @@ int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh&
                                           iy < S.box1[1] && S.box0[2] < iz && iz < S.box1[2];
                             (inside ? in : bd).push_back(d);
                         }
-                std::sort(in.begin(), in.end());
-                std::sort(bd.begin(), bd.end());
                 S.nI = (int)in.size();
                 S.nB = (int)bd.size();
                 S.n = S.nI + S.nB;
-                S.dofs = in;
+                S.dofs = std::move(in);
                 S.dofs.insert(S.dofs.end(), bd.begin(), bd.end());
             }
-    // interface classification by the owner set n(x)
-    hm.gamma_of_dof.assign(hm.ndof, -1);
-    std::map<std::vector<int>, int> key2ent;
+    // interface classification by the owner set n(x).  In a tensor partition the
+    // owner set of node (ix, iy, iz) is fixed by one code per direction: 2s for
+    // the plane between slabs s-1 and s (shared by both), 2s+1 for the inside of
+    // slab s; a node on k planes is shared by 2^k subdomains (k = 1 face, 2 edge,
+    // 3 vertex).  Nodes are visited in ascending dof order, so every entity's
+    // dof list comes out sorted.
+    std::vector<int> code[3];
+    for (int d = 0; d < 3; ++d) {
+        code[d].assign(hm.E[d] + 1, -1);
+        for (int s = 0; s < hm.nsub[d]; ++s)
+            for (int i = hm.off[d][s] + 1; i < hm.off[d][s + 1]; ++i) code[d][i] = 2 * s + 1;
+        for (int s = 1; s < hm.nsub[d]; ++s) code[d][hm.off[d][s]] = 2 * s;
+    }
+    const int nc0 = 2 * hm.nsub[0] + 1, nc1 = 2 * hm.nsub[1] + 1, nc2 = 2 * hm.nsub[2] + 1;
+    std::vector<int> key2ent((size_t)nc0 * nc1 * nc2, -1);
     std::vector<Entity> ents;
+    hm.gamma_of_dof.assign(hm.ndof, -1);
+    hm.gamma.clear();
+    hm.gamma.reserve(hm.ndof);
     for (int iz = 1; iz < Ez; ++iz)
         for (int iy = 1; iy < Ey; ++iy)
             for (int ix = 1; ix < Ex; ++ix) {
-                int a[2], b[2], c[2];
-                int na = slabs_of(0, ix, a), nb = slabs_of(1, iy, b), nc = slabs_of(2, iz, c);
-                int cnt = na * nb * nc;
-                if (cnt < 2) continue;
-                std::vector<int> key;
-                for (int q = 0; q < nc; ++q)
-                    for (int p = 0; p < nb; ++p)
-                        for (int o = 0; o < na; ++o)
-                            key.push_back(a[o] + hm.nsub[0] * (b[p] + hm.nsub[1] * c[q]));
-                std::sort(key.begin(), key.end());
-                int d = dof_of(ix, iy, iz);
-                auto it = key2ent.find(key);
-                int e;
-                if (it == key2ent.end()) {
+                const int cx = code[0][ix], cy = code[1][iy], cz = code[2][iz];
+                const int planes = (~cx & 1) + (~cy & 1) + (~cz & 1);
+                if (planes == 0) continue;
+                const int d = dof_of(ix, iy, iz);
+                const size_t key = (size_t)cx + nc0 * ((size_t)cy + (size_t)nc1 * cz);
+                int e = key2ent[key];
+                if (e < 0) {
                     e = (int)ents.size();
                     key2ent[key] = e;
                     Entity E;
-                    E.kind = cnt == 8 ? 0 : (cnt == 4 ? 1 : (cnt == 2 ? 2 : -1));
-                    if (E.kind < 0) return BDDC_EINVAL;
-                    E.subs = key;
-                    ents.push_back(E);
-                } else {
-                    e = it->second;
+                    E.kind = planes == 3 ? 0 : (planes == 2 ? 1 : 2);
+                    int a[2], b[2], c[2], na = 0, nb = 0, ncz = 0;
+                    if (cx & 1) a[na++] = cx >> 1; else { a[na++] = (cx >> 1) - 1; a[na++] = cx >> 1; }
+                    if (cy & 1) b[nb++] = cy >> 1; else { b[nb++] = (cy >> 1) - 1; b[nb++] = cy >> 1; }
+                    if (cz & 1) c[ncz++] = cz >> 1; else { c[ncz++] = (cz >> 1) - 1; c[ncz++] = cz >> 1; }
+                    for (int q = 0; q < ncz; ++q)
+                        for (int p2 = 0; p2 < nb; ++p2)
+                            for (int o = 0; o < na; ++o)
+                                E.subs.push_back(a[o] + hm.nsub[0] * (b[p2] + hm.nsub[1] * c[q]));
+                    ents.push_back(std::move(E));
                 }
                 ents[e].dofs.push_back(d);
+                hm.gamma_of_dof[d] = (int)hm.gamma.size();
+                hm.gamma.push_back(d);
             }
-    for (auto& E : ents) std::sort(E.dofs.begin(), E.dofs.end());
-    std::sort(ents.begin(), ents.end(), [](const Entity& x, const Entity& y) {
-        if (x.kind != y.kind) return x.kind < y.kind;
-        return x.dofs[0] < y.dofs[0];
+    // entity order: kind, then smallest dof
+    std::vector<int> order(ents.size());
+    for (size_t e = 0; e < ents.size(); ++e) order[e] = (int)e;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        if (ents[x].kind != ents[y].kind) return ents[x].kind < ents[y].kind;
+        return ents[x].dofs[0] < ents[y].dofs[0];
     });
-    hm.ent = ents;
+    hm.ent.clear();
+    hm.ent.reserve(ents.size());
+    for (int e : order) hm.ent.push_back(std::move(ents[e]));
     for (int k = 0; k < 3; ++k) hm.by_kind[k].clear();
     for (int e = 0; e < (int)hm.ent.size(); ++e) {
         Entity& E = hm.ent[e];
         E.slot = (int)hm.by_kind[E.kind].size();
         hm.by_kind[E.kind].push_back(e);
-        for (int d : E.dofs) hm.gamma.push_back(d);
     }
-    std::sort(hm.gamma.begin(), hm.gamma.end());
-    for (int g = 0; g < (int)hm.gamma.size(); ++g) hm.gamma_of_dof[hm.gamma[g]] = g;
     for (int s = 0; s < hm.nsd; ++s) {
         SubInfo& S = hm.sub[s];
         S.gidx.resize(S.nB);
@@ -135,20 +144,31 @@ int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh&
             S.gidx[b] = g;
         }
     }
+    // entity positions within each subdomain's interface list, through a dof ->
+    // position table filled for one subdomain at a time
     for (int e = 0; e < (int)hm.ent.size(); ++e) {
         Entity& E = hm.ent[e];
-        E.pos.resize(E.subs.size());
+        E.pos.assign(E.subs.size(), std::vector<int>(E.dofs.size()));
         for (size_t a = 0; a < E.subs.size(); ++a) {
             SubInfo& S = hm.sub[E.subs[a]];
-            auto b0 = S.dofs.begin() + S.nI;
-            for (int d : E.dofs) {
-                auto it = std::lower_bound(b0, S.dofs.end(), d);
-                if (it == S.dofs.end() || *it != d) return BDDC_EINVAL;
-                E.pos[a].push_back((int)(it - b0));
-            }
             S.ents.push_back(e);
             S.ent_slot.push_back((int)a);
         }
+    }
+    std::vector<int> loc(hm.ndof, -1);
+    for (int s = 0; s < hm.nsd; ++s) {
+        SubInfo& S = hm.sub[s];
+        for (int b = 0; b < S.nB; ++b) loc[S.dofs[S.nI + b]] = b;
+        for (size_t q = 0; q < S.ents.size(); ++q) {
+            Entity& E = hm.ent[S.ents[q]];
+            std::vector<int>& P = E.pos[S.ent_slot[q]];
+            for (size_t l = 0; l < E.dofs.size(); ++l) {
+                const int b = loc[E.dofs[l]];
+                if (b < 0) return BDDC_EINVAL;
+                P[l] = b;
+            }
+        }
+        for (int b = 0; b < S.nB; ++b) loc[S.dofs[S.nI + b]] = -1;
     }
     return BDDC_OK;
 }

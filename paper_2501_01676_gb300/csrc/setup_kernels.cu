@@ -108,6 +108,71 @@ __global__ void k_transform_left(const TBlock* __restrict__ blocks, const int* _
     }
 }
 
+// Change of basis by blocks, one CTA per (subdomain, row block X): for every
+// column block Y gather B = S[pX, pY] (symmetric part if asked), W = B QY,
+// Z = QX^T W, and store Z at the permuted positions (rows and columns of one
+// entity are contiguous runs of the output).  Shared memory: QX, QY, B, W.
+template <class TY, class TD>
+__global__ void k_basis(const XRow* __restrict__ rows, const XSub* __restrict__ subs,
+                        const XBlock* __restrict__ blks, int nmax) {
+    const XRow R = rows[blockIdx.x];
+    const XSub S = subs[R.sub];
+    const XBlock BX = blks[S.blk_off + R.blk];
+    extern __shared__ __align__(16) unsigned char braw[];
+    TY* QX = reinterpret_cast<TY*>(braw);
+    TY* QY = QX + nmax * nmax;
+    TY* Bm = QY + nmax * nmax;
+    TY* W = Bm + nmax * nmax;
+    const int nx = BX.n;
+    const int* px = BX.pos;
+    const int* perm = S.perm;
+    TD* dst = (TD*)S.dst;
+    const int t = threadIdx.x;
+    if (BX.Q)
+        for (int q = t; q < nx * nx; q += TH) QX[q] = (TY)BX.Q[q];
+    for (int yb = 0; yb < S.nblk; ++yb) {
+        const XBlock BY = blks[S.blk_off + yb];
+        const int ny = BY.n;
+        const int* py = BY.pos;
+        for (int q = t; q < nx * ny; q += TH) {
+            const int a = q / ny, b = q - a * ny;
+            const long long ia = px[a], ib = py[b];
+            double v = S.src[ia * S.sld + ib];
+            if (S.sym) v = 0.5 * (v + S.src[ib * S.sld + ia]);
+            Bm[q] = (TY)v;
+        }
+        if (BY.Q)
+            for (int q = t; q < ny * ny; q += TH) QY[q] = (TY)BY.Q[q];
+        __syncthreads();
+        const TY* Wp = Bm;
+        if (BY.Q) {
+            for (int q = t; q < nx * ny; q += TH) {
+                const int a = q / ny, m = q - a * ny;
+                const TY* br = Bm + a * ny;
+                TY s = 0;
+                for (int b = 0; b < ny; ++b) s += br[b] * QY[b * ny + m];
+                W[q] = s;
+            }
+            __syncthreads();
+            Wp = W;
+        }
+        for (int q = t; q < nx * ny; q += TH) {
+            const int l = q / ny, m = q - l * ny;
+            const int pr = perm[px[l]], pc = perm[py[m]];
+            if (pr < 0 || pc < 0) continue;
+            TY z;
+            if (BX.Q) {
+                z = 0;
+                for (int a = 0; a < nx; ++a) z += QX[a * nx + l] * Wp[a * ny + m];
+            } else {
+                z = Wp[l * ny + m];
+            }
+            dst[(long long)pr * S.dld + pc] = (TD)z;
+        }
+        __syncthreads();
+    }
+}
+
 // X[nB + pos[a]][perm[pos[l]]] = DQ[a][l];  X[perm[pos[l]]][nB + pos[a]] = -DQ[a][l]
 template <class TD>
 __global__ void k_fill_dt(const DTJob* __restrict__ jobs, const int* __restrict__ idx) {
@@ -207,6 +272,22 @@ int transform_run(const TBlock* blocks, int count, const int* idx, int maxn, int
 }
 template int transform_run<double>(const TBlock*, int, const int*, int, int, cudaStream_t);
 template int transform_run<float>(const TBlock*, int, const int*, int, int, cudaStream_t);
+
+size_t basis_smem(int nmax, size_t elem) { return 4 * (size_t)nmax * nmax * elem; }
+
+template <class TD>
+int basis_run(const XRow* rows, int nrows, const XSub* subs, const XBlock* blks, int nmax, cudaStream_t st) {
+    if (nrows <= 0) return BDDC_OK;
+    const size_t smem = basis_smem(nmax, sizeof(TD));
+    if (smem > 200 * 1024) return BDDC_EINVAL;
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_basis<TD, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_basis<TD, TD><<<nrows, TH, smem, st>>>(rows, subs, blks, nmax);
+    bddc_note_launches(1);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+template int basis_run<double>(const XRow*, int, const XSub*, const XBlock*, int, cudaStream_t);
+template int basis_run<float>(const XRow*, int, const XSub*, const XBlock*, int, cudaStream_t);
 
 template <class TD>
 int fill_dt_run(const DTJob* jobs, int count, const int* idx, cudaStream_t st) {

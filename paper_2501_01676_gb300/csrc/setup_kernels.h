@@ -57,6 +57,32 @@ struct ExtractJob {
     long long cld;
 };
 
+// Change of basis by blocks: for one subdomain the output is
+//   dst[perm[pX[l]]][perm[pY[m]]] = sum_{a,b} QX[a][l] S[pX[a]][pY[b]] QY[b][m]
+// over all pairs of blocks (X, Y) of the subdomain (S or its symmetric part);
+// a block without Q is the identity (several identity entities may share one).
+struct XBlock {
+    int n;
+    const int* pos;         // n local interface positions (device)
+    const double* Q;        // n x n row-major, columns = new basis; NULL = identity
+};
+struct XSub {
+    const double* src;      // packed S^(i) (FP64)
+    long long sld;
+    int sym;
+    int nblk, blk_off;      // the subdomain's blocks in the block table
+    const int* perm;        // n_B entries: transformed coordinate -> output index (-1: drop)
+    void* dst;
+    long long dld;
+};
+struct XRow {               // one CTA: the rows of one block of one subdomain
+    int sub, blk;
+};
+
+template <class TD>
+int basis_run(const XRow* rows, int nrows, const XSub* subs, const XBlock* blks, int nmax, cudaStream_t st);
+size_t basis_smem(int nmax, size_t elem);
+
 template <class TS, class TD>
 int copy_blocks_run(const CopyJob* jobs, int count, int ychunks, cudaStream_t st);
 template <class TD>

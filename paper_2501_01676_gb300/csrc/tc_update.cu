@@ -2,7 +2,8 @@
 //
 // C[r0:r0+128, c0:c0+128] -= L21[r0:r0+128, 0:K] * U12[0:K, c0:c0+128]   (K = panel width)
 //
-// One CTA (4 warps) per 128 x 128 tile: the threads stage the FP32 operands in
+// One CTA (4 warps) per 128 x 128 tile; K (the panel width, up to 128) is
+// consumed 32 at a time: the threads stage the FP32 operands in
 // shared memory split into TF32 high and low parts (x = hi + lo, both exactly
 // representable in TF32), laid out as K-major "core matrices" (8 rows x 16
 // bytes, no swizzle); one elected thread issues tcgen05.mma kind::tf32 with
@@ -12,6 +13,8 @@
 // accumulator lanes with tcgen05.ld and subtracts them from C.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "bddc_internal.h"
 
@@ -107,7 +110,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // One 128 x 128 tile: C[0:nr, 0:nc] (row stride ldc) -= A[0:nr, 0:K] * B[0:K, 0:nc]
-// A row-major (lda), B row-major K x N (ldb).  Returns through *err on a wait timeout.
+// A row-major (lda), B row-major K x N (ldb).  K is consumed in chunks of KMAX:
+// stage the chunk, issue its MMAs, wait for them (the next chunk overwrites the
+// operand buffers).  Returns through *err on a wait timeout.
 __device__ void tc_tile(const float* __restrict__ A, long long lda, const float* __restrict__ B, long long ldb,
                         float* __restrict__ C, long long ldc, int nr, int nc, int K, unsigned char* smem,
                         uint64_t* mbar, uint32_t* tmem_slot, int* err) {
@@ -125,65 +130,75 @@ __device__ void tc_tile(const float* __restrict__ A, long long lda, const float*
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
     }
-    stage(A, lda, nr, K, a_hi, a_lo, false);
-    stage(B, ldb, nc, K, b_hi, b_lo, true);
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    if (threadIdx.x == 0) {
-        const uint32_t idesc = instr_desc(TM, TN);
-        const uint32_t lbo = CORE_BYTES;                     // next core matrix along K
-        const uint32_t sbo = (KMAX / 4) * CORE_BYTES;        // next 8-row group along M / N
-        int acc = 0;
-        for (int kk = 0; kk < (K + 7) / 8; ++kk) {
-            const uint32_t koff = kk * 2 * CORE_BYTES;       // 8 TF32 = two core matrices along K
-            const uint64_t ah = smem_desc(smem_u32(a_hi) + koff, lbo, sbo);
-            const uint64_t al = smem_desc(smem_u32(a_lo) + koff, lbo, sbo);
-            const uint64_t bh = smem_desc(smem_u32(b_hi) + koff, lbo, sbo);
-            const uint64_t bl = smem_desc(smem_u32(b_lo) + koff, lbo, sbo);
-            mma_tf32(tmem, ah, bh, idesc, acc);
-            acc = 1;
-            mma_tf32(tmem, ah, bl, idesc, 1);
-            mma_tf32(tmem, al, bh, idesc, 1);
+    bool ok = true;
+    int chunk = 0;
+    for (int k0 = 0; k0 < K && ok; k0 += KMAX, ++chunk) {
+        const int kw = min(KMAX, K - k0);
+        stage(A + k0, lda, nr, kw, a_hi, a_lo, false);
+        stage(B + (long long)k0 * ldb, ldb, nc, kw, b_hi, b_lo, true);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (threadIdx.x == 0) {
+            const uint32_t idesc = instr_desc(TM, TN);
+            const uint32_t lbo = CORE_BYTES;                     // next core matrix along K
+            const uint32_t sbo = (KMAX / 4) * CORE_BYTES;        // next 8-row group along M / N
+            for (int kk = 0; kk < (kw + 7) / 8; ++kk) {
+                const uint32_t koff = kk * 2 * CORE_BYTES;       // 8 TF32 = two core matrices along K
+                const uint64_t ah = smem_desc(smem_u32(a_hi) + koff, lbo, sbo);
+                const uint64_t al = smem_desc(smem_u32(a_lo) + koff, lbo, sbo);
+                const uint64_t bh = smem_desc(smem_u32(b_hi) + koff, lbo, sbo);
+                const uint64_t bl = smem_desc(smem_u32(b_lo) + koff, lbo, sbo);
+                mma_tf32(tmem, ah, bh, idesc, (chunk > 0 || kk > 0) ? 1 : 0);
+                mma_tf32(tmem, ah, bl, idesc, 1);
+                mma_tf32(tmem, al, bh, idesc, 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(mbar)));
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         smem_u32(mbar)));
-    }
-    // bounded wait for the MMAs (phase 0)
-    {
+        // bounded wait for this chunk's MMAs (mbarrier phase = chunk parity)
         uint32_t done = 0;
-        long long it = 0;
-        while (!done && it < WAIT_LIMIT) {
+        long long itn = 0;
+        const uint32_t parity = (uint32_t)(chunk & 1);
+        while (!done && itn < WAIT_LIMIT) {
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
-                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                 "selp.u32 %0, 1, 0, p;\n\t}\n"
                 : "=r"(done)
-                : "r"(smem_u32(mbar)));
-            ++it;
+                : "r"(smem_u32(mbar)), "r"(parity));
+            ++itn;
         }
-        if (!done) atomicOr(err, ERR_TIMEOUT_TC);
+        if (!done) {
+            atomicOr(err, ERR_TIMEOUT_TC);
+            ok = false;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (done) {
-            // warp w owns accumulator lanes (rows) 32w .. 32w+31; each 32 x 32 block goes
-            // through shared memory (the operand buffers are free now) so that the lanes
-            // update 32 consecutive columns of one row at a time (coalesced)
-            float* T = reinterpret_cast<float*>(smem) + warp * 32 * 33;
-            for (int c0 = 0; c0 < TN; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+        // every thread has seen the phase complete before the buffers are restaged
+        __syncthreads();
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    }
+    if (ok && K > 0) {
+        // warp w owns accumulator lanes (rows) 32w .. 32w+31; each 32 x 32 block goes
+        // through shared memory (the operand buffers are free now) so that the lanes
+        // update 32 consecutive columns of one row at a time (coalesced)
+        float* Tt = reinterpret_cast<float*>(smem) + warp * 32 * 33;
+        for (int c0 = 0; c0 < TN; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) T[lane * 33 + j] = v[j];
-                __syncwarp();
-                const int col = c0 + lane;
-                for (int r = 0; r < 32; ++r) {
-                    const int row = warp * 32 + r;
-                    if (row < nr && col < nc) C[(long long)row * ldc + col] -= T[r * 33 + lane];
-                }
-                __syncwarp();
+            for (int j = 0; j < 32; ++j) Tt[lane * 33 + j] = v[j];
+            __syncwarp();
+            const int col = c0 + lane;
+            for (int r = 0; r < 32; ++r) {
+                const int row = warp * 32 + r;
+                if (row < nr && col < nc) C[(long long)row * ldc + col] -= Tt[r * 33 + lane];
             }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -199,31 +214,22 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_selftest(const float* A, cons
     tc_tile(A, KMAX, B, TN, C, TN, nr, nc, K, tsm, &mbar, &tslot, err);
 }
 
-template <int NB>
-__global__ void __launch_bounds__(TC_THREADS) k_tc_update(const EngItem<float>* __restrict__ items, int p,
-                                                          const float* __restrict__ dscr, int* err) {
+__global__ void __launch_bounds__(TC_THREADS) k_tc_update(const EngItem<float>* __restrict__ items, int p, int nb,
+                                                          int nt, int* err) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     const EngItem<float> it = items[blockIdx.x];
     if (p >= it.k) return;
-    const int w = min(NB, it.k - p);
-    const int n = it.n, ld = it.ld;
+    const int w = min(nb, it.k - p);
+    const int n = it.n;
+    const long long ld = it.ld;
     const int m0 = p + w;
-    const int mrem = n - m0;
-    const int nt = (mrem + TM - 1) / TM;
     const int y = blockIdx.y;
-    float* A = it.a;
-    if (y == 0) {
-        const float* ds = dscr + (long long)blockIdx.x * NB * NB;
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int r = wid; r < w; r += TC_THREADS / 32)
-            if (lane < w) A[(long long)(p + r) * ld + p + lane] = ds[r * w + lane];
-        return;
-    }
-    if (y > nt * nt) return;
-    const int ti = (y - 1) / nt, tj = (y - 1) - ti * nt;
+    const int ti = y / nt, tj = y - ti * nt;
     const int r0 = m0 + ti * TM, c0 = m0 + tj * TN;
+    if (r0 >= n || c0 >= n) return;
+    float* A = it.a;
     tc_tile(A + (long long)r0 * ld + p, ld, A + (long long)p * ld + c0, ld, A + (long long)r0 * ld + c0, ld,
             min(TM, n - r0), min(TN, n - c0), w, tsm, &mbar, &tslot, err);
 }
@@ -242,12 +248,11 @@ int tc_selftest_run(const float* A, const float* B, float* C, int nr, int nc, in
     return BDDC_OK;
 }
 
-int tc_update_run(const EngItem<float>* items_dev, int count, int maxn, int p, const float* dscr, int* err,
-                  cudaStream_t st) {
-    const int mrem = maxn - p;
+int tc_update_run(const EngItem<float>* items_dev, int count, int maxn, int p, int nb, int* err, cudaStream_t st) {
+    const int mrem = std::max(maxn - p, 1);
     const int nt = (mrem + TM - 1) / TM;
-    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_tc_update<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    k_tc_update<32><<<dim3(count, 1 + nt * nt), TC_THREADS, TC_SMEM, st>>>(items_dev, p, dscr, err);
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    k_tc_update<<<dim3(count, nt * nt), TC_THREADS, TC_SMEM, st>>>(items_dev, p, nb, nt, err);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
