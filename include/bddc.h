@@ -133,7 +133,9 @@ void bddc_default_opts(bddc_opts* o);
  * complements S^(i) (Sect. 3), deluxe scaling, face GEPs, new edge GEPs,
  * constrained local solvers, coarse matrix and its FP64 inverse).
  * tol_eig > 0 overrides opts->theta_E.  stream: a cudaStream_t or NULL for
- * the legacy default stream.  On success *out owns all device memory. */
+ * the legacy default stream.  On success *out owns all device memory.
+ * Subdomains with more than 2048 interior dofs (a slab of more than 14
+ * elements in every direction) are rejected with BDDC_EINVAL. */
 int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs,
                const bddc_partition* part, double tol_eig,
                const bddc_opts* opts, void* stream, bddc_ctx** out);

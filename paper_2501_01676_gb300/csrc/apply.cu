@@ -91,6 +91,29 @@ __global__ void __launch_bounds__(GEMV_THREADS) k_gemv(const T* __restrict__ poo
         double* outc = out + (long long)c * out_ld;
         for (int q = t; q < ncols; q += GEMV_THREADS) xs[q] = (T)inc[iidx[it.col0 + q]];
         __syncthreads();
+        if (((it.moff + it.col0) % VW) != 0 || (it.ld % VW) != 0) {
+            // rows not 16-byte aligned: scalar loads, several in flight per lane
+            for (int r = it.row0 + 2 * wid; r < rend; r += 2 * (GEMV_THREADS / 32)) {
+                const bool two = r + 1 < rend;
+                const T* row0 = M + (long long)r * it.ld;
+                const T* row1 = M + (long long)(two ? r + 1 : r) * it.ld;
+                T acc0 = 0, acc1 = 0;
+#pragma unroll 4
+                for (int q = lane; q < ncols; q += 32) {
+                    const T x = xs[q];
+                    acc0 += __ldg(row0 + q) * x;
+                    if (two) acc1 += __ldg(row1 + q) * x;
+                }
+                acc0 = warp_sum(acc0);
+                acc1 = warp_sum(acc1);
+                if (lane == 0) {
+                    atomicAdd(&outc[oidx[r]], (double)acc0);
+                    if (two) atomicAdd(&outc[oidx[r + 1]], (double)acc1);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         for (int r = it.row0 + 2 * wid; r < rend; r += 2 * (GEMV_THREADS / 32)) {
             const bool two = r + 1 < rend;
             const VT* rv0 = reinterpret_cast<const VT*>(M + (long long)r * it.ld);
@@ -212,7 +235,7 @@ template int gemv_run<float>(const float*, const GemvItem*, int, const int*, con
 namespace {
 
 constexpr int TRI_THREADS = 256;
-constexpr int TRI_MAXN = 2048;
+constexpr int TRI_MAXN = BDDC_MAX_INTERIOR;
 
 struct TriItem {
     long long aoff;    // matrix offset in the factor pool
@@ -240,6 +263,7 @@ __device__ __forceinline__ void warp_rows_dot(const T* __restrict__ A, long long
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < R; ++j) s[j] = (T)0;
+#pragma unroll 4
     for (int c = c0 + lane; c < c1; c += 32) {
         const T xv = x[c];
 #pragma unroll
@@ -311,39 +335,31 @@ __device__ void bwd_upper(const T* A, int ld, int nI, T* y) {
     }
 }
 
+// Forward half of the condensation: y = L_II^{-1} f_I, stored negated (the
+// batched GEMV then adds L_BI (-y) to g, and recovery continues from it).
 template <class T>
 __global__ void __launch_bounds__(TRI_THREADS) k_condense(const T* __restrict__ pool,
                                                           const TriItem* __restrict__ items,
                                                           const int* __restrict__ lists,
                                                           const double* __restrict__ F,
-                                                          double* __restrict__ g,
                                                           double* __restrict__ ystore, int nrhs,
-                                                          long long ldF, long long ldG,
-                                                          long long ldY) {
+                                                          long long ldF, long long ldY) {
     const TriItem it = items[blockIdx.x];
     __shared__ T y[TRI_MAXN];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int t = threadIdx.x;
     const T* A = pool + it.aoff;
     const int* dofs = lists + it.dof_off;
-    const int* gidx = lists + it.gidx_off;
-    const int nB = it.n - it.nI;
     for (int c = 0; c < nrhs; ++c) {
         for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = (T)F[c * ldF + dofs[q]];
         __syncthreads();
         fwd_unit_lower<T>(A, it.ld, it.nI, y);
-        // g -= L_BI y: eight rows per warp at a time
-        for (int rb = 8 * wid; rb < nB; rb += 8 * (TRI_THREADS / 32)) {
-            T s[8];
-            warp_rows_dot<T, 8>(A + (long long)it.nI * it.ld, it.ld, rb, nB, 0, it.nI, y, s);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (lane == j && rb + j < nB) atomicAdd(&g[c * ldG + gidx[rb + j]], -(double)s[j]);
-        }
-        for (int q = t; q < it.nI; q += TRI_THREADS) ystore[c * ldY + it.yoff + q] = (double)y[q];
+        for (int q = t; q < it.nI; q += TRI_THREADS) ystore[c * ldY + it.yoff + q] = -(double)y[q];
         __syncthreads();
     }
 }
 
+// Backward half of the recovery: ystore holds -(y - U_IB u_B) (the batched GEMV
+// has added U_IB u_B to -y); u_I = U_II^{-1} (y - U_IB u_B), u_B copied.
 template <class T>
 __global__ void __launch_bounds__(TRI_THREADS) k_recover(const T* __restrict__ pool,
                                                          const TriItem* __restrict__ items,
@@ -355,24 +371,13 @@ __global__ void __launch_bounds__(TRI_THREADS) k_recover(const T* __restrict__ p
                                                          long long ldY) {
     const TriItem it = items[blockIdx.x];
     __shared__ T y[TRI_MAXN];
-    __shared__ T ub[TRI_MAXN];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int t = threadIdx.x;
     const T* A = pool + it.aoff;
     const int* dofs = lists + it.dof_off;
     const int* gidx = lists + it.gidx_off;
     const int nB = it.n - it.nI;
     for (int c = 0; c < nrhs; ++c) {
-        for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = (T)ystore[c * ldY + it.yoff + q];
-        for (int q = t; q < nB; q += TRI_THREADS) ub[q] = (T)uG[c * ldG + gidx[q]];
-        __syncthreads();
-        // y -= U_IB u_B: eight rows per warp at a time
-        for (int rb = 8 * wid; rb < it.nI; rb += 8 * (TRI_THREADS / 32)) {
-            T s[8];
-            warp_rows_dot<T, 8>(A + it.nI, it.ld, rb, it.nI, 0, nB, ub, s);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (lane == j && rb + j < it.nI) y[rb + j] -= s[j];
-        }
+        for (int q = t; q < it.nI; q += TRI_THREADS) y[q] = (T)(-ystore[c * ldY + it.yoff + q]);
         __syncthreads();
         bwd_upper<T>(A, it.ld, it.nI, y);
         for (int q = t; q < it.nI; q += TRI_THREADS) u[c * ldU + dofs[q]] = (double)y[q];
@@ -391,20 +396,22 @@ struct TriBatch {
 template <class T>
 int condense_run(const T* pool, const void* items, int count, const int* lists, const double* F,
                  double* g, double* ystore, int nrhs, long long ldF, long long ldG, long long ldY,
-                 cudaStream_t st) {
+                 const GemvItem* ci, int nci, double ci_bytes, cudaStream_t st) {
     ktimer_begin(KT_TRI, st);
-    k_condense<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, F, g, ystore,
-                                                 nrhs, ldF, ldG, ldY);
+    k_condense<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, F, ystore, nrhs, ldF, ldY);
     ktimer_end(KT_TRI, st, 0.0, 0.0);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
-    return BDDC_OK;
+    // g += L_BI (-y)
+    return gemv_run<T>(pool, ci, nci, lists, ystore, g, 0, nrhs, (int)ldY, (int)ldG, st, nullptr, ci_bytes);
 }
 
 template <class T>
 int recover_run(const T* pool, const void* items, int count, const int* lists, const double* uG,
-                const double* ystore, double* u, int nrhs, long long ldG, long long ldU,
-                long long ldY, cudaStream_t st) {
+                double* ystore, double* u, int nrhs, long long ldG, long long ldU,
+                long long ldY, const GemvItem* ri, int nri, double ri_bytes, cudaStream_t st) {
+    // -y += U_IB u_B
+    BDDC_TRY(gemv_run<T>(pool, ri, nri, lists, uG, ystore, 0, nrhs, (int)ldG, (int)ldY, st, nullptr, ri_bytes));
     ktimer_begin(KT_TRI, st);
     k_recover<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, uG, ystore, u,
                                                 nrhs, ldG, ldU, ldY);
@@ -427,17 +434,14 @@ void tri_item_fill(void* dst, long long aoff, int n, int nI, int ld, int dof_off
     t->yoff = yoff;
 }
 
-template int condense_run<double>(const double*, const void*, int, const int*, const double*,
-                                  double*, double*, int, long long, long long, long long,
-                                  cudaStream_t);
-template int condense_run<float>(const float*, const void*, int, const int*, const double*, double*,
-                                 double*, int, long long, long long, long long, cudaStream_t);
-template int recover_run<double>(const double*, const void*, int, const int*, const double*,
-                                 const double*, double*, int, long long, long long, long long,
-                                 cudaStream_t);
-template int recover_run<float>(const float*, const void*, int, const int*, const double*,
-                                const double*, double*, int, long long, long long, long long,
-                                cudaStream_t);
+template int condense_run<double>(const double*, const void*, int, const int*, const double*, double*, double*,
+                                  int, long long, long long, long long, const GemvItem*, int, double, cudaStream_t);
+template int condense_run<float>(const float*, const void*, int, const int*, const double*, double*, double*,
+                                 int, long long, long long, long long, const GemvItem*, int, double, cudaStream_t);
+template int recover_run<double>(const double*, const void*, int, const int*, const double*, double*, double*,
+                                 int, long long, long long, long long, const GemvItem*, int, double, cudaStream_t);
+template int recover_run<float>(const float*, const void*, int, const int*, const double*, double*, double*,
+                                int, long long, long long, long long, const GemvItem*, int, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // small vector kernels

@@ -11,38 +11,49 @@
 // |beta|_{K,inf} is the maximum over the 8 vertices and the 27 Gauss points.
 // h_K = sqrt(hx^2 + hy^2 + hz^2).  Entry (i,j) = a(phi_j, phi_i).
 //
-// One block of 64 threads per element, one thread per matrix entry.  The
-// element matrix is scattered (FP64 atomics) into
+// 64 threads per element (four elements per CTA), one thread per matrix
+// entry.  The element matrix is scattered (FP64 atomics) into
 //   * the dense local matrix A^(s) of its subdomain (FP64 or FP32 copy),
 //   * the global 27-point FP64 stencil of the free dofs (refinement residual),
 //   * the global load vector.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "bddc_internal.h"
 
 namespace {
 
-struct AsmParams {
-    int E[3];
-    double h[3];
-    double tau, c;
-    double K0[64];        // reference stiffness int grad phi_j . grad phi_i on an h-box
-    double M0[64];        // reference mass
+// Reference tables of the uniform brick (one per context, in device memory).
+struct AsmTables {
     double N[27 * 8];     // shape values at the Gauss points
     double G[27 * 8 * 3]; // physical gradients
     double w[27];         // weights * |J|
     double wN[27 * 8];    // w_q N_a(x_q)
+    double K0[64];        // int grad phi_j . grad phi_i
+    double M0[64];        // int phi_j phi_i
+};
+struct AsmScalars {
+    int E[3];
+    double h[3];
+    double tau, c;
 };
 
-__constant__ AsmParams cP;
+constexpr int ASM_EPB = 4;                 // elements per CTA (64 threads each)
+constexpr int ASM_THREADS = 64 * ASM_EPB;
 
-__device__ __forceinline__ int dof_of(int ix, int iy, int iz) {
-    if (ix <= 0 || iy <= 0 || iz <= 0 || ix >= cP.E[0] || iy >= cP.E[1] || iz >= cP.E[2]) return -1;
-    return (ix - 1) + (cP.E[0] - 1) * ((iy - 1) + (cP.E[1] - 1) * (iz - 1));
+__device__ __forceinline__ int dof_of(const AsmScalars& P, int ix, int iy, int iz) {
+    if (ix <= 0 || iy <= 0 || iz <= 0 || ix >= P.E[0] || iy >= P.E[1] || iz >= P.E[2]) return -1;
+    return (ix - 1) + (P.E[0] - 1) * ((iy - 1) + (P.E[1] - 1) * (iz - 1));
 }
 
+// Persistent CTAs of four 64-thread element slots; the reference tables are
+// read once per CTA into shared memory (divergent table reads then cost no
+// serialisation).  Per element: nodal data (8 threads), Gauss-point data (27
+// threads), the max |beta| by warp shuffles, then one thread per entry (i, j).
 template <class TA>
-__global__ void __launch_bounds__(64) k_assemble(
+__global__ void __launch_bounds__(ASM_THREADS) k_assemble(
+    AsmScalars P, const AsmTables* __restrict__ tab, int nelem,
     const double* __restrict__ nu_elem, const double* __restrict__ beta_node,
     const double* __restrict__ f_node, const double* __restrict__ divb_node, double3 beta_const,
     const int* __restrict__ slab_of_x, const int* __restrict__ slab_of_y,
@@ -51,123 +62,128 @@ __global__ void __launch_bounds__(64) k_assemble(
     const int* __restrict__ box0, const int* __restrict__ boxn,
     TA* __restrict__ Aloc, const long long* __restrict__ a_off, const int* __restrict__ a_ld,
     double* __restrict__ stencil, double* __restrict__ F) {
-    const int e = blockIdx.x;
-    const int t = threadIdx.x;
-    const int Ex = cP.E[0], Ey = cP.E[1];
-    const int ex = e % Ex, ey = (e / Ex) % Ey, ez = e / (Ex * Ey);
-    __shared__ double sb[8][3], sf[8], sdv[8];
-    __shared__ double bg[27][8], Lp[27][8], wLp[27][8], wf[27], cq[27];
-    __shared__ double P[8][9];
-    __shared__ double bmax2[64];
-    __shared__ double CK;
-    if (t < 8) {
-        int ix = ex + (t & 1), iy = ey + ((t >> 1) & 1), iz = ez + ((t >> 2) & 1);
-        long long nd = ix + (long long)(Ex + 1) * (iy + (long long)(Ey + 1) * iz);
-        if (beta_node) {
-            sb[t][0] = beta_node[3 * nd];
-            sb[t][1] = beta_node[3 * nd + 1];
-            sb[t][2] = beta_node[3 * nd + 2];
-        } else {
-            sb[t][0] = beta_const.x;
-            sb[t][1] = beta_const.y;
-            sb[t][2] = beta_const.z;
-        }
-        sf[t] = f_node ? f_node[nd] : 0.0;
-        sdv[t] = divb_node ? divb_node[nd] : 0.0;
+    __shared__ AsmTables tb;
+    __shared__ double sb[ASM_EPB][8][3], sf[ASM_EPB][8], sdv[ASM_EPB][8];
+    __shared__ double bg[ASM_EPB][27][8], Lp[ASM_EPB][27][8], wLp[ASM_EPB][27][8];
+    __shared__ double wf[ASM_EPB][27], cq[ASM_EPB][27];
+    __shared__ double Pm[ASM_EPB][8][9];
+    __shared__ double bmx[ASM_EPB][2];
+    __shared__ double CKs[ASM_EPB];
+    {
+        const double* src = reinterpret_cast<const double*>(tab);
+        double* dst = reinterpret_cast<double*>(&tb);
+        for (int q = threadIdx.x; q < (int)(sizeof(AsmTables) / sizeof(double)); q += ASM_THREADS) dst[q] = src[q];
     }
     __syncthreads();
-    // per Gauss point q (thread q): beta, f, c~, beta.grad phi_a, L phi_a, w_q L phi_a
-    double bm = 0.0;
-    if (t < 27) {
-        double b0 = 0, b1 = 0, b2 = 0, ff = 0, dd = 0;
-        for (int a = 0; a < 8; ++a) {
-            double n = cP.N[t * 8 + a];
-            b0 += n * sb[a][0];
-            b1 += n * sb[a][1];
-            b2 += n * sb[a][2];
-            ff += n * sf[a];
-            dd += n * sdv[a];
+    const int slot = threadIdx.x >> 6, t = threadIdx.x & 63, lane = threadIdx.x & 31;
+    const int Ex = P.E[0], Ey = P.E[1];
+    const double hK = sqrt(P.h[0] * P.h[0] + P.h[1] * P.h[1] + P.h[2] * P.h[2]);
+    for (int e0 = blockIdx.x * ASM_EPB; e0 < nelem; e0 += gridDim.x * ASM_EPB) {
+        const int e = e0 + slot;
+        const bool act = e < nelem;
+        const int ex = act ? e % Ex : 0, ey = act ? (e / Ex) % Ey : 0, ez = act ? e / (Ex * Ey) : 0;
+        if (act && t < 8) {
+            const int ix = ex + (t & 1), iy = ey + ((t >> 1) & 1), iz = ez + ((t >> 2) & 1);
+            const long long nd = ix + (long long)(Ex + 1) * (iy + (long long)(Ey + 1) * iz);
+            if (beta_node) {
+                sb[slot][t][0] = beta_node[3 * nd];
+                sb[slot][t][1] = beta_node[3 * nd + 1];
+                sb[slot][t][2] = beta_node[3 * nd + 2];
+            } else {
+                sb[slot][t][0] = beta_const.x;
+                sb[slot][t][1] = beta_const.y;
+                sb[slot][t][2] = beta_const.z;
+            }
+            sf[slot][t] = f_node ? f_node[nd] : 0.0;
+            sdv[slot][t] = divb_node ? divb_node[nd] : 0.0;
         }
-        const double w = cP.w[t];
-        wf[t] = w * ff;
-        cq[t] = w * (cP.c - 0.5 * dd);
-        for (int a = 0; a < 8; ++a) {
-            const double* g = &cP.G[(t * 8 + a) * 3];
-            double v = b0 * g[0] + b1 * g[1] + b2 * g[2];
-            double l = v + cP.c * cP.N[t * 8 + a];
-            bg[t][a] = v;
-            Lp[t][a] = l;
-            wLp[t][a] = w * l;
+        __syncthreads();
+        // Gauss point q = t: beta, f, c~, beta.grad phi_a, L phi_a, w_q L phi_a
+        double bm = 0.0;
+        if (act && t < 27) {
+            double b0 = 0, b1 = 0, b2 = 0, ff = 0, dd = 0;
+            for (int a = 0; a < 8; ++a) {
+                const double n = tb.N[t * 8 + a];
+                b0 += n * sb[slot][a][0];
+                b1 += n * sb[slot][a][1];
+                b2 += n * sb[slot][a][2];
+                ff += n * sf[slot][a];
+                dd += n * sdv[slot][a];
+            }
+            const double w = tb.w[t];
+            wf[slot][t] = w * ff;
+            cq[slot][t] = w * (P.c - 0.5 * dd);
+            for (int a = 0; a < 8; ++a) {
+                const double* g = &tb.G[(t * 8 + a) * 3];
+                const double v = b0 * g[0] + b1 * g[1] + b2 * g[2];
+                const double l = v + P.c * tb.N[t * 8 + a];
+                bg[slot][t][a] = v;
+                Lp[slot][t][a] = l;
+                wLp[slot][t][a] = w * l;
+            }
+            bm = b0 * b0 + b1 * b1 + b2 * b2;
+        } else if (act && t >= 32 && t < 40) {
+            const int a = t - 32;
+            bm = sb[slot][a][0] * sb[slot][a][0] + sb[slot][a][1] * sb[slot][a][1] + sb[slot][a][2] * sb[slot][a][2];
         }
-        bm = b0 * b0 + b1 * b1 + b2 * b2;
-    } else if (t >= 32 && t < 40) {
-        int a = t - 32;
-        bm = sb[a][0] * sb[a][0] + sb[a][1] * sb[a][1] + sb[a][2] * sb[a][2];
-    }
-    bmax2[t] = bm;
-    __syncthreads();
-    if (t == 0) {
-        double m2 = 0.0;
-        for (int q = 0; q < 64; ++q) m2 = fmax(m2, bmax2[q]);
-        double bmax = sqrt(m2);
-        double hK = sqrt(cP.h[0] * cP.h[0] + cP.h[1] * cP.h[1] + cP.h[2] * cP.h[2]);
-        double nu = nu_elem[e];
-        double PK = hK * bmax / (2.0 * nu);
-        CK = (PK >= 1.0) ? cP.tau * hK / (2.0 * bmax) : cP.tau * hK * hK / (4.0 * nu);
-    }
-    const int i = t >> 3, j = t & 7;      // test i, trial j
-    // GLS part sum_q w L phi_j L phi_i and P_ij = sum_q w N_i beta.grad phi_j
-    double gls = 0.0, pij = 0.0, reac = 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+        if (lane == 0) bmx[slot][t >> 5] = bm;
+        __syncthreads();
+        // GLS part sum_q w L phi_j L phi_i and P_ij = sum_q w N_i beta.grad phi_j
+        const int i = t >> 3, j = t & 7;      // test i, trial j
+        double gls = 0.0, pij = 0.0, reac = 0.0, CK = 0.0;
+        if (act) {
+            const double bmax = sqrt(fmax(bmx[slot][0], bmx[slot][1]));
+            const double nu = nu_elem[e];
+            const double PK = hK * bmax / (2.0 * nu);
+            CK = (PK >= 1.0) ? P.tau * hK / (2.0 * bmax) : P.tau * hK * hK / (4.0 * nu);
 #pragma unroll 9
-    for (int q = 0; q < 27; ++q) {
-        gls += wLp[q][j] * Lp[q][i];
-        pij += cP.wN[q * 8 + i] * bg[q][j];
+            for (int q = 0; q < 27; ++q) {
+                gls += wLp[slot][q][j] * Lp[slot][q][i];
+                pij += tb.wN[q * 8 + i] * bg[slot][q][j];
+            }
+            if (divb_node) {
+                for (int q = 0; q < 27; ++q) reac += cq[slot][q] * tb.N[q * 8 + i] * tb.N[q * 8 + j];
+            } else {
+                reac = P.c * tb.M0[i * 8 + j];
+            }
+            Pm[slot][i][j] = pij;
+        }
+        __syncthreads();
+        if (act) {
+            const double acc = nu_elem[e] * tb.K0[i * 8 + j] + CK * gls + reac + 0.5 * (pij - Pm[slot][j][i]);
+            double fl = 0.0;
+            if (j == 0)
+                for (int q = 0; q < 27; ++q) fl += wf[slot][q] * (tb.N[q * 8 + i] + CK * Lp[slot][q][i]);
+            // node indices of the entry
+            const int ix = ex + (i & 1), iy = ey + ((i >> 1) & 1), iz = ez + ((i >> 2) & 1);
+            const int jx = ex + (j & 1), jy = ey + ((j >> 1) & 1), jz = ez + ((j >> 2) & 1);
+            const int di = dof_of(P, ix, iy, iz), dj = dof_of(P, jx, jy, jz);
+            if (di >= 0 && dj >= 0) {
+                const int o = (jx - ix + 1) + 3 * (jy - iy + 1) + 9 * (jz - iz + 1);
+                atomicAdd(&stencil[(long long)di * 27 + o], acc);
+                // local matrix of the owning subdomain
+                const int s = slab_of_x[ex] + nsx * (slab_of_y[ey] + nsy * slab_of_z[ez]);
+                const int* b0 = &box0[3 * s];
+                const int* bn = &boxn[3 * s];
+                const int li = lut[lut_off[s] + (ix - b0[0]) + bn[0] * ((iy - b0[1]) + bn[1] * (iz - b0[2]))];
+                const int lj = lut[lut_off[s] + (jx - b0[0]) + bn[0] * ((jy - b0[1]) + bn[1] * (jz - b0[2]))];
+                atomicAdd(&Aloc[a_off[s] + (long long)li * a_ld[s] + lj], (TA)acc);
+            }
+            if (j == 0 && di >= 0) atomicAdd(&F[di], fl);
+        }
+        __syncthreads();       // the slot's shared data is rewritten by the next element
     }
-    if (divb_node) {
-        for (int q = 0; q < 27; ++q) reac += cq[q] * cP.N[q * 8 + i] * cP.N[q * 8 + j];
-    } else {
-        reac = cP.c * cP.M0[i * 8 + j];
-    }
-    P[i][j] = pij;
-    __syncthreads();
-    const double acc = nu_elem[e] * cP.K0[i * 8 + j] + CK * gls + reac + 0.5 * (pij - P[j][i]);
-    double fl = 0.0;
-    if (j == 0)
-        for (int q = 0; q < 27; ++q) fl += wf[q] * (cP.N[q * 8 + i] + CK * Lp[q][i]);
-    // node indices of the entry
-    const int ix = ex + (i & 1), iy = ey + ((i >> 1) & 1), iz = ez + ((i >> 2) & 1);
-    const int jx = ex + (j & 1), jy = ey + ((j >> 1) & 1), jz = ez + ((j >> 2) & 1);
-    const int di = dof_of(ix, iy, iz), dj = dof_of(jx, jy, jz);
-    if (di >= 0 && dj >= 0) {
-        int o = (jx - ix + 1) + 3 * (jy - iy + 1) + 9 * (jz - iz + 1);
-        atomicAdd(&stencil[(long long)di * 27 + o], acc);
-        // local matrix of the owning subdomain
-        int s = slab_of_x[ex] + nsx * (slab_of_y[ey] + nsy * slab_of_z[ez]);
-        const int* b0 = &box0[3 * s];
-        const int* bn = &boxn[3 * s];
-        int li = lut[lut_off[s] + (ix - b0[0]) + bn[0] * ((iy - b0[1]) + bn[1] * (iz - b0[2]))];
-        int lj = lut[lut_off[s] + (jx - b0[0]) + bn[0] * ((jy - b0[1]) + bn[1] * (jz - b0[2]))];
-        atomicAdd(&Aloc[a_off[s] + (long long)li * a_ld[s] + lj], (TA)acc);
-    }
-    if (j == 0 && di >= 0) atomicAdd(&F[di], fl);
-}
-
-double host_N(int a, double x, double y, double z) {
-    double fx = (a & 1) ? x : 1 - x, fy = ((a >> 1) & 1) ? y : 1 - y, fz = ((a >> 2) & 1) ? z : 1 - z;
-    return fx * fy * fz;
 }
 
 }  // namespace
 
-// Fill the constant tables (Gauss rule, shape tables, reference stiffness).
-int assemble_init(const HostMesh& hm, double tau, double c) {
-    AsmParams P;
-    for (int d = 0; d < 3; ++d) {
-        P.E[d] = hm.E[d];
-        P.h[d] = hm.h[d];
-    }
-    P.tau = tau;
-    P.c = c;
+// The reference tables of the brick h[0] x h[1] x h[2]: 3-point Gauss rule per
+// direction, Q1 shape values and gradients, weights, stiffness and mass.
+int assemble_tables_bytes() { return (int)sizeof(AsmTables); }
+void assemble_tables(const HostMesh& hm, void* out) {
+    AsmTables& P = *reinterpret_cast<AsmTables*>(out);
     const double r = sqrt(3.0 / 5.0);
     const double xg[3] = {0.5 - 0.5 * r, 0.5, 0.5 + 0.5 * r};
     const double wg[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
@@ -205,36 +221,44 @@ int assemble_init(const HostMesh& hm, double tau, double c) {
             P.K0[i * 8 + j] = k0;
             P.M0[i * 8 + j] = m0;
         }
-    (void)host_N;
-    BDDC_CUDA_TRY(cudaMemcpyToSymbol(cP, &P, sizeof(P)));
-    return BDDC_OK;
 }
 
 template <class TA>
-int assemble_launch(const HostMesh& hm, const double* nu, const double* beta, const double* f,
-                    const double* divb, const double bconst[3], const int* slab_x, const int* slab_y,
-                    const int* slab_z, const int* lut, const long long* lut_off, const int* box0,
-                    const int* boxn, TA* Aloc, const long long* a_off, const int* a_ld,
-                    double* stencil, double* F, cudaStream_t st) {
+int assemble_launch(const HostMesh& hm, double tau, double c, const void* tables, const double* nu,
+                    const double* beta, const double* f, const double* divb, const double bconst[3],
+                    const int* slab_x, const int* slab_y, const int* slab_z, const int* lut,
+                    const long long* lut_off, const int* box0, const int* boxn, TA* Aloc,
+                    const long long* a_off, const int* a_ld, double* stencil, double* F, cudaStream_t st) {
+    AsmScalars P;
+    for (int d = 0; d < 3; ++d) {
+        P.E[d] = hm.E[d];
+        P.h[d] = hm.h[d];
+    }
+    P.tau = tau;
+    P.c = c;
     double3 bc = make_double3(bconst[0], bconst[1], bconst[2]);
-    k_assemble<TA><<<hm.nelem, 64, 0, st>>>(nu, beta, f, divb, bc, slab_x, slab_y, slab_z, hm.nsub[0],
-                                            hm.nsub[1], lut, lut_off, box0, boxn, Aloc, a_off, a_ld,
-                                            stencil, F);
+    int dev = 0, nsm = 0, occ = 0;
+    BDDC_CUDA_TRY(cudaGetDevice(&dev));
+    BDDC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_assemble<TA>, ASM_THREADS, 0));
+    const long long groups = ((long long)hm.nelem + ASM_EPB - 1) / ASM_EPB;
+    const int grid = (int)std::max(1LL, std::min(groups, (long long)nsm * std::max(occ, 1)));
+    k_assemble<TA><<<grid, ASM_THREADS, 0, st>>>(P, (const AsmTables*)tables, hm.nelem, nu, beta, f, divb, bc,
+                                                 slab_x, slab_y, slab_z, hm.nsub[0], hm.nsub[1], lut, lut_off,
+                                                 box0, boxn, Aloc, a_off, a_ld, stencil, F);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
-template int assemble_launch<double>(const HostMesh&, const double*, const double*, const double*,
-                                     const double*, const double*, const int*, const int*,
-                                     const int*, const int*, const long long*, const int*,
-                                     const int*, double*, const long long*, const int*, double*,
-                                     double*, cudaStream_t);
-template int assemble_launch<float>(const HostMesh&, const double*, const double*, const double*,
-                                    const double*, const double*, const int*, const int*,
-                                    const int*, const int*, const long long*, const int*,
-                                    const int*, float*, const long long*, const int*, double*,
-                                    double*, cudaStream_t);
+template int assemble_launch<double>(const HostMesh&, double, double, const void*, const double*, const double*,
+                                     const double*, const double*, const double*, const int*, const int*,
+                                     const int*, const int*, const long long*, const int*, const int*, double*,
+                                     const long long*, const int*, double*, double*, cudaStream_t);
+template int assemble_launch<float>(const HostMesh&, double, double, const void*, const double*, const double*,
+                                    const double*, const double*, const double*, const int*, const int*,
+                                    const int*, const int*, const long long*, const int*, const int*, float*,
+                                    const long long*, const int*, double*, double*, cudaStream_t);
 
 // Global FP64 residual r = F - A u with the 27-point stencil (refinement).
 __global__ void k_stencil_residual(const double* __restrict__ S, const double* __restrict__ u,

@@ -100,6 +100,10 @@ struct DevArena {                    // all device allocations of a context
     void release();
 };
 
+// Largest interior (dofs strictly inside one subdomain) the condense / recover
+// kernels hold in shared memory: 2048 = a 13^3 interior (H/h <= 13 per slab).
+constexpr int BDDC_MAX_INTERIOR = 2048;
+
 // Batched partial LU (Schur complement engine) item descriptor.
 template <class T>
 struct EngItem {

@@ -34,23 +34,27 @@
 #include "mlp.h"
 #include "setup_kernels.h"
 
-int assemble_init(const HostMesh& hm, double tau, double c);
+int assemble_tables_bytes();
+void assemble_tables(const HostMesh& hm, void* out);
 template <class TA>
-int assemble_launch(const HostMesh& hm, const double* nu, const double* beta, const double* f,
-                    const double* divb, const double bconst[3], const int* slab_x, const int* slab_y,
-                    const int* slab_z, const int* lut, const long long* lut_off, const int* box0,
-                    const int* boxn, TA* Aloc, const long long* a_off, const int* a_ld,
-                    double* stencil, double* F, cudaStream_t st);
+int assemble_launch(const HostMesh& hm, double tau, double c, const void* tables, const double* nu,
+                    const double* beta, const double* f, const double* divb, const double bconst[3],
+                    const int* slab_x, const int* slab_y, const int* slab_z, const int* lut,
+                    const long long* lut_off, const int* box0, const int* boxn, TA* Aloc,
+                    const long long* a_off, const int* a_ld, double* stencil, double* F, cudaStream_t st);
 int stencil_residual(const HostMesh& hm, const double* S, const double* u, const double* F, double* r,
                      int nrhs, cudaStream_t st);
+// Condensation g += f_B - A_BI A_II^{-1} f_I and interior recovery, each as one
+// triangular-solve kernel (CTA per subdomain) plus one batched GEMV over the
+// rectangular factor blocks (ci: L_BI, ri: U_IB).
 template <class T>
 int condense_run(const T* pool, const void* items, int count, const int* lists, const double* F,
                  double* g, double* ystore, int nrhs, long long ldF, long long ldG, long long ldY,
-                 cudaStream_t st);
+                 const GemvItem* ci, int nci, double ci_bytes, cudaStream_t st);
 template <class T>
 int recover_run(const T* pool, const void* items, int count, const int* lists, const double* uG,
-                const double* ystore, double* u, int nrhs, long long ldG, long long ldU, long long ldY,
-                cudaStream_t st);
+                double* ystore, double* u, int nrhs, long long ldG, long long ldU, long long ldY,
+                const GemvItem* ri, int nri, double ri_bytes, cudaStream_t st);
 size_t tri_item_size();
 void tri_item_fill(void* dst, long long aoff, int n, int nI, int ld, int dof_off, int gidx_off,
                    long long yoff);
@@ -206,6 +210,9 @@ struct bddc_ctx {
     // condense / recover
     void* tri = nullptr;
     int* tri_lists = nullptr;
+    GemvItem *itCI = nullptr, *itRI = nullptr;   // L_BI and U_IB blocks of the interior factors
+    int nitCI = 0, nitRI = 0;
+    double bytesCI = 0, bytesRI = 0;
     double* ystore = nullptr;
     long long ny = 0;
     // work vectors
@@ -416,10 +423,13 @@ static int setup_impl(bddc_ctx* C) {
     BDDC_TRY(C->alloc(&C->F, hm.ndof));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->stencil, 0, sizeof(double) * 27 * (size_t)hm.ndof, st));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->F, 0, sizeof(double) * hm.ndof, st));
-    BDDC_TRY(assemble_init(hm, C->o.tau, C->c));
+    std::vector<char> tabs((size_t)assemble_tables_bytes());
+    assemble_tables(hm, tabs.data());
+    char* d_tabs = nullptr;
+    BDDC_TRY(C->upload(&d_tabs, tabs));
     ktimer_begin(KT_ASSEMBLE, st);
-    BDDC_TRY(assemble_launch<T>(hm, C->nu, C->beta, C->f, C->divb, C->bconst, d_sx, d_sy, d_sz, d_lut,
-                                d_lutoff, d_box0, d_boxn, A, d_aoff, d_ald, C->stencil, C->F, st));
+    BDDC_TRY(assemble_launch<T>(hm, C->o.tau, C->c, d_tabs, C->nu, C->beta, C->f, C->divb, C->bconst, d_sx, d_sy,
+                                d_sz, d_lut, d_lutoff, d_box0, d_boxn, A, d_aoff, d_ald, C->stencil, C->F, st));
     ktimer_end(KT_ASSEMBLE, st, 0.0, 0.0);
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
     C->stats.t_assemble_ms = ms_since(t0);
@@ -880,6 +890,7 @@ static int setup_impl(bddc_ctx* C) {
         BDDC_TRY(C->upload(&d_hm, hmv));
         std::vector<EdgeJob> ej;
         int maxnw = 1, maxnz = 1;
+        size_t maxwork = 0;
         for (size_t ei = 0; ei < edges.size(); ++ei) {
             int e = edges[ei];
             Entity& E = hm.ent[e];
@@ -908,6 +919,7 @@ static int setup_impl(bddc_ctx* C) {
             maxnw = std::max(maxnw, (m - 1) * n);
             maxnz = std::max(maxnz, m * n + J.nH);
             T* ew = nullptr;
+            maxwork = std::max(maxwork, edge_work_doubles(n, m, J.nH));
             BDDC_TRY(C->alloc(&ew, edge_work_doubles(n, m, J.nH)));
             J.work = ew;
             BDDC_TRY(C->alloc(&C->BB[e], (size_t)(m - 1) * n * (m - 1) * n));
@@ -921,7 +933,7 @@ static int setup_impl(bddc_ctx* C) {
         EdgeJob* d_ej;
         BDDC_TRY(C->upload(&d_ej, ej));
         ktimer_begin(KT_EDGE, st);
-        BDDC_TRY(edge_run<T>(d_ej, (int)ej.size(), maxnw, maxnz, C->err, st));
+        BDDC_TRY(edge_run<T>(d_ej, (int)ej.size(), maxnw, maxnz, maxwork, C->err, st));
         ktimer_end(KT_EDGE, st, 0.0, 0.0);
     }
     BDDC_CUDA_TRY(cudaMemcpyAsync(C->kk.data(), C->d_k, sizeof(int) * nent, cudaMemcpyDeviceToHost, st));
@@ -1156,18 +1168,43 @@ static int setup_impl(bddc_ctx* C) {
         std::vector<int> lists;
         std::vector<char> items(tri_item_size() * nsd);
         long long yo = 0;
+        std::vector<GemvItem> ci, ri;
+        const double ts = sizeof(T), iv = 8.0 + 4.0;
         for (int s = 0; s < nsd; ++s) {
             SubInfo& S = hm.sub[s];
+            const int nI = S.nI, nB = S.nB, ld = C->ald[s];
             int dof_off = (int)lists.size();
             lists.insert(lists.end(), S.dofs.begin(), S.dofs.end());
             int go = (int)lists.size();
             lists.insert(lists.end(), S.gidx.begin(), S.gidx.end());
-            tri_item_fill(items.data() + tri_item_size() * s, C->aoff[s], S.n, S.nI, C->ald[s], dof_off, go, yo);
+            tri_item_fill(items.data() + tri_item_size() * s, C->aoff[s], S.n, S.nI, ld, dof_off, go, yo);
+            // y positions of the subdomain, and the interface map behind nI unused slots
+            // (the U_IB items read columns nI .. n-1 of A through input slots nI .. n-1)
+            const int yi = (int)lists.size();
+            for (int q = 0; q < nI; ++q) lists.push_back((int)(yo + q));
+            const int gp = (int)lists.size();
+            lists.insert(lists.end(), (size_t)nI, 0);
+            lists.insert(lists.end(), S.gidx.begin(), S.gidx.end());
+            if (nI > 0 && nB > 0) {
+                for (int r0 = 0; r0 < nB; r0 += 32)
+                    ci.push_back(GemvItem{C->aoff[s] + (long long)nI * ld, nB, nI, ld, yi, go, r0,
+                                          std::min(32, nB - r0), 0, nI});
+                for (int c0 = 0; c0 < nB; c0 += 2048)
+                    for (int r0 = 0; r0 < nI; r0 += 32)
+                        ri.push_back(GemvItem{C->aoff[s], nI, S.n, ld, gp, yi, r0, std::min(32, nI - r0), nI + c0,
+                                              std::min(2048, nB - c0)});
+                C->bytesCI += ts * nB * nI + iv * (nI + nB);
+                C->bytesRI += ts * nI * nB + iv * (nB + nI);
+            }
             yo += S.nI;
         }
         C->ny = std::max(yo, 1LL);
         BDDC_TRY(C->upload(&C->tri_lists, lists));
         BDDC_TRY(C->upload((char**)&C->tri, items));
+        BDDC_TRY(C->upload(&C->itCI, ci));
+        BDDC_TRY(C->upload(&C->itRI, ri));
+        C->nitCI = (int)ci.size();
+        C->nitRI = (int)ri.size();
     }
     BDDC_CUDA_TRY(cudaStreamSynchronize(st));
     C->stats.t_coarse_ms = ms_since(t0);
@@ -1219,16 +1256,14 @@ template <class T>
 static int gm_iteration(bddc_ctx* C) {
     const long long n = C->nG;
     const int* skip = &C->gst->stop;
-    BDDC_TRY(gm_copy_row(C->V, n, C->vcur, n, C->gst, C->st));
+    // vcur = V[j] (written by the cycle start or the previous normalisation)
     BDDC_TRY(op_M<T>(C, C->vcur, skip));
     BDDC_TRY(op_S<T>(C, C->zc, C->w, skip));
-    BDDC_TRY(gm_dots(C->V, n, C->w, n, C->gst, C->partial, C->hh, 0, C->gm_m + 1, C->st));
-    BDDC_TRY(gm_orth_update(C->V, n, C->w, n, C->gst, C->hh, C->st));
-    BDDC_TRY(gm_dots(C->V, n, C->w, n, C->gst, C->partial, C->hh2, 0, C->gm_m + 1, C->st));
-    BDDC_TRY(gm_orth_update(C->V, n, C->w, n, C->gst, C->hh2, C->st));
-    BDDC_TRY(gm_norm2(C->w, n, C->gst, C->partial, C->st));
+    BDDC_TRY(gm_pass(0, C->V, n, C->w, n, C->gst, nullptr, C->hh, C->partial, C->st));
+    BDDC_TRY(gm_pass(1, C->V, n, C->w, n, C->gst, C->hh, C->hh2, C->partial, C->st));
+    BDDC_TRY(gm_pass(2, C->V, n, C->w, n, C->gst, C->hh2, nullptr, C->partial, C->st));
     BDDC_TRY(gm_givens(C->gst, C->H, C->cs, C->sn, C->gv, C->hh, C->hh2, C->st));
-    BDDC_TRY(gm_normalize(C->V, n, C->w, n, C->gst, C->st));
+    BDDC_TRY(gm_normalize(C->V, n, C->w, n, C->gst, C->vcur, C->st));
     return BDDC_OK;
 }
 
@@ -1294,7 +1329,7 @@ static int gmres(bddc_ctx* C, const double* b, double* x, double rtol, int max_i
             BDDC_TRY(vec_axpby(C->r, b, 1.0, -1.0, n, st));
         }
         first = false;
-        BDDC_TRY(gm_cycle_start(C->r, n, C->gst, C->gv, C->partial, C->V, st));
+        BDDC_TRY(gm_cycle_start(C->r, n, C->gst, C->gv, C->partial, C->V, C->vcur, st));
         for (int guard = 0; guard < 100000; ++guard) {
             BDDC_CUDA_TRY(cudaMemcpyAsync(C->hst, C->gst, sizeof(GmState), cudaMemcpyDeviceToHost, st));
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1336,11 +1371,11 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
     BDDC_TRY(norm2(C, Fdev, ndof, &Fn));
     if (!C->mixed) {
         BDDC_TRY(gather_run(Fdev, C->gamma_dofs, C->g, (int)nG, st));
-        BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, Fdev, C->g, C->ystore, 1, ndof, nG, C->ny, st));
+        BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, Fdev, C->g, C->ystore, 1, ndof, nG, C->ny, C->itCI, C->nitCI, C->bytesCI, st));
         int it = 0;
         BDDC_TRY(gmres<T>(C, C->g, C->xG, C->o.rtol, C->o.max_iter, &it, &relres, &conv));
         iters_total = it;
-        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, udev, 1, nG, ndof, C->ny, st));
+        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, udev, 1, nG, ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
         steps = 1;
     } else {
         // FP64 iterative refinement on the global system with FP32 BDDC-GMRES as inner solver
@@ -1353,14 +1388,14 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
                 break;
             }
             BDDC_TRY(gather_run(C->res, C->gamma_dofs, C->g, (int)nG, st));
-            BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->res, C->g, C->ystore, 1, ndof, nG, C->ny, st));
+            BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->res, C->g, C->ystore, 1, ndof, nG, C->ny, C->itCI, C->nitCI, C->bytesCI, st));
             int it = 0, cv = 0;
             double rr = 0.0;
             // the loosest inner tolerance that still reaches rtol (with a factor-2 margin)
             const double tol_k = std::max(C->o.inner_rtol, 0.5 * C->o.rtol * Fn / rn);
             BDDC_TRY(gmres<T>(C, C->g, C->xG, std::min(tol_k, 0.5), C->o.max_iter - iters_total, &it, &rr, &cv));
             iters_total += it;
-            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, C->corr, 1, nG, ndof, C->ny, st));
+            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, C->corr, 1, nG, ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
             BDDC_TRY(vec_axpby(udev, C->corr, 1.0, 1.0, ndof, st));
             BDDC_TRY(stencil_residual(hm, C->stencil, udev, Fdev, C->res, 1, st));
             BDDC_TRY(norm2(C, C->res, ndof, &rn));
@@ -1510,6 +1545,11 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     const auto t0 = std::chrono::steady_clock::now();
     BDDC_TRY(build_host_mesh(mesh, part, C->hm));
     HostMesh& hm = C->hm;
+    for (const SubInfo& S : hm.sub)
+        if (S.nI > BDDC_MAX_INTERIOR) {
+            bddc_set_last_error("subdomain interior larger than the interior-solve limit", __FILE__, __LINE__);
+            return BDDC_EINVAL;
+        }
     if (!k || !k->nu_elem) return BDDC_EINVAL;
     if (k->mem == BDDC_MEM_HOST) {
         for (int e = 0; e < hm.nelem; ++e)

@@ -20,9 +20,10 @@
 // Right-looking blocked algorithm, panel width NB (128 in FP32, 64 in FP64).
 // Per panel three launches, each batched over all items:
 //   k_diag    one CTA per item factors the NB x NB diagonal block in shared
-//             memory, 32 columns at a time (warp-level LU of each 32 x 32
-//             block, strip substitutions, rank-32 update), writes L11\U11
-//             back and the pivot reciprocals to a scratch;
+//             memory, 32 columns at a time (the 32 pivot steps restricted to
+//             the column panel and the row strip, one barrier each, then a
+//             rank-32 update of the rest), writes L11\U11 back and the pivot
+//             reciprocals to a scratch;
 //   k_trsm    L21 = M21 U11^{-1} in 64-row chunks and U12 = L11^{-1} M12 in
 //             64-column chunks (the latter solved transposed, so both run the
 //             same blocked substitution: per 32-column block subtract the
@@ -59,12 +60,9 @@ constexpr int UPD_THREADS = 256;
 constexpr int CH = 64;      // rows (columns) of L21 (U12) per k_trsm CTA
 constexpr int KC = 32;      // K chunk of the update
 constexpr int IB = 32;      // inner block of the diagonal factorisation
-constexpr int ILD = IB + 1;
 
-template <class T>
-__device__ __forceinline__ bool bad_pivot(T v) {
-    return !(fabs((double)v) > 1e-300) || !isfinite((double)v);
-}
+__device__ __forceinline__ bool bad_pivot(double v) { return !(fabs(v) > 1e-300) || !isfinite(v); }
+__device__ __forceinline__ bool bad_pivot(float v) { return !(fabsf(v) > 0.f) || !isfinite(v); }
 
 // Per-item scratch: reciprocals of the NB pivots of the current diagonal block.
 template <class T>
@@ -132,64 +130,42 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag(const EngItem<T>* __re
     __syncthreads();
     for (int b0 = 0; b0 < w; b0 += IB) {
         const int bw = min(IB, w - b0);
-        // (a) unblocked LU of the 32 x 32 diagonal block, one warp, lane = row
-        if (wid == 0) {
-            bool bad = false;
-            for (int j = 0; j < bw; ++j) {
-                T piv = D[(b0 + j) * LD + b0 + j];
-                if (bad_pivot(piv)) {
-                    bad = true;
-                    piv = (T)1;
-                }
-                const T ri = (T)1 / piv;
-                __syncwarp();
-                if (lane == j) {
-                    D[(b0 + j) * LD + b0 + j] = piv;
-                    dinv[b0 + j] = ri;
-                }
-                if (lane > j && lane < bw) {
-                    T* row = D + (b0 + lane) * LD + b0;
-                    const T* prow = D + (b0 + j) * LD + b0;
-                    const T l = row[j] * ri;
-                    row[j] = l;
-#pragma unroll 4
-                    for (int c = j + 1; c < bw; ++c) row[c] -= l * prow[c];
-                }
-                __syncwarp();
-            }
-            if (bad && lane == 0) atomicOr(err, ERR_PIVOT);
-        }
-        __syncthreads();
-        // (b) strips by substitution, one 8-lane group per vector: rows below solve
-        //     x U_bb = a, columns to the right solve L_bb y = a (the transposed
-        //     form of the same recurrence, unit diagonal)
+        // (a) the block's 32 pivots, all threads, one barrier per pivot: step jj
+        //     updates the column panel (rows below jj, columns jj+1 .. b0+bw-1) and
+        //     the row strip (rows jj+1 .. b0+bw-1, columns b0+bw .. w-1) with the
+        //     unscaled column jj; the column is scaled after the barrier (no later
+        //     step of the block reads it).
         const int rem = w - b0 - bw;
-        if (rem > 0) {
-            const int grp = t >> 3, cg = t & 7;
-            constexpr int NG = DIAG_THREADS / 8;
-            const T* Db = D + b0 * LD + b0;
-            for (int j0 = 0; j0 < 2 * rem; j0 += NG) {
-                const int job = j0 + grp;
-                const bool valid = job < 2 * rem;
-                const bool colv = job >= rem;
-                const int g = b0 + bw + (colv ? job - rem : job);
-                T acc[1][4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int c = cg + 8 * e;
-                    acc[0][e] = (valid && c < bw) ? (colv ? D[(b0 + c) * LD + g] : D[g * LD + b0 + c]) : (T)0;
-                }
-                // groups of one warp may differ in side: pass the side's strides per lane
-                subst8<T, 1>(acc, Db, colv ? 1 : LD, colv ? LD : 1, colv ? nullptr : dinv + b0, bw, cg);
-                if (valid) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = cg + 8 * e;
-                        if (c < bw) {
-                            if (colv) D[(b0 + c) * LD + g] = acc[0][e];
-                            else D[g * LD + b0 + c] = acc[0][e];
-                        }
+        {
+            const int ty = t >> 5;                 // 16 row lanes
+            constexpr int NRL = DIAG_THREADS / 32;
+            for (int jj = b0; jj < b0 + bw; ++jj) {
+                T piv = D[jj * LD + jj];
+                const bool bad = bad_pivot(piv);
+                if (bad) piv = (T)1;
+                const T ri = (T)1 / piv;
+                const int cend = b0 + bw;
+                // column panel: c = jj + 1 + lane (< cend), rows jj+1+ty, stepping NRL
+                {
+                    const int c = jj + 1 + lane;
+                    if (c < cend) {
+                        const T u = D[jj * LD + c] * ri;
+                        for (int r = jj + 1 + ty; r < w; r += NRL) D[r * LD + c] -= D[r * LD + jj] * u;
                     }
+                }
+                // row strip: rows jj+1 .. cend-1, columns cend .. w-1
+                for (int r = jj + 1 + ty; r < cend; r += NRL) {
+                    const T l = D[r * LD + jj] * ri;
+                    for (int c = cend + lane; c < w; c += 32) D[r * LD + c] -= l * D[jj * LD + c];
+                }
+                __syncthreads();
+                for (int r = jj + 1 + t; r < w; r += DIAG_THREADS) D[r * LD + jj] *= ri;
+                if (t == 0) {
+                    if (bad) {
+                        D[jj * LD + jj] = piv;
+                        atomicOr(err, ERR_PIVOT);
+                    }
+                    dinv[jj] = ri;
                 }
             }
         }
@@ -338,8 +314,11 @@ __device__ __forceinline__ void lds16<double>(const double* p, double* out) {
 // M22 -= L21 U12 on one TILE x TILE tile.  Thread (tr, tc) of a 16 x 16 grid owns
 // rows {tr*H + a, TILE/2 + tr*H + a} and columns {tc*H + b, TILE/2 + tc*H + b},
 // H = TILE/32 (16-byte shared-memory vectors, conflict-free per quarter warp).
+// part: 0 every tile; 1 the first tile row and column (with TILE == NB, the
+// next panel's diagonal block and strips); 2 the other tiles.
 template <class T, int NB, int TILE>
-__global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __restrict__ items, int p, int nt) {
+__global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __restrict__ items, int p, int nt,
+                                                        int part) {
     const EngItem<T> it = items[blockIdx.x];
     if (p >= it.k) return;
     const int w = min(NB, it.k - p);
@@ -347,7 +326,17 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
     const long long ld = it.ld;
     const int m0 = p + w;
     const int y = blockIdx.y;
-    const int ti = y / nt, tj = y - ti * nt;
+    int ti, tj;
+    if (part == 0) {
+        ti = y / nt;
+        tj = y - ti * nt;
+    } else if (part == 1) {
+        ti = y < nt ? 0 : y - nt + 1;
+        tj = y < nt ? y : 0;
+    } else {
+        ti = 1 + y / (nt - 1);
+        tj = 1 + y % (nt - 1);
+    }
     const int r0 = m0 + ti * TILE, c0 = m0 + tj * TILE;
     if (r0 >= n || c0 >= n) return;
     constexpr int H = TILE / 32;              // elements per half per thread (4 in FP32, 2 in FP64)
@@ -420,23 +409,59 @@ long long engine_scratch_elems(int count, bool dbl) {
     return (long long)count * (dbl ? scratch_per_item<double>() : scratch_per_item<float>());
 }
 
+namespace {
+// Side stream and events of the look-ahead (one set per host thread).
+struct LookAhead {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int dev = -1;
+    int init() {
+        int d = 0;
+        BDDC_CUDA_TRY(cudaGetDevice(&d));
+        if (side && d == dev) return BDDC_OK;
+        dev = d;                              // (a stream of another device is left alive)
+        BDDC_CUDA_TRY(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        BDDC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        BDDC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        return BDDC_OK;
+    }
+};
+thread_local LookAhead g_la;
+}  // namespace
+
+// Per panel p: k_diag, k_trsm, k_update.  With look-ahead (FP32/FP64 CUDA-core
+// updates, kernel timer off) the update of panel p is split: the first tile row
+// and column -- exactly the next panel's diagonal block and strips -- go first;
+// the next panel's k_diag and k_trsm then run on a side stream while the main
+// stream updates the remaining tiles, which they do not touch.
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* dscr, int* err,
                cudaStream_t st, const int* hn, const int* hk, bool tc) {
     constexpr int NB = EngCfg<T>::NB, TILE = EngCfg<T>::TILE;
+    static_assert(NB == TILE, "the look-ahead split needs one tile per panel");
     if (count <= 0 || maxk <= 0) return BDDC_OK;
     const size_t dsm = diag_smem<T>();
     const size_t tsm = trsm_smem<T>();
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_diag<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_trsm<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    const bool timed = ktimer_on(KT_ENGINE_UPDATE) || ktimer_on(KT_ENGINE_PANEL);
+    const bool use_tc = tc && sizeof(T) == 4;
+    const bool ahead = !timed && !use_tc && maxk > NB;
+    if (ahead) BDDC_TRY(g_la.init());
+    auto panel = [&](int p, cudaStream_t s) -> int {
+        const int nch = (std::max(maxn - p, 1) + CH - 1) / CH;
+        k_diag<T, NB><<<count, DIAG_THREADS, dsm, s>>>(items_dev, p, dscr, err);
+        k_trsm<T, NB><<<dim3(count, 2 * nch), TRSM_THREADS, tsm, s>>>(items_dev, p, dscr, nch);
+        bddc_note_launches(2);
+        return BDDC_OK;
+    };
     for (int p = 0; p < maxk; p += NB) {
         const int mrem = std::max(maxn - p, 1);          // bound of the trailing size
-        const int nch = (mrem + CH - 1) / CH;
         const int nt = (mrem + TILE - 1) / TILE;
         // algorithmic work of this panel: trailing update 2 m^2 w; diagonal block
         // (2/3) w^3 and substitutions 2 w^2 m
         double fu = 0.0, fp = 0.0, bu = 0.0;
-        if (hn && (ktimer_on(KT_ENGINE_UPDATE) || ktimer_on(KT_ENGINE_PANEL)))
+        if (hn && timed)
             for (int i = 0; i < count; ++i) {
                 if (p >= hk[i]) continue;
                 double w = std::min(NB, hk[i] - p), m = hn[i] - p - w;
@@ -444,26 +469,45 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
                 fp += 2.0 * w * w * w / 3.0 + 2.0 * w * w * m;
                 bu += sizeof(T) * (2.0 * m * m + 2.0 * m * w);   // read + write M22, read L21, U12
             }
-        ktimer_begin(KT_ENGINE_PANEL, st);
-        k_diag<T, NB><<<count, DIAG_THREADS, dsm, st>>>(items_dev, p, dscr, err);
-        k_trsm<T, NB><<<dim3(count, 2 * nch), TRSM_THREADS, tsm, st>>>(items_dev, p, dscr, nch);
-        bddc_note_launches(2);
-        ktimer_end(KT_ENGINE_PANEL, st, fp, 0.0);
+        if (p == 0 || !ahead) {
+            ktimer_begin(KT_ENGINE_PANEL, st);
+            BDDC_TRY(panel(p, st));
+            ktimer_end(KT_ENGINE_PANEL, st, fp, 0.0);
+        }
+        const bool next = ahead && p + NB < maxk && nt > 1;
+        if (next) {
+            k_update<T, NB, TILE><<<dim3(count, 2 * nt - 1), UPD_THREADS, 0, st>>>(items_dev, p, nt, 1);
+            BDDC_CUDA_TRY(cudaEventRecord(g_la.fork, st));
+            BDDC_CUDA_TRY(cudaStreamWaitEvent(g_la.side, g_la.fork, 0));
+            BDDC_TRY(panel(p + NB, g_la.side));
+            BDDC_CUDA_TRY(cudaEventRecord(g_la.join, g_la.side));
+            k_update<T, NB, TILE><<<dim3(count, (nt - 1) * (nt - 1)), UPD_THREADS, 0, st>>>(items_dev, p, nt, 2);
+            BDDC_CUDA_TRY(cudaStreamWaitEvent(st, g_la.join, 0));
+            bddc_note_launches(2);
+            continue;
+        }
+        if (ahead && p + NB < maxk) {
+            // a single tile row remains: no split; the next panel follows in order
+            k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt, 0);
+            bddc_note_launches(1);
+            BDDC_TRY(panel(p + NB, st));
+            continue;
+        }
         ktimer_begin(KT_ENGINE_UPDATE, st);
         if constexpr (sizeof(T) == 4) {
-            if (tc) {
+            if (use_tc) {
                 BDDC_TRY(tc_update_run(reinterpret_cast<const EngItem<float>*>(items_dev), count, maxn, p, NB,
                                        err, st));
             } else {
-                k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt);
+                k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt, 0);
                 bddc_note_launches(1);
             }
         } else {
-            (void)tc;
-            k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt);
+            k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt, 0);
             bddc_note_launches(1);
         }
         ktimer_end(KT_ENGINE_UPDATE, st, fu, bu);
+        if (ahead && p + NB < maxk) BDDC_TRY(panel(p + NB, st));
     }
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;

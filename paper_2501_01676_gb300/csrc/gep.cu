@@ -589,7 +589,8 @@ __device__ int qr_basis(T* C, int n, int m, T* Q, T* vbuf /* n*n */, T* norms,
 
 // ------------------------------------------------------------------- face
 template <class T>
-__global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, int* __restrict__ err) {
+__global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, int* __restrict__ err,
+                                             long long work_off) {
     const FaceJob J = jobs[blockIdx.x];
     const int n = J.n, np = (n + 1) & ~1;
     extern __shared__ __align__(16) unsigned char shm_raw[];
@@ -601,7 +602,7 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     __shared__ int pp[64], qq[64];
     __shared__ int order[128];
     __shared__ unsigned char done[256];
-    T* w = (T*)J.work;
+    T* w = work_off >= 0 ? shm + work_off : (T*)J.work;   // workspace in shared memory when it fits
     const int nn = n * n;
     T *Si = w, *Sj = w + nn, *Ssum = w + 2 * nn, *Dij = w + 3 * nn /* n x 2n */;
     T *BF = w + 5 * nn, *Bti = w + 6 * nn, *Btj = w + 7 * nn, *Bt = w + 8 * nn;
@@ -630,10 +631,10 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     bar();
     const T* Di = Dij;
     const T* Dj = Dij + n;
-    mm(T1, n, false, Dj, 2 * n, false, W1, n, n, n, n, 1.0, 0.0);
-    mm(Dj, 2 * n, true, W1, n, false, BF, n, n, n, n, 1.0, 0.0);
-    mm(T2, n, false, Di, 2 * n, false, W1, n, n, n, n, 1.0, 0.0);
-    mm(Di, 2 * n, true, W1, n, false, BF, n, n, n, n, 1.0, 1.0);
+    mm(T1, n, false, Dj, 2 * n, false, W1, n, n, n, n, (T)1, (T)0);
+    mm(Dj, 2 * n, true, W1, n, false, BF, n, n, n, n, (T)1, (T)0);
+    mm(T2, n, false, Di, 2 * n, false, W1, n, n, n, n, (T)1, (T)0);
+    mm(Di, 2 * n, true, W1, n, false, BF, n, n, n, n, (T)1, (T)1);
     symmetrize(BF, n, n);
     // parallel sum B~_i : B~_j = B~_i - B~_i (B~_i + B~_j)^+ B~_i
     copy_mat(J.Bti, J.ldbi, Bti, n, n, n);
@@ -673,7 +674,7 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
         const int s = nsel_s;
         if (s > 0) {
             // Cm = B_F V(:, 0..s)   (n x s)
-            mm(BF, n, false, V, r, false, Cm, s, n, s, n, 1.0, 0.0);
+            mm(BF, n, false, V, r, false, Cm, s, n, s, n, (T)1, (T)0);
             k = qr_basis(Cm, n, s, T1, vb, aux + n, aux + 2 * n);
         } else {
             for (int q = threadIdx.x; q < nn; q += GT) T1[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
@@ -687,14 +688,15 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     }
     // outputs: Q (row-major n x n), D^(i) Q, D^(j) Q
     for (int q = threadIdx.x; q < nn; q += GT) J.Q[q] = T1[q];
-    mm(Di, 2 * n, false, T1, n, false, J.DQi, n, n, n, n, 1.0, 0.0);
-    mm(Dj, 2 * n, false, T1, n, false, J.DQj, n, n, n, n, 1.0, 0.0);
+    mm(Di, 2 * n, false, T1, n, false, J.DQi, n, n, n, n, (T)1, (T)0);
+    mm(Dj, 2 * n, false, T1, n, false, J.DQj, n, n, n, n, (T)1, (T)0);
     if (threadIdx.x == 0) *J.k = k;
 }
 
 // ------------------------------------------------------------------- edge
 template <class T>
-__global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, int* __restrict__ err) {
+__global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, int* __restrict__ err,
+                                             long long work_off) {
     const EdgeJob J = jobs[blockIdx.x];
     const int n = J.n, m = J.m, nw = (m - 1) * n, mn = m * n;
     const int nz = mn + J.nH;
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
     __shared__ int pp[64], qq[64];
     __shared__ int order[128];
     __shared__ unsigned char done[1024];
-    T* w = (T*)J.work;
+    T* w = work_off >= 0 ? shm + work_off : (T*)J.work;   // workspace in shared memory when it fits
     const int nn = n * n;
     T* Ssum = w;                     // n x n
     T* Dall = Ssum + nn;             // n x (m n): [D^(k_1) ... D^(k_m)]
@@ -763,8 +765,8 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
     for (int q = threadIdx.x; q < nw * nw; q += GT) ME[q] = 0.0;
     bar();
     for (int t = 0; t < m; ++t) {
-        mm(BE + t * nn, n, false, Tk + t * n * mn, mn, false, T1, nw, n, nw, n, 1.0, 0.0);
-        mm(Tk + t * n * mn, mn, true, T1, nw, false, ME, nw, nw, nw, n, 1.0, 1.0);
+        mm(BE + t * nn, n, false, Tk + t * n * mn, mn, false, T1, nw, n, nw, n, (T)1, (T)0);
+        mm(Tk + t * n * mn, mn, true, T1, nw, false, ME, nw, nw, nw, n, (T)1, (T)1);
     }
     symmetrize(ME, nw, nw);
     if (J.mode == 0) {
@@ -854,40 +856,67 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
     for (int q = threadIdx.x; q < nn; q += GT) J.Q[q] = Qo[q];
     bar();
     for (int t = 0; t < m; ++t)
-        mm(Dall + t * n, mn, false, Qo, n, false, J.DQ[t], n, n, n, n, 1.0, 0.0);
+        mm(Dall + t * n, mn, false, Qo, n, false, J.DQ[t], n, n, n, n, (T)1, (T)0);
     if (threadIdx.x == 0) *J.k = k;
 }
 
 }  // namespace
 
-size_t face_work_doubles(int n) { return (size_t)21 * n * n + 3 * n + 64; }
+size_t face_work_doubles(int n) { return (size_t)20 * n * n + 3 * n + 64; }
 size_t edge_work_doubles(int n, int m, int nH) {
     size_t nw = (size_t)(m - 1) * n, mn = (size_t)m * n, nz = mn + nH;
     return (size_t)n * n * (3 + m) + (size_t)n * mn * (1 + m) + 6 * nw * nw + 2 * nz * nz +
            (size_t)n * nw * (m - 1) + nw + (size_t)m * nw + n + 64;
 }
 
+// Dynamic shared memory of a GEP launch: the Jacobi pair (base bytes) and, when
+// the device allows it, the per-job workspace too (returned offset in elements;
+// -1 keeps the workspace in the jobs' global buffers).
+template <class T>
+static int gep_smem(const void* fn, size_t base, size_t work_elems, size_t* smem, long long* off) {
+    cudaFuncAttributes fa;
+    BDDC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+    int dev = 0, optin = 0;
+    BDDC_CUDA_TRY(cudaGetDevice(&dev));
+    BDDC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t want = base + work_elems * sizeof(T);
+    if (fa.sharedSizeBytes + want <= (size_t)optin) {
+        *smem = want;
+        *off = (long long)(base / sizeof(T));
+    } else {
+        *smem = base;
+        *off = -1;
+    }
+    return BDDC_OK;
+}
+
 template <class T>
 int face_run(const FaceJob* jobs_dev, int count, int maxn, int* err, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
     int np = (maxn + 1) & ~1;
-    size_t smem = (size_t)2 * np * (np + 1) * sizeof(T);
-    if (np > 128 || smem > 200 * 1024) return BDDC_EINVAL;
+    const size_t base = (size_t)2 * np * (np + 1) * sizeof(T);
+    if (np > 128 || base > 200 * 1024) return BDDC_EINVAL;
+    size_t smem = 0;
+    long long off = -1;
+    BDDC_TRY(gep_smem<T>((const void*)k_face<T>, base, face_work_doubles(maxn), &smem, &off));
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_face<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_face<T><<<count, GT, smem, st>>>(jobs_dev, err);
+    k_face<T><<<count, GT, smem, st>>>(jobs_dev, err, off);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
 template <class T>
-int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, int* err, cudaStream_t st) {
+int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, size_t max_work, int* err, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
     int np = (maxnw + 1) & ~1;
-    size_t smem = (size_t)2 * np * (np + 1) * sizeof(T);
-    if (np > 128 || smem > 200 * 1024 || maxnz > 1024) return BDDC_EINVAL;
+    const size_t base = (size_t)2 * np * (np + 1) * sizeof(T);
+    if (np > 128 || base > 200 * 1024 || maxnz > 1024) return BDDC_EINVAL;
+    size_t smem = 0;
+    long long off = -1;
+    BDDC_TRY(gep_smem<T>((const void*)k_edge<T>, base, max_work, &smem, &off));
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_edge<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_edge<T><<<count, GT, smem, st>>>(jobs_dev, err);
+    k_edge<T><<<count, GT, smem, st>>>(jobs_dev, err, off);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
@@ -895,5 +924,5 @@ int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, int* err,
 
 template int face_run<double>(const FaceJob*, int, int, int*, cudaStream_t);
 template int face_run<float>(const FaceJob*, int, int, int*, cudaStream_t);
-template int edge_run<double>(const EdgeJob*, int, int, int, int*, cudaStream_t);
-template int edge_run<float>(const EdgeJob*, int, int, int, int*, cudaStream_t);
+template int edge_run<double>(const EdgeJob*, int, int, int, size_t, int*, cudaStream_t);
+template int edge_run<float>(const EdgeJob*, int, int, int, size_t, int*, cudaStream_t);

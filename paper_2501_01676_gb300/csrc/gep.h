@@ -53,4 +53,4 @@ size_t edge_work_doubles(int n, int m, int nH);
 template <class T>
 int face_run(const FaceJob* jobs_dev, int count, int maxn, int* err, cudaStream_t st);
 template <class T>
-int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, int* err, cudaStream_t st);
+int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, size_t max_work, int* err, cudaStream_t st);

@@ -1,8 +1,8 @@
 // FP64 Arnoldi / Givens kernels of right-preconditioned GMRES (Sect. 4: the
 // iteration stops when the residual falls below the tolerance or after 300
-// iterations).  Classical Gram-Schmidt applied twice (CGS2): every
-// orthogonalisation pass is one batched dot-product kernel (two-stage,
-// deterministic reduction with warp shuffles) and one fused update kernel.
+// iterations).  Classical Gram-Schmidt applied twice (CGS2) in three fused
+// passes (dots; update + dots; update + norm), each one launch whose last CTA
+// reduces the per-chunk partial sums in a fixed order.
 // All scalars of the iteration (Hessenberg column, rotations, residual
 // estimate, stop flag) stay on the device so a fixed block of iterations can
 // be replayed as one CUDA graph; every kernel returns at once when the stop
@@ -16,7 +16,7 @@ namespace {
 
 constexpr int DOT_THREADS = 256;
 constexpr int DOT_ROWS = 8;      // rows per block of the dot kernel
-constexpr int DOT_CHUNK = 4096;  // vector elements per block
+constexpr int DOT_CHUNK = 1024;  // vector elements per block (several CTAs per row group)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -57,6 +57,99 @@ __global__ void __launch_bounds__(DOT_THREADS) k_dots(const double* __restrict__
         double s = 0.0;
         for (int q = 0; q < DOT_THREADS / 32; ++q) s += red[q][threadIdx.x];
         partial[(long long)(r0 + threadIdx.x) * nchunk + blockIdx.x] = s;
+    }
+}
+
+constexpr int PASS_THREADS = 256;
+constexpr int PASS_EPT = 4;                       // vector elements per thread
+constexpr int PASS_CHUNK = PASS_THREADS * PASS_EPT;
+
+// One CGS2 pass: optional w -= V[0..j] hin (element-parallel, w held in
+// registers), then the partial sums of V[0..j] . w (or of w . w) of this CTA's
+// chunk, and the last CTA to finish reduces the partials in chunk order.
+template <int MODE>
+__global__ void __launch_bounds__(PASS_THREADS) k_pass(const double* __restrict__ V, long long ldv,
+                                                       double* __restrict__ w, long long n, GmState* __restrict__ S,
+                                                       const double* __restrict__ hin, double* __restrict__ hout,
+                                                       double* __restrict__ partial, int nchunk) {
+    if (S->stop) return;
+    const int nr = S->j + 1;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const long long e0 = (long long)blockIdx.x * PASS_CHUNK + t;
+    __shared__ double red[PASS_THREADS / 32][8];
+    __shared__ int last;
+    double wv[PASS_EPT];
+#pragma unroll
+    for (int k = 0; k < PASS_EPT; ++k) {
+        const long long e = e0 + (long long)k * PASS_THREADS;
+        wv[k] = e < n ? w[e] : 0.0;
+    }
+    if (MODE != 0) {
+        for (int i = 0; i < nr; ++i) {
+            const double c = hin[i];
+            const double* vi = V + (long long)i * ldv;
+#pragma unroll
+            for (int k = 0; k < PASS_EPT; ++k) {
+                const long long e = e0 + (long long)k * PASS_THREADS;
+                if (e < n) wv[k] -= c * vi[e];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PASS_EPT; ++k) {
+            const long long e = e0 + (long long)k * PASS_THREADS;
+            if (e < n) w[e] = wv[k];
+        }
+    }
+    const int nrows = MODE == 2 ? 1 : nr;
+    for (int r0 = 0; r0 < nrows; r0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            acc[q] = 0.0;
+            if (r0 + q < nrows) {
+                const double* vi = MODE == 2 ? nullptr : V + (long long)(r0 + q) * ldv;
+#pragma unroll
+                for (int k = 0; k < PASS_EPT; ++k) {
+                    const long long e = e0 + (long long)k * PASS_THREADS;
+                    if (e < n) acc[q] += (MODE == 2 ? wv[k] : vi[e]) * wv[k];
+                }
+            }
+            acc[q] = warp_sum(acc[q]);
+        }
+        if (lane < 8) {
+            double v = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q == lane) v = acc[q];
+            red[wid][lane] = v;
+        }
+        __syncthreads();
+        if (t < 8 && r0 + t < nrows) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < PASS_THREADS / 32; ++q) s += red[q][t];
+            partial[(long long)(r0 + t) * nchunk + blockIdx.x] = s;
+        }
+        __syncthreads();
+    }
+    // last CTA: reduce the partials of all chunks
+    __threadfence();
+    if (t == 0) last = atomicAdd(&S->cnt, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int row = wid; row < nrows; row += PASS_THREADS / 32) {
+        double s = 0.0;
+        for (int c = lane; c < nchunk; c += 32) s += partial[(long long)row * nchunk + c];
+        s = warp_sum(s);
+        if (lane == 0) {
+            if (MODE == 2) S->nrm2 = s;
+            else hout[row] = s;
+        }
+    }
+    if (t == 0) {
+        S->cnt = 0;
+        if (MODE == 0) S->need_norm = 0;
     }
 }
 
@@ -129,15 +222,19 @@ __global__ void k_givens(GmState* __restrict__ S, double* __restrict__ H, double
 }
 
 // V[j] = w * scale  (j already advanced)
+// V[j] = w * scale and the next preconditioner input vcur = V[j]
 __global__ void k_normalize(double* __restrict__ V, long long ldv, const double* __restrict__ w,
-                            long long n, GmState* __restrict__ S) {
+                            long long n, GmState* __restrict__ S, double* __restrict__ vcur) {
     if (!S->need_norm) return;
     const int j = S->j;
     if (j > S->m) return;
     const double sc = S->scale;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x)
-        V[j * ldv + e] = w[e] * sc;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double v = w[e] * sc;
+        V[j * ldv + e] = v;
+        vcur[e] = v;
+    }
 }
 
 __global__ void k_clear_norm(GmState* S) { S->need_norm = 0; }
@@ -259,10 +356,21 @@ int gm_givens(GmState* S, double* H, double* cs, double* sn, double* gv, const d
     return BDDC_OK;
 }
 
-int gm_normalize(double* V, long long ldv, const double* w, long long n, GmState* S, cudaStream_t st) {
-    k_normalize<<<grid_for(n), 256, 0, st>>>(V, ldv, w, n, S);
+int gm_normalize(double* V, long long ldv, const double* w, long long n, GmState* S, double* vcur,
+                 cudaStream_t st) {
+    // need_norm is cleared by the next iteration's first pass (k_pass<0>)
+    k_normalize<<<grid_for(n), 256, 0, st>>>(V, ldv, w, n, S, vcur);
     bddc_note_launches(1);
-    k_clear_norm<<<1, 1, 0, st>>>(S);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
+int gm_pass(int mode, const double* V, long long ldv, double* w, long long n, GmState* S, const double* hin,
+            double* hout, double* partial, cudaStream_t st) {
+    const int nchunk = (int)((n + PASS_CHUNK - 1) / PASS_CHUNK);
+    if (mode == 0) k_pass<0><<<nchunk, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk);
+    else if (mode == 1) k_pass<1><<<nchunk, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk);
+    else k_pass<2><<<nchunk, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
@@ -277,7 +385,7 @@ int gm_copy_row(const double* V, long long ldv, double* out, long long n, const 
 }
 
 int gm_cycle_start(const double* r, long long n, GmState* S, double* gv, double* partial, double* V0,
-                   cudaStream_t st) {
+                   double* vcur, cudaStream_t st) {
     int nchunk = gm_nchunk(n);
     // plain norm pass that ignores the stop flag: use a private state copy
     k_dots<<<dim3(nchunk, 1), DOT_THREADS, 0, st>>>(nullptr, 0, r, n, S + 1, 1, partial, nchunk);
@@ -285,7 +393,8 @@ int gm_cycle_start(const double* r, long long n, GmState* S, double* gv, double*
     k_cycle_start<<<1, 32, 0, st>>>(S, gv, partial, nchunk);
     bddc_note_launches(1);
     k_scale_into<<<grid_for(n), 256, 0, st>>>(V0, r, n, S);
-    bddc_note_launches(1);
+    k_scale_into<<<grid_for(n), 256, 0, st>>>(vcur, r, n, S);
+    bddc_note_launches(2);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }

@@ -10,7 +10,7 @@ struct GmState {
     int total;       // iterations over all cycles
     int max_iter;
     int need_norm;
-    int pad;
+    int cnt;         // CTAs of a fused pass that have stored their partial sums
     double tol;      // absolute residual target rtol * ||b||
     double beta;     // initial residual norm of the cycle
     double res;      // current residual estimate |g_{j}|
@@ -26,11 +26,16 @@ int gm_orth_update(const double* V, long long ldv, double* w, long long n, const
                    const double* c, cudaStream_t st);
 int gm_givens(GmState* S, double* H, double* cs, double* sn, double* gv, const double* h,
               const double* h2, cudaStream_t st);
-int gm_normalize(double* V, long long ldv, const double* w, long long n, GmState* S, cudaStream_t st);
+int gm_normalize(double* V, long long ldv, const double* w, long long n, GmState* S, double* vcur,
+                 cudaStream_t st);
+// One fused CGS2 pass over the Krylov basis V[0..j] (one launch, last-CTA reduction):
+//   mode 0: hout = V^T w;  1: w -= V hin, then hout = V^T w;  2: w -= V hin, then S->nrm2 = w.w
+int gm_pass(int mode, const double* V, long long ldv, double* w, long long n, GmState* S, const double* hin,
+            double* hout, double* partial, cudaStream_t st);
 int gm_copy_row(const double* V, long long ldv, double* out, long long n, const GmState* S,
                 cudaStream_t st);
 int gm_cycle_start(const double* r, long long n, GmState* S, double* gv, double* partial, double* V0,
-                   cudaStream_t st);
+                   double* vcur, cudaStream_t st);
 int gm_finish(const double* V, long long ldv, const GmState* S, const double* H, const double* gv,
               double* y, double* t, long long n, cudaStream_t st);
 int vec_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st);
