@@ -193,7 +193,7 @@ int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, i
 /* Kernel timer for roofline reporting: after bddc_kernel_timer(kind) every
  * launch of that kernel class (1 engine trailing update, 2 engine panel,
  * 3 apply GEMV, 4 face GEP, 5 edge GEP, 6 element assembly, 7 change of basis,
- * 8 interior condense / recover solves; 0 off) is bracketed by CUDA events on
+ * 8 interior condense / recover solves, 9 coarse inverse; 0 off) is bracketed by CUDA events on
  * its stream (launches captured into graphs are not).  _read synchronises on
  * the recorded events and returns their summed duration, the number of
  * launches and, where the library knows them, the algorithmic flops and

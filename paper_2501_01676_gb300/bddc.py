@@ -161,7 +161,8 @@ def load_mlp_params():
         return None
     return np.ascontiguousarray(np.load(MLP_PARAMS_FILE), dtype=np.float32)
 
-KT_NONE, KT_ENGINE_UPDATE, KT_ENGINE_PANEL, KT_GEMV, KT_FACE, KT_EDGE, KT_ASSEMBLE, KT_TRANSFORM, KT_TRI = range(9)
+(KT_NONE, KT_ENGINE_UPDATE, KT_ENGINE_PANEL, KT_GEMV, KT_FACE, KT_EDGE, KT_ASSEMBLE, KT_TRANSFORM, KT_TRI,
+ KT_COARSE) = range(10)
 
 
 def kernel_timer(kind):

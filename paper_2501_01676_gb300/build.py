@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbddc.so")
 SOURCES = ["host_mesh.cpp", "assemble.cu", "engine.cu", "apply.cu", "gmres.cu", "gep.cu",
-           "setup_kernels.cu", "capi.cu", "static_apply.cu", "mlp.cu", "tc_update.cu"]
+           "setup_kernels.cu", "capi.cu", "static_apply.cu", "mlp.cu", "tc_update.cu",
+           "coarse_inv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

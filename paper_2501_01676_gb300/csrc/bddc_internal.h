@@ -33,7 +33,7 @@ void bddc_note_launches(unsigned long long n);
 
 // Optional CUDA-event timing of one kernel class (for roofline reporting).
 enum { KT_NONE = 0, KT_ENGINE_UPDATE = 1, KT_ENGINE_PANEL = 2, KT_GEMV = 3, KT_FACE = 4, KT_EDGE = 5,
-       KT_ASSEMBLE = 6, KT_TRANSFORM = 7, KT_TRI = 8, KT_LAST = 8 };
+       KT_ASSEMBLE = 6, KT_TRANSFORM = 7, KT_TRI = 8, KT_COARSE = 9, KT_LAST = 9 };
 bool ktimer_on(int kind);
 void ktimer_begin(int kind, cudaStream_t st);
 void ktimer_end(int kind, cudaStream_t st, double flops, double bytes);
@@ -44,6 +44,7 @@ enum {
     ERR_JACOBI = 2,       // Jacobi eigen sweep cap reached
     ERR_SIZE = 4,         // a size exceeded a compiled limit
     ERR_TIMEOUT_TC = 8,   // a bounded wait for tensor-core work gave up
+    ERR_TIMEOUT_ENGINE = 16,  // a bounded wait of the engine's task kernel gave up
 };
 
 // ---------------------------------------------------------------------------
@@ -104,6 +105,12 @@ struct DevArena {                    // all device allocations of a context
 // kernels hold in shared memory: 2048 = a 13^3 interior (H/h <= 13 per slab).
 constexpr int BDDC_MAX_INTERIOR = 2048;
 
+// Coarse matrices up to this order are inverted by one CTA (FP32 Gauss-Jordan
+// in shared memory) plus FP64 Newton-Schulz steps.
+constexpr int COARSE_GJ_MAX = 160;
+int coarse_inverse_small(const double* S, int n, double* X, int ldx, double* work, double* resid, int ns_steps,
+                         int* err, cudaStream_t st);
+
 // Batched partial LU (Schur complement engine) item descriptor.
 template <class T>
 struct EngItem {
@@ -118,8 +125,9 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* di
                int* err, cudaStream_t st, const int* host_n = nullptr, const int* host_k = nullptr,
                bool tensor_cores = false);
 
-// Scratch elements engine_run needs for `count` items (FP64 if dbl).
-long long engine_scratch_elems(int count, bool dbl);
+// Scratch elements engine_run needs for `count` items eliminating up to maxk
+// unknowns (FP64 if dbl).
+long long engine_scratch_elems(int count, bool dbl, int maxk);
 
 // Tensor-core (tcgen05, split TF32) trailing update of one FP32 engine panel of width <= nb.
 int tc_update_run(const EngItem<float>* items_dev, int count, int maxn, int p, int nb, int* err, cudaStream_t st);

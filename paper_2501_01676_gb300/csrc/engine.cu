@@ -38,6 +38,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "bddc_internal.h"
 
@@ -54,7 +56,7 @@ struct EngCfg<double> {
     static constexpr int NB = 64, TILE = 64;
 };
 
-constexpr int DIAG_THREADS = 512;
+constexpr int DIAG_THREADS = 256;     // small, so that it fits beside an update CTA (look-ahead)
 constexpr int TRSM_THREADS = 256;
 constexpr int UPD_THREADS = 256;
 constexpr int CH = 64;      // rows (columns) of L21 (U12) per k_trsm CTA
@@ -64,11 +66,9 @@ constexpr int IB = 32;      // inner block of the diagonal factorisation
 __device__ __forceinline__ bool bad_pivot(double v) { return !(fabs(v) > 1e-300) || !isfinite(v); }
 __device__ __forceinline__ bool bad_pivot(float v) { return !(fabsf(v) > 0.f) || !isfinite(v); }
 
-// Per-item scratch: reciprocals of the NB pivots of the current diagonal block.
-template <class T>
-__host__ __device__ constexpr long long scratch_per_item() {
-    return (long long)EngCfg<T>::NB;
-}
+// Per-item scratch: the reciprocal pivots of every panel (NB per panel, so that
+// a panel's pivots stay valid while the next panel is factored in the task
+// kernel); `stride` elements per item.
 
 // Solve x U = b within one 32-column block for NR vectors held by a group of 8
 // lanes (lane cg of the group owns entries cg, cg+8, cg+16, cg+24 of every
@@ -110,22 +110,21 @@ __device__ __forceinline__ void subst8(T (&acc)[NR][4], const T* __restrict__ U,
 // code is kept compact (loops over shared memory, no long unrolled chains): it
 // runs once per launch, so straight-line code would be fetched from beyond the
 // instruction cache for every instruction.
+// (global loads of matrix data go through L2, __ldcg: in the persistent task
+// kernel other CTAs write it during the launch)
 template <class T, int NB>
-__global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag(const EngItem<T>* __restrict__ items, int p,
-                                                          T* __restrict__ scr, int* __restrict__ err) {
-    const EngItem<T> it = items[blockIdx.x];
-    if (p >= it.k) return;
+__device__ void diag_body(const EngItem<T>& it, int p, T* __restrict__ out, int* __restrict__ err,
+                          unsigned char* dsm) {
     const int w = min(NB, it.k - p);
     const long long ld = it.ld;
     T* A = it.a + (long long)p * ld + p;
     constexpr int LD = NB + 1;
-    extern __shared__ __align__(16) unsigned char dsm[];
     T* D = reinterpret_cast<T*>(dsm);        // NB x LD: L\U of the diagonal block
     T* dinv = D + NB * LD;                    // NB reciprocal pivots
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int q = t; q < w * w; q += DIAG_THREADS) {
         const int r = q / w, c = q - r * w;
-        D[r * LD + c] = A[r * ld + c];
+        D[r * LD + c] = __ldcg(A + r * ld + c);
     }
     __syncthreads();
     for (int b0 = 0; b0 < w; b0 += IB) {
@@ -195,12 +194,20 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag(const EngItem<T>* __re
         }
         __syncthreads();
     }
-    T* out = scr + (long long)blockIdx.x * scratch_per_item<T>();
     for (int q = t; q < w; q += DIAG_THREADS) out[q] = dinv[q];
     for (int q = t; q < w * w; q += DIAG_THREADS) {
         const int r = q / w, c = q - r * w;
         A[r * ld + c] = D[r * LD + c];
     }
+}
+
+template <class T, int NB>
+__global__ void __launch_bounds__(DIAG_THREADS, 2) k_diag(const EngItem<T>* __restrict__ items, int p,
+                                                          T* __restrict__ scr, long long stride, int* __restrict__ err) {
+    const EngItem<T> it = items[blockIdx.x];
+    if (p >= it.k) return;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    diag_body<T, NB>(it, p, scr + (long long)blockIdx.x * stride + (p / NB) * NB, err, dsm);
 }
 
 // Blocked substitution on a chunk of R <= CH rows, X (R x w, in shared memory):
@@ -210,37 +217,31 @@ __global__ void __launch_bounds__(DIAG_THREADS, 1) k_diag(const EngItem<T>* __re
 // solved blocks (register-blocked, 2 rows x 4 columns per thread), then
 // substitute within the block (subst8: 8 lanes per row pair).
 template <class T, int NB>
-__global__ void __launch_bounds__(TRSM_THREADS, 2) k_trsm(const EngItem<T>* __restrict__ items, int p,
-                                                          const T* __restrict__ scr, int nch) {
-    const EngItem<T> it = items[blockIdx.x];
-    if (p >= it.k) return;
+__device__ void trsm_body(const EngItem<T>& it, int p, bool colside, int chunk, const T* __restrict__ pinv,
+                          unsigned char* tsm_) {
     const int w = min(NB, it.k - p);
     const int n = it.n;
     const long long ld = it.ld;
     const int m0 = p + w;
-    const bool colside = (int)blockIdx.y >= nch;
-    const int chunk = colside ? blockIdx.y - nch : blockIdx.y;
     const int g0 = m0 + chunk * CH;
     if (g0 >= n) return;
     const int R = min(CH, n - g0);
     constexpr int LDX = NB + 1;
-    extern __shared__ __align__(16) unsigned char tsm_[];
     T* X = reinterpret_cast<T*>(tsm_);        // CH x LDX
     T* Us = X + CH * LDX;                     // NB x 33: U(l, b0 + c) for l < b0 + 32
     T* dv = Us + NB * (IB + 1);               // 32 reciprocal diagonal entries of the block
     const T* A = it.a;
-    const T* pinv = scr + (long long)blockIdx.x * scratch_per_item<T>();
     const int t = threadIdx.x;
     if (!colside) {
         for (int q = t; q < CH * w; q += TRSM_THREADS) {
             const int r = q / w, c = q - r * w;
-            X[r * LDX + c] = r < R ? A[(long long)(g0 + r) * ld + p + c] : (T)0;
+            X[r * LDX + c] = r < R ? __ldcg(A + (long long)(g0 + r) * ld + p + c) : (T)0;
         }
     } else {
         // X[c][k] = M12[k][c]: rows of M12 are contiguous along c
         for (int q = t; q < CH * w; q += TRSM_THREADS) {
             const int k = q / CH, c = q - k * CH;
-            X[c * LDX + k] = c < R ? A[(long long)(p + k) * ld + g0 + c] : (T)0;
+            X[c * LDX + k] = c < R ? __ldcg(A + (long long)(p + k) * ld + g0 + c) : (T)0;
         }
     }
     const int rg = t >> 3, cg = t & 7;        // rows 2rg, 2rg+1; columns cg + 8e
@@ -250,14 +251,14 @@ __global__ void __launch_bounds__(TRSM_THREADS, 2) k_trsm(const EngItem<T>* __re
         if (!colside) {
             for (int q = t; q < nl * IB; q += TRSM_THREADS) {
                 const int l = q / IB, c = q - l * IB;
-                Us[l * (IB + 1) + c] = c < bw ? A[(long long)(p + l) * ld + p + b0 + c] : (T)0;
+                Us[l * (IB + 1) + c] = c < bw ? __ldcg(A + (long long)(p + l) * ld + p + b0 + c) : (T)0;
             }
-            if (t < IB) dv[t] = t < bw ? pinv[b0 + t] : (T)1;
+            if (t < IB) dv[t] = t < bw ? __ldcg(pinv + b0 + t) : (T)1;
         } else {
             // U(l, b0 + c) = L11[b0 + c][l]: rows of L11, read along l
             for (int q = t; q < nl * IB; q += TRSM_THREADS) {
                 const int c = q / nl, l = q - c * nl;
-                Us[l * (IB + 1) + c] = c < bw ? A[(long long)(p + b0 + c) * ld + p + l] : (T)0;
+                Us[l * (IB + 1) + c] = c < bw ? __ldcg(A + (long long)(p + b0 + c) * ld + p + l) : (T)0;
             }
             if (t < IB) dv[t] = (T)1;
         }
@@ -298,6 +299,17 @@ __global__ void __launch_bounds__(TRSM_THREADS, 2) k_trsm(const EngItem<T>* __re
     }
 }
 
+template <class T, int NB>
+__global__ void __launch_bounds__(TRSM_THREADS, 2) k_trsm(const EngItem<T>* __restrict__ items, int p,
+                                                          const T* __restrict__ scr, long long stride, int nch) {
+    const EngItem<T> it = items[blockIdx.x];
+    if (p >= it.k) return;
+    const bool colside = (int)blockIdx.y >= nch;
+    const int chunk = colside ? blockIdx.y - nch : blockIdx.y;
+    extern __shared__ __align__(16) unsigned char tsm_[];
+    trsm_body<T, NB>(it, p, colside, chunk, scr + (long long)blockIdx.x * stride + (p / NB) * NB, tsm_);
+}
+
 template <class T>
 __device__ __forceinline__ void lds16(const T* p, T* out);
 template <>
@@ -314,35 +326,18 @@ __device__ __forceinline__ void lds16<double>(const double* p, double* out) {
 // M22 -= L21 U12 on one TILE x TILE tile.  Thread (tr, tc) of a 16 x 16 grid owns
 // rows {tr*H + a, TILE/2 + tr*H + a} and columns {tc*H + b, TILE/2 + tc*H + b},
 // H = TILE/32 (16-byte shared-memory vectors, conflict-free per quarter warp).
-// part: 0 every tile; 1 the first tile row and column (with TILE == NB, the
-// next panel's diagonal block and strips); 2 the other tiles.
 template <class T, int NB, int TILE>
-__global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __restrict__ items, int p, int nt,
-                                                        int part) {
-    const EngItem<T> it = items[blockIdx.x];
-    if (p >= it.k) return;
+__device__ void update_body(const EngItem<T>& it, int p, int ti, int tj, unsigned char* usm) {
     const int w = min(NB, it.k - p);
     const int n = it.n;
     const long long ld = it.ld;
     const int m0 = p + w;
-    const int y = blockIdx.y;
-    int ti, tj;
-    if (part == 0) {
-        ti = y / nt;
-        tj = y - ti * nt;
-    } else if (part == 1) {
-        ti = y < nt ? 0 : y - nt + 1;
-        tj = y < nt ? y : 0;
-    } else {
-        ti = 1 + y / (nt - 1);
-        tj = 1 + y % (nt - 1);
-    }
     const int r0 = m0 + ti * TILE, c0 = m0 + tj * TILE;
     if (r0 >= n || c0 >= n) return;
     constexpr int H = TILE / 32;              // elements per half per thread (4 in FP32, 2 in FP64)
     constexpr int LDT = TILE + 4;
-    __shared__ __align__(16) T Ls[KC][LDT];  // L21 chunk, transposed: Ls[k][r]
-    __shared__ __align__(16) T Us[KC][LDT];  // U12 chunk: Us[k][c]
+    T (*Ls)[LDT] = reinterpret_cast<T (*)[LDT]>(usm);                       // L21 chunk, transposed
+    T (*Us)[LDT] = reinterpret_cast<T (*)[LDT]>(usm + sizeof(T) * KC * LDT);  // U12 chunk
     T* A = it.a;
     const int t = threadIdx.x;
     const int tr = t >> 4, tc = t & 15;
@@ -356,12 +351,12 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
         for (int q = t; q < TILE * KC; q += UPD_THREADS) {
             const int r = q / KC, k = q - r * KC;
             const int gr = r0 + r;
-            Ls[k][r] = (gr < n && k < kw) ? A[(long long)gr * ld + p + k0 + k] : (T)0;
+            Ls[k][r] = (gr < n && k < kw) ? __ldcg(A + (long long)gr * ld + p + k0 + k) : (T)0;
         }
         for (int q = t; q < TILE * KC; q += UPD_THREADS) {
             const int k = q / TILE, c = q - k * TILE;
             const int gc = c0 + c;
-            Us[k][c] = (gc < n && k < kw) ? A[(long long)(p + k0 + k) * ld + gc] : (T)0;
+            Us[k][c] = (gc < n && k < kw) ? __ldcg(A + (long long)(p + k0 + k) * ld + gc) : (T)0;
         }
         __syncthreads();
 #pragma unroll 4
@@ -386,9 +381,36 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
 #pragma unroll
         for (int b = 0; b < 2 * H; ++b) {
             const int gc = c0 + (b < H ? tc * H + b : TILE / 2 + tc * H + b - H);
-            if (gc < n) row[gc] -= acc[a][b];
+            if (gc < n) row[gc] = __ldcg(row + gc) - acc[a][b];
         }
     }
+}
+
+template <class T, int TILE>
+__host__ __device__ constexpr size_t upd_smem() { return 2 * sizeof(T) * KC * (TILE + 4); }
+
+// M22 -= L21 U12, one TILE x TILE tile per CTA.  part: 0 every tile; 1 the first
+// tile row and column (with TILE == NB, the next panel's diagonal block and
+// strips); 2 the other tiles.
+template <class T, int NB, int TILE>
+__global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __restrict__ items, int p, int nt,
+                                                        int part) {
+    const EngItem<T> it = items[blockIdx.x];
+    if (p >= it.k) return;
+    const int y = blockIdx.y;
+    int ti, tj;
+    if (part == 0) {
+        ti = y / nt;
+        tj = y - ti * nt;
+    } else if (part == 1) {
+        ti = y < nt ? 0 : y - nt + 1;
+        tj = y < nt ? y : 0;
+    } else {
+        ti = 1 + y / (nt - 1);
+        tj = 1 + y % (nt - 1);
+    }
+    __shared__ __align__(16) unsigned char usm[upd_smem<T, TILE>()];
+    update_body<T, NB, TILE>(it, p, ti, tj, usm);
 }
 
 template <class T>
@@ -403,10 +425,148 @@ size_t diag_smem() {
     return sizeof(T) * ((size_t)NB * (NB + 1) + NB);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent task kernel.  The host lists the tasks of all panels of all items
+// in a topological order (every task after the tasks it depends on, the next
+// panel's diagonal block and strips ahead of the bulk of the current update);
+// resident CTAs take tasks from an atomic counter, wait for their inputs on
+// per-task completion flags and run them.  A CTA only waits for tasks taken
+// earlier, which running CTAs hold, so the scheme needs no co-residency.  Every
+// wait is bounded: on expiry the kernel flags ERR_TIMEOUT_ENGINE and stops
+// waiting (the tasks then finish without their inputs, the error is reported).
+// ---------------------------------------------------------------------------
+struct EngTask {
+    int type;     // 0 diagonal block, 1 L21 row chunk a, 2 U12 column chunk a, 3 tile (a, b)
+    int item;
+    int panel;
+    int a, b;
+};
+struct EngMeta {
+    int off;      // first flag of the item
+    int P;        // panels of the item
+    int NCH;      // chunk slots per panel
+    int NT;       // tile slots per panel and direction
+};
+
+__device__ __forceinline__ int flag_diag(const EngMeta& m, int pi) { return m.off + pi; }
+__device__ __forceinline__ int flag_row(const EngMeta& m, int pi, int c) { return m.off + m.P + pi * m.NCH + c; }
+__device__ __forceinline__ int flag_col(const EngMeta& m, int pi, int c) {
+    return m.off + m.P + m.P * m.NCH + pi * m.NCH + c;
+}
+__device__ __forceinline__ int flag_tile(const EngMeta& m, int pi, int ti, int tj) {
+    return m.off + m.P + 2 * m.P * m.NCH + (pi * m.NT + ti) * m.NT + tj;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* f) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    return v;
+}
+
+constexpr long long ENG_WAIT_LIMIT = 1LL << 24;    // x ~0.1 us sleeps: a few seconds
+
+__device__ void wait_flag(const int* f, int* abort_flag, int* err) {
+    long long it = 0;
+    while (ld_acquire(f) == 0) {
+        if (*(volatile int*)abort_flag) return;
+        if (++it > ENG_WAIT_LIMIT) {
+            atomicOr(err, ERR_TIMEOUT_ENGINE);
+            atomicExch(abort_flag, 1);
+            return;
+        }
+        __nanosleep(100);
+    }
+}
+
+// wait for every tile of the previous panel overlapping rows [r0, r1) x cols [c0, c1)
+// (coordinates relative to the previous panel's trailing origin)
+__device__ void wait_prev_tiles(const int* flags, const EngMeta& m, int pi_prev, int ntp, int r0, int r1, int c0,
+                                int c1, int tile, int* abort_flag, int* err) {
+    const int t0 = r0 / tile, t1 = min((r1 - 1) / tile, ntp - 1);
+    const int u0 = c0 / tile, u1 = min((c1 - 1) / tile, ntp - 1);
+    for (int a = t0; a <= t1; ++a)
+        for (int b = u0; b <= u1; ++b) wait_flag(flags + flag_tile(m, pi_prev, a, b), abort_flag, err);
+}
+
+template <class T, int NB, int TILE>
+__global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T>* __restrict__ items,
+                                                                 const EngTask* __restrict__ tasks, int ntasks,
+                                                                 const EngMeta* __restrict__ meta, int* flags,
+                                                                 int* next, int* abort_flag, T* __restrict__ scr,
+                                                                 long long stride, int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char esm[];
+    __shared__ int s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(next, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= ntasks) break;
+        const EngTask tk = tasks[idx];
+        const EngItem<T> it = items[tk.item];
+        const EngMeta m = meta[tk.item];
+        const int pi = tk.panel, p = pi * NB;
+        const int w = min(NB, it.k - p);
+        const int m0 = p + w;
+        int own;
+        if (threadIdx.x == 0) {
+            // inputs: the previous panel's update of the region, and this panel's factors
+            const int pp = p - NB;                         // previous panel's trailing origin is p
+            const int ntp = (it.n - p + TILE - 1) / TILE;  // its tiles per direction
+            if (tk.type == 0) {
+                if (pi > 0) wait_prev_tiles(flags, m, pi - 1, ntp, 0, w, 0, w, TILE, abort_flag, err);
+            } else if (tk.type == 1 || tk.type == 2) {
+                wait_flag(flags + flag_diag(m, pi), abort_flag, err);
+                if (pi > 0) {
+                    const int g0 = w + tk.a * CH, g1 = min(it.n - p, g0 + CH);
+                    if (tk.type == 1) wait_prev_tiles(flags, m, pi - 1, ntp, g0, g1, 0, w, TILE, abort_flag, err);
+                    else wait_prev_tiles(flags, m, pi - 1, ntp, 0, w, g0, g1, TILE, abort_flag, err);
+                }
+            } else {
+                const int nch = (it.n - m0 + CH - 1) / CH;
+                const int ca = (tk.a * TILE) / CH, cb = min(nch - 1, ((tk.a + 1) * TILE - 1) / CH);
+                for (int c = ca; c <= cb; ++c) wait_flag(flags + flag_row(m, pi, c), abort_flag, err);
+                const int da = (tk.b * TILE) / CH, db = min(nch - 1, ((tk.b + 1) * TILE - 1) / CH);
+                for (int c = da; c <= db; ++c) wait_flag(flags + flag_col(m, pi, c), abort_flag, err);
+                if (pi > 0) {
+                    const int r0 = w + tk.a * TILE, c0 = w + tk.b * TILE;
+                    wait_prev_tiles(flags, m, pi - 1, ntp, r0, min(it.n - p, r0 + TILE), c0,
+                                    min(it.n - p, c0 + TILE), TILE, abort_flag, err);
+                }
+            }
+            (void)pp;
+        }
+        __syncthreads();
+        T* pv = scr + (long long)tk.item * stride + (long long)pi * NB;
+        if (tk.type == 0) {
+            diag_body<T, NB>(it, p, pv, err, esm);
+            own = flag_diag(m, pi);
+        } else if (tk.type == 1 || tk.type == 2) {
+            trsm_body<T, NB>(it, p, tk.type == 2, tk.a, pv, esm);
+            own = tk.type == 1 ? flag_row(m, pi, tk.a) : flag_col(m, pi, tk.a);
+        } else {
+            update_body<T, NB, TILE>(it, p, tk.a, tk.b, esm);
+            own = flag_tile(m, pi, tk.a, tk.b);
+        }
+        __threadfence();        // every thread's results, before the completion flag
+        __syncthreads();
+        if (threadIdx.x == 0)
+            asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(flags + own), "r"(1) : "memory");
+    }
+}
+
+template <class T>
+size_t task_smem() {
+    constexpr int TILE = EngCfg<T>::TILE;
+    return std::max(std::max(diag_smem<T>(), trsm_smem<T>()), upd_smem<T, TILE>());
+}
+
 }  // namespace
 
-long long engine_scratch_elems(int count, bool dbl) {
-    return (long long)count * (dbl ? scratch_per_item<double>() : scratch_per_item<float>());
+long long engine_scratch_elems(int count, bool dbl, int maxk) {
+    const int nb = dbl ? EngCfg<double>::NB : EngCfg<float>::NB;
+    const long long np = std::max(1, (maxk + nb - 1) / nb);
+    return (long long)count * nb * np;
 }
 
 namespace {
@@ -420,38 +580,138 @@ struct LookAhead {
         BDDC_CUDA_TRY(cudaGetDevice(&d));
         if (side && d == dev) return BDDC_OK;
         dev = d;                              // (a stream of another device is left alive)
-        BDDC_CUDA_TRY(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        int lo = 0, hi = 0;
+        BDDC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        // highest priority: the next panel's CTAs take SM slots as update CTAs retire
+        BDDC_CUDA_TRY(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi));
         BDDC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
         BDDC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
         return BDDC_OK;
     }
 };
 thread_local LookAhead g_la;
+
+// Task list of the persistent kernel (host), in the order described above.
+template <class T>
+static void build_tasks(const int* hn, const int* hk, int count, std::vector<EngTask>& tasks,
+                        std::vector<EngMeta>& meta, int& nflags) {
+    constexpr int NB = EngCfg<T>::NB, TILE = EngCfg<T>::TILE;
+    meta.resize(count);
+    nflags = 0;
+    int Pmax = 0;
+    for (int i = 0; i < count; ++i) {
+        EngMeta& m = meta[i];
+        m.P = hk[i] > 0 ? (hk[i] + NB - 1) / NB : 0;
+        m.NCH = std::max(1, (hn[i] + CH - 1) / CH);
+        m.NT = std::max(1, (hn[i] + TILE - 1) / TILE);
+        m.off = nflags;
+        nflags += m.P * (1 + 2 * m.NCH + m.NT * m.NT);
+        Pmax = std::max(Pmax, m.P);
+    }
+    auto geom = [&](int i, int pi, int& nch, int& nt) {
+        const int p = pi * NB, w = std::min(NB, hk[i] - p), mrem = hn[i] - p - w;
+        nch = (mrem + CH - 1) / CH;
+        nt = (mrem + TILE - 1) / TILE;
+    };
+    auto add_diag = [&](int pi) {
+        for (int i = 0; i < count; ++i)
+            if (pi < meta[i].P) tasks.push_back(EngTask{0, i, pi, 0, 0});
+    };
+    auto add_rc = [&](int pi) {
+        for (int i = 0; i < count; ++i) {
+            if (pi >= meta[i].P) continue;
+            int nch, nt;
+            geom(i, pi, nch, nt);
+            for (int c = 0; c < nch; ++c) {
+                tasks.push_back(EngTask{1, i, pi, c, 0});
+                tasks.push_back(EngTask{2, i, pi, c, 0});
+            }
+        }
+    };
+    auto add_tiles = [&](int pi, bool first) {
+        for (int i = 0; i < count; ++i) {
+            if (pi >= meta[i].P) continue;
+            int nch, nt;
+            geom(i, pi, nch, nt);
+            for (int a = 0; a < nt; ++a)
+                for (int b = 0; b < nt; ++b)
+                    if ((a == 0 || b == 0) == first) tasks.push_back(EngTask{3, i, pi, a, b});
+        }
+    };
+    // D(0) RC(0) Uf(0) | D(1) Ur(0) RC(1) Uf(1) | D(2) Ur(1) ...: the next diagonal
+    // block starts as soon as its tile is updated, the bulk of the current update
+    // fills the GPU meanwhile, and the strips that need the new factors come after
+    if (Pmax == 0) return;
+    add_diag(0);
+    add_rc(0);
+    add_tiles(0, true);
+    for (int pi = 0; pi < Pmax; ++pi) {
+        if (pi + 1 < Pmax) add_diag(pi + 1);
+        add_tiles(pi, false);
+        if (pi + 1 < Pmax) {
+            add_rc(pi + 1);
+            add_tiles(pi + 1, true);
+        }
+    }
+}
 }  // namespace
 
-// Per panel p: k_diag, k_trsm, k_update.  With look-ahead (FP32/FP64 CUDA-core
-// updates, kernel timer off) the update of panel p is split: the first tile row
-// and column -- exactly the next panel's diagonal block and strips -- go first;
-// the next panel's k_diag and k_trsm then run on a side stream while the main
-// stream updates the remaining tiles, which they do not touch.
+// Eliminate the leading k_i unknowns of every item.  Default: one persistent
+// task kernel per call.  With the kernel timer on (or the tensor-core update)
+// the per-panel launches k_diag, k_trsm, k_update run instead, so that every
+// launch of a kernel class can be bracketed by events.
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* dscr, int* err,
                cudaStream_t st, const int* hn, const int* hk, bool tc) {
     constexpr int NB = EngCfg<T>::NB, TILE = EngCfg<T>::TILE;
-    static_assert(NB == TILE, "the look-ahead split needs one tile per panel");
+    static_assert(NB == TILE, "the task dependencies assume one tile per panel");
     if (count <= 0 || maxk <= 0) return BDDC_OK;
+    const long long stride = (long long)NB * std::max(1, (maxk + NB - 1) / NB);
+    const bool timed = ktimer_on(KT_ENGINE_UPDATE) || ktimer_on(KT_ENGINE_PANEL);
+    const bool use_tc = tc && sizeof(T) == 4;
+    if (!timed && !use_tc && hn && hk) {
+        std::vector<EngTask> tasks;
+        std::vector<EngMeta> meta;
+        int nflags = 0;
+        build_tasks<T>(hn, hk, count, tasks, meta, nflags);
+        if (tasks.empty()) return BDDC_OK;
+        // one allocation for the task list, the item table and the flags, freed by
+        // the stream-ordered allocator after the launch
+        const size_t tb = tasks.size() * sizeof(EngTask), mb = meta.size() * sizeof(EngMeta);
+        const size_t fb = sizeof(int) * ((size_t)nflags + 2);
+        const size_t o1 = (tb + 255) & ~size_t(255), o2 = o1 + ((mb + 255) & ~size_t(255));
+        std::vector<unsigned char> host(o2);
+        memcpy(host.data(), tasks.data(), tb);
+        memcpy(host.data() + o1, meta.data(), mb);
+        unsigned char* dev = nullptr;
+        BDDC_CUDA_TRY(cudaMallocAsync((void**)&dev, o2 + fb, st));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(dev, host.data(), o2, cudaMemcpyHostToDevice, st));
+        int* flags = reinterpret_cast<int*>(dev + o2);
+        BDDC_CUDA_TRY(cudaMemsetAsync(flags, 0, fb, st));
+        const size_t sm = task_smem<T>();
+        auto kern = k_engine_tasks<T, NB, TILE>;
+        BDDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int dev_id = 0, nsm = 0, occ = 0;
+        BDDC_CUDA_TRY(cudaGetDevice(&dev_id));
+        BDDC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id));
+        BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, UPD_THREADS, sm));
+        const int grid = (int)std::min<long long>((long long)nsm * std::max(occ, 1), (long long)tasks.size());
+        kern<<<grid, UPD_THREADS, sm, st>>>(items_dev, reinterpret_cast<const EngTask*>(dev), (int)tasks.size(),
+                                             reinterpret_cast<const EngMeta*>(dev + o1), flags, flags + nflags,
+                                             flags + nflags + 1, dscr, stride, err);
+        bddc_note_launches(1);
+        BDDC_CUDA_TRY(cudaGetLastError());
+        BDDC_CUDA_TRY(cudaFreeAsync(dev, st));
+        return BDDC_OK;
+    }
     const size_t dsm = diag_smem<T>();
     const size_t tsm = trsm_smem<T>();
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_diag<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_trsm<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    const bool timed = ktimer_on(KT_ENGINE_UPDATE) || ktimer_on(KT_ENGINE_PANEL);
-    const bool use_tc = tc && sizeof(T) == 4;
-    const bool ahead = !timed && !use_tc && maxk > NB;
-    if (ahead) BDDC_TRY(g_la.init());
     auto panel = [&](int p, cudaStream_t s) -> int {
         const int nch = (std::max(maxn - p, 1) + CH - 1) / CH;
-        k_diag<T, NB><<<count, DIAG_THREADS, dsm, s>>>(items_dev, p, dscr, err);
-        k_trsm<T, NB><<<dim3(count, 2 * nch), TRSM_THREADS, tsm, s>>>(items_dev, p, dscr, nch);
+        k_diag<T, NB><<<count, DIAG_THREADS, dsm, s>>>(items_dev, p, dscr, stride, err);
+        k_trsm<T, NB><<<dim3(count, 2 * nch), TRSM_THREADS, tsm, s>>>(items_dev, p, dscr, stride, nch);
         bddc_note_launches(2);
         return BDDC_OK;
     };
@@ -469,30 +729,9 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
                 fp += 2.0 * w * w * w / 3.0 + 2.0 * w * w * m;
                 bu += sizeof(T) * (2.0 * m * m + 2.0 * m * w);   // read + write M22, read L21, U12
             }
-        if (p == 0 || !ahead) {
-            ktimer_begin(KT_ENGINE_PANEL, st);
-            BDDC_TRY(panel(p, st));
-            ktimer_end(KT_ENGINE_PANEL, st, fp, 0.0);
-        }
-        const bool next = ahead && p + NB < maxk && nt > 1;
-        if (next) {
-            k_update<T, NB, TILE><<<dim3(count, 2 * nt - 1), UPD_THREADS, 0, st>>>(items_dev, p, nt, 1);
-            BDDC_CUDA_TRY(cudaEventRecord(g_la.fork, st));
-            BDDC_CUDA_TRY(cudaStreamWaitEvent(g_la.side, g_la.fork, 0));
-            BDDC_TRY(panel(p + NB, g_la.side));
-            BDDC_CUDA_TRY(cudaEventRecord(g_la.join, g_la.side));
-            k_update<T, NB, TILE><<<dim3(count, (nt - 1) * (nt - 1)), UPD_THREADS, 0, st>>>(items_dev, p, nt, 2);
-            BDDC_CUDA_TRY(cudaStreamWaitEvent(st, g_la.join, 0));
-            bddc_note_launches(2);
-            continue;
-        }
-        if (ahead && p + NB < maxk) {
-            // a single tile row remains: no split; the next panel follows in order
-            k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt, 0);
-            bddc_note_launches(1);
-            BDDC_TRY(panel(p + NB, st));
-            continue;
-        }
+        ktimer_begin(KT_ENGINE_PANEL, st);
+        BDDC_TRY(panel(p, st));
+        ktimer_end(KT_ENGINE_PANEL, st, fp, 0.0);
         ktimer_begin(KT_ENGINE_UPDATE, st);
         if constexpr (sizeof(T) == 4) {
             if (use_tc) {
@@ -507,7 +746,6 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
             bddc_note_launches(1);
         }
         ktimer_end(KT_ENGINE_UPDATE, st, fu, bu);
-        if (ahead && p + NB < maxk) BDDC_TRY(panel(p + NB, st));
     }
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
