@@ -119,6 +119,8 @@ typedef struct {
     double t_mesh_ms;        /* host numbering / entity lists / coefficient staging */
     double t_basis_ms;       /* change of basis + extended elimination (part of
                                 t_coarse_ms)                                      */
+    int coarse_path;         /* coarse inverse by 0: elimination, 1: FP32 Gauss-
+                                Jordan + FP64 Newton-Schulz (n_Pi <= 128)          */
 } bddc_stats;
 
 typedef struct bddc_ctx bddc_ctx;

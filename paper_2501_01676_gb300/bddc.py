@@ -49,7 +49,8 @@ class Stats(ct.Structure):
                 ("nsub", ct.c_int), ("edges_skipped", ct.c_int), ("setup_ms", ct.c_double),
                 ("solve_ms", ct.c_double), ("t_assemble_ms", ct.c_double), ("t_factor_ms", ct.c_double),
                 ("t_face_ms", ct.c_double), ("t_edge_ms", ct.c_double), ("t_coarse_ms", ct.c_double),
-                ("jacobi_sweeps_max", ct.c_int), ("t_mesh_ms", ct.c_double), ("t_basis_ms", ct.c_double)]
+                ("jacobi_sweeps_max", ct.c_int), ("t_mesh_ms", ct.c_double), ("t_basis_ms", ct.c_double),
+                ("coarse_path", ct.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -107,7 +107,7 @@ constexpr int BDDC_MAX_INTERIOR = 2048;
 
 // Coarse matrices up to this order are inverted by one CTA (FP32 Gauss-Jordan
 // in shared memory) plus FP64 Newton-Schulz steps.
-constexpr int COARSE_GJ_MAX = 160;
+constexpr int COARSE_GJ_MAX = 128;
 int coarse_inverse_small(const double* S, int n, double* X, int ldx, double* work, double* resid, int ns_steps,
                          int* err, cudaStream_t st);
 

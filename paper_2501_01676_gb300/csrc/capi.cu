@@ -1095,7 +1095,7 @@ static int setup_impl(bddc_ctx* C) {
         double* resid = nullptr;
         BDDC_TRY(C->alloc(&work, 2LL * nPi * nPi));
         BDDC_TRY(C->alloc(&resid, 3));
-        const int steps = C->mixed ? 2 : 3;
+        const int steps = C->mixed ? 3 : 4;
         int* gjflag = nullptr;                    // a failed FP32 pivot only shows in the residual
         BDDC_TRY(C->alloc(&gjflag, 1));
         BDDC_TRY(coarse_inverse_small(SPi, nPi, C->SPiInv, ldc, work, resid, steps, gjflag, st));
@@ -1217,6 +1217,7 @@ static int setup_impl(bddc_ctx* C) {
         const double floor64 = 8.0 * nPi * 1.11e-16 * hres[1] * hres[2];
         const double target = C->mixed ? std::max(1e-9, floor64) : std::max(1e-14, floor64);
         coarse_done = std::isfinite(hres[0]) && hres[0] <= target;
+        C->stats.coarse_path = coarse_done ? 1 : 0;
     }
     if (nPi > 0 && !coarse_done) {
         double* Xc = nullptr;

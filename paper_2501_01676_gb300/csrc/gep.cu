@@ -231,12 +231,12 @@ __device__ void pinv_schur_tail(T* M, int ld, int n, int r0, unsigned char* done
         }
         if (bi_s < 0 || !(best_s > tol)) break;
         const int p = bi_s;
-        const T dp = M[p * ld + p];
+        const T rdp = (T)1 / M[p * ld + p];
         // update all not-yet-eliminated rows/cols (including the kept block)
         CTA_FOR_2D(i, j, n, n) {
             if (i == p || j == p) continue;
             if ((i >= r0 && done[i]) || (j >= r0 && done[j])) continue;
-            M[i * ld + j] -= M[i * ld + p] * M[p * ld + j] / dp;
+            M[i * ld + j] -= M[i * ld + p] * rdp * M[p * ld + j];
         }
         bar();
         if (threadIdx.x == 0) done[p] = 1;
@@ -415,6 +415,254 @@ __device__ void trsm_lower_t(const T* Ls, int ldl, T* X, int ldx, int n, int m) 
     }
 }
 
+// Largest order the tridiagonal eigen-solver handles (shared-memory vectors).
+constexpr int TRI_EIG_MAX = 128;
+
+// Sturm count: eigenvalues of the symmetric tridiagonal (d, e) below x.
+template <class T>
+__device__ __forceinline__ int sturm_count(const T* d, const T* e2, int n, T x, T pivmin) {
+    int c = 0;
+    T q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < (T)0;
+    for (int i = 1; i < n; ++i) {
+        q = d[i] - x - e2[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        c += q < (T)0;
+    }
+    return c;
+}
+
+// Eigen-decomposition of the symmetric n x n matrix A (shared memory, stride ld;
+// destroyed) for the eigenvalues >= thr only: every eigenvalue goes to sig[0..n)
+// in decreasing order; the eigenvectors of the first s (those >= thr) to the
+// columns 0..s-1 of V (row stride ldv); s is returned.  Steps: Householder
+// reduction to tridiagonal form (reflectors kept in A's lower part), all
+// eigenvalues by parallel multisection on Sturm counts (8 lanes per eigenvalue),
+// inverse iteration with partial pivoting on the tridiagonal for the selected
+// ones (re-orthogonalised within clusters), back-transformation by the
+// reflectors.  work: 5 n elements per selected eigenvalue, cap of them; when more
+// than cap eigenvalues are selected no vector is computed and -s is returned.
+template <class T>
+__device__ int tridiag_eig_sel(T* A, int ld, int n, T thr, T* sig, T* V, int ldv, T* work, int cap) {
+    __shared__ T td[TRI_EIG_MAX], te[TRI_EIG_MAX], te2[TRI_EIG_MAX], tb[TRI_EIG_MAX], tv[TRI_EIG_MAX],
+        tp[TRI_EIG_MAX];
+    __shared__ T sc_s[2];
+    __shared__ int s_sel;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    // ---- 1. tridiagonalisation: step k zeroes A[k+2.., k]
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        if (wid == 0) {
+            T sg = 0;
+            for (int i = 1 + lane; i < m; i += 32) {
+                const T x = A[(k + 1 + i) * ld + k];
+                sg += x * x;
+            }
+            sg = wsum(sg);
+            if (lane == 0) {
+                const T x0 = A[(k + 1) * ld + k];
+                if (sg == (T)0) {
+                    sc_s[0] = 0;          // beta: column already reduced
+                    te[k] = x0;
+                    tv[0] = 0;
+                } else {
+                    const T nrm = sqrt(x0 * x0 + sg);
+                    const T alpha = x0 >= (T)0 ? -nrm : nrm;
+                    const T v0 = x0 - alpha;
+                    tv[0] = v0;
+                    sc_s[0] = (T)2 / (v0 * v0 + sg);
+                    te[k] = alpha;
+                }
+                td[k] = A[k * ld + k];
+            }
+            __syncwarp();
+            for (int i = 1 + lane; i < m; i += 32) tv[i] = A[(k + 1 + i) * ld + k];
+        }
+        bar();
+        const T beta = sc_s[0];
+        if (beta != (T)0) {
+            // p = beta A_sub v
+            for (int i = t; i < m; i += GT) {
+                const T* row = A + (k + 1 + i) * ld + k + 1;
+                T acc = 0;
+                for (int j = 0; j < m; ++j) acc += row[j] * tv[j];
+                tp[i] = beta * acc;
+            }
+            bar();
+            if (wid == 0) {
+                T kk = 0;
+                for (int i = lane; i < m; i += 32) kk += tp[i] * tv[i];
+                kk = wsum(kk);
+                if (lane == 0) sc_s[1] = (T)0.5 * beta * kk;
+            }
+            bar();
+            const T K = sc_s[1];
+            for (int i = t; i < m; i += GT) tp[i] -= K * tv[i];      // w = p - K v
+            bar();
+            CTA_FOR_2D(i, j, m, m) A[(k + 1 + i) * ld + k + 1 + j] -= tv[i] * tp[j] + tp[i] * tv[j];
+        }
+        // keep the reflector (v, beta) for the back-transformation
+        for (int i = t; i < m; i += GT) A[(k + 1 + i) * ld + k] = tv[i];
+        if (t == 0) tb[k] = beta;
+        bar();
+    }
+    if (t == 0) {
+        if (n >= 2) {
+            td[n - 2] = A[(n - 2) * ld + n - 2];
+            te[n - 2] = A[(n - 1) * ld + n - 2];
+        }
+        td[n - 1] = A[(n - 1) * ld + n - 1];
+    }
+    bar();
+    for (int i = t; i + 1 < n; i += GT) te2[i] = te[i] * te[i];
+    // Gershgorin interval
+    if (t == 0) {
+        T lo = td[0], hi = td[0], amax = 0;
+        for (int i = 0; i < n; ++i) {
+            const T r = (i > 0 ? fabs(te[i - 1]) : (T)0) + (i + 1 < n ? fabs(te[i]) : (T)0);
+            lo = fmin(lo, td[i] - r);
+            hi = fmax(hi, td[i] + r);
+            amax = fmax(amax, fmax(fabs(td[i]), r));
+        }
+        sc_s[0] = lo - (T)1e-6 * (amax + (T)1e-30);
+        sc_s[1] = hi + (T)1e-6 * (amax + (T)1e-30);
+    }
+    bar();
+    // ---- 2. all eigenvalues: 8 lanes per eigenvalue, 9-section per round
+    {
+        const T lo0 = sc_s[0], hi0 = sc_s[1];
+        const T pivmin = (T)1e-30 + (T)4 * (T)Tol<T>::tiny;
+        const int sub = lane & 7;
+        for (int g0 = 0; g0 < n; g0 += GT / 8) {
+            const int g = g0 + (t >> 3);                // ascending index j
+            const bool act = g < n;
+            T a = lo0, b = hi0;
+            for (int round = 0; round < 12; ++round) {
+                const T x = a + (b - a) * (T)(sub + 1) / (T)9;
+                const int c = act ? sturm_count(td, te2, n, x, pivmin) : n;
+                const unsigned ok = __ballot_sync(0xffffffffu, c <= g) >> (lane & 24);
+                const int cnt = __popc(ok & 0xffu);    // points (increasing) at or below lambda_g
+                const T xa = __shfl_sync(0xffffffffu, x, (lane & 24) + max(cnt - 1, 0));
+                const T xb = __shfl_sync(0xffffffffu, x, (lane & 24) + min(cnt, 7));
+                const T na = cnt > 0 ? xa : a;
+                const T nb = cnt < 8 ? xb : b;
+                a = na;
+                b = nb;
+            }
+            if (act && sub == 0) sig[n - 1 - g] = (T)0.5 * (a + b);
+        }
+    }
+    bar();
+    if (t == 0) {
+        int c = 0;
+        while (c < n && sig[c] >= thr) ++c;
+        s_sel = c;
+    }
+    bar();
+    const int s = s_sel;
+    if (s == 0) return 0;
+    if (s > cap) return -s;
+    // ---- 3. inverse iteration on T - lambda I (thread per selected eigenvalue)
+    T amax = 0;
+    for (int i = 0; i < n; ++i) amax = fmax(amax, fabs(td[i]) + (i + 1 < n ? fabs(te[i]) : (T)0));
+    const T eps = sizeof(T) == 4 ? (T)1.2e-7 : (T)2.3e-16;
+    for (int it = 0; it < 3; ++it) {
+        for (int q = t; q < s; q += GT) {
+            T* x = V + q;                                    // column q, stride ldv
+            T* u0 = work + (size_t)q * 5 * n;
+            T* u1 = u0 + n;
+            T* u2 = u1 + n;
+            T* ml = u2 + n;
+            T* sw = ml + n;
+            const T lam = sig[q];
+            if (it == 0)
+                for (int i = 0; i < n; ++i)                  // a start vector particular to q
+                    x[i * ldv] = (T)1 + (T)0.25 * sin((T)(0.7 + 0.37 * q) * (T)(i + 1));
+            // factor T - lam I with partial pivoting (rows i, i+1)
+            T a = td[0] - lam, b = n > 1 ? te[0] : (T)0, c2 = 0;
+            for (int i = 0; i < n; ++i) {
+                if (i + 1 < n) {
+                    const T cdn = te[i];                     // subdiagonal of row i+1
+                    const T an = td[i + 1] - lam;
+                    const T bn = i + 2 < n ? te[i + 1] : (T)0;
+                    if (fabs(a) >= fabs(cdn)) {
+                        const T mlt = a != (T)0 ? cdn / a : (T)0;
+                        u0[i] = a; u1[i] = b; u2[i] = c2; ml[i] = mlt; sw[i] = 0;
+                        a = an - mlt * b;
+                        b = bn;
+                        c2 = 0;
+                    } else {
+                        const T mlt = a / cdn;
+                        u0[i] = cdn; u1[i] = an; u2[i] = bn; ml[i] = mlt; sw[i] = 1;
+                        a = b - mlt * an;
+                        b = -mlt * bn;
+                        c2 = 0;
+                    }
+                } else {
+                    u0[i] = a; u1[i] = 0; u2[i] = 0;
+                }
+                if (fabs(u0[i]) < eps * amax) u0[i] = u0[i] >= (T)0 ? eps * amax : -eps * amax;
+            }
+            // forward: apply the row operations to x
+            for (int i = 0; i + 1 < n; ++i) {
+                T xi = x[i * ldv], xn = x[(i + 1) * ldv];
+                if (sw[i] != (T)0) {
+                    const T tmp = xi;
+                    xi = xn;
+                    xn = tmp;
+                }
+                x[i * ldv] = xi;
+                x[(i + 1) * ldv] = xn - ml[i] * xi;
+            }
+            // back substitution with the banded U (diagonal u0, superdiagonals u1, u2)
+            for (int i = n - 1; i >= 0; --i) {
+                T v = x[i * ldv];
+                if (i + 1 < n) v -= u1[i] * x[(i + 1) * ldv];
+                if (i + 2 < n) v -= u2[i] * x[(i + 2) * ldv];
+                x[i * ldv] = v / u0[i];
+            }
+            T nn = 0;
+            for (int i = 0; i < n; ++i) nn += x[i * ldv] * x[i * ldv];
+            nn = (T)1 / sqrt(fmax(nn, (T)1e-300));
+            for (int i = 0; i < n; ++i) x[i * ldv] *= nn;
+        }
+        bar();
+        // re-orthogonalise within clusters (eigenvalues closer than 1e-3 of the spread)
+        if (t == 0) {
+            const T gap = (T)1e-3 * fmax(amax, (T)1e-30);
+            for (int q = 1; q < s; ++q) {
+                for (int r = 0; r < q; ++r) {
+                    if (fabs(sig[r] - sig[q]) > gap) continue;
+                    T dp = 0;
+                    for (int i = 0; i < n; ++i) dp += V[i * ldv + r] * V[i * ldv + q];
+                    for (int i = 0; i < n; ++i) V[i * ldv + q] -= dp * V[i * ldv + r];
+                }
+                T nn = 0;
+                for (int i = 0; i < n; ++i) nn += V[i * ldv + q] * V[i * ldv + q];
+                nn = (T)1 / sqrt(fmax(nn, (T)1e-300));
+                for (int i = 0; i < n; ++i) V[i * ldv + q] *= nn;
+            }
+        }
+        bar();
+    }
+    // ---- 4. back-transformation: x <- H_0 ... H_{n-3} x, one warp per vector
+    for (int q = wid; q < s; q += GT / 32) {
+        for (int k = n - 3; k >= 0; --k) {
+            const T beta = tb[k];
+            if (beta == (T)0) continue;
+            const int m = n - k - 1;
+            T dp = 0;
+            for (int i = lane; i < m; i += 32) dp += A[(k + 1 + i) * ld + k] * V[(k + 1 + i) * ldv + q];
+            dp = wsum(dp) * beta;
+            for (int i = lane; i < m; i += 32) V[(k + 1 + i) * ldv + q] -= dp * A[(k + 1 + i) * ld + k];
+            __syncwarp();
+        }
+    }
+    bar();
+    return s;
+}
+
 // Solve X v = sigma (X + Y) v for symmetric PSD X, Y (n x n in global scratch).
 // On exit: sig[0..r) decreasing, Vout (n x r, row stride r) = eigenvectors
 // with Vout^T (X+Y) Vout = I, r returned.  FP64 (the oracle's reading):
@@ -424,7 +672,7 @@ __device__ void trsm_lower_t(const T* Ls, int ldl, T* X, int ldx, int n, int m) 
 template <class T>
 __device__ int sigma_pencil(const T* X, const T* Y, int n, T* Ash, T* Vsh, int np, int ld,
                             T* work1, T* work2, T* sig, T* Vout, T* cs,
-                            T* sn, int* pp, int* qq, int* order, int* err, int* sweeps) {
+                            T* sn, int* pp, int* qq, int* order, int* err, int* sweeps, T thr) {
     __shared__ int r_s;
     CTA_FOR_2D(i, j, n, n) {
         Ash[i * ld + j] = (T)0.5 * (X[i * n + j] + X[j * n + i]) + (T)0.5 * (Y[i * n + j] + Y[j * n + i]);
@@ -448,6 +696,20 @@ __device__ int sigma_pencil(const T* X, const T* Y, int n, T* Ash, T* Vsh, int n
             }
         }
         bar();
+        if (n <= TRI_EIG_MAX) {
+            // eigenvectors are needed for the selected eigenvalues only: tridiagonal
+            // route; the matrix is kept in work2 in case more are selected than fit
+            CTA_FOR_2D(i, j, n, n) work2[i * n + j] = Ash[i * ld + j];
+            bar();
+            const int cap = (np * ld) / (5 * n);
+            const int s = tridiag_eig_sel(Ash, ld, n, thr, sig, Vout, n, Vsh, cap);
+            if (s >= 0) {
+                if (s > 0) trsm_lower_t(work1, n, Vout, n, n, s);        // V = L^{-T} Y
+                return n;
+            }
+            CTA_FOR_2D(i, j, n, n) Ash[i * ld + j] = work2[i * n + j];
+            bar();
+        }
         int sw = jacobi(Ash, Vsh, n, np, ld, cs, sn, pp, qq, err);
         if (threadIdx.x == 0) atomicMax(sweeps, sw);
         sort_desc(Ash, ld, n, order);
@@ -656,8 +918,8 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     symmetrize(Bt, n, n);
     int k = 0;
     if (J.mode == 0) {
-        int r = sigma_pencil(BF, Bt, n, Ash, Vsh, np, ldj, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1);
         const T sth = (T)(J.theta / (1.0 + J.theta) - Tol<T>::slack);
+        int r = sigma_pencil(BF, Bt, n, Ash, Vsh, np, ldj, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1, sth);
         __shared__ int nsel_s;
         if (threadIdx.x == 0) {
             int c = 0;
@@ -820,8 +1082,8 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
     for (int q = threadIdx.x; q < nn; q += GT) Qo[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
     bar();
     if (J.mode == 0) {
-        int r = sigma_pencil(ME, BB, nw, Ash, Vsh, np, ldj, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1);
         const T sth = (T)(J.theta / (1.0 + J.theta) - Tol<T>::slack);
+        int r = sigma_pencil(ME, BB, nw, Ash, Vsh, np, ldj, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1, sth);
         __shared__ int nsel_s;
         if (threadIdx.x == 0) {
             int c = 0;
