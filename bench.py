@@ -181,7 +181,7 @@ def run_ours(args):
     clocks = Clocks()
     barrier(dist)
     clocks.start()
-    B.kernel_timer(B.KT_ENGINE_UPDATE)       # CUDA events around every trailing-update launch
+    B.kernel_timer(B.KT_ENGINE_TASKS)        # CUDA events around each launch of the engine's task kernel
     l0 = B.kernel_launches()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -238,19 +238,21 @@ def run_ours(args):
             e2e_times.append((t1 - t0) * 1e3)
     e2e_ms = max_over_ranks(dist, sum(e2e_times) / len(e2e_times))
     hbm, which = peaks()
-    # The dominant setup kernel: the Schur engine's trailing update C -= L21 U12
-    # (FP32 CUDA cores, 128 x 128 tiles, panel width K = 128).  It does 2*K = 256
-    # flops per 8 bytes of C read and written (32 flop/B), above the FP32 ridge of
-    # ~11.8 flop/B (80.6 TFLOP/s over 6.8 TB/s), so the FP32 pipe bounds it
-    # ("alu": 152 SMs x 128 FP32 lanes x 2 flops x the sampled SM clock).  The
-    # timed launches run without the look-ahead split (the kernel timer disables
-    # it), one full trailing update per launch.
+    # The dominant kernel: the elimination engine's persistent task kernel (FP32
+    # CUDA cores; one launch per elimination: subdomain Schur complements, face
+    # Schur complements, constrained-solver / coarse-basis extended matrices).
+    # Its algorithmic work is the blocked LU's: per panel of width w over a
+    # trailing size m, 2 m^2 w (update) + 2 w^2 m (substitutions) + (2/3) w^3.
+    # With w = 128 the update does 32 flop per byte of the trailing matrix read
+    # and written, above the FP32 ridge of ~11.8 flop/B (80.6 TFLOP/s over
+    # 6.8 TB/s): the FP32 pipe bounds it ("alu": 152 SMs x 128 FP32 lanes x 2
+    # flops x the sampled SM clock).
     secs = kt["ms"] * 1e-3
     gbs = kt["bytes"] / secs / 1e9 if secs > 0 else 0.0
     tfl = kt["flops"] / secs / 1e12 if secs > 0 else 0.0
     sm_mhz = ck.get("sm_mhz") or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    roofline = {"kernel": "k_update<float> (Schur engine trailing update, FP32 CUDA cores, 128x128 tiles, K=128)",
+    roofline = {"kernel": "k_engine_tasks<float,128,128> (blocked LU task kernel: 128-wide panels, 128x128 update tiles)",
                 "bound": "alu", "achieved": round(tfl, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                 "frac": round(tfl / fp32_peak, 4), "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 x median sampled SM clock",

@@ -100,6 +100,9 @@ typedef struct {
     int tensor_cores;      /* MIXED: 1 = trailing updates of the FP32 eliminations on
                               the tensor cores (tcgen05, split TF32), 0 = FP32 CUDA
                               cores; ignored by the FP64 path                       */
+    int coarse_elim;       /* 1: invert S_Pi by the elimination engine always; 0:
+                              small S_Pi (n_Pi <= 128) by FP32 Gauss-Jordan + FP64
+                              Newton-Schulz when its residual check passes          */
 } bddc_opts;
 
 typedef struct {
@@ -128,7 +131,7 @@ typedef struct bddc_ctx bddc_ctx;
 /* Fill `o` with the defaults of Sect. 4: Theta_E = 10, Theta_F = 1 + ln(H/h),
  * tau = 0.7, FP64, no restart, 300 iterations, rtol 1e-8, new edge GEP,
  * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip, CUDA-core
- * trailing updates (tensor_cores 0). */
+ * trailing updates (tensor_cores 0), coarse_elim 0. */
 void bddc_default_opts(bddc_opts* o);
 
 /* Setup (call stack: assembly, batched Dirichlet factorisation + Schur
@@ -195,7 +198,9 @@ int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, i
 /* Kernel timer for roofline reporting: after bddc_kernel_timer(kind) every
  * launch of that kernel class (1 engine trailing update, 2 engine panel,
  * 3 apply GEMV, 4 face GEP, 5 edge GEP, 6 element assembly, 7 change of basis,
- * 8 interior condense / recover solves, 9 coarse inverse; 0 off) is bracketed by CUDA events on
+ * 8 interior condense / recover solves, 9 coarse inverse, 10 the engine's
+ * persistent task kernel (1 and 2 switch the engine to per-panel launches);
+ * 0 off) is bracketed by CUDA events on
  * its stream (launches captured into graphs are not).  _read synchronises on
  * the recorded events and returns their summed duration, the number of
  * launches and, where the library knows them, the algorithmic flops and

@@ -39,7 +39,8 @@ class Opts(ct.Structure):
                 ("precision", ct.c_int), ("restart", ct.c_int), ("max_iter", ct.c_int),
                 ("rtol", ct.c_double), ("edge_gep", ct.c_int), ("face_gep", ct.c_int),
                 ("all_primal", ct.c_int), ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
-                ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p), ("tensor_cores", ct.c_int)]
+                ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p), ("tensor_cores", ct.c_int),
+                ("coarse_elim", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -163,7 +164,7 @@ def load_mlp_params():
     return np.ascontiguousarray(np.load(MLP_PARAMS_FILE), dtype=np.float32)
 
 (KT_NONE, KT_ENGINE_UPDATE, KT_ENGINE_PANEL, KT_GEMV, KT_FACE, KT_EDGE, KT_ASSEMBLE, KT_TRANSFORM, KT_TRI,
- KT_COARSE) = range(10)
+ KT_COARSE, KT_ENGINE_TASKS) = range(11)
 
 
 def kernel_timer(kind):

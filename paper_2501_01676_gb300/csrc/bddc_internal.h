@@ -33,7 +33,7 @@ void bddc_note_launches(unsigned long long n);
 
 // Optional CUDA-event timing of one kernel class (for roofline reporting).
 enum { KT_NONE = 0, KT_ENGINE_UPDATE = 1, KT_ENGINE_PANEL = 2, KT_GEMV = 3, KT_FACE = 4, KT_EDGE = 5,
-       KT_ASSEMBLE = 6, KT_TRANSFORM = 7, KT_TRI = 8, KT_COARSE = 9, KT_LAST = 9 };
+       KT_ASSEMBLE = 6, KT_TRANSFORM = 7, KT_TRI = 8, KT_COARSE = 9, KT_ENGINE_TASKS = 10, KT_LAST = 10 };
 bool ktimer_on(int kind);
 void ktimer_begin(int kind, cudaStream_t st);
 void ktimer_end(int kind, cudaStream_t st, double flops, double bytes);

@@ -1087,7 +1087,7 @@ static int setup_impl(bddc_ctx* C) {
     const int ldc = r4(std::max(nPi, 1));
     BDDC_TRY(C->alloc(&C->SPiInv, (size_t)std::max(nPi, 1) * ldc));
     bool coarse_done = false;
-    const bool coarse_small = nPi > 0 && nPi <= COARSE_GJ_MAX;
+    const bool coarse_small = nPi > 0 && nPi <= COARSE_GJ_MAX && !C->o.coarse_elim;
     double* hres = reinterpret_cast<double*>(C->hst + 3);    // pinned: max|I - S X|, ||S||, ||X||
     ktimer_begin(KT_COARSE, st);
     if (coarse_small) {
@@ -1511,6 +1511,7 @@ void bddc_default_opts(bddc_opts* o) {
     o->learned_skip_p = -1.0;
     o->mlp_params = nullptr;
     o->tensor_cores = 0;
+    o->coarse_elim = 0;
 }
 
 const char* bddc_strerror(int code) {

@@ -36,6 +36,7 @@
 // traffic of the update) by the width: NB = 128 does a quarter of the
 // passes of a 32-wide panel.
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <algorithm>
 #include <cstring>
@@ -323,9 +324,27 @@ __device__ __forceinline__ void lds16<double>(const double* p, double* out) {
     out[0] = v.x; out[1] = v.y;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <class T, int TILE>
+struct UpdLayout {
+    static constexpr int VW = 16 / sizeof(T);          // elements per 16-byte copy
+    static constexpr int LKP = KC + VW;                // L21 chunk, row-major [r][k]
+    static constexpr int UKP = TILE + VW;              // U12 chunk, row-major [k][c]
+    static constexpr int BUF = TILE * LKP + KC * UKP;  // elements of one buffer
+};
+
 // M22 -= L21 U12 on one TILE x TILE tile.  Thread (tr, tc) of a 16 x 16 grid owns
 // rows {tr*H + a, TILE/2 + tr*H + a} and columns {tc*H + b, TILE/2 + tc*H + b},
-// H = TILE/32 (16-byte shared-memory vectors, conflict-free per quarter warp).
+// H = TILE/32.  The K-chunks of L21 and U12 are double-buffered in shared memory
+// by 16-byte cp.async.cg copies (L2 only: coherent with other CTAs' writes in the
+// task kernel), so the next chunk's loads overlap this chunk's FMAs; a trailing
+// origin not 16-byte aligned (only a last, narrower panel) takes plain loads.
 template <class T, int NB, int TILE>
 __device__ void update_body(const EngItem<T>& it, int p, int ti, int tj, unsigned char* usm) {
     const int w = min(NB, it.k - p);
@@ -334,10 +353,9 @@ __device__ void update_body(const EngItem<T>& it, int p, int ti, int tj, unsigne
     const int m0 = p + w;
     const int r0 = m0 + ti * TILE, c0 = m0 + tj * TILE;
     if (r0 >= n || c0 >= n) return;
+    typedef UpdLayout<T, TILE> LY;
     constexpr int H = TILE / 32;              // elements per half per thread (4 in FP32, 2 in FP64)
-    constexpr int LDT = TILE + 4;
-    T (*Ls)[LDT] = reinterpret_cast<T (*)[LDT]>(usm);                       // L21 chunk, transposed
-    T (*Us)[LDT] = reinterpret_cast<T (*)[LDT]>(usm + sizeof(T) * KC * LDT);  // U12 chunk
+    constexpr int VW = LY::VW, LKP = LY::LKP, UKP = LY::UKP;
     T* A = it.a;
     const int t = threadIdx.x;
     const int tr = t >> 4, tc = t & 15;
@@ -346,32 +364,81 @@ __device__ void update_body(const EngItem<T>& it, int p, int ti, int tj, unsigne
     for (int a = 0; a < 2 * H; ++a)
 #pragma unroll
         for (int b = 0; b < 2 * H; ++b) acc[a][b] = (T)0;
-    for (int k0 = 0; k0 < w; k0 += KC) {
+    T* buf0 = reinterpret_cast<T*>(usm);
+    T* buf1 = buf0 + LY::BUF;
+    const bool aligned = (m0 % VW) == 0 && (p % VW) == 0 && (ld % VW) == 0 &&
+                         (reinterpret_cast<unsigned long long>(A) & 15) == 0;
+    auto issue = [&](int k0, T* Lb, T* Ub) {
+        const int kw = min(KC, w - k0);
+        for (int q = t; q < TILE * (KC / VW); q += UPD_THREADS) {
+            const int r = q / (KC / VW), kv = (q - r * (KC / VW)) * VW;
+            const int gr = r0 + r;
+            int bytes = 0;
+            const T* src = A;
+            if (gr < n && kv < kw) {
+                bytes = min(VW, kw - kv) * (int)sizeof(T);
+                src = A + (long long)gr * ld + p + k0 + kv;
+            }
+            cp_async16(Lb + r * LKP + kv, src, bytes);
+        }
+        for (int q = t; q < KC * (TILE / VW); q += UPD_THREADS) {
+            const int k = q / (TILE / VW), cv = (q - k * (TILE / VW)) * VW;
+            const int gc = c0 + cv;
+            int bytes = 0;
+            const T* src = A;
+            if (k < kw && gc < n) {
+                bytes = min(VW, n - gc) * (int)sizeof(T);
+                src = A + (long long)(p + k0 + k) * ld + gc;
+            }
+            cp_async16(Ub + k * UKP + cv, src, bytes);
+        }
+        cp_async_commit();
+    };
+    auto load_plain = [&](int k0, T* Lb, T* Ub) {
         const int kw = min(KC, w - k0);
         for (int q = t; q < TILE * KC; q += UPD_THREADS) {
             const int r = q / KC, k = q - r * KC;
             const int gr = r0 + r;
-            Ls[k][r] = (gr < n && k < kw) ? __ldcg(A + (long long)gr * ld + p + k0 + k) : (T)0;
+            Lb[r * LKP + k] = (gr < n && k < kw) ? __ldcg(A + (long long)gr * ld + p + k0 + k) : (T)0;
         }
         for (int q = t; q < TILE * KC; q += UPD_THREADS) {
             const int k = q / TILE, c = q - k * TILE;
             const int gc = c0 + c;
-            Us[k][c] = (gc < n && k < kw) ? __ldcg(A + (long long)(p + k0 + k) * ld + gc) : (T)0;
+            Ub[k * UKP + c] = (gc < n && k < kw) ? __ldcg(A + (long long)(p + k0 + k) * ld + gc) : (T)0;
         }
-        __syncthreads();
+    };
+    if (aligned) issue(0, buf0, buf0 + TILE * LKP);
+    int b = 0;
+    for (int k0 = 0; k0 < w; k0 += KC, b ^= 1) {
+        T* Lc = b ? buf1 : buf0;
+        T* Uc = Lc + TILE * LKP;
+        if (aligned) {
+            cp_async_wait_all();          // this chunk (issued one iteration earlier)
+            __syncthreads();              // ... of every thread; the other buffer is free
+            if (k0 + KC < w) {
+                T* Ln = b ? buf0 : buf1;
+                issue(k0 + KC, Ln, Ln + TILE * LKP);
+            }
+        } else {
+            __syncthreads();
+            load_plain(k0, Lc, Uc);
+            __syncthreads();
+        }
 #pragma unroll 4
         for (int k = 0; k < KC; ++k) {
             T lv[2 * H], uv[2 * H];
-            lds16<T>(&Ls[k][tr * H], lv);
-            lds16<T>(&Ls[k][TILE / 2 + tr * H], lv + H);
-            lds16<T>(&Us[k][tc * H], uv);
-            lds16<T>(&Us[k][TILE / 2 + tc * H], uv + H);
+#pragma unroll
+            for (int a = 0; a < H; ++a) {
+                lv[a] = Lc[(tr * H + a) * LKP + k];
+                lv[H + a] = Lc[(TILE / 2 + tr * H + a) * LKP + k];
+            }
+            lds16<T>(&Uc[k * UKP + tc * H], uv);
+            lds16<T>(&Uc[k * UKP + TILE / 2 + tc * H], uv + H);
 #pragma unroll
             for (int a = 0; a < 2 * H; ++a)
 #pragma unroll
-                for (int b = 0; b < 2 * H; ++b) acc[a][b] += lv[a] * uv[b];
+                for (int bb = 0; bb < 2 * H; ++bb) acc[a][bb] += lv[a] * uv[bb];
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int a = 0; a < 2 * H; ++a) {
@@ -379,15 +446,15 @@ __device__ void update_body(const EngItem<T>& it, int p, int ti, int tj, unsigne
         if (gr >= n) continue;
         T* row = A + (long long)gr * ld;
 #pragma unroll
-        for (int b = 0; b < 2 * H; ++b) {
-            const int gc = c0 + (b < H ? tc * H + b : TILE / 2 + tc * H + b - H);
-            if (gc < n) row[gc] = __ldcg(row + gc) - acc[a][b];
+        for (int bb = 0; bb < 2 * H; ++bb) {
+            const int gc = c0 + (bb < H ? tc * H + bb : TILE / 2 + tc * H + bb - H);
+            if (gc < n) row[gc] = __ldcg(row + gc) - acc[a][bb];
         }
     }
 }
 
 template <class T, int TILE>
-__host__ __device__ constexpr size_t upd_smem() { return 2 * sizeof(T) * KC * (TILE + 4); }
+__host__ __device__ constexpr size_t upd_smem() { return 2 * sizeof(T) * UpdLayout<T, TILE>::BUF; }
 
 // M22 -= L21 U12, one TILE x TILE tile per CTA.  part: 0 every tile; 1 the first
 // tile row and column (with TILE == NB, the next panel's diagonal block and
@@ -409,7 +476,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
         ti = 1 + y / (nt - 1);
         tj = 1 + y % (nt - 1);
     }
-    __shared__ __align__(16) unsigned char usm[upd_smem<T, TILE>()];
+    extern __shared__ __align__(16) unsigned char usm[];
     update_body<T, NB, TILE>(it, p, ti, tj, usm);
 }
 
@@ -696,9 +763,21 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         BDDC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id));
         BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, UPD_THREADS, sm));
         const int grid = (int)std::min<long long>((long long)nsm * std::max(occ, 1), (long long)tasks.size());
+        double fl = 0.0, by = 0.0;
+        if (ktimer_on(KT_ENGINE_TASKS))
+            for (int i = 0; i < count; ++i)
+                for (int p = 0; p < hk[i]; p += NB) {
+                    // trailing update 2 m^2 w, substitutions 2 w^2 m, diagonal block (2/3) w^3;
+                    // bytes: the trailing matrix read and written once per panel
+                    const double w = std::min(NB, hk[i] - p), m = hn[i] - p - w;
+                    fl += 2.0 * m * m * w + 2.0 * w * w * m + 2.0 * w * w * w / 3.0;
+                    by += sizeof(T) * (2.0 * m * m + 4.0 * m * w + 2.0 * w * w);
+                }
+        ktimer_begin(KT_ENGINE_TASKS, st);
         kern<<<grid, UPD_THREADS, sm, st>>>(items_dev, reinterpret_cast<const EngTask*>(dev), (int)tasks.size(),
                                              reinterpret_cast<const EngMeta*>(dev + o1), flags, flags + nflags,
                                              flags + nflags + 1, dscr, stride, err);
+        ktimer_end(KT_ENGINE_TASKS, st, fl, by);
         bddc_note_launches(1);
         BDDC_CUDA_TRY(cudaGetLastError());
         BDDC_CUDA_TRY(cudaFreeAsync(dev, st));
@@ -706,8 +785,10 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
     }
     const size_t dsm = diag_smem<T>();
     const size_t tsm = trsm_smem<T>();
+    const size_t usm_b = upd_smem<T, TILE>();
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_diag<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_trsm<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_update<T, NB, TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)usm_b));
     auto panel = [&](int p, cudaStream_t s) -> int {
         const int nch = (std::max(maxn - p, 1) + CH - 1) / CH;
         k_diag<T, NB><<<count, DIAG_THREADS, dsm, s>>>(items_dev, p, dscr, stride, err);
@@ -738,11 +819,11 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
                 BDDC_TRY(tc_update_run(reinterpret_cast<const EngItem<float>*>(items_dev), count, maxn, p, NB,
                                        err, st));
             } else {
-                k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt, 0);
+                k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, usm_b, st>>>(items_dev, p, nt, 0);
                 bddc_note_launches(1);
             }
         } else {
-            k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, 0, st>>>(items_dev, p, nt, 0);
+            k_update<T, NB, TILE><<<dim3(count, nt * nt), UPD_THREADS, usm_b, st>>>(items_dev, p, nt, 0);
             bddc_note_launches(1);
         }
         ktimer_end(KT_ENGINE_UPDATE, st, fu, bu);

@@ -1,0 +1,130 @@
+"""Alternative GPU paths that must agree with each other and with the oracle.
+
+* The elimination engine runs either as one persistent task kernel (default)
+  or as per-panel launches (taken whenever the kernel timer watches the engine).
+  Both run the same task bodies in the same panel order; the assembly's atomic
+  sums make two setups differ in the last bits, so the Schur complements agree
+  to 1e-12 (FP64) / 1e-5 (FP32) of their largest entry.
+* The coarse inverse: FP32 Gauss-Jordan + FP64 Newton-Schulz for small coarse
+  problems versus the elimination of [[S_Pi, -I], [I, 0]]; the FP64 preconditioner
+  applies agree to 1e-11 relative and the oracle's apply to 1e-9.
+* The FP32 face pencils (tridiagonal route, selected eigenpairs only) against the
+  FP64 route: the same constraint counts, eigenvalues sigma = lambda / (1 + lambda)
+  within 1e-4, and the same constraint spans.
+"""
+import numpy as np
+import pytest
+
+from oracle import bddc as obddc
+from paper_2501_01676_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def B():
+    from paper_2501_01676_gb300 import bddc
+    return bddc
+
+
+def uneven_small():
+    p = W.random_small(11, (2, 2, 2), 3, (-2, 0))
+    p.slabs = [[9, 7], [8, 10], [6, 9]]
+    ne, h, X, Y, Z = W._grid(p.slabs)
+    rng = np.random.default_rng(7)
+    p.nu_elem = 10.0 ** rng.uniform(-2, 0, size=ne[0] * ne[1] * ne[2])
+    p.beta_node = np.tile(np.array([1.0, -0.5, 0.25]), (X.size, 1))
+    p.f_node = np.ones(X.size)
+    return p
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("prob", [lambda: W.uniform(2, 8, nu=0.05, beta=(1.0, 0.5, 0.25)), uneven_small])
+def test_task_kernel_equals_per_panel_launches(precision, prob):
+    p = prob()
+    b = B()
+    b.kernel_timer(b.KT_ENGINE_UPDATE)          # per-panel launches
+    try:
+        ref = b.Solver(p, precision=precision)
+        nsd = ref.stats()["nsub"]
+        S_ref = [ref.schur(s) for s in range(nsd)]
+    finally:
+        b.kernel_timer(b.KT_NONE)
+    task = b.Solver(p, precision=precision)       # persistent task kernel
+    tol = 1e-12 if precision == 0 else 1e-5
+    for s in range(nsd):
+        assert np.abs(task.schur(s) - S_ref[s]).max() <= tol * np.abs(S_ref[s]).max(), s
+    u1, st1 = task.solve()
+    u0, st0 = ref.solve()
+    assert abs(st0["iters"] - st1["iters"]) <= 1
+    # both solves stop at the 1e-8 residual: FP32 factors that differ in the last
+    # bits give solutions that agree to about kappa * 1e-8
+    utol = 1e-9 if precision == 0 else 1e-6
+    assert (u1 - u0).abs().max().item() <= utol * u0.abs().max().item()
+
+
+def test_coarse_inverse_paths_agree():
+    import torch
+    p = W.random_small(5, (3, 3, 3), 3, (-2, 1))
+    o = obddc.BDDC(p)
+    small = B().Solver(p)
+    elim = B().Solver(p, coarse_elim=1)
+    assert small.stats()["coarse_path"] == 1 and elim.stats()["coarse_path"] == 0
+    assert small.stats()["n_pi"] <= 128
+    r = np.random.default_rng(2).standard_normal(o.nG)
+    rd = torch.from_numpy(r).cuda()
+    z_small = small.apply(rd).cpu().numpy()
+    z_elim = elim.apply(rd).cpu().numpy()
+    assert np.linalg.norm(z_small - z_elim) <= 1e-11 * np.linalg.norm(z_elim)
+    zo = o.apply_M(r)
+    assert np.linalg.norm(z_small - zo) <= 1e-9 * np.linalg.norm(zo)
+
+
+def test_large_coarse_space_takes_the_elimination():
+    p = W.uniform(5, 3, nu=0.2, beta=(1.0, 0.0, 0.5))
+    s = B().Solver(p, precision=1)
+    st = s.stats()
+    assert st["n_pi"] > 128 and st["coarse_path"] == 0
+    u, sv = s.solve()
+    assert sv["converged"] and sv["relres"] <= 1e-8
+
+
+def _angle(Qa, Qb):
+    """Largest principal-angle sine between the column spans."""
+    if Qa.shape[1] == 0 and Qb.shape[1] == 0:
+        return 0.0
+    qa, _ = np.linalg.qr(Qa)
+    qb, _ = np.linalg.qr(Qb)
+    sv = np.linalg.svd(qa.T @ qb, compute_uv=False)
+    return float(np.sqrt(max(0.0, 1.0 - sv.min() ** 2)))
+
+
+def _sigma_desc(lam):
+    """sigma = lambda / (1 + lambda) of the reported eigenvalues, decreasing (NaN: not computed)."""
+    lam = lam[~np.isnan(lam)]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        sig = np.where(np.isinf(lam), 1.0, lam / (1.0 + lam))
+    return np.sort(sig)[::-1]
+
+
+@pytest.mark.parametrize("prob", [lambda: W.config2(), lambda: W.rotating_checker(3, 2, 6)])
+def test_fp32_face_pencils_match_fp64(prob):
+    p = prob()
+    f64 = B().Solver(p, precision=0)
+    f32 = B().Solver(p, precision=1)
+    e64, e32 = f64.entities(2), f32.entities(2)
+    assert len(e64) == len(e32)
+    theta = 1.0 + np.log(max(max(s) for s in p.slabs))
+    sth = theta / (1.0 + theta)
+    checked = 0
+    for a, b in zip(e64, e32):
+        assert a["subs"] == b["subs"]
+        sa, sb = _sigma_desc(a["lam"]), _sigma_desc(b["lam"])
+        m = min(int(np.sum(sa >= 0.3)), len(sb))
+        assert np.abs(sa[:m] - sb[:m]).max(initial=0.0) <= 1e-4
+        if len(sa) and np.min(np.abs(sa - sth)) < 1e-3:
+            continue            # an eigenvalue at the threshold may fall either way in FP32
+        assert a["k"] == b["k"]
+        if a["k"] > 0:
+            assert _angle(a["Q"], b["Q"]) <= 1e-3
+        checked += 1
+    assert checked >= len(e64) // 2
