@@ -26,6 +26,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "bddc_internal.h"
@@ -535,36 +536,11 @@ static int setup_impl(bddc_ctx* C) {
         std::vector<int> permv;
         std::vector<GatherJob> gj;
         std::vector<EngItem<T>> items;
-        std::vector<long long> fo;
-        long long ftot = 0;
-        for (int e : faces)
-            for (int a = 0; a < 2; ++a) {
-                int s = hm.ent[e].subs[a];
-                fo.push_back(ftot);
-                ftot += (long long)hm.sub[s].nB * r4(hm.sub[s].nB);
-            }
-        T* FB = nullptr;
-        if (face_mode == 0) BDDC_TRY(C->alloc(&FB, ftot));
-        int q = 0;
-        for (int e : faces) {
-            Entity& E = hm.ent[e];
-            for (int a = 0; a < 2; ++a, ++q) {
-                int s = E.subs[a];
-                int nB = hm.sub[s].nB, nF = (int)E.dofs.size();
-                std::vector<char> inF(nB, 0);
-                for (int p : E.pos[a]) inF[p] = 1;
-                int off = (int)permv.size();
-                for (int b = 0; b < nB; ++b)
-                    if (!inF[b]) permv.push_back(b);
-                for (int p : E.pos[a]) permv.push_back(p);
-                if (face_mode == 0) {
-                    gj.push_back(GatherJob{C->S64 + C->soff[s], C->sld[s], nB, off, 1, FB + fo[q], r4(nB)});
-                    items.push_back(EngItem<T>{FB + fo[q], nB, nB - nF, r4(nB)});
-                }
-            }
-        }
-        int* d_perm;
-        BDDC_TRY(C->upload(&d_perm, permv));
+        // Face Schur complements of B^(i) (the symmetric part of S^(i)) in two levels,
+        // both exact by the quotient property of Schur complements: (1) per
+        // subdomain eliminate the edge and vertex positions, leaving the Schur
+        // complement on its face positions; (2) per (face, side) eliminate the other
+        // faces' positions from it.  Level 1 is shared by the subdomain's faces.
         double* Bt64 = nullptr;
         std::vector<long long> bo;
         long long btot = 0;
@@ -574,22 +550,85 @@ static int setup_impl(bddc_ctx* C) {
             btot += 2LL * nF * nF;
         }
         BDDC_TRY(C->alloc(&Bt64, btot));
+        int* d_perm = nullptr;
         if (face_mode == 0) {
+            std::vector<int> nFP(nsd), nEV(nsd);
+            std::vector<std::vector<int>> fpos(nsd);              // face positions, in entity order
+            std::vector<std::unordered_map<int, int>> foff(nsd);  // face entity -> offset in fpos
+            std::vector<long long> w1o(nsd);
+            long long w1tot = 0;
+            for (int s = 0; s < nsd; ++s) {
+                SubInfo& S = hm.sub[s];
+                std::vector<int> ev;
+                for (size_t q = 0; q < S.ents.size(); ++q) {
+                    Entity& E = hm.ent[S.ents[q]];
+                    const std::vector<int>& ps = E.pos[S.ent_slot[q]];
+                    if (E.kind == 2) {
+                        foff[s][S.ents[q]] = (int)fpos[s].size();
+                        fpos[s].insert(fpos[s].end(), ps.begin(), ps.end());
+                    } else {
+                        ev.insert(ev.end(), ps.begin(), ps.end());
+                    }
+                }
+                nEV[s] = (int)ev.size();
+                nFP[s] = (int)fpos[s].size();
+                w1o[s] = w1tot;
+                w1tot += (long long)S.nB * r4(S.nB);
+                const int off = (int)permv.size();
+                permv.insert(permv.end(), ev.begin(), ev.end());
+                permv.insert(permv.end(), fpos[s].begin(), fpos[s].end());
+                gj.push_back(GatherJob{C->S64 + C->soff[s], C->sld[s], S.nB, off, 1, nullptr, r4(S.nB), nullptr});
+                items.push_back(EngItem<T>{nullptr, S.nB, nEV[s], r4(S.nB)});
+            }
+            T* W1 = nullptr;
+            BDDC_TRY(C->alloc(&W1, (size_t)std::max(w1tot, 1LL)));
+            for (int s = 0; s < nsd; ++s) {
+                gj[s].dst = W1 + w1o[s];
+                items[s].a = W1 + w1o[s];
+            }
+            // level 2: per (face, side), from the trailing face block of level 1
+            std::vector<long long> f2o;
+            long long f2tot = 0;
+            for (int e : faces)
+                for (int a = 0; a < 2; ++a) {
+                    const int s = hm.ent[e].subs[a];
+                    f2o.push_back(f2tot);
+                    f2tot += (long long)nFP[s] * r4(nFP[s]);
+                }
+            T* FB = nullptr;
+            BDDC_TRY(C->alloc(&FB, (size_t)std::max(f2tot, 1LL)));
+            std::vector<GatherJob> gj2;
+            std::vector<EngItem<T>> items2;
+            std::vector<CopyJob> cj;
+            int q = 0;
+            for (size_t fi = 0; fi < faces.size(); ++fi) {
+                const int e = faces[fi];
+                Entity& E = hm.ent[e];
+                const int nF = (int)E.dofs.size();
+                for (int a = 0; a < 2; ++a, ++q) {
+                    const int s = E.subs[a];
+                    const int n2 = nFP[s], f0 = foff[s][e];
+                    const int off = (int)permv.size();
+                    for (int b = 0; b < n2; ++b)
+                        if (b < f0 || b >= f0 + nF) permv.push_back(b);
+                    for (int b = 0; b < nF; ++b) permv.push_back(f0 + b);
+                    const int l1 = r4(hm.sub[s].nB);
+                    gj2.push_back(GatherJob{nullptr, l1, n2, off, 1, FB + f2o[q], r4(n2),
+                                            W1 + w1o[s] + (long long)nEV[s] * l1 + nEV[s]});
+                    items2.push_back(EngItem<T>{FB + f2o[q], n2, n2 - nF, r4(n2)});
+                    cj.push_back(CopyJob{FB + f2o[q], r4(n2), n2 - nF, n2 - nF, nF, nF,
+                                         Bt64 + bo[fi] + (long long)a * nF * nF, nF, 1.0});
+                }
+            }
+            BDDC_TRY(C->upload(&d_perm, permv));
             GatherJob* d_gj;
             BDDC_TRY(C->upload(&d_gj, gj));
             BDDC_TRY(gather_perm_run<T>(d_gj, (int)gj.size(), d_perm, 64, st));
             BDDC_TRY(run_engine<T>(C, items));
-            std::vector<CopyJob> cj;
-            q = 0;
-            for (size_t fi = 0; fi < faces.size(); ++fi) {
-                Entity& E = hm.ent[faces[fi]];
-                int nF = (int)E.dofs.size();
-                for (int a = 0; a < 2; ++a, ++q) {
-                    int nB = hm.sub[E.subs[a]].nB;
-                    cj.push_back(CopyJob{FB + fo[q], r4(nB), nB - nF, nB - nF, nF, nF,
-                                         Bt64 + bo[fi] + (long long)a * nF * nF, nF, 1.0});
-                }
-            }
+            GatherJob* d_gj2;
+            BDDC_TRY(C->upload(&d_gj2, gj2));
+            BDDC_TRY(gather_perm_run<T>(d_gj2, (int)gj2.size(), d_perm, 64, st));
+            BDDC_TRY(run_engine<T>(C, items2));
             CopyJob* d_cj;
             BDDC_TRY(C->upload(&d_cj, cj));
             BDDC_TRY((copy_blocks_run<T, double>(d_cj, (int)cj.size(), 8, st)));
@@ -876,7 +915,7 @@ static int setup_impl(bddc_ctx* C) {
                     int n = (int)perm.size();
                     int off = (int)gidxv.size();
                     gidxv.insert(gidxv.end(), perm.begin(), perm.end());
-                    gj.push_back(GatherJob{W64 + w64off[s], nkeep[s], n, off, 0, EB + etot, n});
+                    gj.push_back(GatherJob{W64 + w64off[s], nkeep[s], n, off, 0, EB + etot, n, nullptr});
                     items.push_back(EngItem<T>{EB + etot, n, nel, n});
                     ito[ei].push_back(etot + (long long)nel * n + nel);
                     itn[ei].push_back(n);
@@ -1273,6 +1312,45 @@ static int op_M(bddc_ctx* C, const double* x, const int* skip) {
     return BDDC_OK;
 }
 
+// Executable GMRES graphs of destroyed contexts, per host thread.  A new context
+// takes one and updates it from its own capture (cudaGraphExecUpdate succeeds
+// when only kernel parameters differ); each executable graph belongs to one live
+// context at a time.
+namespace {
+struct GraphPool {
+    std::vector<std::pair<int, cudaGraphExec_t>> execs;     // (device, graph)
+    ~GraphPool() {
+        for (auto& e : execs) cudaGraphExecDestroy(e.second);
+    }
+};
+thread_local GraphPool g_graph_pool;
+}  // namespace
+
+static cudaGraphExec_t graph_pool_take(cudaGraph_t g) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    auto& v = g_graph_pool.execs;
+    for (size_t i = v.size(); i-- > 0;) {
+        if (v[i].first != dev) continue;
+        cudaGraphExec_t e = v[i].second;
+        v.erase(v.begin() + (long)i);
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(e, g, &info) == cudaSuccess) return e;
+        cudaGetLastError();
+        cudaGraphExecDestroy(e);
+    }
+    return nullptr;
+}
+
+static void graph_pool_give(cudaGraphExec_t e) {
+    if (!e) return;
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && g_graph_pool.execs.size() < 4)
+        g_graph_pool.execs.push_back({dev, e});
+    else
+        cudaGraphExecDestroy(e);
+}
+
 static int norm2(bddc_ctx* C, const double* x, long long n, double* out_host) {
     // uses the spare state slot (never stopped)
     int nchunk = gm_nchunk(n);
@@ -1346,7 +1424,10 @@ static int gmres(bddc_ctx* C, const double* b, double* x, double rtol, int max_i
             BDDC_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
             if (ty == cudaGraphNodeTypeKernel) ++C->graph_kernels;
         }
-        BDDC_CUDA_TRY(cudaGraphInstantiate(&C->graph, g, 0));
+        // an executable graph left by a destroyed context of the same shape is
+        // retargeted to this context's buffers (no new instantiation)
+        C->graph = graph_pool_take(g);
+        if (!C->graph) BDDC_CUDA_TRY(cudaGraphInstantiate(&C->graph, g, 0));
         cudaGraphDestroy(g);
         C->graph_iters = K;
     }
@@ -1530,7 +1611,8 @@ const char* bddc_strerror(int code) {
 
 void bddc_destroy(bddc_ctx* C) {
     if (!C) return;
-    if (C->graph) cudaGraphExecDestroy(C->graph);
+    if (C->st) cudaStreamSynchronize(C->st);     // the graph may still be running
+    graph_pool_give(C->graph);
     for (void* p : C->allocs) cudaFreeAsync(p, C->st);
     if (C->st) cudaStreamSynchronize(C->st);
     for (cudaEvent_t e : C->phase_ev)

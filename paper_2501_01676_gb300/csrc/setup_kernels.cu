@@ -33,12 +33,13 @@ __global__ void k_gather_perm(const GatherJob* __restrict__ jobs, const int* __r
     const GatherJob J = jobs[blockIdx.x];
     const int* p = idx + J.perm_off;
     TD* dst = (TD*)J.dst;
+    const TD* sT = (const TD*)J.srcT;
     for (int a = blockIdx.y; a < J.n; a += gridDim.y) {
         const long long ia = p[a];
         for (int b = threadIdx.x; b < J.n; b += TH) {
             const long long ib = p[b];
-            double v = J.src[ia * J.sld + ib];
-            if (J.sym) v = 0.5 * (v + J.src[ib * J.sld + ia]);
+            double v = J.src ? J.src[ia * J.sld + ib] : (double)sT[ia * J.sld + ib];
+            if (J.sym) v = 0.5 * (v + (J.src ? J.src[ib * J.sld + ia] : (double)sT[ib * J.sld + ia]));
             dst[(long long)a * J.dld + b] = (TD)v;
         }
     }

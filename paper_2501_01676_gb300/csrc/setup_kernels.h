@@ -12,13 +12,14 @@ struct CopyJob {            // dst[r][c] = scale * src[r0 + r][c0 + c]
 };
 
 struct GatherJob {          // dst[a][b] = S[p_a][p_b] (sym: symmetric part)
-    const double* src;
+    const double* src;      // FP64 source, or NULL: srcT (the destination precision)
     long long sld;
     int n;
     int perm_off;
     int sym;
     void* dst;
     long long dld;
+    const void* srcT;
 };
 
 struct TBlock {             // one entity block of one subdomain's change of basis
