@@ -130,8 +130,8 @@ typedef struct bddc_ctx bddc_ctx;
 
 /* Fill `o` with the defaults of Sect. 4: Theta_E = 10, Theta_F = 1 + ln(H/h),
  * tau = 0.7, FP64, no restart, 300 iterations, rtol 1e-8, new edge GEP,
- * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip, CUDA-core
- * trailing updates (tensor_cores 0), coarse_elim 0. */
+ * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip, tensor-core
+ * trailing updates in the MIXED path (tensor_cores 1), coarse_elim 0. */
 void bddc_default_opts(bddc_opts* o);
 
 /* Setup (call stack: assembly, batched Dirichlet factorisation + Schur

@@ -1591,7 +1591,7 @@ void bddc_default_opts(bddc_opts* o) {
     o->max_refine = 8;
     o->learned_skip_p = -1.0;
     o->mlp_params = nullptr;
-    o->tensor_cores = 0;
+    o->tensor_cores = 1;
     o->coarse_elim = 0;
 }
 

@@ -43,6 +43,7 @@
 #include <vector>
 
 #include "bddc_internal.h"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -67,139 +68,217 @@ constexpr int IB = 32;      // inner block of the diagonal factorisation
 __device__ __forceinline__ bool bad_pivot(double v) { return !(fabs(v) > 1e-300) || !isfinite(v); }
 __device__ __forceinline__ bool bad_pivot(float v) { return !(fabsf(v) > 0.f) || !isfinite(v); }
 
+// 16-byte shared-memory load into out[0 .. 16 / sizeof(T) - 1]
+template <class T>
+__device__ __forceinline__ void lds16(const T* p, T* out);
+template <>
+__device__ __forceinline__ void lds16<float>(const float* p, float* out) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void lds16<double>(const double* p, double* out) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    out[0] = v.x; out[1] = v.y;
+}
+
 // Per-item scratch: the reciprocal pivots of every panel (NB per panel, so that
 // a panel's pivots stay valid while the next panel is factored in the task
 // kernel); `stride` elements per item.
 
-// Solve x U = b within one 32-column block for NR vectors held by a group of 8
-// lanes (lane cg of the group owns entries cg, cg+8, cg+16, cg+24 of every
-// vector in acc[.][0..3]).  U(c, c') = U[c*s1 + c'*s2] for c < c' < bw; its
-// diagonal enters through the reciprocals d (nullptr: unit diagonal).  Column
-// c is final once the update from columns < c is in: its owner scales it and
-// broadcasts it by shuffle, and every lane updates its later columns, so the
-// dependent chain is 32 short steps instead of a 32 x 32 triangle per thread.
-// All 32 lanes of the warp must call it (the shuffles are warp-wide).
-template <class T, int NR>
-__device__ __forceinline__ void subst8(T (&acc)[NR][4], const T* __restrict__ U, int s1, int s2,
-                                       const T* __restrict__ d, int bw, int cg) {
+constexpr int TS = IB + 4;          // row length of the shifted triangle copies (16-byte rows, conflict-free writes)
+
+// One warp factors the bw x bw block Db (bw <= 32, leading dimension LD) in
+// registers: lane c holds column c.  Step j broadcasts the pivot and the
+// unscaled column j from lane j (all 32 shuffles first, off the pivot's
+// dependency chain); the lanes right of j subtract x(j + r, j) * (U(j, c) /
+// pivot), one FMA per entry.  Column j itself stays unscaled in registers: each
+// lane keeps its pivot reciprocal and scales its L entries when they are
+// written out.  The rows are shifted down one register per step (row j + 1
+// moves to x[0]), so every register index is static inside a compact loop.
+// Row j is final after step j: it is written back to Db and, shifted so that
+// the distance from the diagonal is the column index, to Us[j][c - j] = U(j, c)
+// (c > j) and Ls[c][j - c] = L(j, c) (j > c); the strip solves read those rows
+// as 16-byte vectors.  Rows and columns past bw are padded with the identity (no
+// effect on the real part).
+template <class T>
+__device__ __forceinline__ void lu_warp32(T* __restrict__ Db, int LD, int bw, T* __restrict__ dv,
+                                          T* __restrict__ Us, T* __restrict__ Ls, int* __restrict__ err,
+                                          int lane) {
+    T x[IB];
 #pragma unroll
-    for (int ec = 0; ec < 4; ++ec) {
-        for (int gc = 0; gc < 8; ++gc) {
-            const int c = gc + 8 * ec;
-            if (c >= bw) break;
-            const T dc = d ? d[c] : (T)1;
-            T x[NR];
+    for (int r = 0; r < IB; ++r) x[r] = (r < bw && lane < bw) ? Db[r * LD + lane] : (r == lane ? (T)1 : (T)0);
+    T myri = (T)1;
+#pragma unroll 1
+    for (int j = 0; j < IB; ++j) {
+        // FP32: all shuffles up front (32 more registers); FP64: next to their FMAs
+        constexpr int NS = sizeof(T) == 4 ? IB : 1;
+        T sv[NS];
 #pragma unroll
-            for (int a = 0; a < NR; ++a) {
-                x[a] = __shfl_sync(0xffffffffu, acc[a][ec] * dc, gc, 8);
-                if (cg == gc) acc[a][ec] = x[a];
-            }
+        for (int r = 0; r < NS; ++r) sv[r] = __shfl_sync(0xffffffffu, x[r], j);
+        T piv = sv[0];
+        const bool bad = bad_pivot(piv);
+        if (bad) piv = (T)1;
+        const T ri = (T)1 / piv;
+        myri = lane == j ? ri : myri;
+        // row j: L(j, c) for c < j (scaled now), the pivot, U(j, c) for c > j
+        const T rowv = lane < j ? x[0] * myri : (lane == j ? piv : x[0]);
+        const T m = lane > j ? x[0] * ri : (T)0;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int cp = cg + 8 * e;
-                if (cp > c && cp < bw) {
-                    const T u = U[c * s1 + cp * s2];
+        for (int r = 1; r < IB; ++r)
+            x[r - 1] = x[r] - (NS == IB ? sv[r % NS] : __shfl_sync(0xffffffffu, x[r], j)) * m;
+        x[IB - 1] = (T)0;
+        if (j < bw && lane < bw) Db[j * LD + lane] = rowv;
+        if (lane == j && j < bw) {
+            dv[j] = ri;
+            if (bad) atomicOr(err, ERR_PIVOT);
+        }
+        if (lane > j) Us[j * TS + lane - j] = rowv;
+        if (lane < j) Ls[lane * TS + j - lane] = rowv;
+    }
+}
+
+// Rank-32 update of the trailing block of the diagonal block (rows and columns
+// b0 + 32 .. w - 1): 16 x 16 threads, thread (ty, tx) owns rows b0 + 32 + ty + 16 i
+// and columns b0 + 32 + tx + 16 j, i, j < MR (MR = the stage's ceil(rem / 16),
+// rounded up to the instantiated sizes).
+template <class T, int MR>
+__device__ __forceinline__ void diag_rank32(T* __restrict__ D, int LD, int b0, int w, int t) {
+    const int base = b0 + IB;
+    const int ty = t >> 4, tx = t & 15;
+    T acc[MR][MR];
 #pragma unroll
-                    for (int a = 0; a < NR; ++a) acc[a][e] -= x[a] * u;
-                }
-            }
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MR; ++j) acc[i][j] = (T)0;
+#pragma unroll 2
+    for (int l = 0; l < IB; ++l) {
+        T a[MR], b[MR];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+            const int r = base + ty + 16 * i, c = base + tx + 16 * i;
+            a[i] = r < w ? D[r * LD + b0 + l] : (T)0;
+            b[i] = c < w ? D[(b0 + l) * LD + c] : (T)0;
+        }
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MR; ++j) acc[i][j] += a[i] * b[j];
+    }
+#pragma unroll
+    for (int i = 0; i < MR; ++i) {
+        const int r = base + ty + 16 * i;
+#pragma unroll
+        for (int j = 0; j < MR; ++j) {
+            const int c = base + tx + 16 * j;
+            if (r < w && c < w) D[r * LD + c] -= acc[i][j];
         }
     }
 }
 
-// LU of the w x w diagonal block in shared memory, 32 columns at a time.  The
-// code is kept compact (loops over shared memory, no long unrolled chains): it
-// runs once per launch, so straight-line code would be fetched from beyond the
-// instruction cache for every instruction.
-// (global loads of matrix data go through L2, __ldcg: in the persistent task
-// kernel other CTAs write it during the launch)
+// LU of the w x w diagonal block in shared memory, 32 columns at a time.  Per
+// 32-column stage b0:
+//   (1) one warp factors the 32 x 32 block (lu_warp32);
+//   (2) the rows below it solve y <- y U^{-1} and the columns right of it
+//       z <- L^{-1} z, one thread per row / column with the 32 values in
+//       registers (same shift-down scheme: the value finished in step c leaves
+//       through y[0], U(c, c + l) / L(c + l, c) come from the shifted triangle
+//       copies, 16 bytes per load; the slots past the block hold stale values
+//       that never reach a real one);
+//   (3) the rank-32 update of the trailing block, 16 x 16 threads with register
+//       tiles.
+// Three barriers per stage instead of one per pivot; the loops stay compact
+// (this body runs once per launch: straight-line code would be fetched from
+// beyond the instruction cache).
 template <class T, int NB>
-__device__ void diag_body(const EngItem<T>& it, int p, T* __restrict__ out, int* __restrict__ err,
+__device__ __noinline__ void diag_body(const EngItem<T>& it, int p, T* __restrict__ out, int* __restrict__ err,
                           unsigned char* dsm) {
+    static_assert(NB - IB <= DIAG_THREADS / 2, "one thread per strip row / column");
     const int w = min(NB, it.k - p);
     const long long ld = it.ld;
     T* A = it.a + (long long)p * ld + p;
     constexpr int LD = NB + 1;
+    constexpr int MR = (NB - IB + 15) / 16;  // register tile of the trailing update
     T* D = reinterpret_cast<T*>(dsm);        // NB x LD: L\U of the diagonal block
     T* dinv = D + NB * LD;                    // NB reciprocal pivots
+    T* Ut = dinv + NB;                        // IB x TS: Ut[c][l] = U(b0 + c, b0 + c + l)
+    T* Lt = Ut + IB * TS;                     // IB x TS: Lt[r][l] = L(b0 + r + l, b0 + r)
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    for (int q = t; q < w * w; q += DIAG_THREADS) {
-        const int r = q / w, c = q - r * w;
-        D[r * LD + c] = __ldcg(A + r * ld + c);
+    // thread t reads column t % NB of rows t / NB + RPI u, 16 loads in flight
+    constexpr int RPI = DIAG_THREADS / NB;
+    const int lc = t % NB, lr = t / NB;
+#pragma unroll 1
+    for (int r0 = 0; r0 < w; r0 += 16 * RPI) {
+        T v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int r = r0 + lr + u * RPI;
+            if (r < w && lc < w) v[u] = __ldcg(A + r * ld + lc);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int r = r0 + lr + u * RPI;
+            if (r < w && lc < w) D[r * LD + lc] = v[u];
+        }
     }
     __syncthreads();
+#pragma unroll 1
     for (int b0 = 0; b0 < w; b0 += IB) {
         const int bw = min(IB, w - b0);
-        // (a) the block's 32 pivots, all threads, one barrier per pivot: step jj
-        //     updates the column panel (rows below jj, columns jj+1 .. b0+bw-1) and
-        //     the row strip (rows jj+1 .. b0+bw-1, columns b0+bw .. w-1) with the
-        //     unscaled column jj; the column is scaled after the barrier (no later
-        //     step of the block reads it).
         const int rem = w - b0 - bw;
+        if (wid == 0) lu_warp32<T>(D + b0 * LD + b0, LD, bw, dinv + b0, Ut, Lt, err, lane);
+        __syncthreads();
+        if (rem <= 0) break;
+        const int base = b0 + IB;
+        if (t < DIAG_THREADS / 2) {
+            const int r = base + t;
+            if (r < w) {
+                T y[IB];
+#pragma unroll
+                for (int l = 0; l < IB; ++l) y[l] = D[r * LD + b0 + l];
+#pragma unroll 1
+                for (int c = 0; c < IB; ++c) {
+                    T u[IB];
+#pragma unroll
+                    for (int q = 0; q < IB; q += 16 / (int)sizeof(T)) lds16<T>(Ut + c * TS + q, u + q);
+                    const T z = y[0] * dinv[b0 + c];
+                    D[r * LD + b0 + c] = z;
+#pragma unroll
+                    for (int l = 1; l < IB; ++l) y[l - 1] = y[l] - z * u[l];
+                }
+            }
+        } else {
+            const int cc = base + t - DIAG_THREADS / 2;
+            if (cc < w) {
+                T y[IB];
+#pragma unroll
+                for (int l = 0; l < IB; ++l) y[l] = D[(b0 + l) * LD + cc];
+#pragma unroll 1
+                for (int r = 0; r < IB; ++r) {
+                    T lt[IB];
+#pragma unroll
+                    for (int q = 0; q < IB; q += 16 / (int)sizeof(T)) lds16<T>(Lt + r * TS + q, lt + q);
+                    const T v = y[0];
+                    D[(b0 + r) * LD + cc] = v;
+#pragma unroll
+                    for (int l = 1; l < IB; ++l) y[l - 1] = y[l] - v * lt[l];
+                }
+            }
+        }
+        __syncthreads();
         {
-            const int ty = t >> 5;                 // 16 row lanes
-            constexpr int NRL = DIAG_THREADS / 32;
-            for (int jj = b0; jj < b0 + bw; ++jj) {
-                T piv = D[jj * LD + jj];
-                const bool bad = bad_pivot(piv);
-                if (bad) piv = (T)1;
-                const T ri = (T)1 / piv;
-                const int cend = b0 + bw;
-                // column panel: c = jj + 1 + lane (< cend), rows jj+1+ty, stepping NRL
-                {
-                    const int c = jj + 1 + lane;
-                    if (c < cend) {
-                        const T u = D[jj * LD + c] * ri;
-                        for (int r = jj + 1 + ty; r < w; r += NRL) D[r * LD + c] -= D[r * LD + jj] * u;
-                    }
-                }
-                // row strip: rows jj+1 .. cend-1, columns cend .. w-1
-                for (int r = jj + 1 + ty; r < cend; r += NRL) {
-                    const T l = D[r * LD + jj] * ri;
-                    for (int c = cend + lane; c < w; c += 32) D[r * LD + c] -= l * D[jj * LD + c];
-                }
-                __syncthreads();
-                for (int r = jj + 1 + t; r < w; r += DIAG_THREADS) D[r * LD + jj] *= ri;
-                if (t == 0) {
-                    if (bad) {
-                        D[jj * LD + jj] = piv;
-                        atomicOr(err, ERR_PIVOT);
-                    }
-                    dinv[jj] = ri;
-                }
-            }
-        }
-        __syncthreads();
-        // (c) rank-bw update of the remaining rem x rem block; lane = column within a
-        //     32-column group, four rows per thread
-        if (rem > 0) {
-            const int ncg = (rem + 31) / 32, nrg = (rem + 3) / 4;
-            const int base = b0 + bw;
-            for (int job = wid; job < ncg * nrg; job += DIAG_THREADS / 32) {
-                const int cg = job % ncg, rg = job / ncg;
-                const int c = base + cg * 32 + lane;
-                const int r0 = base + rg * 4;
-                if (c < w) {
-                    T acc[4] = {0, 0, 0, 0};
-                    for (int l = 0; l < bw; ++l) {
-                        const T u = D[(b0 + l) * LD + c];
-#pragma unroll
-                        for (int a = 0; a < 4; ++a)
-                            if (r0 + a < w) acc[a] += D[(r0 + a) * LD + b0 + l] * u;
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-                        if (r0 + a < w) D[(r0 + a) * LD + c] -= acc[a];
-                }
-            }
+            const int nr = (rem + 15) / 16;
+            if (nr <= 2) diag_rank32<T, 2>(D, LD, b0, w, t);
+            else if (MR <= 4 || nr <= 4) diag_rank32<T, (MR < 4 ? MR : 4)>(D, LD, b0, w, t);
+            else diag_rank32<T, MR>(D, LD, b0, w, t);
         }
         __syncthreads();
     }
+    __syncthreads();
     for (int q = t; q < w; q += DIAG_THREADS) out[q] = dinv[q];
-    for (int q = t; q < w * w; q += DIAG_THREADS) {
-        const int r = q / w, c = q - r * w;
-        A[r * ld + c] = D[r * LD + c];
-    }
+    if (lc < w)
+#pragma unroll 4
+        for (int r = lr; r < w; r += RPI) A[r * ld + lc] = D[r * LD + lc];
 }
 
 template <class T, int NB>
@@ -211,12 +290,52 @@ __global__ void __launch_bounds__(DIAG_THREADS, 2) k_diag(const EngItem<T>* __re
     diag_body<T, NB>(it, p, scr + (long long)blockIdx.x * stride + (p / NB) * NB, err, dsm);
 }
 
+// X[:, b0 + 32 .. w) -= X[:, b0 .. b0 + 32) U[b0 .. b0 + 32, b0 + 32 .. w) on a
+// CH-row chunk in shared memory: 16 x 16 threads, thread (ty, tx) owns rows
+// ty + 16 i (i < CH / 16) and columns b0 + 32 + tx + 16 j (j < MC).
+template <class T, int NB, int MC>
+__device__ __forceinline__ void trsm_rank32(T* __restrict__ X, const T* __restrict__ Us, int b0, int w, int t) {
+    constexpr int LDX = NB + 1, MR = CH / 16;
+    const int ty = t >> 4, tx = t & 15;
+    const int base = b0 + IB;
+    T acc[MR][MC];
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) acc[i][j] = (T)0;
+#pragma unroll 2
+    for (int l = 0; l < IB; ++l) {
+        T a[MR], b[MC];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) a[i] = X[(ty + 16 * i) * LDX + b0 + l];
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+            const int c = base + tx + 16 * j;
+            b[j] = c < w ? Us[(b0 + l) * LDX + c] : (T)0;
+        }
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) acc[i][j] += a[i] * b[j];
+    }
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+            const int c = base + tx + 16 * j;
+            if (c < w) X[(ty + 16 * i) * LDX + c] -= acc[i][j];
+        }
+}
+
 // Blocked substitution on a chunk of R <= CH rows, X (R x w, in shared memory):
 //   X <- X U^{-1}, U upper triangular w x w given by the accessor U(l, c), l <= c.
-// L21 chunks use U = U11 (pivot reciprocals from k_diag); U12 chunks are solved
-// transposed with U = L11^T (unit diagonal).  Per 32-column block: subtract the
-// solved blocks (register-blocked, 2 rows x 4 columns per thread), then
-// substitute within the block (subst8: 8 lanes per row pair).
+// L21 chunks use U = U11 (pivot reciprocals from the diagonal task); U12 chunks
+// are solved transposed with U = L11^T (unit diagonal).  The chunk and the whole
+// triangle are loaded once, up front (a few L2 round trips, several loads in
+// flight per thread).  Per 32-column block: substitute within the block (one
+// thread per row, the block's triangle rows as 16-byte vector loads), then
+// subtract its contribution from all later columns at once (right-looking,
+// register tiles of CH/16 x up to 6 per thread).
 template <class T, int NB>
 __device__ void trsm_body(const EngItem<T>& it, int p, bool colside, int chunk, const T* __restrict__ pinv,
                           unsigned char* tsm_) {
@@ -229,74 +348,125 @@ __device__ void trsm_body(const EngItem<T>& it, int p, bool colside, int chunk, 
     const int R = min(CH, n - g0);
     constexpr int LDX = NB + 1;
     T* X = reinterpret_cast<T*>(tsm_);        // CH x LDX
-    T* Us = X + CH * LDX;                     // NB x 33: U(l, b0 + c) for l < b0 + 32
-    T* dv = Us + NB * (IB + 1);               // 32 reciprocal diagonal entries of the block
+    T* Us = X + CH * LDX;                     // NB x LDX: U(l, c)
+    T* dv = Us + NB * LDX;                    // NB reciprocal diagonal entries (1 for L11^T)
     const T* A = it.a;
     const int t = threadIdx.x;
+    // loads: 16 in flight per thread before their stores, no index divisions
     if (!colside) {
-        for (int q = t; q < CH * w; q += TRSM_THREADS) {
-            const int r = q / w, c = q - r * w;
-            X[r * LDX + c] = r < R ? __ldcg(A + (long long)(g0 + r) * ld + p + c) : (T)0;
+        constexpr int RX = TRSM_THREADS / NB;
+        const int xc = t % NB, xr = t / NB;
+#pragma unroll 1
+        for (int r0 = 0; r0 < CH; r0 += 16 * RX) {
+            T v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int r = r0 + xr + u * RX;
+                v[u] = (r < R && xc < w) ? __ldcg(A + (long long)(g0 + r) * ld + p + xc) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) X[(r0 + xr + u * RX) * LDX + xc] = v[u];
         }
+        // U11: rows of the diagonal block, upper part (the strict lower part is never read)
+#pragma unroll 1
+        for (int l0 = 0; l0 < w; l0 += 16 * RX) {
+            T v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int l = l0 + xr + u * RX;
+                v[u] = (l < w && xc < w && xc >= l) ? __ldcg(A + (long long)(p + l) * ld + p + xc) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int l = l0 + xr + u * RX;
+                if (l < NB) Us[l * LDX + xc] = v[u];
+            }
+        }
+        if (t < NB) dv[t] = t < w ? __ldcg(pinv + t) : (T)1;
     } else {
         // X[c][k] = M12[k][c]: rows of M12 are contiguous along c
-        for (int q = t; q < CH * w; q += TRSM_THREADS) {
-            const int k = q / CH, c = q - k * CH;
-            X[c * LDX + k] = c < R ? __ldcg(A + (long long)(p + k) * ld + g0 + c) : (T)0;
+        constexpr int RK = TRSM_THREADS / CH;
+        const int xc = t % CH, xk = t / CH;
+#pragma unroll 1
+        for (int k0 = 0; k0 < NB; k0 += 16 * RK) {
+            T v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = k0 + xk + u * RK;
+                v[u] = (k < w && xc < R) ? __ldcg(A + (long long)(p + k) * ld + g0 + xc) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) X[xc * LDX + k0 + xk + u * RK] = v[u];
         }
+        // U(l, c) = L11[c][l] for l < c: rows c of L11, read along l
+        constexpr int RC = TRSM_THREADS / NB;
+        const int ul = t % NB, uc = t / NB;
+#pragma unroll 1
+        for (int c0 = 0; c0 < w; c0 += 16 * RC) {
+            T v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int c = c0 + uc + u * RC;
+                v[u] = (c < w && ul < c) ? __ldcg(A + (long long)(p + c) * ld + p + ul) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int c = c0 + uc + u * RC;
+                if (c < NB) Us[ul * LDX + c] = v[u];
+            }
+        }
+        if (t < NB) dv[t] = (T)1;
     }
-    const int rg = t >> 3, cg = t & 7;        // rows 2rg, 2rg+1; columns cg + 8e
+    T* Sh = dv + NB;                          // IB x TS: Sh[c][l] = U(b0 + c, b0 + c + l)
+    __syncthreads();
+#pragma unroll 1
     for (int b0 = 0; b0 < w; b0 += IB) {
         const int bw = min(IB, w - b0);
-        const int nl = b0 + bw;
-        if (!colside) {
-            for (int q = t; q < nl * IB; q += TRSM_THREADS) {
-                const int l = q / IB, c = q - l * IB;
-                Us[l * (IB + 1) + c] = c < bw ? __ldcg(A + (long long)(p + l) * ld + p + b0 + c) : (T)0;
-            }
-            if (t < IB) dv[t] = t < bw ? __ldcg(pinv + b0 + t) : (T)1;
-        } else {
-            // U(l, b0 + c) = L11[b0 + c][l]: rows of L11, read along l
-            for (int q = t; q < nl * IB; q += TRSM_THREADS) {
-                const int c = q / nl, l = q - c * nl;
-                Us[l * (IB + 1) + c] = c < bw ? __ldcg(A + (long long)(p + b0 + c) * ld + p + l) : (T)0;
-            }
-            if (t < IB) dv[t] = (T)1;
+        // the block's triangle, shifted so that its rows load as 16-byte vectors
+        for (int q = t; q < IB * IB; q += TRSM_THREADS) {
+            const int c = q >> 5, l = q & 31;
+            Sh[c * TS + l] = c + l < bw ? Us[(b0 + c) * LDX + b0 + c + l] : (T)0;
         }
         __syncthreads();
-        T acc[2][4];
+        // (1) substitution within the block, one thread per row, the row's 32
+        //     entries in registers; the entry finished in step c leaves through y[0]
+        if (t < CH) {
+            T y[IB];
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+            for (int l = 0; l < IB; ++l) y[l] = X[t * LDX + b0 + l];
+#pragma unroll 1
+            for (int c = 0; c < bw; ++c) {
+                T u[IB];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[a][e] = X[(2 * rg + a) * LDX + b0 + cg + 8 * e];
-        for (int l = 0; l < b0; ++l) {
-            const T x0 = X[(2 * rg) * LDX + l], x1 = X[(2 * rg + 1) * LDX + l];
+                for (int q = 0; q < IB; q += 16 / (int)sizeof(T)) lds16<T>(Sh + c * TS + q, u + q);
+                const T z = y[0] * dv[b0 + c];
+                X[t * LDX + b0 + c] = z;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const T u = Us[l * (IB + 1) + cg + 8 * e];
-                acc[0][e] -= x0 * u;
-                acc[1][e] -= x1 * u;
+                for (int l = 1; l < IB; ++l) y[l - 1] = y[l] - z * u[l];
             }
         }
-        subst8<T, 2>(acc, Us + b0 * (IB + 1), IB + 1, 1, dv, bw, cg);
-        __syncthreads();        // every read of this block's X and of Us is done
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) X[(2 * rg + a) * LDX + b0 + cg + 8 * e] = acc[a][e];
         __syncthreads();
+        // (2) right-looking update of the columns after the block
+        const int rem = w - b0 - bw;
+        if (rem > 0) {
+            const int nc = (rem + 15) / 16;
+            if (nc <= 2) trsm_rank32<T, NB, 2>(X, Us, b0, w, t);
+            else if (nc <= 4) trsm_rank32<T, NB, (NB >= 96 ? 4 : 2)>(X, Us, b0, w, t);
+            else trsm_rank32<T, NB, (NB >= 128 ? 6 : 2)>(X, Us, b0, w, t);
+            __syncthreads();
+        }
     }
     T* Aw = it.a;
     if (!colside) {
-        for (int q = t; q < R * w; q += TRSM_THREADS) {
-            const int r = q / w, c = q - r * w;
-            Aw[(long long)(g0 + r) * ld + p + c] = X[r * LDX + c];
-        }
+        const int xc = t % NB, xr = t / NB;
+        if (xc < w)
+#pragma unroll 4
+            for (int r = xr; r < R; r += TRSM_THREADS / NB) Aw[(long long)(g0 + r) * ld + p + xc] = X[r * LDX + xc];
     } else {
-        for (int q = t; q < R * w; q += TRSM_THREADS) {
-            const int k = q / R, c = q - k * R;
-            Aw[(long long)(p + k) * ld + g0 + c] = X[c * LDX + k];
-        }
+        const int xc = t % CH, xk = t / CH;
+        if (xc < R)
+#pragma unroll 4
+            for (int k = xk; k < w; k += TRSM_THREADS / CH) Aw[(long long)(p + k) * ld + g0 + xc] = X[xc * LDX + k];
     }
 }
 
@@ -309,19 +479,6 @@ __global__ void __launch_bounds__(TRSM_THREADS, 2) k_trsm(const EngItem<T>* __re
     const int chunk = colside ? blockIdx.y - nch : blockIdx.y;
     extern __shared__ __align__(16) unsigned char tsm_[];
     trsm_body<T, NB>(it, p, colside, chunk, scr + (long long)blockIdx.x * stride + (p / NB) * NB, tsm_);
-}
-
-template <class T>
-__device__ __forceinline__ void lds16(const T* p, T* out);
-template <>
-__device__ __forceinline__ void lds16<float>(const float* p, float* out) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-}
-template <>
-__device__ __forceinline__ void lds16<double>(const double* p, double* out) {
-    const double2 v = *reinterpret_cast<const double2*>(p);
-    out[0] = v.x; out[1] = v.y;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
@@ -338,6 +495,51 @@ struct UpdLayout {
     static constexpr int UKP = TILE + VW;              // U12 chunk, row-major [k][c]
     static constexpr int BUF = TILE * LKP + KC * UKP;  // elements of one buffer
 };
+
+// Load (STORE = false) or store (STORE = true) the thread's 2H x 2H part of a
+// TILE x TILE tile at (r0, c0): rows {tr*H + a, TILE/2 + tr*H + a}, columns
+// {tc*H + b, TILE/2 + tc*H + b}.  Loads element by element, unconditionally
+// (all of them can be in flight at once without extra registers): an
+// out-of-range element loads its clamped neighbour and is never stored.  Loads
+// go through L2 only (__ldcg).  Stores move runs of H columns
+// as one 16-byte access when the tile origin and leading dimension allow it and
+// the run is in range (out-of-range elements are not stored).
+template <class T, int H, int TILE, bool STORE>
+__device__ __forceinline__ void tile_io(T (&acc)[2 * H][2 * H], T* __restrict__ A, long long ld, int r0, int c0,
+                                        int n, int tr, int tc, bool vec) {
+    static_assert(H * sizeof(T) == 16, "one 16-byte access per run");
+#pragma unroll
+    for (int a = 0; a < 2 * H; ++a) {
+        const int gr = r0 + (a < H ? tr * H + a : TILE / 2 + tr * H + a - H);
+        T* row = A + (long long)gr * ld;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int gc = c0 + h * (TILE / 2) + tc * H;
+            T* q = row + gc;
+            if (STORE && vec && gr < n && gc + H <= n) {
+                {
+                    if (sizeof(T) == 4) {
+                        *reinterpret_cast<float4*>(q) = make_float4((float)acc[a][h * H], (float)acc[a][h * H + 1],
+                                                                    (float)acc[a][h * H + 2], (float)acc[a][h * H + 3]);
+                    } else {
+                        *reinterpret_cast<double2*>(q) = make_double2((double)acc[a][h * H], (double)acc[a][h * H + 1]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < H; ++b) {
+                    if (STORE) {
+                        if (gr < n && gc + b < n) q[b] = acc[a][h * H + b];
+                    } else {
+                        // unconditional load from the clamped position (an out-of-range
+                        // accumulator is never stored): no select, no extra registers
+                        acc[a][h * H + b] = __ldcg(A + (long long)min(gr, n - 1) * ld + min(gc + b, n - 1));
+                    }
+                }
+            }
+        }
+    }
+}
 
 // M22 -= L21 U12 on one TILE x TILE tile.  Thread (tr, tc) of a 16 x 16 grid owns
 // rows {tr*H + a, TILE/2 + tr*H + a} and columns {tc*H + b, TILE/2 + tc*H + b},
@@ -360,10 +562,6 @@ __device__ void update_body(const EngItem<T>& it, int p, int ti, int tj, unsigne
     const int t = threadIdx.x;
     const int tr = t >> 4, tc = t & 15;
     T acc[2 * H][2 * H];
-#pragma unroll
-    for (int a = 0; a < 2 * H; ++a)
-#pragma unroll
-        for (int b = 0; b < 2 * H; ++b) acc[a][b] = (T)0;
     T* buf0 = reinterpret_cast<T*>(usm);
     T* buf1 = buf0 + LY::BUF;
     const bool aligned = (m0 % VW) == 0 && (p % VW) == 0 && (ld % VW) == 0 &&
@@ -395,19 +593,40 @@ __device__ void update_body(const EngItem<T>& it, int p, int ti, int tj, unsigne
         cp_async_commit();
     };
     auto load_plain = [&](int k0, T* Lb, T* Ub) {
+        // PER elements per thread and operand, in batches of 8 loads in flight before their stores
+        constexpr int PER = TILE * KC / UPD_THREADS, BT = PER < 8 ? PER : 8;
         const int kw = min(KC, w - k0);
-        for (int q = t; q < TILE * KC; q += UPD_THREADS) {
-            const int r = q / KC, k = q - r * KC;
-            const int gr = r0 + r;
-            Lb[r * LKP + k] = (gr < n && k < kw) ? __ldcg(A + (long long)gr * ld + p + k0 + k) : (T)0;
+        for (int u0 = 0; u0 < PER; u0 += BT) {
+            T v[BT];
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                const int q = t + (u0 + u) * UPD_THREADS, r = q / KC, k = q - r * KC, gr = r0 + r;
+                v[u] = (gr < n && k < kw) ? __ldcg(A + (long long)gr * ld + p + k0 + k) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                const int q = t + (u0 + u) * UPD_THREADS, r = q / KC, k = q - r * KC;
+                Lb[r * LKP + k] = v[u];
+            }
         }
-        for (int q = t; q < TILE * KC; q += UPD_THREADS) {
-            const int k = q / TILE, c = q - k * TILE;
-            const int gc = c0 + c;
-            Ub[k * UKP + c] = (gc < n && k < kw) ? __ldcg(A + (long long)(p + k0 + k) * ld + gc) : (T)0;
+        for (int u0 = 0; u0 < PER; u0 += BT) {
+            T v[BT];
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                const int q = t + (u0 + u) * UPD_THREADS, k = q / TILE, c = q - k * TILE, gc = c0 + c;
+                v[u] = (gc < n && k < kw) ? __ldcg(A + (long long)(p + k0 + k) * ld + gc) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                const int q = t + (u0 + u) * UPD_THREADS, k = q / TILE, c = q - k * TILE;
+                Ub[k * UKP + c] = v[u];
+            }
         }
     };
     if (aligned) issue(0, buf0, buf0 + TILE * LKP);
+    // the accumulators start from the tile of M22 (loads in flight with the first chunk's
+    // copies); the K loop subtracts L21 U12 from them and the epilogue only stores
+    tile_io<T, H, TILE, false>(acc, A, ld, r0, c0, n, tr, tc, aligned);
     int b = 0;
     for (int k0 = 0; k0 < w; k0 += KC, b ^= 1) {
         T* Lc = b ? buf1 : buf0;
@@ -437,20 +656,10 @@ __device__ void update_body(const EngItem<T>& it, int p, int ti, int tj, unsigne
 #pragma unroll
             for (int a = 0; a < 2 * H; ++a)
 #pragma unroll
-                for (int bb = 0; bb < 2 * H; ++bb) acc[a][bb] += lv[a] * uv[bb];
+                for (int bb = 0; bb < 2 * H; ++bb) acc[a][bb] -= lv[a] * uv[bb];
         }
     }
-#pragma unroll
-    for (int a = 0; a < 2 * H; ++a) {
-        const int gr = r0 + (a < H ? tr * H + a : TILE / 2 + tr * H + a - H);
-        if (gr >= n) continue;
-        T* row = A + (long long)gr * ld;
-#pragma unroll
-        for (int bb = 0; bb < 2 * H; ++bb) {
-            const int gc = c0 + (bb < H ? tc * H + bb : TILE / 2 + tc * H + bb - H);
-            if (gc < n) row[gc] = __ldcg(row + gc) - acc[a][bb];
-        }
-    }
+    tile_io<T, H, TILE, true>(acc, A, ld, r0, c0, n, tr, tc, aligned);
 }
 
 template <class T, int TILE>
@@ -483,13 +692,162 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(const EngItem<T>* __rest
 template <class T>
 size_t trsm_smem() {
     constexpr int NB = EngCfg<T>::NB;
-    return sizeof(T) * ((size_t)CH * (NB + 1) + (size_t)NB * (IB + 1) + IB);
+    return sizeof(T) * ((size_t)CH * (NB + 1) + (size_t)NB * (NB + 1) + NB + IB * TS);
 }
 
 template <class T>
 size_t diag_smem() {
     constexpr int NB = EngCfg<T>::NB;
-    return sizeof(T) * ((size_t)NB * (NB + 1) + NB);
+    return sizeof(T) * ((size_t)NB * (NB + 1) + NB + 2 * IB * TS);
+}
+
+// M22 -= L21 U12 on one 128 x 128 tile on the tensor cores (tcgen05, split TF32,
+// FP32 accumulation in tensor memory), inside the persistent task kernel.  The
+// CTA holds 128 tensor-memory columns (the accumulator) and one mbarrier for its
+// whole life; nphase counts the mbarrier phases completed so far.  Per K-chunk
+// of 32: the chunk's operands (loaded into registers while the previous chunk's
+// MMAs run) are split into TF32 hi / lo parts and stored in the K-major
+// core-matrix layout (a warp's 16-byte stores cover whole 128-byte rows of core
+// matrices: no bank conflicts), one thread issues the 12 MMAs and commits them to
+// the mbarrier.  The epilogue reads the accumulator (warp w: rows 32 (w % 4) ..,
+// columns 64 (w / 4) ..), turns each 32 x 32 block around in shared memory and
+// subtracts it from the tile row by row (coalesced); the tile's lines were
+// prefetched into L2 when the task started.  Returns false if a bounded wait
+// expired (the error is flagged).
+template <int NB>
+__device__ __noinline__ bool tc_tile_body(const EngItem<float>& it, int p, int ti, int tj, unsigned char* smem, uint32_t tmem,
+                             uint32_t mbar, uint32_t& nphase, int* __restrict__ err) {
+    using namespace tcx;
+    static_assert(NB == 128, "one 128 x 128 MMA tile per task");
+    const int w = min(NB, it.k - p);
+    const int n = it.n;
+    const long long ld = it.ld;
+    const int m0 = p + w;
+    const int r0 = m0 + ti * 128, c0 = m0 + tj * 128;
+    if (r0 >= n || c0 >= n) return true;
+    const int rows = min(128, n - r0), cols = min(128, n - c0);
+    float* A = it.a;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int OPB = 128 * KMAX * 4;       // bytes of one operand part
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + OPB;
+    unsigned char* b_hi = smem + 2 * OPB;
+    unsigned char* b_lo = smem + 3 * OPB;
+    {
+        // the tile's lines into L2 now: the epilogue reads them after the K loop
+        for (int q = t; q < rows * 5; q += UPD_THREADS) {
+            const int r = q / 5, l = q - r * 5;
+            const int c = min(l * 32, cols - 1);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (long long)(r0 + r) * ld + c0 + c));
+        }
+    }
+    const bool vec = (ld & 3) == 0 && (reinterpret_cast<unsigned long long>(A) & 15) == 0;
+    // register staging: A part (row, 4 consecutive k) x 4, B part (n, k) x 16
+    float av[4][4], bv[16];
+    auto load = [&](int k0) {
+        const int kw = min(KMAX, w - k0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = t + u * UPD_THREADS;
+            const int row = (q >> 6) * 8 + (q & 7), k4 = ((q >> 3) & 7) * 4;
+            const float* src = A + (long long)(r0 + min(row, rows - 1)) * ld + p + k0 + k4;
+            if (vec && k4 + 4 <= kw) {
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(src));
+                av[u][0] = v.x; av[u][1] = v.y; av[u][2] = v.z; av[u][3] = v.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) av[u][e] = k4 + e < kw ? __ldcg(src + e) : 0.f;
+            }
+            if (row >= rows) av[u][0] = av[u][1] = av[u][2] = av[u][3] = 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int q = t + u * UPD_THREADS;
+            const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
+            bv[u] = (k < kw && nn < cols) ? __ldcg(A + (long long)(p + k0 + k) * ld + c0 + nn) : 0.f;
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = t + u * UPD_THREADS;
+            const int row = (q >> 6) * 8 + (q & 7), k4 = ((q >> 3) & 7) * 4;
+            float h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                h[e] = tf32_round(av[u][e]);
+                l[e] = tf32_round(av[u][e] - h[e]);
+            }
+            *reinterpret_cast<float4*>(a_hi + cm_off(row, k4)) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4*>(a_lo + cm_off(row, k4)) = make_float4(l[0], l[1], l[2], l[3]);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int q = t + u * UPD_THREADS;
+            const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
+            const float h = tf32_round(bv[u]);
+            *reinterpret_cast<float*>(b_hi + cm_off(nn, k)) = h;
+            *reinterpret_cast<float*>(b_lo + cm_off(nn, k)) = tf32_round(bv[u] - h);
+        }
+    };
+    bool ok = true;
+    load(0);
+    for (int k0 = 0; k0 < w; k0 += KMAX) {
+        if (k0 > 0) {
+            // the previous chunk's MMAs have read the operand buffers
+            ok = mbar_wait(mbar, nphase & 1) && ok;
+            ++nphase;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        }
+        store();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (t == 0) {
+            mma_chunk(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo), min(KMAX, w - k0),
+                      k0 == 0);
+            mma_commit(mbar);
+        }
+        if (k0 + KMAX < w) load(k0 + KMAX);
+    }
+    ok = mbar_wait(mbar, nphase & 1) && ok;
+    ++nphase;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!ok) {
+        if (t == 0) atomicOr(err, ERR_TIMEOUT_TC);
+        return false;
+    }
+    // warp w: accumulator lanes (tile rows) 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63;
+    // each 32 x 32 block turns around in shared memory (the operand buffers are
+    // free now) so that a warp reads and writes 32 consecutive columns of a row
+    const int wq = warp & 3, h = warp >> 2;
+    float* Tt = reinterpret_cast<float*>(smem) + warp * 32 * 33;
+#pragma unroll 1
+    for (int cb = 64 * h; cb < 64 * h + 64; cb += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)cb, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) Tt[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int col = cb + lane;
+        const bool cin = col < cols;
+        float c[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const int row = 32 * wq + r;
+            c[r] = (cin && row < rows) ? __ldcg(A + (long long)(r0 + row) * ld + c0 + col) : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const int row = 32 * wq + r;
+            if (cin && row < rows) A[(long long)(r0 + row) * ld + c0 + col] = c[r] - Tt[r * 33 + lane];
+        }
+        __syncwarp();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -555,7 +913,7 @@ __device__ void wait_prev_tiles(const int* flags, const EngMeta& m, int pi_prev,
         for (int b = u0; b <= u1; ++b) wait_flag(flags + flag_tile(m, pi_prev, a, b), abort_flag, err);
 }
 
-template <class T, int NB, int TILE>
+template <class T, int NB, int TILE, bool TC>
 __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T>* __restrict__ items,
                                                                  const EngTask* __restrict__ tasks, int ntasks,
                                                                  const EngMeta* __restrict__ meta, int* flags,
@@ -563,6 +921,28 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
                                                                  long long stride, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char esm[];
     __shared__ int s_idx;
+    // tensor-core tiles (FP32 only): 128 tensor-memory columns and one mbarrier for
+    // the CTA's lifetime
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    uint32_t tmem = 0, nphase = 0;
+    // (a separate instantiation: a kernel with tensor-memory allocation gets one CTA per SM)
+    constexpr bool tc = TC && sizeof(T) == 4;
+    if constexpr (tc) {
+        if ((threadIdx.x >> 5) == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(
+                tcx::smem_u32(&s_tmem)));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+        }
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tcx::smem_u32(&s_mbar)));
+            asm volatile("fence.mbarrier_init.release.cluster;\n");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        tmem = s_tmem;
+    }
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(next, 1);
         __syncthreads();
@@ -612,13 +992,28 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
             trsm_body<T, NB>(it, p, tk.type == 2, tk.a, pv, esm);
             own = tk.type == 1 ? flag_row(m, pi, tk.a) : flag_col(m, pi, tk.a);
         } else {
-            update_body<T, NB, TILE>(it, p, tk.a, tk.b, esm);
+            if constexpr (tc) {
+                {
+                    if (!tc_tile_body<NB>(reinterpret_cast<const EngItem<float>&>(it), p, tk.a, tk.b, esm, tmem,
+                                          tcx::smem_u32(&s_mbar), nphase, err) &&
+                        threadIdx.x == 0)
+                        atomicExch(abort_flag, 1);
+                }
+            } else {
+                update_body<T, NB, TILE>(it, p, tk.a, tk.b, esm);
+            }
             own = flag_tile(m, pi, tk.a, tk.b);
         }
         __threadfence();        // every thread's results, before the completion flag
         __syncthreads();
         if (threadIdx.x == 0)
             asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(flags + own), "r"(1) : "memory");
+    }
+    if constexpr (tc) {
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
     }
 }
 
@@ -736,7 +1131,7 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
     const long long stride = (long long)NB * std::max(1, (maxk + NB - 1) / NB);
     const bool timed = ktimer_on(KT_ENGINE_UPDATE) || ktimer_on(KT_ENGINE_PANEL);
     const bool use_tc = tc && sizeof(T) == 4;
-    if (!timed && !use_tc && hn && hk) {
+    if (!timed && hn && hk) {
         std::vector<EngTask> tasks;
         std::vector<EngMeta> meta;
         int nflags = 0;
@@ -756,12 +1151,19 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         int* flags = reinterpret_cast<int*>(dev + o2);
         BDDC_CUDA_TRY(cudaMemsetAsync(flags, 0, fb, st));
         const size_t sm = task_smem<T>();
-        auto kern = k_engine_tasks<T, NB, TILE>;
+        auto kern = use_tc ? k_engine_tasks<T, NB, TILE, true> : k_engine_tasks<T, NB, TILE, false>;
         BDDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        // all of the SM's configurable memory as shared memory: two CTAs of this size per SM
+        BDDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         int dev_id = 0, nsm = 0, occ = 0;
         BDDC_CUDA_TRY(cudaGetDevice(&dev_id));
         BDDC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id));
-        BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, UPD_THREADS, sm));
+        // residency from the CUDA-core instantiation (same registers and shared memory):
+        // the occupancy calculator reports one CTA per SM for a kernel that allocates
+        // tensor memory, but two CTAs of 128 columns each (of 512) run side by side
+        auto kcc = k_engine_tasks<T, NB, TILE, false>;
+        BDDC_CUDA_TRY(cudaFuncSetAttribute(kcc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kcc, UPD_THREADS, sm));
         const int grid = (int)std::min<long long>((long long)nsm * std::max(occ, 1), (long long)tasks.size());
         double fl = 0.0, by = 0.0;
         if (ktimer_on(KT_ENGINE_TASKS))

@@ -17,58 +17,13 @@
 #include <algorithm>
 
 #include "bddc_internal.h"
+#include "tc_common.cuh"
 
 namespace {
 
+using namespace tcx;
 constexpr int TM = 128, TN = 128;         // tile; the MMA is M = 128, N = 128
-constexpr int KMAX = 32;                  // panel width handled per launch
 constexpr int TC_THREADS = 128;
-constexpr int CORE_BYTES = 128;           // 8 rows x 16 bytes
-constexpr long long WAIT_LIMIT = 1LL << 24;
-
-// byte offset of element (row, k) in a K-major core-matrix layout of a
-// rows x KMAX FP32 operand: core matrix (row/8, k/4) at ((row/8)*(KMAX/4) + k/4)*128
-__device__ __forceinline__ int cm_off(int row, int k) {
-    return ((row >> 3) * (KMAX / 4) + (k >> 2)) * CORE_BYTES + (row & 7) * 16 + (k & 3) * 4;
-}
-
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor: start, leading-dimension byte offset (between
-// core matrices adjacent in K), stride byte offset (between core matrices
-// adjacent in M/N), descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;   // base offset 0, layout type 0 (no swizzle)
-}
-
-// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
-    return (1u << 4)                 // D format F32
-           | (2u << 7)               // A format TF32
-           | (2u << 10)              // B format TF32
-           | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 
 // Stage a 128 x K FP32 block (row r, column k at src[r*ld + k], rows >= nrows and
 // k >= K are zero) as TF32 hi / lo core-matrix operands.
@@ -91,22 +46,6 @@ __device__ __forceinline__ void stage(const float* __restrict__ src, long long l
         *reinterpret_cast<float*>(hi + cm_off(row, k)) = h;
         *reinterpret_cast<float*>(lo + cm_off(row, k)) = l;
     }
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // One 128 x 128 tile: C[0:nr, 0:nc] (row stride ldc) -= A[0:nr, 0:K] * B[0:K, 0:nc]
