@@ -18,23 +18,24 @@
 // not trapped.
 //
 // Right-looking blocked algorithm, panel width NB (128 in FP32, 64 in FP64).
-// Per panel three launches, each batched over all items:
-//   k_diag    one CTA per item factors the NB x NB diagonal block in shared
-//             memory, 32 columns at a time (the 32 pivot steps restricted to
-//             the column panel and the row strip, one barrier each, then a
-//             rank-32 update of the rest), writes L11\U11 back and the pivot
+// Per panel three kinds of task, each batched over all items:
+//   diagonal  one CTA factors the NB x NB diagonal block in shared memory, 32
+//             columns at a time (one warp factors the 32 x 32 sub-block in
+//             registers, one thread per row / column solves the strips, a
+//             register-tiled rank-32 update), writes L11\U11 back and the pivot
 //             reciprocals to a scratch;
-//   k_trsm    L21 = M21 U11^{-1} in 64-row chunks and U12 = L11^{-1} M12 in
+//   strip     L21 = M21 U11^{-1} in 64-row chunks and U12 = L11^{-1} M12 in
 //             64-column chunks (the latter solved transposed, so both run the
-//             same blocked substitution: per 32-column block subtract the
-//             solved blocks, then substitute within the block);
-//   k_update  M22 -= L21 U12 in TILE x TILE tiles, K staged through shared
-//             memory in chunks of 32, register-blocked (8 x 8 per thread in
-//             FP32, 4 x 4 in FP64).  The FP32 update can run on the tensor
-//             cores instead (tc_update.cu).
-// A wider panel divides the passes over the trailing matrices (the HBM
-// traffic of the update) by the width: NB = 128 does a quarter of the
-// passes of a 32-wide panel.
+//             same code: per 32-column block a thread-per-row substitution, then a
+//             right-looking update of the later columns);
+//   update    M22 -= L21 U12 in TILE x TILE tiles: on the tensor cores (tcgen05,
+//             split TF32, FP32 path by default) or on the CUDA cores (register
+//             tiles, K staged through shared memory in chunks of 32).
+// One persistent task kernel runs all panels of all items (below); with the
+// kernel timer on, per-panel launches k_diag, k_trsm, k_update (or the
+// tensor-core k_tc_update) run the same bodies.  A wider panel divides the passes
+// over the trailing matrices (the HBM traffic of the update) by the width:
+// NB = 128 does a quarter of the passes of a 32-wide panel.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1119,9 +1120,10 @@ static void build_tasks(const int* hn, const int* hk, int count, std::vector<Eng
 }  // namespace
 
 // Eliminate the leading k_i unknowns of every item.  Default: one persistent
-// task kernel per call.  With the kernel timer on (or the tensor-core update)
-// the per-panel launches k_diag, k_trsm, k_update run instead, so that every
-// launch of a kernel class can be bracketed by events.
+// task kernel per call (update tiles on the tensor cores when tc is set and T is
+// float).  With the kernel timer on, the per-panel launches k_diag, k_trsm,
+// k_update (k_tc_update) run instead, so that every launch of a kernel class can
+// be bracketed by events.
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* dscr, int* err,
                cudaStream_t st, const int* hn, const int* hk, bool tc) {

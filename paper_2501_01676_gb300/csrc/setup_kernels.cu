@@ -27,21 +27,41 @@ __global__ void k_copy_blocks(const CopyJob* __restrict__ jobs) {
     }
 }
 
-// dst[a][b] = S[p_a][p_b] (optionally symmetrised), p = perm list
+// dst[a][b] = S[p_a][p_b] (optionally symmetrised), p = perm list.  32 x 32
+// tiles, 8 rows of 32 lanes: the lanes run along b for S[p_a][p_b] and along a
+// for the transposed term S[p_b][p_a] (staged in shared memory), so both reads
+// follow the contiguous runs of the permutation.
 template <class TD>
 __global__ void k_gather_perm(const GatherJob* __restrict__ jobs, const int* __restrict__ idx) {
     const GatherJob J = jobs[blockIdx.x];
     const int* p = idx + J.perm_off;
     TD* dst = (TD*)J.dst;
     const TD* sT = (const TD*)J.srcT;
-    for (int a = blockIdx.y; a < J.n; a += gridDim.y) {
-        const long long ia = p[a];
-        for (int b = threadIdx.x; b < J.n; b += TH) {
-            const long long ib = p[b];
-            double v = J.src ? J.src[ia * J.sld + ib] : (double)sT[ia * J.sld + ib];
-            if (J.sym) v = 0.5 * (v + (J.src ? J.src[ib * J.sld + ia] : (double)sT[ib * J.sld + ia]));
-            dst[(long long)a * J.dld + b] = (TD)v;
+    __shared__ double T2[32][33];
+    const int nt = (J.n + 31) / 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    constexpr int RY = TH / 32;
+    auto S = [&](long long i, long long j) -> double {
+        return J.src ? J.src[i * J.sld + j] : (double)sT[i * J.sld + j];
+    };
+    for (int tile = blockIdx.y; tile < nt * nt; tile += gridDim.y) {
+        const int a0 = (tile / nt) * 32, b0 = (tile % nt) * 32;
+        if (J.sym) {
+            for (int bb = ty; bb < 32; bb += RY) {
+                const int b = b0 + bb, a = a0 + tx;
+                T2[bb][tx] = (a < J.n && b < J.n) ? S(p[b], p[a]) : 0.0;
+            }
+            __syncthreads();
         }
+        for (int aa = ty; aa < 32; aa += RY) {
+            const int a = a0 + aa, b = b0 + tx;
+            if (a < J.n && b < J.n) {
+                double v = S(p[a], p[b]);
+                if (J.sym) v = 0.5 * (v + T2[tx][aa]);
+                dst[(long long)a * J.dld + b] = (TD)v;
+            }
+        }
+        if (J.sym) __syncthreads();
     }
 }
 
