@@ -50,6 +50,10 @@ extern "C" {
 
 #define BDDC_PREC_FP64  0   /* every factor and operator in FP64                  */
 #define BDDC_PREC_MIXED 1   /* FP32 factors/operators + FP64 iterative refinement  */
+#define BDDC_PREC_BF16  2   /* as MIXED, the trailing updates of the FP32 dense
+                               eliminations on the tensor cores with BF16 operands
+                               (FP32 accumulation); the refinement restores FP64
+                               accuracy of the solution, at more iterations        */
 
 #define BDDC_EDGE_NONE 0
 #define BDDC_EDGE_NEW  1    /* edge GEP on prior-selected primal constraints      */
@@ -84,7 +88,7 @@ typedef struct {
     double theta_E;        /* edge threshold Theta_E (Sect. 4: 10)                 */
     double theta_F;        /* face threshold; <= 0: 1 + ln(H/h) per face (Sect. 4) */
     double tau;            /* stabilisation constant (Sect. 2: 0.7)               */
-    int precision;         /* BDDC_PREC_FP64 or BDDC_PREC_MIXED                    */
+    int precision;         /* BDDC_PREC_FP64, BDDC_PREC_MIXED or BDDC_PREC_BF16    */
     int restart;           /* GMRES restart length, 0: no restart                 */
     int max_iter;          /* iteration cap (Sect. 4: 300)                        */
     double rtol;           /* relative residual target (Sect. 4: 1e-8)            */
@@ -99,7 +103,7 @@ typedef struct {
                                 setup; NULL: no learned skip                        */
     int tensor_cores;      /* MIXED: 1 = trailing updates of the FP32 eliminations on
                               the tensor cores (tcgen05, split TF32), 0 = FP32 CUDA
-                              cores; ignored by the FP64 path                       */
+                              cores; ignored by the FP64 and BF16 paths             */
     int coarse_elim;       /* 1: invert S_Pi by the elimination engine always; 0:
                               small S_Pi (n_Pi <= 128) by FP32 Gauss-Jordan + FP64
                               Newton-Schulz when its residual check passes          */

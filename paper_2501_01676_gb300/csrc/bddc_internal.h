@@ -120,10 +120,14 @@ struct EngItem {
     int ld;      // leading dimension (elements)
 };
 
+// Trailing-update kind of the FP32 eliminations: CUDA cores, tensor cores with
+// split-TF32 operands (about FP32 accuracy), tensor cores with BF16 operands.
+enum { TC_NONE = 0, TC_SPLIT_TF32 = 1, TC_BF16 = 2 };
+
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* diag_scratch,
                int* err, cudaStream_t st, const int* host_n = nullptr, const int* host_k = nullptr,
-               bool tensor_cores = false);
+               int tensor_cores = TC_NONE);
 
 // Scratch elements engine_run needs for `count` items eliminating up to maxk
 // unknowns (FP64 if dbl).

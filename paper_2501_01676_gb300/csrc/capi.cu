@@ -266,8 +266,8 @@ static int run_engine(bddc_ctx* C, const std::vector<EngItem<T>>& items) {
         hn[i] = items[i].n;
         hk[i] = items[i].k;
     }
-    return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st, hn.data(), hk.data(),
-                         C->o.tensor_cores != 0);
+    const int kind = C->o.precision == BDDC_PREC_BF16 ? TC_BF16 : (C->o.tensor_cores ? TC_SPLIT_TF32 : TC_NONE);
+    return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st, hn.data(), hk.data(), kind);
 }
 
 // Change of basis of a list of entity blocks (TBlock, grouped by output
@@ -1755,11 +1755,12 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs, const bddc_part
     if (opts) C->o = *opts;
     else bddc_default_opts(&C->o);
     if (tol_eig > 0) C->o.theta_E = tol_eig;
-    if (C->o.max_iter <= 0 || !(C->o.rtol >= 0) || C->o.restart < 0) {
+    if (C->o.max_iter <= 0 || !(C->o.rtol >= 0) || C->o.restart < 0 || C->o.precision < BDDC_PREC_FP64 ||
+        C->o.precision > BDDC_PREC_BF16) {
         delete C;
         return BDDC_EINVAL;
     }
-    C->mixed = C->o.precision == BDDC_PREC_MIXED;
+    C->mixed = C->o.precision != BDDC_PREC_FP64;
     C->st = (cudaStream_t)stream;
     if (C->st == nullptr) {
         // a blocking stream: ordered with the legacy default stream, and capturable

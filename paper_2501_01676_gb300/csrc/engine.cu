@@ -45,6 +45,7 @@
 
 #include "bddc_internal.h"
 #include "tc_common.cuh"
+#include <cuda_bf16.h>
 
 namespace {
 
@@ -715,9 +716,10 @@ size_t diag_smem() {
 // subtracts it from the tile row by row (coalesced); the tile's lines were
 // prefetched into L2 when the task started.  Returns false if a bounded wait
 // expired (the error is flagged).
-template <int NB>
+template <int NB, int KIND>
 __device__ __noinline__ bool tc_tile_body(const EngItem<float>& it, int p, int ti, int tj, unsigned char* smem, uint32_t tmem,
                              uint32_t mbar, uint32_t& nphase, int* __restrict__ err) {
+    static_assert(KIND == TC_SPLIT_TF32 || KIND == TC_BF16, "operand kind");
     using namespace tcx;
     static_assert(NB == 128, "one 128 x 128 MMA tile per task");
     const int w = min(NB, it.k - p);
@@ -769,6 +771,27 @@ __device__ __noinline__ bool tc_tile_body(const EngItem<float>& it, int p, int t
         }
     };
     auto store = [&]() {
+        if constexpr (KIND == TC_BF16) {
+            // one BF16 operand each: A (row, 4 k) as one 8-byte store, B element by element
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = t + u * UPD_THREADS;
+                const int row = (q >> 6) * 8 + (q & 7), k4 = ((q >> 3) & 7) * 4;
+                const __nv_bfloat162 lo2 = __floats2bfloat162_rn(av[u][0], av[u][1]);
+                const __nv_bfloat162 hi2 = __floats2bfloat162_rn(av[u][2], av[u][3]);
+                uint2 pk;
+                pk.x = *reinterpret_cast<const uint32_t*>(&lo2);
+                pk.y = *reinterpret_cast<const uint32_t*>(&hi2);
+                *reinterpret_cast<uint2*>(a_hi + cm_off16(row, k4)) = pk;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int q = t + u * UPD_THREADS;
+                const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
+                *reinterpret_cast<__nv_bfloat16*>(b_hi + cm_off16(nn, k)) = __float2bfloat16_rn(bv[u]);
+            }
+            return;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int q = t + u * UPD_THREADS;
@@ -806,8 +829,11 @@ __device__ __noinline__ bool tc_tile_body(const EngItem<float>& it, int p, int t
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (t == 0) {
-            mma_chunk(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo), min(KMAX, w - k0),
-                      k0 == 0);
+            if constexpr (KIND == TC_BF16)
+                mma_chunk_bf16(tmem, smem_u32(a_hi), smem_u32(b_hi), min(KMAX, w - k0), k0 == 0);
+            else
+                mma_chunk(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo), min(KMAX, w - k0),
+                          k0 == 0);
             mma_commit(mbar);
         }
         if (k0 + KMAX < w) load(k0 + KMAX);
@@ -914,7 +940,7 @@ __device__ void wait_prev_tiles(const int* flags, const EngMeta& m, int pi_prev,
         for (int b = u0; b <= u1; ++b) wait_flag(flags + flag_tile(m, pi_prev, a, b), abort_flag, err);
 }
 
-template <class T, int NB, int TILE, bool TC>
+template <class T, int NB, int TILE, int TCK>
 __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T>* __restrict__ items,
                                                                  const EngTask* __restrict__ tasks, int ntasks,
                                                                  const EngMeta* __restrict__ meta, int* flags,
@@ -928,7 +954,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
     __shared__ __align__(8) uint64_t s_mbar;
     uint32_t tmem = 0, nphase = 0;
     // (a separate instantiation: a kernel with tensor-memory allocation gets one CTA per SM)
-    constexpr bool tc = TC && sizeof(T) == 4;
+    constexpr bool tc = TCK != TC_NONE && sizeof(T) == 4;
     if constexpr (tc) {
         if ((threadIdx.x >> 5) == 0) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(
@@ -995,7 +1021,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
         } else {
             if constexpr (tc) {
                 {
-                    if (!tc_tile_body<NB>(reinterpret_cast<const EngItem<float>&>(it), p, tk.a, tk.b, esm, tmem,
+                    if (!tc_tile_body<NB, (TCK == TC_BF16 ? TC_BF16 : TC_SPLIT_TF32)>(
+                            reinterpret_cast<const EngItem<float>&>(it), p, tk.a, tk.b, esm, tmem,
                                           tcx::smem_u32(&s_mbar), nphase, err) &&
                         threadIdx.x == 0)
                         atomicExch(abort_flag, 1);
@@ -1033,27 +1060,6 @@ long long engine_scratch_elems(int count, bool dbl, int maxk) {
 }
 
 namespace {
-// Side stream and events of the look-ahead (one set per host thread).
-struct LookAhead {
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    int dev = -1;
-    int init() {
-        int d = 0;
-        BDDC_CUDA_TRY(cudaGetDevice(&d));
-        if (side && d == dev) return BDDC_OK;
-        dev = d;                              // (a stream of another device is left alive)
-        int lo = 0, hi = 0;
-        BDDC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        // highest priority: the next panel's CTAs take SM slots as update CTAs retire
-        BDDC_CUDA_TRY(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi));
-        BDDC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        BDDC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-        return BDDC_OK;
-    }
-};
-thread_local LookAhead g_la;
-
 // Task list of the persistent kernel (host), in the order described above.
 template <class T>
 static void build_tasks(const int* hn, const int* hk, int count, std::vector<EngTask>& tasks,
@@ -1126,14 +1132,16 @@ static void build_tasks(const int* hn, const int* hk, int count, std::vector<Eng
 // be bracketed by events.
 template <class T>
 int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* dscr, int* err,
-               cudaStream_t st, const int* hn, const int* hk, bool tc) {
+               cudaStream_t st, const int* hn, const int* hk, int tc) {
     constexpr int NB = EngCfg<T>::NB, TILE = EngCfg<T>::TILE;
     static_assert(NB == TILE, "the task dependencies assume one tile per panel");
     if (count <= 0 || maxk <= 0) return BDDC_OK;
     const long long stride = (long long)NB * std::max(1, (maxk + NB - 1) / NB);
     const bool timed = ktimer_on(KT_ENGINE_UPDATE) || ktimer_on(KT_ENGINE_PANEL);
-    const bool use_tc = tc && sizeof(T) == 4;
-    if (!timed && hn && hk) {
+    const int tck = sizeof(T) == 4 ? tc : TC_NONE;
+    const bool use_tc = tck != TC_NONE;
+    // (the BF16 tiles exist only in the task kernel: it runs even with the timer on)
+    if ((!timed || tck == TC_BF16) && hn && hk) {
         std::vector<EngTask> tasks;
         std::vector<EngMeta> meta;
         int nflags = 0;
@@ -1153,7 +1161,8 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         int* flags = reinterpret_cast<int*>(dev + o2);
         BDDC_CUDA_TRY(cudaMemsetAsync(flags, 0, fb, st));
         const size_t sm = task_smem<T>();
-        auto kern = use_tc ? k_engine_tasks<T, NB, TILE, true> : k_engine_tasks<T, NB, TILE, false>;
+        auto kern = !use_tc ? k_engine_tasks<T, NB, TILE, TC_NONE>
+                    : (tck == TC_BF16 ? k_engine_tasks<T, NB, TILE, TC_BF16> : k_engine_tasks<T, NB, TILE, TC_SPLIT_TF32>);
         BDDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         // all of the SM's configurable memory as shared memory: two CTAs of this size per SM
         BDDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1163,7 +1172,7 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         // residency from the CUDA-core instantiation (same registers and shared memory):
         // the occupancy calculator reports one CTA per SM for a kernel that allocates
         // tensor memory, but two CTAs of 128 columns each (of 512) run side by side
-        auto kcc = k_engine_tasks<T, NB, TILE, false>;
+        auto kcc = k_engine_tasks<T, NB, TILE, TC_NONE>;
         BDDC_CUDA_TRY(cudaFuncSetAttribute(kcc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kcc, UPD_THREADS, sm));
         const int grid = (int)std::min<long long>((long long)nsm * std::max(occ, 1), (long long)tasks.size());
@@ -1237,6 +1246,6 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
 }
 
 template int engine_run<double>(const EngItem<double>*, int, int, int, double*, int*, cudaStream_t,
-                                const int*, const int*, bool);
+                                const int*, const int*, int);
 template int engine_run<float>(const EngItem<float>*, int, int, int, float*, int*, cudaStream_t,
-                               const int*, const int*, bool);
+                               const int*, const int*, int);

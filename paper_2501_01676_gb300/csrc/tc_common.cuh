@@ -115,3 +115,44 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 }  // namespace tcx
+
+// ---------------------------------------------------------------------------
+// BF16 operands (kind::f16 with A = B = BF16, FP32 accumulation): one MMA per
+// product, 8 BF16 values along K per core-matrix row, K = 16 per MMA.
+namespace tcx {
+
+// byte offset of element (row, k) in the K-major core-matrix layout of a
+// rows x KMAX BF16 operand: core matrix (row/8, k/8) at ((row/8)*(KMAX/8) + k/8)*128
+__device__ __forceinline__ int cm_off16(int row, int k) {
+    return ((row >> 3) * (KMAX / 8) + (k >> 3)) * CORE_BYTES + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
+    return (1u << 4)                 // D format F32
+           | (1u << 7)               // A format BF16
+           | (1u << 10)              // B format BF16
+           | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// MMAs of one staged BF16 chunk (kw <= KMAX valid K entries).
+__device__ __forceinline__ void mma_chunk_bf16(uint32_t tmem, uint32_t a, uint32_t b, int kw, bool first) {
+    const uint32_t idesc = instr_desc_bf16(128, 128);
+    const uint32_t lbo = CORE_BYTES;                     // next core matrix along K
+    const uint32_t sbo = (KMAX / 8) * CORE_BYTES;        // next 8-row group along M / N
+    for (int kk = 0; kk < (kw + 15) / 16; ++kk) {
+        const uint32_t koff = kk * 2 * CORE_BYTES;       // 16 BF16 = two core matrices along K
+        mma_bf16(tmem, smem_desc(a + koff, lbo, sbo), smem_desc(b + koff, lbo, sbo), idesc,
+                 (first && kk == 0) ? 0 : 1);
+    }
+}
+
+}  // namespace tcx

@@ -43,3 +43,27 @@ def test_engine_tensor_cores_match_cuda_cores():
     ub, sb = b.solve()
     assert sa["converged"] and sb["converged"]
     assert (ua - ub).abs().max().item() <= 1e-7 * ub.abs().max().item()
+
+
+def test_bf16_updates_schur_and_refined_solution():
+    """precision 2: the trailing updates of the FP32 eliminations on the tensor cores
+    with BF16 operands (FP32 accumulation).  The Schur complements carry a BF16-level
+    error, clearly above the split-TF32 path's (so the BF16 tiles did run), and the
+    FP64 refinement still reaches the 1e-8 residual and the FP64 solution."""
+    from paper_2501_01676_gb300 import workloads as W
+    p = W.uniform(2, 8, nu=0.05, beta=(1.0, 0.5, 0.25))
+    bf = B().Solver(p, precision=2)
+    tf = B().Solver(p, precision=1, tensor_cores=1)
+    f64 = B().Solver(p, precision=0)
+    e_bf = e_tf = 0.0
+    for sd in range(f64.stats()["nsub"]):
+        S = f64.schur(sd)
+        nS = np.linalg.norm(S)
+        e_bf = max(e_bf, np.linalg.norm(bf.schur(sd) - S) / nS)
+        e_tf = max(e_tf, np.linalg.norm(tf.schur(sd) - S) / nS)
+    assert e_bf <= 5e-2
+    assert e_bf >= 10 * e_tf
+    u, st = bf.solve()
+    assert st["converged"] and st["relres"] <= 1e-8
+    u64, _ = f64.solve()
+    assert (u - u64).abs().max().item() <= 1e-6 * u64.abs().max().item()
