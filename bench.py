@@ -45,6 +45,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM traffic per launch of the engine task kernel (mean of the four launches of
+# one step, profiles/engine_traffic_config2.md) and the hash of the sources it was
+# measured on: reported only while they are unchanged.
+ENGINE_TRAFFIC_BYTES = 133731584
+ENGINE_TRAFFIC_SOURCES = ("engine.cu", "tc_common.cuh", "bddc_internal.h")
+ENGINE_TRAFFIC_SHA256 = "9ea7868344f8a53fc27076ea43407fd7b70bea88b7dbf7ea8dcffbd201fe089f"
+
+
+def engine_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    try:
+        for f in ENGINE_TRAFFIC_SOURCES:
+            with open(os.path.join(ROOT, "paper_2501_01676_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return ENGINE_TRAFFIC_BYTES if h.hexdigest() == ENGINE_TRAFFIC_SHA256 else None
+
+
 def measured_bf16_tflops():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -266,7 +286,7 @@ def run_ours(args):
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     roofline = {"kernel": "k_engine_tasks<float,128,128> (blocked LU task kernel: 128-wide panels, 128x128 update tiles)",
                 "bound": "alu", "achieved": round(tfl, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                "frac": round(tfl / fp32_peak, 4), "traffic": None,
+                "frac": round(tfl / fp32_peak, 4), "traffic": engine_traffic(),
                 "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 x median sampled SM clock",
                 "launches": kt["launches"], "avg_launch_us": round(1e3 * kt["ms"] / max(kt["launches"], 1), 2),
                 "flops_per_launch": round(kt["flops"] / max(kt["launches"], 1)),
