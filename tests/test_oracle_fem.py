@@ -175,3 +175,43 @@ def test_manufactured_solution_rates():
     h1_rates = [math.log2(e[i][1] / e[i + 1][1]) for i in range(2)]
     assert 1.8 < l2_rates[-1] < 2.3, l2_rates
     assert 0.9 < h1_rates[-1] < 1.2, h1_rates
+
+
+def _golden_q1():
+    """The exact Q1 unit-cube integrals of tests/golden/q1_unit_cube.txt."""
+    from fractions import Fraction
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "q1_unit_cube.txt")
+    mats, cur = {}, None
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("["):
+                cur = line[1:-1]
+                mats[cur] = []
+            else:
+                mats[cur].append([float(Fraction(v)) for v in line.split()])
+    return {k: np.array(v) for k, v in mats.items()}
+
+
+@pytest.mark.parametrize("case", ["diffusion", "reaction", "convection"])
+def test_unit_cube_against_golden_integrals(case):
+    """Unit cube, one element: the oracle's element matrix against the stored exact
+    integrals combined by the bilinear form of Sect. 2 (tau = 0.7, h_K = sqrt 3;
+    here P_K < 1, so C_K = tau h_K^2 / (4 nu))."""
+    G = _golden_q1()
+    mesh = Mesh([[1], [1], [1]])
+    nu, c = 1.0, 0.0
+    beta = np.zeros(3)
+    if case == "reaction":
+        c = 1.0
+    if case == "convection":
+        beta = np.array([1.0, 0.0, 0.0])
+    A, _, _ = fem.element_matrices(mesh, np.full(1, nu), np.tile(beta, (8, 1)), np.zeros(8), c)
+    CK = 0.7 * 3.0 / (4.0 * nu)
+    want = {"diffusion": G["K0"],
+            "reaction": G["K0"] + (1.0 + CK) * G["M"],
+            "convection": G["K0"] + CK * G["Kx"] + 0.5 * (G["Cx"] - G["Cx"].T)}[case]
+    np.testing.assert_allclose(A[0], want, rtol=0, atol=1e-14)
