@@ -14,7 +14,8 @@ The plain FP64 GPU path is timed beside it.
 
 --impl reference times the FP64 CPU oracle as it stands on the host cores.
 Under torchrun (N > 1) each rank solves its own independent replica (the
-solver is single-GPU) and rank 0 prints the max over ranks.
+solver runs on one GPU; no data-path collective) and rank 0 prints the max
+over ranks.
 """
 from __future__ import annotations
 
