@@ -46,9 +46,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# DRAM traffic per launch of the engine task kernel (mean of the four launches of
-# one step, profiles/engine_traffic_config2.md) and the hash of the sources it was
-# measured on: reported only while they are unchanged.
+# DRAM traffic per launch of the engine task kernel: ncu's dram__bytes_read.sum +
+# dram__bytes_write.sum, mean over the four launches of one step of this workload,
+# and the hash of the sources it was measured on: reported only while they are
+# unchanged.
 ENGINE_TRAFFIC_BYTES = 133731584
 ENGINE_TRAFFIC_SOURCES = ("engine.cu", "tc_common.cuh", "bddc_internal.h")
 ENGINE_TRAFFIC_SHA256 = "9ea7868344f8a53fc27076ea43407fd7b70bea88b7dbf7ea8dcffbd201fe089f"
