@@ -790,28 +790,28 @@ __device__ __noinline__ bool tc_tile_body(const EngItem<float>& it, int p, int t
                 const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
                 *reinterpret_cast<__nv_bfloat16*>(b_hi + cm_off16(nn, k)) = __float2bfloat16_rn(bv[u]);
             }
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int q = t + u * UPD_THREADS;
-            const int row = (q >> 6) * 8 + (q & 7), k4 = ((q >> 3) & 7) * 4;
-            float h[4], l[4];
+            for (int u = 0; u < 4; ++u) {
+                const int q = t + u * UPD_THREADS;
+                const int row = (q >> 6) * 8 + (q & 7), k4 = ((q >> 3) & 7) * 4;
+                float h[4], l[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                h[e] = tf32_round(av[u][e]);
-                l[e] = tf32_round(av[u][e] - h[e]);
+                for (int e = 0; e < 4; ++e) {
+                    h[e] = tf32_round(av[u][e]);
+                    l[e] = tf32_round(av[u][e] - h[e]);
+                }
+                *reinterpret_cast<float4*>(a_hi + cm_off(row, k4)) = make_float4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<float4*>(a_lo + cm_off(row, k4)) = make_float4(l[0], l[1], l[2], l[3]);
             }
-            *reinterpret_cast<float4*>(a_hi + cm_off(row, k4)) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4*>(a_lo + cm_off(row, k4)) = make_float4(l[0], l[1], l[2], l[3]);
-        }
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int q = t + u * UPD_THREADS;
-            const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
-            const float h = tf32_round(bv[u]);
-            *reinterpret_cast<float*>(b_hi + cm_off(nn, k)) = h;
-            *reinterpret_cast<float*>(b_lo + cm_off(nn, k)) = tf32_round(bv[u] - h);
+            for (int u = 0; u < 16; ++u) {
+                const int q = t + u * UPD_THREADS;
+                const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
+                const float h = tf32_round(bv[u]);
+                *reinterpret_cast<float*>(b_hi + cm_off(nn, k)) = h;
+                *reinterpret_cast<float*>(b_lo + cm_off(nn, k)) = tf32_round(bv[u] - h);
+            }
         }
     };
     bool ok = true;

@@ -82,8 +82,7 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar));
 }
 
-// Bounded wait for the mbarrier phase with the given parity; false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     uint32_t done = 0;
     long long itn = 0;
     while (!done && itn < WAIT_LIMIT) {
@@ -96,6 +95,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         ++itn;
     }
     return done != 0;
+}
+
+// Bounded wait for the mbarrier phase with the given parity; false on expiry.  An
+// expired wait is followed by a second bounded one, so that the MMAs in flight
+// (which read the operand buffers and write the accumulator) have finished before
+// the caller reuses either or releases the tensor memory.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    if (mbar_try(mbar, parity)) return true;
+    mbar_try(mbar, parity);
+    return false;
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {

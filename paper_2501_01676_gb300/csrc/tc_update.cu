@@ -99,20 +99,9 @@ __device__ void tc_tile(const float* __restrict__ A, long long lda, const float*
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                              smem_u32(mbar)));
         }
-        // bounded wait for this chunk's MMAs (mbarrier phase = chunk parity)
-        uint32_t done = 0;
-        long long itn = 0;
-        const uint32_t parity = (uint32_t)(chunk & 1);
-        while (!done && itn < WAIT_LIMIT) {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                "selp.u32 %0, 1, 0, p;\n\t}\n"
-                : "=r"(done)
-                : "r"(smem_u32(mbar)), "r"(parity));
-            ++itn;
-        }
-        if (!done) {
+        // bounded wait for this chunk's MMAs (mbarrier phase = chunk parity; an
+        // expired wait is followed by a second bounded one)
+        if (!mbar_wait(smem_u32(mbar), (uint32_t)(chunk & 1))) {
             atomicOr(err, ERR_TIMEOUT_TC);
             ok = false;
         }
