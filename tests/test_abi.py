@@ -49,3 +49,15 @@ def test_host_only_calls(libpath):
     assert bddc.lib().bddc_strerror(-1).decode() == "invalid argument"
     # invalid arguments are rejected before any device work
     assert bddc.lib().bddc_setup(None, None, None, 0.0, None, None, None) == -1
+
+
+def test_precision_modes_match_the_header():
+    """The binding's precision constants equal the header's; the defaults are the FP64
+    path, tensor-core trailing updates for the mixed path, and the small-coarse route."""
+    from paper_2501_01676_gb300 import bddc
+    txt = open(os.path.join(ROOT, "include", "bddc.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (BDDC_PREC_\w+)\s+(\d+)", txt)}
+    assert consts == {"BDDC_PREC_FP64": bddc.PREC_FP64, "BDDC_PREC_MIXED": bddc.PREC_MIXED,
+                      "BDDC_PREC_BF16": bddc.PREC_BF16}
+    o = bddc.default_opts()
+    assert o.precision == bddc.PREC_FP64 and o.tensor_cores == 1 and o.coarse_elim == 0
