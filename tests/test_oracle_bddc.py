@@ -412,3 +412,158 @@ def test_gmres_is_minimal_residual():
         assert abs(np.linalg.norm(b - A @ x) - ref) < 1e-9 * np.linalg.norm(b)
     x, info = gmres(lambda v: A @ v, b, rtol=1e-12, restart=7, max_iter=300)
     assert info['converged'] and info['relres'] < 1e-11
+
+
+# ---------------------------------------------------------------- conventional edge GEP
+# Pins of BDDC.edge_gep_old (Sect. 3, eq. equ-4-8-E and the estimates before it)
+# built without the oracle's parallel_sum, schur or B_E assembly.
+
+@pytest.fixture(scope="module")
+def old222():
+    # 2x2x2 subdomains: every subdomain touches the Dirichlet boundary, so each
+    # B^(k) is positive definite and the brute-force minimisation below is a
+    # plain constrained quadratic problem.
+    return bddc.BDDC(W.random_small(4, (2, 2, 2), 4, (-3, 3)), edge_gep='old', theta_E=3.0)
+
+
+def _edge_blocks(o, ei):
+    subs = list(o.mesh.entities[ei]['subs'])
+    BE = {k: o.B[k][np.ix_(o.pos[(ei, k)], o.pos[(ei, k)])] for k in subs}
+    D = {k: o.D[(ei, k)] for k in subs}
+    return subs, BE, D
+
+
+def _double_sum(subs, BE, D, w):
+    """sum_i sum_{k != i} |D^(k) (w_iE - w_kE)|^2_{B_E^(i)}: the quantity the
+    paper bounds (third line of the edge estimate before eq. equ-4-8-E)."""
+    tot = 0.0
+    for i in subs:
+        for k in subs:
+            if k != i:
+                d = D[k] @ (w[i] - w[k])
+                tot += d @ BE[i] @ d
+    return tot
+
+
+def _BE_from_double_sum(subs, BE, D, n):
+    """B_E as the symmetric matrix whose form is q(v) = 1/2 sum_{i0} DS(delta_{i0} v):
+    placing v on one subdomain at a time and summing counts every term of the
+    double sum twice.  Built by polarisation on the unit vectors."""
+    def q(v):
+        tot = 0.0
+        for i0 in subs:
+            w = {k: (v if k == i0 else np.zeros(n)) for k in subs}
+            tot += _double_sum(subs, BE, D, w)
+        return 0.5 * tot
+    M = np.zeros((n, n))
+    E = np.eye(n)
+    for a in range(n):
+        for b in range(n):
+            M[a, b] = 0.25 * (q(E[a] + E[b]) - q(E[a] - E[b]))
+    return M
+
+
+def _Btilde_brute(o, ei):
+    """v^T B~_E v = min { sum_k w_k^T B^(k) w_k : sum_k w_kE = v } (the multi-way
+    parallel sum of the Schur complements onto E, by the minimal energy of the
+    Schur complement and of the parallel sum).  With B = blockdiag(B^(k)) and
+    C the sum of the edge restrictions, the minimum is v^T (C B^-1 C^T)^-1 v."""
+    subs = list(o.mesh.entities[ei]['subs'])
+    n = len(o.mesh.entities[ei]['dofs'])
+    sizes = [o.B[k].shape[0] for k in subs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    C = np.zeros((n, offs[-1]))
+    for a, k in enumerate(subs):
+        for t in range(n):
+            C[t, offs[a] + o.pos[(ei, k)][t]] = 1.0
+    Bblk = sla.block_diag(*[o.B[k] for k in subs])
+    return np.linalg.inv(C @ np.linalg.solve(Bblk, C.T))
+
+
+def test_old_edge_B_is_positive_definite_here(old222):
+    for k in range(old222.mesh.nsd):
+        assert np.linalg.eigvalsh(old222.B[k]).min() > 0
+
+
+def test_old_edge_BE_from_double_sum(old222):
+    """B_E of the oracle equals the matrix of the paper's double sum."""
+    o = old222
+    for ei, info in o.edge_info.items():
+        subs, BE, D = _edge_blocks(o, ei)
+        n = BE[subs[0]].shape[0]
+        ref = _BE_from_double_sum(subs, BE, D, n)
+        np.testing.assert_allclose(info['BE'], ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def test_old_edge_jump_bounded_by_double_sum(old222):
+    """Cauchy-Schwarz step of the edge estimate: sum_i |w_iE - sum_k D^(k) w_kE|^2_{B_E^(i)}
+    <= (|n(E)| - 1) DS(w), and DS(w) <= 2 sum_i w_iE^T B_E w_iE."""
+    o = old222
+    r = rng(21)
+    for ei, info in o.edge_info.items():
+        subs, BE, D = _edge_blocks(o, ei)
+        n = BE[subs[0]].shape[0]
+        for _ in range(10):
+            w = {k: r.standard_normal(n) for k in subs}
+            hat = sum(D[k] @ w[k] for k in subs)
+            jump = sum((w[i] - hat) @ BE[i] @ (w[i] - hat) for i in subs)
+            ds = _double_sum(subs, BE, D, w)
+            assert jump <= (len(subs) - 1) * ds * (1 + 1e-10) + 1e-14
+            assert ds <= 2 * sum(w[i] @ info['BE'] @ w[i] for i in subs) * (1 + 1e-10) + 1e-14
+
+
+def test_old_edge_Btilde_brute_force(old222):
+    """B~_E = B~_E^(1) : ... : B~_E^(m) against the constrained energy minimum."""
+    o = old222
+    for ei, info in o.edge_info.items():
+        ref = _Btilde_brute(o, ei)
+        np.testing.assert_allclose(info['Bt'], ref, rtol=1e-8, atol=1e-10 * np.abs(ref).max())
+
+
+def test_old_edge_pencil_matches_eigh(old222):
+    """Eigenvalues, selection and constraint span of the conventional edge GEP
+    against scipy.linalg.eigh on the independently built B_E and B~_E."""
+    o = old222
+    selected = 0
+    for ei, info in o.edge_info.items():
+        subs, BE, D = _edge_blocks(o, ei)
+        n = BE[subs[0]].shape[0]
+        X = _BE_from_double_sum(subs, BE, D, n)
+        Y = _Btilde_brute(o, ei)
+        lam, V = sla.eigh(0.5 * (X + X.T), 0.5 * (Y + Y.T))
+        order = np.argsort(-lam)
+        lam, V = lam[order], V[:, order]
+        np.testing.assert_allclose(info['lam'], lam, rtol=1e-8, atol=1e-12 * abs(lam).max())
+        sel = np.nonzero(lam >= o.theta_E)[0]
+        assert len(info['sel']) == len(sel)
+        assert info['Q'].shape[1] == len(sel)
+        selected += len(sel)
+        if len(sel):
+            Qref = np.linalg.qr(X @ V[:, sel])[0]
+            sv = np.linalg.svd(info['Q'].T @ Qref, compute_uv=False)
+            np.testing.assert_allclose(sv, 1.0, atol=1e-8)
+    assert selected > 0
+
+
+def test_old_edge_lemma(old222):
+    """Lemma (conventional edge constraints): for w_k satisfying
+    (B_E v_l)^T (w_iE - w_jE) = 0 for the selected l,
+    DS(w) <= 2 Theta_E sum_i w_iE^T B~_E w_iE <= 2 Theta_E sum_i w_i^T B^(i) w_i."""
+    o = old222
+    r = rng(22)
+    for ei, info in o.edge_info.items():
+        subs, BE, D = _edge_blocks(o, ei)
+        Q = info['Q']
+        Bt = _Btilde_brute(o, ei)
+        for _ in range(20):
+            w = {k: r.standard_normal(o.B[k].shape[0]) for k in subs}
+            ref = w[subs[0]][o.pos[(ei, subs[0])]]
+            for k in subs[1:]:
+                p = o.pos[(ei, k)]
+                w[k][p] -= Q @ (Q.T @ (w[k][p] - ref))
+            wE = {k: w[k][o.pos[(ei, k)]] for k in subs}
+            ds = _double_sum(subs, BE, D, wE)
+            mid = 2 * o.theta_E * sum(wE[k] @ Bt @ wE[k] for k in subs)
+            full = 2 * o.theta_E * sum(w[k] @ o.B[k] @ w[k] for k in subs)
+            assert ds <= mid * (1 + 1e-8) + 1e-12
+            assert mid <= full * (1 + 1e-8) + 1e-12
