@@ -104,9 +104,11 @@ typedef struct {
     int tensor_cores;      /* MIXED: 1 = trailing updates of the FP32 eliminations on
                               the tensor cores (tcgen05, split TF32), 0 = FP32 CUDA
                               cores; ignored by the FP64 and BF16 paths             */
-    int coarse_elim;       /* 1: invert S_Pi by the elimination engine always; 0:
-                              small S_Pi (n_Pi <= 128) by FP32 Gauss-Jordan + FP64
-                              Newton-Schulz when its residual check passes          */
+    int coarse_elim;       /* 1: invert S_Pi explicitly by the elimination engine
+                              always (dense, 4.7 n_Pi^3 flops); 0: small S_Pi
+                              (n_Pi <= 128) by FP32 Gauss-Jordan + FP64 Newton-
+                              Schulz when its residual check passes, otherwise the
+                              nested-dissection sparse LU of S_Pi (coarse_path 2)   */
 } bddc_opts;
 
 typedef struct {
@@ -126,8 +128,15 @@ typedef struct {
     double t_mesh_ms;        /* host numbering / entity lists / coefficient staging */
     double t_basis_ms;       /* change of basis + extended elimination (part of
                                 t_coarse_ms)                                      */
-    int coarse_path;         /* coarse inverse by 0: elimination, 1: FP32 Gauss-
-                                Jordan + FP64 Newton-Schulz (n_Pi <= 128)          */
+    int coarse_path;         /* coarse problem by 0: explicit FP64 inverse from the
+                                elimination of [[S_Pi, -I], [I, 0]], 1: FP32 Gauss-
+                                Jordan + FP64 Newton-Schulz (n_Pi <= 128), 2: FP64
+                                sparse LU by nested dissection of the subdomain grid
+                                (multifrontal; the apply runs its forward and
+                                backward sweeps)                                   */
+    int coarse_fronts;       /* path 2: dense fronts (separators) of the tree       */
+    int coarse_levels;       /* path 2: height of the tree (sweep launches per side) */
+    double coarse_factor_gflop; /* path 2: flops of the front eliminations / 1e9    */
 } bddc_stats;
 
 typedef struct bddc_ctx bddc_ctx;

@@ -51,7 +51,8 @@ class Stats(ct.Structure):
                 ("solve_ms", ct.c_double), ("t_assemble_ms", ct.c_double), ("t_factor_ms", ct.c_double),
                 ("t_face_ms", ct.c_double), ("t_edge_ms", ct.c_double), ("t_coarse_ms", ct.c_double),
                 ("jacobi_sweeps_max", ct.c_int), ("t_mesh_ms", ct.c_double), ("t_basis_ms", ct.c_double),
-                ("coarse_path", ct.c_int)]
+                ("coarse_path", ct.c_int), ("coarse_fronts", ct.c_int), ("coarse_levels", ct.c_int),
+                ("coarse_factor_gflop", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

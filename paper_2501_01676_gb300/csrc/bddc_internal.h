@@ -159,6 +159,55 @@ template <class T>
 int gemv_t_run(const T* pool, const GemvItem* items_dev, int nitems, const int* idx, const double* in,
                double* out, int nrhs, int in_ld, int out_ld, cudaStream_t st, const int* skip, double bytes);
 
+// ---------------------------------------------------------------------------
+// Coarse problem by nested dissection of the subdomain grid (coarse_plan.cpp,
+// coarse_nd.cu).  Front a eliminates its n own primal unknowns; its boundary
+// holds b unknowns of ancestor fronts.  The extended front
+//   [[F11, F12, -I], [F21, F22, 0], [I, 0, 0]]     (order N = 2n + b)
+// loses its n leading unknowns in the elimination engine, which leaves
+//   [[F22 - F21 F11^-1 F12, F21 F11^-1], [-F11^-1 F12, F11^-1]]
+// in its trailing block: the update added into the parent, the forward-sweep
+// operator and the backward-sweep operator.
+// ---------------------------------------------------------------------------
+struct NDFront {
+    int n, b;              // own / boundary unknowns
+    int N, ld;             // extended order and its leading dimension
+    long long foff;        // offset of the extended front in the front pool
+    long long wf_off;      // forward operator -F21 F11^-1 (b x n, leading dim wf_ld), operator pool
+    long long wb_off;      // backward operator [-F11^-1 F12 | F11^-1] (n x (b + n), leading dim wb_ld)
+    int wf_ld, wb_ld;
+    int vars_off;          // index pool: n + b global primal indices (own, then boundary)
+    int map_off;           // index pool: b positions in the parent's front (-1: root)
+    int parent;            // -1: root
+    int height, depth;     // height: 0 at the leaves; depth: 0 at the roots
+};
+
+struct NDPlan {
+    int nPi = 0;
+    std::vector<NDFront> fr;                      // pre-order: parents before their subtrees
+    std::vector<std::vector<int>> by_height;      // fronts per height (factorisation, forward sweep)
+    std::vector<std::vector<int>> by_depth;       // fronts per depth (backward sweep)
+    std::vector<int> idx;                         // index pool
+    long long fpool = 0, opool = 0;               // elements of the front and operator pools
+    std::vector<std::vector<GemvItem>> fwd, bwd;  // solve items per height / per depth
+    double flops = 0.0;                           // factorisation flops (extended fronts)
+    double bytes_solve = 0.0;                     // algorithmic bytes of one solve
+};
+
+// Host symbolic plan from the entities' primal counts and offsets (HostMesh).
+int nd_plan(const HostMesh& hm, int nPi, NDPlan& P);
+
+// One CTA row-slice of a front: rows [row0, row0 + nrows) of front `front`.
+struct NDRowJob {
+    int front, row0, nrows;
+};
+// Fill the extended fronts of the jobs from the dense coarse matrix S (nPi x nPi, FP64).
+int nd_fill_run(const NDFront* fr_dev, const NDRowJob* jobs, int njobs, const int* idx, const double* S, int nPi,
+                double* F, cudaStream_t st);
+// Add the trailing (update) blocks of the child fronts of the jobs (rows of the
+// child's b x b update) into their parents' fronts.
+int nd_add_run(const NDFront* fr_dev, const NDRowJob* jobs, int njobs, const int* idx, double* F, cudaStream_t st);
+
 // Small-matrix kernels for the GEPs live in gep.cu; launchers:
 struct FaceJob;   // defined in gep.cu
 struct EdgeJob;

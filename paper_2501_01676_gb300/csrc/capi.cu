@@ -203,6 +203,13 @@ struct bddc_ctx {
     std::vector<int> mald, mcld, np_s;
     double* SPiInv = nullptr;
     float* SPiInv32 = nullptr;         // MIXED: FP32 copy of the FP64 coarse inverse
+    // coarse problem by nested dissection (coarse_path 2): FP64 fronts and sweep operators
+    bool coarse_nd = false;
+    double* ndOps = nullptr;
+    int* ndIdx = nullptr;
+    GemvItem *ndFwd = nullptr, *ndBwd = nullptr;
+    std::vector<int> ndFwdOff, ndBwdOff;     // per group: first item (last entry: total)
+    std::vector<double> ndFwdBytes, ndBwdBytes;
     int* gidx_pool = nullptr;
     GemvItem *itS = nullptr, *itM1 = nullptr, *itC = nullptr, *itM3 = nullptr;
     int nitS = 0, nitM1 = 0, nitC = 0, nitM3 = 0, maxcols = 0;
@@ -370,6 +377,117 @@ static int change_basis(bddc_ctx* C, const std::vector<TBlock>& tb, const int* d
     BDDC_TRY(C->upload(&d_xs, xs));
     BDDC_TRY(C->upload(&d_xr, xr));
     return basis_run<T>(d_xr, (int)xr.size(), d_xs, d_xb, nmax, st);
+}
+
+// Coarse problem by nested dissection of the subdomain grid: symbolic plan on
+// the host, then per height of the tree (leaves first) the fronts are filled
+// from S_Pi, the children's updates are added, the engine eliminates the own
+// unknowns of every front of that height in one launch (FP64), and the sweep
+// operators are copied out of the trailing blocks.
+static int coarse_nd_setup(bddc_ctx* C, const double* SPi) {
+    cudaStream_t st = C->st;
+    const int nPi = C->nPi;
+    NDPlan P;
+    BDDC_TRY(nd_plan(C->hm, nPi, P));
+    double* Fp = nullptr;
+    BDDC_TRY(C->alloc(&Fp, (size_t)P.fpool));
+    BDDC_TRY(C->alloc(&C->ndOps, (size_t)P.opool));
+    BDDC_TRY(C->upload(&C->ndIdx, P.idx));
+    NDFront* d_fr = nullptr;
+    BDDC_TRY(C->upload(&d_fr, P.fr));
+    const int H = (int)P.by_height.size();
+    // row jobs of every height, uploaded once
+    const int RJ = 8;
+    std::vector<NDRowJob> fill, add;
+    std::vector<int> fill_off(H + 1, 0), add_off(H + 1, 0);
+    std::vector<CopyJob> cj;
+    std::vector<int> cj_off(H + 1, 0);
+    for (int h = 0; h < H; ++h) {
+        fill_off[h] = (int)fill.size();
+        add_off[h] = (int)add.size();
+        cj_off[h] = (int)cj.size();
+        for (int a : P.by_height[h]) {
+            const NDFront& f = P.fr[a];
+            for (int r0 = 0; r0 < f.N; r0 += RJ) fill.push_back(NDRowJob{a, r0, std::min(RJ, f.N - r0)});
+            if (f.b > 0 && f.n > 0)
+                cj.push_back(CopyJob{Fp + f.foff, f.ld, f.n, f.n + f.b, f.b, f.n, C->ndOps + f.wf_off, f.wf_ld, -1.0});
+            if (f.n > 0)
+                cj.push_back(CopyJob{Fp + f.foff, f.ld, f.n + f.b, f.n, f.n, f.b + f.n, C->ndOps + f.wb_off, f.wb_ld,
+                                     1.0});
+        }
+        // children (at lower heights) of this height's fronts
+        for (int a = 0; a < (int)P.fr.size(); ++a) {
+            const NDFront& f = P.fr[a];
+            if (f.parent < 0 || f.b == 0 || P.fr[f.parent].height != h) continue;
+            for (int r0 = 0; r0 < f.b; r0 += RJ) add.push_back(NDRowJob{a, r0, std::min(RJ, f.b - r0)});
+        }
+    }
+    fill_off[H] = (int)fill.size();
+    add_off[H] = (int)add.size();
+    cj_off[H] = (int)cj.size();
+    NDRowJob *d_fill = nullptr, *d_add = nullptr;
+    CopyJob* d_cj = nullptr;
+    BDDC_TRY(C->upload(&d_fill, fill));
+    BDDC_TRY(C->upload(&d_add, add));
+    BDDC_TRY(C->upload(&d_cj, cj));
+    for (int h = 0; h < H; ++h) {
+        BDDC_TRY(nd_fill_run(d_fr, d_fill + fill_off[h], fill_off[h + 1] - fill_off[h], C->ndIdx, SPi, nPi, Fp, st));
+        BDDC_TRY(nd_add_run(d_fr, d_add + add_off[h], add_off[h + 1] - add_off[h], C->ndIdx, Fp, st));
+        std::vector<EngItem<double>> items;
+        for (int a : P.by_height[h])
+            if (P.fr[a].n > 0) items.push_back(EngItem<double>{Fp + P.fr[a].foff, P.fr[a].N, P.fr[a].n, P.fr[a].ld});
+        BDDC_TRY(run_engine<double>(C, items));
+        if (cj_off[h + 1] > cj_off[h])
+            BDDC_TRY((copy_blocks_run<double, double>(d_cj + cj_off[h], cj_off[h + 1] - cj_off[h], 8, st)));
+    }
+    // sweep items, concatenated per group
+    std::vector<GemvItem> fw, bw;
+    C->ndFwdOff.assign(1, 0);
+    C->ndBwdOff.assign(1, 0);
+    C->ndFwdBytes.clear();
+    C->ndBwdBytes.clear();
+    for (int h = 0; h < H; ++h) {
+        fw.insert(fw.end(), P.fwd[h].begin(), P.fwd[h].end());
+        C->ndFwdOff.push_back((int)fw.size());
+        double by = 0.0;
+        for (int a : P.by_height[h]) by += 8.0 * P.fr[a].b * P.fr[a].n + 12.0 * (P.fr[a].n + P.fr[a].b);
+        C->ndFwdBytes.push_back(by);
+    }
+    for (int d = 0; d < (int)P.by_depth.size(); ++d) {
+        bw.insert(bw.end(), P.bwd[d].begin(), P.bwd[d].end());
+        C->ndBwdOff.push_back((int)bw.size());
+        double by = 0.0;
+        for (int a : P.by_depth[d])
+            by += 8.0 * P.fr[a].n * (P.fr[a].b + P.fr[a].n) + 12.0 * (P.fr[a].b + 2.0 * P.fr[a].n);
+        C->ndBwdBytes.push_back(by);
+    }
+    BDDC_TRY(C->upload(&C->ndFwd, fw));
+    BDDC_TRY(C->upload(&C->ndBwd, bw));
+    C->coarse_nd = true;
+    C->stats.coarse_fronts = (int)P.fr.size();
+    C->stats.coarse_levels = H;
+    C->stats.coarse_factor_gflop = P.flops * 1e-9;
+    return BDDC_OK;
+}
+
+// y2 = [y (nPi) | x (nPi)]: y holds the coarse right-hand side on entry (it is
+// transformed in place by the forward sweep), x receives S_Pi^-1 y.
+static int coarse_nd_solve(bddc_ctx* C, double* y2, const int* skip) {
+    const int nPi = C->nPi;
+    BDDC_CUDA_TRY(cudaMemsetAsync(y2 + nPi, 0, sizeof(double) * nPi, C->st));
+    for (size_t h = 0; h + 1 < C->ndFwdOff.size(); ++h) {
+        const int a = C->ndFwdOff[h], b = C->ndFwdOff[h + 1];
+        if (b > a)
+            BDDC_TRY(gemv_run<double>(C->ndOps, C->ndFwd + a, b - a, C->ndIdx, y2, y2, 0, 1, 0, 0, C->st, skip,
+                                      C->ndFwdBytes[h]));
+    }
+    for (size_t d = 0; d + 1 < C->ndBwdOff.size(); ++d) {
+        const int a = C->ndBwdOff[d], b = C->ndBwdOff[d + 1];
+        if (b > a)
+            BDDC_TRY(gemv_run<double>(C->ndOps, C->ndBwd + a, b - a, C->ndIdx, y2, y2, 0, 1, 0, 0, C->st, skip,
+                                      C->ndBwdBytes[d]));
+    }
+    return BDDC_OK;
 }
 
 template <class T>
@@ -1258,6 +1376,11 @@ static int setup_impl(bddc_ctx* C) {
         coarse_done = std::isfinite(hres[0]) && hres[0] <= target;
         C->stats.coarse_path = coarse_done ? 1 : 0;
     }
+    if (nPi > 0 && !coarse_done && !C->o.coarse_elim) {
+        BDDC_TRY(coarse_nd_setup(C, SPi));
+        coarse_done = true;
+        C->stats.coarse_path = 2;
+    }
     if (nPi > 0 && !coarse_done) {
         double* Xc = nullptr;
         BDDC_TRY(C->alloc(&Xc, 4LL * nPi * nPi));
@@ -1270,7 +1393,7 @@ static int setup_impl(bddc_ctx* C) {
         BDDC_TRY((copy_blocks_run<double, double>(d_cj, 1, 64, st)));
     }
     ktimer_end(KT_COARSE, st, 0.0, 0.0);
-    if (nPi > 0 && C->mixed) {
+    if (nPi > 0 && C->mixed && !C->coarse_nd) {
         // the coarse problem is solved in FP64; the mixed apply streams its inverse in FP32
         BDDC_TRY(C->alloc(&C->SPiInv32, (size_t)std::max(nPi, 1) * ldc));
         std::vector<CopyJob> cj2{CopyJob{C->SPiInv, ldc, 0, 0, nPi, nPi, C->SPiInv32, ldc, 1.0}};
@@ -1292,24 +1415,36 @@ static int op_S(bddc_ctx* C, const double* x, double* y, const int* skip) {
                        C->bytesS);
 }
 
-// zc[0:nG] = M^-1 x (zc[nG:nG+nPi] holds the coarse residual)
+// zc[0:nG] = M^-1 x with caller-chosen work vectors: zc (nG + nPi; zc[nG:]
+// receives the coarse residual) and upi (nPi, the coarse solution), where
+// upi == zc + nG + nPi (the nested-dissection sweeps address both through one
+// base pointer).
 template <class T>
-static int op_M(bddc_ctx* C, const double* x, const int* skip) {
-    BDDC_CUDA_TRY(cudaMemsetAsync(C->zc, 0, sizeof(double) * (C->nG + C->nPi), C->st));
-    BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, C->zc, C->maxcols, 1, 0, 0, C->st, skip,
+static int op_M_into(bddc_ctx* C, const double* x, double* zc, double* upi, const int* skip) {
+    BDDC_CUDA_TRY(cudaMemsetAsync(zc, 0, sizeof(double) * (C->nG + C->nPi), C->st));
+    BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, zc, C->maxcols, 1, 0, 0, C->st, skip,
                          C->bytesM1));
     if (C->nPi > 0) {
-        BDDC_CUDA_TRY(cudaMemsetAsync(C->uPi, 0, sizeof(double) * C->nPi, C->st));
-        if (C->mixed)
-            BDDC_TRY(gemv_run<float>(C->SPiInv32, C->itC, C->nitC, C->gidx_pool, C->zc, C->uPi, C->maxcols, 1, 0, 0,
-                                     C->st, skip, C->bytesC32));
-        else
-            BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, C->zc, C->uPi, C->maxcols, 1, 0, 0,
-                                      C->st, skip, C->bytesC));
-        BDDC_TRY(gemv_t_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, C->uPi, C->zc, 1, 0, 0, C->st, skip,
+        if (C->coarse_nd) {
+            BDDC_TRY(coarse_nd_solve(C, zc + C->nG, skip));
+        } else {
+            BDDC_CUDA_TRY(cudaMemsetAsync(upi, 0, sizeof(double) * C->nPi, C->st));
+            if (C->mixed)
+                BDDC_TRY(gemv_run<float>(C->SPiInv32, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0,
+                                         C->st, skip, C->bytesC32));
+            else
+                BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0,
+                                          C->st, skip, C->bytesC));
+        }
+        BDDC_TRY(gemv_t_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, upi, zc, 1, 0, 0, C->st, skip,
                                C->bytesM3));
     }
     return BDDC_OK;
+}
+
+template <class T>
+static int op_M(bddc_ctx* C, const double* x, const int* skip) {
+    return op_M_into<T>(C, x, C->zc, C->uPi, skip);
 }
 
 // Executable GMRES graphs of destroyed contexts, per host thread.  A new context
@@ -1532,25 +1667,6 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
     return conv ? BDDC_OK : BDDC_NOT_CONVERGED;
 }
 
-// M^-1 applied with caller-supplied work vectors (zc: n_gamma + n_pi, upi:
-// n_pi); used by the entry point whose work vectors live in static memory.
-template <class T>
-static int op_M_into(bddc_ctx* C, const double* x, double* zc, double* upi) {
-    BDDC_CUDA_TRY(cudaMemsetAsync(zc, 0, sizeof(double) * (C->nG + C->nPi), C->st));
-    BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, zc, C->maxcols, 1, 0, 0, C->st, nullptr));
-    if (C->nPi > 0) {
-        BDDC_CUDA_TRY(cudaMemsetAsync(upi, 0, sizeof(double) * C->nPi, C->st));
-        if (C->mixed)
-            BDDC_TRY(gemv_run<float>(C->SPiInv32, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0, C->st,
-                                     nullptr));
-        else
-            BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0, C->st,
-                                      nullptr));
-        BDDC_TRY(gemv_t_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, upi, zc, 1, 0, 0, C->st, nullptr, 0.0));
-    }
-    return BDDC_OK;
-}
-
 int bddc_apply_into(bddc_ctx* C, const double* r, double* z, int nrhs, double* work, size_t work_doubles) {
     if (!C || !r || !z || nrhs < 1 || !work) return BDDC_EINVAL;
     const size_t need = (size_t)C->nG + 2 * (size_t)C->nPi;
@@ -1561,8 +1677,8 @@ int bddc_apply_into(bddc_ctx* C, const double* r, double* z, int nrhs, double* w
     double* zc = work;
     double* upi = work + C->nG + C->nPi;
     for (int c = 0; c < nrhs; ++c) {
-        if (C->mixed) BDDC_TRY(op_M_into<float>(C, r + (long long)c * C->nG, zc, upi));
-        else BDDC_TRY(op_M_into<double>(C, r + (long long)c * C->nG, zc, upi));
+        if (C->mixed) BDDC_TRY(op_M_into<float>(C, r + (long long)c * C->nG, zc, upi, nullptr));
+        else BDDC_TRY(op_M_into<double>(C, r + (long long)c * C->nG, zc, upi, nullptr));
         BDDC_CUDA_TRY(cudaMemcpyAsync(z + (long long)c * C->nG, zc, sizeof(double) * C->nG,
                                       cudaMemcpyDeviceToDevice, C->st));
     }
@@ -1691,8 +1807,8 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     else BDDC_TRY(setup_impl<double>(C));
     // solve buffers
     const long long nG = C->nG, ndof = hm.ndof;
-    BDDC_TRY(C->alloc(&C->zc, nG + C->nPi + 1));
-    BDDC_TRY(C->alloc(&C->uPi, C->nPi + 1));
+    BDDC_TRY(C->alloc(&C->zc, nG + 2 * (long long)C->nPi + 1));
+    C->uPi = C->zc + nG + C->nPi;
     BDDC_TRY(C->alloc(&C->g, nG));
     BDDC_TRY(C->alloc(&C->xG, nG));
     BDDC_TRY(C->alloc(&C->r, nG));

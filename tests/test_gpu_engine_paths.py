@@ -5,9 +5,11 @@
   Both run the same task bodies in the same panel order; the assembly's atomic
   sums make two setups differ in the last bits, so the Schur complements agree
   to 1e-12 (FP64) / 1e-5 (FP32) of their largest entry.
-* The coarse inverse: FP32 Gauss-Jordan + FP64 Newton-Schulz for small coarse
-  problems versus the elimination of [[S_Pi, -I], [I, 0]]; the FP64 preconditioner
-  applies agree to 1e-11 relative and the oracle's apply to 1e-9.
+* The coarse problem: FP32 Gauss-Jordan + FP64 Newton-Schulz for small coarse
+  problems, the sparse LU by nested dissection of the subdomain grid for larger
+  ones, and the explicit inverse from the elimination of [[S_Pi, -I], [I, 0]];
+  the FP64 preconditioner applies agree to 1e-11 relative and the oracle's apply
+  to 1e-9.
 * The FP32 face pencils (tridiagonal route, selected eigenpairs only) against the
   FP64 route: the same constraint counts, eigenvalues sigma = lambda / (1 + lambda)
   within 1e-4, and the same constraint spans.
@@ -79,13 +81,55 @@ def test_coarse_inverse_paths_agree():
     assert np.linalg.norm(z_small - zo) <= 1e-9 * np.linalg.norm(zo)
 
 
-def test_large_coarse_space_takes_the_elimination():
+def test_large_coarse_space_takes_nested_dissection():
     p = W.uniform(5, 3, nu=0.2, beta=(1.0, 0.0, 0.5))
     s = B().Solver(p, precision=1)
     st = s.stats()
-    assert st["n_pi"] > 128 and st["coarse_path"] == 0
+    assert st["n_pi"] > 128 and st["coarse_path"] == 2 and st["coarse_fronts"] > 1
     u, sv = s.solve()
     assert sv["converged"] and sv["relres"] <= 1e-8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nested_dissection_coarse_matches_dense_inverse_and_oracle(precision):
+    """The sparse nested-dissection LU of S_Pi against its explicit dense inverse
+    (both FP64) inside M^-1 r, and against the oracle's M^-1 r."""
+    import torch
+    p = W.random_small(6, (4, 4, 3), 3, (-2, 1))
+    nd = B().Solver(p, precision=precision, theta_F=1.0)
+    dense = B().Solver(p, precision=precision, theta_F=1.0, coarse_elim=1)
+    st = nd.stats()
+    assert st["coarse_path"] == 2 and dense.stats()["coarse_path"] == 0
+    assert st["n_pi"] > 128 and st["coarse_levels"] >= 3
+    rng = np.random.default_rng(3)
+    o = obddc.BDDC(p, theta_F=1.0) if precision == 0 else None
+    for _ in range(2):
+        r = rng.standard_normal(nd.n_gamma)
+        rd = torch.from_numpy(r).cuda()
+        z_nd = nd.apply(rd).cpu().numpy()
+        z_dense = dense.apply(rd).cpu().numpy()
+        # FP64 coarse solves on both sides; MIXED streams the dense inverse in FP32
+        tol = 1e-11 if precision == 0 else 1e-5
+        assert np.linalg.norm(z_nd - z_dense) <= tol * np.linalg.norm(z_dense)
+        if o is not None:
+            assert o.nPi == st["n_pi"]
+            zo = o.apply_M(r)
+            assert np.linalg.norm(z_nd - zo) <= 1e-9 * np.linalg.norm(zo)
+    u, sv = nd.solve()
+    assert sv["converged"]
+
+
+def test_nested_dissection_coarse_uneven_partition():
+    """Uneven slabs (per-direction H/h from 6 to 10, 6x6x6 subdomains): the
+    nested-dissection coarse solve against the dense inverse."""
+    import torch
+    p = W.config4()
+    nd = B().Solver(p, precision=0)
+    dense = B().Solver(p, precision=0, coarse_elim=1)
+    assert nd.stats()["coarse_path"] == 2
+    r = torch.from_numpy(np.random.default_rng(4).standard_normal(nd.n_gamma)).cuda()
+    z_nd, z_dense = nd.apply(r), dense.apply(r)
+    assert (z_nd - z_dense).norm().item() <= 1e-11 * z_dense.norm().item()
 
 
 def _angle(Qa, Qb):
