@@ -109,6 +109,10 @@ typedef struct {
                               (n_Pi <= 128) by FP32 Gauss-Jordan + FP64 Newton-
                               Schulz when its residual check passes, otherwise the
                               nested-dissection sparse LU of S_Pi (coarse_path 2)   */
+    int apply_launch;      /* 0: M^-1 r as one persistent launch (local part, coarse
+                              restriction, coarse solve and prolongation as work
+                              items with completion counters); 1: one launch per
+                              phase (the reference path of the tests)              */
 } bddc_opts;
 
 typedef struct {
@@ -144,7 +148,8 @@ typedef struct bddc_ctx bddc_ctx;
 /* Fill `o` with the defaults of Sect. 4: Theta_E = 10, Theta_F = 1 + ln(H/h),
  * tau = 0.7, FP64, no restart, 300 iterations, rtol 1e-8, new edge GEP,
  * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip, tensor-core
- * trailing updates in the MIXED path (tensor_cores 1), coarse_elim 0. */
+ * trailing updates in the MIXED path (tensor_cores 1), coarse_elim 0,
+ * apply_launch 0. */
 void bddc_default_opts(bddc_opts* o);
 
 /* Setup (call stack: assembly, batched Dirichlet factorisation + Schur
@@ -212,7 +217,8 @@ int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, i
  * launch of that kernel class (1 engine trailing update, 2 engine panel,
  * 3 apply GEMV, 4 face GEP, 5 edge GEP, 6 element assembly, 7 change of basis,
  * 8 interior condense / recover solves, 9 coarse inverse, 10 the engine's
- * persistent task kernel (1 and 2 switch the engine to per-panel launches);
+ * persistent task kernel, 11 the one-launch preconditioner apply (1 and 2
+ * switch the engine to per-panel launches);
  * 0 off) is bracketed by CUDA events on
  * its stream (launches captured into graphs are not).  _read synchronises on
  * the recorded events and returns their summed duration, the number of

@@ -40,7 +40,7 @@ class Opts(ct.Structure):
                 ("rtol", ct.c_double), ("edge_gep", ct.c_int), ("face_gep", ct.c_int),
                 ("all_primal", ct.c_int), ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
                 ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p), ("tensor_cores", ct.c_int),
-                ("coarse_elim", ct.c_int)]
+                ("coarse_elim", ct.c_int), ("apply_launch", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -165,7 +165,7 @@ def load_mlp_params():
     return np.ascontiguousarray(np.load(MLP_PARAMS_FILE), dtype=np.float32)
 
 (KT_NONE, KT_ENGINE_UPDATE, KT_ENGINE_PANEL, KT_GEMV, KT_FACE, KT_EDGE, KT_ASSEMBLE, KT_TRANSFORM, KT_TRI,
- KT_COARSE, KT_ENGINE_TASKS) = range(11)
+ KT_COARSE, KT_ENGINE_TASKS, KT_APPLY_TASKS) = range(12)
 
 
 def kernel_timer(kind):

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbddc.so")
 SOURCES = ["host_mesh.cpp", "assemble.cu", "engine.cu", "apply.cu", "gmres.cu", "gep.cu",
            "setup_kernels.cu", "capi.cu", "static_apply.cu", "mlp.cu", "tc_update.cu",
-           "coarse_inv.cu", "coarse_plan.cpp", "coarse_nd.cu"]
+           "coarse_inv.cu", "coarse_plan.cpp", "coarse_nd.cu", "apply_tasks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

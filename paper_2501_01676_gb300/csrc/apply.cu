@@ -176,8 +176,18 @@ __global__ void __launch_bounds__(GEMV_THREADS) k_gemv_t(const T* __restrict__ p
         for (int q = t; q < it.ncols; q += GEMV_THREADS) xs[q] = (T)inc[iidx[it.col0 + q]];
         __syncthreads();
         for (int r = it.row0 + t; r < it.row0 + it.nrows; r += GEMV_THREADS) {
+            const T* col = Mt + (long long)it.col0 * it.ld + r;
             T acc = 0;
-            for (int q = 0; q < it.ncols; ++q) acc += Mt[(long long)(it.col0 + q) * it.ld + r] * xs[q];
+            int q = 0;
+            // eight independent loads in flight per thread
+            for (; q + 8 <= it.ncols; q += 8) {
+                T a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = __ldg(col + (long long)(q + u) * it.ld);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += a[u] * xs[q + u];
+            }
+            for (; q < it.ncols; ++q) acc += __ldg(col + (long long)q * it.ld) * xs[q];
             atomicAdd(&outc[oidx[r]], (double)acc);
         }
         __syncthreads();

@@ -33,7 +33,8 @@ void bddc_note_launches(unsigned long long n);
 
 // Optional CUDA-event timing of one kernel class (for roofline reporting).
 enum { KT_NONE = 0, KT_ENGINE_UPDATE = 1, KT_ENGINE_PANEL = 2, KT_GEMV = 3, KT_FACE = 4, KT_EDGE = 5,
-       KT_ASSEMBLE = 6, KT_TRANSFORM = 7, KT_TRI = 8, KT_COARSE = 9, KT_ENGINE_TASKS = 10, KT_LAST = 10 };
+       KT_ASSEMBLE = 6, KT_TRANSFORM = 7, KT_TRI = 8, KT_COARSE = 9, KT_ENGINE_TASKS = 10, KT_APPLY_TASKS = 11,
+       KT_LAST = 11 };
 bool ktimer_on(int kind);
 void ktimer_begin(int kind, cudaStream_t st);
 void ktimer_end(int kind, cudaStream_t st, double flops, double bytes);
@@ -45,6 +46,7 @@ enum {
     ERR_SIZE = 4,         // a size exceeded a compiled limit
     ERR_TIMEOUT_TC = 8,   // a bounded wait for tensor-core work gave up
     ERR_TIMEOUT_ENGINE = 16,  // a bounded wait of the engine's task kernel gave up
+    ERR_TIMEOUT_APPLY = 32,   // a bounded wait of the preconditioner's task kernel gave up
 };
 
 // ---------------------------------------------------------------------------
@@ -196,6 +198,8 @@ struct NDPlan {
 
 // Host symbolic plan from the entities' primal counts and offsets (HostMesh).
 int nd_plan(const HostMesh& hm, int nPi, NDPlan& P);
+// Row and column extent of one sweep work item.
+constexpr int ND_ITEM_ROWS = 16, ND_ITEM_COLS = 256;
 
 // One CTA row-slice of a front: rows [row0, row0 + nrows) of front `front`.
 struct NDRowJob {
@@ -207,6 +211,35 @@ int nd_fill_run(const NDFront* fr_dev, const NDRowJob* jobs, int njobs, const in
 // Add the trailing (update) blocks of the child fronts of the jobs (rows of the
 // child's b x b update) into their parents' fronts.
 int nd_add_run(const NDFront* fr_dev, const NDRowJob* jobs, int njobs, const int* idx, double* F, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// M^-1 r as one persistent launch (apply_tasks.cu): work items in topological
+// order with completion counters.
+// ---------------------------------------------------------------------------
+enum { AP_LOCAL = 0,    // rows of [P_i ; Psi_i^T D_i^T]: r -> zc (local part, coarse restriction)
+       AP_SWEEP = 1,    // nested-dissection sweep operator (FP64): y2 -> y2, index pool B
+       AP_DENSE = 2,    // explicit coarse inverse (FP64): y -> x inside y2
+       AP_PROLONG = 3   // D_i Phi_i stored transposed: x -> zc
+};
+// counters: [0] next coarse-queue item, [1] abort, [2] restriction items done,
+// [3] coarse-solve items done, [4] next local-queue item, [5] next restriction
+// item, then per front: forward items of its children done, its backward items done
+enum { AP_CTR_NEXT = 0, AP_CTR_ABORT = 1, AP_CTR_LOCAL = 2, AP_CTR_COARSE = 3, AP_CTR_NEXT_LOCAL = 4,
+       AP_CTR_NEXT_RES = 5, AP_CTR_FRONTS = 6 };
+struct ApTask {
+    GemvItem it;
+    int kind;
+    int w0, t0, w1, t1;    // wait until ctr[w] >= t (w < 0: no wait)
+    int s0, s1;            // ctr[s] += 1 when done (s < 0: none)
+};
+template <class T>
+int apply_tasks_blocks();
+// tasks: the restriction queue (nres items), the coarse queue (ntasks items),
+// then the local queue (nlocal items)
+template <class T>
+int apply_tasks_run(const ApTask* tasks, int nres, int ntasks, int nlocal, int nblocks, int* ctr, int nctr,
+                    const T* MA, const double* CO, const T* MC, const int* idxA, const int* idxB, const double* r,
+                    double* zc, int nG, int nPi, int* err, const int* skip, double bytes, cudaStream_t st);
 
 // Small-matrix kernels for the GEPs live in gep.cu; launchers:
 struct FaceJob;   // defined in gep.cu

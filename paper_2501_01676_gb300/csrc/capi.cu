@@ -202,7 +202,6 @@ struct bddc_ctx {
     std::vector<long long> maoff, mcoff;
     std::vector<int> mald, mcld, np_s;
     double* SPiInv = nullptr;
-    float* SPiInv32 = nullptr;         // MIXED: FP32 copy of the FP64 coarse inverse
     // coarse problem by nested dissection (coarse_path 2): FP64 fronts and sweep operators
     bool coarse_nd = false;
     double* ndOps = nullptr;
@@ -210,11 +209,16 @@ struct bddc_ctx {
     GemvItem *ndFwd = nullptr, *ndBwd = nullptr;
     std::vector<int> ndFwdOff, ndBwdOff;     // per group: first item (last entry: total)
     std::vector<double> ndFwdBytes, ndBwdBytes;
+    // M^-1 r as one persistent launch (apply_tasks.cu)
+    ApTask* apTasks = nullptr;
+    int nApRes = 0, nApTasks = 0, nApLocal = 0, nApCtr = 0, apBlocks = 0;
+    int* apCtr = nullptr;
+    double apBytes = 0.0;
     int* gidx_pool = nullptr;
     GemvItem *itS = nullptr, *itM1 = nullptr, *itC = nullptr, *itM3 = nullptr;
     int nitS = 0, nitM1 = 0, nitC = 0, nitM3 = 0, maxcols = 0;
     // algorithmic bytes of one product: matrix stream + gathered inputs + scattered outputs
-    double bytesS = 0, bytesM1 = 0, bytesC = 0, bytesC32 = 0, bytesM3 = 0;
+    double bytesS = 0, bytesM1 = 0, bytesC = 0, bytesM3 = 0;
     // condense / recover
     void* tri = nullptr;
     int* tri_lists = nullptr;
@@ -384,10 +388,9 @@ static int change_basis(bddc_ctx* C, const std::vector<TBlock>& tb, const int* d
 // from S_Pi, the children's updates are added, the engine eliminates the own
 // unknowns of every front of that height in one launch (FP64), and the sweep
 // operators are copied out of the trailing blocks.
-static int coarse_nd_setup(bddc_ctx* C, const double* SPi) {
+static int coarse_nd_setup(bddc_ctx* C, const double* SPi, NDPlan& P) {
     cudaStream_t st = C->st;
     const int nPi = C->nPi;
-    NDPlan P;
     BDDC_TRY(nd_plan(C->hm, nPi, P));
     double* Fp = nullptr;
     BDDC_TRY(C->alloc(&Fp, (size_t)P.fpool));
@@ -467,6 +470,91 @@ static int coarse_nd_setup(bddc_ctx* C, const double* SPi) {
     C->stats.coarse_fronts = (int)P.fr.size();
     C->stats.coarse_levels = H;
     C->stats.coarse_factor_gflop = P.flops * 1e-9;
+    return BDDC_OK;
+}
+
+// Work items of M^-1 r in topological order for the one-launch apply: the local
+// part with the coarse restriction, the coarse solve (forward sweep by height,
+// backward sweep by depth, or the explicit inverse), the prolongation.
+template <class T>
+static int build_apply_tasks(bddc_ctx* C, const std::vector<GemvItem>& iM1, const std::vector<GemvItem>& iLoc,
+                             const std::vector<GemvItem>& iCt, const std::vector<GemvItem>& iM3, const NDPlan* P) {
+    std::vector<ApTask> t;
+    auto add = [&](const GemvItem& it, int kind, int w0, int t0, int w1, int t1, int s0, int s1) {
+        ApTask a;
+        a.it = it;
+        a.kind = kind;
+        a.w0 = w0;
+        a.t0 = t0;
+        a.w1 = w1;
+        a.t1 = t1;
+        a.s0 = s0;
+        a.s1 = s1;
+        t.push_back(a);
+    };
+    const int nA = (int)iM1.size();
+    for (const GemvItem& it : iM1) add(it, AP_LOCAL, -1, 0, -1, 0, AP_CTR_LOCAL, -1);
+    C->nApRes = nA;
+    int ncoarse = 0;
+    int nfr = 0;
+    if (C->nPi > 0 && P) {
+        nfr = (int)P->fr.size();
+        auto fctr = [&](int a) { return AP_CTR_FRONTS + a; };           // forward items of a's children done
+        auto bctr = [&](int a) { return AP_CTR_FRONTS + nfr + a; };     // backward items of a done
+        std::vector<int> nfw(nfr, 0), nbw(nfr, 0), nchild_fw(nfr, 0);
+        // items per front, recounted from the plan's sizes
+        auto nitems = [](int rows, int cols) {
+            return ((rows + ND_ITEM_ROWS - 1) / ND_ITEM_ROWS) * ((cols + ND_ITEM_COLS - 1) / ND_ITEM_COLS);
+        };
+        for (int a = 0; a < nfr; ++a) {
+            const NDFront& f = P->fr[a];
+            nfw[a] = (f.b > 0 && f.n > 0) ? nitems(f.b, f.n) : 0;
+            nbw[a] = f.n > 0 ? nitems(f.n, f.b + f.n) : 0;
+            if (f.parent >= 0) nchild_fw[f.parent] += nfw[a];
+        }
+        // forward items by height, front by front, in the plan's item order
+        for (size_t h = 0; h < P->by_height.size(); ++h) {
+            size_t k = 0;
+            for (int a : P->by_height[h]) {
+                const NDFront& f = P->fr[a];
+                for (int q = 0; q < nfw[a]; ++q, ++k)
+                    add(P->fwd[h][k], AP_SWEEP, AP_CTR_LOCAL, nA, nchild_fw[a] > 0 ? fctr(a) : -1, nchild_fw[a],
+                        f.parent >= 0 ? fctr(f.parent) : -1, -1);
+            }
+            if (k != P->fwd[h].size()) return BDDC_EINVAL;
+        }
+        for (size_t d = 0; d < P->by_depth.size(); ++d) {
+            size_t k = 0;
+            for (int a : P->by_depth[d]) {
+                const NDFront& f = P->fr[a];
+                for (int q = 0; q < nbw[a]; ++q, ++k) {
+                    if (f.parent < 0)
+                        add(P->bwd[d][k], AP_SWEEP, AP_CTR_LOCAL, nA, nchild_fw[a] > 0 ? fctr(a) : -1, nchild_fw[a],
+                            bctr(a), AP_CTR_COARSE);
+                    else
+                        add(P->bwd[d][k], AP_SWEEP, bctr(f.parent), nbw[f.parent], -1, 0, bctr(a), AP_CTR_COARSE);
+                    ++ncoarse;
+                }
+            }
+            if (k != P->bwd[d].size()) return BDDC_EINVAL;
+        }
+        C->apBytes = C->bytesM1 + P->bytes_solve + C->bytesM3;
+    } else if (C->nPi > 0) {
+        for (const GemvItem& it : iCt) add(it, AP_DENSE, AP_CTR_LOCAL, nA, -1, 0, AP_CTR_COARSE, -1);
+        ncoarse = (int)iCt.size();
+        C->apBytes = C->bytesM1 + C->bytesC + C->bytesM3;
+    } else {
+        C->apBytes = C->bytesM1;
+    }
+    if (C->nPi > 0)
+        for (const GemvItem& it : iM3) add(it, AP_PROLONG, AP_CTR_COARSE, ncoarse, -1, 0, -1, -1);
+    C->nApTasks = (int)t.size() - nA;
+    for (const GemvItem& it : iLoc) add(it, AP_LOCAL, -1, 0, -1, 0, -1, -1);
+    C->nApLocal = (int)t.size() - nA - C->nApTasks;
+    C->nApCtr = AP_CTR_FRONTS + 2 * nfr;
+    BDDC_TRY(C->upload(&C->apTasks, t));
+    BDDC_TRY(C->alloc(&C->apCtr, (size_t)C->nApCtr));
+    C->apBlocks = apply_tasks_blocks<T>();
     return BDDC_OK;
 }
 
@@ -1242,12 +1330,12 @@ static int setup_impl(bddc_ctx* C) {
     // (read back after the host has built the apply's work items); otherwise, or
     // when rejected, [[S_Pi, -I], [I, 0]] -> S_Pi^{-1} by the elimination engine.
     const int ldc = r4(std::max(nPi, 1));
-    BDDC_TRY(C->alloc(&C->SPiInv, (size_t)std::max(nPi, 1) * ldc));
     bool coarse_done = false;
     const bool coarse_small = nPi > 0 && nPi <= COARSE_GJ_MAX && !C->o.coarse_elim;
     double* hres = reinterpret_cast<double*>(C->hst + 3);    // pinned: max|I - S X|, ||S||, ||X||
     ktimer_begin(KT_COARSE, st);
     if (coarse_small) {
+        BDDC_TRY(C->alloc(&C->SPiInv, (size_t)std::max(nPi, 1) * ldc));
         double* work = nullptr;
         double* resid = nullptr;
         BDDC_TRY(C->alloc(&work, 2LL * nPi * nPi));
@@ -1260,7 +1348,7 @@ static int setup_impl(bddc_ctx* C) {
     }
     // gemv work items
     std::vector<int> gi;
-    std::vector<GemvItem> iS, iM1, iC, iM3;
+    std::vector<GemvItem> iS, iM1, iC, iM3, iCt, iM1loc, iM1res;
     const int nG = C->nG;
     auto split = [](std::vector<GemvItem>& v, long long moff, int rows, int cols, int ld, int io, int oo,
                     int RB = 32, int CB = 2048) {
@@ -1300,6 +1388,16 @@ static int setup_impl(bddc_ctx* C) {
         for (int q = 0; q < nps; ++q) gi.push_back(nG + idxv[rpi_off[s] + q]);
         split(iS, C->soff[s], nB, nB, C->sld[s], og, og, RBs);
         split(iM1, C->maoff[s], nB + nps, nB, C->mald[s], og, om1, RBs);
+        // the one-launch apply: local rows and coarse-restriction rows as separate items
+        for (int c0 = 0; c0 < nB; c0 += 2048) {
+            const int nc = std::min(2048, nB - c0);
+            for (int r0 = 0; r0 < nB; r0 += RBs)
+                iM1loc.push_back(GemvItem{C->maoff[s], nB + nps, nB, C->mald[s], og, om1, r0,
+                                          std::min(RBs, nB - r0), c0, nc});
+            for (int r0 = nB; r0 < nB + nps; r0 += 32)
+                iM1res.push_back(GemvItem{C->maoff[s], nB + nps, nB, C->mald[s], og, om1, r0,
+                                          std::min(32, nB + nps - r0), c0, nc});
+        }
         if (nps > 0) split(iM3, C->mcoff[s], nB, nps, C->mcld[s], orp, og, 256);
         const double ts = sizeof(T), iv = 8.0 + 4.0;   // FP64 value + int32 index per gather/scatter
         C->bytesS += ts * nB * nB + iv * 2.0 * nB;
@@ -1312,8 +1410,13 @@ static int setup_impl(bddc_ctx* C) {
         int oi = (int)gi.size();
         for (int q = 0; q < nPi; ++q) gi.push_back(q);
         if (nPi > 0) split(iC, 0, nPi, nPi, ldc, oc, oi, 32, 512);
+        // the same product inside the one-launch apply: y -> x within [y | x]
+        int ty = (int)gi.size();
+        for (int q = 0; q < nPi; ++q) gi.push_back(q);
+        int tx = (int)gi.size();
+        for (int q = 0; q < nPi; ++q) gi.push_back(nPi + q);
+        if (nPi > 0) split(iCt, 0, nPi, nPi, ldc, ty, tx, 32, 512);
         C->bytesC = 8.0 * nPi * nPi + 24.0 * nPi;
-        C->bytesC32 = 4.0 * nPi * nPi + 24.0 * nPi;
     }
     BDDC_TRY(C->upload(&C->gidx_pool, gi));
     BDDC_TRY(C->upload(&C->itS, iS));
@@ -1376,12 +1479,14 @@ static int setup_impl(bddc_ctx* C) {
         coarse_done = std::isfinite(hres[0]) && hres[0] <= target;
         C->stats.coarse_path = coarse_done ? 1 : 0;
     }
+    NDPlan ndp;
     if (nPi > 0 && !coarse_done && !C->o.coarse_elim) {
-        BDDC_TRY(coarse_nd_setup(C, SPi));
+        BDDC_TRY(coarse_nd_setup(C, SPi, ndp));
         coarse_done = true;
         C->stats.coarse_path = 2;
     }
     if (nPi > 0 && !coarse_done) {
+        if (!C->SPiInv) BDDC_TRY(C->alloc(&C->SPiInv, (size_t)std::max(nPi, 1) * ldc));
         double* Xc = nullptr;
         BDDC_TRY(C->alloc(&Xc, 4LL * nPi * nPi));
         BDDC_TRY(coarse_ext_run(SPi, Xc, nPi, st));
@@ -1393,14 +1498,7 @@ static int setup_impl(bddc_ctx* C) {
         BDDC_TRY((copy_blocks_run<double, double>(d_cj, 1, 64, st)));
     }
     ktimer_end(KT_COARSE, st, 0.0, 0.0);
-    if (nPi > 0 && C->mixed && !C->coarse_nd) {
-        // the coarse problem is solved in FP64; the mixed apply streams its inverse in FP32
-        BDDC_TRY(C->alloc(&C->SPiInv32, (size_t)std::max(nPi, 1) * ldc));
-        std::vector<CopyJob> cj2{CopyJob{C->SPiInv, ldc, 0, 0, nPi, nPi, C->SPiInv32, ldc, 1.0}};
-        CopyJob* d_cj2;
-        BDDC_TRY(C->upload(&d_cj2, cj2));
-        BDDC_TRY((copy_blocks_run<double, float>(d_cj2, 1, 64, st)));
-    }
+    BDDC_TRY(build_apply_tasks<T>(C, iM1res, iM1loc, iCt, iM3, C->coarse_nd ? &ndp : nullptr));
     C->phase_mark(6);
     return BDDC_OK;
 }
@@ -1421,6 +1519,13 @@ static int op_S(bddc_ctx* C, const double* x, double* y, const int* skip) {
 // base pointer).
 template <class T>
 static int op_M_into(bddc_ctx* C, const double* x, double* zc, double* upi, const int* skip) {
+    if (C->o.apply_launch == 0 && C->apTasks) {
+        BDDC_CUDA_TRY(cudaMemsetAsync(zc, 0, sizeof(double) * (C->nG + 2 * (size_t)C->nPi), C->st));
+        return apply_tasks_run<T>(C->apTasks, C->nApRes, C->nApTasks, C->nApLocal, C->apBlocks, C->apCtr, C->nApCtr,
+                                  (const T*)C->MA,
+                                  C->coarse_nd ? C->ndOps : C->SPiInv, (const T*)C->MC, C->gidx_pool, C->ndIdx, x,
+                                  zc, C->nG, C->nPi, C->err, skip, C->apBytes, C->st);
+    }
     BDDC_CUDA_TRY(cudaMemsetAsync(zc, 0, sizeof(double) * (C->nG + C->nPi), C->st));
     BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, zc, C->maxcols, 1, 0, 0, C->st, skip,
                          C->bytesM1));
@@ -1429,12 +1534,8 @@ static int op_M_into(bddc_ctx* C, const double* x, double* zc, double* upi, cons
             BDDC_TRY(coarse_nd_solve(C, zc + C->nG, skip));
         } else {
             BDDC_CUDA_TRY(cudaMemsetAsync(upi, 0, sizeof(double) * C->nPi, C->st));
-            if (C->mixed)
-                BDDC_TRY(gemv_run<float>(C->SPiInv32, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0,
-                                         C->st, skip, C->bytesC32));
-            else
-                BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0,
-                                          C->st, skip, C->bytesC));
+            BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, 1, 0, 0, C->st,
+                                      skip, C->bytesC));
         }
         BDDC_TRY(gemv_t_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, upi, zc, 1, 0, 0, C->st, skip,
                                C->bytesM3));
@@ -1709,6 +1810,7 @@ void bddc_default_opts(bddc_opts* o) {
     o->mlp_params = nullptr;
     o->tensor_cores = 1;
     o->coarse_elim = 0;
+    o->apply_launch = 0;
 }
 
 const char* bddc_strerror(int code) {
@@ -1846,7 +1948,7 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     C->stats.t_edge_ms = C->phase_ms(3, 4);
     C->stats.t_basis_ms = C->phase_ms(4, 5);
     C->stats.t_coarse_ms = C->phase_ms(4, 6);
-    if (herr & (ERR_TIMEOUT_ENGINE | ERR_TIMEOUT_TC)) {
+    if (herr & (ERR_TIMEOUT_ENGINE | ERR_TIMEOUT_TC | ERR_TIMEOUT_APPLY)) {
         bddc_set_last_error("a bounded device wait gave up", __FILE__, __LINE__);
         return BDDC_ETIMEOUT;
     }
@@ -1959,8 +2061,14 @@ int bddc_gmres_solve(bddc_ctx* C, const double* load, double* u, int nrhs, int m
         agg.relres = std::max(agg.relres, one.relres);
         agg.relres_global = std::max(agg.relres_global, one.relres_global);
     }
+    int herr = 0;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&herr, C->err, sizeof(int), cudaMemcpyDeviceToHost, C->st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
     agg.solve_ms = ms_since(t0);
+    if (herr & ERR_TIMEOUT_APPLY) {
+        bddc_set_last_error("a bounded wait of the preconditioner's task kernel gave up", __FILE__, __LINE__);
+        return BDDC_ETIMEOUT;
+    }
     C->stats.iters = agg.iters;
     C->stats.refine_steps = agg.refine_steps;
     C->stats.converged = agg.converged;

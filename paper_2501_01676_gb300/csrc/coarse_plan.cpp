@@ -25,6 +25,8 @@
 
 namespace {
 inline int r4(int n) { return (n + 3) & ~3; }
+// boxes holding at most this many primal unknowns are not dissected further
+constexpr int ND_LEAF_VARS = 160;
 }  // namespace
 
 int nd_plan(const HostMesh& hm, int nPi, NDPlan& P) {
@@ -81,9 +83,14 @@ int nd_plan(const HostMesh& hm, int nPi, NDPlan& P) {
         int d = 0;
         for (int q = 1; q < 3; ++q)
             if (b.hi[q] - b.lo[q] > b.hi[d] - b.lo[d]) d = q;
+        int nvars = 0;
+        for (int e : b.ents) nvars += hm.ent[e].k;
         std::vector<int> s, L, R;
-        if (b.hi[d] - b.lo[d] <= 1) {
-            s = b.ents;                      // cannot be cut further (not reached on tensor partitions)
+        if (b.hi[d] - b.lo[d] <= 1 || nvars <= ND_LEAF_VARS) {
+            // a leaf: every unknown of the box in one front (a box that cannot be
+            // cut, or one small enough that another level would cost more in the
+            // sweeps' dependency chain than its dense front costs to factor)
+            s = b.ents;
         } else {
             const int cut = b.lo[d] + (b.hi[d] - b.lo[d]) / 2;
             for (int e : b.ents) {
@@ -219,8 +226,10 @@ int nd_plan(const HostMesh& hm, int nPi, NDPlan& P) {
     }
     // solve vector: y (the right-hand side, transformed in place by the forward
     // sweep) at [0, nPi), the solution x at [nPi, 2 nPi)
+    // small items (16 rows: one pass of the GEMV's eight two-row warps; 256
+    // columns) spread each front of the sweeps' dependency chain over many CTAs
     auto split = [](std::vector<GemvItem>& v, long long moff, int rows, int cols, int ld, int io, int oo) {
-        const int RB = 32, CB = 2048;
+        const int RB = ND_ITEM_ROWS, CB = ND_ITEM_COLS;
         for (int c0 = 0; c0 < cols; c0 += CB)
             for (int r0 = 0; r0 < rows; r0 += RB)
                 v.push_back(GemvItem{moff, rows, cols, ld, io, oo, r0, std::min(RB, rows - r0), c0,
