@@ -57,6 +57,11 @@ extern "C" {
 
 #define BDDC_EDGE_NONE 0
 #define BDDC_EDGE_NEW  1    /* edge GEP on prior-selected primal constraints      */
+#define BDDC_EDGE_OLD  2    /* conventional edge GEP (Sect. 3, eq. equ-4-8-E):
+                               B_E v = lambda B~_E v with B_E = sum_i sum_{k != i}
+                               D^(k)T B_E^(i) D^(k) and B~_E the parallel sum of the
+                               Schur complements of B^(k) onto E; the comparison
+                               method of the paper's ABDDC-OLD columns            */
 
 /* Box [lo, hi]^3; the unit cube when both are zero. */
 typedef struct { double lo[3], hi[3]; } bddc_mesh;
@@ -92,7 +97,7 @@ typedef struct {
     int restart;           /* GMRES restart length, 0: no restart                 */
     int max_iter;          /* iteration cap (Sect. 4: 300)                        */
     double rtol;           /* relative residual target (Sect. 4: 1e-8)            */
-    int edge_gep;          /* BDDC_EDGE_NONE or BDDC_EDGE_NEW                      */
+    int edge_gep;          /* BDDC_EDGE_NONE, BDDC_EDGE_NEW or BDDC_EDGE_OLD       */
     int face_gep;          /* 1: adaptive face constraints, 0: none               */
     int all_primal;        /* 1: every interface dof primal (exact solver check)   */
     double inner_rtol;     /* MIXED: inner GMRES tolerance per refinement step     */
@@ -168,10 +173,12 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs,
 int bddc_apply(bddc_ctx* ctx, const double* r_dev, double* z_dev, int nrhs);
 
 /* z = M^-1 r exactly as bddc_apply, for callers that cannot allocate device
- * memory where they apply the preconditioner (code capturing its own CUDA
- * graph, where allocation calls are not allowed, or a host framework that
- * owns all device memory).  The paper has no counterpart; it is a property
- * of this library only.  The call allocates nothing: its work vectors
+ * memory where they apply the preconditioner (a host framework that owns all
+ * device memory and forbids libraries from allocating behind its back, or
+ * code where an allocation call could synchronise the device).  The paper has
+ * no counterpart; it is a property of this library only.  The context's
+ * device must be the current device (BDDC_EINVAL otherwise).  The call
+ * allocates nothing: its work vectors
  * (n_gamma + 2 * n_pi doubles) live in one file-scope device array of
  * 2^20 doubles (8 MiB) that every GPU loading the library holds until the
  * process exits; larger problems are rejected with BDDC_EINVAL.  The first
@@ -240,7 +247,8 @@ int bddc_get_schur(const bddc_ctx* ctx, int s, double* out, int* n_b);
  * the entity's dof ids (dofs[n]), its primal count k and, for faces and
  * edges, the orthonormal constraint basis Q (n x k, column-major) and the
  * GEP eigenvalues lambda (ascending sigma order reversed: largest first,
- * +inf for infinite, up to n values; count in *n_eig).  NULL outputs are
+ * +inf for infinite; up to n values for faces and conventional edge GEPs,
+ * (|n(E)| - 1) n for the new edge GEP; count in *n_eig).  NULL outputs are
  * skipped.  *n returns the entity size. */
 int bddc_get_entity_count(const bddc_ctx* ctx, int kind);
 int bddc_get_entity(const bddc_ctx* ctx, int kind, int index, int* subs,

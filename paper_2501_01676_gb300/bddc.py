@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libbddc.so")
 OK, NOT_CONVERGED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 PREC_FP64, PREC_MIXED, PREC_BF16 = 0, 1, 2
-EDGE_NONE, EDGE_NEW = 0, 1
+EDGE_NONE, EDGE_NEW, EDGE_OLD = 0, 1, 2
 
 
 class Mesh(ct.Structure):

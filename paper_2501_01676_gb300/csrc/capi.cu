@@ -123,6 +123,7 @@ struct bddc_ctx {
     bddc_opts o;
     cudaStream_t st = nullptr;
     cudaStream_t own = nullptr;   // created when the caller passes the legacy default stream
+    int device = 0;               // the CUDA device current at setup (owns st and all buffers)
     bool mixed = false;
     std::vector<void*> allocs;
     size_t bytes = 0;
@@ -883,7 +884,12 @@ static int setup_impl(bddc_ctx* C) {
     for (int e : faces) hm.ent[e].k = C->kk[e];
     C->phase_mark(3);
     // ---- 4. edges --------------------------------------------------------------
-    const int edge_mode = C->o.all_primal ? 1 : (C->o.edge_gep == BDDC_EDGE_NEW ? 0 : 2);
+    // edge kernel modes: 0 edge GEP on prior-selected primal constraints, 1 all
+    // primal, 2 no edge constraints, 3 conventional edge GEP
+    const int edge_mode = C->o.all_primal ? 1
+                          : C->o.edge_gep == BDDC_EDGE_NEW ? 0
+                          : C->o.edge_gep == BDDC_EDGE_OLD ? 3 : 2;
+    const bool edge_schur = edge_mode == 0 || edge_mode == 3;   // per-(edge, subdomain) Schur complements
     std::vector<int>& edges = hm.by_kind[1];
     // edge features (always) and the learned skip decision
     C->edge_skipped.assign(edges.size(), 0);
@@ -962,7 +968,7 @@ static int setup_impl(bddc_ctx* C) {
         T* W = nullptr;
         double* W64 = nullptr;
         std::vector<long long> woff(nsd, 0), w64off(nsd, 0);
-        if (edge_mode == 0) {
+        if (edge_schur) {
             long long wtot = 0, w64tot = 0;
             for (int s = 0; s < nsd; ++s) {
                 int nB = hm.sub[s].nB;
@@ -1062,7 +1068,7 @@ static int setup_impl(bddc_ctx* C) {
         std::vector<std::vector<long long>> ito(edges.size());
         std::vector<int> nH(edges.size(), 0);
         T* EB = nullptr;
-        if (edge_mode == 0) {
+        if (edge_schur) {
             long long etot = 0;
             for (size_t ei = 0; ei < edges.size(); ++ei)
                 if (!C->edge_skipped[ei])
@@ -1161,7 +1167,7 @@ static int setup_impl(bddc_ctx* C) {
                 J.ldS[a] = C->sld[s];
                 J.pos[a] = d_pos + pos_off[e][a];
                 J.DQ[a] = C->DQ[e][a];
-                if (J.mode == 0) {
+                if (J.mode == 0 || J.mode == 3) {
                     J.Bt[a] = EB + ito[ei][a];
                     J.ldBt[a] = itn[ei][a];
                     J.h[a] = hsz[ei][a];
@@ -1768,6 +1774,8 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
     return conv ? BDDC_OK : BDDC_NOT_CONVERGED;
 }
 
+int bddc_ctx_device(const bddc_ctx* C) { return C ? C->device : -1; }
+
 int bddc_apply_into(bddc_ctx* C, const double* r, double* z, int nrhs, double* work, size_t work_doubles) {
     if (!C || !r || !z || nrhs < 1 || !work) return BDDC_EINVAL;
     const size_t need = (size_t)C->nG + 2 * (size_t)C->nPi;
@@ -1970,6 +1978,7 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs, const bddc_part
     int prc = keep_pool_memory();
     if (prc != BDDC_OK) return prc;
     bddc_ctx* C = new bddc_ctx();
+    C->device = dev;
     if (opts) C->o = *opts;
     else bddc_default_opts(&C->o);
     if (tol_eig > 0) C->o.theta_E = tol_eig;

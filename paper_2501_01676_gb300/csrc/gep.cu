@@ -1081,7 +1081,69 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
     int k = 0;
     for (int q = threadIdx.x; q < nn; q += GT) Qo[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
     bar();
-    if (J.mode == 0) {
+    if (J.mode == 3) {
+        // conventional edge GEP (Sect. 3, eq. equ-4-8-E):
+        //   B_E = sum_i sum_{k != i} D^(k)T B_E^(i) D^(k),  B~_E = B~_E^(1) : ... : B~_E^(m),
+        // B~_E^(k) the Schur complement of B^(k) onto E alone: the [E, H_k] complement
+        // with H_k eliminated in turn (symmetric pivoting; B^(k)_HH is definite).
+        T* BEo = BB;                   // n x n
+        T* P = ME;                     // running parallel sum, n x n
+        T* At = Cm;                    // n x n
+        for (int q = threadIdx.x; q < nn; q += GT) BEo[q] = 0.0;
+        bar();
+        for (int i = 0; i < m; ++i)
+            for (int t = 0; t < m; ++t) {
+                if (t == i) continue;
+                mm(BE + i * nn, n, false, Dall + t * n, mn, false, W1, n, n, n, n, (T)1, (T)0);
+                mm(Dall + t * n, mn, true, W1, n, false, BEo, n, n, n, n, (T)1, (T)1);
+            }
+        symmetrize(BEo, n, n);
+        const int n2 = 2 * n;
+        for (int t = 0; t < m; ++t) {
+            const int g = n + J.h[t];
+            copy_mat((const T*)J.Bt[t], J.ldBt[t], T1, g, g, g);
+            symmetrize(T1, g, g);
+            pinv_schur_tail(T1, g, g, n, done);
+            copy_mat(T1, g, t == 0 ? P : At, n, n, n);
+            if (t == 0) {
+                symmetrize(P, n, n);
+                continue;
+            }
+            // P : A = P - P (P + A)^+ P: eliminate the tail of [[P, P], [P, P + A]]
+            CTA_FOR_2D(a, b, n2, n2) {
+                const int ra = a < n ? a : a - n, rb = b < n ? b : b - n;
+                T v = P[ra * n + rb];
+                if (a >= n && b >= n) v += At[ra * n + rb];
+                Bt[a * n2 + b] = v;
+            }
+            bar();
+            pinv_schur_tail(Bt, n2, n2, n, done);
+            copy_mat(Bt, n2, P, n, n, n);
+            symmetrize(P, n, n);
+        }
+        const int npn = (n + 1) & ~1;
+        const T sth = (T)(J.theta / (1.0 + J.theta) - Tol<T>::slack);
+        int r = sigma_pencil(BEo, P, n, Ash, Vsh, npn, npn + 1, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1,
+                             sth);
+        __shared__ int nsel_o;
+        if (threadIdx.x == 0) {
+            int c = 0;
+            for (int q = 0; q < r; ++q) {
+                T sg = aux[q];
+                J.lambda[q] = (1.0 - (double)sg <= Tol<T>::slack) ? INFINITY : (double)sg / (1.0 - (double)sg);
+                if (sg >= sth) ++c;
+            }
+            for (int q = r; q < nw; ++q) J.lambda[q] = NAN;
+            *J.neig = r;
+            nsel_o = c;
+        }
+        bar();
+        const int so = nsel_o;
+        if (so > 0) {
+            mm(BEo, n, false, V, r, false, Cm, so, n, so, n, (T)1, (T)0);     // B_E V(:, 0..so)
+            k = qr_basis(Cm, n, so, Qo, vb, aux + nw, aux + nw + (m - 1) * nw);
+        }
+    } else if (J.mode == 0) {
         const T sth = (T)(J.theta / (1.0 + J.theta) - Tol<T>::slack);
         int r = sigma_pencil(ME, BB, nw, Ash, Vsh, np, ldj, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1, sth);
         __shared__ int nsel_s;

@@ -30,7 +30,8 @@ struct EdgeJob {
     int n;                    // edge dofs n_E
     int m;                    // subdomains sharing the edge
     int nH;                   // prior primal unknowns (union, shared ones identified)
-    int mode;                 // 0 GEP, 1 all primal, 2 no edge constraints
+    int mode;                 // 0 GEP on prior-selected primal constraints, 1 all primal,
+                              // 2 no edge constraints, 3 conventional edge GEP
     double theta;             // Theta_E
     const double* S[EDGE_MAX_SUBS];    // packed S^(k) in sorted n(E) order
     int ldS[EDGE_MAX_SUBS];
@@ -42,7 +43,7 @@ struct EdgeJob {
     void* work;
     double* Q;                // out: n x n
     double* DQ[EDGE_MAX_SUBS];// out: D^(k) Q
-    double* lambda;           // out: (m-1) n eigenvalues
+    double* lambda;           // out: (m-1) n eigenvalues (mode 3: n), NaN padded
     double* BBout;            // out: B~~_E ((m-1) n square) for parity checks
     int* neig;
     int* k;

@@ -117,6 +117,33 @@ def test_face_and_edge_constraints(name, theta_E):
     assert st['pnumF'] == o.pnumF and st['pnumE'] == o.pnumE and st['n_pi'] == o.nPi
 
 
+@pytest.mark.parametrize("name", ['r333m3', 'r222m3', 'uneven'])
+def test_conventional_edge_gep(name):
+    """The conventional edge GEP (Sect. 3, eq. equ-4-8-E) on the GPU against the
+    oracle's: eigenvalues, constraint counts and spans, the coarse size and the
+    preconditioner; and the new edge GEP selects no more edge primals."""
+    import torch
+    o = oracle_for(name, edge_gep='old')
+    s = solver(o.prob, edge_gep=2)
+    assert o.pnumE > 0
+    for g, i, e in _match_entities(s, o, 1, 'E'):
+        ref = o.edge_info[i]
+        lam_o, lam_g = ref['lam'], g['lam']
+        assert len(lam_g) == len(lam_o)
+        fin = np.isfinite(lam_o)
+        assert np.array_equal(fin, np.isfinite(lam_g))
+        np.testing.assert_allclose(lam_g[fin], lam_o[fin], rtol=1e-8, atol=1e-12)
+        assert g['k'] == o.Q[i].shape[1]
+        _span_equal(g['Q'], o.Q[i])
+    st = s.stats()
+    assert st['pnumF'] == o.pnumF and st['pnumE'] == o.pnumE and st['n_pi'] == o.nPi
+    r = np.random.default_rng(6).standard_normal(o.nG)
+    z = s.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert rel(z, o.apply_M(r)) < 1e-9
+    new = solver(o.prob).stats()
+    assert new['pnumE'] <= st['pnumE'] and new['pnumF'] == st['pnumF']
+
+
 @pytest.mark.parametrize("name,theta_E", [('r333m3', 1.5), ('uneven', 10.0), ('c1', 10.0)])
 def test_preconditioner_apply(name, theta_E):
     import torch
