@@ -118,6 +118,9 @@ typedef struct {
                               restriction, coarse solve and prolongation as work
                               items with completion counters); 1: one launch per
                               phase (the reference path of the tests)              */
+    int cond_est;          /* 1: estimate the condition number of the preconditioned
+                              operator from every GMRES cycle's Hessenberg
+                              (stats.kappa_est); 0: skip                           */
 } bddc_opts;
 
 typedef struct {
@@ -146,6 +149,10 @@ typedef struct {
     int coarse_fronts;       /* path 2: dense fronts (separators) of the tree       */
     int coarse_levels;       /* path 2: height of the tree (sweep launches per side) */
     double coarse_factor_gflop; /* path 2: flops of the front eliminations / 1e9    */
+    double kappa_est;        /* largest sigma_max / sigma_min of the Hessenberg over
+                                the last solve's GMRES cycles of at most 128
+                                iterations: an estimate of the condition number
+                                of S M^-1 (0: not computed)                       */
 } bddc_stats;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -154,7 +161,7 @@ typedef struct bddc_ctx bddc_ctx;
  * tau = 0.7, FP64, no restart, 300 iterations, rtol 1e-8, new edge GEP,
  * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip, tensor-core
  * trailing updates in the MIXED path (tensor_cores 1), coarse_elim 0,
- * apply_launch 0. */
+ * apply_launch 0, cond_est 1. */
 void bddc_default_opts(bddc_opts* o);
 
 /* Setup (call stack: assembly, batched Dirichlet factorisation + Schur

@@ -40,7 +40,7 @@ class Opts(ct.Structure):
                 ("rtol", ct.c_double), ("edge_gep", ct.c_int), ("face_gep", ct.c_int),
                 ("all_primal", ct.c_int), ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
                 ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p), ("tensor_cores", ct.c_int),
-                ("coarse_elim", ct.c_int), ("apply_launch", ct.c_int)]
+                ("coarse_elim", ct.c_int), ("apply_launch", ct.c_int), ("cond_est", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -52,7 +52,7 @@ class Stats(ct.Structure):
                 ("t_face_ms", ct.c_double), ("t_edge_ms", ct.c_double), ("t_coarse_ms", ct.c_double),
                 ("jacobi_sweeps_max", ct.c_int), ("t_mesh_ms", ct.c_double), ("t_basis_ms", ct.c_double),
                 ("coarse_path", ct.c_int), ("coarse_fronts", ct.c_int), ("coarse_levels", ct.c_int),
-                ("coarse_factor_gflop", ct.c_double)]
+                ("coarse_factor_gflop", ct.c_double), ("kappa_est", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

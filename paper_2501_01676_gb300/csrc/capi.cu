@@ -243,6 +243,7 @@ struct bddc_ctx {
     int graph_iters = 0;
     unsigned long long graph_kernels = 0;
     int* err = nullptr;
+    double* kmax = nullptr;     // largest condition estimate of the solve's GMRES cycles
     double* scal = nullptr;     // pinned host scratch
     // setup phase boundaries on the stream (GPU timeline; read once at the end)
     cudaEvent_t phase_ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -1698,6 +1699,7 @@ static int gmres(bddc_ctx* C, const double* b, double* x, double rtol, int max_i
         }
         total = C->hst->total;
         if (C->hst->j > 0) {
+            if (C->o.cond_est) BDDC_TRY(gm_cond(C->gst, C->H, C->gm_m, C->kmax, st));
             BDDC_TRY(gm_finish(C->V, n, C->gst, C->H, C->gv, C->yy, C->t, n, st));
             BDDC_TRY(op_M<T>(C, C->t, nullptr));
             BDDC_TRY(vec_axpby(x, C->zc, 1.0, 1.0, n, st));
@@ -1819,6 +1821,7 @@ void bddc_default_opts(bddc_opts* o) {
     o->tensor_cores = 1;
     o->coarse_elim = 0;
     o->apply_launch = 0;
+    o->cond_est = 1;
 }
 
 const char* bddc_strerror(int code) {
@@ -1944,6 +1947,7 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     BDDC_TRY(C->alloc(&C->yy, m + 1));
     BDDC_TRY(C->alloc(&C->partial, (size_t)(m + 9) * (gm_nchunk(std::max(nG, ndof)) + 1)));
     BDDC_TRY(C->alloc(&C->gst, 2));
+    BDDC_TRY(C->alloc(&C->kmax, 1));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->gst, 0, 2 * sizeof(GmState), C->st));
     int herr2[2] = {0, 0};
     BDDC_CUDA_TRY(cudaMemcpyAsync(herr2, C->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, C->st));
@@ -2047,6 +2051,7 @@ int bddc_gmres_solve(bddc_ctx* C, const double* load, double* u, int nrhs, int m
     agg.relres = 0;
     agg.relres_global = 0;
     agg.refine_steps = 0;
+    BDDC_CUDA_TRY(cudaMemsetAsync(C->kmax, 0, sizeof(double), C->st));
     for (int c = 0; c < nrhs; ++c) {
         const double* Fd = C->F;
         if (load) {
@@ -2071,8 +2076,11 @@ int bddc_gmres_solve(bddc_ctx* C, const double* load, double* u, int nrhs, int m
         agg.relres_global = std::max(agg.relres_global, one.relres_global);
     }
     int herr = 0;
+    double hk = 0.0;
     BDDC_CUDA_TRY(cudaMemcpyAsync(&herr, C->err, sizeof(int), cudaMemcpyDeviceToHost, C->st));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(&hk, C->kmax, sizeof(double), cudaMemcpyDeviceToHost, C->st));
     BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    C->stats.kappa_est = C->o.cond_est ? hk : 0.0;
     agg.solve_ms = ms_since(t0);
     if (herr & ERR_TIMEOUT_APPLY) {
         bddc_set_last_error("a bounded wait of the preconditioner's task kernel gave up", __FILE__, __LINE__);

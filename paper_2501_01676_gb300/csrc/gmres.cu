@@ -9,6 +9,8 @@
 // flag is set.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "bddc_internal.h"
 #include "gmres.h"
 
@@ -262,6 +264,92 @@ __global__ void k_backsolve(const GmState* __restrict__ S, const double* __restr
     }
 }
 
+// Condition estimate of the preconditioned operator from the cycle's
+// Hessenberg: after the Givens rotations its leading k x k block is the
+// triangular R, whose singular values are those of the (k+1) x k Hessenberg;
+// sigma_max by power iteration on R^T R, sigma_min by inverse iteration
+// (R^T z = x, R x' = z, column-oriented substitutions); kmax = max(kmax, ratio).
+// R is staged in shared memory (cycles of up to GM_COND_MAX columns; longer
+// cycles are not estimated) and two warps run the substitutions.
+constexpr int GM_COND_MAX = 128;
+constexpr int GM_COND_ITERS = 16;
+constexpr int GM_COND_THREADS = 64;
+__global__ void __launch_bounds__(GM_COND_THREADS) k_cond(const GmState* __restrict__ S,
+                                                          const double* __restrict__ H,
+                                                          double* __restrict__ kmax) {
+    extern __shared__ double Rs[];                  // k x k, row-major
+    __shared__ double x[GM_COND_MAX], z[GM_COND_MAX], red[GM_COND_THREADS / 32];
+    const int k = S->j, m = S->m, t = threadIdx.x;
+    if (k <= 0 || k > GM_COND_MAX) return;
+    for (int q = t; q < k * k; q += GM_COND_THREADS) {
+        const int i = q / k, l = q - i * k;
+        Rs[q] = l >= i ? H[(long long)l * (m + 1) + i] : 0.0;
+    }
+    __syncthreads();
+    auto norm = [&](const double* v) {
+        double a = 0.0;
+        for (int i = t; i < k; i += GM_COND_THREADS) a += v[i] * v[i];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if ((t & 31) == 0) red[t >> 5] = a;
+        __syncthreads();
+        double s2 = 0.0;
+        for (int w = 0; w < GM_COND_THREADS / 32; ++w) s2 += red[w];
+        __syncthreads();
+        return sqrt(s2);
+    };
+    // sigma_max: x <- R^T R x
+    for (int i = t; i < k; i += GM_COND_THREADS) x[i] = 1.0 + 1e-3 * i;
+    __syncthreads();
+    double smax = 0.0;
+    for (int it = 0; it < GM_COND_ITERS; ++it) {
+        const double nx = norm(x);
+        for (int i = t; i < k; i += GM_COND_THREADS) x[i] /= nx;
+        __syncthreads();
+        for (int i = t; i < k; i += GM_COND_THREADS) {       // z = R x
+            double a = 0.0;
+            for (int l = i; l < k; ++l) a += Rs[i * k + l] * x[l];
+            z[i] = a;
+        }
+        __syncthreads();
+        smax = norm(z);
+        for (int i = t; i < k; i += GM_COND_THREADS) {       // x = R^T z
+            double a = 0.0;
+            for (int l = 0; l <= i; ++l) a += Rs[l * k + i] * z[l];
+            x[i] = a;
+        }
+        __syncthreads();
+    }
+    // sigma_min: x <- (R^T R)^{-1} x
+    for (int i = t; i < k; i += GM_COND_THREADS) x[i] = 1.0 - 1e-3 * i;
+    __syncthreads();
+    double smin = 0.0;
+    for (int it = 0; it < GM_COND_ITERS; ++it) {
+        const double nx = norm(x);
+        for (int i = t; i < k; i += GM_COND_THREADS) x[i] /= nx;
+        __syncthreads();
+        for (int i = 0; i < k; ++i) {                       // R^T z = x (forward)
+            const double d = Rs[i * k + i];
+            const double zi = d != 0.0 ? x[i] / d : 0.0;
+            if (t == 0) z[i] = zi;
+            for (int r = i + 1 + t; r < k; r += GM_COND_THREADS) x[r] -= Rs[i * k + r] * zi;
+            __syncthreads();
+        }
+        for (int i = k - 1; i >= 0; --i) {                  // R x = z (backward)
+            const double d = Rs[i * k + i];
+            const double xi = d != 0.0 ? z[i] / d : 0.0;
+            if (t == 0) x[i] = xi;
+            for (int r = t; r < i; r += GM_COND_THREADS) z[r] -= Rs[r * k + i] * xi;
+            __syncthreads();
+        }
+        const double g = norm(x);                           // ||(R^T R)^{-1} x|| -> 1 / sigma_min^2
+        smin = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+    }
+    if (t == 0) {
+        const double kap = smin > 0.0 ? smax / smin : INFINITY;
+        if (!(kap <= *kmax)) *kmax = kap;
+    }
+}
+
 __global__ void k_combine(const double* __restrict__ V, long long ldv, const double* __restrict__ y,
                           const GmState* __restrict__ S, double* __restrict__ t, long long n) {
     const int k = S->j;
@@ -411,6 +499,17 @@ int gm_finish(const double* V, long long ldv, const GmState* S, const double* H,
 
 int vec_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st) {
     k_axpby<<<grid_for(n), 256, 0, st>>>(y, x, a, b, n);
+    bddc_note_launches(1);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
+int gm_cond(const GmState* S, const double* H, int mmax, double* kmax, cudaStream_t st) {
+    const int kk = std::min(mmax, GM_COND_MAX);
+    const size_t smem = sizeof(double) * kk * kk;
+    BDDC_CUDA_TRY(cudaFuncSetAttribute(k_cond, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * GM_COND_MAX * GM_COND_MAX)));
+    k_cond<<<1, GM_COND_THREADS, smem, st>>>(S, H, kmax);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;

@@ -39,3 +39,8 @@ int gm_cycle_start(const double* r, long long n, GmState* S, double* gv, double*
 int gm_finish(const double* V, long long ldv, const GmState* S, const double* H, const double* gv,
               double* y, double* t, long long n, cudaStream_t st);
 int vec_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st);
+// Condition estimate sigma_max / sigma_min of the cycle's Hessenberg (the
+// triangular factor left by the Givens rotations); *kmax = max(*kmax, estimate).
+// mmax: the cycle length the Hessenberg was allocated for; cycles longer than
+// 128 columns are not estimated.
+int gm_cond(const GmState* S, const double* H, int mmax, double* kmax, cudaStream_t st);

@@ -133,6 +133,20 @@ def config3(seed_offset=3):
     return Problem('c3_8x8x8_m8_jumps', slabs, nu_sub[sub], beta, np.ones(X.size))
 
 
+def config3_layers(layers=2, seed_offset=3):
+    """The first `layers` of the 8 subdomain layers (in z) of the 8x8x8 jump
+    workload as a problem of its own on the unit cube: the same per-subdomain
+    nu and H/h, 64 * layers subdomains.  A bounded timing sample of that
+    workload (same per-subdomain work)."""
+    rng = np.random.default_rng(20250103 + seed_offset)
+    nu_all = 10.0 ** rng.uniform(-4.0, 0.0, size=512)
+    slabs = [[8] * 8, [8] * 8, [8] * layers]
+    ne, h, X, Y, Z = _grid(slabs)
+    sub = _elem_subdomain(slabs)
+    beta = np.stack([-(Y - 0.5), X - 0.5, np.full_like(X, 0.1)], axis=1)
+    return Problem(f'c3_layers_{layers}', slabs, nu_all[:64 * layers][sub], beta, np.ones(X.size))
+
+
 def config4(seed_offset=4, nrhs=64):
     """6x6x6 subdomains, per-slab H/h ~ U{6..10}, nu=1e-2, beta=(1,1,0), nrhs N(0,1) loads."""
     rng = np.random.default_rng(20250103 + seed_offset)

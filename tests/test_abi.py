@@ -61,3 +61,39 @@ def test_precision_modes_match_the_header():
                       "BDDC_PREC_BF16": bddc.PREC_BF16}
     o = bddc.default_opts()
     assert o.precision == bddc.PREC_FP64 and o.tensor_cores == 1 and o.coarse_elim == 0
+
+
+def _struct_fields(txt, name):
+    """Field names, in order, of `typedef struct { ... } name;` in the header."""
+    body = re.search(r"typedef struct \{((?:(?!typedef).)*?)\}\s*" + name + r";", txt, flags=re.S).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        decl = re.sub(r"\[[^\]]*\]", "", decl)              # array extents
+        for part in decl.split(","):
+            tok = re.findall(r"[A-Za-z_]\w*", part)
+            if tok:
+                names.append(tok[-1])
+    return names
+
+
+@pytest.mark.parametrize("cname,pyname", [("bddc_opts", "Opts"), ("bddc_stats", "Stats"),
+                                          ("bddc_coeffs", "Coeffs")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes structures list the header's fields in the header's order."""
+    from paper_2501_01676_gb300 import bddc
+    txt = open(os.path.join(ROOT, "include", "bddc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    assert [f for f, _ in getattr(bddc, pyname)._fields_] == _struct_fields(txt, cname)
+
+
+def test_edge_modes_and_new_option_defaults():
+    from paper_2501_01676_gb300 import bddc
+    txt = open(os.path.join(ROOT, "include", "bddc.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (BDDC_EDGE_\w+)\s+(\d+)", txt)}
+    assert consts == {"BDDC_EDGE_NONE": bddc.EDGE_NONE, "BDDC_EDGE_NEW": bddc.EDGE_NEW,
+                      "BDDC_EDGE_OLD": bddc.EDGE_OLD}
+    o = bddc.default_opts()
+    assert o.edge_gep == bddc.EDGE_NEW and o.apply_launch == 0 and o.cond_est == 1

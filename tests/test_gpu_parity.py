@@ -223,3 +223,19 @@ def test_config2_full_size():
     assert stm['relres'] <= 1e-8 and stm['converged']
     errm = np.linalg.norm(um.cpu().numpy() - ustar) / np.linalg.norm(ustar)
     assert errm < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_condition_estimate_bounded_by_the_operator(precision):
+    """kappa_est from the GMRES Hessenberg: the singular values of the Arnoldi
+    Hessenberg lie inside those of S M^-1 (right preconditioning), so the
+    estimate never exceeds kappa(S M^-1) of the oracle's dense operators; with
+    GMRES run to 1e-12 the Krylov space reaches the extremes and the estimate is
+    within a factor 2 of it."""
+    o = oracle_for('r222m3')
+    s = solver(o.prob, rtol=1e-12, precision=precision)
+    u, st = s.solve()
+    sv = np.linalg.svd(o.S_dense() @ o.M_dense(), compute_uv=False)
+    kt = sv[0] / sv[-1]
+    assert 1.0 <= st['kappa_est'] <= kt * (1 + 1e-4)
+    assert st['kappa_est'] >= 0.5 * kt
