@@ -273,16 +273,17 @@ int bddc_get_entity(const bddc_ctx* ctx, int kind, int index, int* subs,
  *   0-2 min / max / mean log10 nu over touching elements,
  *   3   max - min over n(E) of the per-subdomain mean log10 nu,
  *   4-6 mean |beta_a|, max |beta_a|, mean |beta| over the edge nodes,
- *   7   edge length (n_E + 1) h_a, 8 (H/h)/10, 9 log10(h_a * f6 / (2 * 10^f2)).
- * Network: 10 -> 64 -> 64 -> 64 (ReLU) -> 8 logits (class = min(k_E, 7)),
+ *   7   edge length (n_E + 1) h_a, 8 (H/h)/10, 9 log10(h_a * f6 / (2 * 10^f2)),
+ *   10  log10(Theta_E) (the GEP's selection threshold).
+ * Network: 11 -> 64 -> 64 -> 64 (ReLU) -> 8 logits (class = min(k_E, 7)),
  * loss = mean softmax cross-entropy.  Parameters are one FP32 array:
- * W1[10][64], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64][8],
+ * W1[11][64], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64][8],
  * b4[8] (row-major, input index first). */
 
-#define BDDC_MLP_FEATURES 10
+#define BDDC_MLP_FEATURES 11
 #define BDDC_MLP_HIDDEN   64
 #define BDDC_MLP_CLASSES  8
-#define BDDC_MLP_PARAMS   9544
+#define BDDC_MLP_PARAMS   9608
 
 /* Edge features of the context (n_edges x BDDC_MLP_FEATURES, FP32 host) and
  * the edge GEP's constraint counts (n_edges ints, -1 where it was skipped),

@@ -15,9 +15,10 @@ contain the closed edge segment:
   7 edge length (n_E + 1) h_a
   8 H/h / 10 (largest slab element count over n(E), scaled)
   9 log10 of the Peclet number h_a * feature6 / (2 * 10^feature2)
-Network: x (10) -> relu(W1 x + b1) (64) -> relu (64) -> relu (64) -> W4 h + b4
+  10 log10 Theta_E (the threshold the edge GEP selects with)
+Network: x (11) -> relu(W1 x + b1) (64) -> relu (64) -> relu (64) -> W4 h + b4
 (8 logits, class c = min(k_E, 7)); loss = mean softmax cross-entropy.
-Flat parameter layout: W1 [10][64], b1, W2 [64][64], b2, W3 [64][64], b3,
+Flat parameter layout: W1 [11][64], b1, W2 [64][64], b2, W3 [64][64], b3,
 W4 [64][8], b4 (row-major, input index first).
 """
 from __future__ import annotations
@@ -26,7 +27,7 @@ import math
 
 import numpy as np
 
-NF, NH, NC = 10, 64, 8
+NF, NH, NC = 11, 64, 8
 SHAPES = [(NF, NH), (NH,), (NH, NH), (NH,), (NH, NH), (NH,), (NH, NC), (NC,)]
 NPARAM = sum(int(np.prod(s)) for s in SHAPES)
 
@@ -98,7 +99,7 @@ def loss_grad(theta, X, y):
     return loss, g
 
 
-def edge_features(mesh, nu_elem, beta_node):
+def edge_features(mesh, nu_elem, beta_node, theta_E=10.0):
     """Feature rows for the mesh's edges in the mesh's edge order."""
     logn = np.log10(np.asarray(nu_elem, dtype=float))
     beta = np.asarray(beta_node, dtype=float)
@@ -133,6 +134,6 @@ def edge_features(mesh, nu_elem, beta_node):
         h = mesh.h[a]
         f = [ln.min(), ln.max(), ln.mean(), max(means) - min(means), bt.mean(), bt.max(), bn.mean(),
              (len(e['dofs']) + 1) * h, m / 10.0,
-             math.log10(max(h * bn.mean() / (2.0 * 10.0 ** ln.mean()), 1e-30))]
+             math.log10(max(h * bn.mean() / (2.0 * 10.0 ** ln.mean()), 1e-30)), math.log10(theta_E)]
         rows.append(f)
     return np.array(rows)

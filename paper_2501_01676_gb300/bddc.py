@@ -114,7 +114,7 @@ def tc_selftest(A, B, C, nr=128, nc=128, K=32):
     check(lib().bddc_tc_selftest(_fptr(A), _fptr(B), _fptr(Cc), nr, nc, K), "bddc_tc_selftest")
     return Cc
 
-MLP_FEATURES, MLP_CLASSES, MLP_PARAMS = 10, 8, 9544
+MLP_FEATURES, MLP_CLASSES, MLP_PARAMS = 11, 8, 9608
 MLP_PARAMS_FILE = os.path.join(HERE, "edge_mlp_params.npy")
 
 

@@ -931,6 +931,7 @@ static int setup_impl(bddc_ctx* C) {
             D.c0 = a0[f0];
             D.c1 = a0[f1];
             D.m = 0;
+            D.theta = E.theta;
             for (int q = 0; q < 4; ++q) {
                 D.subs[q] = q < (int)E.subs.size() ? E.subs[q] : -1;
                 if (q < (int)E.subs.size()) D.m = std::max(D.m, hm.sub[E.subs[q]].max_slab);

@@ -133,6 +133,7 @@ __global__ void k_edge_features(const EdgeDesc* __restrict__ ed, int nedges, con
         f[7] = (float)((nE + 1) * h);
         f[8] = (float)(D.m / 10.0);
         f[9] = (float)log10(fmax(h * bnm / (2.0 * pow(10.0, mean)), 1e-30));
+        f[10] = (float)log10(D.theta);
     }
 }
 

@@ -10,6 +10,7 @@ struct EdgeDesc {
     int c0, c1;        // node coordinates in the two other directions (increasing axis order)
     int subs[4];       // subdomains sharing the edge (-1 padded)
     int m;             // largest slab element count over the subdomains
+    double theta;      // Theta_E of the edge GEP
 };
 
 int mlp_edge_features(const EdgeDesc* ed, int nedges, const double* nu, const double* beta, const double bconst[3],

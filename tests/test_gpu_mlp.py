@@ -20,16 +20,16 @@ def B():
     return bddc
 
 
-@pytest.mark.parametrize("prob", [
-    lambda: W.random_small(4, (3, 3, 3), 3, (-3, 3)),
-    lambda: W.config5(seed_offset=77, nsub=3, m=4),
-    lambda: W.uniform(2, 2, nu=0.3, beta=(0.2, -1.0, 0.5)),      # one-dof edges
+@pytest.mark.parametrize("prob,theta_E", [
+    (lambda: W.random_small(4, (3, 3, 3), 3, (-3, 3)), 10.0),
+    (lambda: W.config5(seed_offset=77, nsub=3, m=4), 2.0),
+    (lambda: W.uniform(2, 2, nu=0.3, beta=(0.2, -1.0, 0.5)), 10.0),      # one-dof edges
 ])
-def test_edge_features_match_oracle(prob):
+def test_edge_features_match_oracle(prob, theta_E):
     p = prob()
-    s = B().Solver(p)
+    s = B().Solver(p, theta_E=theta_E)
     F, cnt = s.edge_features()
-    Fo = omlp.edge_features(Mesh(p.slabs), p.nu_elem, p.beta_node)
+    Fo = omlp.edge_features(Mesh(p.slabs), p.nu_elem, p.beta_node, theta_E=theta_E)
     assert F.shape == Fo.shape
     np.testing.assert_allclose(F, Fo, rtol=1e-6, atol=1e-6)
     k = [g['k'] for g in s.entities(1)]
@@ -92,3 +92,32 @@ def test_learned_skip_gain_on_channel_workload():
     assert st1["t_edge_ms"] < st0["t_edge_ms"]
     d = (u1 - u0).abs().max().item() / u0.abs().max().item()
     assert d < 1e-6
+
+
+@pytest.mark.parametrize("cfg,theta_E", [(5, 3.0), (3, 2.0)])
+def test_learned_skip_keeps_edges_that_select(cfg, theta_E):
+    """At a threshold where the full edge GEP selects constraints on part of
+    the edges (8x8x8 workloads, seeds never trained on), the shipped network
+    runs the GEP on almost every edge that selects: its false skips (skipped
+    edges whose full GEP selects) stay below 5 % of those edges -- the constant
+    rule that skips every edge misses all of them -- while it still skips
+    edges, and the false skips cost at most two GMRES iterations."""
+    params = B().load_mlp_params()
+    if params is None:
+        pytest.skip("no trained parameters shipped")
+    p = W.CONFIGS[cfg]()
+    full = B().Solver(p, precision=1, theta_E=theta_E)
+    u0, st0 = full.solve()
+    _, cnt_full = full.edge_features()
+    skip = B().Solver(p, precision=1, theta_E=theta_E, learned_skip_p=0.9, mlp_params=params)
+    u1, st1 = skip.solve()
+    _, cnt_skip = skip.edge_features()
+    pos = cnt_full > 0
+    skipped = cnt_skip < 0
+    false_skips = int((skipped & pos).sum())
+    print(f"theta_E {theta_E}: edges {len(cnt_full)} selecting {pos.sum()} skipped {skipped.sum()} "
+          f"false skips {false_skips} pnumE {st0['pnumE']}->{st1['pnumE']} iters {st0['iters']}->{st1['iters']}")
+    assert pos.sum() > 0 and skipped.sum() > 0
+    assert false_skips <= 0.05 * pos.sum()
+    assert st0["converged"] and st1["converged"]
+    assert st1["iters"] <= st0["iters"] + 2

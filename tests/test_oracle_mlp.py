@@ -44,6 +44,10 @@ def test_features_constant_coefficients():
         assert abs(f[7] - 1.0 / 3.0) < 1e-12          # an edge spans one subdomain: H = 1/3
         assert abs(f[8] - 0.4) < 1e-12
         assert abs(f[9] - math.log10((1.0 / 12.0) * bn / 0.02)) < 1e-12
+        assert abs(f[10] - 1.0) < 1e-12                # log10 of the default Theta_E = 10
+    F2 = mlp.edge_features(mesh, p.nu_elem, p.beta_node, theta_E=2.0)
+    np.testing.assert_allclose(F2[:, 10], math.log10(2.0), atol=1e-15)
+    np.testing.assert_array_equal(F2[:, :10], F[:, :10])
 
 
 def test_features_jump_ratio():
