@@ -243,6 +243,7 @@ struct bddc_ctx {
     int graph_iters = 0;
     unsigned long long graph_kernels = 0;
     int* err = nullptr;
+    struct BatchWS* bw = nullptr;   // workspace of the batched multi-RHS solver (first use)
     double* kmax = nullptr;     // largest condition estimate of the solve's GMRES cycles
     double* scal = nullptr;     // pinned host scratch
     // setup phase boundaries on the stream (GPU timeline; read once at the end)
@@ -1686,7 +1687,7 @@ static int gmres(bddc_ctx* C, const double* b, double* x, double rtol, int max_i
             BDDC_TRY(vec_axpby(C->r, b, 1.0, -1.0, n, st));
         }
         first = false;
-        BDDC_TRY(gm_cycle_start(C->r, n, C->gst, C->gv, C->partial, C->V, C->vcur, st));
+        BDDC_TRY(gm_cycle_start(C->r, n, C->gst, C->gst + 1, C->gv, C->partial, C->V, C->vcur, st));
         for (int guard = 0; guard < 100000; ++guard) {
             BDDC_CUDA_TRY(cudaMemcpyAsync(C->hst, C->gst, sizeof(GmState), cudaMemcpyDeviceToHost, st));
             BDDC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1777,6 +1778,341 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
     return conv ? BDDC_OK : BDDC_NOT_CONVERGED;
 }
 
+// ---------------------------------------------------------------------------
+// Several right-hand sides at once: independent GMRES runs (one Krylov space
+// per column) in lockstep.  Every operator launch streams each subdomain's
+// matrices once for all columns (the GEMV kernels loop over the columns of a
+// work item while its matrix slice is in cache); the Arnoldi / Givens kernels
+// carry a column grid dimension with one GmState per column, and a column that
+// has converged or reached the cap stops through its own stop flag.
+// ---------------------------------------------------------------------------
+constexpr int BDDC_BATCH_MAX = 64;   // columns per batched solve
+
+struct BatchWS {
+    int nb = 0;
+    long long ldz = 0;                 // column stride of zc: [z (nG) | y (nPi) | x (nPi)]
+    GmBatch B;
+    double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *hh = nullptr, *hh2 = nullptr,
+           *yy = nullptr, *partial = nullptr, *w = nullptr, *vcur = nullptr, *t = nullptr, *r = nullptr,
+           *zc = nullptr, *g = nullptr, *xG = nullptr, *ystore = nullptr, *res = nullptr, *corr = nullptr,
+           *Fin = nullptr, *uglob = nullptr;
+    GmState* gst = nullptr;            // nb states, then nb spare states (plain reductions)
+    GmState* hst = nullptr;            // pinned host copy of the nb states
+    int* allstop = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    unsigned long long graph_kernels = 0;
+    ~BatchWS() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (hst) cudaFreeHost(hst);
+    }
+};
+
+static int batch_ws(bddc_ctx* C, int nb, BatchWS** out) {
+    if (C->bw && C->bw->nb == nb) {
+        *out = C->bw;
+        return BDDC_OK;
+    }
+    delete C->bw;
+    C->bw = nullptr;
+    BatchWS* W = new BatchWS();
+    const long long nG = C->nG, ndof = C->hm.ndof, m = C->gm_m;
+    const long long nchunk = gm_nchunk(std::max(nG, ndof));
+    W->nb = nb;
+    W->ldz = nG + 2LL * C->nPi;
+    W->B = GmBatch{nb, (m + 1) * nG, nG, (m + 1) * (m + 1), m + 2, (m + 9) * (nchunk + 1)};
+    int rc = BDDC_OK;
+    auto A = [&](double** p, long long n) {
+        if (rc == BDDC_OK) rc = C->alloc(p, (size_t)n);
+    };
+    A(&W->V, W->B.sV * nb);
+    A(&W->H, W->B.sH * nb);
+    A(&W->cs, W->B.sSm * nb);
+    A(&W->sn, W->B.sSm * nb);
+    A(&W->gv, W->B.sSm * nb);
+    A(&W->hh, W->B.sSm * nb);
+    A(&W->hh2, W->B.sSm * nb);
+    A(&W->yy, W->B.sSm * nb);
+    A(&W->partial, W->B.sP * nb);
+    A(&W->w, nG * nb);
+    A(&W->vcur, nG * nb);
+    A(&W->t, nG * nb);
+    A(&W->r, nG * nb);
+    A(&W->g, nG * nb);
+    A(&W->xG, nG * nb);
+    A(&W->zc, W->ldz * nb);
+    A(&W->ystore, C->ny * nb);
+    A(&W->res, ndof * nb);
+    A(&W->corr, ndof * nb);
+    A(&W->Fin, ndof * nb);
+    A(&W->uglob, ndof * nb);
+    if (rc == BDDC_OK) rc = C->alloc(&W->gst, 2 * (size_t)nb);
+    if (rc == BDDC_OK && cudaMemsetAsync(W->gst, 0, sizeof(GmState) * 2 * nb, C->st) != cudaSuccess) rc = BDDC_ECUDA;
+    if (rc == BDDC_OK) rc = C->alloc(&W->allstop, 1);
+    if (rc == BDDC_OK && cudaMallocHost(&W->hst, sizeof(GmState) * nb) != cudaSuccess) rc = BDDC_ENOMEM;
+    if (rc != BDDC_OK) {
+        delete W;
+        return rc;
+    }
+    C->bw = W;
+    *out = W;
+    return BDDC_OK;
+}
+
+template <class T>
+static int op_S_multi(bddc_ctx* C, const double* x, long long ldx, double* y, int nb, const int* skip) {
+    BDDC_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * C->nG * nb, C->st));
+    return gemv_run<T>((const T*)C->ST, C->itS, C->nitS, C->gidx_pool, x, y, C->maxcols, nb, (int)ldx, C->nG, C->st,
+                       skip, C->bytesS);
+}
+
+// zc (column stride ldz) = [M^-1 x | coarse residual | coarse solution] for nb columns
+template <class T>
+static int op_M_multi(bddc_ctx* C, const double* x, double* zc, long long ldz, int nb, const int* skip) {
+    cudaStream_t st = C->st;
+    BDDC_CUDA_TRY(cudaMemsetAsync(zc, 0, sizeof(double) * ldz * nb, st));
+    BDDC_TRY(gemv_run<T>((const T*)C->MA, C->itM1, C->nitM1, C->gidx_pool, x, zc, C->maxcols, nb, C->nG, (int)ldz, st,
+                         skip, C->bytesM1));
+    if (C->nPi == 0) return BDDC_OK;
+    double* y2 = zc + C->nG;
+    double* upi = y2 + C->nPi;
+    if (C->coarse_nd) {
+        for (size_t h = 0; h + 1 < C->ndFwdOff.size(); ++h) {
+            const int a = C->ndFwdOff[h], b = C->ndFwdOff[h + 1];
+            if (b > a)
+                BDDC_TRY(gemv_run<double>(C->ndOps, C->ndFwd + a, b - a, C->ndIdx, y2, y2, 0, nb, (int)ldz, (int)ldz,
+                                          st, skip, C->ndFwdBytes[h]));
+        }
+        for (size_t d = 0; d + 1 < C->ndBwdOff.size(); ++d) {
+            const int a = C->ndBwdOff[d], b = C->ndBwdOff[d + 1];
+            if (b > a)
+                BDDC_TRY(gemv_run<double>(C->ndOps, C->ndBwd + a, b - a, C->ndIdx, y2, y2, 0, nb, (int)ldz, (int)ldz,
+                                          st, skip, C->ndBwdBytes[d]));
+        }
+    } else {
+        BDDC_TRY(gemv_run<double>(C->SPiInv, C->itC, C->nitC, C->gidx_pool, zc, upi, C->maxcols, nb, (int)ldz,
+                                  (int)ldz, st, skip, C->bytesC));
+    }
+    return gemv_t_run<T>((const T*)C->MC, C->itM3, C->nitM3, C->gidx_pool, upi, zc, nb, (int)ldz, (int)ldz, st, skip,
+                         C->bytesM3);
+}
+
+template <class T>
+static int gm_iteration_batch(bddc_ctx* C, BatchWS* W) {
+    const long long n = C->nG;
+    const int* skip = W->allstop;
+    BDDC_TRY(op_M_multi<T>(C, W->vcur, W->zc, W->ldz, W->nb, skip));
+    BDDC_TRY(op_S_multi<T>(C, W->zc, W->ldz, W->w, W->nb, skip));
+    BDDC_TRY(gm_pass(0, W->V, n, W->w, n, W->gst, nullptr, W->hh, W->partial, C->st, W->B));
+    BDDC_TRY(gm_pass(1, W->V, n, W->w, n, W->gst, W->hh, W->hh2, W->partial, C->st, W->B));
+    BDDC_TRY(gm_pass(2, W->V, n, W->w, n, W->gst, W->hh2, nullptr, W->partial, C->st, W->B));
+    BDDC_TRY(gm_givens(W->gst, W->H, W->cs, W->sn, W->gv, W->hh, W->hh2, C->st, W->B));
+    BDDC_TRY(gm_normalize(W->V, n, W->w, n, W->gst, W->vcur, C->st, W->B));
+    return gm_all_stopped(W->gst, W->nb, W->allstop, C->st);
+}
+
+// Column norms ||x_c|| of nb vectors of length n (stride ld = n) through the spare states.
+static int norms_batch(bddc_ctx* C, BatchWS* W, const double* x, long long n, int nb, double* out) {
+    GmBatch B = W->B;
+    B.ncol = nb;
+    B.sW = n;
+    BDDC_TRY(gm_norm2(x, n, W->gst + W->nb, W->partial, C->st, B));
+    BDDC_CUDA_TRY(cudaMemcpyAsync(W->hst, W->gst + W->nb, sizeof(GmState) * nb, cudaMemcpyDeviceToHost, C->st));
+    BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+    for (int c = 0; c < nb; ++c) out[c] = std::sqrt(std::max(W->hst[c].nrm2, 0.0));
+    return BDDC_OK;
+}
+
+// GMRES on S X = Bm for the columns of Bm (nG x nb); tol[c] is the absolute
+// residual target of column c (< 0: the column is left at zero).  X is
+// overwritten; iters[c], conv[c] and the true relative residuals are returned.
+template <class T>
+static int gmres_batch(bddc_ctx* C, BatchWS* W, const double* Bm, double* X, const double* tol, const double* bnorm,
+                       const int* max_iter, int* iters, int* conv, double* relres) {
+    const long long n = C->nG;
+    const int nb = W->nb;
+    cudaStream_t st = C->st;
+    BDDC_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * n * nb, st));
+    std::vector<GmState> init(2 * (size_t)nb);
+    memset(init.data(), 0, sizeof(GmState) * init.size());
+    bool any = false;
+    for (int c = 0; c < nb; ++c) {
+        init[c].m = C->gm_m;
+        init[c].max_iter = max_iter[c];
+        init[c].tol = tol[c];
+        init[c].done = (tol[c] < 0.0 || bnorm[c] == 0.0) ? 1 : 0;
+        init[c].converged = init[c].done;
+        iters[c] = 0;
+        conv[c] = init[c].done;
+        relres[c] = 0.0;
+        any = any || !init[c].done;
+    }
+    if (!any) return BDDC_OK;
+    BDDC_CUDA_TRY(cudaMemcpyAsync(W->gst, init.data(), sizeof(GmState) * 2 * nb, cudaMemcpyHostToDevice, st));
+    const int K = 4;
+    const bool use_graph = getenv("BDDC_NO_GRAPH") == nullptr;
+    if (use_graph && W->graph == nullptr) {
+        cudaGraph_t gr;
+        BDDC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        g_capturing = true;
+        int rc = BDDC_OK;
+        for (int q = 0; q < K && rc == BDDC_OK; ++q) rc = gm_iteration_batch<T>(C, W);
+        g_capturing = false;
+        cudaError_t ce = cudaStreamEndCapture(st, &gr);
+        if (rc != BDDC_OK) return rc;
+        BDDC_CUDA_TRY(ce);
+        size_t nn = 0;
+        BDDC_CUDA_TRY(cudaGraphGetNodes(gr, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        BDDC_CUDA_TRY(cudaGraphGetNodes(gr, nodes.data(), &nn));
+        W->graph_kernels = 0;
+        for (auto& nd : nodes) {
+            cudaGraphNodeType ty;
+            BDDC_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+            if (ty == cudaGraphNodeTypeKernel) ++W->graph_kernels;
+        }
+        BDDC_CUDA_TRY(cudaGraphInstantiate(&W->graph, gr, 0));
+        cudaGraphDestroy(gr);
+    }
+    std::vector<GmState> hs(nb);
+    bool first = true;
+    while (true) {
+        if (first) {
+            BDDC_CUDA_TRY(cudaMemcpyAsync(W->r, Bm, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st));
+        } else {
+            BDDC_TRY(op_S_multi<T>(C, X, n, W->r, nb, nullptr));
+            BDDC_TRY(vec_axpby_cols(W->r, n, Bm, n, 1.0, -1.0, n, nb, st));
+        }
+        first = false;
+        BDDC_TRY(gm_cycle_start(W->r, n, W->gst, W->gst + nb, W->gv, W->partial, W->V, W->vcur, st, W->B));
+        BDDC_TRY(gm_all_stopped(W->gst, nb, W->allstop, st));
+        for (int guard = 0; guard < 100000; ++guard) {
+            BDDC_CUDA_TRY(cudaMemcpyAsync(W->hst, W->gst, sizeof(GmState) * nb, cudaMemcpyDeviceToHost, st));
+            BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+            bool all = true;
+            for (int c = 0; c < nb; ++c) all = all && W->hst[c].stop;
+            if (all) break;
+            if (use_graph) {
+                BDDC_CUDA_TRY(cudaGraphLaunch(W->graph, st));
+                bddc_note_launches(W->graph_kernels);
+            } else {
+                for (int q = 0; q < K; ++q) BDDC_TRY(gm_iteration_batch<T>(C, W));
+            }
+        }
+        if (C->o.cond_est) BDDC_TRY(gm_cond(W->gst, W->H, C->gm_m, C->kmax, st, W->B));
+        BDDC_TRY(gm_finish(W->V, n, W->gst, W->H, W->gv, W->yy, W->t, n, st, W->B));
+        BDDC_TRY(op_M_multi<T>(C, W->t, W->zc, W->ldz, nb, nullptr));
+        BDDC_TRY(vec_axpby_cols(X, n, W->zc, W->ldz, 1.0, 1.0, n, nb, st));
+        // columns that converged or reached the cap are done; the others restart
+        BDDC_CUDA_TRY(cudaMemcpyAsync(hs.data(), W->gst, sizeof(GmState) * nb, cudaMemcpyDeviceToHost, st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(st));
+        bool all_done = true;
+        for (int c = 0; c < nb; ++c) {
+            if (!hs[c].done && (hs[c].converged || hs[c].total >= max_iter[c])) hs[c].done = 1;
+            all_done = all_done && hs[c].done;
+        }
+        if (all_done) break;
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W->gst, hs.data(), sizeof(GmState) * nb, cudaMemcpyHostToDevice, st));
+    }
+    // true residuals
+    BDDC_TRY(op_S_multi<T>(C, X, n, W->r, nb, nullptr));
+    BDDC_TRY(vec_axpby_cols(W->r, n, Bm, n, 1.0, -1.0, n, nb, st));
+    std::vector<double> rn(nb);
+    BDDC_TRY(norms_batch(C, W, W->r, n, nb, rn.data()));
+    for (int c = 0; c < nb; ++c) {
+        iters[c] = hs[c].total;
+        conv[c] = init[c].done ? 1 : hs[c].converged;
+        relres[c] = bnorm[c] > 0 ? rn[c] / bnorm[c] : 0.0;
+    }
+    return BDDC_OK;
+}
+
+// The whole solve (condensation, GMRES, recovery; MIXED: FP64 refinement) for
+// nb columns F (ndof x nb, device) -> U (ndof x nb, device).
+template <class T>
+static int solve_batch(bddc_ctx* C, BatchWS* W, const double* F, double* U, bddc_stats* stt) {
+    cudaStream_t st = C->st;
+    HostMesh& hm = C->hm;
+    const long long nG = C->nG, ndof = hm.ndof;
+    const int nb = W->nb;
+    std::vector<double> Fn(nb), rn(nb), bn(nb), tol(nb), rr(nb);
+    std::vector<int> it(nb), cv(nb), itot(nb, 0), steps(nb, 0), convd(nb, 0);
+    BDDC_TRY(norms_batch(C, W, F, ndof, nb, Fn.data()));
+    auto condense_cols = [&](const double* R) -> int {
+        for (int c = 0; c < nb; ++c) BDDC_TRY(gather_run(R + c * ndof, C->gamma_dofs, W->g + c * nG, (int)nG, st));
+        return condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, R, W->g, W->ystore, nb, ndof, nG, C->ny,
+                               C->itCI, C->nitCI, C->bytesCI, st);
+    };
+    double relres_max = 0.0;
+    if (!C->mixed) {
+        BDDC_TRY(condense_cols(F));
+        BDDC_TRY(norms_batch(C, W, W->g, nG, nb, bn.data()));
+        std::vector<int> caps(nb, C->o.max_iter);
+        for (int c = 0; c < nb; ++c) tol[c] = C->o.rtol * bn[c];
+        BDDC_TRY(gmres_batch<T>(C, W, W->g, W->xG, tol.data(), bn.data(), caps.data(), it.data(), cv.data(),
+                                rr.data()));
+        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, W->xG, W->ystore, U, nb, nG, ndof, C->ny,
+                                C->itRI, C->nitRI, C->bytesRI, st));
+        for (int c = 0; c < nb; ++c) {
+            itot[c] = it[c];
+            steps[c] = 1;
+            convd[c] = cv[c];
+            relres_max = std::max(relres_max, rr[c]);
+        }
+    } else {
+        BDDC_CUDA_TRY(cudaMemsetAsync(U, 0, sizeof(double) * ndof * nb, st));
+        BDDC_CUDA_TRY(cudaMemcpyAsync(W->res, F, sizeof(double) * ndof * nb, cudaMemcpyDeviceToDevice, st));
+        for (int c = 0; c < nb; ++c) rn[c] = Fn[c];
+        for (int step = 0; step < C->o.max_refine; ++step) {
+            bool any = false;
+            for (int c = 0; c < nb; ++c) {
+                const bool done = Fn[c] == 0.0 || rn[c] <= C->o.rtol * Fn[c] || itot[c] >= C->o.max_iter;
+                if (done) convd[c] = convd[c] || Fn[c] == 0.0 || rn[c] <= C->o.rtol * Fn[c];
+                any = any || !done;
+            }
+            if (!any) break;
+            BDDC_TRY(condense_cols(W->res));
+            BDDC_TRY(norms_batch(C, W, W->g, nG, nb, bn.data()));
+            std::vector<int> caps(nb, 0);
+            for (int c = 0; c < nb; ++c) {
+                const bool done = Fn[c] == 0.0 || rn[c] <= C->o.rtol * Fn[c] || itot[c] >= C->o.max_iter;
+                const double tk = std::min(std::max(C->o.inner_rtol, 0.5 * C->o.rtol * Fn[c] / rn[c]), 0.5);
+                tol[c] = done ? -1.0 : tk * bn[c];
+                caps[c] = C->o.max_iter - itot[c];
+                if (!done) ++steps[c];
+            }
+            BDDC_TRY(gmres_batch<T>(C, W, W->g, W->xG, tol.data(), bn.data(), caps.data(), it.data(), cv.data(),
+                                    rr.data()));
+            for (int c = 0; c < nb; ++c)
+                if (tol[c] >= 0.0) itot[c] += it[c];
+            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, W->xG, W->ystore, W->corr, nb, nG,
+                                    ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
+            BDDC_TRY(vec_axpby_cols(U, ndof, W->corr, ndof, 1.0, 1.0, ndof, nb, st));
+            BDDC_TRY(stencil_residual(hm, C->stencil, U, F, W->res, nb, st));
+            BDDC_TRY(norms_batch(C, W, W->res, ndof, nb, rn.data()));
+        }
+        for (int c = 0; c < nb; ++c) {
+            convd[c] = convd[c] || Fn[c] == 0.0 || rn[c] <= C->o.rtol * Fn[c];
+            relres_max = std::max(relres_max, Fn[c] > 0 ? rn[c] / Fn[c] : 0.0);
+        }
+    }
+    BDDC_TRY(stencil_residual(hm, C->stencil, U, F, W->res, nb, st));
+    BDDC_TRY(norms_batch(C, W, W->res, ndof, nb, rn.data()));
+    double rg = 0.0;
+    int conv_all = 1, iters = 0, nsteps = 0;
+    for (int c = 0; c < nb; ++c) {
+        rg = std::max(rg, Fn[c] > 0 ? rn[c] / Fn[c] : 0.0);
+        conv_all = conv_all && convd[c];
+        iters += itot[c];
+        nsteps += steps[c];
+    }
+    stt->iters = iters;
+    stt->refine_steps = nsteps;
+    stt->converged = conv_all;
+    stt->relres = relres_max;
+    stt->relres_global = rg;
+    return conv_all ? BDDC_OK : BDDC_NOT_CONVERGED;
+}
+
 int bddc_ctx_device(const bddc_ctx* C) { return C ? C->device : -1; }
 
 int bddc_apply_into(bddc_ctx* C, const double* r, double* z, int nrhs, double* work, size_t work_doubles) {
@@ -1842,6 +2178,7 @@ const char* bddc_strerror(int code) {
 void bddc_destroy(bddc_ctx* C) {
     if (!C) return;
     if (C->st) cudaStreamSynchronize(C->st);     // the graph may still be running
+    delete C->bw;
     graph_pool_give(C->graph);
     for (void* p : C->allocs) cudaFreeAsync(p, C->st);
     if (C->st) cudaStreamSynchronize(C->st);
@@ -2053,7 +2390,36 @@ int bddc_gmres_solve(bddc_ctx* C, const double* load, double* u, int nrhs, int m
     agg.relres_global = 0;
     agg.refine_steps = 0;
     BDDC_CUDA_TRY(cudaMemsetAsync(C->kmax, 0, sizeof(double), C->st));
-    for (int c = 0; c < nrhs; ++c) {
+    // several columns: batched solves of up to BDDC_BATCH_MAX columns each
+    for (int c0 = 0; nrhs > 1 && c0 < nrhs; c0 += BDDC_BATCH_MAX) {
+        const int nb = std::min(BDDC_BATCH_MAX, nrhs - c0);
+        BatchWS* W = nullptr;
+        BDDC_TRY(batch_ws(C, nb, &W));
+        const double* Fd = W->Fin;
+        for (int c = 0; c < nb; ++c) {
+            const double* src = load ? load + (long long)(c0 + c) * ndof : C->F;
+            const cudaMemcpyKind kind = (load && mem == BDDC_MEM_HOST) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+            if (load && mem == BDDC_MEM_DEVICE && c == 0) {
+                Fd = load + (long long)c0 * ndof;   // device loads are used in place
+                break;
+            }
+            BDDC_CUDA_TRY(cudaMemcpyAsync(W->Fin + c * ndof, src, sizeof(double) * ndof, kind, C->st));
+        }
+        double* ud = mem == BDDC_MEM_HOST ? W->uglob : u + (long long)c0 * ndof;
+        bddc_stats one = C->stats;
+        int rc = C->mixed ? solve_batch<float>(C, W, Fd, ud, &one) : solve_batch<double>(C, W, Fd, ud, &one);
+        if (rc < 0) return rc;
+        if (rc != BDDC_OK) worst = rc;
+        if (mem == BDDC_MEM_HOST)
+            BDDC_CUDA_TRY(cudaMemcpyAsync(u + (long long)c0 * ndof, W->uglob, sizeof(double) * ndof * nb,
+                                          cudaMemcpyDeviceToHost, C->st));
+        agg.iters += one.iters;
+        agg.refine_steps += one.refine_steps;
+        agg.converged = agg.converged && one.converged;
+        agg.relres = std::max(agg.relres, one.relres);
+        agg.relres_global = std::max(agg.relres_global, one.relres_global);
+    }
+    for (int c = 0; nrhs == 1 && c < nrhs; ++c) {
         const double* Fd = C->F;
         if (load) {
             if (mem == BDDC_MEM_HOST) {

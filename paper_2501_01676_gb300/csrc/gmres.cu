@@ -30,7 +30,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(DOT_THREADS) k_dots(const double* __restrict__ V, long long ldv,
                                                       const double* __restrict__ w, long long n,
                                                       const GmState* __restrict__ S, int rows_mode,
-                                                      double* __restrict__ partial, int nchunk) {
+                                                      double* __restrict__ partial, int nchunk, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    if (V) V += col * B.sV;
+    w += col * B.sW;
+    partial += col * B.sP;
     if (S->stop) return;
     const int nrows = rows_mode == 0 ? S->j + 1 : 1;   // 0: rows 0..j; 1: w.w
     const int r0 = blockIdx.y * DOT_ROWS;
@@ -73,7 +78,14 @@ template <int MODE>
 __global__ void __launch_bounds__(PASS_THREADS) k_pass(const double* __restrict__ V, long long ldv,
                                                        double* __restrict__ w, long long n, GmState* __restrict__ S,
                                                        const double* __restrict__ hin, double* __restrict__ hout,
-                                                       double* __restrict__ partial, int nchunk) {
+                                                       double* __restrict__ partial, int nchunk, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    V += col * B.sV;
+    w += col * B.sW;
+    if (hin) hin += col * B.sSm;
+    if (hout) hout += col * B.sSm;
+    partial += col * B.sP;
     if (S->stop) return;
     const int nr = S->j + 1;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -157,7 +169,11 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const double* __restrict_
 
 // h[row] (+)= sum_chunks partial; mode 0: h = sum, 1: h += sum, 2: store in S->nrm2
 __global__ void k_dots_reduce(const double* __restrict__ partial, int nchunk, GmState* __restrict__ S,
-                              double* __restrict__ h, int mode, int rows_mode) {
+                              double* __restrict__ h, int mode, int rows_mode, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    partial += col * B.sP;
+    if (h) h += col * B.sSm;
     if (S->stop) return;
     const int nrows = rows_mode == 0 ? S->j + 1 : 1;
     const int lane = threadIdx.x & 31;
@@ -175,7 +191,12 @@ __global__ void k_dots_reduce(const double* __restrict__ partial, int nchunk, Gm
 
 // w -= sum_{i<=j} c[i] V[i]
 __global__ void k_orth_update(const double* __restrict__ V, long long ldv, double* __restrict__ w,
-                              long long n, const GmState* __restrict__ S, const double* __restrict__ c) {
+                              long long n, const GmState* __restrict__ S, const double* __restrict__ c, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    V += col * B.sV;
+    w += col * B.sW;
+    c += col * B.sSm;
     if (S->stop) return;
     const int nr = S->j + 1;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -189,7 +210,15 @@ __global__ void k_orth_update(const double* __restrict__ V, long long ldv, doubl
 // one Arnoldi step's scalar work: Hessenberg column, Givens, residual estimate
 __global__ void k_givens(GmState* __restrict__ S, double* __restrict__ H, double* __restrict__ cs,
                          double* __restrict__ sn, double* __restrict__ gv, const double* __restrict__ h,
-                         const double* __restrict__ h2) {
+                         const double* __restrict__ h2, GmBatch B) {
+    const int bc = blockIdx.z;
+    S += bc;
+    H += bc * B.sH;
+    cs += bc * B.sSm;
+    sn += bc * B.sSm;
+    gv += bc * B.sSm;
+    h += bc * B.sSm;
+    h2 += bc * B.sSm;
     if (threadIdx.x != 0 || S->stop) return;
     const int j = S->j, m = S->m;
     double* col = H + (long long)j * (m + 1);          // column j, length m+1
@@ -226,7 +255,12 @@ __global__ void k_givens(GmState* __restrict__ S, double* __restrict__ H, double
 // V[j] = w * scale  (j already advanced)
 // V[j] = w * scale and the next preconditioner input vcur = V[j]
 __global__ void k_normalize(double* __restrict__ V, long long ldv, const double* __restrict__ w,
-                            long long n, GmState* __restrict__ S, double* __restrict__ vcur) {
+                            long long n, GmState* __restrict__ S, double* __restrict__ vcur, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    V += col * B.sV;
+    w += col * B.sW;
+    vcur += col * B.sW;
     if (!S->need_norm) return;
     const int j = S->j;
     if (j > S->m) return;
@@ -239,11 +273,15 @@ __global__ void k_normalize(double* __restrict__ V, long long ldv, const double*
     }
 }
 
-__global__ void k_clear_norm(GmState* S) { S->need_norm = 0; }
+__global__ void k_clear_norm(GmState* S) { S[blockIdx.z].need_norm = 0; }
 
 // vcur = V[j]
 __global__ void k_copy_row(const double* __restrict__ V, long long ldv, double* __restrict__ out,
-                           long long n, const GmState* __restrict__ S) {
+                           long long n, const GmState* __restrict__ S, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    V += col * B.sV;
+    out += col * B.sW;
     if (S->stop) return;
     const int j = S->j;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -253,7 +291,12 @@ __global__ void k_copy_row(const double* __restrict__ V, long long ldv, double* 
 
 // y = H(1:k,1:k)^{-1} g(1:k), then t = V(:,1:k) y
 __global__ void k_backsolve(const GmState* __restrict__ S, const double* __restrict__ H,
-                            const double* __restrict__ gv, double* __restrict__ y) {
+                            const double* __restrict__ gv, double* __restrict__ y, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    H += col * B.sH;
+    gv += col * B.sSm;
+    y += col * B.sSm;
     if (threadIdx.x != 0) return;
     const int k = S->j, m = S->m;
     for (int i = k - 1; i >= 0; --i) {
@@ -276,9 +319,11 @@ constexpr int GM_COND_ITERS = 16;
 constexpr int GM_COND_THREADS = 64;
 __global__ void __launch_bounds__(GM_COND_THREADS) k_cond(const GmState* __restrict__ S,
                                                           const double* __restrict__ H,
-                                                          double* __restrict__ kmax) {
+                                                          double* __restrict__ kmax, GmBatch B) {
     extern __shared__ double Rs[];                  // k x k, row-major
     __shared__ double x[GM_COND_MAX], z[GM_COND_MAX], red[GM_COND_THREADS / 32];
+    S += blockIdx.z;
+    H += blockIdx.z * B.sH;
     const int k = S->j, m = S->m, t = threadIdx.x;
     if (k <= 0 || k > GM_COND_MAX) return;
     for (int q = t; q < k * k; q += GM_COND_THREADS) {
@@ -345,13 +390,19 @@ __global__ void __launch_bounds__(GM_COND_THREADS) k_cond(const GmState* __restr
         smin = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
     }
     if (t == 0) {
+        // positive doubles order like their bit patterns: max over columns by atomicMax
         const double kap = smin > 0.0 ? smax / smin : INFINITY;
-        if (!(kap <= *kmax)) *kmax = kap;
+        atomicMax(reinterpret_cast<unsigned long long*>(kmax), (unsigned long long)__double_as_longlong(kap));
     }
 }
 
 __global__ void k_combine(const double* __restrict__ V, long long ldv, const double* __restrict__ y,
-                          const GmState* __restrict__ S, double* __restrict__ t, long long n) {
+                          const GmState* __restrict__ S, double* __restrict__ t, long long n, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    V += col * B.sV;
+    y += col * B.sSm;
+    t += col * B.sW;
     const int k = S->j;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
@@ -363,8 +414,17 @@ __global__ void k_combine(const double* __restrict__ V, long long ldv, const dou
 
 // start a cycle from r: beta = ||r||, V[0] = r / beta, g = beta e1
 __global__ void k_cycle_start(GmState* __restrict__ S, double* __restrict__ gv, const double* __restrict__ partial,
-                              int nchunk) {
+                              int nchunk, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    gv += col * B.sSm;
+    partial += col * B.sP;
     if (threadIdx.x != 0) return;
+    if (S->done) {                      // a column that has finished stays stopped and adds nothing
+        S->stop = 1;
+        S->j = 0;
+        return;
+    }
     double s = 0.0;
     for (int c = 0; c < nchunk; ++c) s += partial[c];
     double beta = sqrt(fmax(s, 0.0));
@@ -381,8 +441,12 @@ __global__ void k_cycle_start(GmState* __restrict__ S, double* __restrict__ gv, 
     }
 }
 
-__global__ void k_scale_into(double* __restrict__ dst, const double* __restrict__ src, long long n,
-                             const GmState* __restrict__ S) {
+__global__ void k_scale_into(double* __restrict__ dst, long long sdst, const double* __restrict__ src, long long n,
+                             const GmState* __restrict__ S, GmBatch B) {
+    const int col = blockIdx.z;
+    S += col;
+    dst += col * sdst;
+    src += col * B.sW;
     const double sc = S->scale;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
@@ -390,7 +454,30 @@ __global__ void k_scale_into(double* __restrict__ dst, const double* __restrict_
 }
 
 __global__ void k_axpby(double* __restrict__ y, const double* __restrict__ x, double a, double b,
-                        long long n) {
+                        long long n, GmBatch B) {
+    y += blockIdx.z * B.sW;
+    x += blockIdx.z * B.sW;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+        y[e] = a * x[e] + b * y[e];
+}
+
+// flag = 1 when every column has stopped (the operators' skip flag of a batched solve)
+__global__ void k_all_stopped(const GmState* __restrict__ S, int ncol, int* __restrict__ flag) {
+    __shared__ int any_running;
+    if (threadIdx.x == 0) any_running = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x)
+        if (!S[c].stop) any_running = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = any_running ? 0 : 1;
+}
+
+// y[:, c] = a x[:, c] + b y[:, c] with separate column strides
+__global__ void k_axpby_cols(double* __restrict__ y, long long ldy, const double* __restrict__ x, long long ldx,
+                             double a, double b, long long n) {
+    y += blockIdx.z * ldy;
+    x += blockIdx.z * ldx;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
         y[e] = a * x[e] + b * y[e];
@@ -407,109 +494,116 @@ int gm_nchunk(long long n) { return (int)((n + DOT_CHUNK - 1) / DOT_CHUNK); }
 
 // h (mode 0 set / 1 add) = V[0..j]^T w
 int gm_dots(const double* V, long long ldv, const double* w, long long n, GmState* S, double* partial,
-            double* h, int mode, int max_rows, cudaStream_t st) {
+            double* h, int mode, int max_rows, cudaStream_t st, GmBatch B) {
     int nchunk = gm_nchunk(n);
-    dim3 grid(nchunk, (max_rows + DOT_ROWS - 1) / DOT_ROWS);
-    k_dots<<<grid, DOT_THREADS, 0, st>>>(V, ldv, w, n, S, 0, partial, nchunk);
+    dim3 grid(nchunk, (max_rows + DOT_ROWS - 1) / DOT_ROWS, B.ncol);
+    k_dots<<<grid, DOT_THREADS, 0, st>>>(V, ldv, w, n, S, 0, partial, nchunk, B);
     bddc_note_launches(1);
-    k_dots_reduce<<<(max_rows + 7) / 8, 256, 0, st>>>(partial, nchunk, S, h, mode, 0);
+    k_dots_reduce<<<dim3((max_rows + 7) / 8, 1, B.ncol), 256, 0, st>>>(partial, nchunk, S, h, mode, 0, B);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
 
-int gm_norm2(const double* w, long long n, GmState* S, double* partial, cudaStream_t st) {
+int gm_norm2(const double* w, long long n, GmState* S, double* partial, cudaStream_t st, GmBatch B) {
     int nchunk = gm_nchunk(n);
-    k_dots<<<dim3(nchunk, 1), DOT_THREADS, 0, st>>>(nullptr, 0, w, n, S, 1, partial, nchunk);
+    k_dots<<<dim3(nchunk, 1, B.ncol), DOT_THREADS, 0, st>>>(nullptr, 0, w, n, S, 1, partial, nchunk, B);
     bddc_note_launches(1);
-    k_dots_reduce<<<1, 32, 0, st>>>(partial, nchunk, S, nullptr, 2, 1);
+    k_dots_reduce<<<dim3(1, 1, B.ncol), 32, 0, st>>>(partial, nchunk, S, nullptr, 2, 1, B);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
-
 int gm_orth_update(const double* V, long long ldv, double* w, long long n, const GmState* S,
-                   const double* c, cudaStream_t st) {
-    k_orth_update<<<grid_for(n), 256, 0, st>>>(V, ldv, w, n, S, c);
+                   const double* c, cudaStream_t st, GmBatch B) {
+    k_orth_update<<<dim3(grid_for(n), 1, B.ncol), 256, 0, st>>>(V, ldv, w, n, S, c, B);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
-
 int gm_givens(GmState* S, double* H, double* cs, double* sn, double* gv, const double* h,
-              const double* h2, cudaStream_t st) {
-    k_givens<<<1, 32, 0, st>>>(S, H, cs, sn, gv, h, h2);
+              const double* h2, cudaStream_t st, GmBatch B) {
+    k_givens<<<dim3(1, 1, B.ncol), 32, 0, st>>>(S, H, cs, sn, gv, h, h2, B);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
-
 int gm_normalize(double* V, long long ldv, const double* w, long long n, GmState* S, double* vcur,
-                 cudaStream_t st) {
+                 cudaStream_t st, GmBatch B) {
     // need_norm is cleared by the next iteration's first pass (k_pass<0>)
-    k_normalize<<<grid_for(n), 256, 0, st>>>(V, ldv, w, n, S, vcur);
+    k_normalize<<<dim3(grid_for(n), 1, B.ncol), 256, 0, st>>>(V, ldv, w, n, S, vcur, B);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
-
 int gm_pass(int mode, const double* V, long long ldv, double* w, long long n, GmState* S, const double* hin,
-            double* hout, double* partial, cudaStream_t st) {
+            double* hout, double* partial, cudaStream_t st, GmBatch B) {
     const int nchunk = (int)((n + PASS_CHUNK - 1) / PASS_CHUNK);
-    if (mode == 0) k_pass<0><<<nchunk, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk);
-    else if (mode == 1) k_pass<1><<<nchunk, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk);
-    else k_pass<2><<<nchunk, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk);
+    const dim3 grid(nchunk, 1, B.ncol);
+    if (mode == 0) k_pass<0><<<grid, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk, B);
+    else if (mode == 1) k_pass<1><<<grid, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk, B);
+    else k_pass<2><<<grid, PASS_THREADS, 0, st>>>(V, ldv, w, n, S, hin, hout, partial, nchunk, B);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
-
 int gm_copy_row(const double* V, long long ldv, double* out, long long n, const GmState* S,
-                cudaStream_t st) {
-    k_copy_row<<<grid_for(n), 256, 0, st>>>(V, ldv, out, n, S);
+                cudaStream_t st, GmBatch B) {
+    k_copy_row<<<dim3(grid_for(n), 1, B.ncol), 256, 0, st>>>(V, ldv, out, n, S, B);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
-
-int gm_cycle_start(const double* r, long long n, GmState* S, double* gv, double* partial, double* V0,
-                   double* vcur, cudaStream_t st) {
+int gm_cycle_start(const double* r, long long n, GmState* S, GmState* Sspare, double* gv, double* partial,
+                   double* V0, double* vcur, cudaStream_t st, GmBatch B) {
     int nchunk = gm_nchunk(n);
-    // plain norm pass that ignores the stop flag: use a private state copy
-    k_dots<<<dim3(nchunk, 1), DOT_THREADS, 0, st>>>(nullptr, 0, r, n, S + 1, 1, partial, nchunk);
+    // plain norm pass that ignores the stop flag: private state copies
+    k_dots<<<dim3(nchunk, 1, B.ncol), DOT_THREADS, 0, st>>>(nullptr, 0, r, n, Sspare, 1, partial, nchunk, B);
     bddc_note_launches(1);
-    k_cycle_start<<<1, 32, 0, st>>>(S, gv, partial, nchunk);
+    k_cycle_start<<<dim3(1, 1, B.ncol), 32, 0, st>>>(S, gv, partial, nchunk, B);
     bddc_note_launches(1);
-    k_scale_into<<<grid_for(n), 256, 0, st>>>(V0, r, n, S);
-    k_scale_into<<<grid_for(n), 256, 0, st>>>(vcur, r, n, S);
-    bddc_note_launches(2);
+    k_scale_into<<<dim3(grid_for(n), 1, B.ncol), 256, 0, st>>>(V0, B.sV, r, n, S, B);
+    bddc_note_launches(1);
+    k_scale_into<<<dim3(grid_for(n), 1, B.ncol), 256, 0, st>>>(vcur, B.sW, r, n, S, B);
+    bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
-
 int gm_finish(const double* V, long long ldv, const GmState* S, const double* H, const double* gv,
-              double* y, double* t, long long n, cudaStream_t st) {
-    k_backsolve<<<1, 32, 0, st>>>(S, H, gv, y);
+              double* y, double* t, long long n, cudaStream_t st, GmBatch B) {
+    k_backsolve<<<dim3(1, 1, B.ncol), 32, 0, st>>>(S, H, gv, y, B);
     bddc_note_launches(1);
-    k_combine<<<grid_for(n), 256, 0, st>>>(V, ldv, y, S, t, n);
-    bddc_note_launches(1);
-    BDDC_CUDA_TRY(cudaGetLastError());
-    return BDDC_OK;
-}
-
-int vec_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st) {
-    k_axpby<<<grid_for(n), 256, 0, st>>>(y, x, a, b, n);
+    k_combine<<<dim3(grid_for(n), 1, B.ncol), 256, 0, st>>>(V, ldv, y, S, t, n, B);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
-
-int gm_cond(const GmState* S, const double* H, int mmax, double* kmax, cudaStream_t st) {
+int vec_axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t st, GmBatch B) {
+    k_axpby<<<dim3(grid_for(n), 1, B.ncol), 256, 0, st>>>(y, x, a, b, n, B);
+    bddc_note_launches(1);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+int gm_cond(const GmState* S, const double* H, int mmax, double* kmax, cudaStream_t st, GmBatch B) {
     const int kk = std::min(mmax, GM_COND_MAX);
     const size_t smem = sizeof(double) * kk * kk;
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_cond, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(double) * GM_COND_MAX * GM_COND_MAX)));
-    k_cond<<<1, GM_COND_THREADS, smem, st>>>(S, H, kmax);
+    k_cond<<<dim3(1, 1, B.ncol), GM_COND_THREADS, smem, st>>>(S, H, kmax, B);
+    bddc_note_launches(1);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
+int gm_all_stopped(const GmState* S, int ncol, int* flag, cudaStream_t st) {
+    k_all_stopped<<<1, 256, 0, st>>>(S, ncol, flag);
+    bddc_note_launches(1);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+int vec_axpby_cols(double* y, long long ldy, const double* x, long long ldx, double a, double b, long long n,
+                   int ncol, cudaStream_t st) {
+    k_axpby_cols<<<dim3(grid_for(n), 1, ncol), 256, 0, st>>>(y, ldy, x, ldx, a, b, n);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
