@@ -72,7 +72,8 @@ typedef struct { double lo[3], hi[3]; } bddc_mesh;
 typedef struct { int nsub[3]; const int* elems_per_slab[3]; } bddc_partition;
 
 /* Coefficients (Sect. 2).  All arrays are FP64, in host or device memory as
- * `mem` says, and are copied at setup.
+ * `mem` says, and are copied at setup; bddc_setup rejects (BDDC_EINVAL) a
+ * nu <= 0 or non-finite, and non-finite beta, f, div(beta), c or beta_const.
  *   nu_elem   [nelem]      viscosity per element, > 0
  *   beta_node [3*nnodes]   velocity at the nodes (x,y,z interleaved) or NULL,
  *                          in which case beta_const is used everywhere
@@ -226,6 +227,15 @@ unsigned long long bddc_kernel_launches(void);
  * hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory).  Host buffers;
  * BDDC_ETIMEOUT if the bounded wait for the MMAs gave up. */
 int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, int K);
+
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * CTA runs the wait that the one-launch preconditioner apply uses on its
+ * completion counters, on a counter that nothing increments, with `limit`
+ * polls (1 .. 2^24, about 0.1 us each).  The wait must give up by itself:
+ * the call returns BDDC_ETIMEOUT (the expected outcome) with the device
+ * still usable, BDDC_OK if the wait ended otherwise, BDDC_EINVAL for a limit
+ * out of range.  Synchronous; allocates and frees a few bytes. */
+int bddc_wait_selftest(int limit);
 
 /* Kernel timer for roofline reporting: after bddc_kernel_timer(kind) every
  * launch of that kernel class (1 engine trailing update, 2 engine panel,

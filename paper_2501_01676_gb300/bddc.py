@@ -91,6 +91,7 @@ def lib():
     L.bddc_mlp_loss_grad.argtypes = [fp, vp, vp, ct.c_int, fp, fp, vp]
     L.bddc_mlp_train.argtypes = [fp, vp, vp, ct.c_int, ct.c_int, ct.c_float, fp, vp]
     L.bddc_tc_selftest.argtypes = [fp, fp, fp, ct.c_int, ct.c_int, ct.c_int]
+    L.bddc_wait_selftest.argtypes = [ct.c_int]
     L.bddc_kernel_timer.argtypes = [ct.c_int]
     L.bddc_kernel_timer_read.argtypes = [dp, ct.POINTER(ct.c_longlong), dp, dp]
     L.bddc_kernel_launches.argtypes = []
@@ -103,7 +104,7 @@ EXPORTED = ["bddc_default_opts", "bddc_setup", "bddc_apply", "bddc_schur_apply",
             "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_get_numbering", "bddc_get_schur",
             "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features", "bddc_kernel_launches",
             "bddc_apply_static", "bddc_kernel_timer", "bddc_kernel_timer_read", "bddc_mlp_forward",
-            "bddc_mlp_loss_grad", "bddc_mlp_train", "bddc_tc_selftest"]
+            "bddc_mlp_loss_grad", "bddc_mlp_train", "bddc_tc_selftest", "bddc_wait_selftest"]
 
 
 def tc_selftest(A, B, C, nr=128, nc=128, K=32):
@@ -346,7 +347,9 @@ class Solver:
                 lp = lh.ctypes.data
             rc = lib().bddc_gmres_solve(self.ctx, lp, u.ctypes.data, nrhs, MEM_HOST, ct.byref(st))
             check(rc, "bddc_gmres_solve")
-            return (u[0] if nrhs == 1 else u.T), st.as_dict()
+            out = st.as_dict()
+            out["rc"] = rc
+            return (u[0] if nrhs == 1 else u.T), out
         if load is None:
             u = torch.empty(self.ndof, dtype=torch.float64, device="cuda")
             rc = lib().bddc_gmres_solve(self.ctx, None, _ptr(u), 1, MEM_DEVICE, ct.byref(st))
@@ -360,7 +363,9 @@ class Solver:
             if nrhs > 1:
                 u = u.t().contiguous()
         check(rc, "bddc_gmres_solve")
-        return u, st.as_dict()
+        out = st.as_dict()
+        out["rc"] = rc
+        return u, out
 
     # ---- introspection -------------------------------------------------
     def edge_features(self):
@@ -405,3 +410,9 @@ class Solver:
                             k=k.value, Q=Q[:n.value * k.value].reshape(k.value, n.value).T,
                             lam=lam[:ne.value].copy()))
         return out
+
+
+def wait_selftest(limit):
+    """bddc_wait_selftest: the bounded wait on a counter nothing increments;
+    returns the library's code (BDDC_ETIMEOUT = -5 expected)."""
+    return int(lib().bddc_wait_selftest(int(limit)))

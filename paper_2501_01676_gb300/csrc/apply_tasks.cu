@@ -172,6 +172,29 @@ __device__ __forceinline__ void prefetch_item(const MT* pool, const GemvItem& it
     }
 }
 
+// Bounded wait of one thread until ctr[w] >= target.  Gives up when another
+// waiter has given up (abort flag) or after `limit` polls (~0.1 us each):
+// then it flags ERR_TIMEOUT_APPLY, raises the abort flag and returns false.
+__device__ bool ap_wait_ge(const int* ctr, int w, int target, int* abort_flag, int* err, long long limit) {
+    long long it = 0;
+    while (ld_acquire_i(ctr + w) < target) {
+        if (*(volatile int*)abort_flag) return false;
+        if (++it > limit) {
+            atomicOr(err, ERR_TIMEOUT_APPLY);
+            atomicExch(abort_flag, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// The wait above on a counter that nothing increments (host self-test of the
+// bounded waits): ends by itself after `limit` polls with the error flagged.
+__global__ void k_wait_selftest(int* ctr, int* err, long long limit) {
+    if (threadIdx.x == 0) ap_wait_ge(ctr, 0, 1, ctr + 1, err, limit);
+}
+
 template <class T>
 __global__ void __launch_bounds__(AP_THREADS) k_apply_tasks(const ApTask* __restrict__ tasks, int nres, int ntasks,
                                                            int nlocal, int ncoarse_ctas, int* ctr,
@@ -219,20 +242,7 @@ __global__ void __launch_bounds__(AP_THREADS) k_apply_tasks(const ApTask* __rest
                 const int w = q == 0 ? tk.w0 : tk.w1;
                 const int target = q == 0 ? tk.t0 : tk.t1;
                 if (w < 0 || s_abort) continue;
-                long long it = 0;
-                while (ld_acquire_i(ctr + w) < target) {
-                    if (*(volatile int*)(ctr + AP_CTR_ABORT)) {
-                        s_abort = 1;
-                        break;
-                    }
-                    if (++it > AP_WAIT_LIMIT) {
-                        atomicOr(err, ERR_TIMEOUT_APPLY);
-                        atomicExch(ctr + AP_CTR_ABORT, 1);
-                        s_abort = 1;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
+                if (!ap_wait_ge(ctr, w, target, ctr + AP_CTR_ABORT, err, AP_WAIT_LIMIT)) s_abort = 1;
             }
             __threadfence();
         }
@@ -290,3 +300,23 @@ template int apply_tasks_run<float>(const ApTask*, int, int, int, int, int*, int
 template int apply_tasks_run<double>(const ApTask*, int, int, int, int, int*, int, const double*, const double*,
                                      const double*, const int*, const int*, const double*, double*, int, int, int*,
                                      const int*, double, cudaStream_t);
+
+int wait_selftest_run(long long limit, int* timed_out) {
+    int* d = nullptr;
+    BDDC_CUDA_TRY(cudaMalloc(&d, 3 * sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0, 3 * sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>(d, d + 2, limit);
+        bddc_note_launches(1);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d + 2, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        bddc_set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
+        return BDDC_ECUDA;
+    }
+    *timed_out = (h & ERR_TIMEOUT_APPLY) ? 1 : 0;
+    return BDDC_OK;
+}

@@ -292,3 +292,34 @@ int stencil_residual(const HostMesh& hm, const double* S, const double* u, const
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Input check of the coefficient arrays (Sect. 2 assumes nu > 0)
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_validate(const double* __restrict__ nu, long long nelem, const double* __restrict__ beta,
+                           const double* __restrict__ f, const double* __restrict__ divb, long long nnodes,
+                           int* __restrict__ bad) {
+    int b = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nelem; e += stride)
+        if (!(nu[e] > 0.0) || !isfinite(nu[e])) b = 1;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnodes; q += stride) {
+        if (beta && (!isfinite(beta[3 * q]) || !isfinite(beta[3 * q + 1]) || !isfinite(beta[3 * q + 2]))) b = 1;
+        if (f && !isfinite(f[q])) b = 1;
+        if (divb && !isfinite(divb[q])) b = 1;
+    }
+    if (b) atomicOr(bad, 1);
+}
+}  // namespace
+
+int validate_coeffs_run(const double* nu, long long nelem, const double* beta, const double* f, const double* divb,
+                        long long nnodes, int* dflag, cudaStream_t st) {
+    BDDC_CUDA_TRY(cudaMemsetAsync(dflag, 0, sizeof(int), st));
+    const long long n = std::max(nelem, nnodes);
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1184);
+    k_validate<<<std::max(blocks, 1), 256, 0, st>>>(nu, nelem, beta, f, divb, nnodes, dflag);
+    bddc_note_launches(1);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}

@@ -234,6 +234,14 @@ struct ApTask {
 };
 template <class T>
 int apply_tasks_blocks();
+// One CTA runs the one-launch apply's bounded wait on a counter nothing
+// increments, with `limit` polls; *timed_out = 1 when it gave up as it must.
+int wait_selftest_run(long long limit, int* timed_out);
+// Device check of the coefficient arrays (nu > 0 and finite; beta, f, div beta
+// finite; NULL arrays are skipped): *flag_dev (device int) = 1 when one fails.
+// Asynchronous on st.
+int validate_coeffs_run(const double* nu, long long nelem, const double* beta, const double* f, const double* divb,
+                        long long nnodes, int* flag_dev, cudaStream_t st);
 // tasks: the restriction queue (nres items), the coarse queue (ntasks items),
 // then the local queue (nlocal items)
 template <class T>

@@ -2235,14 +2235,29 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
             return BDDC_EINVAL;
         }
     if (!k || !k->nu_elem) return BDDC_EINVAL;
-    if (k->mem == BDDC_MEM_HOST) {
-        for (int e = 0; e < hm.nelem; ++e)
-            if (!(k->nu_elem[e] > 0.0) || !std::isfinite(k->nu_elem[e])) return BDDC_EINVAL;
+    if (k->mem != BDDC_MEM_HOST && k->mem != BDDC_MEM_DEVICE) return BDDC_EINVAL;
+    if (!std::isfinite(k->c) || !std::isfinite(k->beta_const[0]) || !std::isfinite(k->beta_const[1]) ||
+        !std::isfinite(k->beta_const[2])) {
+        bddc_set_last_error("reaction and constant velocity must be finite", __FILE__, __LINE__);
+        return BDDC_EINVAL;
     }
     BDDC_TRY(copy_coeff(C, &C->nu, k->nu_elem, hm.nelem, k->mem));
     BDDC_TRY(copy_coeff(C, &C->beta, k->beta_node, 3 * (size_t)hm.nnodes, k->mem));
     BDDC_TRY(copy_coeff(C, &C->f, k->f_node, hm.nnodes, k->mem));
     BDDC_TRY(copy_coeff(C, &C->divb, k->divb_node, hm.nnodes, k->mem));
+    {
+        // the coefficient arrays (host or device) are checked on the device before any other work
+        int* vflag = nullptr;
+        BDDC_TRY(C->alloc(&vflag, 1));
+        BDDC_TRY(validate_coeffs_run(C->nu, hm.nelem, C->beta, C->f, C->divb, hm.nnodes, vflag, C->st));
+        int hv = 0;
+        BDDC_CUDA_TRY(cudaMemcpyAsync(&hv, vflag, sizeof(int), cudaMemcpyDeviceToHost, C->st));
+        BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
+        if (hv) {
+            bddc_set_last_error("nu must be positive and finite; beta, f and div(beta) finite", __FILE__, __LINE__);
+            return BDDC_EINVAL;
+        }
+    }
     for (int d = 0; d < 3; ++d) C->bconst[d] = k->beta_const[d];
     C->c = k->c;
     C->nG = (int)hm.gamma.size();
@@ -2554,6 +2569,13 @@ int bddc_tc_selftest(const float* A, const float* B, float* C, int nr, int nc, i
     }
     if (rc == BDDC_OK && herr) rc = BDDC_ETIMEOUT;
     return rc;
+}
+
+int bddc_wait_selftest(int limit) {
+    if (limit < 1 || limit > (1 << 24)) return BDDC_EINVAL;
+    int to = 0;
+    BDDC_TRY(wait_selftest_run(limit, &to));
+    return to ? BDDC_ETIMEOUT : BDDC_OK;
 }
 
 int bddc_kernel_timer(int kind) {
