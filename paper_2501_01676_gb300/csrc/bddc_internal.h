@@ -26,6 +26,11 @@
 
 void bddc_set_last_error(const char* msg, const char* file, int line);
 
+// Host table -> device, asynchronous on st: the bytes are copied into a pinned
+// staging arena of this host thread first (a copy from pageable memory would
+// synchronise the stream before it starts).
+int staged_upload(void* dev, const void* host, size_t bytes, cudaStream_t st);
+
 // Process-wide count of kernels launched by the library (launches recorded
 // while a stream is being captured are not counted; graph replays add their
 // kernel nodes).

@@ -118,6 +118,73 @@ inline double ms_since(std::chrono::steady_clock::time_point t0) {
 }
 }  // namespace
 
+// Pinned staging arena of the host tables uploaded during a setup, one per host
+// thread.  Space is handed out in order; an event recorded after the last copy
+// from the arena tells when all of it has been consumed: the arena restarts from
+// the beginning only after that event (at the start of a setup, or when it is
+// full), and grows when one table does not fit.
+namespace {
+struct PinnedArena {
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+    cudaEvent_t last = nullptr;
+    bool pending = false;
+    ~PinnedArena() {
+        if (last) cudaEventDestroy(last);
+        if (base) cudaFreeHost(base);
+    }
+};
+thread_local PinnedArena g_stage;
+
+int stage_reset() {
+    PinnedArena& A = g_stage;
+    if (A.pending) BDDC_CUDA_TRY(cudaEventSynchronize(A.last));
+    A.pending = false;
+    A.used = 0;
+    return BDDC_OK;
+}
+
+int stage_pinned(size_t bytes, cudaStream_t st, char** out) {
+    (void)st;
+    PinnedArena& A = g_stage;
+    const size_t need = (bytes + 255) & ~size_t(255);
+    if (A.used + need > A.cap) {
+        BDDC_TRY(stage_reset());
+        if (need > A.cap) {
+            if (A.base) cudaFreeHost(A.base);
+            A.base = nullptr;
+            A.cap = std::max(need, std::max(2 * A.cap, size_t(32) << 20));
+            if (cudaHostAlloc((void**)&A.base, A.cap, cudaHostAllocPortable) != cudaSuccess) {
+                A.base = nullptr;
+                A.cap = 0;
+                bddc_set_last_error("pinned staging memory", __FILE__, __LINE__);
+                return BDDC_ENOMEM;
+            }
+        }
+    }
+    *out = A.base + A.used;
+    A.used += need;
+    return BDDC_OK;
+}
+
+int stage_done(cudaStream_t st) {
+    PinnedArena& A = g_stage;
+    if (!A.last) BDDC_CUDA_TRY(cudaEventCreateWithFlags(&A.last, cudaEventDisableTiming));
+    BDDC_CUDA_TRY(cudaEventRecord(A.last, st));
+    A.pending = true;
+    return BDDC_OK;
+}
+}  // namespace
+
+int staged_upload(void* dev, const void* host, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return BDDC_OK;
+    char* h = nullptr;
+    BDDC_TRY(stage_pinned(bytes, st, &h));
+    memcpy(h, host, bytes);
+    BDDC_CUDA_TRY(cudaMemcpyAsync(dev, h, bytes, cudaMemcpyHostToDevice, st));
+    return stage_done(st);
+}
+
 struct bddc_ctx {
     HostMesh hm;
     bddc_opts o;
@@ -167,11 +234,19 @@ struct bddc_ctx {
         *p = (T*)q;
         return BDDC_OK;
     }
+    // Host tables go to the device through a pinned staging arena: a copy from
+    // pageable memory would synchronise the stream first (the host would wait for
+    // all queued GPU work before every table), a copy from pinned memory does not.
     template <class T>
     int upload(T** p, const std::vector<T>& v) {
         BDDC_TRY(alloc(p, v.size()));
-        if (!v.empty()) BDDC_CUDA_TRY(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-        return BDDC_OK;
+        if (v.empty()) return BDDC_OK;
+        const size_t b = v.size() * sizeof(T);
+        char* h = nullptr;
+        BDDC_TRY(stage_pinned(b, st, &h));
+        memcpy(h, v.data(), b);
+        BDDC_CUDA_TRY(cudaMemcpyAsync(*p, h, b, cudaMemcpyHostToDevice, st));
+        return stage_done(st);
     }
 
     // coefficients
@@ -298,25 +373,30 @@ static int change_basis(bddc_ctx* C, const std::vector<TBlock>& tb, const int* d
     std::vector<std::vector<HB>> groups;
     std::vector<const TBlock*> head;
     std::vector<int> gid(tb.size());
+    std::unordered_map<const void*, int> group_of;
+    std::vector<std::vector<int>> members;
     for (size_t i = 0; i < tb.size(); ++i) {
         int g = -1;
-        if (!head.empty() && head.back()->dst == tb[i].dst) g = (int)head.size() - 1;
-        else {
-            for (size_t h = 0; h < head.size(); ++h)
-                if (head[h]->dst == tb[i].dst) g = (int)h;
+        if (!head.empty() && head.back()->dst == tb[i].dst) {
+            g = (int)head.size() - 1;
+        } else {
+            auto f = group_of.find(tb[i].dst);
+            if (f != group_of.end()) g = f->second;
         }
         if (g < 0) {
             g = (int)head.size();
             head.push_back(&tb[i]);
             groups.emplace_back();
+            members.emplace_back();
+            group_of[tb[i].dst] = g;
         }
         gid[i] = g;
+        members[g].push_back((int)i);
     }
     int nmax = 1;
     for (size_t g = 0; g < groups.size(); ++g) {
         std::vector<int> ids;
-        for (size_t i = 0; i < tb.size(); ++i) {
-            if (gid[i] != (int)g) continue;
+        for (int i : members[g]) {
             const TBlock& B = tb[i];
             if (B.identity) {
                 for (int l = 0; l < B.n; ++l) ids.push_back(idxv[B.pos_off + l]);
@@ -2227,6 +2307,7 @@ static int copy_coeff(bddc_ctx* C, double** dst, const double* src, size_t n, in
 
 static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, const bddc_partition* part) {
     const auto t0 = std::chrono::steady_clock::now();
+    BDDC_TRY(stage_reset());
     BDDC_TRY(build_host_mesh(mesh, part, C->hm));
     HostMesh& hm = C->hm;
     for (const SubInfo& S : hm.sub)

@@ -1157,7 +1157,7 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         memcpy(host.data() + o1, meta.data(), mb);
         unsigned char* dev = nullptr;
         BDDC_CUDA_TRY(cudaMallocAsync((void**)&dev, o2 + fb, st));
-        BDDC_CUDA_TRY(cudaMemcpyAsync(dev, host.data(), o2, cudaMemcpyHostToDevice, st));
+        BDDC_TRY(staged_upload(dev, host.data(), o2, st));
         int* flags = reinterpret_cast<int*>(dev + o2);
         BDDC_CUDA_TRY(cudaMemsetAsync(flags, 0, fb, st));
         const size_t sm = task_smem<T>();
