@@ -866,11 +866,20 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     __shared__ unsigned char done[256];
     T* w = work_off >= 0 ? shm + work_off : (T*)J.work;   // workspace in shared memory when it fits
     const int nn = n * n;
-    T *Si = w, *Sj = w + nn, *Ssum = w + 2 * nn, *Dij = w + 3 * nn /* n x 2n */;
-    T *BF = w + 5 * nn, *Bti = w + 6 * nn, *Btj = w + 7 * nn, *Bt = w + 8 * nn;
-    T *T1 = w + 9 * nn, *T2 = w + 10 * nn, *V = w + 11 * nn, *W1 = w + 12 * nn,
-           *W2 = w + 13 * nn, *Cm = w + 14 * nn, *vb = w + 15 * nn, *PS = w + 16 * nn /* 4 nn */;
-    T* aux = w + 20 * nn;   // 3n
+    // Workspace of 8 n^2 elements (units of n^2), reused as the steps go:
+    //   [0,2) Dij = [D^(i) | D^(j)] (kept to the end)   [2,3) B_F (kept)
+    //   deluxe:      [3,4) S_FF^(i)  [4,5) S_FF^(j)  [5,6) their sum
+    //   B_F:         [3,4) sym S^(i) [4,5) sym S^(j) [5,6) product scratch
+    //   parallel sum [3,7) the 2n x 2n matrix        [7,8) B~_F (kept)
+    //   pencil:      [3,4) [4,5) scratch  [5,6) eigenvectors
+    //   basis:       [3,4) constraint vectors  [4,5) reflectors  [6,7) Q
+    T *Dij = w, *BF = w + 2 * nn, *Bt = w + 7 * nn;
+    T *Si = w + 3 * nn, *Sj = w + 4 * nn, *Ssum = w + 5 * nn;
+    T *T1 = Si, *T2 = Sj, *W1 = w + 5 * nn;
+    T* PS = w + 3 * nn;  // 4 nn
+    T *P1 = w + 3 * nn, *P2 = w + 4 * nn, *V = w + 5 * nn;
+    T *Cm = w + 3 * nn, *vb = w + 4 * nn, *Qo = w + 6 * nn;
+    T* aux = w + 8 * nn;   // 3n
     // gather S_FF blocks
     CTA_FOR_2D(a, b, n, n) {
         Si[a * n + b] = J.Si[(long long)J.pi[a] * J.ldi + J.pi[b]];
@@ -885,12 +894,9 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     }
     bar();
     lu_solve(Ssum, n, Dij, 2 * n, n, 2 * n, err);              // [D^(i) | D^(j)]
-    // B_F = D_j^T B_FF^(i) D_j + D_i^T B_FF^(j) D_i   (B_FF = sym(S_FF))
-    CTA_FOR_2D(a, b, n, n) {
-        T1[a * n + b] = (T)0.5 * (Si[a * n + b] + Si[b * n + a]);
-        T2[a * n + b] = (T)0.5 * (Sj[a * n + b] + Sj[b * n + a]);
-    }
-    bar();
+    // B_F = D_j^T B_FF^(i) D_j + D_i^T B_FF^(j) D_i   (B_FF = sym(S_FF), in place)
+    symmetrize(T1, n, n);
+    symmetrize(T2, n, n);
     const T* Di = Dij;
     const T* Dj = Dij + n;
     mm(T1, n, false, Dj, 2 * n, false, W1, n, n, n, n, (T)1, (T)0);
@@ -898,18 +904,14 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     mm(T2, n, false, Di, 2 * n, false, W1, n, n, n, n, (T)1, (T)0);
     mm(Di, 2 * n, true, W1, n, false, BF, n, n, n, n, (T)1, (T)1);
     symmetrize(BF, n, n);
-    // parallel sum B~_i : B~_j = B~_i - B~_i (B~_i + B~_j)^+ B~_i
-    copy_mat(J.Bti, J.ldbi, Bti, n, n, n);
-    copy_mat(J.Btj, J.ldbj, Btj, n, n, n);
-    symmetrize(Bti, n, n);
-    symmetrize(Btj, n, n);
+    // parallel sum B~_i : B~_j = B~_i - B~_i (B~_i + B~_j)^+ B~_i (the symmetric
+    // parts of the two Schur complements, read from global memory)
     const int n2 = 2 * n;
     CTA_FOR_2D(a, b, n2, n2) {
-        T v;
-        if (a < n && b < n) v = Bti[a * n + b];
-        else if (a < n) v = Bti[a * n + b - n];
-        else if (b < n) v = Bti[(a - n) * n + b];
-        else v = Bti[(a - n) * n + b - n] + Btj[(a - n) * n + b - n];
+        const int ra = a < n ? a : a - n, rb = b < n ? b : b - n;
+        T v = (T)0.5 * ((T)J.Bti[(long long)ra * J.ldbi + rb] + (T)J.Bti[(long long)rb * J.ldbi + ra]);
+        if (a >= n && b >= n)
+            v += (T)0.5 * ((T)J.Btj[(long long)ra * J.ldbj + rb] + (T)J.Btj[(long long)rb * J.ldbj + ra]);
         PS[a * n2 + b] = v;        // order [B~_i, B~_i; B~_i, B~_i + B~_j]: eliminate the tail
     }
     bar();
@@ -917,9 +919,10 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
     copy_mat(PS, n2, Bt, n, n, n);
     symmetrize(Bt, n, n);
     int k = 0;
+    T* T1o = Qo;                   // the constraint basis Q (identity when nothing is selected)
     if (J.mode == 0) {
         const T sth = (T)(J.theta / (1.0 + J.theta) - Tol<T>::slack);
-        int r = sigma_pencil(BF, Bt, n, Ash, Vsh, np, ldj, W1, W2, aux, V, cs, sn, pp, qq, order, err, err + 1, sth);
+        int r = sigma_pencil(BF, Bt, n, Ash, Vsh, np, ldj, P1, P2, aux, V, cs, sn, pp, qq, order, err, err + 1, sth);
         __shared__ int nsel_s;
         if (threadIdx.x == 0) {
             int c = 0;
@@ -937,21 +940,21 @@ __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, i
         if (s > 0) {
             // Cm = B_F V(:, 0..s)   (n x s)
             mm(BF, n, false, V, r, false, Cm, s, n, s, n, (T)1, (T)0);
-            k = qr_basis(Cm, n, s, T1, vb, aux + n, aux + 2 * n);
+            k = qr_basis(Cm, n, s, T1o, vb, aux + n, aux + 2 * n);
         } else {
-            for (int q = threadIdx.x; q < nn; q += GT) T1[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
+            for (int q = threadIdx.x; q < nn; q += GT) T1o[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
             bar();
         }
     } else {
-        for (int q = threadIdx.x; q < nn; q += GT) T1[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
+        for (int q = threadIdx.x; q < nn; q += GT) T1o[q] = (q % (n + 1) == 0) ? (T)1 : (T)0;
         if (threadIdx.x == 0) *J.neig = 0;
         bar();
         k = J.mode == 1 ? n : 0;
     }
     // outputs: Q (row-major n x n), D^(i) Q, D^(j) Q
-    for (int q = threadIdx.x; q < nn; q += GT) J.Q[q] = T1[q];
-    mm(Di, 2 * n, false, T1, n, false, J.DQi, n, n, n, n, (T)1, (T)0);
-    mm(Dj, 2 * n, false, T1, n, false, J.DQj, n, n, n, n, (T)1, (T)0);
+    for (int q = threadIdx.x; q < nn; q += GT) J.Q[q] = T1o[q];
+    mm(Di, 2 * n, false, T1o, n, false, J.DQi, n, n, n, n, (T)1, (T)0);
+    mm(Dj, 2 * n, false, T1o, n, false, J.DQj, n, n, n, n, (T)1, (T)0);
     if (threadIdx.x == 0) *J.k = k;
 }
 
@@ -1186,7 +1189,7 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
 
 }  // namespace
 
-size_t face_work_doubles(int n) { return (size_t)20 * n * n + 3 * n + 64; }
+size_t face_work_doubles(int n) { return (size_t)8 * n * n + 3 * n + 64; }
 size_t edge_work_doubles(int n, int m, int nH) {
     size_t nw = (size_t)(m - 1) * n, mn = (size_t)m * n, nz = mn + nH;
     return (size_t)n * n * (3 + m) + (size_t)n * mn * (1 + m) + 6 * nw * nw + 2 * nz * nz +
