@@ -355,7 +355,10 @@ static int run_engine(bddc_ctx* C, const std::vector<EngItem<T>>& items) {
         hn[i] = items[i].n;
         hk[i] = items[i].k;
     }
-    const int kind = C->o.precision == BDDC_PREC_BF16 ? TC_BF16 : (C->o.tensor_cores ? TC_SPLIT_TF32 : TC_NONE);
+    int kind = C->o.precision == BDDC_PREC_BF16 ? TC_BF16 : (C->o.tensor_cores ? TC_SPLIT_TF32 : TC_NONE);
+    // the tensor-core tasks stage rows by 16-byte copies: 16-byte aligned matrices and rows
+    for (auto& it : items)
+        if ((it.ld & 3) != 0 || (reinterpret_cast<uintptr_t>(it.a) & 15) != 0) kind = TC_NONE;
     return engine_run<T>(d, (int)items.size(), maxn, maxk, scr, C->err, C->st, hn.data(), hk.data(), kind);
 }
 
@@ -1155,7 +1158,7 @@ static int setup_impl(bddc_ctx* C) {
             long long etot = 0;
             for (size_t ei = 0; ei < edges.size(); ++ei)
                 if (!C->edge_skipped[ei])
-                    for (int s : hm.ent[edges[ei]].subs) etot += (long long)nkeep[s] * nkeep[s];
+                    for (int s : hm.ent[edges[ei]].subs) etot += (long long)nkeep[s] * r4(nkeep[s]);
             BDDC_TRY(C->alloc(&EB, etot));
             etot = 0;
             for (size_t ei = 0; ei < edges.size(); ++ei) {
@@ -1210,14 +1213,16 @@ static int setup_impl(bddc_ctx* C) {
                     int n = (int)perm.size();
                     int off = (int)gidxv.size();
                     gidxv.insert(gidxv.end(), perm.begin(), perm.end());
-                    gj.push_back(GatherJob{W64 + w64off[s], nkeep[s], n, off, 0, EB + etot, n, nullptr});
-                    items.push_back(EngItem<T>{EB + etot, n, nel, n});
-                    ito[ei].push_back(etot + (long long)nel * n + nel);
-                    itn[ei].push_back(n);
+                    // rows padded to a multiple of 4 elements (16-byte aligned rows for the engine)
+                    const int ldn = r4(n);
+                    gj.push_back(GatherJob{W64 + w64off[s], nkeep[s], n, off, 0, EB + etot, ldn, nullptr});
+                    items.push_back(EngItem<T>{EB + etot, n, nel, ldn});
+                    ito[ei].push_back(etot + (long long)nel * ldn + nel);
+                    itn[ei].push_back(ldn);
                     hsz[ei].push_back((int)hk.size());
                     hoff[ei].push_back((int)hmv.size());
                     hmv.insert(hmv.end(), hk.begin(), hk.end());
-                    etot += (long long)n * n;
+                    etot += (long long)n * ldn;
                 }
             }
             int* d_gi;

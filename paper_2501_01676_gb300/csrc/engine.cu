@@ -23,11 +23,14 @@
 //             columns at a time (one warp factors the 32 x 32 sub-block in
 //             registers, one thread per row / column solves the strips, a
 //             register-tiled rank-32 update), writes L11\U11 back and the pivot
-//             reciprocals to a scratch;
-//   strip     L21 = M21 U11^{-1} in 64-row chunks and U12 = L11^{-1} M12 in
-//             64-column chunks (the latter solved transposed, so both run the
-//             same code: per 32-column block a thread-per-row substitution, then a
-//             right-looking update of the later columns);
+//             reciprocals to a scratch; on the tensor-core path it also forms
+//             U11^{-1} and L11^{-1} (packed in one NB x NB scratch block);
+//   strip     L21 = M21 U11^{-1} and U12 = L11^{-1} M12: on the tensor-core path
+//             as products with the inverses on 128-row / -column chunks; on the
+//             CUDA cores by substitution in 64-row / -column chunks (U12 solved
+//             transposed, so both run the same code: per 32-column block a
+//             thread-per-row substitution, then a right-looking update of the
+//             later columns);
 //   update    M22 -= L21 U12 in TILE x TILE tiles: on the tensor cores (tcgen05,
 //             split TF32, FP32 path by default) or on the CUDA cores (register
 //             tiles, K staged through shared memory in chunks of 32).
@@ -192,9 +195,144 @@ __device__ __forceinline__ void diag_rank32(T* __restrict__ D, int LD, int b0, i
 // Three barriers per stage instead of one per pivot; the loops stay compact
 // (this body runs once per launch: straight-line code would be fetched from
 // beyond the instruction cache).
-template <class T, int NB>
+// In-place inverses of the factors of the w x w diagonal block in shared memory
+// (after its LU; w <= 4 * 32, leading dimension LD): afterwards the upper
+// triangle with the diagonal holds U11^{-1} and the strict lower triangle the
+// strict lower part of L11^{-1} (whose diagonal is 1).  Blocked by 32:
+//   (1) the diagonal blocks: warp 2b inverts U_bb, warp 2b + 1 the unit lower
+//       L_bb, lane c computing column c in registers (U_bb^{-1} from the pivot
+//       reciprocals dinv);
+//   (2) the off-diagonal blocks from the block rows of X U = I and Y L = I,
+//       X_ab = -(sum_{a <= c < b} X_ac U_cb) X_bb   (a < b),
+//       Y_ab = -(sum_{b < c <= a} Y_ac L_cb) Y_bb   (a > b),
+//       one block column per step and factor (X: columns left to right, Y: right
+//       to left), all blocks of the column at once: the products read only blocks
+//       of finished columns and the column's own factor blocks, which are
+//       overwritten after a barrier.  Threads 0..127 take X, 128..255 Y, each 8
+//       entries per block (row tid / 4, columns 8 (tid % 4) ..); the sums and a
+//       masked copy of the column's diagonal inverse block go through tmp
+//       (8 blocks of 32 x 33).
+// The padding of the last 32-block is zeroed first, so that no stale value
+// enters a product.
+template <class T>
+__device__ void diag_inverse(T* __restrict__ D, int LD, int w, const T* __restrict__ dinv, T* __restrict__ tmp,
+                             int t) {
+    const int nbk = (w + IB - 1) / IB, W32 = nbk * IB;
+    for (int q = t; q < W32 * W32; q += DIAG_THREADS) {
+        const int r = q / W32, c = q - r * W32;
+        if (r >= w || c >= w) D[r * LD + c] = (T)0;
+    }
+    __syncthreads();
+    const int wid = t >> 5, lane = t & 31;
+    if ((wid >> 1) < nbk) {
+        const int b0 = IB * (wid >> 1), bw = min(IB, w - b0);
+        T* Bk = D + b0 * LD + b0;
+        T x[IB];
+        if ((wid & 1) == 0) {
+#pragma unroll
+            for (int i = IB - 1; i >= 0; --i) {
+                T s = (T)0;
+#pragma unroll
+                for (int l = i + 1; l < IB; ++l) s += Bk[i * LD + l] * x[l];
+                const T di = i < bw ? dinv[b0 + i] : (T)0;
+                x[i] = i == lane ? di : (i < lane ? -s * di : (T)0);
+            }
+            __syncwarp();
+            if (lane < bw)
+#pragma unroll
+                for (int i = 0; i < IB; ++i)
+                    if (i <= lane) Bk[i * LD + lane] = x[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < IB; ++i) {
+                T s = (T)0;
+#pragma unroll
+                for (int l = 0; l < i; ++l) s += Bk[i * LD + l] * x[l];
+                x[i] = i == lane ? (T)1 : ((i > lane && i < bw) ? -s : (T)0);
+            }
+            __syncwarp();
+            if (lane < bw)
+#pragma unroll
+                for (int i = 0; i < IB; ++i)
+                    if (i > lane && i < bw) Bk[i * LD + lane] = x[i];
+        }
+    }
+    __syncthreads();
+    // off-diagonal blocks from X U = I and Y L = I, one block column per step and
+    // factor, all its blocks at once (reads of the column's factor blocks precede
+    // the writes of its inverse blocks):
+    //   X_ab = -(sum_{a <= c < b} X_ac U_cb) X_bb   (a < b, columns b = 1 .. nbk-1),
+    //   Y_ab = -(sum_{b < c <= a} Y_ac L_cb) Y_bb   (a > b, columns b = nbk-2 .. 0)
+    const bool up = t < DIAG_THREADS / 2;
+    const int tu = up ? t : t - DIAG_THREADS / 2;
+    const int r = tu >> 2, j0 = (tu & 3) * 8;
+    constexpr int BS = IB * (IB + 1);
+    T* Tb = tmp + (up ? 0 : 4 * BS);          // up to 3 product blocks and the masked diagonal block
+    T* Db = Tb + 3 * BS;
+#pragma unroll 1
+    for (int s = 0; s + 1 < nbk; ++s) {
+        const int b = up ? s + 1 : nbk - 2 - s;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            const int j = j0 + jj;
+            const T v = D[(IB * b + r) * LD + IB * b + j];
+            Db[r * (IB + 1) + j] = up ? (r <= j ? v : (T)0) : (r > j ? v : (r == j ? (T)1 : (T)0));
+        }
+#pragma unroll 1
+        for (int q = 0; q <= s; ++q) {
+            const int a = up ? q : b + 1 + q;
+            const int c0 = up ? a : b + 1, c1 = up ? b - 1 : a;
+            T acc[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) acc[jj] = (T)0;
+#pragma unroll 1
+            for (int c = c0; c <= c1; ++c) {
+                const T* F = D + (IB * a + r) * LD + IB * c;    // X_ac / Y_ac, row r
+                const T* G = D + (IB * c) * LD + IB * b + j0;   // U_cb / L_cb
+                if (c == a) {
+                    // the diagonal inverse block: X_aa upper with its diagonal, Y_aa unit lower
+#pragma unroll 4
+                    for (int k = 0; k < IB; ++k) {
+                        T f = F[k];
+                        f = up ? (k >= r ? f : (T)0) : (k < r ? f : (k == r ? (T)1 : (T)0));
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) acc[jj] += f * G[k * LD + jj];
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = 0; k < IB; ++k) {
+                        const T f = F[k];
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) acc[jj] += f * G[k * LD + jj];
+                    }
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) Tb[q * BS + r * (IB + 1) + j0 + jj] = acc[jj];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int q = 0; q <= s; ++q) {
+            const int a = up ? q : b + 1 + q;
+            T acc[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) acc[jj] = (T)0;
+#pragma unroll 4
+            for (int k = 0; k < IB; ++k) {
+                const T f = Tb[q * BS + r * (IB + 1) + k];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) acc[jj] += f * Db[k * (IB + 1) + j0 + jj];
+            }
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) D[(IB * a + r) * LD + IB * b + j0 + jj] = -acc[jj];
+        }
+        __syncthreads();
+    }
+}
+
+template <class T, int NB, bool INV = false>
 __device__ __noinline__ void diag_body(const EngItem<T>& it, int p, T* __restrict__ out, int* __restrict__ err,
-                          unsigned char* dsm) {
+                          unsigned char* dsm, T* __restrict__ inv = nullptr) {
     static_assert(NB - IB <= DIAG_THREADS / 2, "one thread per strip row / column");
     const int w = min(NB, it.k - p);
     const long long ld = it.ld;
@@ -281,6 +419,14 @@ __device__ __noinline__ void diag_body(const EngItem<T>& it, int p, T* __restric
     if (lc < w)
 #pragma unroll 4
         for (int r = lr; r < w; r += RPI) A[r * ld + lc] = D[r * LD + lc];
+    if constexpr (INV) {
+        // the factors' inverses for the strips' tensor-core products, NB x NB row-major
+        __syncthreads();
+        diag_inverse<T>(D, LD, w, dinv, Ut, t);
+        if (lc < w)
+#pragma unroll 4
+            for (int r = lr; r < w; r += RPI) inv[r * NB + lc] = D[r * LD + lc];
+    }
 }
 
 template <class T, int NB>
@@ -700,144 +846,198 @@ size_t trsm_smem() {
 template <class T>
 size_t diag_smem() {
     constexpr int NB = EngCfg<T>::NB;
-    return sizeof(T) * ((size_t)NB * (NB + 1) + NB + 2 * IB * TS);
+    // the LU's shifted triangle copies, then the inverse's 8 blocks of 32 x 33, share one area
+    return sizeof(T) * ((size_t)NB * (NB + 1) + NB + std::max(2 * IB * TS, 8 * IB * (IB + 1)));
 }
 
-// M22 -= L21 U12 on one 128 x 128 tile on the tensor cores (tcgen05, split TF32,
-// FP32 accumulation in tensor memory), inside the persistent task kernel.  The
-// CTA holds 128 tensor-memory columns (the accumulator) and one mbarrier for its
-// whole life; nphase counts the mbarrier phases completed so far.  Per K-chunk
-// of 32: the chunk's operands (loaded into registers while the previous chunk's
-// MMAs run) are split into TF32 hi / lo parts and stored in the K-major
-// core-matrix layout (a warp's 16-byte stores cover whole 128-byte rows of core
-// matrices: no bank conflicts), one thread issues the 12 MMAs and commits them to
-// the mbarrier.  The epilogue reads the accumulator (warp w: rows 32 (w % 4) ..,
-// columns 64 (w / 4) ..), turns each 32 x 32 block around in shared memory and
-// subtracts it from the tile row by row (coalesced); the tile's lines were
-// prefetched into L2 when the task started.  Returns false if a bounded wait
-// expired (the error is flagged).
-template <int NB, int KIND>
-__device__ __noinline__ bool tc_tile_body(const EngItem<float>& it, int p, int ti, int tj, unsigned char* smem, uint32_t tmem,
-                             uint32_t mbar, uint32_t& nphase, int* __restrict__ err) {
+// Shared-memory layout of the tensor-core products: the TF32 hi / lo operand
+// parts of one K-chunk of PK = 16 (K-major core matrices: 8 rows x 16 bytes, the
+// 8-row groups PK / 4 core matrices apart), then NSTG raw FP32 stages filled by
+// cp.async: A as 128 rows x PK (row stride RA floats: conflict-free 16-byte
+// reads) and B as PK rows of a 16-byte aligned window of RB columns (the block's
+// first column sits delta = 0..3 floats into it).
+namespace tcp {
+constexpr int PK = 16, NSTG = 4;
+constexpr int RA = PK + 4, RB = 132;
+constexpr int PART = 128 * PK * 4;                         // bytes of one hi / lo operand part
+constexpr int RAW = (128 * RA + PK * RB) * 4;              // bytes of one raw stage
+constexpr int SMEM = 4 * PART + NSTG * RAW;
+__device__ __forceinline__ int cm(int row, int k) {
+    return ((row >> 3) * (PK / 4) + (k >> 2)) * tcx::CORE_BYTES + (row & 7) * 16 + (k & 3) * 4;
+}
+}  // namespace tcp
+
+// One product on the tensor cores (tcgen05, FP32 accumulation in tensor memory),
+// inside the persistent task kernel:
+//   C -= A B   (AM = BM = 0: the trailing update M22 -= L21 U12 of one tile), or
+//   C  = A B   (the strips: L21 = M21 U11^{-1} with BM = 1, U12 = L11^{-1} M12
+//               with AM = 1, in place: every operand load of the block precedes
+//               the epilogue's stores),
+// on a rows x cols <= 128 x 128 block, K <= 128.  A is rows x K at Ap (element
+// (r, k) at Ap[r lda + k]), B is K x cols at Bp (element (k, c) at Bp[k ldb + c]);
+// AM = 1 reads A as a unit lower triangle (its strict lower part, 1 on the
+// diagonal), BM = 1 reads B as an upper triangle with its diagonal (the packed
+// inverses of the diagonal task).  Ap and the rows of A are 16-byte aligned (lda
+// a multiple of 4), so is ldb; Bp may sit 0..3 floats past an aligned address.
+//
+// Pipeline: the operands move global -> shared memory by 16-byte cp.async copies
+// (L2 only) in chunks of PK along K, NSTG chunks in flight; per chunk the threads
+// split the raw values into TF32 hi / lo parts (KIND = split TF32: hi*hi +
+// hi*lo + lo*hi, about FP32 accuracy) or round them to BF16, in the K-major
+// core-matrix layout, and one thread issues the MMAs and commits them to the
+// mbarrier (bounded wait).  The CTA holds 128 tensor-memory columns (the
+// accumulator) and the mbarrier for its whole life; nphase counts the mbarrier
+// phases completed so far.  The epilogue reads the accumulator (warp w: rows
+// 32 (w % 4) .., columns 64 (w / 4) ..), turns each 32 x 32 block around in shared
+// memory and stores (or subtracts) it row by row (coalesced); for C -= A B the
+// block's lines were prefetched into L2 when the task started.  Returns false if
+// a bounded wait expired (the error is flagged).
+template <int KIND, int AM, int BM>
+__device__ __noinline__ bool tc_prod_body(const float* __restrict__ Ap, long long lda, const float* __restrict__ Bp,
+                                          long long ldb, float* __restrict__ Cp, long long ldc, int rows, int cols,
+                                          int K, unsigned char* smem, uint32_t tmem, uint32_t mbar, uint32_t& nphase,
+                                          int* __restrict__ err) {
     static_assert(KIND == TC_SPLIT_TF32 || KIND == TC_BF16, "operand kind");
     using namespace tcx;
-    static_assert(NB == 128, "one 128 x 128 MMA tile per task");
-    const int w = min(NB, it.k - p);
-    const int n = it.n;
-    const long long ld = it.ld;
-    const int m0 = p + w;
-    const int r0 = m0 + ti * 128, c0 = m0 + tj * 128;
-    if (r0 >= n || c0 >= n) return true;
-    const int rows = min(128, n - r0), cols = min(128, n - c0);
-    float* A = it.a;
+    using namespace tcp;
+    constexpr bool SUB = AM == 0 && BM == 0;
+    if (rows <= 0 || cols <= 0 || K <= 0) return true;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    constexpr int OPB = 128 * KMAX * 4;       // bytes of one operand part
     unsigned char* a_hi = smem;
-    unsigned char* a_lo = smem + OPB;
-    unsigned char* b_hi = smem + 2 * OPB;
-    unsigned char* b_lo = smem + 3 * OPB;
-    {
-        // the tile's lines into L2 now: the epilogue reads them after the K loop
+    unsigned char* a_lo = smem + PART;
+    unsigned char* b_hi = smem + 2 * PART;
+    unsigned char* b_lo = smem + 3 * PART;
+    float* raw0 = reinterpret_cast<float*>(smem + 4 * PART);
+    if constexpr (SUB) {
+        // the block's lines into L2 now: the epilogue reads them after the K loop
         for (int q = t; q < rows * 5; q += UPD_THREADS) {
             const int r = q / 5, l = q - r * 5;
             const int c = min(l * 32, cols - 1);
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (long long)(r0 + r) * ld + c0 + c));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(Cp + (long long)r * ldc + c));
         }
     }
-    const bool vec = (ld & 3) == 0 && (reinterpret_cast<unsigned long long>(A) & 15) == 0;
-    // register staging: A part (row, 4 consecutive k) x 4, B part (n, k) x 16
-    float av[4][4], bv[16];
-    auto load = [&](int k0) {
-        const int kw = min(KMAX, w - k0);
+    const int delta = (int)((reinterpret_cast<unsigned long long>(Bp) >> 2) & 3);
+    const float* Bw = Bp - delta;                  // 16-byte aligned window origin
+    const int nk = (K + PK - 1) / PK;
+    // raw stage of chunk kc: A 128 x 4 groups, B PK x (RB / 4) groups of 16 bytes
+    auto issue = [&](int kc) {
+        float* ra = raw0 + (kc % NSTG) * (RAW / 4);
+        float* rb = ra + 128 * RA;
+        const int k0 = kc * PK;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
             const int q = t + u * UPD_THREADS;
-            const int row = (q >> 6) * 8 + (q & 7), k4 = ((q >> 3) & 7) * 4;
-            const float* src = A + (long long)(r0 + min(row, rows - 1)) * ld + p + k0 + k4;
-            if (vec && k4 + 4 <= kw) {
-                const float4 v = __ldcg(reinterpret_cast<const float4*>(src));
-                av[u][0] = v.x; av[u][1] = v.y; av[u][2] = v.z; av[u][3] = v.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) av[u][e] = k4 + e < kw ? __ldcg(src + e) : 0.f;
-            }
-            if (row >= rows) av[u][0] = av[u][1] = av[u][2] = av[u][3] = 0.f;
+            const int row = q & 127, g = q >> 7;
+            const int kk = k0 + 4 * g;
+            const int bytes = row < rows ? max(0, min(4, K - kk)) * 4 : 0;
+            cp_async16(ra + row * RA + 4 * g, bytes ? Ap + (long long)row * lda + kk : Ap, bytes);
         }
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int q = t + u * UPD_THREADS;
-            const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
-            bv[u] = (k < kw && nn < cols) ? __ldcg(A + (long long)(p + k0 + k) * ld + c0 + nn) : 0.f;
+        for (int q = t; q < PK * (RB / 4); q += UPD_THREADS) {
+            const int kr = q / (RB / 4), g = q - kr * (RB / 4);
+            const int c = 4 * g - delta;           // block column of the group's first float
+            const int bytes = k0 + kr < K ? max(0, min(4, cols - c)) * 4 : 0;
+            cp_async16(rb + kr * RB + 4 * g, bytes ? Bw + (long long)(k0 + kr) * ldb + 4 * g : Bp, bytes);
         }
     };
-    auto store = [&]() {
-        if constexpr (KIND == TC_BF16) {
-            // one BF16 operand each: A (row, 4 k) as one 8-byte store, B element by element
+    // split of chunk kc into the operand parts: thread q -> (row / column q % 128, k group q / 128)
+    auto convert = [&](int kc) {
+        const float* ra = raw0 + (kc % NSTG) * (RAW / 4);
+        const float* rb = ra + 128 * RA;
+        const int k0 = kc * PK;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = t + u * UPD_THREADS;
-                const int row = (q >> 6) * 8 + (q & 7), k4 = ((q >> 3) & 7) * 4;
-                const __nv_bfloat162 lo2 = __floats2bfloat162_rn(av[u][0], av[u][1]);
-                const __nv_bfloat162 hi2 = __floats2bfloat162_rn(av[u][2], av[u][3]);
-                uint2 pk;
-                pk.x = *reinterpret_cast<const uint32_t*>(&lo2);
-                pk.y = *reinterpret_cast<const uint32_t*>(&hi2);
-                *reinterpret_cast<uint2*>(a_hi + cm_off16(row, k4)) = pk;
+        for (int u = 0; u < 2; ++u) {
+            const int q = t + u * UPD_THREADS;
+            const int row = q & 127, g = q >> 7;
+            float a[4], b[4];
+            lds16<float>(ra + row * RA + 4 * g, a);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                b[e] = rb[(4 * g + e) * RB + row + delta];
+                const int kk = k0 + 4 * g + e;
+                if constexpr (AM == 1) a[e] = kk < row ? a[e] : (kk == row && row < rows ? 1.f : 0.f);
+                if constexpr (BM == 1) b[e] = kk <= row ? b[e] : 0.f;
             }
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int q = t + u * UPD_THREADS;
-                const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
-                *reinterpret_cast<__nv_bfloat16*>(b_hi + cm_off16(nn, k)) = __float2bfloat16_rn(bv[u]);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = t + u * UPD_THREADS;
-                const int row = (q >> 6) * 8 + (q & 7), k4 = ((q >> 3) & 7) * 4;
-                float h[4], l[4];
+            if constexpr (KIND == TC_BF16) {
+                // one BF16 operand each, 8 bytes per (row, 4 k): the BF16 layout has 8 k per core-matrix row
+                const __nv_bfloat162 a01 = __floats2bfloat162_rn(a[0], a[1]), a23 = __floats2bfloat162_rn(a[2], a[3]);
+                const __nv_bfloat162 b01 = __floats2bfloat162_rn(b[0], b[1]), b23 = __floats2bfloat162_rn(b[2], b[3]);
+                uint2 pa, pb;
+                pa.x = *reinterpret_cast<const uint32_t*>(&a01);
+                pa.y = *reinterpret_cast<const uint32_t*>(&a23);
+                pb.x = *reinterpret_cast<const uint32_t*>(&b01);
+                pb.y = *reinterpret_cast<const uint32_t*>(&b23);
+                const int off = ((row >> 3) * (PK / 8) + (g >> 1)) * CORE_BYTES + (row & 7) * 16 + (g & 1) * 8;
+                *reinterpret_cast<uint2*>(a_hi + off) = pa;
+                *reinterpret_cast<uint2*>(b_hi + off) = pb;
+            } else {
+                float ah[4], al[4], bh[4], bl[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    h[e] = tf32_round(av[u][e]);
-                    l[e] = tf32_round(av[u][e] - h[e]);
+                    ah[e] = tf32_round(a[e]);
+                    al[e] = tf32_round(a[e] - ah[e]);
+                    bh[e] = tf32_round(b[e]);
+                    bl[e] = tf32_round(b[e] - bh[e]);
                 }
-                *reinterpret_cast<float4*>(a_hi + cm_off(row, k4)) = make_float4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<float4*>(a_lo + cm_off(row, k4)) = make_float4(l[0], l[1], l[2], l[3]);
+                const int off = cm(row, 4 * g);
+                *reinterpret_cast<float4*>(a_hi + off) = make_float4(ah[0], ah[1], ah[2], ah[3]);
+                *reinterpret_cast<float4*>(a_lo + off) = make_float4(al[0], al[1], al[2], al[3]);
+                *reinterpret_cast<float4*>(b_hi + off) = make_float4(bh[0], bh[1], bh[2], bh[3]);
+                *reinterpret_cast<float4*>(b_lo + off) = make_float4(bl[0], bl[1], bl[2], bl[3]);
             }
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int q = t + u * UPD_THREADS;
-                const int nn = ((q >> 5) & 15) * 8 + (q & 7), k = (q >> 9) * 4 + ((q >> 3) & 3);
-                const float h = tf32_round(bv[u]);
-                *reinterpret_cast<float*>(b_hi + cm_off(nn, k)) = h;
-                *reinterpret_cast<float*>(b_lo + cm_off(nn, k)) = tf32_round(bv[u] - h);
+        }
+    };
+    auto mma = [&](int kc) {
+        const int kw = min(PK, K - kc * PK);
+        if constexpr (KIND == TC_BF16) {
+            const uint32_t idesc = instr_desc_bf16(128, 128);
+            // 16 BF16 per MMA = two core matrices along K; the 8-row groups PK / 8 core matrices apart
+            mma_bf16(tmem, smem_desc(smem_u32(a_hi), CORE_BYTES, (PK / 8) * CORE_BYTES),
+                     smem_desc(smem_u32(b_hi), CORE_BYTES, (PK / 8) * CORE_BYTES), idesc, kc > 0 ? 1 : 0);
+        } else {
+            const uint32_t idesc = instr_desc(128, 128);
+            const uint32_t sbo = (PK / 4) * CORE_BYTES;
+            for (int kk = 0; kk < (kw + 7) / 8; ++kk) {
+                const uint32_t koff = kk * 2 * CORE_BYTES;     // 8 TF32 = two core matrices along K
+                const uint64_t ah = smem_desc(smem_u32(a_hi) + koff, CORE_BYTES, sbo);
+                const uint64_t al = smem_desc(smem_u32(a_lo) + koff, CORE_BYTES, sbo);
+                const uint64_t bh = smem_desc(smem_u32(b_hi) + koff, CORE_BYTES, sbo);
+                const uint64_t bl = smem_desc(smem_u32(b_lo) + koff, CORE_BYTES, sbo);
+                mma_tf32(tmem, ah, bh, idesc, (kc == 0 && kk == 0) ? 0 : 1);
+                mma_tf32(tmem, ah, bl, idesc, 1);
+                mma_tf32(tmem, al, bh, idesc, 1);
             }
         }
     };
     bool ok = true;
-    load(0);
-    for (int k0 = 0; k0 < w; k0 += KMAX) {
-        if (k0 > 0) {
-            // the previous chunk's MMAs have read the operand buffers
+#pragma unroll 1
+    for (int kc = 0; kc < NSTG - 1; ++kc) {
+        if (kc < nk) issue(kc);
+        cp_async_commit();
+    }
+#pragma unroll 1
+    for (int kc = 0; kc < nk; ++kc) {
+        // the stage of chunk kc + NSTG - 1 was converted in the previous iteration
+        if (kc + NSTG - 1 < nk) issue(kc + NSTG - 1);
+        cp_async_commit();
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(NSTG - 1) : "memory");
+        if (kc > 0) {
+            // the previous chunk's MMAs have read the operand parts
             ok = mbar_wait(mbar, nphase & 1) && ok;
             ++nphase;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         }
-        store();
+        __syncthreads();
+        convert(kc);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (t == 0) {
-            if constexpr (KIND == TC_BF16)
-                mma_chunk_bf16(tmem, smem_u32(a_hi), smem_u32(b_hi), min(KMAX, w - k0), k0 == 0);
-            else
-                mma_chunk(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo), min(KMAX, w - k0),
-                          k0 == 0);
+            mma(kc);
             mma_commit(mbar);
         }
-        if (k0 + KMAX < w) load(k0 + KMAX);
     }
+    cp_async_wait_all();
     ok = mbar_wait(mbar, nphase & 1) && ok;
     ++nphase;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -846,11 +1046,11 @@ __device__ __noinline__ bool tc_tile_body(const EngItem<float>& it, int p, int t
         if (t == 0) atomicOr(err, ERR_TIMEOUT_TC);
         return false;
     }
-    // warp w: accumulator lanes (tile rows) 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63;
-    // each 32 x 32 block turns around in shared memory (the operand buffers are
-    // free now) so that a warp reads and writes 32 consecutive columns of a row
+    // warp w: accumulator lanes (block rows) 32 (w % 4) .. + 31, columns 64 (w / 4) .. + 63;
+    // each 32 x 32 block turns around in shared memory (the raw stages are free
+    // now) so that a warp reads and writes 32 consecutive columns of a row
     const int wq = warp & 3, h = warp >> 2;
-    float* Tt = reinterpret_cast<float*>(smem) + warp * 32 * 33;
+    float* Tt = raw0 + warp * 32 * 33;
 #pragma unroll 1
     for (int cb = 64 * h; cb < 64 * h + 64; cb += 32) {
         float v[32];
@@ -860,16 +1060,24 @@ __device__ __noinline__ bool tc_tile_body(const EngItem<float>& it, int p, int t
         __syncwarp();
         const int col = cb + lane;
         const bool cin = col < cols;
-        float c[32];
+        if constexpr (SUB) {
+            float c[32];
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            const int row = 32 * wq + r;
-            c[r] = (cin && row < rows) ? __ldcg(A + (long long)(r0 + row) * ld + c0 + col) : 0.f;
-        }
+            for (int r = 0; r < 32; ++r) {
+                const int row = 32 * wq + r;
+                c[r] = (cin && row < rows) ? __ldcg(Cp + (long long)row * ldc + col) : 0.f;
+            }
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            const int row = 32 * wq + r;
-            if (cin && row < rows) A[(long long)(r0 + row) * ld + c0 + col] = c[r] - Tt[r * 33 + lane];
+            for (int r = 0; r < 32; ++r) {
+                const int row = 32 * wq + r;
+                if (cin && row < rows) Cp[(long long)row * ldc + col] = c[r] - Tt[r * 33 + lane];
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int row = 32 * wq + r;
+                if (cin && row < rows) Cp[(long long)row * ldc + col] = Tt[r * 33 + lane];
+            }
         }
         __syncwarp();
     }
@@ -945,7 +1153,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
                                                                  const EngTask* __restrict__ tasks, int ntasks,
                                                                  const EngMeta* __restrict__ meta, int* flags,
                                                                  int* next, int* abort_flag, T* __restrict__ scr,
-                                                                 long long stride, int* __restrict__ err) {
+                                                                 long long stride, T* __restrict__ inv,
+                                                                 long long inv_stride, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char esm[];
     __shared__ int s_idx;
     // tensor-core tiles (FP32 only): 128 tensor-memory columns and one mbarrier for
@@ -955,6 +1164,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
     uint32_t tmem = 0, nphase = 0;
     // (a separate instantiation: a kernel with tensor-memory allocation gets one CTA per SM)
     constexpr bool tc = TCK != TC_NONE && sizeof(T) == 4;
+    // strip chunk: one tensor-core block (128 rows / columns) or CH rows / columns
+    constexpr int SCH = tc ? TILE : CH;
     if constexpr (tc) {
         if ((threadIdx.x >> 5) == 0) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(
@@ -992,15 +1203,15 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
             } else if (tk.type == 1 || tk.type == 2) {
                 wait_flag(flags + flag_diag(m, pi), abort_flag, err);
                 if (pi > 0) {
-                    const int g0 = w + tk.a * CH, g1 = min(it.n - p, g0 + CH);
+                    const int g0 = w + tk.a * SCH, g1 = min(it.n - p, g0 + SCH);
                     if (tk.type == 1) wait_prev_tiles(flags, m, pi - 1, ntp, g0, g1, 0, w, TILE, abort_flag, err);
                     else wait_prev_tiles(flags, m, pi - 1, ntp, 0, w, g0, g1, TILE, abort_flag, err);
                 }
             } else {
-                const int nch = (it.n - m0 + CH - 1) / CH;
-                const int ca = (tk.a * TILE) / CH, cb = min(nch - 1, ((tk.a + 1) * TILE - 1) / CH);
+                const int nch = (it.n - m0 + SCH - 1) / SCH;
+                const int ca = (tk.a * TILE) / SCH, cb = min(nch - 1, ((tk.a + 1) * TILE - 1) / SCH);
                 for (int c = ca; c <= cb; ++c) wait_flag(flags + flag_row(m, pi, c), abort_flag, err);
-                const int da = (tk.b * TILE) / CH, db = min(nch - 1, ((tk.b + 1) * TILE - 1) / CH);
+                const int da = (tk.b * TILE) / SCH, db = min(nch - 1, ((tk.b + 1) * TILE - 1) / SCH);
                 for (int c = da; c <= db; ++c) wait_flag(flags + flag_col(m, pi, c), abort_flag, err);
                 if (pi > 0) {
                     const int r0 = w + tk.a * TILE, c0 = w + tk.b * TILE;
@@ -1013,20 +1224,42 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
         __syncthreads();
         T* pv = scr + (long long)tk.item * stride + (long long)pi * NB;
         if (tk.type == 0) {
-            diag_body<T, NB>(it, p, pv, err, esm);
+            if constexpr (tc) diag_body<T, NB, true>(it, p, pv, err, esm, inv + tk.item * inv_stride + (long long)pi * NB * NB);
+            else diag_body<T, NB>(it, p, pv, err, esm);
             own = flag_diag(m, pi);
         } else if (tk.type == 1 || tk.type == 2) {
-            trsm_body<T, NB>(it, p, tk.type == 2, tk.a, pv, esm);
+            if constexpr (tc) {
+                // L21 = M21 U11^{-1} (128 rows) or U12 = L11^{-1} M12 (128 columns) in place, split TF32
+                float* A = reinterpret_cast<float*>(it.a);
+                const float* Iv = reinterpret_cast<const float*>(inv) + tk.item * inv_stride + (long long)pi * NB * NB;
+                const long long ld = it.ld;
+                const int g0 = m0 + tk.a * SCH, len = min(SCH, it.n - g0);
+                bool ok = true;
+                if (tk.type == 1)
+                    ok = tc_prod_body<TC_SPLIT_TF32, 0, 1>(A + (long long)g0 * ld + p, ld, Iv, NB,
+                                                          A + (long long)g0 * ld + p, ld, len, w, w, esm, tmem,
+                                                          tcx::smem_u32(&s_mbar), nphase, err);
+                else
+                    ok = tc_prod_body<TC_SPLIT_TF32, 1, 0>(Iv, NB, A + (long long)p * ld + g0, ld,
+                                                          A + (long long)p * ld + g0, ld, w, len, w, esm, tmem,
+                                                          tcx::smem_u32(&s_mbar), nphase, err);
+                if (!ok && threadIdx.x == 0) atomicExch(abort_flag, 1);
+            } else {
+                trsm_body<T, NB>(it, p, tk.type == 2, tk.a, pv, esm);
+            }
             own = tk.type == 1 ? flag_row(m, pi, tk.a) : flag_col(m, pi, tk.a);
         } else {
             if constexpr (tc) {
-                {
-                    if (!tc_tile_body<NB, (TCK == TC_BF16 ? TC_BF16 : TC_SPLIT_TF32)>(
-                            reinterpret_cast<const EngItem<float>&>(it), p, tk.a, tk.b, esm, tmem,
-                                          tcx::smem_u32(&s_mbar), nphase, err) &&
-                        threadIdx.x == 0)
-                        atomicExch(abort_flag, 1);
-                }
+                float* A = reinterpret_cast<float*>(it.a);
+                const long long ld = it.ld;
+                const int r0 = m0 + tk.a * TILE, c0 = m0 + tk.b * TILE;
+                if (r0 < it.n && c0 < it.n &&
+                    !tc_prod_body<(TCK == TC_BF16 ? TC_BF16 : TC_SPLIT_TF32), 0, 0>(
+                        A + (long long)r0 * ld + p, ld, A + (long long)p * ld + c0, ld, A + (long long)r0 * ld + c0,
+                        ld, min(TILE, it.n - r0), min(TILE, it.n - c0), w, esm, tmem, tcx::smem_u32(&s_mbar), nphase,
+                        err) &&
+                    threadIdx.x == 0)
+                    atomicExch(abort_flag, 1);
             } else {
                 update_body<T, NB, TILE>(it, p, tk.a, tk.b, esm);
             }
@@ -1046,8 +1279,11 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_engine_tasks(const EngItem<T
 }
 
 template <class T>
-size_t task_smem() {
+size_t task_smem(bool tc) {
     constexpr int TILE = EngCfg<T>::TILE;
+    // tensor-core instantiation: the diagonal body and the products' four operand
+    // parts (the strips run as products too)
+    if (tc) return std::max(diag_smem<T>(), (size_t)tcp::SMEM);
     return std::max(std::max(diag_smem<T>(), trsm_smem<T>()), upd_smem<T, TILE>());
 }
 
@@ -1062,7 +1298,7 @@ long long engine_scratch_elems(int count, bool dbl, int maxk) {
 namespace {
 // Task list of the persistent kernel (host), in the order described above.
 template <class T>
-static void build_tasks(const int* hn, const int* hk, int count, std::vector<EngTask>& tasks,
+static void build_tasks(const int* hn, const int* hk, int count, int CH, std::vector<EngTask>& tasks,
                         std::vector<EngMeta>& meta, int& nflags) {
     constexpr int NB = EngCfg<T>::NB, TILE = EngCfg<T>::TILE;
     meta.resize(count);
@@ -1082,12 +1318,13 @@ static void build_tasks(const int* hn, const int* hk, int count, std::vector<Eng
         nch = (mrem + CH - 1) / CH;
         nt = (mrem + TILE - 1) / TILE;
     };
+    const int lo = 0, hi = count;
     auto add_diag = [&](int pi) {
-        for (int i = 0; i < count; ++i)
+        for (int i = lo; i < hi; ++i)
             if (pi < meta[i].P) tasks.push_back(EngTask{0, i, pi, 0, 0});
     };
     auto add_rc = [&](int pi) {
-        for (int i = 0; i < count; ++i) {
+        for (int i = lo; i < hi; ++i) {
             if (pi >= meta[i].P) continue;
             int nch, nt;
             geom(i, pi, nch, nt);
@@ -1098,7 +1335,7 @@ static void build_tasks(const int* hn, const int* hk, int count, std::vector<Eng
         }
     };
     auto add_tiles = [&](int pi, bool first) {
-        for (int i = 0; i < count; ++i) {
+        for (int i = lo; i < hi; ++i) {
             if (pi >= meta[i].P) continue;
             int nch, nt;
             geom(i, pi, nch, nt);
@@ -1109,7 +1346,10 @@ static void build_tasks(const int* hn, const int* hk, int count, std::vector<Eng
     };
     // D(0) RC(0) Uf(0) | D(1) Ur(0) RC(1) Uf(1) | D(2) Ur(1) ...: the next diagonal
     // block starts as soon as its tile is updated, the bulk of the current update
-    // fills the GPU meanwhile, and the strips that need the new factors come after
+    // fills the GPU meanwhile, and the strips that need the new factors come after.
+    // (All items per panel: the diagonal tasks' chain is hidden behind the other
+    // items' tiles; a task order by groups of items that fit in L2 made the strips
+    // wait for their diagonal blocks.)
     if (Pmax == 0) return;
     add_diag(0);
     add_rc(0);
@@ -1145,22 +1385,28 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         std::vector<EngTask> tasks;
         std::vector<EngMeta> meta;
         int nflags = 0;
-        build_tasks<T>(hn, hk, count, tasks, meta, nflags);
+        // tensor-core strips are 128-row / -column products (one flag per tile row / column)
+        build_tasks<T>(hn, hk, count, use_tc ? TILE : CH, tasks, meta, nflags);
         if (tasks.empty()) return BDDC_OK;
-        // one allocation for the task list, the item table and the flags, freed by
-        // the stream-ordered allocator after the launch
+        // one allocation for the task list, the item table, the flags and (tensor
+        // cores) the inverses of the diagonal blocks' factors (NB x NB per item and
+        // panel), freed by the stream-ordered allocator after the launch
         const size_t tb = tasks.size() * sizeof(EngTask), mb = meta.size() * sizeof(EngMeta);
         const size_t fb = sizeof(int) * ((size_t)nflags + 2);
         const size_t o1 = (tb + 255) & ~size_t(255), o2 = o1 + ((mb + 255) & ~size_t(255));
+        const size_t o3 = o2 + ((fb + 255) & ~size_t(255));
+        const long long inv_stride = use_tc ? (long long)NB * stride : 0;
+        const size_t ib = sizeof(T) * (size_t)inv_stride * (size_t)count;
         std::vector<unsigned char> host(o2);
         memcpy(host.data(), tasks.data(), tb);
         memcpy(host.data() + o1, meta.data(), mb);
         unsigned char* dev = nullptr;
-        BDDC_CUDA_TRY(cudaMallocAsync((void**)&dev, o2 + fb, st));
+        BDDC_CUDA_TRY(cudaMallocAsync((void**)&dev, o3 + ib, st));
         BDDC_TRY(staged_upload(dev, host.data(), o2, st));
         int* flags = reinterpret_cast<int*>(dev + o2);
+        T* inv = use_tc ? reinterpret_cast<T*>(dev + o3) : nullptr;
         BDDC_CUDA_TRY(cudaMemsetAsync(flags, 0, fb, st));
-        const size_t sm = task_smem<T>();
+        const size_t sm = task_smem<T>(use_tc);
         auto kern = !use_tc ? k_engine_tasks<T, NB, TILE, TC_NONE>
                     : (tck == TC_BF16 ? k_engine_tasks<T, NB, TILE, TC_BF16> : k_engine_tasks<T, NB, TILE, TC_SPLIT_TF32>);
         BDDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -1189,7 +1435,7 @@ int engine_run(const EngItem<T>* items_dev, int count, int maxn, int maxk, T* ds
         ktimer_begin(KT_ENGINE_TASKS, st);
         kern<<<grid, UPD_THREADS, sm, st>>>(items_dev, reinterpret_cast<const EngTask*>(dev), (int)tasks.size(),
                                              reinterpret_cast<const EngMeta*>(dev + o1), flags, flags + nflags,
-                                             flags + nflags + 1, dscr, stride, err);
+                                             flags + nflags + 1, dscr, stride, inv, inv_stride, err);
         ktimer_end(KT_ENGINE_TASKS, st, fl, by);
         bddc_note_launches(1);
         BDDC_CUDA_TRY(cudaGetLastError());
