@@ -98,6 +98,43 @@ __device__ void block_argmax(T v, int i, T* vout, int* iout) {
     bar();
 }
 
+// Arg-max over a warp of (value, index); ties keep the smaller index.
+template <class T>
+__device__ __forceinline__ void warp_argmax(T& v, int& i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+    }
+}
+
+// Arg-max of per-warp partial results (rv, ri)[0 .. GT / 32), read by every thread.
+template <class T>
+__device__ __forceinline__ void argmax_of(const T* rv, const int* ri, T* vout, int* iout) {
+    T bv = rv[0];
+    int bi = ri[0];
+#pragma unroll
+    for (int q = 1; q < GT / 32; ++q)
+        if (rv[q] > bv || (rv[q] == bv && ri[q] < bi)) { bv = rv[q]; bi = ri[q]; }
+    *vout = bv;
+    *iout = bi;
+}
+
+// Row updates of the step loops below: with g = GT / rows threads per row (at
+// least 1), thread t takes the rows t / g + (GT / g) u and, within a row, the
+// columns t % g + g v, so that a row's multiplier stays in a register and the
+// threads of a row touch consecutive columns.
+struct RowMap {
+    int g, tr, tq, rs;
+    __device__ explicit RowMap(int rows, int gmax = GT) {
+        g = min(gmax, rows > 0 ? max(1, GT / rows) : GT);
+        tr = (int)threadIdx.x / g;
+        tq = (int)threadIdx.x - tr * g;
+        rs = GT / g;
+    }
+};
+
 // C = alpha * op(A) * op(B) + beta * C ; row-major; transA/transB flags
 template <class T, class TA, class TB, class TC>
 __device__ void mm(const TA* A, int lda, bool ta, const TB* B, int ldb, bool tb, TC* C,
@@ -132,13 +169,18 @@ __device__ void symmetrize(T* A, int ld, int n) {
     bar();
 }
 
-// Solve A X = B in place (A n x n overwritten by its LU, B n x nr overwritten by X);
-// Gaussian elimination with partial pivoting.
+// Solve A X = B in place (A n x n overwritten by its U factor, B n x nr
+// overwritten by X); Gaussian elimination with partial pivoting on [A | B], then
+// back substitution.  Row updates per thread row (GQ threads per row, the
+// multiplier in a register); the back substitution uses x_c = B(c, :) / U(c, c)
+// on the fly (row c is final by then) and divides every row at the end.
 template <class T>
 __device__ void lu_solve(T* A, int lda, T* B, int ldb, int n, int nr, int* err) {
     __shared__ int piv_s;
     __shared__ T pv_s[32];
     __shared__ int pi_s[32];
+    const RowMap rm(n);
+    const int tr = rm.tr, tq = rm.tq, GQ = rm.g, RS = rm.rs;
     for (int c = 0; c < n; ++c) {
         // pivot search by warp 0
         if (threadIdx.x < 32) {
@@ -169,33 +211,37 @@ __device__ void lu_solve(T* A, int lda, T* B, int ldb, int n, int nr, int* err) 
             for (int q = threadIdx.x; q < nr; q += GT) {
                 T t = B[c * ldb + q]; B[c * ldb + q] = B[p * ldb + q]; B[p * ldb + q] = t;
             }
+            bar();
         }
-        bar();
         T d = A[c * lda + c];
         if (d == (T)0) d = (T)Tol<T>::tiny;
-        for (int r = c + 1 + threadIdx.x; r < n; r += GT) A[r * lda + c] /= d;
-        bar();
         const int rem = n - c - 1;
-        const int wid = rem + nr;
-        CTA_FOR_2D(rr, j, rem, wid) {
-            const int r = c + 1 + rr;
-            T l = A[r * lda + c];
-            if (j < rem) A[r * lda + c + 1 + j] -= l * A[c * lda + c + 1 + j];
-            else B[r * ldb + (j - rem)] -= l * B[c * ldb + (j - rem)];
+        for (int r = c + 1 + tr; r < n; r += RS) {
+            const T l = A[r * lda + c] / d;
+#pragma unroll 4
+            for (int j = tq; j < rem; j += GQ) A[r * lda + c + 1 + j] -= l * A[c * lda + c + 1 + j];
+#pragma unroll 4
+            for (int j = tq; j < nr; j += GQ) B[r * ldb + j] -= l * B[c * ldb + j];
         }
         bar();
     }
-    // back substitution, column-parallel over the right-hand sides
-    for (int c = n - 1; c >= 0; --c) {
+    // back substitution
+    for (int c = n - 1; c > 0; --c) {
         T d = A[c * lda + c];
         if (d == (T)0) d = (T)Tol<T>::tiny;
-        for (int q = threadIdx.x; q < nr; q += GT) B[c * ldb + q] /= d;
-        bar();
-        CTA_FOR_2D(r, j, c, nr) {
-            B[r * ldb + j] -= A[r * lda + c] * B[c * ldb + j];
+        for (int r = tr; r < c; r += RS) {
+            const T a = A[r * lda + c];
+#pragma unroll 4
+            for (int j = tq; j < nr; j += GQ) B[r * ldb + j] -= a * (B[c * ldb + j] / d);
         }
         bar();
     }
+    for (int r = tr; r < n; r += RS) {
+        T d = A[r * lda + r];
+        if (d == (T)0) d = (T)Tol<T>::tiny;
+        for (int j = tq; j < nr; j += GQ) B[r * ldb + j] /= d;
+    }
+    bar();
 }
 
 // Generalised Schur complement of a symmetric PSD matrix: eliminate the
@@ -204,43 +250,58 @@ __device__ void lu_solve(T* A, int lda, T* B, int ldb, int n, int nr, int* err) 
 // The leading r0 x r0 block then holds M_ww - M_wr M_rr^+ M_rw.
 template <class T>
 __device__ void pinv_schur_tail(T* M, int ld, int n, int r0, unsigned char* done) {
-    __shared__ T dmax0_s, best_s;
-    __shared__ int bi_s;
+    // One barrier per pivot: the threads that update a diagonal entry of the
+    // tail also reduce the next pivot's arg-max, per warp, into a double-buffered
+    // array that every thread reads after the barrier (ties to the smaller index).
+    __shared__ T dmax0_s;
+    __shared__ T rv[2][GT / 32];
+    __shared__ int ri[2][GT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const RowMap rm(n, 4);      // (more threads per row measured slower on the 2n x 2n sums)
+    const int tr = rm.tr, tq = rm.tq, GQ = rm.g, RS = rm.rs;
     for (int q = threadIdx.x; q < n; q += GT) done[q] = q < r0 ? 1 : 0;
     if (threadIdx.x == 0) {
         T d = 0.0;
         for (int q = r0; q < n; ++q) d = fmax(d, M[q * ld + q]);
         dmax0_s = d;
     }
+    {
+        T b = (T)-1;
+        int bi = n;
+        for (int q = r0 + threadIdx.x; q < n; q += GT)
+            if (M[q * ld + q] > b) { b = M[q * ld + q]; bi = q; }
+        warp_argmax(b, bi);
+        if (lane == 0) { rv[0][wid] = b; ri[0][wid] = bi; }
+    }
     bar();
     const T tol = (T)Tol<T>::drop * dmax0_s;
+    int buf = 0;
     for (int step = r0; step < n; ++step) {
-        {
-            T b = (T)-1;
-            int bi = n;
-            for (int q = r0 + threadIdx.x; q < n; q += GT)
-                if (!done[q] && M[q * ld + q] > b) { b = M[q * ld + q]; bi = q; }
-            T bv;
-            int bidx;
-            block_argmax(b, bi, &bv, &bidx);
-            if (threadIdx.x == 0) {
-                best_s = bv;
-                bi_s = bidx < n ? bidx : -1;
-            }
-            bar();
-        }
-        if (bi_s < 0 || !(best_s > tol)) break;
-        const int p = bi_s;
+        T bv;
+        int p;
+        argmax_of(rv[buf], ri[buf], &bv, &p);
+        if (p >= n || !(bv > tol)) break;        // the same decision in every thread
+        done[p] = 1;                             // same value from every thread; p is skipped below
         const T rdp = (T)1 / M[p * ld + p];
+        T b = (T)-1;
+        int bi = n;
         // update all not-yet-eliminated rows/cols (including the kept block)
-        CTA_FOR_2D(i, j, n, n) {
-            if (i == p || j == p) continue;
-            if ((i >= r0 && done[i]) || (j >= r0 && done[j])) continue;
-            M[i * ld + j] -= M[i * ld + p] * rdp * M[p * ld + j];
+        for (int i = tr; i < n; i += RS) {
+            if (i == p || (i >= r0 && done[i])) continue;
+            const T l = M[i * ld + p] * rdp;
+#pragma unroll 4
+            for (int j = tq; j < n; j += GQ) {
+                // branch-free body (predicated store): the loads of several columns in flight
+                const bool act = j != p && !(j >= r0 && done[j]);
+                const T v = M[i * ld + j] - l * M[p * ld + j];
+                if (act) M[i * ld + j] = v;
+                if (act && j == i && i >= r0 && v > b) { b = v; bi = i; }
+            }
         }
+        warp_argmax(b, bi);
+        if (lane == 0) { rv[buf ^ 1][wid] = b; ri[buf ^ 1][wid] = bi; }
         bar();
-        if (threadIdx.x == 0) done[p] = 1;
-        bar();
+        buf ^= 1;
     }
 }
 
@@ -353,66 +414,84 @@ __device__ void sort_desc(const T* A, int ld, int n, int* order) {
 
 // In-place Cholesky K = L L^T (lower triangle, shared memory, stride ld);
 // returns false when a pivot falls to <= tol * (largest initial diagonal).
+// Step k subtracts A(i, k) A(j, k) / d_k from the trailing lower triangle with
+// column k still unscaled (it is not written in the step), so one barrier per
+// step suffices; the columns are scaled by 1 / sqrt(d_k) at the end.
 template <class T>
 __device__ bool cholesky(T* A, int n, int ld, T tol) {
     __shared__ T dmax_s;
-    __shared__ int ok_s;
+    const RowMap rm(n);
+    const int tr = rm.tr, tq = rm.tq, GQ = rm.g, RS = rm.rs;
     if (threadIdx.x == 0) {
         T m = 0;
         for (int i = 0; i < n; ++i) m = fmax(m, A[i * ld + i]);
         dmax_s = m;
-        ok_s = m > (T)0;
     }
     bar();
-    for (int k = 0; k < n && ok_s; ++k) {
-        T d = A[k * ld + k];
-        bar();
-        if (!(d > tol * dmax_s)) {
-            if (threadIdx.x == 0) ok_s = 0;
-            bar();
-            break;
-        }
-        const T l = sqrt(d);
-        for (int i = k + threadIdx.x; i < n; i += GT) A[i * ld + k] = i == k ? l : A[i * ld + k] / l;
-        bar();
-        const int rem = n - k - 1;
-        CTA_FOR_2D(ii, jj, rem, rem) {
-            if (jj <= ii) {
-                const int i = k + 1 + ii, j = k + 1 + jj;
-                A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
-            }
+    const T dmax = dmax_s;
+    if (!(dmax > (T)0)) return false;
+    for (int k = 0; k < n; ++k) {
+        const T d = A[k * ld + k];
+        if (!(d > tol * dmax)) return false;     // the same decision in every thread
+        const T rd = (T)1 / d;
+        for (int i = k + 1 + tr; i < n; i += RS) {
+            const T l = A[i * ld + k] * rd;
+#pragma unroll 4
+            for (int j = k + 1 + tq; j <= i; j += GQ) A[i * ld + j] -= l * A[j * ld + k];
         }
         bar();
     }
-    return ok_s != 0;
+    for (int i = tr; i < n; i += RS)
+        for (int k = tq; k < i; k += GQ) A[i * ld + k] /= sqrt(A[k * ld + k]);
+    bar();
+    for (int k = threadIdx.x; k < n; k += GT) A[k * ld + k] = sqrt(A[k * ld + k]);
+    bar();
+    return true;
 }
 
 // X <- L^{-1} X for an n x m block X (row stride ldx), L lower in (Ls, ldl).
+// Step k subtracts L(i, k) (X(k, :) / L(k, k)) from the rows below, X(k, :) being
+// final by then; every row is divided by its diagonal entry at the end.  One
+// barrier per step, thread rows as in the eliminations.
 template <class T>
 __device__ void trsm_lower(const T* Ls, int ldl, T* X, int ldx, int n, int m) {
-    for (int k = 0; k < n; ++k) {
+    const RowMap rm(n);
+    const int tr = rm.tr, tq = rm.tq, GQ = rm.g, RS = rm.rs;
+    for (int k = 0; k + 1 < n; ++k) {
         const T inv = (T)1 / Ls[k * ldl + k];
-        for (int c = threadIdx.x; c < m; c += GT) X[k * ldx + c] *= inv;
-        bar();
-        const int rem = n - k - 1;
-        CTA_FOR_2D(ii, c, rem, m) {
-            const int i = k + 1 + ii;
-            X[i * ldx + c] -= Ls[i * ldl + k] * X[k * ldx + c];
+        for (int i = k + 1 + tr; i < n; i += RS) {
+            const T l = Ls[i * ldl + k];
+#pragma unroll 4
+            for (int c = tq; c < m; c += GQ) X[i * ldx + c] -= l * (X[k * ldx + c] * inv);
         }
         bar();
     }
+    for (int k = tr; k < n; k += RS) {
+        const T inv = (T)1 / Ls[k * ldl + k];
+        for (int c = tq; c < m; c += GQ) X[k * ldx + c] *= inv;
+    }
+    bar();
 }
 
-// X <- L^{-T} X for an n x m block X.
+// X <- L^{-T} X for an n x m block X (as above, from the last row up).
 template <class T>
 __device__ void trsm_lower_t(const T* Ls, int ldl, T* X, int ldx, int n, int m) {
-    for (int k = n - 1; k >= 0; --k) {
+    const RowMap rm(n);
+    const int tr = rm.tr, tq = rm.tq, GQ = rm.g, RS = rm.rs;
+    for (int k = n - 1; k > 0; --k) {
         const T inv = (T)1 / Ls[k * ldl + k];
-        for (int c = threadIdx.x; c < m; c += GT) X[k * ldx + c] *= inv;
-        bar();
-        CTA_FOR_2D(i, c, k, m) X[i * ldx + c] -= Ls[k * ldl + i] * X[k * ldx + c];
+        for (int i = tr; i < k; i += RS) {
+            const T l = Ls[k * ldl + i];
+#pragma unroll 4
+            for (int c = tq; c < m; c += GQ) X[i * ldx + c] -= l * (X[k * ldx + c] * inv);
+        }
         bar();
     }
+    for (int k = tr; k < n; k += RS) {
+        const T inv = (T)1 / Ls[k * ldl + k];
+        for (int c = tq; c < m; c += GQ) X[k * ldx + c] *= inv;
+    }
+    bar();
 }
 
 // Largest order the tridiagonal eigen-solver handles (shared-memory vectors).
