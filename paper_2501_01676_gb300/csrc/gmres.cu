@@ -316,12 +316,19 @@ __global__ void k_backsolve(const GmState* __restrict__ S, const double* __restr
 // cycles are not estimated) and two warps run the substitutions.
 constexpr int GM_COND_MAX = 128;
 constexpr int GM_COND_ITERS = 16;
-constexpr int GM_COND_THREADS = 64;
+constexpr int GM_COND_THREADS = 128;
+// kappa_est = sigma_max(R) / sigma_min(R) of the triangular factor R of the
+// Hessenberg: sigma_max(R) by power iteration on R^T R; then R is inverted in
+// place (X = R^{-1}, column by column from X R = I: X(i, j) = -(sum_{i <= l < j}
+// X(i, l) R(l, j)) / R(j, j), two barriers per column) and sigma_min(R) =
+// 1 / sigma_max(X) by the same power iteration on X^T X.  A zero diagonal entry
+// gives kappa_est = infinity.
 __global__ void __launch_bounds__(GM_COND_THREADS) k_cond(const GmState* __restrict__ S,
                                                           const double* __restrict__ H,
                                                           double* __restrict__ kmax, GmBatch B) {
     extern __shared__ double Rs[];                  // k x k, row-major
     __shared__ double x[GM_COND_MAX], z[GM_COND_MAX], red[GM_COND_THREADS / 32];
+    __shared__ int zero_s;
     S += blockIdx.z;
     H += blockIdx.z * B.sH;
     const int k = S->j, m = S->m, t = threadIdx.x;
@@ -330,6 +337,7 @@ __global__ void __launch_bounds__(GM_COND_THREADS) k_cond(const GmState* __restr
         const int i = q / k, l = q - i * k;
         Rs[q] = l >= i ? H[(long long)l * (m + 1) + i] : 0.0;
     }
+    if (t == 0) zero_s = 0;
     __syncthreads();
     auto norm = [&](const double* v) {
         double a = 0.0;
@@ -342,56 +350,58 @@ __global__ void __launch_bounds__(GM_COND_THREADS) k_cond(const GmState* __restr
         __syncthreads();
         return sqrt(s2);
     };
-    // sigma_max: x <- R^T R x
-    for (int i = t; i < k; i += GM_COND_THREADS) x[i] = 1.0 + 1e-3 * i;
-    __syncthreads();
-    double smax = 0.0;
-    for (int it = 0; it < GM_COND_ITERS; ++it) {
-        const double nx = norm(x);
-        for (int i = t; i < k; i += GM_COND_THREADS) x[i] /= nx;
+    // largest singular value of the upper triangle in Rs: power iteration on Rs^T Rs
+    auto sigma_max = [&](double x0, double dx) {
+        for (int i = t; i < k; i += GM_COND_THREADS) x[i] = x0 + dx * i;
         __syncthreads();
-        for (int i = t; i < k; i += GM_COND_THREADS) {       // z = R x
+        double sm = 0.0;
+        for (int it = 0; it < GM_COND_ITERS; ++it) {
+            const double nx = norm(x);
+            for (int i = t; i < k; i += GM_COND_THREADS) x[i] /= nx;
+            __syncthreads();
+            for (int i = t; i < k; i += GM_COND_THREADS) {       // z = R x
+                double a = 0.0;
+                for (int l = i; l < k; ++l) a += Rs[i * k + l] * x[l];
+                z[i] = a;
+            }
+            __syncthreads();
+            sm = norm(z);
+            for (int i = t; i < k; i += GM_COND_THREADS) {       // x = R^T z
+                double a = 0.0;
+                for (int l = 0; l <= i; ++l) a += Rs[l * k + i] * z[l];
+                x[i] = a;
+            }
+            __syncthreads();
+        }
+        return sm;
+    };
+    const double smax = sigma_max(1.0, 1e-3);
+    // X = R^{-1} in place: column j from the finished columns < j and R's column j
+    for (int j = 0; j < k; ++j) {
+        const double d = Rs[j * k + j];
+        if (d == 0.0 && t == 0) zero_s = 1;
+        double v[GM_COND_MAX / GM_COND_THREADS];
+#pragma unroll
+        for (int u = 0; u < GM_COND_MAX / GM_COND_THREADS; ++u) {
+            const int i = t + u * GM_COND_THREADS;
             double a = 0.0;
-            for (int l = i; l < k; ++l) a += Rs[i * k + l] * x[l];
-            z[i] = a;
+            if (i < j)
+                for (int l = i; l < j; ++l) a += Rs[i * k + l] * Rs[l * k + j];
+            v[u] = d != 0.0 ? -a / d : 0.0;
         }
         __syncthreads();
-        smax = norm(z);
-        for (int i = t; i < k; i += GM_COND_THREADS) {       // x = R^T z
-            double a = 0.0;
-            for (int l = 0; l <= i; ++l) a += Rs[l * k + i] * z[l];
-            x[i] = a;
+#pragma unroll
+        for (int u = 0; u < GM_COND_MAX / GM_COND_THREADS; ++u) {
+            const int i = t + u * GM_COND_THREADS;
+            if (i < j) Rs[i * k + j] = v[u];
+            if (i == j) Rs[j * k + j] = d != 0.0 ? 1.0 / d : 0.0;
         }
         __syncthreads();
     }
-    // sigma_min: x <- (R^T R)^{-1} x
-    for (int i = t; i < k; i += GM_COND_THREADS) x[i] = 1.0 - 1e-3 * i;
-    __syncthreads();
-    double smin = 0.0;
-    for (int it = 0; it < GM_COND_ITERS; ++it) {
-        const double nx = norm(x);
-        for (int i = t; i < k; i += GM_COND_THREADS) x[i] /= nx;
-        __syncthreads();
-        for (int i = 0; i < k; ++i) {                       // R^T z = x (forward)
-            const double d = Rs[i * k + i];
-            const double zi = d != 0.0 ? x[i] / d : 0.0;
-            if (t == 0) z[i] = zi;
-            for (int r = i + 1 + t; r < k; r += GM_COND_THREADS) x[r] -= Rs[i * k + r] * zi;
-            __syncthreads();
-        }
-        for (int i = k - 1; i >= 0; --i) {                  // R x = z (backward)
-            const double d = Rs[i * k + i];
-            const double xi = d != 0.0 ? z[i] / d : 0.0;
-            if (t == 0) x[i] = xi;
-            for (int r = t; r < i; r += GM_COND_THREADS) z[r] -= Rs[r * k + i] * xi;
-            __syncthreads();
-        }
-        const double g = norm(x);                           // ||(R^T R)^{-1} x|| -> 1 / sigma_min^2
-        smin = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
-    }
+    const double sxmax = sigma_max(1.0, -1e-3);      // = 1 / sigma_min(R)
     if (t == 0) {
         // positive doubles order like their bit patterns: max over columns by atomicMax
-        const double kap = smin > 0.0 ? smax / smin : INFINITY;
+        const double kap = (zero_s || !(sxmax > 0.0)) ? INFINITY : smax * sxmax;
         atomicMax(reinterpret_cast<unsigned long long*>(kmax), (unsigned long long)__double_as_longlong(kap));
     }
 }
