@@ -90,6 +90,12 @@ struct HostMesh {
     std::vector<int> by_kind[3];    // entity ids per kind in order
 };
 
+// The mesh in two parts: the partition, subdomain boxes and dof lists (all the
+// assembly and the subdomain eliminations need), then the interface
+// classification (entities, Gamma numbering, positions), which setup builds on
+// the host while the GPU assembles; build_host_mesh does both.
+int build_host_boxes(const bddc_mesh* mesh, const bddc_partition* part, HostMesh& hm);
+int build_host_interface(HostMesh& hm);
 int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh& hm);
 
 // ---------------------------------------------------------------------------

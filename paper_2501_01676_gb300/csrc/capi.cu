@@ -774,6 +774,14 @@ static int setup_impl(bddc_ctx* C) {
             C->S64 = (double*)ST;
         }
     }
+    {
+        // the interface classification on the host while the GPU assembles and
+        // eliminates the interiors (nothing above needs it)
+        const auto t0 = std::chrono::steady_clock::now();
+        BDDC_TRY(build_host_interface(hm));
+        C->nG = (int)hm.gamma.size();
+        C->stats.t_mesh_ms += ms_since(t0);
+    }
     C->phase_mark(2);
     // interface maps
     std::vector<int> gl;
@@ -2313,7 +2321,7 @@ static int copy_coeff(bddc_ctx* C, double** dst, const double* src, size_t n, in
 static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, const bddc_partition* part) {
     const auto t0 = std::chrono::steady_clock::now();
     BDDC_TRY(stage_reset());
-    BDDC_TRY(build_host_mesh(mesh, part, C->hm));
+    BDDC_TRY(build_host_boxes(mesh, part, C->hm));
     HostMesh& hm = C->hm;
     for (const SubInfo& S : hm.sub)
         if (S.nI > BDDC_MAX_INTERIOR) {
@@ -2346,7 +2354,6 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     }
     for (int d = 0; d < 3; ++d) C->bconst[d] = k->beta_const[d];
     C->c = k->c;
-    C->nG = (int)hm.gamma.size();
     if (C->o.mlp_params && C->o.learned_skip_p >= 0.0) {
         std::vector<float> hp(C->o.mlp_params, C->o.mlp_params + BDDC_MLP_PARAMS);
         BDDC_TRY(C->upload(&C->mlp_params, hp));

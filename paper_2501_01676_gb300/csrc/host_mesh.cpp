@@ -6,7 +6,7 @@
 
 #include "bddc_internal.h"
 
-int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh& hm) {
+int build_host_boxes(const bddc_mesh* mesh, const bddc_partition* part, HostMesh& hm) {
     if (!part) return BDDC_EINVAL;
     for (int d = 0; d < 3; ++d) {
         if (part->nsub[d] < 1 || !part->elems_per_slab[d]) return BDDC_EINVAL;
@@ -72,6 +72,15 @@ int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh&
                 S.dofs = std::move(in);
                 S.dofs.insert(S.dofs.end(), bd.begin(), bd.end());
             }
+    return BDDC_OK;
+}
+
+int build_host_interface(HostMesh& hm) {
+    const int Ex = hm.E[0], Ey = hm.E[1], Ez = hm.E[2];
+    auto dof_of = [&](int ix, int iy, int iz) -> int {
+        if (ix <= 0 || iy <= 0 || iz <= 0 || ix >= Ex || iy >= Ey || iz >= Ez) return -1;
+        return (ix - 1) + (Ex - 1) * ((iy - 1) + (Ey - 1) * (iz - 1));
+    };
     // interface classification by the owner set n(x).  In a tensor partition the
     // owner set of node (ix, iy, iz) is fixed by one code per direction: 2s for
     // the plane between slabs s-1 and s (shared by both), 2s+1 for the inside of
@@ -171,4 +180,9 @@ int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh&
         for (int b = 0; b < S.nB; ++b) loc[S.dofs[S.nI + b]] = -1;
     }
     return BDDC_OK;
+}
+
+int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh& hm) {
+    const int rc = build_host_boxes(mesh, part, hm);
+    return rc != BDDC_OK ? rc : build_host_interface(hm);
 }
