@@ -260,6 +260,80 @@ template int assemble_launch<float>(const HostMesh&, double, double, const void*
                                     const int*, const int*, const long long*, const int*, const int*, float*,
                                     const long long*, const int*, double*, double*, cudaStream_t);
 
+// Local index of every node of each subdomain's box (x fastest): the interior
+// dofs first, in box order, then the interface dofs in box order, -1 for nodes on
+// the Dirichlet boundary: the order of the subdomain's dof list.  Interior ranks
+// follow from the position in the interior sub-box; interface ranks from a
+// block-wide prefix count over the box, in tiles of LUT_THREADS x LUT_PER nodes
+// (thread t takes LUT_PER consecutive nodes).  One CTA per subdomain.
+constexpr int LUT_THREADS = 256, LUT_PER = 4;
+__global__ void __launch_bounds__(LUT_THREADS) k_build_lut(int Ex, int Ey, int Ez, const int* __restrict__ box0,
+                                                           const int* __restrict__ boxn,
+                                                           const long long* __restrict__ lut_off, int* __restrict__ lut) {
+    const int s = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int b0x = box0[3 * s], b0y = box0[3 * s + 1], b0z = box0[3 * s + 2];
+    const int nx = boxn[3 * s], ny = boxn[3 * s + 1], nz = boxn[3 * s + 2];
+    const long long nn = (long long)nx * ny * nz;
+    const int nI = max(nx - 2, 0) * max(ny - 2, 0) * max(nz - 2, 0);
+    int* L = lut + lut_off[s];
+    __shared__ int wsum[LUT_THREADS / 32];
+    int carry = 0;
+    for (long long base = 0; base < nn; base += (long long)LUT_THREADS * LUT_PER) {
+        int kind[LUT_PER], cnt = 0;
+        int ix[LUT_PER], iy[LUT_PER], iz[LUT_PER];
+#pragma unroll
+        for (int u = 0; u < LUT_PER; ++u) {
+            const long long q = base + (long long)t * LUT_PER + u;
+            kind[u] = 0;
+            ix[u] = iy[u] = iz[u] = 0;
+            if (q < nn) {
+                ix[u] = (int)(q % nx);
+                iy[u] = (int)((q / nx) % ny);
+                iz[u] = (int)(q / ((long long)nx * ny));
+                const int gx = b0x + ix[u], gy = b0y + iy[u], gz = b0z + iz[u];
+                const bool dir = gx <= 0 || gy <= 0 || gz <= 0 || gx >= Ex || gy >= Ey || gz >= Ez;
+                const bool in = ix[u] > 0 && ix[u] < nx - 1 && iy[u] > 0 && iy[u] < ny - 1 && iz[u] > 0 && iz[u] < nz - 1;
+                kind[u] = dir ? 0 : (in ? 1 : 2);
+                cnt += kind[u] == 2;
+            }
+        }
+        // exclusive prefix of the interface counts over the block
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        int wpre = 0, tot = 0;
+        for (int w = 0; w < LUT_THREADS / 32; ++w) {
+            wpre += w < wid ? wsum[w] : 0;
+            tot += wsum[w];
+        }
+        int r = carry + wpre + incl - cnt;
+#pragma unroll
+        for (int u = 0; u < LUT_PER; ++u) {
+            const long long q = base + (long long)t * LUT_PER + u;
+            if (q >= nn) continue;
+            if (kind[u] == 1) L[q] = (ix[u] - 1) + (nx - 2) * ((iy[u] - 1) + (ny - 2) * (iz[u] - 1));
+            else if (kind[u] == 2) L[q] = nI + r++;
+            else L[q] = -1;
+        }
+        carry += tot;
+        __syncthreads();      // wsum is rewritten by the next tile
+    }
+}
+
+int build_lut_run(const HostMesh& hm, const int* box0, const int* boxn, const long long* lut_off, int* lut,
+                  cudaStream_t st) {
+    if (hm.nsd <= 0) return BDDC_OK;
+    k_build_lut<<<hm.nsd, LUT_THREADS, 0, st>>>(hm.E[0], hm.E[1], hm.E[2], box0, boxn, lut_off, lut);
+    bddc_note_launches(1);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+
 // Global FP64 residual r = F - A u with the 27-point stencil (refinement).
 __global__ void k_stencil_residual(const double* __restrict__ S, const double* __restrict__ u,
                                    const double* __restrict__ F, double* __restrict__ r, int fx,

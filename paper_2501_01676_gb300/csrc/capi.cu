@@ -37,6 +37,8 @@
 
 int assemble_tables_bytes();
 void assemble_tables(const HostMesh& hm, void* out);
+int build_lut_run(const HostMesh& hm, const int* box0, const int* boxn, const long long* lut_off, int* lut,
+                  cudaStream_t st);
 template <class TA>
 int assemble_launch(const HostMesh& hm, double tau, double c, const void* tables, const double* nu,
                     const double* beta, const double* f, const double* divb, const double bconst[3],
@@ -683,31 +685,20 @@ static int setup_impl(bddc_ctx* C) {
     BDDC_TRY(C->alloc(&A, atot));
     C->A = A;
     BDDC_CUDA_TRY(cudaMemsetAsync(A, 0, atot * sizeof(T), st));
-    std::vector<int> lut, box0(3 * nsd), boxn(3 * nsd);
+    // node -> local index table of every subdomain box, built on the GPU (k_build_lut)
+    std::vector<int> box0(3 * nsd), boxn(3 * nsd);
     std::vector<long long> lut_off(nsd);
-    std::vector<int> loc(hm.ndof, -1);
+    long long lut_n = 0;
     for (int s = 0; s < nsd; ++s) {
         SubInfo& S = hm.sub[s];
-        lut_off[s] = (long long)lut.size();
-        for (int l = 0; l < S.n; ++l) loc[S.dofs[l]] = l;
-        int bn[3];
+        lut_off[s] = lut_n;
+        long long nb = 1;
         for (int d = 0; d < 3; ++d) {
             box0[3 * s + d] = S.box0[d];
-            bn[d] = S.box1[d] - S.box0[d] + 1;
-            boxn[3 * s + d] = bn[d];
+            boxn[3 * s + d] = S.box1[d] - S.box0[d] + 1;
+            nb *= boxn[3 * s + d];
         }
-        for (int iz = 0; iz < bn[2]; ++iz)
-            for (int iy = 0; iy < bn[1]; ++iy)
-                for (int ix = 0; ix < bn[0]; ++ix) {
-                    int gx = S.box0[0] + ix, gy = S.box0[1] + iy, gz = S.box0[2] + iz;
-                    int v = -1;
-                    if (gx > 0 && gy > 0 && gz > 0 && gx < hm.E[0] && gy < hm.E[1] && gz < hm.E[2]) {
-                        int d = (gx - 1) + (hm.E[0] - 1) * ((gy - 1) + (hm.E[1] - 1) * (gz - 1));
-                        v = loc[d];
-                    }
-                    lut.push_back(v);
-                }
-        for (int l = 0; l < S.n; ++l) loc[S.dofs[l]] = -1;
+        lut_n += nb;
     }
     std::vector<int> slab[3];
     for (int d = 0; d < 3; ++d)
@@ -715,10 +706,11 @@ static int setup_impl(bddc_ctx* C) {
             for (int e = hm.off[d][s]; e < hm.off[d][s + 1]; ++e) slab[d].push_back(s);
     int *d_lut, *d_box0, *d_boxn, *d_sx, *d_sy, *d_sz, *d_ald;
     long long *d_lutoff, *d_aoff;
-    BDDC_TRY(C->upload(&d_lut, lut));
     BDDC_TRY(C->upload(&d_lutoff, lut_off));
     BDDC_TRY(C->upload(&d_box0, box0));
     BDDC_TRY(C->upload(&d_boxn, boxn));
+    BDDC_TRY(C->alloc(&d_lut, (size_t)std::max(lut_n, 1LL)));
+    BDDC_TRY(build_lut_run(hm, d_box0, d_boxn, d_lutoff, d_lut, st));
     BDDC_TRY(C->upload(&d_sx, slab[0]));
     BDDC_TRY(C->upload(&d_sy, slab[1]));
     BDDC_TRY(C->upload(&d_sz, slab[2]));
