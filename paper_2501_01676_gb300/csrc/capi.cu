@@ -869,7 +869,9 @@ static int setup_impl(bddc_ctx* C) {
                 const int off = (int)permv.size();
                 permv.insert(permv.end(), ev.begin(), ev.end());
                 permv.insert(permv.end(), fpos[s].begin(), fpos[s].end());
-                gj.push_back(GatherJob{C->S64 + C->soff[s], C->sld[s], S.nB, off, 1, nullptr, r4(S.nB), nullptr});
+                // from S^(i) in the working precision (in the mixed solver S64 is its FP64 copy:
+                // the same values, twice the bytes)
+                gj.push_back(GatherJob{nullptr, C->sld[s], S.nB, off, 1, nullptr, r4(S.nB), ST + C->soff[s]});
                 items.push_back(EngItem<T>{nullptr, S.nB, nEV[s], r4(S.nB)});
             }
             T* W1 = nullptr;
@@ -905,7 +907,8 @@ static int setup_impl(bddc_ctx* C) {
                         if (b < f0 || b >= f0 + nF) permv.push_back(b);
                     for (int b = 0; b < nF; ++b) permv.push_back(f0 + b);
                     const int l1 = r4(hm.sub[s].nB);
-                    gj2.push_back(GatherJob{nullptr, l1, n2, off, 1, FB + f2o[q], r4(n2),
+                    // (no symmetrisation here: the face GEP reads the symmetric part of its result)
+                    gj2.push_back(GatherJob{nullptr, l1, n2, off, 0, FB + f2o[q], r4(n2),
                                             W1 + w1o[s] + (long long)nEV[s] * l1 + nEV[s]});
                     items2.push_back(EngItem<T>{FB + f2o[q], n2, n2 - nF, r4(n2)});
                     cj.push_back(CopyJob{FB + f2o[q], r4(n2), n2 - nF, n2 - nF, nF, nF,
