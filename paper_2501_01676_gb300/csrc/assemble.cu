@@ -64,11 +64,11 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(
     double* __restrict__ stencil, double* __restrict__ F) {
     __shared__ AsmTables tb;
     __shared__ double sb[ASM_EPB][8][3], sf[ASM_EPB][8], sdv[ASM_EPB][8];
-    __shared__ double bg[ASM_EPB][27][8], Lp[ASM_EPB][27][8], wLp[ASM_EPB][27][8];
-    __shared__ double wf[ASM_EPB][27], cq[ASM_EPB][27];
+    __shared__ double bg[ASM_EPB][27][8], Lp[ASM_EPB][27][8], wbg[ASM_EPB][27][8], cN[ASM_EPB][27][8];
+    __shared__ double wf[ASM_EPB][27];
     __shared__ double Pm[ASM_EPB][8][9];
+    __shared__ double Gs[ASM_EPB][36], Rs[ASM_EPB][36], Fs[ASM_EPB][8][2];
     __shared__ double bmx[ASM_EPB][2];
-    __shared__ double CKs[ASM_EPB];
     {
         const double* src = reinterpret_cast<const double*>(tab);
         double* dst = reinterpret_cast<double*>(&tb);
@@ -112,14 +112,14 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(
             }
             const double w = tb.w[t];
             wf[slot][t] = w * ff;
-            cq[slot][t] = w * (P.c - 0.5 * dd);
+            const double cqv = w * (P.c - 0.5 * dd);
             for (int a = 0; a < 8; ++a) {
                 const double* g = &tb.G[(t * 8 + a) * 3];
                 const double v = b0 * g[0] + b1 * g[1] + b2 * g[2];
-                const double l = v + P.c * tb.N[t * 8 + a];
                 bg[slot][t][a] = v;
-                Lp[slot][t][a] = l;
-                wLp[slot][t][a] = w * l;
+                Lp[slot][t][a] = v + P.c * tb.N[t * 8 + a];
+                wbg[slot][t][a] = w * v;
+                cN[slot][t][a] = cqv * tb.N[t * 8 + a];
             }
             bm = b0 * b0 + b1 * b1 + b2 * b2;
         } else if (act && t >= 32 && t < 40) {
@@ -130,32 +130,67 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(
         for (int o = 16; o > 0; o >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
         if (lane == 0) bmx[slot][t >> 5] = bm;
         __syncthreads();
-        // GLS part sum_q w L phi_j L phi_i and P_ij = sum_q w N_i beta.grad phi_j
+        // The 27-point sums of the element matrix and load vector as work units of
+        // one sum each, spread over all the CTA's threads (unit u: u < 160 G_ij,
+        // 160 <= u < 320 the reaction R_ij, both on the upper triangle i <= j of the
+        // symmetric parts; 320 <= u < 576 P_ij; 576 <= u < 640 the load sums):
+        //   G_ij = sum_q w (beta.grad phi_i)(beta.grad phi_j),  R_ij = sum_q w c~ phi_i phi_j,
+        //   P_ij = sum_q w phi_i beta.grad phi_j,  F1_i = sum_q w f phi_i,  F2_i = sum_q w f L phi_i.
+        // With L phi = beta.grad phi + c phi the GLS sum is exactly
+        //   sum_q w L phi_i L phi_j = G_ij + c (P_ij + P_ji) + c^2 M0_ij.
+        for (int u = threadIdx.x; u < 640; u += ASM_THREADS) {
+            double acc = 0.0;
+            if (u < 320) {
+                const bool gk = u < 160;
+                const int v = gk ? u : u - 160;
+                const int sl = v / 40, e36 = v - sl * 40;
+                if (e36 >= 36 || e0 + sl >= nelem || (!gk && !divb_node)) continue;
+                // packed upper triangle: e36 -> (i, j), i <= j
+                int i = 0, r = e36;
+                while (r >= 8 - i) { r -= 8 - i; ++i; }
+                const int j = i + r;
+                if (gk) {
+#pragma unroll 9
+                    for (int q = 0; q < 27; ++q) acc += wbg[sl][q][i] * bg[sl][q][j];
+                    Gs[sl][e36] = acc;
+                } else {
+#pragma unroll 9
+                    for (int q = 0; q < 27; ++q) acc += cN[sl][q][i] * tb.N[q * 8 + j];
+                    Rs[sl][e36] = acc;
+                }
+            } else if (u < 576) {
+                const int v = u - 320, sl = v >> 6, i = (v >> 3) & 7, j = v & 7;
+                if (e0 + sl >= nelem) continue;
+#pragma unroll 9
+                for (int q = 0; q < 27; ++q) acc += tb.wN[q * 8 + i] * bg[sl][q][j];
+                Pm[sl][i][j] = acc;
+            } else {
+                const int v = u - 576, sl = v >> 4, i = (v >> 1) & 7, part = v & 1;
+                if (e0 + sl >= nelem) continue;
+                if (part == 0) {
+#pragma unroll 9
+                    for (int q = 0; q < 27; ++q) acc += wf[sl][q] * tb.N[q * 8 + i];
+                } else {
+#pragma unroll 9
+                    for (int q = 0; q < 27; ++q) acc += wf[sl][q] * Lp[sl][q][i];
+                }
+                Fs[sl][i][part] = acc;
+            }
+        }
+        __syncthreads();
         const int i = t >> 3, j = t & 7;      // test i, trial j
-        double gls = 0.0, pij = 0.0, reac = 0.0, CK = 0.0;
         if (act) {
             const double bmax = sqrt(fmax(bmx[slot][0], bmx[slot][1]));
             const double nu = nu_elem[e];
             const double PK = hK * bmax / (2.0 * nu);
-            CK = (PK >= 1.0) ? P.tau * hK / (2.0 * bmax) : P.tau * hK * hK / (4.0 * nu);
-#pragma unroll 9
-            for (int q = 0; q < 27; ++q) {
-                gls += wLp[slot][q][j] * Lp[slot][q][i];
-                pij += tb.wN[q * 8 + i] * bg[slot][q][j];
-            }
-            if (divb_node) {
-                for (int q = 0; q < 27; ++q) reac += cq[slot][q] * tb.N[q * 8 + i] * tb.N[q * 8 + j];
-            } else {
-                reac = P.c * tb.M0[i * 8 + j];
-            }
-            Pm[slot][i][j] = pij;
-        }
-        __syncthreads();
-        if (act) {
-            const double acc = nu_elem[e] * tb.K0[i * 8 + j] + CK * gls + reac + 0.5 * (pij - Pm[slot][j][i]);
-            double fl = 0.0;
-            if (j == 0)
-                for (int q = 0; q < 27; ++q) fl += wf[slot][q] * (tb.N[q * 8 + i] + CK * Lp[slot][q][i]);
+            const double CK = (PK >= 1.0) ? P.tau * hK / (2.0 * bmax) : P.tau * hK * hK / (4.0 * nu);
+            const int lo = i < j ? i : j, hi = i < j ? j : i;
+            const int e36 = lo * 8 - (lo * (lo - 1)) / 2 + (hi - lo);
+            const double pij = Pm[slot][i][j], pji = Pm[slot][j][i];
+            const double gls = Gs[slot][e36] + P.c * (pij + pji) + P.c * P.c * tb.M0[i * 8 + j];
+            const double reac = divb_node ? Rs[slot][e36] : P.c * tb.M0[i * 8 + j];
+            const double acc = nu * tb.K0[i * 8 + j] + CK * gls + reac + 0.5 * (pij - pji);
+            const double fl = j == 0 ? Fs[slot][i][0] + CK * Fs[slot][i][1] : 0.0;
             // node indices of the entry
             const int ix = ex + (i & 1), iy = ey + ((i >> 1) & 1), iz = ez + ((i >> 2) & 1);
             const int jx = ex + (j & 1), jy = ey + ((j >> 1) & 1), jz = ez + ((j >> 2) & 1);
