@@ -154,6 +154,13 @@ typedef struct {
                                 the last solve's GMRES cycles of at most 128
                                 iterations: an estimate of the condition number
                                 of S M^-1 (0: not computed)                       */
+    int gemv_rows;           /* rows per work item of the S x kernel, picked at
+                                setup by timing 32, 64, 128 and 256 on the
+                                context's own operators (the first setup of a
+                                shape class in the process measures; later ones
+                                reuse the choice)                                  */
+    double gemv_tune_us;     /* the chosen list's time per product when this setup
+                                measured it (0: the choice was reused)             */
 } bddc_stats;
 
 typedef struct bddc_ctx bddc_ctx;

@@ -52,7 +52,8 @@ class Stats(ct.Structure):
                 ("t_face_ms", ct.c_double), ("t_edge_ms", ct.c_double), ("t_coarse_ms", ct.c_double),
                 ("jacobi_sweeps_max", ct.c_int), ("t_mesh_ms", ct.c_double), ("t_basis_ms", ct.c_double),
                 ("coarse_path", ct.c_int), ("coarse_fronts", ct.c_int), ("coarse_levels", ct.c_int),
-                ("coarse_factor_gflop", ct.c_double), ("kappa_est", ct.c_double)]
+                ("coarse_factor_gflop", ct.c_double), ("kappa_est", ct.c_double),
+                ("gemv_rows", ct.c_int), ("gemv_tune_us", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -25,6 +25,8 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <functional>
+#include <tuple>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -664,6 +666,62 @@ static int coarse_nd_solve(bddc_ctx* C, double* y2, const int* skip) {
                                       C->ndBwdBytes[d]));
     }
     return BDDC_OK;
+}
+
+// Rows per S x work item, chosen by measurement: every candidate's item list is
+// timed on the context's own operators (CUDA events on the setup stream, one
+// warm-up launch, the mean of three), the first time a shape class (subdomains,
+// interface rows, precision) is seen in the process; later setups of the class
+// reuse the choice.  The measurement waits for the setup work queued before it.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, long long, int>, int> g_tune_rows;
+
+template <class T>
+static int tune_gemv_rows(bddc_ctx* C, const std::vector<GemvItem>& iS0, int rb0,
+                          const std::function<void(std::vector<GemvItem>&, int)>& build, int* rb_out,
+                          double* us_out) {
+    *rb_out = rb0;
+    *us_out = 0.0;
+    double *x = nullptr, *y = nullptr;
+    BDDC_TRY(C->alloc(&x, (size_t)C->nG));
+    BDDC_TRY(C->alloc(&y, (size_t)C->nG));
+    BDDC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * C->nG, C->st));
+    BDDC_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * C->nG, C->st));
+    cudaEvent_t e0, e1;
+    BDDC_CUDA_TRY(cudaEventCreate(&e0));
+    BDDC_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e300;
+    int rc = BDDC_OK;
+    for (int rb : {32, 64, 128, 256}) {
+        std::vector<GemvItem> v;
+        if (rb == rb0) v = iS0;
+        else build(v, rb);
+        GemvItem* d = nullptr;
+        if ((rc = C->upload(&d, v)) != BDDC_OK) break;
+        const int nit = (int)v.size();
+        if ((rc = gemv_run<T>((const T*)C->ST, d, nit, C->gidx_pool, x, y, C->maxcols, 1, 0, 0, C->st, nullptr)) !=
+            BDDC_OK)
+            break;
+        if (cudaEventRecord(e0, C->st) != cudaSuccess) { rc = BDDC_ECUDA; break; }
+        for (int r = 0; r < 3 && rc == BDDC_OK; ++r)
+            rc = gemv_run<T>((const T*)C->ST, d, nit, C->gidx_pool, x, y, C->maxcols, 1, 0, 0, C->st, nullptr);
+        if (rc != BDDC_OK) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, C->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = BDDC_ECUDA;
+            break;
+        }
+        const double us = 1000.0 * ms / 3.0;
+        if (us < best) {
+            best = us;
+            *rb_out = rb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == BDDC_OK) *us_out = best;
+    return rc;
 }
 
 template <class T>
@@ -1472,11 +1530,13 @@ static int setup_impl(bddc_ctx* C) {
     long long rows_tot = 0;
     for (int s = 0; s < nsd; ++s) rows_tot += hm.sub[s].nB;
     const int RBs = (int)std::max(32LL, std::min(128LL, (rows_tot / (4 * 152) + 31) / 32 * 32));
+    std::vector<int> og_s(nsd);
     for (int s = 0; s < nsd; ++s) {
         SubInfo& S = hm.sub[s];
         int nB = S.nB, nps = C->np_s[s];
         C->maxcols = std::max(C->maxcols, nB);
         int og = (int)gi.size();
+        og_s[s] = og;
         gi.insert(gi.end(), S.gidx.begin(), S.gidx.end());
         int orp = (int)gi.size();
         for (int q = 0; q < nps; ++q) gi.push_back(idxv[rpi_off[s] + q]);
@@ -1516,6 +1576,35 @@ static int setup_impl(bddc_ctx* C) {
         C->bytesC = 8.0 * nPi * nPi + 24.0 * nPi;
     }
     BDDC_TRY(C->upload(&C->gidx_pool, gi));
+    {
+        // rows per S x work item: measured once per shape class and process
+        auto build = [&](std::vector<GemvItem>& v, int rb) {
+            for (int s = 0; s < nsd; ++s) split(v, C->soff[s], hm.sub[s].nB, hm.sub[s].nB, C->sld[s], og_s[s], og_s[s], rb);
+        };
+        const auto key = std::make_tuple(nsd, rows_tot, (int)sizeof(T));
+        int rb = RBs;
+        double us = 0.0;
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto f = g_tune_rows.find(key);
+            if (f != g_tune_rows.end()) {
+                rb = f->second;
+                have = true;
+            }
+        }
+        if (!have) {
+            BDDC_TRY(tune_gemv_rows<T>(C, iS, RBs, build, &rb, &us));
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_rows[key] = rb;
+        }
+        if (rb != RBs) {
+            iS.clear();
+            build(iS, rb);
+        }
+        C->stats.gemv_rows = rb;
+        C->stats.gemv_tune_us = us;
+    }
     BDDC_TRY(C->upload(&C->itS, iS));
     BDDC_TRY(C->upload(&C->itM1, iM1));
     BDDC_TRY(C->upload(&C->itC, iC));

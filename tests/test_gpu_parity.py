@@ -77,6 +77,25 @@ def test_schur_apply(name):
     assert rel(y, o.apply_S(x)) < 1e-10
 
 
+def test_gemv_rows_measured_once_per_shape():
+    """The rows per S x work item are picked at setup by timing the candidates on
+    the context's operators: the choice is one of them, a second setup of the same
+    shape reuses it without measuring, and its S x still equals the oracle's."""
+    import torch
+    o = oracle_for("uneven")
+    s1 = solver(o.prob)
+    st1 = s1.stats()
+    assert st1["gemv_rows"] in (32, 64, 128, 256)
+    s2 = solver(o.prob)
+    st2 = s2.stats()
+    assert st2["gemv_rows"] == st1["gemv_rows"] and st2["gemv_tune_us"] == 0.0
+    x = np.random.default_rng(5).standard_normal(o.nG)
+    y = s2.schur_apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, o.apply_S(x)) < 1e-10
+    s1.close()
+    s2.close()
+
+
 def _match_entities(s, o, kind_code, kind_char):
     ge = s.entities(kind_code)
     oe = [(i, e) for i, e in enumerate(o.mesh.entities) if e['kind'] == kind_char]
