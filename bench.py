@@ -223,6 +223,62 @@ def summary(ms, st):
     return out
 
 
+# The paper's Table 4 (m = 6), row nu_1 = 1, nu_2 = 1e-7: iterations (pnumF, pnumE)
+# of ABDDC-OLD and ABDDC-NEW for Tests 1-3 (P1 tetrahedra, MATLAB) - context only.
+EX41_PAPER_M6 = {"old": {1: (9, 4, 20), 2: (9, 3, 17), 3: (7, 0, 30)},
+                 "new": {1: (10, 4, 9), 2: (11, 3, 6), 3: (10, 0, 6)}}
+
+
+def example41_part(B, W, stream, flush):
+    """Example 4.1 (Sect. 4) at m = 6, nu_1 = 1, nu_2 = 1e-7: the P1 Kuhn-tetrahedron
+    discretisation with u = 1 on z = 0, Tests 1-3, the new and the conventional edge
+    GEP, FP64 solver: iterations, (pnumF, pnumE), time to solve."""
+    try:
+        out = {"workload": "Example 4.1: 2x2x2 cubic subdomains of 6^3 cubes split into six P1 tetrahedra, "
+                           "c = 1, a = (-2 pi y, 2 pi x, sin 2 pi x), u = 1 on z = 0, nu_1 = 1, nu_2 = 1e-7",
+               "paper_table4_row": EX41_PAPER_M6}
+        for test in (1, 2, 3):
+            p = W.example41(test=test, m=6, nu1=1.0, nu2=1e-7)
+            arrays = B.resident_arrays(p)
+            for name, mode in (("new", B.EDGE_NEW), ("old", B.EDGE_OLD)):
+                ms, st, _ = timed(B, p, stream, arrays, B.PREC_FP64, flush, 2, edge_gep=mode)
+                out[f"test{test}_{name}"] = {"ms": round(ms, 3), "iters": st["iters"], "pnumF": st["pnumF"],
+                                             "pnumE": st["pnumE"], "relres_global": st["relres_global"]}
+        return out
+    except Exception as e:        # reported in the line, never fatal to the benchmark
+        return {"error": repr(e)[:300]}
+
+
+# The paper's random-viscosity table: n(m) -> OLD and NEW iterations (pnumF, pnumE).
+EX41_PAPER_RANDOM = {"2(4)": ((10, 4, 8), (11, 4, 0)), "2(8)": ((12, 14, 33), (15, 14, 0)),
+                     "2(12)": ((13, 15, 51), (16, 15, 9)), "3(4)": ((13, 18, 60), (17, 18, 0)),
+                     "3(8)": ((17, 64, 201), (25, 64, 18)), "3(12)": ((18, 72, 301), (24, 72, 54)),
+                     "4(4)": ((15, 52, 187), (24, 52, 18)), "4(8)": ((19, 181, 593), (36, 181, 112)),
+                     "4(12)": ((19, 181, 909), (30, 181, 309))}
+
+
+def example41_random_part(B, W, stream, flush):
+    """Example 4.1's data on n^3 cubic subdomains of m^3 cubes (P1) with a random
+    viscosity 10^U(-3,3) per cube, n(m) as in the paper's random-viscosity table, the
+    new and the conventional edge GEP, FP64 solver."""
+    try:
+        out = {"workload": "Example 4.1 data on n^3 subdomains of m^3 cubes (six P1 tetrahedra each), "
+                           "nu = 10^U(-3,3) per cube (seeded)", "paper_old_new": EX41_PAPER_RANDOM}
+        for n in (2, 3, 4):
+            for m in (4, 8, 12):
+                p = W.example41_random(n, m)
+                arrays = B.resident_arrays(p)
+                row = {}
+                for name, mode in (("new", B.EDGE_NEW), ("old", B.EDGE_OLD)):
+                    ms, st, _ = timed(B, p, stream, arrays, B.PREC_FP64, flush, 1, edge_gep=mode)
+                    row[name] = {"ms": round(ms, 3), "iters": st["iters"], "pnumF": st["pnumF"],
+                                 "pnumE": st["pnumE"]}
+                out[f"{n}({m})"] = row
+        return out
+    except Exception as e:        # reported in the line, never fatal to the benchmark
+        return {"error": repr(e)[:300]}
+
+
 def run_ours(args):
     import torch
 
@@ -333,6 +389,8 @@ def run_ours(args):
     ms2, st2, u2 = timed(B, p2, stream, a2, B.PREC_MIXED, flush, max(1, min(args.steps, 10)), **learned)
     ms2_64, st2_64, u2_64 = timed(B, p2, stream, a2, B.PREC_FP64, flush, few)
     apply = apply_bandwidth(B, W, hbm, which) if args.apply else None
+    ex41 = example41_part(B, W, stream, flush)
+    ex41r = example41_random_part(B, W, stream, flush)
     out = {
         "metric": METRIC, "value": round(ms_step, 4), "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": False,
@@ -355,6 +413,8 @@ def run_ours(args):
         "channel_workload": {"workload": WORKLOAD_C5, "learned_skip": summary(ms5, st5),
                              "without_skip": summary(ms5_ns, st5_ns), "conventional_edge_gep": summary(ms5_old, st5_old)},
         "workload_4x4x4": {"workload": WORKLOAD_C2, "mixed": summary(ms2, st2), "plain_fp64": summary(ms2_64, st2_64)},
+        "example_4_1": ex41,
+        "example_4_1_random_nu": ex41r,
         "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

@@ -63,6 +63,10 @@ extern "C" {
                                Schur complements of B^(k) onto E; the comparison
                                method of the paper's ABDDC-OLD columns            */
 
+#define BDDC_ELEM_Q1   0    /* trilinear hexahedra (bricks)                        */
+#define BDDC_ELEM_P1   1    /* linear tetrahedra: each brick split into the six
+                               tetrahedra around its main diagonal (Sect. 4)       */
+
 /* Box [lo, hi]^3; the unit cube when both are zero. */
 typedef struct { double lo[3], hi[3]; } bddc_mesh;
 
@@ -79,7 +83,11 @@ typedef struct { int nsub[3]; const int* elems_per_slab[3]; } bddc_partition;
  *                          in which case beta_const is used everywhere
  *   f_node    [nnodes]     source at the nodes, or NULL (f = 0)
  *   divb_node [nnodes]     div(beta) at the nodes, or NULL (0)
- * beta, f and div(beta) are interpolated trilinearly inside each element. */
+ *   g_node    [nnodes]     Dirichlet values at the nodes (only the boundary
+ *                          nodes' are used), or NULL (homogeneous); they enter
+ *                          the loads of the neighbouring free nodes
+ * beta, f and div(beta) are interpolated trilinearly inside each element (Q1),
+ * or linearly inside each tetrahedron (element BDDC_ELEM_P1). */
 typedef struct {
     const double* nu_elem;
     const double* beta_node;
@@ -88,6 +96,7 @@ typedef struct {
     const double* f_node;
     const double* divb_node;
     int mem;
+    const double* g_node;
 } bddc_coeffs;
 
 typedef struct {
@@ -122,6 +131,9 @@ typedef struct {
     int cond_est;          /* 1: estimate the condition number of the preconditioned
                               operator from every GMRES cycle's Hessenberg
                               (stats.kappa_est); 0: skip                           */
+    int element;           /* BDDC_ELEM_Q1: trilinear bricks; BDDC_ELEM_P1: linear
+                              elements on the six tetrahedra of each brick around
+                              its main diagonal (Sect. 4, Example 4.1)            */
 } bddc_opts;
 
 typedef struct {
@@ -169,7 +181,7 @@ typedef struct bddc_ctx bddc_ctx;
  * tau = 0.7, FP64, no restart, 300 iterations, rtol 1e-8, new edge GEP,
  * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip, tensor-core
  * trailing updates in the MIXED path (tensor_cores 1), coarse_elim 0,
- * apply_launch 0, cond_est 1. */
+ * apply_launch 0, cond_est 1, element BDDC_ELEM_Q1. */
 void bddc_default_opts(bddc_opts* o);
 
 /* Setup (call stack: assembly, batched Dirichlet factorisation + Schur

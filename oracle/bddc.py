@@ -160,7 +160,9 @@ class BDDC:
         self.all_primal = all_primal
         self.ref_choice = ref_choice or {}
         f_node = prob.f_node if prob.f_node is not None else np.zeros(prob.beta_node.shape[0])
-        Ae, Fe, nodes = fem.element_matrices(mesh, prob.nu_elem, prob.beta_node, f_node, prob.c)
+        Ae, Fe, nodes = fem.element_matrices(mesh, prob.nu_elem, prob.beta_node, f_node, prob.c,
+                                             element=getattr(prob, 'element', 'q1'))
+        Fe = fem.lift_dirichlet(mesh, Ae, Fe, nodes, getattr(prob, 'dirichlet_node', None))
         self.Ae, self.Fe, self.enodes = Ae, Fe, nodes
         self.A, F = fem.assemble_global(mesh, Ae, Fe, nodes)
         self.F = F if prob.load is None else np.asarray(prob.load, dtype=float)

@@ -1,4 +1,5 @@
-"""Stabilised Q1 finite elements for -div(nu grad u) + beta.grad u + c u = f.
+"""Stabilised Q1 (and P1 Kuhn-tetrahedron) finite elements for
+-div(nu grad u) + beta.grad u + c u = f.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
@@ -16,6 +17,13 @@ variational problem a = b + z = g), with these readings:
   zero the P_K < 1 branch of C(x) is taken.
 * 3x3x3 Gauss-Legendre quadrature on every element.
 * Entry (i,j) of an element matrix is a(phi_j, phi_i): trial j, test i.
+* P1 (the paper's element, Sect. 4): each brick split into the six Kuhn
+  tetrahedra around its main diagonal; per tetrahedron beta, f, div(beta) are
+  interpolated linearly from its vertices, ||beta||_{K,inf} is the largest
+  vertex |beta|, h_K its diameter (the brick's diagonal), and a 4-point degree-2
+  rule integrates every term exactly; the brick's 8 x 8 matrix is the sum.
+* Non-homogeneous Dirichlet values g enter through the element loads
+  (lift_dirichlet).
 """
 from __future__ import annotations
 
@@ -70,13 +78,98 @@ def element_nodes(mesh):
     return out
 
 
+def p1_tables(h):
+    """The six Kuhn tetrahedra of a brick h[0] x h[1] x h[2] (Sect. 4: each cube
+    divided into six tetrahedra): tetrahedron k for the k-th permutation p of the
+    axes has the vertices 0, e_p0, e_p0 + e_p1, (1,1,1) (local node a has the
+    coordinate bits a & 1, a >> 1 & 1, a >> 2 & 1, so the vertices are the local
+    nodes 0, 1 << p0, 1 << p0 | 1 << p1, 7); all six share the main diagonal, and
+    the same split in every brick is conforming.  Returns vid (6,4) local node ids,
+    G (6,4,3) gradients of the barycentric coordinates, the volume of one
+    tetrahedron, and the 4-point degree-2 rule: lam (4 points, 4 barycentric
+    coordinates) with equal weights volume / 4."""
+    import itertools
+    vid = np.zeros((6, 4), dtype=int)
+    G = np.zeros((6, 4, 3))
+    xyz = np.array([[(a & 1) * h[0], ((a >> 1) & 1) * h[1], ((a >> 2) & 1) * h[2]] for a in range(8)])
+    vol = 0.0
+    for k, p in enumerate(itertools.permutations(range(3))):
+        v1 = 1 << p[0]
+        v2 = v1 | (1 << p[1])
+        vid[k] = [0, v1, v2, 7]
+        P = xyz[vid[k]]
+        D = P[1:] - P[0]                                      # rows P_k - P_0
+        Dit = np.linalg.inv(D).T                               # row k-1: grad lambda_k
+        G[k, 1:] = Dit
+        G[k, 0] = -Dit.sum(axis=0)
+        vol = abs(np.linalg.det(D)) / 6.0
+    a = (5.0 + 3.0 * np.sqrt(5.0)) / 20.0
+    b = (5.0 - np.sqrt(5.0)) / 20.0
+    lam = np.full((4, 4), b)
+    np.fill_diagonal(lam, a)
+    return vid, G, vol, lam
+
+
+def _p1_element_matrices(mesh, nu, beta, fa, dva, c, tau):
+    """Brick matrices of the P1 discretisation on the six Kuhn tetrahedra of each
+    brick: the tetrahedra's 4 x 4 matrices and loads summed into the brick's 8
+    nodes.  Per tetrahedron, as for Q1 (Sect. 2 forms): nu from the brick, beta, f
+    and div(beta) interpolated linearly from its 4 vertices, ||beta||_{K,inf} the
+    largest |beta| over its vertices, h_K its diameter (the brick's diagonal),
+    the 4-point degree-2 rule (exact: every integrand is at most quadratic)."""
+    hx, hy, hz = mesh.h
+    vid, G, vol, lam = p1_tables(mesh.h)
+    E = beta.shape[0]
+    hK = np.sqrt(hx * hx + hy * hy + hz * hz)
+    A = np.zeros((E, 8, 8))
+    F = np.zeros((E, 8))
+    w = np.full(4, vol / 4.0)
+    for k in range(6):
+        v = vid[k]
+        bv = beta[:, v, :]                                     # (E,4,3)
+        bq = np.einsum('qa,ead->eqd', lam, bv)
+        fq = np.einsum('qa,ea->eq', lam, fa[:, v])
+        dq = np.einsum('qa,ea->eq', lam, dva[:, v])
+        bmax = np.linalg.norm(bv, axis=2).max(axis=1)
+        PK = hK * bmax / (2.0 * nu)
+        with np.errstate(divide='ignore', invalid='ignore'):
+            C_adv = tau * hK / (2.0 * bmax)
+        C_dif = tau * hK * hK / (4.0 * nu)
+        CK = np.where(PK >= 1.0, C_adv, C_dif)
+        bg = np.einsum('eqd,ad->eqa', bq, G[k])                # beta.grad lambda_a at q
+        Lphi = bg + c * lam[None, :, :]
+        ct = c - 0.5 * dq
+        diff = nu[:, None, None] * vol * (G[k] @ G[k].T)[None, :, :]
+        stab = np.einsum('e,q,eqj,eqi->eij', CK, w, Lphi, Lphi)
+        reac = np.einsum('q,eq,qj,qi->eij', w, ct, lam, lam)
+        skew = 0.5 * (np.einsum('q,eqj,qi->eij', w, bg, lam) - np.einsum('q,eqi,qj->eij', w, bg, lam))
+        At = diff + stab + reac + skew
+        Ft = np.einsum('q,eq,qi->ei', w, fq, lam) + np.einsum('e,q,eq,eqi->ei', CK, w, fq, Lphi)
+        A[:, v[:, None], v[None, :]] += At
+        F[:, v] += Ft
+    return A, F
+
+
+def lift_dirichlet(mesh, Ae, Fe, nodes, g_node):
+    """Non-homogeneous Dirichlet values: u = g on the boundary nodes enters as the
+    load correction F_i -= sum_j a(phi_j, phi_i) g_j over the boundary nodes j of
+    each element (the free-dof system of u - (the boundary interpolant of g))."""
+    if g_node is None:
+        return Fe
+    bnd = node_to_dof(mesh)[nodes] < 0                          # (E,8)
+    gb = np.where(bnd, np.asarray(g_node, dtype=float)[nodes], 0.0)
+    return Fe - np.einsum('eij,ej->ei', Ae, gb)
+
+
 def element_matrices(mesh, nu_elem, beta_node, f_node, c=0.0, divb_node=None, tau=TAU,
-                     elems=None):
+                     elems=None, element='q1'):
     """Element matrices A[e,i,j] = a_K(phi_j, phi_i) and loads F[e,i] = g_K(phi_i).
 
     Sect. 2: b(u,v) = int nu grad u.grad v + C Lu Lv + c~ u v,
     z(u,v) = 1/2 int (beta.grad u v - beta.grad v u),
     g(v) = int f v + C f Lv, with P_K and C(x) as defined there.
+    element 'q1': trilinear bricks; 'p1': linear elements on the six Kuhn
+    tetrahedra of each brick (Sect. 4), returned per brick.
     """
     nodes = element_nodes(mesh)
     if elems is not None:
@@ -85,6 +178,11 @@ def element_matrices(mesh, nu_elem, beta_node, f_node, c=0.0, divb_node=None, ta
     else:
         nu = np.asarray(nu_elem, dtype=float)
     hx, hy, hz = mesh.h
+    if element == 'p1':
+        fa = np.asarray(f_node, dtype=float)[nodes]
+        dva = np.zeros_like(fa) if divb_node is None else np.asarray(divb_node, dtype=float)[nodes]
+        A, F = _p1_element_matrices(mesh, nu, np.asarray(beta_node, dtype=float)[nodes], fa, dva, c, tau)
+        return A, F, nodes
     N, G, wq = q1_tables(mesh.h)
     detJ = hx * hy * hz
     beta = np.asarray(beta_node, dtype=float)[nodes]          # (E,8,3)

@@ -19,6 +19,7 @@ OK, NOT_CONVERGED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 PREC_FP64, PREC_MIXED, PREC_BF16 = 0, 1, 2
 EDGE_NONE, EDGE_NEW, EDGE_OLD = 0, 1, 2
+ELEM_Q1, ELEM_P1 = 0, 1
 
 
 class Mesh(ct.Structure):
@@ -31,7 +32,8 @@ class Partition(ct.Structure):
 
 class Coeffs(ct.Structure):
     _fields_ = [("nu_elem", ct.c_void_p), ("beta_node", ct.c_void_p), ("beta_const", ct.c_double * 3),
-                ("c", ct.c_double), ("f_node", ct.c_void_p), ("divb_node", ct.c_void_p), ("mem", ct.c_int)]
+                ("c", ct.c_double), ("f_node", ct.c_void_p), ("divb_node", ct.c_void_p), ("mem", ct.c_int),
+                ("g_node", ct.c_void_p)]
 
 
 class Opts(ct.Structure):
@@ -40,7 +42,8 @@ class Opts(ct.Structure):
                 ("rtol", ct.c_double), ("edge_gep", ct.c_int), ("face_gep", ct.c_int),
                 ("all_primal", ct.c_int), ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
                 ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p), ("tensor_cores", ct.c_int),
-                ("coarse_elim", ct.c_int), ("apply_launch", ct.c_int), ("cond_est", ct.c_int)]
+                ("coarse_elim", ct.c_int), ("apply_launch", ct.c_int), ("cond_est", ct.c_int),
+                ("element", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -217,8 +220,9 @@ def resident_arrays(problem, pinned_host=False):
     pinned host memory (for end-to-end timing through host pointers)."""
     import torch
     out = {}
-    for name in ("nu_elem", "beta_node", "f_node"):
-        arr = getattr(problem, name)
+    for name, attr in (("nu_elem", "nu_elem"), ("beta_node", "beta_node"), ("f_node", "f_node"),
+                       ("g_node", "dirichlet_node")):
+        arr = getattr(problem, attr, None)
         if arr is None:
             out[name] = None
             continue
@@ -245,6 +249,7 @@ class Solver:
                          max_iter=problem.max_iter)
         if problem.theta_F is not None:
             o.theta_F = problem.theta_F
+        o.element = ELEM_P1 if getattr(problem, "element", "q1") == "p1" else ELEM_Q1
         self._mlp = None
         for k, v in opts.items():
             if k == "mlp_params":
@@ -263,7 +268,8 @@ class Solver:
         mesh = Mesh()
         co = Coeffs()
         self._keep = []
-        fields = {"nu_elem": problem.nu_elem, "beta_node": problem.beta_node, "f_node": problem.f_node}
+        fields = {"nu_elem": problem.nu_elem, "beta_node": problem.beta_node, "f_node": problem.f_node,
+                  "g_node": getattr(problem, "dirichlet_node", None)}
         for name, arr in fields.items():
             if arrays is not None:
                 t = arrays.get(name)

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(
     const int* __restrict__ lut, const long long* __restrict__ lut_off,
     const int* __restrict__ box0, const int* __restrict__ boxn,
     TA* __restrict__ Aloc, const long long* __restrict__ a_off, const int* __restrict__ a_ld,
-    double* __restrict__ stencil, double* __restrict__ F) {
+    double* __restrict__ stencil, double* __restrict__ F, const double* __restrict__ gnode) {
     __shared__ AsmTables tb;
     __shared__ double sb[ASM_EPB][8][3], sf[ASM_EPB][8], sdv[ASM_EPB][8];
     __shared__ double bg[ASM_EPB][27][8], Lp[ASM_EPB][27][8], wbg[ASM_EPB][27][8], cN[ASM_EPB][27][8];
@@ -206,18 +206,222 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(
                 const int lj = lut[lut_off[s] + (jx - b0[0]) + bn[0] * ((jy - b0[1]) + bn[1] * (jz - b0[2]))];
                 atomicAdd(&Aloc[a_off[s] + (long long)li * a_ld[s] + lj], (TA)acc);
             }
+            // Dirichlet values on the boundary node j enter the load of node i
+            if (gnode && di >= 0 && dj < 0)
+                atomicAdd(&F[di], -acc * gnode[jx + (long long)(Ex + 1) * (jy + (long long)(Ey + 1) * jz)]);
             if (j == 0 && di >= 0) atomicAdd(&F[di], fl);
         }
         __syncthreads();       // the slot's shared data is rewritten by the next element
     }
 }
 
+// P1 on the six Kuhn tetrahedra of each brick (Sect. 4): tetrahedron k holds the
+// local nodes vid[k] = {0, 1 << p0, 1 << p0 | 1 << p1, 7} for the k-th axis
+// permutation p; G its barycentric gradients, pos[k][a] the position of brick node
+// a in it (-1: not a vertex), the 4-point degree-2 rule lam[q][a] with weights
+// vol / 4.
+struct AsmTablesP1 {
+    double G[6][4][3];
+    double lam[4][4];
+    double vol;
+    int vid[6][4];
+    int pos[6][8];
+};
+
+// Brick matrices of the P1 discretisation, four bricks per CTA (64 threads each):
+// (1) nodal data; (2) per (tetrahedron, point) beta, f, c~ and beta.grad lambda_a by
+// linear interpolation from the tetrahedron's vertices, and per tetrahedron the
+// weight C(x) from its largest vertex |beta| and h_K = the brick's diagonal; (3)
+// the 96 tetrahedron matrix entries and 24 loads, each a 4-point sum; (4) one
+// thread per brick entry sums the tetrahedra holding both nodes and scatters as
+// for Q1 (dense A^(s), stencil, loads, Dirichlet lifting).
+template <class TA>
+__global__ void __launch_bounds__(ASM_THREADS) k_assemble_p1(
+    AsmScalars P, const AsmTablesP1* __restrict__ tab, int nelem,
+    const double* __restrict__ nu_elem, const double* __restrict__ beta_node,
+    const double* __restrict__ f_node, const double* __restrict__ divb_node, double3 beta_const,
+    const int* __restrict__ slab_of_x, const int* __restrict__ slab_of_y,
+    const int* __restrict__ slab_of_z, int nsx, int nsy,
+    const int* __restrict__ lut, const long long* __restrict__ lut_off,
+    const int* __restrict__ box0, const int* __restrict__ boxn,
+    TA* __restrict__ Aloc, const long long* __restrict__ a_off, const int* __restrict__ a_ld,
+    double* __restrict__ stencil, double* __restrict__ F, const double* __restrict__ gnode) {
+    __shared__ AsmTablesP1 tb;
+    __shared__ double sb[ASM_EPB][8][3], sf[ASM_EPB][8], sdv[ASM_EPB][8], sn2[ASM_EPB][8];
+    __shared__ double bgq[ASM_EPB][6][4][4], Lq[ASM_EPB][6][4][4], fq[ASM_EPB][6][4], ctq[ASM_EPB][6][4];
+    __shared__ double CKt[ASM_EPB][6], Mt[ASM_EPB][6][4][4], Ft[ASM_EPB][6][4];
+    {
+        const int* src = reinterpret_cast<const int*>(tab);
+        int* dst = reinterpret_cast<int*>(&tb);
+        for (int q = threadIdx.x; q < (int)(sizeof(AsmTablesP1) / sizeof(int)); q += ASM_THREADS) dst[q] = src[q];
+    }
+    __syncthreads();
+    const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int Ex = P.E[0], Ey = P.E[1];
+    const double hK = sqrt(P.h[0] * P.h[0] + P.h[1] * P.h[1] + P.h[2] * P.h[2]);
+    const double w = 0.25 * tb.vol;
+    for (int e0 = blockIdx.x * ASM_EPB; e0 < nelem; e0 += gridDim.x * ASM_EPB) {
+        const int e = e0 + slot;
+        const bool act = e < nelem;
+        const int ex = act ? e % Ex : 0, ey = act ? (e / Ex) % Ey : 0, ez = act ? e / (Ex * Ey) : 0;
+        if (act && t < 8) {
+            const int ix = ex + (t & 1), iy = ey + ((t >> 1) & 1), iz = ez + ((t >> 2) & 1);
+            const long long nd = ix + (long long)(Ex + 1) * (iy + (long long)(Ey + 1) * iz);
+            double b0 = beta_const.x, b1 = beta_const.y, b2 = beta_const.z;
+            if (beta_node) {
+                b0 = beta_node[3 * nd];
+                b1 = beta_node[3 * nd + 1];
+                b2 = beta_node[3 * nd + 2];
+            }
+            sb[slot][t][0] = b0;
+            sb[slot][t][1] = b1;
+            sb[slot][t][2] = b2;
+            sn2[slot][t] = b0 * b0 + b1 * b1 + b2 * b2;
+            sf[slot][t] = f_node ? f_node[nd] : 0.0;
+            sdv[slot][t] = divb_node ? divb_node[nd] : 0.0;
+        }
+        __syncthreads();
+        if (act && t < 24) {
+            const int k = t >> 2, q = t & 3;
+            double b0 = 0, b1 = 0, b2 = 0, ff = 0, dd = 0;
+            for (int a = 0; a < 4; ++a) {
+                const int v = tb.vid[k][a];
+                const double l = tb.lam[q][a];
+                b0 += l * sb[slot][v][0];
+                b1 += l * sb[slot][v][1];
+                b2 += l * sb[slot][v][2];
+                ff += l * sf[slot][v];
+                dd += l * sdv[slot][v];
+            }
+            for (int a = 0; a < 4; ++a) {
+                const double g = b0 * tb.G[k][a][0] + b1 * tb.G[k][a][1] + b2 * tb.G[k][a][2];
+                bgq[slot][k][q][a] = g;
+                Lq[slot][k][q][a] = g + P.c * tb.lam[q][a];
+            }
+            fq[slot][k][q] = ff;
+            ctq[slot][k][q] = P.c - 0.5 * dd;
+        } else if (act && t >= 32 && t < 38) {
+            const int k = t - 32;
+            double m2 = 0.0;
+            for (int a = 0; a < 4; ++a) m2 = fmax(m2, sn2[slot][tb.vid[k][a]]);
+            const double bmax = sqrt(m2), nu = nu_elem[e];
+            const double PK = hK * bmax / (2.0 * nu);
+            CKt[slot][k] = (PK >= 1.0) ? P.tau * hK / (2.0 * bmax) : P.tau * hK * hK / (4.0 * nu);
+        }
+        __syncthreads();
+        if (act) {
+            const double nu = nu_elem[e];
+            for (int u = t; u < 120; u += 64) {
+                if (u < 96) {
+                    const int k = u >> 4, a = (u >> 2) & 3, b = u & 3;      // test a, trial b
+                    const double* Ga = tb.G[k][a];
+                    const double* Gb = tb.G[k][b];
+                    double st = 0.0, re = 0.0, sk = 0.0;
+                    for (int q = 0; q < 4; ++q) {
+                        st += Lq[slot][k][q][b] * Lq[slot][k][q][a];
+                        re += ctq[slot][k][q] * tb.lam[q][a] * tb.lam[q][b];
+                        sk += bgq[slot][k][q][b] * tb.lam[q][a] - bgq[slot][k][q][a] * tb.lam[q][b];
+                    }
+                    Mt[slot][k][a][b] = nu * tb.vol * (Ga[0] * Gb[0] + Ga[1] * Gb[1] + Ga[2] * Gb[2]) +
+                                        w * (CKt[slot][k] * st + re + 0.5 * sk);
+                } else {
+                    const int v = u - 96, k = v >> 2, a = v & 3;
+                    double s1 = 0.0, s2 = 0.0;
+                    for (int q = 0; q < 4; ++q) {
+                        s1 += fq[slot][k][q] * tb.lam[q][a];
+                        s2 += fq[slot][k][q] * Lq[slot][k][q][a];
+                    }
+                    Ft[slot][k][a] = w * (s1 + CKt[slot][k] * s2);
+                }
+            }
+        }
+        __syncthreads();
+        if (act) {
+            const int i = t >> 3, j = t & 7;      // test i, trial j
+            double acc = 0.0, fl = 0.0;
+            for (int k = 0; k < 6; ++k) {
+                const int pi = tb.pos[k][i], pj = tb.pos[k][j];
+                if (pi >= 0 && pj >= 0) acc += Mt[slot][k][pi][pj];
+                if (j == 0 && pi >= 0) fl += Ft[slot][k][pi];
+            }
+            const int ix = ex + (i & 1), iy = ey + ((i >> 1) & 1), iz = ez + ((i >> 2) & 1);
+            const int jx = ex + (j & 1), jy = ey + ((j >> 1) & 1), jz = ez + ((j >> 2) & 1);
+            const int di = dof_of(P, ix, iy, iz), dj = dof_of(P, jx, jy, jz);
+            if (di >= 0 && dj >= 0) {
+                const int o = (jx - ix + 1) + 3 * (jy - iy + 1) + 9 * (jz - iz + 1);
+                atomicAdd(&stencil[(long long)di * 27 + o], acc);
+                const int s = slab_of_x[ex] + nsx * (slab_of_y[ey] + nsy * slab_of_z[ez]);
+                const int* b0 = &box0[3 * s];
+                const int* bn = &boxn[3 * s];
+                const int li = lut[lut_off[s] + (ix - b0[0]) + bn[0] * ((iy - b0[1]) + bn[1] * (iz - b0[2]))];
+                const int lj = lut[lut_off[s] + (jx - b0[0]) + bn[0] * ((jy - b0[1]) + bn[1] * (jz - b0[2]))];
+                atomicAdd(&Aloc[a_off[s] + (long long)li * a_ld[s] + lj], (TA)acc);
+            }
+            if (gnode && di >= 0 && dj < 0)
+                atomicAdd(&F[di], -acc * gnode[jx + (long long)(Ex + 1) * (jy + (long long)(Ey + 1) * jz)]);
+            if (j == 0 && di >= 0) atomicAdd(&F[di], fl);
+        }
+        __syncthreads();       // the slot's shared data is rewritten by the next brick
+    }
+}
+
 }  // namespace
 
+// The P1 tables of the brick h[0] x h[1] x h[2]: the six Kuhn tetrahedra (vertex
+// coordinates from the node bits), their barycentric gradients (the rows of the
+// inverse transpose of the edge matrix [x1 - x0; x2 - x0; x3 - x0], the first
+// gradient minus their sum), one tetrahedron's volume, and the symmetric 4-point
+// rule with barycentric coordinates (5 +- 3 sqrt 5) / 20 and (5 - sqrt 5) / 20.
+static void assemble_tables_p1(const HostMesh& hm, AsmTablesP1& P) {
+    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    double xyz[8][3];
+    for (int a = 0; a < 8; ++a)
+        for (int d = 0; d < 3; ++d) xyz[a][d] = ((a >> d) & 1) * hm.h[d];
+    for (int k = 0; k < 6; ++k) {
+        const int v1 = 1 << perm[k][0], v2 = v1 | (1 << perm[k][1]);
+        const int v[4] = {0, v1, v2, 7};
+        for (int a = 0; a < 8; ++a) P.pos[k][a] = -1;
+        for (int a = 0; a < 4; ++a) {
+            P.vid[k][a] = v[a];
+            P.pos[k][v[a]] = a;
+        }
+        double D[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) D[r][d] = xyz[v[r + 1]][d] - xyz[0][d];
+        const double det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                           D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                           D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+        // inverse transpose by cofactors: (D^{-T})[r][d] = cof(D)[r][d] / det
+        double cof[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) {
+                const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+                cof[r][d] = D[r1][d1] * D[r2][d2] - D[r1][d2] * D[r2][d1];
+            }
+        for (int d = 0; d < 3; ++d) P.G[k][0][d] = 0.0;
+        for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) {
+                P.G[k][r + 1][d] = cof[r][d] / det;
+                P.G[k][0][d] -= cof[r][d] / det;
+            }
+        P.vol = fabs(det) / 6.0;
+    }
+    const double qa = (5.0 + 3.0 * sqrt(5.0)) / 20.0, qb = (5.0 - sqrt(5.0)) / 20.0;
+    for (int q = 0; q < 4; ++q)
+        for (int a = 0; a < 4; ++a) P.lam[q][a] = q == a ? qa : qb;
+}
+
 // The reference tables of the brick h[0] x h[1] x h[2]: 3-point Gauss rule per
-// direction, Q1 shape values and gradients, weights, stiffness and mass.
-int assemble_tables_bytes() { return (int)sizeof(AsmTables); }
-void assemble_tables(const HostMesh& hm, void* out) {
+// direction, Q1 shape values and gradients, weights, stiffness and mass; or the P1
+// tables (element 1).
+int assemble_tables_bytes(int element) {
+    return element == 1 ? (int)sizeof(AsmTablesP1) : (int)sizeof(AsmTables);
+}
+void assemble_tables(const HostMesh& hm, void* out, int element) {
+    if (element == 1) {
+        assemble_tables_p1(hm, *reinterpret_cast<AsmTablesP1*>(out));
+        return;
+    }
     AsmTables& P = *reinterpret_cast<AsmTables*>(out);
     const double r = sqrt(3.0 / 5.0);
     const double xg[3] = {0.5 - 0.5 * r, 0.5, 0.5 + 0.5 * r};
@@ -263,7 +467,8 @@ int assemble_launch(const HostMesh& hm, double tau, double c, const void* tables
                     const double* beta, const double* f, const double* divb, const double bconst[3],
                     const int* slab_x, const int* slab_y, const int* slab_z, const int* lut,
                     const long long* lut_off, const int* box0, const int* boxn, TA* Aloc,
-                    const long long* a_off, const int* a_ld, double* stencil, double* F, cudaStream_t st) {
+                    const long long* a_off, const int* a_ld, double* stencil, double* F, const double* gnode,
+                    int element, cudaStream_t st) {
     AsmScalars P;
     for (int d = 0; d < 3; ++d) {
         P.E[d] = hm.E[d];
@@ -275,12 +480,20 @@ int assemble_launch(const HostMesh& hm, double tau, double c, const void* tables
     int dev = 0, nsm = 0, occ = 0;
     BDDC_CUDA_TRY(cudaGetDevice(&dev));
     BDDC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_assemble<TA>, ASM_THREADS, 0));
+    if (element == 1)
+        BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_assemble_p1<TA>, ASM_THREADS, 0));
+    else
+        BDDC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_assemble<TA>, ASM_THREADS, 0));
     const long long groups = ((long long)hm.nelem + ASM_EPB - 1) / ASM_EPB;
     const int grid = (int)std::max(1LL, std::min(groups, (long long)nsm * std::max(occ, 1)));
-    k_assemble<TA><<<grid, ASM_THREADS, 0, st>>>(P, (const AsmTables*)tables, hm.nelem, nu, beta, f, divb, bc,
-                                                 slab_x, slab_y, slab_z, hm.nsub[0], hm.nsub[1], lut, lut_off,
-                                                 box0, boxn, Aloc, a_off, a_ld, stencil, F);
+    if (element == 1)
+        k_assemble_p1<TA><<<grid, ASM_THREADS, 0, st>>>(P, (const AsmTablesP1*)tables, hm.nelem, nu, beta, f, divb,
+                                                        bc, slab_x, slab_y, slab_z, hm.nsub[0], hm.nsub[1], lut,
+                                                        lut_off, box0, boxn, Aloc, a_off, a_ld, stencil, F, gnode);
+    else
+        k_assemble<TA><<<grid, ASM_THREADS, 0, st>>>(P, (const AsmTables*)tables, hm.nelem, nu, beta, f, divb, bc,
+                                                     slab_x, slab_y, slab_z, hm.nsub[0], hm.nsub[1], lut, lut_off,
+                                                     box0, boxn, Aloc, a_off, a_ld, stencil, F, gnode);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
@@ -289,11 +502,13 @@ int assemble_launch(const HostMesh& hm, double tau, double c, const void* tables
 template int assemble_launch<double>(const HostMesh&, double, double, const void*, const double*, const double*,
                                      const double*, const double*, const double*, const int*, const int*,
                                      const int*, const int*, const long long*, const int*, const int*, double*,
-                                     const long long*, const int*, double*, double*, cudaStream_t);
+                                     const long long*, const int*, double*, double*, const double*, int,
+                                     cudaStream_t);
 template int assemble_launch<float>(const HostMesh&, double, double, const void*, const double*, const double*,
                                     const double*, const double*, const double*, const int*, const int*,
                                     const int*, const int*, const long long*, const int*, const int*, float*,
-                                    const long long*, const int*, double*, double*, cudaStream_t);
+                                    const long long*, const int*, double*, double*, const double*, int,
+                                     cudaStream_t);
 
 // Local index of every node of each subdomain's box (x fastest): the interior
 // dofs first, in box order, then the interface dofs in box order, -1 for nodes on
@@ -407,8 +622,8 @@ int stencil_residual(const HostMesh& hm, const double* S, const double* u, const
 // ---------------------------------------------------------------------------
 namespace {
 __global__ void k_validate(const double* __restrict__ nu, long long nelem, const double* __restrict__ beta,
-                           const double* __restrict__ f, const double* __restrict__ divb, long long nnodes,
-                           int* __restrict__ bad) {
+                           const double* __restrict__ f, const double* __restrict__ divb,
+                           const double* __restrict__ g, long long nnodes, int* __restrict__ bad) {
     int b = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nelem; e += stride)
@@ -417,17 +632,18 @@ __global__ void k_validate(const double* __restrict__ nu, long long nelem, const
         if (beta && (!isfinite(beta[3 * q]) || !isfinite(beta[3 * q + 1]) || !isfinite(beta[3 * q + 2]))) b = 1;
         if (f && !isfinite(f[q])) b = 1;
         if (divb && !isfinite(divb[q])) b = 1;
+        if (g && !isfinite(g[q])) b = 1;
     }
     if (b) atomicOr(bad, 1);
 }
 }  // namespace
 
 int validate_coeffs_run(const double* nu, long long nelem, const double* beta, const double* f, const double* divb,
-                        long long nnodes, int* dflag, cudaStream_t st) {
+                        const double* g, long long nnodes, int* dflag, cudaStream_t st) {
     BDDC_CUDA_TRY(cudaMemsetAsync(dflag, 0, sizeof(int), st));
     const long long n = std::max(nelem, nnodes);
     const int blocks = (int)std::min<long long>((n + 255) / 256, 1184);
-    k_validate<<<std::max(blocks, 1), 256, 0, st>>>(nu, nelem, beta, f, divb, nnodes, dflag);
+    k_validate<<<std::max(blocks, 1), 256, 0, st>>>(nu, nelem, beta, f, divb, g, nnodes, dflag);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;

@@ -252,6 +252,7 @@ int wait_selftest_run(long long limit, int* timed_out);
 // finite; NULL arrays are skipped): *flag_dev (device int) = 1 when one fails.
 // Asynchronous on st.
 int validate_coeffs_run(const double* nu, long long nelem, const double* beta, const double* f, const double* divb,
+                        const double* g,
                         long long nnodes, int* flag_dev, cudaStream_t st);
 // tasks: the restriction queue (nres items), the coarse queue (ntasks items),
 // then the local queue (nlocal items)

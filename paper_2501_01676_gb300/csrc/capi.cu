@@ -37,8 +37,8 @@
 #include "mlp.h"
 #include "setup_kernels.h"
 
-int assemble_tables_bytes();
-void assemble_tables(const HostMesh& hm, void* out);
+int assemble_tables_bytes(int element);
+void assemble_tables(const HostMesh& hm, void* out, int element);
 int build_lut_run(const HostMesh& hm, const int* box0, const int* boxn, const long long* lut_off, int* lut,
                   cudaStream_t st);
 template <class TA>
@@ -46,7 +46,7 @@ int assemble_launch(const HostMesh& hm, double tau, double c, const void* tables
                     const double* beta, const double* f, const double* divb, const double bconst[3],
                     const int* slab_x, const int* slab_y, const int* slab_z, const int* lut,
                     const long long* lut_off, const int* box0, const int* boxn, TA* Aloc,
-                    const long long* a_off, const int* a_ld, double* stencil, double* F, cudaStream_t st);
+                    const long long* a_off, const int* a_ld, double* stencil, double* F, const double* gnode, int element, cudaStream_t st);
 int stencil_residual(const HostMesh& hm, const double* S, const double* u, const double* F, double* r,
                      int nrhs, cudaStream_t st);
 // Condensation g += f_B - A_BI A_II^{-1} f_I and interior recovery, each as one
@@ -255,6 +255,7 @@ struct bddc_ctx {
 
     // coefficients
     double *nu = nullptr, *beta = nullptr, *f = nullptr, *divb = nullptr;
+    double* gdir = nullptr;     // Dirichlet values at the nodes (NULL: zero)
     double bconst[3] = {0, 0, 0};
     double c = 0.0;
     // assembly / factors
@@ -778,13 +779,14 @@ static int setup_impl(bddc_ctx* C) {
     BDDC_TRY(C->alloc(&C->F, hm.ndof));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->stencil, 0, sizeof(double) * 27 * (size_t)hm.ndof, st));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->F, 0, sizeof(double) * hm.ndof, st));
-    std::vector<char> tabs((size_t)assemble_tables_bytes());
-    assemble_tables(hm, tabs.data());
+    std::vector<char> tabs((size_t)assemble_tables_bytes(C->o.element));
+    assemble_tables(hm, tabs.data(), C->o.element);
     char* d_tabs = nullptr;
     BDDC_TRY(C->upload(&d_tabs, tabs));
     ktimer_begin(KT_ASSEMBLE, st);
     BDDC_TRY(assemble_launch<T>(hm, C->o.tau, C->c, d_tabs, C->nu, C->beta, C->f, C->divb, C->bconst, d_sx, d_sy,
-                                d_sz, d_lut, d_lutoff, d_box0, d_boxn, A, d_aoff, d_ald, C->stencil, C->F, st));
+                                d_sz, d_lut, d_lutoff, d_box0, d_boxn, A, d_aoff, d_ald, C->stencil, C->F, C->gdir,
+                                C->o.element, st));
     ktimer_end(KT_ASSEMBLE, st, 0.0, 0.0);
     C->phase_mark(1);
     // ---- 2. partial LU: S^(i) ---------------------------------------------
@@ -2336,6 +2338,7 @@ void bddc_default_opts(bddc_opts* o) {
     o->coarse_elim = 0;
     o->apply_launch = 0;
     o->cond_est = 1;
+    o->element = BDDC_ELEM_Q1;
 }
 
 const char* bddc_strerror(int code) {
@@ -2414,6 +2417,10 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
         }
     if (!k || !k->nu_elem) return BDDC_EINVAL;
     if (k->mem != BDDC_MEM_HOST && k->mem != BDDC_MEM_DEVICE) return BDDC_EINVAL;
+    if (C->o.element != BDDC_ELEM_Q1 && C->o.element != BDDC_ELEM_P1) {
+        bddc_set_last_error("element must be BDDC_ELEM_Q1 or BDDC_ELEM_P1", __FILE__, __LINE__);
+        return BDDC_EINVAL;
+    }
     if (!std::isfinite(k->c) || !std::isfinite(k->beta_const[0]) || !std::isfinite(k->beta_const[1]) ||
         !std::isfinite(k->beta_const[2])) {
         bddc_set_last_error("reaction and constant velocity must be finite", __FILE__, __LINE__);
@@ -2423,16 +2430,18 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     BDDC_TRY(copy_coeff(C, &C->beta, k->beta_node, 3 * (size_t)hm.nnodes, k->mem));
     BDDC_TRY(copy_coeff(C, &C->f, k->f_node, hm.nnodes, k->mem));
     BDDC_TRY(copy_coeff(C, &C->divb, k->divb_node, hm.nnodes, k->mem));
+    BDDC_TRY(copy_coeff(C, &C->gdir, k->g_node, hm.nnodes, k->mem));
     {
         // the coefficient arrays (host or device) are checked on the device before any other work
         int* vflag = nullptr;
         BDDC_TRY(C->alloc(&vflag, 1));
-        BDDC_TRY(validate_coeffs_run(C->nu, hm.nelem, C->beta, C->f, C->divb, hm.nnodes, vflag, C->st));
+        BDDC_TRY(validate_coeffs_run(C->nu, hm.nelem, C->beta, C->f, C->divb, C->gdir, hm.nnodes, vflag, C->st));
         int hv = 0;
         BDDC_CUDA_TRY(cudaMemcpyAsync(&hv, vflag, sizeof(int), cudaMemcpyDeviceToHost, C->st));
         BDDC_CUDA_TRY(cudaStreamSynchronize(C->st));
         if (hv) {
-            bddc_set_last_error("nu must be positive and finite; beta, f and div(beta) finite", __FILE__, __LINE__);
+            bddc_set_last_error("nu must be positive and finite; beta, f, div(beta) and the Dirichlet values finite",
+                                __FILE__, __LINE__);
             return BDDC_EINVAL;
         }
     }

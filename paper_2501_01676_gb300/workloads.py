@@ -40,6 +40,8 @@ class Problem:
     rtol: float = 1e-8
     max_iter: int = 300
     meta: dict = field(default_factory=dict)
+    element: str = 'q1'                  # 'q1' bricks, 'p1' the six Kuhn tetrahedra of each brick
+    dirichlet_node: Optional[np.ndarray] = None   # Dirichlet values at the nodes (None: zero)
 
     @property
     def ne(self):
@@ -243,3 +245,47 @@ def rotating_checker(test=3, nsub=2, m=6, nu_hi=1.0, nu_lo=1e-7, c=1.0):
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
+
+
+# Example 4.1 of the paper (Sect. 4): Omega = (-1/2,1/2)^2 x (0,1), 2 x 2 x 2 cubic
+# subdomains of m^3 cubes, each cube split into six tetrahedra (P1), c = 1,
+# velocity (-2 pi y, 2 pi x, sin 2 pi x), f = 0, u = 1 on z = 0 and 0 on the rest
+# of the boundary.  The domain is the unit cube shifted by (-1/2, -1/2, 0): the grid
+# is the unit cube's and the velocity is evaluated at the shifted coordinates.
+# Subdomain numbering (reading of "anticlockwise helicoidal"): Omega_1..Omega_4
+# anticlockwise around the bottom layer from (x < 0, y < 0), Omega_5..Omega_8 the same
+# in the top layer, the only order that gives Omega_8 = (-1/2,0) x (0,1/2) x (1/2,1)
+# and Test 1's halves x < 0 / x > 0.  Tests 1-3 give nu_1 to the subdomains listed
+# and nu_2 to the others.
+EX41_HELIX = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+EX41_TESTS = {1: (1, 4, 5, 8), 2: (1, 5, 6, 8), 3: (1, 3, 6, 8)}
+
+
+def example41(test=1, m=6, nu1=1.0, nu2=1e-7, theta_E=10.0):
+    slabs = [[m, m], [m, m], [m, m]]
+    ne, h, X, Y, Z = _grid(slabs)
+    sub = _elem_subdomain(slabs)
+    nu_sub = np.full(8, nu2)
+    for k in EX41_TESTS[test]:
+        sx, sy, sz = EX41_HELIX[k - 1]
+        nu_sub[sx + 2 * (sy + 2 * sz)] = nu1
+    x, y = X - 0.5, Y - 0.5
+    beta = np.stack([-2 * np.pi * y, 2 * np.pi * x, np.sin(2 * np.pi * x)], axis=1)
+    g = np.where(np.isclose(Z, 0.0), 1.0, 0.0)
+    return Problem(f"example41_test{test}_m{m}", slabs, nu_sub[sub], beta, None, c=1.0, theta_E=theta_E,
+                   element='p1', dirichlet_node=g, meta={"test": test, "m": m, "nu": (nu1, nu2)})
+
+
+def example41_random(n=2, m=4, seed_offset=6, theta_E=10.0):
+    """Example 4.1's domain, velocity, reaction and boundary data on n x n x n cubic
+    subdomains of m^3 cubes (P1 tetrahedra) with a random viscosity per cube,
+    nu = 10^r, r ~ U(-3, 3) (Sect. 4, the random-viscosity table, columns n(m))."""
+    slabs = [[m] * n, [m] * n, [m] * n]
+    ne, h, X, Y, Z = _grid(slabs)
+    rng = np.random.default_rng([20250103 + seed_offset, n, m])
+    nu = 10.0 ** rng.uniform(-3.0, 3.0, ne[0] * ne[1] * ne[2])
+    x, y = X - 0.5, Y - 0.5
+    beta = np.stack([-2 * np.pi * y, 2 * np.pi * x, np.sin(2 * np.pi * x)], axis=1)
+    g = np.where(np.isclose(Z, 0.0), 1.0, 0.0)
+    return Problem(f"example41_random_n{n}_m{m}", slabs, nu, beta, None, c=1.0, theta_E=theta_E,
+                   element='p1', dirichlet_node=g, meta={"n": n, "m": m})
