@@ -223,27 +223,39 @@ def summary(ms, st):
     return out
 
 
-# The paper's Table 4 (m = 6), row nu_1 = 1, nu_2 = 1e-7: iterations (pnumF, pnumE)
-# of ABDDC-OLD and ABDDC-NEW for Tests 1-3 (P1 tetrahedra, MATLAB) - context only.
-EX41_PAPER_M6 = {"old": {1: (9, 4, 20), 2: (9, 3, 17), 3: (7, 0, 30)},
-                 "new": {1: (10, 4, 9), 2: (11, 3, 6), 3: (10, 0, 6)}}
+# The paper's Tables 4 (m = 6, row nu_1 = 1, nu_2 = 1e-7) and 5 (m = 4, 8, 16):
+# iterations (pnumF, pnumE) of ABDDC-OLD and ABDDC-NEW for Tests 1-3 (P1
+# tetrahedra, MATLAB) - context only.
+EX41_PAPER = {4: {"old": ((8, 4, 12), (9, 3, 10), (7, 0, 18)), "new": ((9, 4, 3), (10, 3, 3), (9, 0, 6))},
+              6: {"old": ((9, 4, 20), (9, 3, 17), (7, 0, 30)), "new": ((10, 4, 9), (11, 3, 6), (10, 0, 6))},
+              8: {"old": ((10, 4, 28), (10, 3, 24), (7, 0, 42)), "new": ((11, 4, 10), (12, 3, 7), (15, 0, 6))},
+              16: {"old": ((12, 6, 61), (11, 5, 55), (8, 4, 90)), "new": ((14, 6, 24), (16, 5, 12), (16, 4, 9))}}
 
 
 def example41_part(B, W, stream, flush):
-    """Example 4.1 (Sect. 4) at m = 6, nu_1 = 1, nu_2 = 1e-7: the P1 Kuhn-tetrahedron
-    discretisation with u = 1 on z = 0, Tests 1-3, the new and the conventional edge
-    GEP, FP64 solver: iterations, (pnumF, pnumE), time to solve."""
+    """Example 4.1 (Sect. 4) at m = 4, 6, 8, 16, nu_1 = 1, nu_2 = 1e-7: the P1
+    Kuhn-tetrahedron discretisation with u = 1 on z = 0, Tests 1-3, the new and the
+    conventional edge GEP, FP64 solver: iterations, (pnumF, pnumE), time to solve
+    (one setup + solve; m = 16 has faces of 225 and interiors of 3375 dofs)."""
     try:
-        out = {"workload": "Example 4.1: 2x2x2 cubic subdomains of 6^3 cubes split into six P1 tetrahedra, "
+        out = {"workload": "Example 4.1: 2x2x2 cubic subdomains of m^3 cubes split into six P1 tetrahedra, "
                            "c = 1, a = (-2 pi y, 2 pi x, sin 2 pi x), u = 1 on z = 0, nu_1 = 1, nu_2 = 1e-7",
-               "paper_table4_row": EX41_PAPER_M6}
-        for test in (1, 2, 3):
-            p = W.example41(test=test, m=6, nu1=1.0, nu2=1e-7)
-            arrays = B.resident_arrays(p)
-            for name, mode in (("new", B.EDGE_NEW), ("old", B.EDGE_OLD)):
-                ms, st, _ = timed(B, p, stream, arrays, B.PREC_FP64, flush, 2, edge_gep=mode)
-                out[f"test{test}_{name}"] = {"ms": round(ms, 3), "iters": st["iters"], "pnumF": st["pnumF"],
-                                             "pnumE": st["pnumE"], "relres_global": st["relres_global"]}
+               "paper_tables_4_5": {str(m): v for m, v in EX41_PAPER.items()}}
+        for m in (4, 6, 8, 16):
+            for test in (1, 2, 3):
+                p = W.example41(test=test, m=m, nu1=1.0, nu2=1e-7)
+                arrays = B.resident_arrays(p)
+                for name, mode in (("new", B.EDGE_NEW), ("old", B.EDGE_OLD)):
+                    ms, st, _ = timed(B, p, stream, arrays, B.PREC_FP64, flush, 1, warmup=1 if m < 16 else 0,
+                                      edge_gep=mode)
+                    out[f"m{m}_test{test}_{name}"] = {"ms": round(ms, 3), "iters": st["iters"],
+                                                      "pnumF": st["pnumF"], "pnumE": st["pnumE"],
+                                                      "relres_global": st["relres_global"]}
+        p = W.example41(test=1, m=16, nu1=1.0, nu2=1e-7)
+        ms, st, _ = timed(B, p, stream, B.resident_arrays(p), B.PREC_MIXED, flush, 1)
+        out["m16_test1_new_mixed"] = {"ms": round(ms, 3), "iters": st["iters"], "pnumF": st["pnumF"],
+                                      "pnumE": st["pnumE"], "relres_global": st["relres_global"],
+                                      "setup_ms": round(st["setup_ms"], 3), "solve_ms": round(st["solve_ms"], 3)}
         return out
     except Exception as e:        # reported in the line, never fatal to the benchmark
         return {"error": repr(e)[:300]}

@@ -189,8 +189,9 @@ void bddc_default_opts(bddc_opts* o);
  * constrained local solvers, coarse matrix and its FP64 inverse).
  * tol_eig > 0 overrides opts->theta_E.  stream: a cudaStream_t or NULL for
  * the legacy default stream.  On success *out owns all device memory.
- * Subdomains with more than 2048 interior dofs (a slab of more than 14
- * elements in every direction) are rejected with BDDC_EINVAL. */
+ * Subdomains with more than 8192 interior dofs (a box of more than 21
+ * elements in every direction) and faces of more than 256 dofs (more than
+ * 17 x 17 elements) are rejected with BDDC_EINVAL. */
 int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs,
                const bddc_partition* part, double tol_eig,
                const bddc_opts* opts, void* stream, bddc_ctx** out);
@@ -232,6 +233,11 @@ int bddc_gmres_solve(bddc_ctx* ctx, const double* load, double* u, int nrhs,
 int  bddc_get_stats(const bddc_ctx* ctx, bddc_stats* stats);
 void bddc_destroy(bddc_ctx* ctx);
 const char* bddc_strerror(int code);
+/* The message of the last failure recorded on the calling thread (what was
+ * rejected or which CUDA call failed, with the source location), or "" when
+ * none was recorded since the thread's last bddc_setup.  The string is owned by
+ * the library and valid until the thread's next call. */
+const char* bddc_last_error(void);
 
 /* ---- introspection (tests and benchmarks; host output buffers) ---------- */
 

@@ -85,6 +85,8 @@ def lib():
     L.bddc_destroy.argtypes = [vp]
     L.bddc_strerror.argtypes = [ct.c_int]
     L.bddc_strerror.restype = ct.c_char_p
+    L.bddc_last_error.restype = ct.c_char_p
+    L.bddc_last_error.argtypes = []
     L.bddc_get_numbering.argtypes = [vp, ip]
     L.bddc_get_schur.argtypes = [vp, ct.c_int, dp, ip]
     L.bddc_get_entity_count.argtypes = [vp, ct.c_int]
@@ -105,7 +107,7 @@ def lib():
 
 
 EXPORTED = ["bddc_default_opts", "bddc_setup", "bddc_apply", "bddc_schur_apply", "bddc_gmres_solve",
-            "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_get_numbering", "bddc_get_schur",
+            "bddc_get_stats", "bddc_destroy", "bddc_strerror", "bddc_last_error", "bddc_get_numbering", "bddc_get_schur",
             "bddc_get_entity_count", "bddc_get_entity", "bddc_get_edge_features", "bddc_kernel_launches",
             "bddc_apply_static", "bddc_kernel_timer", "bddc_kernel_timer_read", "bddc_mlp_forward",
             "bddc_mlp_loss_grad", "bddc_mlp_train", "bddc_tc_selftest", "bddc_wait_selftest"]
@@ -191,7 +193,8 @@ def kernel_launches():
 class BDDCError(RuntimeError):
     def __init__(self, code, where):
         msg = lib().bddc_strerror(code).decode()
-        super().__init__(f"{where}: {msg} (code {code})")
+        detail = lib().bddc_last_error().decode()
+        super().__init__(f"{where}: {msg} (code {code})" + (f": {detail}" if detail and detail != msg else ""))
         self.code = code
 
 

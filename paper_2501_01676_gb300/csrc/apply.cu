@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(GEMV_THREADS) k_gemv(const T* __restrict__ poo
                                                        const int* __restrict__ skip) {
     if (skip && *skip) return;
     const GemvItem it = items[blockIdx.x];
+    if (it.ncols > GEMV_MAXCOLS) return;          // never built so (items are sliced); no staging overrun
     __shared__ __align__(16) T xs[GEMV_MAXCOLS];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int* iidx = idx + it.iidx_off;
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(GEMV_THREADS) k_gemv_t(const T* __restrict__ p
                                                          const int* __restrict__ skip) {
     if (skip && *skip) return;
     const GemvItem it = items[blockIdx.x];
+    if (it.ncols > GEMV_MAXCOLS) return;
     __shared__ T xs[GEMV_MAXCOLS];
     const int t = threadIdx.x;
     const int* iidx = idx + it.iidx_off;
@@ -245,7 +247,6 @@ template int gemv_run<float>(const float*, const GemvItem*, int, const int*, con
 namespace {
 
 constexpr int TRI_THREADS = 256;
-constexpr int TRI_MAXN = BDDC_MAX_INTERIOR;
 
 struct TriItem {
     long long aoff;    // matrix offset in the factor pool
@@ -355,7 +356,8 @@ __global__ void __launch_bounds__(TRI_THREADS) k_condense(const T* __restrict__ 
                                                           double* __restrict__ ystore, int nrhs,
                                                           long long ldF, long long ldY) {
     const TriItem it = items[blockIdx.x];
-    __shared__ T y[TRI_MAXN];
+    extern __shared__ __align__(16) unsigned char tri_raw[];
+    T* y = reinterpret_cast<T*>(tri_raw);          // nI entries (the launch sizes it for the largest)
     const int t = threadIdx.x;
     const T* A = pool + it.aoff;
     const int* dofs = lists + it.dof_off;
@@ -380,7 +382,8 @@ __global__ void __launch_bounds__(TRI_THREADS) k_recover(const T* __restrict__ p
                                                          long long ldG, long long ldU,
                                                          long long ldY) {
     const TriItem it = items[blockIdx.x];
-    __shared__ T y[TRI_MAXN];
+    extern __shared__ __align__(16) unsigned char tri_raw[];
+    T* y = reinterpret_cast<T*>(tri_raw);          // nI entries (the launch sizes it for the largest)
     const int t = threadIdx.x;
     const T* A = pool + it.aoff;
     const int* dofs = lists + it.dof_off;
@@ -403,12 +406,24 @@ struct TriBatch {
     int count;
 };
 
+// Dynamic shared memory of the substitution kernels: the largest interior vector.
+template <class T, class K>
+static int tri_smem(K kern, int maxnI, size_t* bytes) {
+    if (maxnI < 1 || maxnI > BDDC_MAX_INTERIOR) return BDDC_EINVAL;
+    *bytes = (size_t)maxnI * sizeof(T);
+    if (*bytes > 48 * 1024)
+        BDDC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*bytes));
+    return BDDC_OK;
+}
+
 template <class T>
-int condense_run(const T* pool, const void* items, int count, const int* lists, const double* F,
+int condense_run(const T* pool, const void* items, int count, int maxnI, const int* lists, const double* F,
                  double* g, double* ystore, int nrhs, long long ldF, long long ldG, long long ldY,
                  const GemvItem* ci, int nci, double ci_bytes, cudaStream_t st) {
+    size_t sm = 0;
+    BDDC_TRY(tri_smem<T>(k_condense<T>, maxnI, &sm));
     ktimer_begin(KT_TRI, st);
-    k_condense<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, F, ystore, nrhs, ldF, ldY);
+    k_condense<T><<<count, TRI_THREADS, sm, st>>>(pool, (const TriItem*)items, lists, F, ystore, nrhs, ldF, ldY);
     ktimer_end(KT_TRI, st, 0.0, 0.0);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
@@ -417,13 +432,15 @@ int condense_run(const T* pool, const void* items, int count, const int* lists, 
 }
 
 template <class T>
-int recover_run(const T* pool, const void* items, int count, const int* lists, const double* uG,
+int recover_run(const T* pool, const void* items, int count, int maxnI, const int* lists, const double* uG,
                 double* ystore, double* u, int nrhs, long long ldG, long long ldU,
                 long long ldY, const GemvItem* ri, int nri, double ri_bytes, cudaStream_t st) {
     // -y += U_IB u_B
     BDDC_TRY(gemv_run<T>(pool, ri, nri, lists, uG, ystore, 0, nrhs, (int)ldG, (int)ldY, st, nullptr, ri_bytes));
+    size_t sm = 0;
+    BDDC_TRY(tri_smem<T>(k_recover<T>, maxnI, &sm));
     ktimer_begin(KT_TRI, st);
-    k_recover<T><<<count, TRI_THREADS, 0, st>>>(pool, (const TriItem*)items, lists, uG, ystore, u,
+    k_recover<T><<<count, TRI_THREADS, sm, st>>>(pool, (const TriItem*)items, lists, uG, ystore, u,
                                                 nrhs, ldG, ldU, ldY);
     ktimer_end(KT_TRI, st, 0.0, 0.0);
     bddc_note_launches(1);
@@ -444,13 +461,13 @@ void tri_item_fill(void* dst, long long aoff, int n, int nI, int ld, int dof_off
     t->yoff = yoff;
 }
 
-template int condense_run<double>(const double*, const void*, int, const int*, const double*, double*, double*,
+template int condense_run<double>(const double*, const void*, int, int, const int*, const double*, double*, double*,
                                   int, long long, long long, long long, const GemvItem*, int, double, cudaStream_t);
-template int condense_run<float>(const float*, const void*, int, const int*, const double*, double*, double*,
+template int condense_run<float>(const float*, const void*, int, int, const int*, const double*, double*, double*,
                                  int, long long, long long, long long, const GemvItem*, int, double, cudaStream_t);
-template int recover_run<double>(const double*, const void*, int, const int*, const double*, double*, double*,
+template int recover_run<double>(const double*, const void*, int, int, const int*, const double*, double*, double*,
                                  int, long long, long long, long long, const GemvItem*, int, double, cudaStream_t);
-template int recover_run<float>(const float*, const void*, int, const int*, const double*, double*, double*,
+template int recover_run<float>(const float*, const void*, int, int, const int*, const double*, double*, double*,
                                 int, long long, long long, long long, const GemvItem*, int, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------

@@ -115,8 +115,9 @@ struct DevArena {                    // all device allocations of a context
 };
 
 // Largest interior (dofs strictly inside one subdomain) the condense / recover
-// kernels hold in shared memory: 2048 = a 13^3 interior (H/h <= 13 per slab).
-constexpr int BDDC_MAX_INTERIOR = 2048;
+// kernels hold in shared memory: 8192 (a 20^3 interior, H/h <= 21 per slab; the
+// FP64 vector takes 64 KB).
+constexpr int BDDC_MAX_INTERIOR = 8192;
 
 // Coarse matrices up to this order are inverted by one CTA (FP32 Gauss-Jordan
 // in shared memory) plus FP64 Newton-Schulz steps.

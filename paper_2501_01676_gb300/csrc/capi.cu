@@ -53,11 +53,11 @@ int stencil_residual(const HostMesh& hm, const double* S, const double* u, const
 // triangular-solve kernel (CTA per subdomain) plus one batched GEMV over the
 // rectangular factor blocks (ci: L_BI, ri: U_IB).
 template <class T>
-int condense_run(const T* pool, const void* items, int count, const int* lists, const double* F,
+int condense_run(const T* pool, const void* items, int count, int maxnI, const int* lists, const double* F,
                  double* g, double* ystore, int nrhs, long long ldF, long long ldG, long long ldY,
                  const GemvItem* ci, int nci, double ci_bytes, cudaStream_t st);
 template <class T>
-int recover_run(const T* pool, const void* items, int count, const int* lists, const double* uG,
+int recover_run(const T* pool, const void* items, int count, int maxnI, const int* lists, const double* uG,
                 double* ystore, double* u, int nrhs, long long ldG, long long ldU, long long ldY,
                 const GemvItem* ri, int nri, double ri_bytes, cudaStream_t st);
 size_t tri_item_size();
@@ -304,6 +304,7 @@ struct bddc_ctx {
     void* tri = nullptr;
     int* tri_lists = nullptr;
     GemvItem *itCI = nullptr, *itRI = nullptr;   // L_BI and U_IB blocks of the interior factors
+    int max_nI = 1;                               // largest subdomain interior (substitution kernels)
     int nitCI = 0, nitRI = 0;
     double bytesCI = 0, bytesRI = 0;
     double* ystore = nullptr;
@@ -990,11 +991,12 @@ static int setup_impl(bddc_ctx* C) {
         }
         std::vector<FaceJob> fj;
         int maxn = 0;
+        for (int e : faces) maxn = std::max(maxn, (int)hm.ent[e].dofs.size());
+        const bool eig_global = face_eig_global<T>(maxn);
         for (size_t fi = 0; fi < faces.size(); ++fi) {
             int e = faces[fi];
             Entity& E = hm.ent[e];
             int n = (int)E.dofs.size();
-            maxn = std::max(maxn, n);
             FaceJob J;
             memset(&J, 0, sizeof(J));
             J.n = n;
@@ -1011,7 +1013,7 @@ static int setup_impl(bddc_ctx* C) {
             J.Btj = Bt64 + bo[fi] + (long long)n * n;
             J.ldbi = J.ldbj = n;
             T* fw = nullptr;
-            BDDC_TRY(C->alloc(&fw, face_work_doubles(n)));
+            BDDC_TRY(C->alloc(&fw, face_work_doubles(n) + (eig_global ? face_eig_doubles(n) : 0)));
             J.work = fw;
             J.Q = C->Q[e];
             J.DQi = C->DQ[e][0];
@@ -1304,7 +1306,10 @@ static int setup_impl(bddc_ctx* C) {
             int e = edges[ei];
             Entity& E = hm.ent[e];
             int n = (int)E.dofs.size(), m = (int)E.subs.size();
-            if (m > EDGE_MAX_SUBS) return BDDC_EINVAL;
+            if (m > EDGE_MAX_SUBS) {
+                bddc_set_last_error("an edge shared by more than 4 subdomains", __FILE__, __LINE__);
+                return BDDC_EINVAL;
+            }
             EdgeJob J;
             memset(&J, 0, sizeof(J));
             J.n = n;
@@ -1638,9 +1643,10 @@ static int setup_impl(bddc_ctx* C) {
             lists.insert(lists.end(), (size_t)nI, 0);
             lists.insert(lists.end(), S.gidx.begin(), S.gidx.end());
             if (nI > 0 && nB > 0) {
-                for (int r0 = 0; r0 < nB; r0 += 32)
-                    ci.push_back(GemvItem{C->aoff[s] + (long long)nI * ld, nB, nI, ld, yi, go, r0,
-                                          std::min(32, nB - r0), 0, nI});
+                for (int c0 = 0; c0 < nI; c0 += 2048)      // column slices of the kernel's staging width
+                    for (int r0 = 0; r0 < nB; r0 += 32)
+                        ci.push_back(GemvItem{C->aoff[s] + (long long)nI * ld, nB, nI, ld, yi, go, r0,
+                                              std::min(32, nB - r0), c0, std::min(2048, nI - c0)});
                 for (int c0 = 0; c0 < nB; c0 += 2048)
                     for (int r0 = 0; r0 < nI; r0 += 32)
                         ri.push_back(GemvItem{C->aoff[s], nI, S.n, ld, gp, yi, r0, std::min(32, nI - r0), nI + c0,
@@ -1649,6 +1655,7 @@ static int setup_impl(bddc_ctx* C) {
                 C->bytesRI += ts * nI * nB + iv * (nB + nI);
             }
             yo += S.nI;
+            C->max_nI = std::max(C->max_nI, S.nI);
         }
         C->ny = std::max(yo, 1LL);
         BDDC_TRY(C->upload(&C->tri_lists, lists));
@@ -1909,11 +1916,11 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
     BDDC_TRY(norm2(C, Fdev, ndof, &Fn));
     if (!C->mixed) {
         BDDC_TRY(gather_run(Fdev, C->gamma_dofs, C->g, (int)nG, st));
-        BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, Fdev, C->g, C->ystore, 1, ndof, nG, C->ny, C->itCI, C->nitCI, C->bytesCI, st));
+        BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, Fdev, C->g, C->ystore, 1, ndof, nG, C->ny, C->itCI, C->nitCI, C->bytesCI, st));
         int it = 0;
         BDDC_TRY(gmres<T>(C, C->g, C->xG, C->o.rtol, C->o.max_iter, &it, &relres, &conv));
         iters_total = it;
-        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, udev, 1, nG, ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
+        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, C->xG, C->ystore, udev, 1, nG, ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
         steps = 1;
     } else {
         // FP64 iterative refinement on the global system with FP32 BDDC-GMRES as inner solver
@@ -1926,14 +1933,14 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
                 break;
             }
             BDDC_TRY(gather_run(C->res, C->gamma_dofs, C->g, (int)nG, st));
-            BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->res, C->g, C->ystore, 1, ndof, nG, C->ny, C->itCI, C->nitCI, C->bytesCI, st));
+            BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, C->res, C->g, C->ystore, 1, ndof, nG, C->ny, C->itCI, C->nitCI, C->bytesCI, st));
             int it = 0, cv = 0;
             double rr = 0.0;
             // the loosest inner tolerance that still reaches rtol (with a factor-2 margin)
             const double tol_k = std::max(C->o.inner_rtol, 0.5 * C->o.rtol * Fn / rn);
             BDDC_TRY(gmres<T>(C, C->g, C->xG, std::min(tol_k, 0.5), C->o.max_iter - iters_total, &it, &rr, &cv));
             iters_total += it;
-            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, C->xG, C->ystore, C->corr, 1, nG, ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
+            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, C->xG, C->ystore, C->corr, 1, nG, ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
             BDDC_TRY(vec_axpby(udev, C->corr, 1.0, 1.0, ndof, st));
             BDDC_TRY(stencil_residual(hm, C->stencil, udev, Fdev, C->res, 1, st));
             BDDC_TRY(norm2(C, C->res, ndof, &rn));
@@ -2218,7 +2225,7 @@ static int solve_batch(bddc_ctx* C, BatchWS* W, const double* F, double* U, bddc
     BDDC_TRY(norms_batch(C, W, F, ndof, nb, Fn.data()));
     auto condense_cols = [&](const double* R) -> int {
         for (int c = 0; c < nb; ++c) BDDC_TRY(gather_run(R + c * ndof, C->gamma_dofs, W->g + c * nG, (int)nG, st));
-        return condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, R, W->g, W->ystore, nb, ndof, nG, C->ny,
+        return condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, R, W->g, W->ystore, nb, ndof, nG, C->ny,
                                C->itCI, C->nitCI, C->bytesCI, st);
     };
     double relres_max = 0.0;
@@ -2229,7 +2236,7 @@ static int solve_batch(bddc_ctx* C, BatchWS* W, const double* F, double* U, bddc
         for (int c = 0; c < nb; ++c) tol[c] = C->o.rtol * bn[c];
         BDDC_TRY(gmres_batch<T>(C, W, W->g, W->xG, tol.data(), bn.data(), caps.data(), it.data(), cv.data(),
                                 rr.data()));
-        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, W->xG, W->ystore, U, nb, nG, ndof, C->ny,
+        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, W->xG, W->ystore, U, nb, nG, ndof, C->ny,
                                 C->itRI, C->nitRI, C->bytesRI, st));
         for (int c = 0; c < nb; ++c) {
             itot[c] = it[c];
@@ -2263,7 +2270,7 @@ static int solve_batch(bddc_ctx* C, BatchWS* W, const double* F, double* U, bddc
                                     rr.data()));
             for (int c = 0; c < nb; ++c)
                 if (tol[c] >= 0.0) itot[c] += it[c];
-            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->tri_lists, W->xG, W->ystore, W->corr, nb, nG,
+            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, W->xG, W->ystore, W->corr, nb, nG,
                                     ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
             BDDC_TRY(vec_axpby_cols(U, ndof, W->corr, ndof, 1.0, 1.0, ndof, nb, st));
             BDDC_TRY(stencil_residual(hm, C->stencil, U, F, W->res, nb, st));
@@ -2340,6 +2347,8 @@ void bddc_default_opts(bddc_opts* o) {
     o->cond_est = 1;
     o->element = BDDC_ELEM_Q1;
 }
+
+const char* bddc_last_error(void) { return g_last_error.c_str(); }
 
 const char* bddc_strerror(int code) {
     switch (code) {
@@ -2511,6 +2520,7 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
 
 int bddc_setup(const bddc_mesh* mesh, const bddc_coeffs* coeffs, const bddc_partition* part,
                double tol_eig, const bddc_opts* opts, void* stream, bddc_ctx** out) {
+    g_last_error.clear();
     if (!out || !part || !coeffs) return BDDC_EINVAL;
     *out = nullptr;
     int dev = 0;

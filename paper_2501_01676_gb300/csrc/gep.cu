@@ -495,7 +495,7 @@ __device__ void trsm_lower_t(const T* Ls, int ldl, T* X, int ldx, int n, int m) 
 }
 
 // Largest order the tridiagonal eigen-solver handles (shared-memory vectors).
-constexpr int TRI_EIG_MAX = 128;
+constexpr int TRI_EIG_MAX = FACE_NMAX;
 
 // Sturm count: eigenvalues of the symmetric tridiagonal (d, e) below x.
 template <class T>
@@ -929,20 +929,23 @@ __device__ int qr_basis(T* C, int n, int m, T* Q, T* vbuf /* n*n */, T* norms,
 }
 
 // ------------------------------------------------------------------- face
+// ash_global: the two eigen-work matrices (A, V of the Jacobi / tridiagonal steps)
+// live in the job's global workspace after its face_work_doubles(n) elements
+// instead of shared memory (faces too large for shared memory).
 template <class T>
 __global__ void __launch_bounds__(GT) k_face(const FaceJob* __restrict__ jobs, int* __restrict__ err,
-                                             long long work_off) {
+                                             long long work_off, int ash_global) {
     const FaceJob J = jobs[blockIdx.x];
     const int n = J.n, np = (n + 1) & ~1;
     extern __shared__ __align__(16) unsigned char shm_raw[];
     T* shm = reinterpret_cast<T*>(shm_raw);
-    T* Ash = shm;
-    const int ldj = np + 1;                    // odd shared-memory row stride
-    T* Vsh = shm + np * ldj;
-    __shared__ T cs[64], sn[64];
-    __shared__ int pp[64], qq[64];
-    __shared__ int order[128];
-    __shared__ unsigned char done[256];
+    const int ldj = np + 1;                    // odd row stride (no bank conflicts in shared memory)
+    T* Ash = ash_global ? (T*)J.work + face_work_doubles(n) : shm;
+    T* Vsh = Ash + np * ldj;
+    __shared__ T cs[FACE_NMAX / 2], sn[FACE_NMAX / 2];
+    __shared__ int pp[FACE_NMAX / 2], qq[FACE_NMAX / 2];
+    __shared__ int order[FACE_NMAX];
+    __shared__ unsigned char done[2 * FACE_NMAX];
     T* w = work_off >= 0 ? shm + work_off : (T*)J.work;   // workspace in shared memory when it fits
     const int nn = n * n;
     // Workspace of 8 n^2 elements (units of n^2), reused as the steps go:
@@ -1268,7 +1271,11 @@ __global__ void __launch_bounds__(GT) k_edge(const EdgeJob* __restrict__ jobs, i
 
 }  // namespace
 
-size_t face_work_doubles(int n) { return (size_t)8 * n * n + 3 * n + 64; }
+__host__ __device__ size_t face_work_doubles(int n) { return (size_t)8 * n * n + 3 * n + 64; }
+size_t face_eig_doubles(int n) {
+    const size_t np = (size_t)((n + 1) & ~1);
+    return 2 * np * (np + 1);
+}
 size_t edge_work_doubles(int n, int m, int nH) {
     size_t nw = (size_t)(m - 1) * n, mn = (size_t)m * n, nz = mn + nH;
     return (size_t)n * n * (3 + m) + (size_t)n * mn * (1 + m) + 6 * nw * nw + 2 * nz * nz +
@@ -1297,16 +1304,28 @@ static int gep_smem(const void* fn, size_t base, size_t work_elems, size_t* smem
 }
 
 template <class T>
+bool face_eig_global(int maxn) {
+    return (size_t)face_eig_doubles(maxn) * sizeof(T) > 160 * 1024;
+}
+template bool face_eig_global<double>(int);
+template bool face_eig_global<float>(int);
+
+template <class T>
 int face_run(const FaceJob* jobs_dev, int count, int maxn, int* err, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
-    int np = (maxn + 1) & ~1;
-    const size_t base = (size_t)2 * np * (np + 1) * sizeof(T);
-    if (np > 128 || base > 200 * 1024) return BDDC_EINVAL;
+    if (maxn > FACE_NMAX) {
+        bddc_set_last_error("a face has more dofs than the face GEP kernel handles (256)", __FILE__, __LINE__);
+        return BDDC_EINVAL;
+    }
+    // the eigen-work matrices in shared memory when they fit, else in each job's
+    // workspace (allocated with face_eig_doubles(n) more elements by the caller)
+    const int glob = face_eig_global<T>(maxn) ? 1 : 0;
+    const size_t base = glob ? 0 : face_eig_doubles(maxn) * sizeof(T);
     size_t smem = 0;
     long long off = -1;
     BDDC_TRY(gep_smem<T>((const void*)k_face<T>, base, face_work_doubles(maxn), &smem, &off));
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_face<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_face<T><<<count, GT, smem, st>>>(jobs_dev, err, off);
+    k_face<T><<<count, GT, smem, st>>>(jobs_dev, err, off, glob);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
@@ -1317,7 +1336,11 @@ int edge_run(const EdgeJob* jobs_dev, int count, int maxnw, int maxnz, size_t ma
     if (count <= 0) return BDDC_OK;
     int np = (maxnw + 1) & ~1;
     const size_t base = (size_t)2 * np * (np + 1) * sizeof(T);
-    if (np > 128 || base > 200 * 1024 || maxnz > 1024) return BDDC_EINVAL;
+    if (np > 128 || base > 200 * 1024 || maxnz > 1024) {
+        bddc_set_last_error("an edge GEP larger than the edge kernel handles ((m-1) n_E <= 128, n_z <= 1024)",
+                            __FILE__, __LINE__);
+        return BDDC_EINVAL;
+    }
     size_t smem = 0;
     long long off = -1;
     BDDC_TRY(gep_smem<T>((const void*)k_edge<T>, base, max_work, &smem, &off));

@@ -4,6 +4,7 @@
 #include <stddef.h>
 
 #define EDGE_MAX_SUBS 4
+#define FACE_NMAX 256          // largest face (dofs) of the face GEP kernel
 
 struct FaceJob {
     int n;                    // face dofs n_F
@@ -17,7 +18,7 @@ struct FaceJob {
     const double* Bti;        // Schur complement of B^(i) onto F (ld ldbi)
     const double* Btj;
     int ldbi, ldbj;
-    void* work;               // face_work_doubles(n) elements of the kernel precision
+    void* work;               // face_work_doubles(n) (+ face_eig_doubles(n)) elements of the kernel precision
     double* Q;                // out: n x n orthogonal, first k columns primal (row-major)
     double* DQi;              // out: D^(i) Q
     double* DQj;              // out: D^(j) Q
@@ -49,7 +50,13 @@ struct EdgeJob {
     int* k;
 };
 
-size_t face_work_doubles(int n);
+__host__ __device__ size_t face_work_doubles(int n);
+// Elements of the two eigen-work matrices of a face of n dofs; face_eig_global<T>
+// tells whether the kernel keeps them in global memory (then every job's
+// workspace holds face_work_doubles(n) + face_eig_doubles(n) elements).
+size_t face_eig_doubles(int n);
+template <class T>
+bool face_eig_global(int maxn);
 size_t edge_work_doubles(int n, int m, int nH);
 template <class T>
 int face_run(const FaceJob* jobs_dev, int count, int maxn, int* err, cudaStream_t st);

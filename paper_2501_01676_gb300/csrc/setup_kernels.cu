@@ -68,16 +68,18 @@ __global__ void k_gather_perm(const GatherJob* __restrict__ jobs, const int* __r
 // Right multiplication Y[r][pos[l]] = sum_a B[r][pos[a]] Q[a][l] for one entity block
 // (arithmetic and the scratch Y in precision TY).
 template <class TY>
-__global__ void k_transform_right(const TBlock* __restrict__ blocks, const int* __restrict__ idx) {
+__global__ void k_transform_right(const TBlock* __restrict__ blocks, const int* __restrict__ idx, int qglob) {
     const TBlock B = blocks[blockIdx.x];
     extern __shared__ __align__(16) unsigned char qraw[];
     TY* Qs = reinterpret_cast<TY*>(qraw);
     const int n = B.n;
     const int* pos = idx + B.pos_off;
     TY* Y = (TY*)B.y;
-    if (!B.identity)
+    if (!B.identity && !qglob)
         for (int q = threadIdx.x; q < n * n; q += TH) Qs[q] = (TY)B.Q[q];
     __syncthreads();
+    // Q from shared memory, or straight from global memory (qglob: too large to stage)
+    auto Qv = [&](int a, int l) -> TY { return qglob ? (TY)B.Q[a * n + l] : Qs[a * n + l]; };
     const int rpi = n < TH ? TH / n : 1;                 // rows per CTA pass
     const int lr = (int)threadIdx.x / n, l0 = (int)threadIdx.x % n;
     if (lr >= rpi) return;
@@ -93,7 +95,7 @@ __global__ void k_transform_right(const TBlock* __restrict__ blocks, const int* 
             for (int a = 0; a < n; ++a) {
                 TY sv = (TY)row[pos[a]];
                 if (B.sym) sv = (TY)0.5 * (sv + (TY)B.src[(long long)pos[a] * B.sld + r]);
-                v += sv * Qs[a * n + l];
+                v += sv * Qv(a, l);
             }
         }
         Y[(long long)r * B.yld + pos[l]] = v;
@@ -103,7 +105,7 @@ __global__ void k_transform_right(const TBlock* __restrict__ blocks, const int* 
 // Left multiplication Z[pos[l]][c] = sum_a Q[a][l] Y[pos[a]][c] and the
 // permuted store X[perm[pos[l]]][perm[c]] = Z (entries with perm < 0 dropped).
 template <class TY, class TD>
-__global__ void k_transform_left(const TBlock* __restrict__ blocks, const int* __restrict__ idx) {
+__global__ void k_transform_left(const TBlock* __restrict__ blocks, const int* __restrict__ idx, int qglob) {
     const TBlock B = blocks[blockIdx.x];
     extern __shared__ __align__(16) unsigned char qraw[];
     TY* Qs = reinterpret_cast<TY*>(qraw);
@@ -111,9 +113,10 @@ __global__ void k_transform_left(const TBlock* __restrict__ blocks, const int* _
     const int* pos = idx + B.pos_off;
     const int* perm = idx + B.perm_off;
     const TY* Y = (const TY*)B.y;
-    if (!B.identity)
+    if (!B.identity && !qglob)
         for (int q = threadIdx.x; q < n * n; q += TH) Qs[q] = (TY)B.Q[q];
     __syncthreads();
+    auto Qv = [&](int a, int l) -> TY { return qglob ? (TY)B.Q[a * n + l] : Qs[a * n + l]; };
     TD* X = (TD*)B.dst;
     for (int l = 0; l < n; ++l)
     for (int c = blockIdx.y * TH + threadIdx.x; c < B.nrows; c += gridDim.y * TH) {
@@ -123,7 +126,7 @@ __global__ void k_transform_left(const TBlock* __restrict__ blocks, const int* _
         if (B.identity) v = Y[(long long)pos[l] * B.yld + c];
         else {
             v = 0;
-            for (int a = 0; a < n; ++a) v += Qs[a * n + l] * Y[(long long)pos[a] * B.yld + c];
+            for (int a = 0; a < n; ++a) v += Qv(a, l) * Y[(long long)pos[a] * B.yld + c];
         }
         X[(long long)pr * B.dld + pc] = (TD)v;
     }
@@ -280,13 +283,14 @@ template int gather_perm_run<float>(const GatherJob*, int, const int*, int, cuda
 template <class TD>
 int transform_run(const TBlock* blocks, int count, const int* idx, int maxn, int ychunks, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;
-    size_t smem = (size_t)maxn * maxn * sizeof(TD);
-    if (smem > 200 * 1024) return BDDC_EINVAL;
+    // Q staged in shared memory when it fits, else read from global memory (L1 / L2)
+    const int qglob = (size_t)maxn * maxn * sizeof(TD) > 200 * 1024 ? 1 : 0;
+    const size_t smem = qglob ? 0 : (size_t)maxn * maxn * sizeof(TD);
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_right<TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_transform_left<TD, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_transform_right<TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
+    k_transform_right<TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx, qglob);
     bddc_note_launches(1);
-    k_transform_left<TD, TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx);
+    k_transform_left<TD, TD><<<dim3(count, ychunks), TH, smem, st>>>(blocks, idx, qglob);
     bddc_note_launches(1);
     BDDC_CUDA_TRY(cudaGetLastError());
     return BDDC_OK;
@@ -300,7 +304,10 @@ template <class TD>
 int basis_run(const XRow* rows, int nrows, const XSub* subs, const XBlock* blks, int nmax, cudaStream_t st) {
     if (nrows <= 0) return BDDC_OK;
     const size_t smem = basis_smem(nmax, sizeof(TD));
-    if (smem > 200 * 1024) return BDDC_EINVAL;
+    if (smem > 200 * 1024) {
+        bddc_set_last_error("change-of-basis blocks larger than shared memory", __FILE__, __LINE__);
+        return BDDC_EINVAL;
+    }
     BDDC_CUDA_TRY(cudaFuncSetAttribute(k_basis<TD, TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_basis<TD, TD><<<nrows, TH, smem, st>>>(rows, subs, blks, nmax);
     bddc_note_launches(1);

@@ -2,7 +2,8 @@
 
 * invalid inputs are rejected with BDDC_EINVAL before any solver work: a
   viscosity <= 0 or NaN (host and device arrays), a non-finite velocity, a
-  slab without elements;
+  slab without elements, a subdomain interior above 8192 dofs, a face above
+  256 dofs;
 * a solve that reaches its iteration cap returns BDDC_NOT_CONVERGED with the
   iterate written (finite, the residual reduced);
 * the bounded device waits end by themselves: the one-launch apply's wait,
@@ -51,6 +52,20 @@ def test_rejects_empty_slab():
     p = W.random_small(1, (2, 2, 2), 3, (-2, 0))
     p.slabs = [[3, 0], [3, 3], [3, 3]]
     _expect_einval(p)
+
+
+def _box_problem(slabs):
+    ne = [sum(s) for s in slabs]
+    n = (ne[0] + 1) * (ne[1] + 1) * (ne[2] + 1)
+    return W.Problem("box", slabs, np.ones(ne[0] * ne[1] * ne[2]), np.tile([1.0, 0.5, 0.25], (n, 1)), np.ones(n))
+
+
+def test_rejects_too_large_interior_and_face():
+    _expect_einval(_box_problem([[22], [22], [22]]))          # 21^3 = 9261 interior dofs
+    _expect_einval(_box_problem([[2, 2], [18, 18], [18, 18]]))  # x-faces of 17 x 17 = 289 dofs
+    s = B().Solver(_box_problem([[2, 2], [17, 17], [17, 17]]))  # 16 x 16 = 256: accepted
+    assert s.stats()["pnumF"] >= 0
+    s.close()
 
 
 def test_iteration_cap_returns_not_converged_with_result():

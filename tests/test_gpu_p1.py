@@ -8,7 +8,11 @@ non-homogeneous Dirichlet values on the GPU, against the oracle:
 * Example 4.1 at m = 4 (Tests 1-3, nu_1 = 1, nu_2 = 1e-7, the paper's Table 5 row),
   new and conventional edge GEPs: the constraint counts (pnumF, pnumE) equal the
   oracle's and the iteration counts are within one of the oracle's GMRES;
-* the same on the random-viscosity variant (2^3 and 3^3 subdomains of 4^3 cubes).
+* the same on the random-viscosity variant (2^3 and 3^3 subdomains of 4^3 cubes);
+* Example 4.1 at m = 16 (the paper's Table 5 row): faces of 225 dofs (the face
+  GEP kernel's global-memory path) and 3375 interior dofs per subdomain: the
+  large face eigenvalues, constraint counts and iterations against the oracle
+  (FP64), and the mixed solver's global residual.
 """
 import numpy as np
 import pytest
@@ -113,4 +117,37 @@ def test_example41_random_viscosity_matches_the_oracle(n, edge):
     assert (st["pnumF"], st["pnumE"]) == (o.pnumF, o.pnumE)
     _, sv = s.solve()
     assert sv["converged"] and abs(sv["iters"] - info["iters"]) <= 1
+    s.close()
+
+
+def _face_lambdas(s, o):
+    ge = s.entities(2)
+    by = {e['subs']: i for i, e in enumerate(o.mesh.entities) if e['kind'] == 'F'}
+    return [(g, o.face_info[by[g['subs']]]) for g in ge]
+
+
+@pytest.mark.parametrize("edge", ["new", "old"])
+def test_example41_m16_large_faces_match_the_oracle(edge):
+    p = W.example41(test=1, m=16, nu1=1.0, nu2=1e-7)
+    o = obddc.BDDC(p, edge_gep=edge)
+    _, info = o.solve()
+    s = B().Solver(p, edge_gep=B().EDGE_NEW if edge == "new" else B().EDGE_OLD)
+    for g, ref in _face_lambdas(s, o):
+        assert len(g['dofs']) == 225
+        lo, lg = ref['lam'], g['lam']
+        big = np.isfinite(lo) & (lo > 0.5)
+        np.testing.assert_allclose(lg[big], lo[big], rtol=1e-6)
+        assert g['k'] == ref['Q'].shape[1]
+    st = s.stats()
+    assert (st['pnumF'], st['pnumE']) == (o.pnumF, o.pnumE)
+    _, sv = s.solve()
+    assert sv["converged"] and abs(sv["iters"] - info["iters"]) <= 1
+    s.close()
+
+
+def test_example41_m16_mixed_precision_reaches_the_global_residual():
+    p = W.example41(test=2, m=16, nu1=1.0, nu2=1e-7)
+    s = B().Solver(p, precision=B().PREC_MIXED)
+    _, sv = s.solve()
+    assert sv["converged"] and sv["relres_global"] <= 1e-8
     s.close()
