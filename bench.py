@@ -252,10 +252,18 @@ def example41_part(B, W, stream, flush):
                                                       "pnumF": st["pnumF"], "pnumE": st["pnumE"],
                                                       "relres_global": st["relres_global"]}
         p = W.example41(test=1, m=16, nu1=1.0, nu2=1e-7)
-        ms, st, _ = timed(B, p, stream, B.resident_arrays(p), B.PREC_MIXED, flush, 1)
-        out["m16_test1_new_mixed"] = {"ms": round(ms, 3), "iters": st["iters"], "pnumF": st["pnumF"],
-                                      "pnumE": st["pnumE"], "relres_global": st["relres_global"],
-                                      "setup_ms": round(st["setup_ms"], 3), "solve_ms": round(st["solve_ms"], 3)}
+        arrays = B.resident_arrays(p)
+        # m = 16 with the dense interior elimination and with one level of local
+        # nested dissection (2 x 2 x 2 child boxes per subdomain), FP64 and mixed
+        for key, prec, nd in (("m16_test1_new_mixed", B.PREC_MIXED, 0), ("m16_test1_new_fp64_local_nd", B.PREC_FP64, 1),
+                              ("m16_test1_new_mixed_local_nd", B.PREC_MIXED, 1)):
+            ms, st, _ = timed(B, p, stream, arrays, prec, flush, 1, local_nd=nd)
+            out[key] = {"ms": round(ms, 3), "iters": st["iters"], "pnumF": st["pnumF"], "pnumE": st["pnumE"],
+                        "relres_global": st["relres_global"], "setup_ms": round(st["setup_ms"], 3),
+                        "solve_ms": round(st["solve_ms"], 3), "factor_gflop": round(st["factor_gflop"], 3),
+                        "setup_breakdown_ms": {k: round(st[k], 3) for k in ("t_assemble_ms", "t_factor_ms",
+                                                                             "t_face_ms", "t_edge_ms",
+                                                                             "t_coarse_ms")}}
         return out
     except Exception as e:        # reported in the line, never fatal to the benchmark
         return {"error": repr(e)[:300]}

@@ -134,6 +134,16 @@ typedef struct {
     int element;           /* BDDC_ELEM_Q1: trilinear bricks; BDDC_ELEM_P1: linear
                               elements on the six tetrahedra of each brick around
                               its main diagonal (Sect. 4, Example 4.1)            */
+    int local_nd;          /* 0: each subdomain's interior eliminated as one dense
+                              block; 1: one level of nested dissection: the
+                              subdomain box split into up to 2 x 2 x 2 child boxes
+                              (every slab of 2 or more elements halved), the
+                              children's interiors eliminated first (dense, in a
+                              batch), their Schur complements summed into the
+                              subdomain's matrix over its separator planes and
+                              interface, then the separators eliminated; S^(i) is
+                              the same operator (Sect. 3), with ~1/12 of the
+                              flops and ~1/5 of the memory at H/h = 16         */
 } bddc_opts;
 
 typedef struct {
@@ -173,6 +183,9 @@ typedef struct {
                                 reuse the choice)                                  */
     double gemv_tune_us;     /* the chosen list's time per product when this setup
                                 measured it (0: the choice was reused)             */
+    int nd_children;         /* local_nd = 1: child boxes over all subdomains (0: off) */
+    double factor_gflop;     /* flops of the subdomain eliminations / 1e9 (children
+                                and separators with local_nd = 1)                 */
 } bddc_stats;
 
 typedef struct bddc_ctx bddc_ctx;
@@ -181,7 +194,7 @@ typedef struct bddc_ctx bddc_ctx;
  * tau = 0.7, FP64, no restart, 300 iterations, rtol 1e-8, new edge GEP,
  * face GEP on, inner_rtol 1e-6, max_refine 8, no learned skip, tensor-core
  * trailing updates in the MIXED path (tensor_cores 1), coarse_elim 0,
- * apply_launch 0, cond_est 1, element BDDC_ELEM_Q1. */
+ * apply_launch 0, cond_est 1, element BDDC_ELEM_Q1, local_nd 0. */
 void bddc_default_opts(bddc_opts* o);
 
 /* Setup (call stack: assembly, batched Dirichlet factorisation + Schur

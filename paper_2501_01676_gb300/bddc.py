@@ -43,7 +43,7 @@ class Opts(ct.Structure):
                 ("all_primal", ct.c_int), ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
                 ("learned_skip_p", ct.c_double), ("mlp_params", ct.c_void_p), ("tensor_cores", ct.c_int),
                 ("coarse_elim", ct.c_int), ("apply_launch", ct.c_int), ("cond_est", ct.c_int),
-                ("element", ct.c_int)]
+                ("element", ct.c_int), ("local_nd", ct.c_int)]
 
 
 class Stats(ct.Structure):
@@ -56,7 +56,8 @@ class Stats(ct.Structure):
                 ("jacobi_sweeps_max", ct.c_int), ("t_mesh_ms", ct.c_double), ("t_basis_ms", ct.c_double),
                 ("coarse_path", ct.c_int), ("coarse_fronts", ct.c_int), ("coarse_levels", ct.c_int),
                 ("coarse_factor_gflop", ct.c_double), ("kappa_est", ct.c_double),
-                ("gemv_rows", ct.c_int), ("gemv_tune_us", ct.c_double)]
+                ("gemv_rows", ct.c_int), ("gemv_tune_us", ct.c_double), ("nd_children", ct.c_int),
+                ("factor_gflop", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

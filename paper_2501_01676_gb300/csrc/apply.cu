@@ -371,14 +371,16 @@ __global__ void __launch_bounds__(TRI_THREADS) k_condense(const T* __restrict__ 
 }
 
 // Backward half of the recovery: ystore holds -(y - U_IB u_B) (the batched GEMV
-// has added U_IB u_B to -y); u_I = U_II^{-1} (y - U_IB u_B), u_B copied.
+// has added U_IB u_B to -y); u_I = U_II^{-1} (y - U_IB u_B), u_B copied.  uG may
+// be u itself (the child boxes of local nested dissection recover from the
+// solution already written on their boundaries), so neither is restrict.
 template <class T>
 __global__ void __launch_bounds__(TRI_THREADS) k_recover(const T* __restrict__ pool,
                                                          const TriItem* __restrict__ items,
                                                          const int* __restrict__ lists,
-                                                         const double* __restrict__ uG,
+                                                         const double* uG,
                                                          const double* __restrict__ ystore,
-                                                         double* __restrict__ u, int nrhs,
+                                                         double* u, int nrhs,
                                                          long long ldG, long long ldU,
                                                          long long ldY) {
     const TriItem it = items[blockIdx.x];

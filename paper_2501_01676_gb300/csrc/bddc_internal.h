@@ -98,6 +98,20 @@ int build_host_boxes(const bddc_mesh* mesh, const bddc_partition* part, HostMesh
 int build_host_interface(HostMesh& hm);
 int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh& hm);
 
+// One level of nested dissection inside every subdomain: the child boxes (each
+// slab of c >= 2 elements split into c/2 and c - c/2 elements) form a mesh of
+// their own on the same grid (same dof numbering); every subdomain's numbering is
+// rewritten to [separator dofs, interface dofs] (nI = the separators: the
+// subdomain-interior nodes on a child box boundary); map[c] gives, for each
+// interface dof of child c (in its own order), its index in the subdomain's new
+// numbering.
+struct LocalND {
+    HostMesh child;
+    std::vector<int> parent;                  // child -> subdomain
+    std::vector<std::vector<int>> map;        // child -> subdomain-local indices of its interface dofs
+};
+int build_local_nd(HostMesh& hm, LocalND& nd);
+
 // ---------------------------------------------------------------------------
 // Device buffers
 // ---------------------------------------------------------------------------

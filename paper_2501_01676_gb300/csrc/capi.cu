@@ -19,6 +19,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -189,6 +191,17 @@ int staged_upload(void* dev, const void* host, size_t bytes, cudaStream_t st) {
     return stage_done(st);
 }
 
+// Condensation / recovery data of one level of box eliminations (the subdomains,
+// or with local nested dissection also the child boxes).
+struct TriSet {
+    void* tri = nullptr;                          // one TriItem per box
+    int* lists = nullptr;
+    GemvItem *itCI = nullptr, *itRI = nullptr;    // L_BI and U_IB blocks of the interior factors
+    int count = 0, max_nI = 1, nitCI = 0, nitRI = 0;
+    double bytesCI = 0, bytesRI = 0;
+    long long ny = 1;                             // entries of the stored y_i of all boxes
+};
+
 struct bddc_ctx {
     HostMesh hm;
     bddc_opts o;
@@ -301,14 +314,16 @@ struct bddc_ctx {
     // algorithmic bytes of one product: matrix stream + gathered inputs + scattered outputs
     double bytesS = 0, bytesM1 = 0, bytesC = 0, bytesM3 = 0;
     // condense / recover
-    void* tri = nullptr;
-    int* tri_lists = nullptr;
-    GemvItem *itCI = nullptr, *itRI = nullptr;   // L_BI and U_IB blocks of the interior factors
-    int max_nI = 1;                               // largest subdomain interior (substitution kernels)
-    int nitCI = 0, nitRI = 0;
-    double bytesCI = 0, bytesRI = 0;
+    TriSet tp;                  // the subdomains (interior = separators with local_nd)
     double* ystore = nullptr;
-    long long ny = 0;
+    // local nested dissection (opts.local_nd): child boxes, their matrices and
+    // substitution data, and the load with their corrections
+    std::unique_ptr<LocalND> lnd;
+    void* Ac = nullptr;
+    std::vector<long long> aoffc;
+    std::vector<int> aldc;
+    TriSet tc;
+    double *Fc = nullptr, *yc = nullptr;
     // work vectors
     double *zc = nullptr, *uPi = nullptr, *g = nullptr, *xG = nullptr, *r = nullptr, *w = nullptr,
            *vcur = nullptr, *t = nullptr;
@@ -726,12 +741,192 @@ static int tune_gemv_rows(bddc_ctx* C, const std::vector<GemvItem>& iS0, int rb0
     return rc;
 }
 
+// Element assembly into the dense matrices of a list of boxes (the subdomains, or
+// the child boxes of local nested dissection) stored at (aoff, ald) in pool, in
+// each box's own numbering (interior, then interface, box order); the global
+// stencil and load (C->stencil, C->F, zeroed by the caller) are assembled with it.
+template <class T>
+static int assemble_boxes(bddc_ctx* C, const HostMesh& mesh, T* pool, const std::vector<long long>& aoff,
+                          const std::vector<int>& ald) {
+    cudaStream_t st = C->st;
+    const int nbox = mesh.nsd;
+    // node -> local index table of every box, built on the GPU (k_build_lut)
+    std::vector<int> box0(3 * nbox), boxn(3 * nbox);
+    std::vector<long long> lut_off(nbox);
+    long long lut_n = 0;
+    for (int s = 0; s < nbox; ++s) {
+        const SubInfo& S = mesh.sub[s];
+        lut_off[s] = lut_n;
+        long long nb = 1;
+        for (int d = 0; d < 3; ++d) {
+            box0[3 * s + d] = S.box0[d];
+            boxn[3 * s + d] = S.box1[d] - S.box0[d] + 1;
+            nb *= boxn[3 * s + d];
+        }
+        lut_n += nb;
+    }
+    std::vector<int> slab[3];
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < mesh.nsub[d]; ++s)
+            for (int e = mesh.off[d][s]; e < mesh.off[d][s + 1]; ++e) slab[d].push_back(s);
+    int *d_lut, *d_box0, *d_boxn, *d_sx, *d_sy, *d_sz, *d_ald;
+    long long *d_lutoff, *d_aoff;
+    BDDC_TRY(C->upload(&d_lutoff, lut_off));
+    BDDC_TRY(C->upload(&d_box0, box0));
+    BDDC_TRY(C->upload(&d_boxn, boxn));
+    BDDC_TRY(C->alloc(&d_lut, (size_t)std::max(lut_n, 1LL)));
+    BDDC_TRY(build_lut_run(mesh, d_box0, d_boxn, d_lutoff, d_lut, st));
+    BDDC_TRY(C->upload(&d_sx, slab[0]));
+    BDDC_TRY(C->upload(&d_sy, slab[1]));
+    BDDC_TRY(C->upload(&d_sz, slab[2]));
+    BDDC_TRY(C->upload(&d_aoff, aoff));
+    BDDC_TRY(C->upload(&d_ald, ald));
+    std::vector<char> tabs((size_t)assemble_tables_bytes(C->o.element));
+    assemble_tables(mesh, tabs.data(), C->o.element);
+    char* d_tabs = nullptr;
+    BDDC_TRY(C->upload(&d_tabs, tabs));
+    ktimer_begin(KT_ASSEMBLE, st);
+    BDDC_TRY(assemble_launch<T>(mesh, C->o.tau, C->c, d_tabs, C->nu, C->beta, C->f, C->divb, C->bconst, d_sx, d_sy,
+                                d_sz, d_lut, d_lutoff, d_box0, d_boxn, pool, d_aoff, d_ald, C->stencil, C->F, C->gdir,
+                                C->o.element, st));
+    ktimer_end(KT_ASSEMBLE, st, 0.0, 0.0);
+    return BDDC_OK;
+}
+
+// Condensation / recovery data of a list of boxes whose factors sit in one pool
+// (aoff, ald): per box its dof list (interior, then interface), the map of its
+// interface to the output vector (the Gamma numbering, or with global_out the
+// global dofs: the child boxes of local nested dissection condense into a copy of
+// the load and recover from the global solution), and the GEMV items of L_BI and
+// U_IB in column slices of the kernel's staging width.
+template <class T>
+static int build_tri(bddc_ctx* C, const std::vector<SubInfo>& subs, const std::vector<long long>& aoff,
+                     const std::vector<int>& ald, bool global_out, TriSet& ts) {
+    const int nbox = (int)subs.size();
+    std::vector<int> lists;
+    std::vector<char> items(tri_item_size() * std::max(nbox, 1));
+    long long yo = 0;
+    std::vector<GemvItem> ci, ri;
+    const double tsz = sizeof(T), iv = 8.0 + 4.0;
+    ts = TriSet();
+    for (int s = 0; s < nbox; ++s) {
+        const SubInfo& S = subs[s];
+        const int nI = S.nI, nB = S.nB, ld = ald[s];
+        const int dof_off = (int)lists.size();
+        lists.insert(lists.end(), S.dofs.begin(), S.dofs.end());
+        const int go = (int)lists.size();
+        const std::vector<int> omap = global_out ? std::vector<int>(S.dofs.begin() + nI, S.dofs.end()) : S.gidx;
+        if ((int)omap.size() != nB) return BDDC_EINVAL;
+        lists.insert(lists.end(), omap.begin(), omap.end());
+        tri_item_fill(items.data() + tri_item_size() * s, aoff[s], S.n, nI, ld, dof_off, go, yo);
+        // y positions of the box, and the interface map behind nI unused slots
+        // (the U_IB items read columns nI .. n-1 of A through input slots nI .. n-1)
+        const int yi = (int)lists.size();
+        for (int q = 0; q < nI; ++q) lists.push_back((int)(yo + q));
+        const int gp = (int)lists.size();
+        lists.insert(lists.end(), (size_t)nI, 0);
+        lists.insert(lists.end(), omap.begin(), omap.end());
+        if (nI > 0 && nB > 0) {
+            for (int c0 = 0; c0 < nI; c0 += 2048)
+                for (int r0 = 0; r0 < nB; r0 += 32)
+                    ci.push_back(GemvItem{aoff[s] + (long long)nI * ld, nB, nI, ld, yi, go, r0, std::min(32, nB - r0),
+                                          c0, std::min(2048, nI - c0)});
+            for (int c0 = 0; c0 < nB; c0 += 2048)
+                for (int r0 = 0; r0 < nI; r0 += 32)
+                    ri.push_back(GemvItem{aoff[s], nI, S.n, ld, gp, yi, r0, std::min(32, nI - r0), nI + c0,
+                                          std::min(2048, nB - c0)});
+            ts.bytesCI += tsz * nB * nI + iv * (nI + nB);
+            ts.bytesRI += tsz * nI * nB + iv * (nB + nI);
+        }
+        yo += nI;
+        ts.max_nI = std::max(ts.max_nI, nI);
+    }
+    if ((long long)lists.size() + yo > INT_MAX) return BDDC_EINVAL;
+    ts.count = nbox;
+    ts.ny = std::max(yo, 1LL);
+    BDDC_TRY(C->upload(&ts.lists, lists));
+    BDDC_TRY(C->upload((char**)&ts.tri, items));
+    BDDC_TRY(C->upload(&ts.itCI, ci));
+    BDDC_TRY(C->upload(&ts.itRI, ri));
+    ts.nitCI = (int)ci.size();
+    ts.nitRI = (int)ri.size();
+    return BDDC_OK;
+}
+
+// g = F_Gamma - A_Gamma,I A_II^{-1} F_I for nrhs columns (F, Fw: ndof x nrhs; g: nG
+// x nrhs; y of the boxes stored for the recovery).  With local nested dissection the
+// children's interiors are condensed first, into Fw (a copy of F that receives
+// their corrections on the separators and the interface), then the separators.
+template <class T>
+static int condense_all(bddc_ctx* C, const double* F, double* g, double* ystore, double* Fw, double* yc, int nrhs,
+                        cudaStream_t st) {
+    const long long nG = C->nG, ndof = C->hm.ndof;
+    const double* Fp = F;
+    if (C->lnd) {
+        const TriSet& c = C->tc;
+        BDDC_CUDA_TRY(cudaMemcpyAsync(Fw, F, sizeof(double) * ndof * nrhs, cudaMemcpyDeviceToDevice, st));
+        BDDC_TRY(condense_run<T>((const T*)C->Ac, c.tri, c.count, c.max_nI, c.lists, F, Fw, yc, nrhs, ndof, ndof, c.ny,
+                                 c.itCI, c.nitCI, c.bytesCI, st));
+        Fp = Fw;
+    }
+    for (int c = 0; c < nrhs; ++c) BDDC_TRY(gather_run(Fp + c * ndof, C->gamma_dofs, g + c * nG, (int)nG, st));
+    const TriSet& t = C->tp;
+    return condense_run<T>((const T*)C->A, t.tri, t.count, t.max_nI, t.lists, Fp, g, ystore, nrhs, ndof, nG, t.ny,
+                           t.itCI, t.nitCI, t.bytesCI, st);
+}
+
+// u = [A_II^{-1}(F_I - A_I,Gamma x_Gamma); x_Gamma] from the stored y (nrhs columns);
+// with local nested dissection the separators first, then the children's
+// interiors from the solution just written on their boundaries.
+template <class T>
+static int recover_all(bddc_ctx* C, const double* xG, double* ystore, double* u, double* yc, int nrhs,
+                       cudaStream_t st) {
+    const long long nG = C->nG, ndof = C->hm.ndof;
+    const TriSet& t = C->tp;
+    BDDC_TRY(recover_run<T>((const T*)C->A, t.tri, t.count, t.max_nI, t.lists, xG, ystore, u, nrhs, nG, ndof, t.ny,
+                            t.itRI, t.nitRI, t.bytesRI, st));
+    if (C->lnd) {
+        const TriSet& c = C->tc;
+        BDDC_TRY(recover_run<T>((const T*)C->Ac, c.tri, c.count, c.max_nI, c.lists, u, yc, u, nrhs, ndof, ndof, c.ny,
+                                c.itRI, c.nitRI, c.bytesRI, st));
+    }
+    return BDDC_OK;
+}
+
 template <class T>
 static int setup_impl(bddc_ctx* C) {
     HostMesh& hm = C->hm;
     cudaStream_t st = C->st;
     const int nsd = hm.nsd;
     C->phase_mark(0);
+    // ---- 0. local nested dissection: child boxes, subdomains renumbered to
+    //         [separators, interface] ---------------------------------------
+    if (C->o.local_nd) {
+        C->lnd.reset(new LocalND);
+        BDDC_TRY(build_local_nd(hm, *C->lnd));
+        for (const SubInfo& K : C->lnd->child.sub)
+            if (K.nI > BDDC_MAX_INTERIOR) {
+                bddc_set_last_error("child box interior larger than the interior-solve limit", __FILE__, __LINE__);
+                return BDDC_EINVAL;
+            }
+    }
+    for (const SubInfo& S : hm.sub)
+        if (S.nI > BDDC_MAX_INTERIOR) {
+            bddc_set_last_error("subdomain interior (separators with local_nd) larger than the interior-solve limit",
+                                __FILE__, __LINE__);
+            return BDDC_EINVAL;
+        }
+    // element -> subdomain slab maps (edge features of the learned skip)
+    int *d_sx = nullptr, *d_sy = nullptr, *d_sz = nullptr;
+    {
+        std::vector<int> slab[3];
+        for (int d = 0; d < 3; ++d)
+            for (int s = 0; s < hm.nsub[d]; ++s)
+                for (int e = hm.off[d][s]; e < hm.off[d][s + 1]; ++e) slab[d].push_back(s);
+        BDDC_TRY(C->upload(&d_sx, slab[0]));
+        BDDC_TRY(C->upload(&d_sy, slab[1]));
+        BDDC_TRY(C->upload(&d_sz, slab[2]));
+    }
     // ---- 1. assembly --------------------------------------------------------
     C->aoff.resize(nsd);
     C->ald.resize(nsd);
@@ -745,57 +940,74 @@ static int setup_impl(bddc_ctx* C) {
     BDDC_TRY(C->alloc(&A, atot));
     C->A = A;
     BDDC_CUDA_TRY(cudaMemsetAsync(A, 0, atot * sizeof(T), st));
-    // node -> local index table of every subdomain box, built on the GPU (k_build_lut)
-    std::vector<int> box0(3 * nsd), boxn(3 * nsd);
-    std::vector<long long> lut_off(nsd);
-    long long lut_n = 0;
-    for (int s = 0; s < nsd; ++s) {
-        SubInfo& S = hm.sub[s];
-        lut_off[s] = lut_n;
-        long long nb = 1;
-        for (int d = 0; d < 3; ++d) {
-            box0[3 * s + d] = S.box0[d];
-            boxn[3 * s + d] = S.box1[d] - S.box0[d] + 1;
-            nb *= boxn[3 * s + d];
-        }
-        lut_n += nb;
-    }
-    std::vector<int> slab[3];
-    for (int d = 0; d < 3; ++d)
-        for (int s = 0; s < hm.nsub[d]; ++s)
-            for (int e = hm.off[d][s]; e < hm.off[d][s + 1]; ++e) slab[d].push_back(s);
-    int *d_lut, *d_box0, *d_boxn, *d_sx, *d_sy, *d_sz, *d_ald;
-    long long *d_lutoff, *d_aoff;
-    BDDC_TRY(C->upload(&d_lutoff, lut_off));
-    BDDC_TRY(C->upload(&d_box0, box0));
-    BDDC_TRY(C->upload(&d_boxn, boxn));
-    BDDC_TRY(C->alloc(&d_lut, (size_t)std::max(lut_n, 1LL)));
-    BDDC_TRY(build_lut_run(hm, d_box0, d_boxn, d_lutoff, d_lut, st));
-    BDDC_TRY(C->upload(&d_sx, slab[0]));
-    BDDC_TRY(C->upload(&d_sy, slab[1]));
-    BDDC_TRY(C->upload(&d_sz, slab[2]));
-    BDDC_TRY(C->upload(&d_aoff, C->aoff));
-    BDDC_TRY(C->upload(&d_ald, C->ald));
     BDDC_TRY(C->alloc(&C->stencil, (size_t)27 * hm.ndof));
     BDDC_TRY(C->alloc(&C->F, hm.ndof));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->stencil, 0, sizeof(double) * 27 * (size_t)hm.ndof, st));
     BDDC_CUDA_TRY(cudaMemsetAsync(C->F, 0, sizeof(double) * hm.ndof, st));
-    std::vector<char> tabs((size_t)assemble_tables_bytes(C->o.element));
-    assemble_tables(hm, tabs.data(), C->o.element);
-    char* d_tabs = nullptr;
-    BDDC_TRY(C->upload(&d_tabs, tabs));
-    ktimer_begin(KT_ASSEMBLE, st);
-    BDDC_TRY(assemble_launch<T>(hm, C->o.tau, C->c, d_tabs, C->nu, C->beta, C->f, C->divb, C->bconst, d_sx, d_sy,
-                                d_sz, d_lut, d_lutoff, d_box0, d_boxn, A, d_aoff, d_ald, C->stencil, C->F, C->gdir,
-                                C->o.element, st));
-    ktimer_end(KT_ASSEMBLE, st, 0.0, 0.0);
+    double fl = 0.0;           // flops of the box eliminations
+    auto elim_flops = [](double n, double k) {
+        const double m = n - k;
+        return 2.0 / 3.0 * k * k * k + 2.0 * k * k * m + 2.0 * k * m * m;
+    };
+    if (!C->lnd) {
+        BDDC_TRY(assemble_boxes<T>(C, hm, A, C->aoff, C->ald));
+    } else {
+        // children: assembly, interior eliminations, then their Schur complements
+        // added into the subdomains' matrices over [separators, interface]
+        const HostMesh& ch = C->lnd->child;
+        const int nch = ch.nsd;
+        C->aoffc.resize(nch);
+        C->aldc.resize(nch);
+        long long ctot = 0;
+        for (int c = 0; c < nch; ++c) {
+            C->aldc[c] = r4(ch.sub[c].n);
+            C->aoffc[c] = ctot;
+            ctot += (long long)ch.sub[c].n * C->aldc[c];
+        }
+        T* Ac = nullptr;
+        BDDC_TRY(C->alloc(&Ac, std::max(ctot, 1LL)));
+        C->Ac = Ac;
+        BDDC_CUDA_TRY(cudaMemsetAsync(Ac, 0, ctot * sizeof(T), st));
+        BDDC_TRY(assemble_boxes<T>(C, ch, Ac, C->aoffc, C->aldc));
+        std::vector<EngItem<T>> items;
+        for (int c = 0; c < nch; ++c)
+            if (ch.sub[c].nI > 0) {
+                items.push_back(EngItem<T>{Ac + C->aoffc[c], ch.sub[c].n, ch.sub[c].nI, C->aldc[c]});
+                fl += elim_flops(ch.sub[c].n, ch.sub[c].nI);
+            }
+        if (!items.empty()) BDDC_TRY(run_engine<T>(C, items));
+        std::vector<int> mapv;
+        std::vector<long long> moff(nch);
+        for (int c = 0; c < nch; ++c) {
+            moff[c] = (long long)mapv.size();
+            mapv.insert(mapv.end(), C->lnd->map[c].begin(), C->lnd->map[c].end());
+        }
+        int* d_map = nullptr;
+        BDDC_TRY(C->upload(&d_map, mapv));
+        std::vector<ExtendJob> xj;
+        for (int c = 0; c < nch; ++c) {
+            const SubInfo& K = ch.sub[c];
+            if (K.nB == 0) continue;
+            const int p = C->lnd->parent[c];
+            xj.push_back(ExtendJob{Ac + C->aoffc[c] + (long long)K.nI * C->aldc[c] + K.nI, C->aldc[c], K.nB,
+                                   d_map + moff[c], A + C->aoff[p], C->ald[p]});
+        }
+        ExtendJob* d_xj = nullptr;
+        BDDC_TRY(C->upload(&d_xj, xj));
+        BDDC_TRY(extend_add_run<T>(d_xj, (int)xj.size(), 16, st));
+        C->stats.nd_children = nch;
+    }
     C->phase_mark(1);
-    // ---- 2. partial LU: S^(i) ---------------------------------------------
+    // ---- 2. partial LU: S^(i) (with local_nd: the separators) ---------------
     {
-        std::vector<EngItem<T>> items(nsd);
+        std::vector<EngItem<T>> items;
         for (int s = 0; s < nsd; ++s)
-            items[s] = EngItem<T>{A + C->aoff[s], hm.sub[s].n, hm.sub[s].nI, C->ald[s]};
-        BDDC_TRY(run_engine<T>(C, items));
+            if (!C->lnd || hm.sub[s].nI > 0) {
+                items.push_back(EngItem<T>{A + C->aoff[s], hm.sub[s].n, hm.sub[s].nI, C->ald[s]});
+                fl += elim_flops(hm.sub[s].n, hm.sub[s].nI);
+            }
+        if (!items.empty()) BDDC_TRY(run_engine<T>(C, items));
+        C->stats.factor_gflop = fl * 1e-9;
     }
     C->soff.resize(nsd);
     C->sld.resize(nsd);
@@ -1621,50 +1833,8 @@ static int setup_impl(bddc_ctx* C) {
     C->nitC = (int)iC.size();
     C->nitM3 = (int)iM3.size();
     // condense / recover items
-    {
-        std::vector<int> lists;
-        std::vector<char> items(tri_item_size() * nsd);
-        long long yo = 0;
-        std::vector<GemvItem> ci, ri;
-        const double ts = sizeof(T), iv = 8.0 + 4.0;
-        for (int s = 0; s < nsd; ++s) {
-            SubInfo& S = hm.sub[s];
-            const int nI = S.nI, nB = S.nB, ld = C->ald[s];
-            int dof_off = (int)lists.size();
-            lists.insert(lists.end(), S.dofs.begin(), S.dofs.end());
-            int go = (int)lists.size();
-            lists.insert(lists.end(), S.gidx.begin(), S.gidx.end());
-            tri_item_fill(items.data() + tri_item_size() * s, C->aoff[s], S.n, S.nI, ld, dof_off, go, yo);
-            // y positions of the subdomain, and the interface map behind nI unused slots
-            // (the U_IB items read columns nI .. n-1 of A through input slots nI .. n-1)
-            const int yi = (int)lists.size();
-            for (int q = 0; q < nI; ++q) lists.push_back((int)(yo + q));
-            const int gp = (int)lists.size();
-            lists.insert(lists.end(), (size_t)nI, 0);
-            lists.insert(lists.end(), S.gidx.begin(), S.gidx.end());
-            if (nI > 0 && nB > 0) {
-                for (int c0 = 0; c0 < nI; c0 += 2048)      // column slices of the kernel's staging width
-                    for (int r0 = 0; r0 < nB; r0 += 32)
-                        ci.push_back(GemvItem{C->aoff[s] + (long long)nI * ld, nB, nI, ld, yi, go, r0,
-                                              std::min(32, nB - r0), c0, std::min(2048, nI - c0)});
-                for (int c0 = 0; c0 < nB; c0 += 2048)
-                    for (int r0 = 0; r0 < nI; r0 += 32)
-                        ri.push_back(GemvItem{C->aoff[s], nI, S.n, ld, gp, yi, r0, std::min(32, nI - r0), nI + c0,
-                                              std::min(2048, nB - c0)});
-                C->bytesCI += ts * nB * nI + iv * (nI + nB);
-                C->bytesRI += ts * nI * nB + iv * (nB + nI);
-            }
-            yo += S.nI;
-            C->max_nI = std::max(C->max_nI, S.nI);
-        }
-        C->ny = std::max(yo, 1LL);
-        BDDC_TRY(C->upload(&C->tri_lists, lists));
-        BDDC_TRY(C->upload((char**)&C->tri, items));
-        BDDC_TRY(C->upload(&C->itCI, ci));
-        BDDC_TRY(C->upload(&C->itRI, ri));
-        C->nitCI = (int)ci.size();
-        C->nitRI = (int)ri.size();
-    }
+    BDDC_TRY(build_tri<T>(C, hm.sub, C->aoff, C->ald, false, C->tp));
+    if (C->lnd) BDDC_TRY(build_tri<T>(C, C->lnd->child.sub, C->aoffc, C->aldc, true, C->tc));
     if (coarse_small) {
         BDDC_CUDA_TRY(cudaStreamSynchronize(st));
         // FP64 rounding floor of I - S X: a few n eps ||S|| ||X||; the mixed apply
@@ -1915,12 +2085,11 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
     double Fn = 0.0;
     BDDC_TRY(norm2(C, Fdev, ndof, &Fn));
     if (!C->mixed) {
-        BDDC_TRY(gather_run(Fdev, C->gamma_dofs, C->g, (int)nG, st));
-        BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, Fdev, C->g, C->ystore, 1, ndof, nG, C->ny, C->itCI, C->nitCI, C->bytesCI, st));
+        BDDC_TRY(condense_all<T>(C, Fdev, C->g, C->ystore, C->Fc, C->yc, 1, st));
         int it = 0;
         BDDC_TRY(gmres<T>(C, C->g, C->xG, C->o.rtol, C->o.max_iter, &it, &relres, &conv));
         iters_total = it;
-        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, C->xG, C->ystore, udev, 1, nG, ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
+        BDDC_TRY(recover_all<T>(C, C->xG, C->ystore, udev, C->yc, 1, st));
         steps = 1;
     } else {
         // FP64 iterative refinement on the global system with FP32 BDDC-GMRES as inner solver
@@ -1932,15 +2101,14 @@ static int solve_one(bddc_ctx* C, const double* Fdev, double* udev, bddc_stats* 
                 conv = 1;
                 break;
             }
-            BDDC_TRY(gather_run(C->res, C->gamma_dofs, C->g, (int)nG, st));
-            BDDC_TRY(condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, C->res, C->g, C->ystore, 1, ndof, nG, C->ny, C->itCI, C->nitCI, C->bytesCI, st));
+            BDDC_TRY(condense_all<T>(C, C->res, C->g, C->ystore, C->Fc, C->yc, 1, st));
             int it = 0, cv = 0;
             double rr = 0.0;
             // the loosest inner tolerance that still reaches rtol (with a factor-2 margin)
             const double tol_k = std::max(C->o.inner_rtol, 0.5 * C->o.rtol * Fn / rn);
             BDDC_TRY(gmres<T>(C, C->g, C->xG, std::min(tol_k, 0.5), C->o.max_iter - iters_total, &it, &rr, &cv));
             iters_total += it;
-            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, C->xG, C->ystore, C->corr, 1, nG, ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
+            BDDC_TRY(recover_all<T>(C, C->xG, C->ystore, C->corr, C->yc, 1, st));
             BDDC_TRY(vec_axpby(udev, C->corr, 1.0, 1.0, ndof, st));
             BDDC_TRY(stencil_residual(hm, C->stencil, udev, Fdev, C->res, 1, st));
             BDDC_TRY(norm2(C, C->res, ndof, &rn));
@@ -1981,7 +2149,7 @@ struct BatchWS {
     double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *hh = nullptr, *hh2 = nullptr,
            *yy = nullptr, *partial = nullptr, *w = nullptr, *vcur = nullptr, *t = nullptr, *r = nullptr,
            *zc = nullptr, *g = nullptr, *xG = nullptr, *ystore = nullptr, *res = nullptr, *corr = nullptr,
-           *Fin = nullptr, *uglob = nullptr;
+           *Fin = nullptr, *uglob = nullptr, *Fc = nullptr, *yc = nullptr;
     GmState* gst = nullptr;            // nb states, then nb spare states (plain reductions)
     GmState* hst = nullptr;            // pinned host copy of the nb states
     int* allstop = nullptr;
@@ -2026,7 +2194,11 @@ static int batch_ws(bddc_ctx* C, int nb, BatchWS** out) {
     A(&W->g, nG * nb);
     A(&W->xG, nG * nb);
     A(&W->zc, W->ldz * nb);
-    A(&W->ystore, C->ny * nb);
+    A(&W->ystore, C->tp.ny * nb);
+    if (C->lnd) {
+        A(&W->Fc, ndof * nb);
+        A(&W->yc, C->tc.ny * nb);
+    }
     A(&W->res, ndof * nb);
     A(&W->corr, ndof * nb);
     A(&W->Fin, ndof * nb);
@@ -2224,9 +2396,7 @@ static int solve_batch(bddc_ctx* C, BatchWS* W, const double* F, double* U, bddc
     std::vector<int> it(nb), cv(nb), itot(nb, 0), steps(nb, 0), convd(nb, 0);
     BDDC_TRY(norms_batch(C, W, F, ndof, nb, Fn.data()));
     auto condense_cols = [&](const double* R) -> int {
-        for (int c = 0; c < nb; ++c) BDDC_TRY(gather_run(R + c * ndof, C->gamma_dofs, W->g + c * nG, (int)nG, st));
-        return condense_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, R, W->g, W->ystore, nb, ndof, nG, C->ny,
-                               C->itCI, C->nitCI, C->bytesCI, st);
+        return condense_all<T>(C, R, W->g, W->ystore, W->Fc, W->yc, nb, st);
     };
     double relres_max = 0.0;
     if (!C->mixed) {
@@ -2236,8 +2406,7 @@ static int solve_batch(bddc_ctx* C, BatchWS* W, const double* F, double* U, bddc
         for (int c = 0; c < nb; ++c) tol[c] = C->o.rtol * bn[c];
         BDDC_TRY(gmres_batch<T>(C, W, W->g, W->xG, tol.data(), bn.data(), caps.data(), it.data(), cv.data(),
                                 rr.data()));
-        BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, W->xG, W->ystore, U, nb, nG, ndof, C->ny,
-                                C->itRI, C->nitRI, C->bytesRI, st));
+        BDDC_TRY(recover_all<T>(C, W->xG, W->ystore, U, W->yc, nb, st));
         for (int c = 0; c < nb; ++c) {
             itot[c] = it[c];
             steps[c] = 1;
@@ -2270,8 +2439,7 @@ static int solve_batch(bddc_ctx* C, BatchWS* W, const double* F, double* U, bddc
                                     rr.data()));
             for (int c = 0; c < nb; ++c)
                 if (tol[c] >= 0.0) itot[c] += it[c];
-            BDDC_TRY(recover_run<T>((const T*)C->A, C->tri, hm.nsd, C->max_nI, C->tri_lists, W->xG, W->ystore, W->corr, nb, nG,
-                                    ndof, C->ny, C->itRI, C->nitRI, C->bytesRI, st));
+            BDDC_TRY(recover_all<T>(C, W->xG, W->ystore, W->corr, W->yc, nb, st));
             BDDC_TRY(vec_axpby_cols(U, ndof, W->corr, ndof, 1.0, 1.0, ndof, nb, st));
             BDDC_TRY(stencil_residual(hm, C->stencil, U, F, W->res, nb, st));
             BDDC_TRY(norms_batch(C, W, W->res, ndof, nb, rn.data()));
@@ -2346,6 +2514,7 @@ void bddc_default_opts(bddc_opts* o) {
     o->apply_launch = 0;
     o->cond_est = 1;
     o->element = BDDC_ELEM_Q1;
+    o->local_nd = 0;
 }
 
 const char* bddc_last_error(void) { return g_last_error.c_str(); }
@@ -2419,11 +2588,16 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     BDDC_TRY(stage_reset());
     BDDC_TRY(build_host_boxes(mesh, part, C->hm));
     HostMesh& hm = C->hm;
-    for (const SubInfo& S : hm.sub)
-        if (S.nI > BDDC_MAX_INTERIOR) {
-            bddc_set_last_error("subdomain interior larger than the interior-solve limit", __FILE__, __LINE__);
-            return BDDC_EINVAL;
-        }
+    if (C->o.local_nd != 0 && C->o.local_nd != 1) {
+        bddc_set_last_error("local_nd must be 0 or 1", __FILE__, __LINE__);
+        return BDDC_EINVAL;
+    }
+    if (!C->o.local_nd)          // (with local_nd the children and separators are checked at setup)
+        for (const SubInfo& S : hm.sub)
+            if (S.nI > BDDC_MAX_INTERIOR) {
+                bddc_set_last_error("subdomain interior larger than the interior-solve limit", __FILE__, __LINE__);
+                return BDDC_EINVAL;
+            }
     if (!k || !k->nu_elem) return BDDC_EINVAL;
     if (k->mem != BDDC_MEM_HOST && k->mem != BDDC_MEM_DEVICE) return BDDC_EINVAL;
     if (C->o.element != BDDC_ELEM_Q1 && C->o.element != BDDC_ELEM_P1) {
@@ -2480,7 +2654,11 @@ static int setup_body(bddc_ctx* C, const bddc_mesh* mesh, const bddc_coeffs* k, 
     BDDC_TRY(C->alloc(&C->corr, ndof));
     BDDC_TRY(C->alloc(&C->uglob, ndof));
     BDDC_TRY(C->alloc(&C->Fin, ndof));
-    BDDC_TRY(C->alloc(&C->ystore, C->ny));
+    BDDC_TRY(C->alloc(&C->ystore, C->tp.ny));
+    if (C->lnd) {
+        BDDC_TRY(C->alloc(&C->Fc, ndof));
+        BDDC_TRY(C->alloc(&C->yc, C->tc.ny));
+    }
     BDDC_TRY(C->upload(&C->gamma_dofs, hm.gamma));
     int m = C->o.restart > 0 ? std::min(C->o.restart, C->o.max_iter) : C->o.max_iter;
     m = std::max(m, 1);

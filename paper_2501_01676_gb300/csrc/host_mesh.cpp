@@ -186,3 +186,105 @@ int build_host_mesh(const bddc_mesh* mesh, const bddc_partition* part, HostMesh&
     const int rc = build_host_boxes(mesh, part, hm);
     return rc != BDDC_OK ? rc : build_host_interface(hm);
 }
+
+int build_local_nd(HostMesh& hm, LocalND& nd) {
+    // child slabs and the parent slab of each
+    std::vector<int> cs[3], pslab[3];
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < hm.nsub[d]; ++s) {
+            const int c = hm.off[d][s + 1] - hm.off[d][s];
+            if (c >= 2) {
+                cs[d].push_back(c / 2);
+                cs[d].push_back(c - c / 2);
+                pslab[d].push_back(s);
+                pslab[d].push_back(s);
+            } else {
+                cs[d].push_back(c);
+                pslab[d].push_back(s);
+            }
+        }
+    bddc_partition cp;
+    bddc_mesh mesh;
+    for (int d = 0; d < 3; ++d) {
+        cp.nsub[d] = (int)cs[d].size();
+        cp.elems_per_slab[d] = cs[d].data();
+        mesh.lo[d] = hm.lo[d];
+        mesh.hi[d] = hm.lo[d] + hm.h[d] * hm.E[d];
+    }
+    BDDC_TRY(build_host_boxes(&mesh, &cp, nd.child));
+    const HostMesh& ch = nd.child;
+    if (ch.ndof != hm.ndof || ch.E[0] != hm.E[0] || ch.E[1] != hm.E[1] || ch.E[2] != hm.E[2]) return BDDC_EINVAL;
+    nd.parent.assign(ch.nsd, -1);
+    for (int cz = 0; cz < ch.nsub[2]; ++cz)
+        for (int cy = 0; cy < ch.nsub[1]; ++cy)
+            for (int cx = 0; cx < ch.nsub[0]; ++cx)
+                nd.parent[cx + ch.nsub[0] * (cy + ch.nsub[1] * cz)] =
+                    pslab[0][cx] + hm.nsub[0] * (pslab[1][cy] + hm.nsub[1] * pslab[2][cz]);
+    const int Ex = hm.E[0], Ey = hm.E[1], Ez = hm.E[2];
+    auto dof_of = [&](int ix, int iy, int iz) -> int {
+        if (ix <= 0 || iy <= 0 || iz <= 0 || ix >= Ex || iy >= Ey || iz >= Ez) return -1;
+        return (ix - 1) + (Ex - 1) * ((iy - 1) + (Ey - 1) * (iz - 1));
+    };
+    // subdomain numbering [separators, interface], and a node -> new index table per box
+    std::vector<std::vector<int>> lidx(hm.nsd);
+    for (int s = 0; s < hm.nsd; ++s) {
+        SubInfo& S = hm.sub[s];
+        int mid[3], n[3];
+        for (int d = 0; d < 3; ++d) {
+            const int c = S.box1[d] - S.box0[d];
+            mid[d] = c >= 2 ? S.box0[d] + c / 2 : -1;
+            n[d] = c + 1;
+        }
+        std::vector<int>& L = lidx[s];
+        L.assign((size_t)n[0] * n[1] * n[2], -1);
+        std::vector<int> sep;
+        for (int pass = 0; pass < 2; ++pass) {       // separators first, then the interface
+            int nb = 0;
+            for (int iz = S.box0[2]; iz <= S.box1[2]; ++iz)
+                for (int iy = S.box0[1]; iy <= S.box1[1]; ++iy)
+                    for (int ix = S.box0[0]; ix <= S.box1[0]; ++ix) {
+                        const int g = dof_of(ix, iy, iz);
+                        if (g < 0) continue;
+                        const bool inside = S.box0[0] < ix && ix < S.box1[0] && S.box0[1] < iy && iy < S.box1[1] &&
+                                            S.box0[2] < iz && iz < S.box1[2];
+                        const long long q = (ix - S.box0[0]) + (long long)n[0] * ((iy - S.box0[1]) +
+                                                                                   (long long)n[1] * (iz - S.box0[2]));
+                        if (pass == 0 && inside && (ix == mid[0] || iy == mid[1] || iz == mid[2])) {
+                            L[q] = (int)sep.size();
+                            sep.push_back(g);
+                        } else if (pass == 1 && !inside) {
+                            L[q] = (int)sep.size() + nb++;
+                        }
+                    }
+            if (pass == 1 && nb != S.nB) return BDDC_EINVAL;
+        }
+        std::vector<int> dofs = sep;
+        dofs.insert(dofs.end(), S.dofs.begin() + S.nI, S.dofs.end());
+        S.dofs = std::move(dofs);
+        S.nI = (int)sep.size();
+        S.n = S.nI + S.nB;
+    }
+    // child interface dof -> subdomain-local index
+    nd.map.assign(ch.nsd, std::vector<int>());
+    for (int c = 0; c < ch.nsd; ++c) {
+        const SubInfo& K = ch.sub[c];
+        const int p = nd.parent[c];
+        if (p < 0) return BDDC_EINVAL;
+        const SubInfo& S = hm.sub[p];
+        const int n0 = S.box1[0] - S.box0[0] + 1, n1 = S.box1[1] - S.box0[1] + 1;
+        std::vector<int>& M = nd.map[c];
+        M.resize(K.nB);
+        for (int j = 0; j < K.nB; ++j) {
+            const int g = K.dofs[K.nI + j];
+            const int ix = g % (Ex - 1) + 1, iy = (g / (Ex - 1)) % (Ey - 1) + 1, iz = g / ((Ex - 1) * (Ey - 1)) + 1;
+            if (ix < S.box0[0] || ix > S.box1[0] || iy < S.box0[1] || iy > S.box1[1] || iz < S.box0[2] ||
+                iz > S.box1[2])
+                return BDDC_EINVAL;
+            const int li = lidx[p][(ix - S.box0[0]) + (long long)n0 * ((iy - S.box0[1]) + (long long)n1 * (iz - S.box0[2]))];
+            if (li < 0 || li >= S.n) return BDDC_EINVAL;
+            M[j] = li;
+        }
+    }
+    (void)Ez;
+    return BDDC_OK;
+}

@@ -269,6 +269,31 @@ template int copy_blocks_run<float, double>(const CopyJob*, int, int, cudaStream
 template int copy_blocks_run<float, float>(const CopyJob*, int, int, cudaStream_t);
 template int copy_blocks_run<double, float>(const CopyJob*, int, int, cudaStream_t);
 
+namespace {
+template <class T>
+__global__ void k_extend_add(const ExtendJob* __restrict__ jobs) {
+    const ExtendJob J = jobs[blockIdx.x];
+    const T* S = (const T*)J.src;
+    T* D = (T*)J.dst;
+    const long long nn = (long long)J.n * J.n;
+    for (long long q = (long long)blockIdx.y * TH + threadIdx.x; q < nn; q += (long long)gridDim.y * TH) {
+        const int a = (int)(q / J.n), b = (int)(q - (long long)a * J.n);
+        atomicAdd(&D[(long long)J.map[a] * J.dld + J.map[b]], S[(long long)a * J.sld + b]);
+    }
+}
+}  // namespace
+
+template <class T>
+int extend_add_run(const ExtendJob* jobs, int count, int ychunks, cudaStream_t st) {
+    if (count <= 0) return BDDC_OK;
+    k_extend_add<T><<<dim3(count, ychunks), TH, 0, st>>>(jobs);
+    bddc_note_launches(1);
+    BDDC_CUDA_TRY(cudaGetLastError());
+    return BDDC_OK;
+}
+template int extend_add_run<double>(const ExtendJob*, int, int, cudaStream_t);
+template int extend_add_run<float>(const ExtendJob*, int, int, cudaStream_t);
+
 template <class TD>
 int gather_perm_run(const GatherJob* jobs, int count, const int* idx, int ychunks, cudaStream_t st) {
     if (count <= 0) return BDDC_OK;

@@ -80,6 +80,20 @@ struct XRow {               // one CTA: the rows of one block of one subdomain
     int sub, blk;
 };
 
+// Extend-add of one child box's Schur complement into its subdomain's matrix:
+//   dst[map[a]][map[b]] += src[a][b]  (a, b < n; several children add into the
+// same separator and interface entries, so the adds are atomic).
+struct ExtendJob {
+    const void* src;        // the child's S (kernel precision), row stride sld
+    long long sld;
+    int n;
+    const int* map;         // n subdomain-local indices (device)
+    void* dst;              // the subdomain's matrix (kernel precision)
+    long long dld;
+};
+template <class T>
+int extend_add_run(const ExtendJob* jobs, int count, int ychunks, cudaStream_t st);
+
 template <class TD>
 int basis_run(const XRow* rows, int nrows, const XSub* subs, const XBlock* blks, int nmax, cudaStream_t st);
 size_t basis_smem(int nmax, size_t elem);
