@@ -10,7 +10,9 @@ none of the method's arithmetic.
 Modules
 -------
 mesh    tensor hexahedral mesh, tensor partition, interface classification
-fem     stabilised Q1 element integrals (Sect. 2), global assembly, direct solve
+fem     stabilised Q1 element integrals (Sect. 2), P1 on the six Kuhn
+        tetrahedra of each brick (Sect. 4, Example 4.1), lifting of
+        non-homogeneous Dirichlet values, global assembly, direct solve
 bddc    subdomain Schur complements, deluxe scaling, face GEP, new and
         conventional edge GEPs, primal constraints, the BDDC preconditioner
         (Sect. 3)
