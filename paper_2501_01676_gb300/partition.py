@@ -24,8 +24,8 @@ This module holds the host logic: rank blocks (contiguous boxes of the
 subdomain grid, so that the interface between ranks is a few planes), dof
 ownership, the neighbour lists, and the three exchanges written against a
 `torch.distributed`-like object.  The per-rank arithmetic is the library's
-kernels on the rank's own subdomains; with one GPU per process and no
-multi-GPU machine in this build, the partition is exercised by CPU ranks.
+kernels on the rank's own subdomains; the tests exercise the partition and
+the exchanges with CPU ranks (gloo).
 """
 from __future__ import annotations
 
