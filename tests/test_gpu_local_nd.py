@@ -102,3 +102,34 @@ def test_local_nd_example41_m16_matches_the_dense_elimination():
         assert rel(s.schur(sd), d.schur(sd)) < 1e-9
     s.close()
     d.close()
+
+
+def test_local_nd_full_size_jump_workload():
+    """The 8 x 8 x 8-subdomain jump workload (H/h = 8, 4096 child boxes) in the
+    mixed solver: the same constraint counts as the dense elimination, the global
+    FP64 residual at the 1e-8 rule, sampled S^(i) equal to the dense path's to
+    FP32 rounding."""
+    p = W.config3()
+    mesh = Mesh(p.slabs)
+    Ae, Fe, nodes = fem.element_matrices(mesh, p.nu_elem, p.beta_node, p.f_node, p.c)
+    A, F = fem.assemble_global(mesh, Ae, Fe, nodes)
+    d = B().Solver(p, precision=1)
+    s = B().Solver(p, precision=1, local_nd=1)
+    sd, ss = d.stats(), s.stats()
+    assert ss["nd_children"] == 4096
+    assert (ss["pnumF"], ss["pnumE"], ss["n_pi"]) == (sd["pnumF"], sd["pnumE"], sd["n_pi"])
+    for k in (0, 73, 292, 511):
+        assert rel(s.schur(k), d.schur(k)) < 1e-4, k
+    u, st = s.solve()
+    u = u.cpu().numpy()
+    assert st["converged"] and np.linalg.norm(F - A @ u) / np.linalg.norm(F) <= 1e-8
+    s.close()
+    d.close()
+    for nd in (0, 1):                       # warm second setups, for the record
+        t = B().Solver(p, precision=1, local_nd=nd)
+        _, sv = t.solve()
+        tt = t.stats()
+        print(f"local_nd={nd}: setup {tt['setup_ms']:.1f} ms (eliminations {tt['factor_gflop']:.1f} GFLOP, "
+              f"assembly phase {tt['t_assemble_ms']:.2f} ms, factor phase {tt['t_factor_ms']:.2f} ms) "
+              f"solve {sv['solve_ms']:.1f} ms, {sv['iters']} iterations")
+        t.close()
