@@ -16,9 +16,14 @@ not come from the oracle itself:
   through the lifting (this fails for a wrong sign or index in the lifting, a
   dropped term of the stabilisation, or a transposed convection term);
 * Example 4.1's data: the subdomain viscosities of Tests 1-3 and the boundary
-  values.
+  values;
+* the unit-cube brick matrices (diffusion, reaction, convection with its
+  stabilisation) against the exact rational integrals of
+  tests/golden/p1_unit_brick.txt (written by make_p1_unit_brick.py from the
+  tetrahedra's barycentric gradients alone).
 """
 import numpy as np
+import pytest
 
 from oracle import fem
 from oracle.mesh import Mesh
@@ -123,3 +128,43 @@ def test_example41_random_viscosity_data():
     assert np.array_equal(p.nu_elem, W.example41_random(n=3, m=2).nu_elem)
     ne, h, X, Y, Z = W._grid(p.slabs)
     assert np.all(p.dirichlet_node[Z == 0.0] == 1.0) and np.all(p.dirichlet_node[Z > 0.0] == 0.0)
+
+
+def _golden_p1():
+    """The exact P1 unit-cube integrals of tests/golden/p1_unit_brick.txt."""
+    from fractions import Fraction
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "p1_unit_brick.txt")
+    mats, cur = {}, None
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("["):
+                cur = line[1:-1]
+                mats[cur] = []
+            else:
+                mats[cur].append([float(Fraction(v)) for v in line.split()])
+    return {k: np.array(v) for k, v in mats.items()}
+
+
+@pytest.mark.parametrize("case", ["diffusion", "reaction", "convection"])
+def test_p1_unit_cube_against_golden_integrals(case):
+    """Unit cube, one brick of six tetrahedra: the oracle's P1 brick matrix against
+    the stored exact integrals combined by the bilinear form of Sect. 2 (tau = 0.7,
+    h_K = sqrt 3, here P_K < 1 on every tetrahedron: C_K = tau h_K^2 / (4 nu))."""
+    G = _golden_p1()
+    mesh = Mesh([[1], [1], [1]])
+    nu, c = 1.0, 0.0
+    beta = np.zeros(3)
+    if case == "reaction":
+        c = 1.0
+    if case == "convection":
+        beta = np.array([1.0, 0.0, 0.0])
+    A, _, _ = fem.element_matrices(mesh, np.full(1, nu), np.tile(beta, (8, 1)), np.zeros(8), c, element='p1')
+    CK = 0.7 * 3.0 / (4.0 * nu)
+    want = {"diffusion": G["K0"],
+            "reaction": G["K0"] + (1.0 + CK) * G["M"],
+            "convection": G["K0"] + CK * G["Kx"] + 0.5 * (G["Cx"] - G["Cx"].T)}[case]
+    np.testing.assert_allclose(A[0], want, rtol=0, atol=1e-14)
