@@ -20,7 +20,9 @@ not come from the oracle itself:
 * the unit-cube brick matrices (diffusion, reaction, convection with its
   stabilisation) against the exact rational integrals of
   tests/golden/p1_unit_brick.txt (written by make_p1_unit_brick.py from the
-  tetrahedra's barycentric gradients alone).
+  tetrahedra's barycentric gradients alone);
+* the advective stabilisation branch is homogeneous of degree one in beta, with
+  ||beta||_{K,inf} taken over all four vertices of each tetrahedron.
 """
 import numpy as np
 import pytest
@@ -168,3 +170,24 @@ def test_p1_unit_cube_against_golden_integrals(case):
             "reaction": G["K0"] + (1.0 + CK) * G["M"],
             "convection": G["K0"] + CK * G["Kx"] + 0.5 * (G["Cx"] - G["Cx"].T)}[case]
     np.testing.assert_allclose(A[0], want, rtol=0, atol=1e-14)
+
+
+def test_p1_advective_stabilisation_is_homogeneous_of_degree_one():
+    """In the advective branch (P_K >= 1) C_K = tau h_K / (2 ||beta||_{K,inf}) and the
+    GLS term is C_K int (beta.grad u)(beta.grad v), so with c = 0 the symmetric part of
+    the element matrix minus diffusion grows linearly in the size of beta.  Here beta
+    is non-zero only at the brick's node 7, a vertex of all six tetrahedra: the
+    vertex maximum must see it (a maximum over three of the four vertices would take
+    the diffusive branch and grow quadratically)."""
+    mesh = Mesh([[1], [1], [1]])
+    nu = 1e-8
+
+    def sym_part(scale):
+        beta = np.zeros((8, 3))
+        beta[7] = scale * np.array([0.6, -0.3, 0.9])
+        A, _, _ = fem.element_matrices(mesh, np.full(1, nu), beta, np.zeros(8), 0.0, element='p1')
+        return 0.5 * (A[0] + A[0].T)
+
+    S0, S1, S2 = sym_part(0.0), sym_part(1.0), sym_part(2.0)
+    assert np.abs(S1 - S0).max() > 1e-3
+    np.testing.assert_allclose(S2 - S0, 2.0 * (S1 - S0), rtol=1e-12, atol=1e-15)
