@@ -6,7 +6,9 @@ checks the plan's structure (children tile the subdomains, the maps hold the
 same global dofs, every interior dof is a separator or interior to one child)
 and its algebra: for random child matrices the Schur complement onto the
 interface by one dense elimination equals the children's Schur complements
-extend-added by the plan's maps with the separators eliminated afterwards.
+extend-added by the plan's maps with the separators eliminated afterwards, and
+condensation and recovery in the library's order (children, then separators;
+separators, then children) equal one dense condensation and recovery.
 """
 import os
 import shutil
