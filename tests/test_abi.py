@@ -97,3 +97,17 @@ def test_edge_modes_and_new_option_defaults():
                       "BDDC_EDGE_OLD": bddc.EDGE_OLD}
     o = bddc.default_opts()
     assert o.edge_gep == bddc.EDGE_NEW and o.apply_launch == 0 and o.cond_est == 1
+
+
+def test_element_constants_last_error_and_local_nd_default():
+    """The element constants equal the header's; the defaults are Q1 bricks and the
+    dense interior elimination; a rejected setup leaves its reason in
+    bddc_last_error (host-only: the null arguments are refused before device work)."""
+    from paper_2501_01676_gb300 import bddc
+    txt = open(os.path.join(ROOT, "include", "bddc.h")).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (BDDC_ELEM_\w+)\s+(\d+)", txt)}
+    assert consts == {"BDDC_ELEM_Q1": bddc.ELEM_Q1, "BDDC_ELEM_P1": bddc.ELEM_P1}
+    o = bddc.default_opts()
+    assert o.element == bddc.ELEM_Q1 and o.local_nd == 0
+    assert bddc.lib().bddc_setup(None, None, None, 0.0, None, None, None) == -1
+    assert isinstance(bddc.lib().bddc_last_error().decode(), str)
